@@ -1,0 +1,1081 @@
+/*
+ * oracle.c -- plain FP64 CPU oracle for the finite-volume time step of
+ * Clawpack-classic and SharpClaw (PyClaw, Ketcheson et al.).
+ *
+ * TEST INFRASTRUCTURE ONLY (see oracle.h).  Written for readability against
+ * the paper and the published methods it cites, not for speed: every step is
+ * a separate pass over whole arrays, in the order the method states it.
+ * OpenMP pragmas only split independent rows/columns; per-cell arithmetic and
+ * every reduction order are fixed, so results do not depend on thread count.
+ *
+ * Compiled with -O2 -ffp-contract=off (no FMA contraction).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+#include "oracle.h"
+
+#define MAXM 8
+#define MAXW 8
+
+/* ------------------------------------------------------------------------ */
+/* problem shape                                                             */
+/* ------------------------------------------------------------------------ */
+
+int orc_num_eqn(int rp, int ndim) {
+  switch (rp) {
+    case ORC_RP_ADVECTION: return 1;
+    case ORC_RP_ACOUSTICS: return ndim == 1 ? 2 : 3;
+    case ORC_RP_SW_ROE: return ndim == 1 ? 2 : 3;
+    case ORC_RP_EULER_ROE:
+    case ORC_RP_EULER_HLLE: return ndim == 1 ? 3 : 4;
+    case ORC_RP_ELASTICITY_FWAVE: return 2;
+  }
+  return 0;
+}
+
+int orc_num_waves(int rp, int ndim) {
+  switch (rp) {
+    case ORC_RP_ADVECTION: return 1;
+    case ORC_RP_ACOUSTICS: return 2;
+    case ORC_RP_SW_ROE: return ndim == 1 ? 2 : 3;
+    case ORC_RP_EULER_ROE: return ndim == 1 ? 3 : 4;
+    case ORC_RP_EULER_HLLE: return 2;
+    case ORC_RP_ELASTICITY_FWAVE: return 2;
+  }
+  return 0;
+}
+
+int orc_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* index of the momentum / velocity component normal to direction dir */
+static int comp_n(const orc_prob* P, int dir) { return P->ndim == 1 ? 1 : 1 + dir; }
+/* index of the tangential component (-1 in 1D) */
+static int comp_t(const orc_prob* P, int dir) { return P->ndim == 1 ? -1 : 2 - dir; }
+/* index of the energy component of the Euler equations */
+static int comp_e(const orc_prob* P) { return P->ndim == 1 ? 2 : 3; }
+static int is_fwave(const orc_prob* P) { return P->rp == ORC_RP_ELASTICITY_FWAVE; }
+
+/* ------------------------------------------------------------------------ */
+/* eigen-decompositions (LeVeque FVM book: acoustics, shallow water, Euler)  */
+/* Each helper works in a frame whose "normal" component is a and tangential */
+/* component b (b < 0: no tangential component).  Given a jump d it returns   */
+/* the eigen-coefficients alpha, eigenvectors r[p*m+k] and speeds lam[p].    */
+/* ------------------------------------------------------------------------ */
+
+/* Linear acoustics with constant rho, K: c = sqrt(K/rho), Z = rho c.
+ * r1 = (-Z, 1) speed -c, r2 = (Z, 1) speed +c on (p, u_a); when with_shear,
+ * a third zero-speed eigenvector (0, 0, 1) carries the tangential velocity. */
+static int acoustics_eig(const orc_prob* P, int a, int b, int with_shear, const double* d,
+                         double* alpha, double* r, double* lam) {
+  int m = P->num_eqn;
+  double rho = P->params[0], K = P->params[1];
+  double c = sqrt(K / rho);
+  double Z = rho * c;
+  int nw = (with_shear && b >= 0) ? 3 : 2;
+  memset(r, 0, sizeof(double) * nw * m);
+  alpha[0] = (-d[0] + Z * d[a]) / (2.0 * Z);
+  alpha[1] = (d[0] + Z * d[a]) / (2.0 * Z);
+  r[0 * m + 0] = -Z; r[0 * m + a] = 1.0; lam[0] = -c;
+  r[1 * m + 0] = Z;  r[1 * m + a] = 1.0; lam[1] = c;
+  if (nw == 3) { alpha[2] = d[b]; r[2 * m + b] = 1.0; lam[2] = 0.0; }
+  return nw;
+}
+
+/* Shallow water at a Roe state (un, ut, c = sqrt(g hbar)).  Waves ordered
+ * (un - c, [shear un], un + c). */
+static int sw_eig(const orc_prob* P, int a, int b, double un, double ut, double c,
+                  const double* d, double* alpha, double* r, double* lam) {
+  int m = P->num_eqn;
+  int nw = (b >= 0) ? 3 : 2;
+  int last = nw - 1;
+  memset(r, 0, sizeof(double) * nw * m);
+  alpha[0] = ((un + c) * d[0] - d[a]) / (2.0 * c);
+  alpha[last] = (d[a] - (un - c) * d[0]) / (2.0 * c);
+  r[0 * m + 0] = 1.0; r[0 * m + a] = un - c; lam[0] = un - c;
+  r[last * m + 0] = 1.0; r[last * m + a] = un + c; lam[last] = un + c;
+  if (b >= 0) {
+    alpha[1] = d[b] - ut * d[0];
+    r[0 * m + b] = ut;
+    r[1 * m + b] = 1.0; lam[1] = un;
+    r[last * m + b] = ut;
+  }
+  return nw;
+}
+
+/* Euler (ideal gas) at a Roe state (un, ut, H, c, c2 = c*c).  Waves ordered
+ * (un - c, entropy un, [shear un], un + c). */
+static int euler_eig(const orc_prob* P, int a, int b, double un, double ut, double H,
+                     double c, double c2, const double* d, double* alpha, double* r,
+                     double* lam) {
+  int m = P->num_eqn;
+  int e = comp_e(P);
+  double gm1 = P->params[0] - 1.0;
+  int nw = (b >= 0) ? 4 : 3;
+  int last = nw - 1;
+  double ash = (b >= 0) ? d[b] - ut * d[0] : 0.0;
+  double a2 = gm1 * ((H - un * un) * d[0] + un * d[a] - d[e] + ut * ash) / c2;
+  double a4 = (d[a] + (c - un) * d[0] - c * a2) / (2.0 * c);
+  double a1 = d[0] - a2 - a4;
+  memset(r, 0, sizeof(double) * nw * m);
+  alpha[0] = a1;
+  r[0 * m + 0] = 1.0; r[0 * m + a] = un - c; r[0 * m + e] = H - un * c; lam[0] = un - c;
+  alpha[1] = a2;
+  r[1 * m + 0] = 1.0; r[1 * m + a] = un; r[1 * m + e] = 0.5 * (un * un + ut * ut); lam[1] = un;
+  if (b >= 0) {
+    r[0 * m + b] = ut;
+    r[1 * m + b] = ut;
+    alpha[2] = ash;
+    r[2 * m + b] = 1.0; r[2 * m + e] = ut; lam[2] = un;
+    r[last * m + b] = ut;
+  }
+  alpha[last] = a4;
+  r[last * m + 0] = 1.0; r[last * m + a] = un + c; r[last * m + e] = H + un * c;
+  lam[last] = un + c;
+  return nw;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Roe averages                                                              */
+/* ------------------------------------------------------------------------ */
+
+/* shallow water: hbar = (hl+hr)/2, sqrt(h)-weighted velocities, c = sqrt(g hbar) */
+static void sw_roe_avg(const orc_prob* P, int dir, const double* ql, const double* qr,
+                       double* un, double* ut, double* c) {
+  int n = comp_n(P, dir), t = comp_t(P, dir);
+  double g = P->params[0];
+  double hl = ql[0], hr = qr[0];
+  double sl = sqrt(hl), sr = sqrt(hr);
+  double ul = ql[n] / hl, ur = qr[n] / hr;
+  double hbar = 0.5 * (hl + hr);
+  *un = (sl * ul + sr * ur) / (sl + sr);
+  if (t >= 0) {
+    double vl = ql[t] / hl, vr = qr[t] / hr;
+    *ut = (sl * vl + sr * vr) / (sl + sr);
+  } else {
+    *ut = 0.0;
+  }
+  *c = sqrt(g * hbar);
+}
+
+/* Euler pressure p = (gamma-1)(E - (mn^2 + mt^2)/(2 rho)) */
+static double euler_pressure(const orc_prob* P, const double* q) {
+  int e = comp_e(P);
+  double gm1 = P->params[0] - 1.0;
+  double ke = q[1] * q[1];
+  if (P->ndim == 2) ke = q[1] * q[1] + q[2] * q[2];
+  return gm1 * (q[e] - 0.5 * ke / q[0]);
+}
+
+/* Euler Roe averages: sqrt(rho)-weighted un, ut, H; c2 = (gamma-1)(H - (un^2+ut^2)/2) */
+static void euler_roe_avg(const orc_prob* P, int dir, const double* ql, const double* qr,
+                          double* un, double* ut, double* H, double* c, double* c2) {
+  int n = comp_n(P, dir), t = comp_t(P, dir), e = comp_e(P);
+  double gm1 = P->params[0] - 1.0;
+  double rl = ql[0], rr = qr[0];
+  double pl = euler_pressure(P, ql), pr = euler_pressure(P, qr);
+  double ul = ql[n] / rl, ur = qr[n] / rr;
+  double vl = 0.0, vr = 0.0;
+  if (t >= 0) { vl = ql[t] / rl; vr = qr[t] / rr; }
+  double Hl = (ql[e] + pl) / rl, Hr = (qr[e] + pr) / rr;
+  double sl = sqrt(rl), sr = sqrt(rr);
+  double den = sl + sr;
+  *un = (sl * ul + sr * ur) / den;
+  *ut = (sl * vl + sr * vr) / den;
+  *H = (sl * Hl + sr * Hr) / den;
+  *c2 = gm1 * (*H - 0.5 * (*un * *un + *ut * *ut));
+  *c = sqrt(*c2);
+}
+
+/* characteristic speeds u - c (which = 0) or u + c (which = 1) of one state */
+static double state_speed(const orc_prob* P, int dir, const double* q, int which) {
+  int n = comp_n(P, dir);
+  double u = q[n] / q[0];
+  double c;
+  if (P->rp == ORC_RP_SW_ROE) {
+    c = sqrt(P->params[0] * q[0]);
+  } else {
+    double p = euler_pressure(P, q);
+    c = sqrt(P->params[0] * p / q[0]);
+  }
+  return which == 0 ? u - c : u + c;
+}
+
+/* Euler flux in direction dir */
+static void euler_flux(const orc_prob* P, int dir, const double* q, double* f) {
+  int n = comp_n(P, dir), t = comp_t(P, dir), e = comp_e(P);
+  double p = euler_pressure(P, q);
+  double u = q[n] / q[0];
+  f[0] = q[n];
+  f[n] = q[n] * u + p;
+  if (t >= 0) f[t] = q[t] * u;
+  f[e] = u * (q[e] + p);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Riemann solvers (normal)                                                  */
+/* ------------------------------------------------------------------------ */
+
+static void split_by_speed(int m, int nw, const double* W, const double* s, double* amdq,
+                           double* apdq) {
+  for (int k = 0; k < m; ++k) { amdq[k] = 0.0; apdq[k] = 0.0; }
+  for (int p = 0; p < nw; ++p)
+    for (int k = 0; k < m; ++k) {
+      amdq[k] += fmin(s[p], 0.0) * W[p * m + k];
+      apdq[k] += fmax(s[p], 0.0) * W[p * m + k];
+    }
+}
+
+/* f-waves: A^-dQ = sum_{s<0} Z, A^+dQ = sum_{s>0} Z, s = 0 split half/half */
+static void split_fwaves(int m, int nw, const double* Z, const double* s, double* amdq,
+                         double* apdq) {
+  for (int k = 0; k < m; ++k) { amdq[k] = 0.0; apdq[k] = 0.0; }
+  for (int p = 0; p < nw; ++p)
+    for (int k = 0; k < m; ++k) {
+      if (s[p] < 0.0) amdq[k] += Z[p * m + k];
+      else if (s[p] > 0.0) apdq[k] += Z[p * m + k];
+      else { amdq[k] += 0.5 * Z[p * m + k]; apdq[k] += 0.5 * Z[p * m + k]; }
+    }
+}
+
+/* Harten-Hyman entropy fix for the first (u-c) and last (u+c) families.
+ * Returns 1 and writes amdq/apdq when a transonic rarefaction is found. */
+static int harten_hyman(const orc_prob* P, int dir, int m, int nw, const double* ql,
+                        const double* qr, const double* W, const double* s, double* amdq,
+                        double* apdq) {
+  double total[MAXM];
+  double qm[MAXM];
+  int last = nw - 1;
+  for (int k = 0; k < m; ++k) {
+    total[k] = 0.0;
+    for (int p = 0; p < nw; ++p) total[k] += s[p] * W[p * m + k];
+  }
+  /* family 1: middle state Q_l + W^1 */
+  for (int k = 0; k < m; ++k) qm[k] = ql[k] + W[0 * m + k];
+  {
+    double lamL = state_speed(P, dir, ql, 0);
+    double lamR = state_speed(P, dir, qm, 0);
+    if (lamL < 0.0 && lamR > 0.0) {
+      double beta = (lamR - s[0]) / (lamR - lamL);
+      for (int k = 0; k < m; ++k) {
+        amdq[k] = beta * lamL * W[0 * m + k];
+        apdq[k] = total[k] - amdq[k];
+      }
+      return 1;
+    }
+  }
+  /* last family: middle state Q_r - W^last */
+  for (int k = 0; k < m; ++k) qm[k] = qr[k] - W[last * m + k];
+  {
+    double lamL = state_speed(P, dir, qm, 1);
+    double lamR = state_speed(P, dir, qr, 1);
+    if (lamL < 0.0 && lamR > 0.0) {
+      double beta = (lamR - s[last]) / (lamR - lamL);
+      for (int k = 0; k < m; ++k) {
+        apdq[k] = (1.0 - beta) * lamR * W[last * m + k];
+        amdq[k] = total[k] - apdq[k];
+      }
+      return 1;
+    }
+  }
+  return 0;
+}
+
+void orc_riemann(const orc_prob* P, int dir, const double* ql, const double* qr,
+                 const double* auxl, const double* auxr, double* wave, double* s,
+                 double* amdq, double* apdq) {
+  int m = P->num_eqn;
+  int nw = orc_num_waves(P->rp, P->ndim);
+  int n = comp_n(P, dir), t = comp_t(P, dir);
+  double d[MAXM], alpha[MAXW], r[MAXW * MAXM];
+  for (int k = 0; k < m; ++k) d[k] = qr[k] - ql[k];
+  switch (P->rp) {
+    case ORC_RP_ADVECTION: {
+      wave[0] = d[0];
+      s[0] = P->params[dir];
+      break;
+    }
+    case ORC_RP_ACOUSTICS: {
+      acoustics_eig(P, n, t, 0, d, alpha, r, s);
+      for (int p = 0; p < nw; ++p)
+        for (int k = 0; k < m; ++k) wave[p * m + k] = alpha[p] * r[p * m + k];
+      break;
+    }
+    case ORC_RP_SW_ROE: {
+      double un, ut, c;
+      sw_roe_avg(P, dir, ql, qr, &un, &ut, &c);
+      sw_eig(P, n, t, un, ut, c, d, alpha, r, s);
+      for (int p = 0; p < nw; ++p)
+        for (int k = 0; k < m; ++k) wave[p * m + k] = alpha[p] * r[p * m + k];
+      break;
+    }
+    case ORC_RP_EULER_ROE: {
+      double un, ut, H, c, c2;
+      euler_roe_avg(P, dir, ql, qr, &un, &ut, &H, &c, &c2);
+      euler_eig(P, n, t, un, ut, H, c, c2, d, alpha, r, s);
+      for (int p = 0; p < nw; ++p)
+        for (int k = 0; k < m; ++k) wave[p * m + k] = alpha[p] * r[p * m + k];
+      break;
+    }
+    case ORC_RP_EULER_HLLE: {
+      double un, ut, H, c, c2;
+      double fl[MAXM], fr[MAXM], qs[MAXM];
+      euler_roe_avg(P, dir, ql, qr, &un, &ut, &H, &c, &c2);
+      double sl = fmin(state_speed(P, dir, ql, 0), un - c);
+      double sr = fmax(state_speed(P, dir, qr, 1), un + c);
+      euler_flux(P, dir, ql, fl);
+      euler_flux(P, dir, qr, fr);
+      for (int k = 0; k < m; ++k)
+        qs[k] = (fr[k] - fl[k] - sr * qr[k] + sl * ql[k]) / (sl - sr);
+      for (int k = 0; k < m; ++k) {
+        wave[0 * m + k] = qs[k] - ql[k];
+        wave[1 * m + k] = qr[k] - qs[k];
+      }
+      s[0] = sl;
+      s[1] = sr;
+      break;
+    }
+    case ORC_RP_ELASTICITY_FWAVE: {
+      /* sigma(eps) = exp(K eps) - 1, u = m / rho, flux f = (-u, -sigma) */
+      double rl = auxl[0], Kl = auxl[1], rr = auxr[0], Kr = auxr[1];
+      double el = exp(Kl * ql[0]), er = exp(Kr * qr[0]);
+      double sigl = el - 1.0, sigr = er - 1.0;
+      double ul = ql[1] / rl, ur = qr[1] / rr;
+      double cl = sqrt(Kl * el / rl), cr = sqrt(Kr * er / rr);
+      double Zl = rl * cl, Zr = rr * cr;
+      double d1 = ul - ur;       /* (-u_r) - (-u_l) */
+      double d2 = sigl - sigr;   /* (-sigma_r) - (-sigma_l) */
+      double b1 = (Zr * d1 + d2) / (Zl + Zr);
+      double b2 = (Zl * d1 - d2) / (Zl + Zr);
+      wave[0] = b1; wave[1] = b1 * Zl; s[0] = -cl;
+      wave[2] = b2; wave[3] = -b2 * Zr; s[1] = cr;
+      break;
+    }
+  }
+  if (is_fwave(P)) {
+    split_fwaves(m, nw, wave, s, amdq, apdq);
+    return;
+  }
+  if (P->entropy_fix && (P->rp == ORC_RP_SW_ROE || P->rp == ORC_RP_EULER_ROE)) {
+    if (harten_hyman(P, dir, m, nw, ql, qr, wave, s, amdq, apdq)) return;
+  }
+  split_by_speed(m, nw, wave, s, amdq, apdq);
+}
+
+/* ------------------------------------------------------------------------ */
+/* transverse solvers (2D)                                                   */
+/* ------------------------------------------------------------------------ */
+
+void orc_transverse(const orc_prob* P, int dir, const double* ql, const double* qr,
+                    const double* auxl, const double* auxr, const double* asdq,
+                    double* bmasdq, double* bpasdq) {
+  (void)auxl; (void)auxr;
+  int m = P->num_eqn;
+  int n = comp_n(P, dir), t = comp_t(P, dir);
+  int tdir = 1 - dir;
+  double beta[MAXW], r[MAXW * MAXM], lam[MAXW];
+  int nw = 0;
+  for (int k = 0; k < m; ++k) { bmasdq[k] = 0.0; bpasdq[k] = 0.0; }
+  switch (P->rp) {
+    case ORC_RP_ADVECTION: {
+      double v = P->params[tdir];
+      bmasdq[0] = fmin(v, 0.0) * asdq[0];
+      bpasdq[0] = fmax(v, 0.0) * asdq[0];
+      return;
+    }
+    case ORC_RP_ACOUSTICS:
+      /* eigenvectors of the transverse direction: frame normal = t */
+      nw = acoustics_eig(P, t, n, 0, asdq, beta, r, lam);
+      break;
+    case ORC_RP_SW_ROE: {
+      double un, ut, c;
+      sw_roe_avg(P, dir, ql, qr, &un, &ut, &c);
+      nw = sw_eig(P, t, n, ut, un, c, asdq, beta, r, lam);
+      break;
+    }
+    case ORC_RP_EULER_ROE:
+    case ORC_RP_EULER_HLLE: {
+      double un, ut, H, c, c2;
+      euler_roe_avg(P, dir, ql, qr, &un, &ut, &H, &c, &c2);
+      nw = euler_eig(P, t, n, ut, un, H, c, c2, asdq, beta, r, lam);
+      break;
+    }
+    default:
+      return;
+  }
+  for (int p = 0; p < nw; ++p)
+    for (int k = 0; k < m; ++k) {
+      bmasdq[k] += fmin(lam[p], 0.0) * beta[p] * r[p * m + k];
+      bpasdq[k] += fmax(lam[p], 0.0) * beta[p] * r[p * m + k];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* characteristic matrices for SharpClaw (Roe state of the interface)        */
+/* ------------------------------------------------------------------------ */
+
+int orc_char_matrices(const orc_prob* P, int dir, const double* ql, const double* qr,
+                      double* Lmat, double* Rmat) {
+  int m = P->num_eqn;
+  int n = comp_n(P, dir), t = comp_t(P, dir);
+  double e[MAXM], alpha[MAXW], r[MAXW * MAXM], lam[MAXW];
+  double un = 0, ut = 0, H = 0, c = 0, c2 = 0;
+  if (P->rp == ORC_RP_ELASTICITY_FWAVE) return ORC_EINVAL;
+  if (P->rp == ORC_RP_SW_ROE) sw_roe_avg(P, dir, ql, qr, &un, &ut, &c);
+  if (P->rp == ORC_RP_EULER_ROE || P->rp == ORC_RP_EULER_HLLE)
+    euler_roe_avg(P, dir, ql, qr, &un, &ut, &H, &c, &c2);
+  for (int col = 0; col < m; ++col) {
+    for (int k = 0; k < m; ++k) e[k] = (k == col) ? 1.0 : 0.0;
+    switch (P->rp) {
+      case ORC_RP_ADVECTION: alpha[0] = e[0]; r[0] = 1.0; break;
+      case ORC_RP_ACOUSTICS: acoustics_eig(P, n, t, 1, e, alpha, r, lam); break;
+      case ORC_RP_SW_ROE: sw_eig(P, n, t, un, ut, c, e, alpha, r, lam); break;
+      default: euler_eig(P, n, t, un, ut, H, c, c2, e, alpha, r, lam); break;
+    }
+    /* column col of L is L e_col = alpha */
+    for (int p = 0; p < m; ++p) Lmat[p * m + col] = alpha[p];
+  }
+  /* R[k][p] = r_p[k] */
+  for (int p = 0; p < m; ++p)
+    for (int k = 0; k < m; ++k) Rmat[k * m + p] = r[p * m + k];
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* limiters (LeVeque FVM book, Sec. 6.9)                                     */
+/* ------------------------------------------------------------------------ */
+
+double orc_phi(int lim, double th) {
+  switch (lim) {
+    case ORC_LIM_MINMOD: return fmax(0.0, fmin(1.0, th));
+    case ORC_LIM_SUPERBEE: return fmax(0.0, fmax(fmin(1.0, 2.0 * th), fmin(2.0, th)));
+    case ORC_LIM_VANLEER: return (th + fabs(th)) / (1.0 + fabs(th));
+    case ORC_LIM_MC: return fmax(0.0, fmin((1.0 + th) / 2.0, fmin(2.0, 2.0 * th)));
+    default: return 1.0;
+  }
+}
+
+/* Second-order correction flux at one interface (Eq. (lwflux), LeVeque 1997):
+ * F = 1/2 sum_p c_p Wlim^p, c_p = |s|(1 - dt/dx |s|) (waves) or
+ * sign(s)(1 - dt/dx |s|) (f-waves).  Wlim^p = phi(theta) W^p with
+ * theta = (W^p_up . W^p)/(W^p . W^p), upwind side by the sign of s^p
+ * (s > 0: left neighbour, otherwise right); a zero wave stays zero. */
+static void correction_flux(const orc_prob* P, int m, int nw, const double* Wl,
+                            const double* W, const double* Wr, const double* s, double dtdx,
+                            double* F) {
+  double Wt[MAXW * MAXM];
+  for (int p = 0; p < nw; ++p) {
+    double nrm = 0.0;
+    for (int k = 0; k < m; ++k) nrm += W[p * m + k] * W[p * m + k];
+    double phi = 1.0;
+    if (nrm == 0.0) {
+      phi = 0.0;
+    } else if (P->lim != ORC_LIM_NONE) {
+      const double* Wu = (s[p] > 0.0) ? Wl : Wr;
+      double dot = 0.0;
+      for (int k = 0; k < m; ++k) dot += Wu[p * m + k] * W[p * m + k];
+      phi = orc_phi(P->lim, dot / nrm);
+    }
+    for (int k = 0; k < m; ++k) Wt[p * m + k] = phi * W[p * m + k];
+  }
+  for (int k = 0; k < m; ++k) {
+    double acc = 0.0;
+    for (int p = 0; p < nw; ++p) {
+      double a = fabs(s[p]);
+      double sg = is_fwave(P) ? (s[p] > 0.0 ? 1.0 : (s[p] < 0.0 ? -1.0 : 0.0)) : a;
+      acc += sg * (1.0 - dtdx * a) * Wt[p * m + k];
+    }
+    F[k] = 0.5 * acc;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* ghost cells (Sec. 5: periodic, reflecting, outflow, inflow)               */
+/* ------------------------------------------------------------------------ */
+
+static int wall_comp(const orc_prob* P, int dir) {
+  if (P->rp == ORC_RP_ADVECTION) return -1;
+  return comp_n(P, dir);
+}
+
+/* value of ghost cell index i (outside 0..n-1) along one direction */
+static void ghost_source(int bc, int n, int i, int* src, int* mirror) {
+  *mirror = 0;
+  if (i < 0) {
+    int k = -i; /* 1..g */
+    if (bc == ORC_BC_PERIODIC) *src = n - k;
+    else if (bc == ORC_BC_WALL) { *src = k - 1; *mirror = 1; }
+    else *src = 0;
+  } else {
+    int k = i - (n - 1);
+    if (bc == ORC_BC_PERIODIC) *src = k - 1;
+    else if (bc == ORC_BC_WALL) { *src = n - k; *mirror = 1; }
+    else *src = n - 1;
+  }
+}
+
+void orc_fill_ghost(const orc_prob* P, const double* q, int ncomp, int g, int is_aux,
+                    double* qg) {
+  int nx = P->nx, ny = (P->ndim == 2) ? P->ny : 1;
+  int gy = (P->ndim == 2) ? g : 0;
+  int NX = nx + 2 * g, NY = ny + 2 * gy;
+  size_t plane = (size_t)NX * NY;
+  for (int c = 0; c < ncomp; ++c)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i)
+        qg[c * plane + (size_t)(j + gy) * NX + (i + g)] = q[(size_t)c * nx * ny + (size_t)j * nx + i];
+  /* x ghosts on interior rows */
+  for (int j = 0; j < ny; ++j)
+    for (int side = 0; side < 2; ++side)
+      for (int k = 1; k <= g; ++k) {
+        int i = side == 0 ? -k : nx - 1 + k;
+        int bc = side == 0 ? P->bc_lo[0] : P->bc_hi[0];
+        int src, mir;
+        ghost_source(bc, nx, i, &src, &mir);
+        for (int c = 0; c < ncomp; ++c) {
+          double v = qg[c * plane + (size_t)(j + gy) * NX + (src + g)];
+          if (!is_aux) {
+            if (bc == ORC_BC_INFLOW) v = P->inflow[c];
+            else if (mir && c == wall_comp(P, 0)) v = -v;
+          }
+          qg[c * plane + (size_t)(j + gy) * NX + (i + g)] = v;
+        }
+      }
+  if (P->ndim < 2) return;
+  /* y ghosts on all columns, including the x ghosts (defines the corners) */
+  for (int i = -g; i < nx + g; ++i)
+    for (int side = 0; side < 2; ++side)
+      for (int k = 1; k <= g; ++k) {
+        int j = side == 0 ? -k : ny - 1 + k;
+        int bc = side == 0 ? P->bc_lo[1] : P->bc_hi[1];
+        int src, mir;
+        ghost_source(bc, ny, j, &src, &mir);
+        for (int c = 0; c < ncomp; ++c) {
+          double v = qg[c * plane + (size_t)(src + gy) * NX + (i + g)];
+          if (!is_aux) {
+            if (bc == ORC_BC_INFLOW) v = P->inflow[c];
+            else if (mir && c == wall_comp(P, 1)) v = -v;
+          }
+          qg[c * plane + (size_t)(j + gy) * NX + (i + g)] = v;
+        }
+      }
+}
+
+/* ------------------------------------------------------------------------ */
+/* helpers to read one cell of a ghosted array                               */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  const double* a;
+  int ncomp, NX, NY, g, gy;
+} garr;
+
+static void gcell(const garr* G, int i, int j, double* out) {
+  size_t plane = (size_t)G->NX * G->NY;
+  size_t off = (size_t)(j + G->gy) * G->NX + (i + G->g);
+  for (int c = 0; c < G->ncomp; ++c) out[c] = G->a[c * plane + off];
+}
+
+static double* ghosted(const orc_prob* P, const double* q, int ncomp, int g, int is_aux,
+                       garr* G) {
+  int ny = (P->ndim == 2) ? P->ny : 1;
+  int gy = (P->ndim == 2) ? g : 0;
+  G->ncomp = ncomp; G->g = g; G->gy = gy;
+  G->NX = P->nx + 2 * g; G->NY = ny + 2 * gy;
+  double* buf = (double*)malloc(sizeof(double) * (size_t)ncomp * G->NX * G->NY + 8);
+  if (ncomp > 0) orc_fill_ghost(P, q, ncomp, g, is_aux, buf);
+  G->a = buf;
+  return buf;
+}
+
+/* ------------------------------------------------------------------------ */
+/* classic 1D step (Eq. (fluxdiff) with Eq. (lwflux) in fluctuation form)   */
+/* ------------------------------------------------------------------------ */
+
+static int classic1d(const orc_prob* P, double* q, const double* aux, double dt, double* cfl) {
+  int N = P->nx, m = P->num_eqn, ma = P->num_aux;
+  int nw = orc_num_waves(P->rp, 1);
+  double dtdx = dt / P->dx;
+  garr Q, A;
+  double* qb = ghosted(P, q, m, 2, 0, &Q);
+  double* ab = ghosted(P, aux, ma, 2, 1, &A);
+  int nint = N + 3; /* interfaces i = -1 .. N+1, stored at i+1 */
+  double* W = (double*)malloc(sizeof(double) * nint * nw * m);
+  double* S = (double*)malloc(sizeof(double) * nint * nw);
+  double* AM = (double*)malloc(sizeof(double) * nint * m);
+  double* AP = (double*)malloc(sizeof(double) * nint * m);
+  double* F = (double*)calloc((size_t)(N + 1) * m, sizeof(double));
+  double smax = 0.0;
+  for (int i = -1; i <= N + 1; ++i) {
+    double ql[MAXM], qr[MAXM], al[MAXM] = {0}, ar[MAXM] = {0};
+    gcell(&Q, i - 1, 0, ql);
+    gcell(&Q, i, 0, qr);
+    if (ma) { gcell(&A, i - 1, 0, al); gcell(&A, i, 0, ar); }
+    int ii = i + 1;
+    orc_riemann(P, 0, ql, qr, al, ar, W + ii * nw * m, S + ii * nw, AM + ii * m, AP + ii * m);
+    if (i >= 0 && i <= N)
+      for (int p = 0; p < nw; ++p) {
+        double a = fabs(S[ii * nw + p]);
+        if (!(a <= smax)) smax = a; /* NaN propagates */
+      }
+  }
+  if (P->order == 2)
+    for (int i = 0; i <= N; ++i) {
+      int ii = i + 1;
+      correction_flux(P, m, nw, W + (ii - 1) * nw * m, W + ii * nw * m, W + (ii + 1) * nw * m,
+                      S + ii * nw, dtdx, F + i * m);
+    }
+  for (int i = 0; i < N; ++i)
+    for (int k = 0; k < m; ++k) {
+      double* qk = q + (size_t)k * N + i;
+      *qk = *qk - dtdx * (AP[(i + 1) * m + k] + AM[(i + 2) * m + k]) -
+            dtdx * (F[(i + 1) * m + k] - F[i * m + k]);
+    }
+  *cfl = dt * smax / P->dx;
+  free(qb); free(ab); free(W); free(S); free(AM); free(AP); free(F);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* classic 2D unsplit step with transverse propagation (LeVeque 1997)        */
+/* ------------------------------------------------------------------------ */
+
+/* per x-interface (or y-interface) record */
+typedef struct {
+  double amdq[MAXM], apdq[MAXM], F[MAXM];
+  double bm_ap[MAXM], bp_ap[MAXM], bm_am[MAXM], bp_am[MAXM];
+} iface_rec;
+
+/* One sweep in direction dir over lines; fills recs for interfaces 0..n of
+ * lines -1..nl (line index l stored at l+1) and the per-line max speed. */
+static void sweep(const orc_prob* P, int dir, const garr* Q, const garr* A, double dtdn,
+                  iface_rec* recs, double* line_smax) {
+  int m = P->num_eqn, ma = P->num_aux;
+  int nw = orc_num_waves(P->rp, 2);
+  int n = dir == 0 ? P->nx : P->ny;   /* cells along the line */
+  int nl = dir == 0 ? P->ny : P->nx;  /* number of interior lines */
+  #pragma omp parallel for schedule(static)
+  for (int l = -1; l <= nl; ++l) {
+    int nint = n + 3;
+    double* W = (double*)malloc(sizeof(double) * nint * nw * m);
+    double* S = (double*)malloc(sizeof(double) * nint * nw);
+    double* AM = (double*)malloc(sizeof(double) * nint * m);
+    double* AP = (double*)malloc(sizeof(double) * nint * m);
+    double smax = 0.0;
+    for (int i = -1; i <= n + 1; ++i) {
+      double ql[MAXM], qr[MAXM], al[MAXM] = {0}, ar[MAXM] = {0};
+      if (dir == 0) { gcell(Q, i - 1, l, ql); gcell(Q, i, l, qr); }
+      else { gcell(Q, l, i - 1, ql); gcell(Q, l, i, qr); }
+      if (ma) {
+        if (dir == 0) { gcell(A, i - 1, l, al); gcell(A, i, l, ar); }
+        else { gcell(A, l, i - 1, al); gcell(A, l, i, ar); }
+      }
+      int ii = i + 1;
+      orc_riemann(P, dir, ql, qr, al, ar, W + ii * nw * m, S + ii * nw, AM + ii * m, AP + ii * m);
+      if (i >= 0 && i <= n && l >= 0 && l < nl)
+        for (int p = 0; p < nw; ++p) {
+          double a = fabs(S[ii * nw + p]);
+          if (!(a <= smax)) smax = a;
+        }
+    }
+    line_smax[l + 1] = smax;
+    for (int i = 0; i <= n; ++i) {
+      int ii = i + 1;
+      iface_rec* R = recs + (size_t)(l + 1) * (n + 1) + i;
+      for (int k = 0; k < m; ++k) {
+        R->amdq[k] = AM[ii * m + k];
+        R->apdq[k] = AP[ii * m + k];
+        R->F[k] = 0.0;
+      }
+      if (P->order == 2)
+        correction_flux(P, m, nw, W + (ii - 1) * nw * m, W + ii * nw * m,
+                        W + (ii + 1) * nw * m, S + ii * nw, dtdn, R->F);
+      if (P->transverse) {
+        double ql[MAXM], qr[MAXM], al[MAXM] = {0}, ar[MAXM] = {0};
+        double ap[MAXM], am[MAXM];
+        if (dir == 0) { gcell(Q, i - 1, l, ql); gcell(Q, i, l, qr); }
+        else { gcell(Q, l, i - 1, ql); gcell(Q, l, i, qr); }
+        if (ma) {
+          if (dir == 0) { gcell(A, i - 1, l, al); gcell(A, i, l, ar); }
+          else { gcell(A, l, i - 1, al); gcell(A, l, i, ar); }
+        }
+        for (int k = 0; k < m; ++k) {
+          if (P->transverse == 2) {
+            ap[k] = R->apdq[k] - R->F[k];
+            am[k] = R->amdq[k] + R->F[k];
+          } else {
+            ap[k] = R->apdq[k];
+            am[k] = R->amdq[k];
+          }
+        }
+        orc_transverse(P, dir, ql, qr, al, ar, ap, R->bm_ap, R->bp_ap);
+        orc_transverse(P, dir, ql, qr, al, ar, am, R->bm_am, R->bp_am);
+      } else {
+        for (int k = 0; k < m; ++k) {
+          R->bm_ap[k] = 0.0; R->bp_ap[k] = 0.0; R->bm_am[k] = 0.0; R->bp_am[k] = 0.0;
+        }
+      }
+    }
+    free(W); free(S); free(AM); free(AP);
+  }
+}
+
+static int classic2d(const orc_prob* P, double* q, const double* aux, double dt, double* cfl) {
+  int nx = P->nx, ny = P->ny, m = P->num_eqn, ma = P->num_aux;
+  double dtdx = dt / P->dx, dtdy = dt / P->dy;
+  garr Q, A;
+  double* qb = ghosted(P, q, m, 2, 0, &Q);
+  double* ab = ghosted(P, aux, ma, 2, 1, &A);
+  /* x-interfaces: i = 0..nx on rows -1..ny ; y-interfaces: j = 0..ny on columns -1..nx */
+  iface_rec* X = (iface_rec*)malloc(sizeof(iface_rec) * (size_t)(ny + 2) * (nx + 1));
+  iface_rec* Y = (iface_rec*)malloc(sizeof(iface_rec) * (size_t)(nx + 2) * (ny + 1));
+  double* smx = (double*)malloc(sizeof(double) * (ny + 2));
+  double* smy = (double*)malloc(sizeof(double) * (nx + 2));
+  sweep(P, 0, &Q, &A, dtdx, X, smx);
+  sweep(P, 1, &Q, &A, dtdy, Y, smy);
+#define XR(i, j) (X + (size_t)((j) + 1) * (nx + 1) + (i))
+#define YR(i, j) (Y + (size_t)((i) + 1) * (ny + 1) + (j))
+  /* total correction fluxes: normal part plus transverse contributions */
+  double* Ft = (double*)malloc(sizeof(double) * (size_t)ny * (nx + 1) * m);
+  double* Gt = (double*)malloc(sizeof(double) * (size_t)nx * (ny + 1) * m);
+  #pragma omp parallel for schedule(static)
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i <= nx; ++i)
+      for (int k = 0; k < m; ++k) {
+        /* x-interface (i,j) receives A^+ b^+ of y-interface (i-1, j), A^- b^+ of (i, j),
+           A^+ b^- of (i-1, j+1) and A^- b^- of (i, j+1) */
+        double tr = YR(i - 1, j)->bp_ap[k] + YR(i, j)->bm_ap[k] + YR(i - 1, j + 1)->bp_am[k] +
+                    YR(i, j + 1)->bm_am[k];
+        Ft[((size_t)j * (nx + 1) + i) * m + k] = XR(i, j)->F[k] - 0.5 * dtdy * tr;
+      }
+  #pragma omp parallel for schedule(static)
+  for (int i = 0; i < nx; ++i)
+    for (int j = 0; j <= ny; ++j)
+      for (int k = 0; k < m; ++k) {
+        /* y-interface (i,j) receives B^+ a^+ of x-interface (i, j-1), B^- a^+ of (i, j),
+           B^+ a^- of (i+1, j-1) and B^- a^- of (i+1, j) */
+        double tr = XR(i, j - 1)->bp_ap[k] + XR(i, j)->bm_ap[k] + XR(i + 1, j - 1)->bp_am[k] +
+                    XR(i + 1, j)->bm_am[k];
+        Gt[((size_t)i * (ny + 1) + j) * m + k] = YR(i, j)->F[k] - 0.5 * dtdx * tr;
+      }
+  #pragma omp parallel for schedule(static)
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i)
+      for (int k = 0; k < m; ++k) {
+        double* qk = q + (size_t)k * nx * ny + (size_t)j * nx + i;
+        double fl = Ft[((size_t)j * (nx + 1) + i) * m + k];
+        double fr = Ft[((size_t)j * (nx + 1) + i + 1) * m + k];
+        double gb = Gt[((size_t)i * (ny + 1) + j) * m + k];
+        double gtp = Gt[((size_t)i * (ny + 1) + j + 1) * m + k];
+        *qk = *qk - dtdx * (XR(i, j)->apdq[k] + XR(i + 1, j)->amdq[k]) -
+              dtdy * (YR(i, j)->apdq[k] + YR(i, j + 1)->amdq[k]) - dtdx * (fr - fl) -
+              dtdy * (gtp - gb);
+      }
+#undef XR
+#undef YR
+  double sx = 0.0, sy = 0.0;
+  for (int l = 0; l < ny + 2; ++l) if (!(smx[l] <= sx)) sx = smx[l];
+  for (int l = 0; l < nx + 2; ++l) if (!(smy[l] <= sy)) sy = smy[l];
+  double nx_ = dt * sx / P->dx, ny_ = dt * sy / P->dy;
+  *cfl = (nx_ >= ny_ || isnan(nx_)) ? nx_ : ny_;
+  free(qb); free(ab); free(X); free(Y); free(smx); free(smy); free(Ft); free(Gt);
+  return ORC_OK;
+}
+
+int orc_classic_step(const orc_prob* P, double* q, const double* aux, double dt, double* cfl) {
+  if (P->ndim == 1) return classic1d(P, q, aux, dt, cfl);
+  return classic2d(P, q, aux, dt, cfl);
+}
+
+/* ------------------------------------------------------------------------ */
+/* SharpClaw: WENO5 reconstruction + fluctuations + SSP-RK3                  */
+/* ------------------------------------------------------------------------ */
+
+/* Jiang-Shu WENO5, left-biased value at x_{i+1/2} from v_{i-2..i+2} */
+double orc_weno5(const double* v, double eps) {
+  double a = v[0], b = v[1], c = v[2], d = v[3], e = v[4];
+  double q0 = (2.0 * a - 7.0 * b + 11.0 * c) / 6.0;
+  double q1 = (-b + 5.0 * c + 2.0 * d) / 6.0;
+  double q2 = (2.0 * c + 5.0 * d - e) / 6.0;
+  double t0 = a - 2.0 * b + c, u0 = a - 4.0 * b + 3.0 * c;
+  double t1 = b - 2.0 * c + d, u1 = b - d;
+  double t2 = c - 2.0 * d + e, u2 = 3.0 * c - 4.0 * d + e;
+  double b0 = 13.0 / 12.0 * (t0 * t0) + 0.25 * (u0 * u0);
+  double b1 = 13.0 / 12.0 * (t1 * t1) + 0.25 * (u1 * u1);
+  double b2 = 13.0 / 12.0 * (t2 * t2) + 0.25 * (u2 * u2);
+  double e0 = eps + b0, e1 = eps + b1, e2 = eps + b2;
+  double a0 = 0.1 / (e0 * e0), a1 = 0.6 / (e1 * e1), a2 = 0.3 / (e2 * e2);
+  double sum = a0 + a1 + a2;
+  return (a0 * q0 + a1 * q1 + a2 * q2) / sum;
+}
+
+int orc_sharp_L(const orc_prob* P, const double* q, const double* aux, double* L, double* smax) {
+  int m = P->num_eqn, ma = P->num_aux;
+  int nx = P->nx, ny = (P->ndim == 2) ? P->ny : 1;
+  size_t ncell = (size_t)nx * ny;
+  garr Q, A;
+  double* qb = ghosted(P, q, m, 3, 0, &Q);
+  double* ab = ghosted(P, aux, ma, 3, 1, &A);
+  if (P->char_decomp && P->rp == ORC_RP_ELASTICITY_FWAVE) { free(qb); free(ab); return ORC_EINVAL; }
+  for (size_t c = 0; c < ncell * m; ++c) L[c] = 0.0;
+  smax[0] = 0.0; smax[1] = 0.0;
+  for (int dir = 0; dir < P->ndim; ++dir) {
+    int n = dir == 0 ? nx : ny;
+    int nl = dir == 0 ? ny : nx;
+    double dn = dir == 0 ? P->dx : P->dy;
+    double* lmax = (double*)calloc(nl, sizeof(double));
+    #pragma omp parallel for schedule(static)
+    for (int l = 0; l < nl; ++l) {
+      double* qL = (double*)malloc(sizeof(double) * (n + 1) * m);  /* left edge of cell i   */
+      double* qR = (double*)malloc(sizeof(double) * (n + 1) * m);  /* right edge of cell i-1 */
+      double* AM = (double*)malloc(sizeof(double) * (n + 1) * m);
+      double* AP = (double*)malloc(sizeof(double) * (n + 1) * m);
+      double sm = 0.0;
+      /* reconstruction at every interface i - 1/2, i = 0..n */
+      for (int i = 0; i <= n; ++i) {
+        double cells[6][MAXM], w[6][MAXM];
+        double Lm[MAXM * MAXM], Rm[MAXM * MAXM];
+        for (int k6 = 0; k6 < 6; ++k6) {
+          int ci = i - 3 + k6;
+          if (dir == 0) gcell(&Q, ci, l, cells[k6]); else gcell(&Q, l, ci, cells[k6]);
+        }
+        if (P->char_decomp) {
+          orc_char_matrices(P, dir, cells[2], cells[3], Lm, Rm);
+          for (int k6 = 0; k6 < 6; ++k6)
+            for (int p = 0; p < m; ++p) {
+              double acc = 0.0;
+              for (int k = 0; k < m; ++k) acc += Lm[p * m + k] * cells[k6][k];
+              w[k6][p] = acc;
+            }
+        } else {
+          for (int k6 = 0; k6 < 6; ++k6)
+            for (int p = 0; p < m; ++p) w[k6][p] = cells[k6][p];
+        }
+        double wm[MAXM], wp[MAXM];
+        for (int p = 0; p < m; ++p) {
+          double v[5];
+          for (int k = 0; k < 5; ++k) v[k] = w[k][p];        /* cells i-3..i+1 */
+          wm[p] = orc_weno5(v, P->weno_eps);                  /* right edge of cell i-1 */
+          for (int k = 0; k < 5; ++k) v[k] = w[5 - k][p];    /* cells i+2..i-2 */
+          wp[p] = orc_weno5(v, P->weno_eps);                  /* left edge of cell i */
+        }
+        for (int k = 0; k < m; ++k) {
+          if (P->char_decomp) {
+            double am = 0.0, ap = 0.0;
+            for (int p = 0; p < m; ++p) { am += Rm[k * m + p] * wm[p]; ap += Rm[k * m + p] * wp[p]; }
+            qR[i * m + k] = am;
+            qL[i * m + k] = ap;
+          } else {
+            qR[i * m + k] = wm[k];
+            qL[i * m + k] = wp[k];
+          }
+        }
+      }
+      /* interface Riemann problems (q^R_{i-1}, q^L_i) */
+      for (int i = 0; i <= n; ++i) {
+        double al[MAXM] = {0}, ar[MAXM] = {0};
+        double W[MAXW * MAXM], S[MAXW];
+        if (ma) {
+          if (dir == 0) { gcell(&A, i - 1, l, al); gcell(&A, i, l, ar); }
+          else { gcell(&A, l, i - 1, al); gcell(&A, l, i, ar); }
+        }
+        orc_riemann(P, dir, qR + i * m, qL + i * m, al, ar, W, S, AM + i * m, AP + i * m);
+        for (int p = 0; p < orc_num_waves(P->rp, P->ndim); ++p) {
+          double a = fabs(S[p]);
+          if (!(a <= sm)) sm = a;
+        }
+      }
+      /* total fluctuation inside each cell: Riemann problem (q^L_i, q^R_i) */
+      for (int i = 0; i < n; ++i) {
+        double al[MAXM] = {0};
+        double W[MAXW * MAXM], S[MAXW], am[MAXM], ap[MAXM];
+        if (ma) { if (dir == 0) gcell(&A, i, l, al); else gcell(&A, l, i, al); }
+        orc_riemann(P, dir, qL + i * m, qR + (i + 1) * m, al, al, W, S, am, ap);
+        size_t cell = dir == 0 ? (size_t)l * nx + i : (size_t)i * nx + l;
+        for (int k = 0; k < m; ++k) {
+          double adq = am[k] + ap[k];
+          L[(size_t)k * ncell + cell] =
+              L[(size_t)k * ncell + cell] - (AP[i * m + k] + AM[(i + 1) * m + k] + adq) / dn;
+        }
+      }
+      lmax[l] = sm;
+      free(qL); free(qR); free(AM); free(AP);
+    }
+    for (int l = 0; l < nl; ++l) if (!(lmax[l] <= smax[dir])) smax[dir] = lmax[l];
+    free(lmax);
+  }
+  free(qb); free(ab);
+  return ORC_OK;
+}
+
+/* Shu-Osher SSP-RK3 stage: out = a_k Q^n + b_k (Q^(k) + dt L(Q^(k))) */
+static double rk3_stage(int stage, double qn, double qk, double Lk, double dt) {
+  if (stage == 0) return qk + dt * Lk;
+  if (stage == 1) return 0.75 * qn + 0.25 * (qk + dt * Lk);
+  return (1.0 / 3.0) * qn + (2.0 / 3.0) * (qk + dt * Lk);
+}
+
+double orc_ssp_rk3_linear(double lambda, double dt, double q0) {
+  double q1 = rk3_stage(0, q0, q0, lambda * q0, dt);
+  double q2 = rk3_stage(1, q0, q1, lambda * q1, dt);
+  return rk3_stage(2, q0, q2, lambda * q2, dt);
+}
+
+int orc_sharp_step(const orc_prob* P, double* q, const double* aux, double dt, double* cfl) {
+  int ny = (P->ndim == 2) ? P->ny : 1;
+  size_t ntot = (size_t)P->nx * ny * P->num_eqn;
+  double* qn = (double*)malloc(sizeof(double) * ntot);
+  double* qk = (double*)malloc(sizeof(double) * ntot);
+  double* L = (double*)malloc(sizeof(double) * ntot);
+  memcpy(qn, q, sizeof(double) * ntot);
+  memcpy(qk, q, sizeof(double) * ntot);
+  double nu = 0.0;
+  int st = ORC_OK;
+  for (int stage = 0; stage < 3; ++stage) {
+    double smax[2];
+    st = orc_sharp_L(P, qk, aux, L, smax);
+    if (st != ORC_OK) break;
+    for (int d = 0; d < P->ndim; ++d) {
+      double v = dt * smax[d] / (d == 0 ? P->dx : P->dy);
+      if (!(v <= nu)) nu = v;
+    }
+    for (size_t c = 0; c < ntot; ++c) qk[c] = rk3_stage(stage, qn[c], qk[c], L[c], dt);
+  }
+  memcpy(q, qk, sizeof(double) * ntot);
+  *cfl = nu;
+  free(qn); free(qk); free(L);
+  return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* CFL control (Sec. 5: check the Courant number, choose the next step)      */
+/* ------------------------------------------------------------------------ */
+
+void orc_max_speeds(const orc_prob* P, const double* q, const double* aux, double* smax) {
+  int m = P->num_eqn, ma = P->num_aux, nw = orc_num_waves(P->rp, P->ndim);
+  int nx = P->nx, ny = (P->ndim == 2) ? P->ny : 1;
+  garr Q, A;
+  double* qb = ghosted(P, q, m, 2, 0, &Q);
+  double* ab = ghosted(P, aux, ma, 2, 1, &A);
+  smax[0] = 0.0; smax[1] = 0.0;
+  for (int dir = 0; dir < P->ndim; ++dir) {
+    int n = dir == 0 ? nx : ny, nl = dir == 0 ? ny : nx;
+    for (int l = 0; l < nl; ++l)
+      for (int i = 0; i <= n; ++i) {
+        double ql[MAXM], qr[MAXM], al[MAXM] = {0}, ar[MAXM] = {0};
+        double W[MAXW * MAXM], S[MAXW], am[MAXM], ap[MAXM];
+        if (dir == 0) { gcell(&Q, i - 1, l, ql); gcell(&Q, i, l, qr); }
+        else { gcell(&Q, l, i - 1, ql); gcell(&Q, l, i, qr); }
+        if (ma) {
+          if (dir == 0) { gcell(&A, i - 1, l, al); gcell(&A, i, l, ar); }
+          else { gcell(&A, l, i - 1, al); gcell(&A, l, i, ar); }
+        }
+        orc_riemann(P, dir, ql, qr, al, ar, W, S, am, ap);
+        for (int p = 0; p < nw; ++p) {
+          double a = fabs(S[p]);
+          if (!(a <= smax[dir])) smax[dir] = a;
+        }
+      }
+  }
+  free(qb); free(ab);
+}
+
+/* final-time clipping: the step that would pass t_end is shortened to reach it */
+static int clip_dt(double t, double t_end, double* dt) {
+  if (t + *dt >= t_end) { *dt = t_end - t; return 1; }
+  return 0;
+}
+
+static int all_finite(const double* q, size_t n) {
+  for (size_t i = 0; i < n; ++i) if (!isfinite(q[i])) return 0;
+  return 1;
+}
+
+int orc_evolve(const orc_prob* P, double* q, const double* aux, double t0, double t_end,
+               int max_steps, orc_run_info* info) {
+  int ny = (P->ndim == 2) ? P->ny : 1;
+  size_t ntot = (size_t)P->nx * ny * P->num_eqn;
+  double* qold = (double*)malloc(sizeof(double) * ntot);
+  double t = t0, dt;
+  int steps = 0, rejects = 0, retries = 0, status = ORC_OK;
+  double cfl_last = 0.0, cfl_seen = 0.0;
+  if (P->dt_initial > 0.0) {
+    dt = P->dt_initial;
+  } else {
+    double smax[2], rate = 0.0;
+    orc_max_speeds(P, q, aux, smax);
+    for (int d = 0; d < P->ndim; ++d) {
+      double v = smax[d] / (d == 0 ? P->dx : P->dy);
+      if (v > rate) rate = v;
+    }
+    dt = rate > 0.0 ? P->cfl_desired / rate : P->dt_max;
+  }
+  if (dt > P->dt_max) dt = P->dt_max;
+  int final = clip_dt(t, t_end, &dt);
+  while (t < t_end && steps < max_steps) {
+    double nu;
+    memcpy(qold, q, sizeof(double) * ntot);
+    if (P->scheme == ORC_SHARPCLAW) status = orc_sharp_step(P, q, aux, dt, &nu);
+    else status = orc_classic_step(P, q, aux, dt, &nu);
+    if (status != ORC_OK) break;
+    if (isnan(nu) || !all_finite(q, ntot)) {
+      memcpy(q, qold, sizeof(double) * ntot);
+      status = ORC_ENONPHYSICAL;
+      break;
+    }
+    if (nu > P->cfl_max) {
+      ++rejects;
+      ++retries;
+      memcpy(q, qold, sizeof(double) * ntot);
+      if (retries > P->max_retries) { status = ORC_ECFL; break; }
+      dt = dt * P->cfl_desired / nu;
+      if (dt > P->dt_max) dt = P->dt_max;
+      final = clip_dt(t, t_end, &dt);
+      continue;
+    }
+    t = final ? t_end : t + dt;
+    ++steps;
+    retries = 0;
+    cfl_last = nu;
+    if (nu > cfl_seen) cfl_seen = nu;
+    dt = nu > 0.0 ? dt * P->cfl_desired / nu : P->dt_max;
+    if (dt > P->dt_max) dt = P->dt_max;
+    final = clip_dt(t, t_end, &dt);
+  }
+  if (info) {
+    info->t = t; info->dt_next = dt; info->cfl_last = cfl_last; info->cfl_max_seen = cfl_seen;
+    info->steps = steps; info->rejects = rejects; info->status = status;
+  }
+  free(qold);
+  return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* conserved totals: (sum_i Q_i) dV per field, Neumaier compensated sum      */
+/* ------------------------------------------------------------------------ */
+
+void orc_totals(const orc_prob* P, const double* q, double* out) {
+  int ny = (P->ndim == 2) ? P->ny : 1;
+  size_t n = (size_t)P->nx * ny;
+  double dV = (P->ndim == 2) ? P->dx * P->dy : P->dx;
+  for (int k = 0; k < P->num_eqn; ++k) {
+    double s = 0.0, c = 0.0;
+    for (size_t i = 0; i < n; ++i) {
+      double x = q[(size_t)k * n + i];
+      double t = s + x;
+      if (fabs(s) >= fabs(x)) c += (s - t) + x;
+      else c += (x - t) + s;
+      s = t;
+    }
+    out[k] = (s + c) * dV;
+  }
+}

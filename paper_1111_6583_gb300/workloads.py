@@ -1,0 +1,267 @@
+"""Seeded synthetic workloads shaped like the paper's examples.
+
+This module holds problem descriptions and initial data only -- none of the
+finite-volume method's arithmetic.  Both the CUDA path (through the binding)
+and the CPU oracle consume what it returns, so it imports neither.
+
+A workload spec is a plain dict:
+
+    ndim, n, lower, upper            grid (cell counts, domain box)
+    rp, scheme, lim, order,          method (Riemann solver, classic/SharpClaw,
+    transverse, char_decomp,          limiter, order, transverse mode, WENO
+    entropy_fix, weno_eps             projection, Harten-Hyman fix, epsilon)
+    bc_lower, bc_upper, inflow       boundary conditions per direction
+    params                           solver constants (rho,K | g | gamma | u,v)
+    cfl_desired, cfl_max,            CFL controller
+    dt_initial, dt_max, max_retries
+    t_end                            final time
+    q0, aux                          float64 arrays [m][ny][nx] ([m][nx] in 1D)
+
+Seeds: base 6583, numpy PCG64.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+SEED = 6583
+
+
+def _centers(lo, hi, n):
+    dx = (hi - lo) / n
+    return lo + (np.arange(n) + 0.5) * dx
+
+
+def _base(ndim, n, lower, upper, rp, **kw):
+    spec = dict(ndim=ndim, n=list(n), lower=list(lower), upper=list(upper), rp=rp,
+                scheme="classic", lim="mc", order=2, transverse=2, char_decomp=0,
+                entropy_fix=1, weno_eps=1e-6, bc_lower=["periodic"] * ndim,
+                bc_upper=["periodic"] * ndim, inflow=[], params=[], cfl_desired=0.9,
+                cfl_max=1.0, dt_initial=0.0, dt_max=1e30, max_retries=8)
+    spec.update(kw)
+    return spec
+
+
+# --------------------------------------------------------------------------
+# 1D linear acoustics pulse (Table 1 system, 1D form)
+# --------------------------------------------------------------------------
+def acoustics_1d(n=2000, t_end=2.0, lim="mc"):
+    """x in [-1,1], periodic, rho=1, K=4 (c=2), p0 = exp(-100 x^2) + 1 on
+    [0.3,0.5], u0 = 0; at t=2 both pulses are back at their start."""
+    x = _centers(-1.0, 1.0, n)
+    p = np.exp(-100.0 * x * x) + ((x >= 0.3) & (x <= 0.5)).astype(np.float64)
+    q0 = np.stack([p, np.zeros_like(p)])
+    spec = _base(1, [n], [-1.0], [1.0], "acoustics", lim=lim, params=[1.0, 4.0],
+                 bc_lower=["periodic"], bc_upper=["periodic"])
+    spec.update(q0=np.ascontiguousarray(q0), aux=None, t_end=t_end)
+    return spec
+
+
+# --------------------------------------------------------------------------
+# 2D shallow-water radial dam break (Table 1 shallow-water workload)
+# --------------------------------------------------------------------------
+def sw_dambreak_2d(n=1024, t_end=1.5, transverse=2, lim="mc"):
+    """[-2.5,2.5]^2, h = 2 for r < 0.5 else 1, hu = hv = 0, g = 1, walls,
+    Roe + Harten-Hyman, MC limiter, CFL 0.9."""
+    x = _centers(-2.5, 2.5, n)
+    X, Y = np.meshgrid(x, x, indexing="xy")  # [ny][nx]
+    r = np.sqrt(X * X + Y * Y)
+    h = np.where(r < 0.5, 2.0, 1.0)
+    q0 = np.stack([h, np.zeros_like(h), np.zeros_like(h)])
+    spec = _base(2, [n, n], [-2.5, -2.5], [2.5, 2.5], "sw_roe", lim=lim, transverse=transverse,
+                 params=[1.0], bc_lower=["wall", "wall"], bc_upper=["wall", "wall"])
+    spec.update(q0=np.ascontiguousarray(q0), aux=None, t_end=t_end)
+    return spec
+
+
+# --------------------------------------------------------------------------
+# 2D Euler shock-bubble (Sec. 6.2, planar form)
+# --------------------------------------------------------------------------
+def post_shock_state(mach=2.0, gamma=1.4, rho1=1.0, p1=1.0):
+    """Rankine-Hugoniot state behind a shock of the given Mach number moving
+    into gas at rest (rho1, p1): returns (rho2, u2, p2)."""
+    c1 = math.sqrt(gamma * p1 / rho1)
+    m2 = mach * mach
+    p2 = p1 * (1.0 + 2.0 * gamma / (gamma + 1.0) * (m2 - 1.0))
+    rho2 = rho1 * (gamma + 1.0) * m2 / ((gamma - 1.0) * m2 + 2.0)
+    u2 = mach * c1 * (1.0 - rho1 / rho2)
+    return rho2, u2, p2
+
+
+def shock_bubble_2d(nx=2048, ny=1024, t_end=0.2, scheme="sharpclaw", gamma=1.4,
+                    sub=16, char_decomp=1):
+    """[0,2]x[0,1]; Mach-2 planar shock at x = 0.2 moving into rho = p = 1;
+    bubble rho = 0.1, p = 1, radius 0.2 at (0.5, 0.5), cell-averaged by a
+    sub x sub sample of the inside fraction; inflow (post-shock) left, extrap
+    right, walls top/bottom; SharpClaw WENO5 + SSP-RK3 by default."""
+    x = _centers(0.0, 2.0, nx)
+    y = _centers(0.0, 1.0, ny)
+    dx, dy = 2.0 / nx, 1.0 / ny
+    # inside fraction of the bubble per cell from a sub x sub point sample
+    off = (np.arange(sub) + 0.5) / sub - 0.5
+    frac = np.zeros((ny, nx))
+    X, Y = np.meshgrid(x, y, indexing="xy")
+    for a in off:
+        for b in off:
+            xs = X + a * dx
+            ys = Y + b * dy
+            frac += ((xs - 0.5) ** 2 + (ys - 0.5) ** 2 < 0.04)
+    frac /= sub * sub
+    rho = frac * 0.1 + (1.0 - frac) * 1.0
+    E_amb = 1.0 / (gamma - 1.0)
+    E = np.full_like(rho, E_amb)
+    rho2, u2, p2 = post_shock_state(2.0, gamma)
+    E2 = p2 / (gamma - 1.0) + 0.5 * rho2 * u2 * u2
+    left = X < 0.2
+    rho = np.where(left, rho2, rho)
+    mx = np.where(left, rho2 * u2, 0.0)
+    my = np.zeros_like(rho)
+    E = np.where(left, E2, E)
+    q0 = np.stack([rho, mx, my, E])
+    spec = _base(2, [nx, ny], [0.0, 0.0], [2.0, 1.0], "euler_roe", scheme=scheme,
+                 char_decomp=char_decomp, params=[gamma],
+                 bc_lower=["inflow", "wall"], bc_upper=["extrap", "wall"],
+                 inflow=[rho2, rho2 * u2, 0.0, E2],
+                 cfl_desired=0.5 if scheme == "sharpclaw" else 0.8,
+                 cfl_max=0.6 if scheme == "sharpclaw" else 1.0)
+    spec.update(q0=np.ascontiguousarray(q0), aux=None, t_end=t_end)
+    return spec
+
+
+# --------------------------------------------------------------------------
+# Listing 1: 2D Euler Riemann problem (Lax-Liu case 6), the paper's hello world
+# --------------------------------------------------------------------------
+def euler_quadrants_2d(n=100, t_end=0.3, gamma=1.4):
+    """Unit square, extrapolation BCs, gamma 1.4; the four-quadrant initial
+    data of the paper's first listing."""
+    x = _centers(0.0, 1.0, n)
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    l = (X < 0.5).astype(float); r = (X >= 0.5).astype(float)
+    b = (Y < 0.5).astype(float); t = (Y >= 0.5).astype(float)
+    rho = 2.0 * l * t + 1.0 * l * b + 1.0 * r * t + 3.0 * r * b
+    mx = 0.75 * t - 0.75 * b
+    my = 0.5 * l - 0.5 * r
+    E = 0.5 * rho * (mx ** 2 + my ** 2) + 1.0 / (gamma - 1.0)
+    q0 = np.stack([rho, mx, my, E])
+    spec = _base(2, [n, n], [0.0, 0.0], [1.0, 1.0], "euler_roe", params=[gamma],
+                 bc_lower=["extrap", "extrap"], bc_upper=["extrap", "extrap"])
+    spec.update(q0=np.ascontiguousarray(q0), aux=None, t_end=t_end)
+    return spec
+
+
+# --------------------------------------------------------------------------
+# 1D nonlinear elasticity in a layered medium (Sec. 6.3, 1D analogue)
+# --------------------------------------------------------------------------
+def layered_medium(x, width=0.5):
+    """(rho, K) = (1, 1) on even layers [2k w, (2k+1) w), (4, 4) on odd ones."""
+    odd = (np.floor(x / width).astype(np.int64) % 2) == 1
+    rho = np.where(odd, 4.0, 1.0)
+    K = np.where(odd, 4.0, 1.0)
+    return rho, K
+
+
+def elasticity_member(n, amp, width, dx=1.0 / 32.0, t_end=50.0):
+    L = n * dx
+    x = _centers(0.0, L, n)
+    rho, K = layered_medium(x)
+    sig0 = amp * np.exp(-((x - 0.5 * L) / width) ** 2)
+    eps0 = np.log1p(sig0) / K
+    q0 = np.stack([eps0, np.zeros_like(eps0)])
+    aux = np.stack([rho, K])
+    spec = _base(1, [n], [0.0], [L], "elasticity_fwave", num_aux=2,
+                 bc_lower=["periodic"], bc_upper=["periodic"])
+    spec.update(q0=np.ascontiguousarray(q0), aux=np.ascontiguousarray(aux), t_end=t_end)
+    return spec
+
+
+def elasticity_ensemble(members=4096, seed=SEED, lo_exp=12, hi_exp=16, t_end=50.0):
+    """Uneven 1D elasticity ensemble: N_k = round(2^(lo + (hi-lo) u)), amplitude
+    U(0.1, 0.5), width U(1, 5), dx = 1/32 (16 cells per layer), periodic."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    u = rng.random(members)
+    amp = rng.uniform(0.1, 0.5, members)
+    width = rng.uniform(1.0, 5.0, members)
+    sizes = np.rint(2.0 ** (lo_exp + (hi_exp - lo_exp) * u)).astype(np.int64)
+    return [dict(n=int(sizes[k]), amp=float(amp[k]), width=float(width[k]), t_end=t_end)
+            for k in range(members)]
+
+
+# --------------------------------------------------------------------------
+# serving stream: 2D shallow-water humps
+# --------------------------------------------------------------------------
+def sw_humps_2d(n, humps, t_end):
+    """[0,1]^2, depth 1 plus Gaussian humps (a, w, cx, cy), walls, g = 1."""
+    x = _centers(0.0, 1.0, n)
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    h = np.ones((n, n))
+    for (a, w, cx, cy) in humps:
+        r2 = (X - cx) ** 2 + (Y - cy) ** 2
+        h = h + a * np.exp(-r2 / (w * w))
+    q0 = np.stack([h, np.zeros_like(h), np.zeros_like(h)])
+    spec = _base(2, [n, n], [0.0, 0.0], [1.0, 1.0], "sw_roe", params=[1.0],
+                 bc_lower=["wall", "wall"], bc_upper=["wall", "wall"])
+    spec.update(q0=np.ascontiguousarray(q0), aux=None, t_end=t_end)
+    return spec
+
+
+def serving_stream(requests=2000, rate=200.0, seed=SEED + 5, lo_exp=6, hi_exp=10):
+    """Poisson arrivals (exponential gaps of mean 1/rate); n = round(2^(6+4u));
+    1-3 humps of height U(0.1,1), width U(0.05,0.3), centres U(0.15,0.85)^2;
+    t_end U(0.5, 2)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gaps = rng.exponential(1.0 / rate, requests)
+    arrivals = np.cumsum(gaps)
+    out = []
+    for k in range(requests):
+        u = rng.random()
+        n = int(round(2.0 ** (lo_exp + (hi_exp - lo_exp) * u)))
+        nh = int(rng.integers(1, 4))
+        humps = [(float(rng.uniform(0.1, 1.0)), float(rng.uniform(0.05, 0.3)),
+                  float(rng.uniform(0.15, 0.85)), float(rng.uniform(0.15, 0.85)))
+                 for _ in range(nh)]
+        out.append(dict(arrival=float(arrivals[k]), n=n, humps=humps,
+                        t_end=float(rng.uniform(0.5, 2.0))))
+    return out
+
+
+# --------------------------------------------------------------------------
+# small generic cases for parity tests
+# --------------------------------------------------------------------------
+def random_smooth_2d(rp, nx, ny, seed=SEED, params=None, bc="periodic", **kw):
+    """Smooth positive random field (a few Fourier modes) for the given system."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x = _centers(0.0, 1.0, nx)
+    y = _centers(0.0, 1.0, ny)
+    X, Y = np.meshgrid(x, y, indexing="xy")
+
+    def field(amp):
+        f = np.zeros_like(X)
+        for _ in range(3):
+            kx, ky = rng.integers(1, 4, 2)
+            ph = rng.uniform(0, 2 * np.pi)
+            f += amp * rng.uniform(0.3, 1.0) * np.sin(2 * np.pi * (kx * X + ky * Y) + ph)
+        return f
+
+    if rp == "sw_roe":
+        q0 = np.stack([1.0 + field(0.1), field(0.1), field(0.1)])
+        params = params or [1.0]
+    elif rp in ("euler_roe", "euler_hlle"):
+        rho = 1.0 + field(0.1)
+        mx, my = field(0.2), field(0.2)
+        p = 1.0 + field(0.1)
+        E = p / 0.4 + 0.5 * (mx * mx + my * my) / rho
+        q0 = np.stack([rho, mx, my, E])
+        params = params or [1.4]
+    elif rp == "acoustics":
+        q0 = np.stack([field(0.5), field(0.5), field(0.5)])
+        params = params or [1.0, 4.0]
+    elif rp == "advection":
+        q0 = np.stack([field(1.0)])
+        params = params or [1.0, 0.5]
+    else:
+        raise ValueError(rp)
+    spec = _base(2, [nx, ny], [0.0, 0.0], [1.0, 1.0], rp, params=params,
+                 bc_lower=[bc, bc], bc_upper=[bc, bc], **kw)
+    spec.update(q0=np.ascontiguousarray(q0), aux=None, t_end=kw.get("t_end", 0.1))
+    return spec
