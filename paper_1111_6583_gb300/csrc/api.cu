@@ -1,0 +1,1351 @@
+// api.cu -- host runtime behind the C ABI of include/clawgpu.h: solver handles,
+// batches and the continuous-batching server.  All numerical work happens in
+// the fused kernels; this file validates arguments, owns work buffers and
+// control blocks, orders work on the caller's stream, captures CUDA graphs of
+// step attempts, and runs the step-size autotuner.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "claw_common.cuh"
+#include "kernels.h"
+
+using namespace claw;
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+const char* kVersion = "clawgpu 1.0 (sm_103a)";
+
+KernelSet kernels_for(int rp, int nd, int prec) {
+  switch (rp) {
+    case CLAW_RP_ADVECTION: return claw_kernels_advection(nd, prec);
+    case CLAW_RP_ACOUSTICS: return claw_kernels_acoustics(nd, prec);
+    case CLAW_RP_SW_ROE: return claw_kernels_sw(nd, prec);
+    case CLAW_RP_EULER_ROE: return claw_kernels_euler_roe(nd, prec);
+    case CLAW_RP_EULER_HLLE: return claw_kernels_euler_hlle(nd, prec);
+    case CLAW_RP_ELASTICITY_FWAVE: return claw_kernels_elasticity(nd, prec);
+  }
+  return KernelSet{};
+}
+
+template <typename R>
+void fill_consts(const claw_method& m, MConsts<R>& C) {
+  std::memset(&C, 0, sizeof(C));
+  for (int k = 0; k < 8; ++k) {
+    C.p[k] = (R)m.params[k];
+    C.inflow[k] = (R)m.inflow[k];
+  }
+  if (m.rp == CLAW_RP_ACOUSTICS) {
+    const double c = std::sqrt(m.params[1] / m.params[0]);
+    const double Z = m.params[0] * c;
+    C.aco_c = (R)c;
+    C.aco_Z = (R)Z;
+    C.aco_h = (R)(1.0 / (2.0 * Z));
+  }
+  C.g = (R)m.params[0];
+  C.gamma = (R)m.params[0];
+  C.gm1 = (R)(m.params[0] - 1.0);
+  C.weno_eps = (R)m.weno_eps;
+  C.lim = m.lim;
+  C.order = m.order;
+  C.transverse = m.transverse;
+  C.entropy_fix = m.entropy_fix;
+  C.char_decomp = m.char_decomp;
+  for (int d = 0; d < 2; ++d) {
+    C.bc_lo[d] = m.bc_lower[d];
+    C.bc_hi[d] = m.bc_upper[d];
+  }
+}
+
+std::vector<unsigned char> make_consts(const claw_method& m) {
+  std::vector<unsigned char> v;
+  if (m.prec == CLAW_FP64) {
+    v.resize(sizeof(MConsts<double>));
+    fill_consts<double>(m, *(MConsts<double>*)v.data());
+  } else {
+    v.resize(sizeof(MConsts<float>));
+    fill_consts<float>(m, *(MConsts<float>*)v.data());
+  }
+  return v;
+}
+
+int num_eqn(int rp, int nd) {
+  switch (rp) {
+    case CLAW_RP_ADVECTION: return 1;
+    case CLAW_RP_ACOUSTICS: return nd + 1;
+    case CLAW_RP_SW_ROE: return nd + 1;
+    case CLAW_RP_EULER_ROE:
+    case CLAW_RP_EULER_HLLE: return nd + 2;
+    case CLAW_RP_ELASTICITY_FWAVE: return nd == 1 ? 2 : 0;
+  }
+  return 0;
+}
+
+// validate a method against a dimension; returns an error message or nullptr
+const char* check_method(const claw_method& m, int nd) {
+  if (nd != 1 && nd != 2) return "ndim must be 1 or 2";
+  if (m.rp < 0 || m.rp > 5) return "unknown Riemann solver";
+  if (num_eqn(m.rp, nd) == 0) return "solver not available in this dimension";
+  if (m.num_eqn != num_eqn(m.rp, nd)) return "num_eqn does not match the Riemann solver";
+  const int na = m.rp == CLAW_RP_ELASTICITY_FWAVE ? 2 : 0;
+  if (m.num_aux != na) return "num_aux does not match the Riemann solver";
+  if (m.scheme != CLAW_CLASSIC && m.scheme != CLAW_SHARPCLAW) return "unknown scheme";
+  if (m.prec != CLAW_FP64 && m.prec != CLAW_FP32) return "unknown precision";
+  if (m.lim < 0 || m.lim > 4) return "unknown limiter";
+  if (m.scheme == CLAW_CLASSIC && m.order != 1 && m.order != 2) return "order must be 1 or 2";
+  if (m.transverse < 0 || m.transverse > 2) return "transverse must be 0, 1 or 2";
+  if (m.scheme == CLAW_SHARPCLAW && m.weno_order != 5) return "weno_order must be 5";
+  if (m.scheme == CLAW_SHARPCLAW && m.char_decomp && m.rp == CLAW_RP_ELASTICITY_FWAVE)
+    return "no characteristic projection for the f-wave elasticity solver";
+  if (!(m.cfl_desired > 0) || !(m.cfl_max >= m.cfl_desired)) return "need 0 < cfl_desired <= cfl_max";
+  if (!(m.dt_max > 0)) return "dt_max must be positive";
+  if (m.max_retries < 0) return "max_retries must be >= 0";
+  for (int d = 0; d < nd; ++d) {
+    if (m.bc_lower[d] < 0 || m.bc_lower[d] > 3 || m.bc_upper[d] < 0 || m.bc_upper[d] > 3)
+      return "unknown boundary condition";
+    if ((m.bc_lower[d] == CLAW_BC_PERIODIC) != (m.bc_upper[d] == CLAW_BC_PERIODIC))
+      return "periodic boundaries must be paired";
+  }
+  if ((m.rp == CLAW_RP_ACOUSTICS) && !(m.params[0] > 0 && m.params[1] > 0))
+    return "acoustics needs rho > 0 and K > 0";
+  if ((m.rp == CLAW_RP_SW_ROE) && !(m.params[0] > 0)) return "shallow water needs g > 0";
+  if ((m.rp == CLAW_RP_EULER_ROE || m.rp == CLAW_RP_EULER_HLLE) && !(m.params[0] > 1))
+    return "Euler needs gamma > 1";
+  return nullptr;
+}
+
+const char* check_grid(const claw_grid& g) {
+  if (g.ndim != 1 && g.ndim != 2) return "ndim must be 1 or 2";
+  for (int d = 0; d < g.ndim; ++d) {
+    if (g.n[d] < 4) return "each direction needs at least 4 cells";
+    if (g.n[d] > (int64_t)INT_MAX / 2) return "too many cells in one direction";
+    if (!(g.upper[d] > g.lower[d])) return "upper must exceed lower";
+  }
+  return nullptr;
+}
+
+int tiles_of(int scheme, int nd, int prec, int nx, int ny, int bw, int h) {
+  if (scheme == CLAW_CLASSIC)
+    return nd == 1 ? classic1d_tiles(nx, classic1d_T(prec)) : classic2d_tiles(nx, ny, bw, h);
+  return nd == 1 ? sharp_tiles(nx, 1, kSharpTX1, 1) : sharp_tiles(nx, ny, kSharpTX2, kSharpTY2);
+}
+
+int maxspeed_tiles(int nx, int ny) {
+  const long long n = (long long)nx * ny;
+  return (int)((n + kMaxspeedCells - 1) / kMaxspeedCells);
+}
+
+DevCtl make_ctl(const claw_method& m, const claw_grid& g, int nbuf, double t0, double t_end) {
+  DevCtl c;
+  std::memset(&c, 0, sizeof(c));
+  c.t = t0;
+  c.t_end = t_end;
+  c.dt_max = m.dt_max;
+  c.cfl_desired = m.cfl_desired;
+  c.cfl_max = m.cfl_max;
+  c.dx[0] = (g.upper[0] - g.lower[0]) / (double)g.n[0];
+  c.dx[1] = g.ndim == 2 ? (g.upper[1] - g.lower[1]) / (double)g.n[1] : 1.0;
+  c.dt_init = m.dt_initial;
+  c.max_steps = LLONG_MAX;
+  c.nbuf = nbuf;
+  c.max_retries = m.max_retries;
+  c.ndim = g.ndim;
+  c.done = (t0 >= t_end) ? 1 : 0;
+  return c;
+}
+
+size_t state_bytes_of(const claw_method& m, const claw_grid& g) {
+  const size_t es = m.prec == CLAW_FP64 ? 8 : 4;
+  size_t cells = (size_t)g.n[0] * (g.ndim == 2 ? (size_t)g.n[1] : 1);
+  return cells * m.num_eqn * es;
+}
+size_t aux_bytes_of(const claw_method& m, const claw_grid& g) {
+  const size_t es = m.prec == CLAW_FP64 ? 8 : 4;
+  size_t cells = (size_t)g.n[0] * (g.ndim == 2 ? (size_t)g.n[1] : 1);
+  return cells * m.num_aux * es;
+}
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+void fill_info(const DevCtl& c, claw_step_info* info) {
+  if (!info) return;
+  info->t = c.t;
+  info->dt_used = c.dt_used;
+  info->dt_next = c.dt;
+  info->cfl = c.nu_last;
+  info->cfl_max_seen = c.nu_max_seen;
+  info->steps = c.steps;
+  info->rejects = c.rejects;
+  info->accepted = c.accepted;
+  info->status = c.status;
+}
+
+// Launch one attempt (classic: one kernel; SharpClaw: three stage kernels).
+cudaError_t launch_attempt(const KernelSet& ks, int scheme, const Member* mem, const Tile* tiles,
+                           int ntiles, const void* consts, int bw, int h, cudaStream_t st) {
+  LaunchArgs a{mem, tiles, ntiles, consts, bw, h, 0, st};
+  if (scheme == CLAW_CLASSIC) return ks.classic(a);
+  for (int s = 0; s < 3; ++s) {
+    a.stage = s;
+    cudaError_t e = ks.sharp(a);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+double now_s() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+// ===========================================================================
+// single-grid solver
+// ===========================================================================
+struct claw_solver {
+  claw_method m;
+  claw_grid g;
+  int nd = 1, prec = 0, nbuf = 2;
+  KernelSet ks{};
+  std::vector<unsigned char> consts;
+  cudaStream_t ustream = nullptr, st = nullptr;
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+  void* q_user = nullptr;
+  const void* aux = nullptr;
+  void* work = nullptr;
+  size_t sbytes = 0;
+  DevCtl* d_ctl = nullptr;
+  DevCtl* h_ctl = nullptr;  // pinned
+  Member* d_mem = nullptr;
+  Member h_mem{};
+  DevCtl* d_ctl_tune = nullptr;
+  Member* d_mem_tune = nullptr;
+  double* d_part = nullptr;
+  double* h_part = nullptr;  // pinned
+  int npart = 0;
+  int ntiles = 0, bw = 128, h = 32;
+  int tuned = 0;
+  cudaGraphExec_t gexec = nullptr;
+  int gk = 0;
+  int bound = 0;
+  std::string err;
+};
+
+namespace {
+
+claw_status fail(claw_solver* s, const char* what, cudaError_t e = cudaSuccess) {
+  std::string msg = what;
+  if (e != cudaSuccess) {
+    msg += ": ";
+    msg += cudaGetErrorString(e);
+  }
+  if (s) s->err = msg;
+  g_err = msg;
+  return e != cudaSuccess ? CLAW_ECUDA : CLAW_EINVAL;
+}
+
+#define SCK(call)                                      \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return fail(s, #call, e_);  \
+  } while (0)
+
+cudaError_t enter(claw_solver* s) {
+  cudaError_t e = cudaEventRecord(s->ev_a, s->ustream);
+  if (e != cudaSuccess) return e;
+  return cudaStreamWaitEvent(s->st, s->ev_a, 0);
+}
+cudaError_t leave(claw_solver* s) {
+  cudaError_t e = cudaEventRecord(s->ev_b, s->st);
+  if (e != cudaSuccess) return e;
+  return cudaStreamWaitEvent(s->ustream, s->ev_b, 0);
+}
+
+cudaError_t solver_attempt(claw_solver* s, cudaStream_t st) {
+  return launch_attempt(s->ks, s->m.scheme, s->d_mem, nullptr, s->ntiles, s->consts.data(), s->bw,
+                        s->h, st);
+}
+
+cudaError_t read_ctl(claw_solver* s) {
+  cudaError_t e = cudaMemcpyAsync(s->h_ctl, s->d_ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, s->st);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(s->st);
+}
+
+cudaError_t upload_member(claw_solver* s) {
+  s->h_mem.ntiles = s->ntiles;
+  return cudaMemcpyAsync(s->d_mem, &s->h_mem, sizeof(Member), cudaMemcpyHostToDevice, s->st);
+}
+
+void drop_graph(claw_solver* s) {
+  if (s->gexec) cudaGraphExecDestroy(s->gexec);
+  s->gexec = nullptr;
+  s->gk = 0;
+}
+
+cudaError_t build_graph(claw_solver* s, int k) {
+  drop_graph(s);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  for (int i = 0; i < k && e == cudaSuccess; ++i) e = solver_attempt(s, s->st);
+  cudaError_t e2 = cudaStreamEndCapture(s->st, &g);
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return e;
+  }
+  if (e2 != cudaSuccess) return e2;
+  e = cudaGraphInstantiate(&s->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e == cudaSuccess) s->gk = k;
+  return e;
+}
+
+// Time candidate (bw, h) shapes of the 2D classic kernel on the bound state
+// with a dry control block (attempts leave t, dt and the state untouched) and
+// keep the fastest.
+cudaError_t autotune(claw_solver* s) {
+  if (s->m.scheme != CLAW_CLASSIC || s->nd != 2) {
+    s->tuned = 1;
+    return cudaSuccess;
+  }
+  cudaError_t e = cudaSuccess;
+  if (!s->d_ctl_tune) {
+    if ((e = cudaMalloc(&s->d_ctl_tune, sizeof(DevCtl))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&s->d_mem_tune, sizeof(Member))) != cudaSuccess) return e;
+  }
+  if ((e = cudaMemcpyAsync(s->d_ctl_tune, s->d_ctl, sizeof(DevCtl), cudaMemcpyDeviceToDevice,
+                           s->st)) != cudaSuccess)
+    return e;
+  if ((e = launch_set_dry(s->d_ctl_tune, 1, s->st)) != cudaSuccess) return e;
+  if ((e = launch_set_t_end(s->d_ctl_tune, 1, INFINITY, 0, s->st)) != cudaSuccess) return e;
+  Member mt = s->h_mem;
+  mt.ctl = s->d_ctl_tune;
+  const int nx = (int)s->g.n[0], ny = (int)s->g.n[1];
+  const int bws[2] = {64, 128};
+  const int hs[5] = {8, 16, 32, 64, 128};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int bb = 128, bh = 32;
+  for (int ib = 0; ib < 2; ++ib)
+    for (int ih = 0; ih < 5; ++ih) {
+      const int bw = bws[ib], h = hs[ih];
+      if (h > 2 * ny) continue;
+      const int nt = classic2d_tiles(nx, ny, bw, h);
+      mt.ntiles = nt;
+      if ((e = cudaMemcpyAsync(s->d_mem_tune, &mt, sizeof(Member), cudaMemcpyHostToDevice,
+                               s->st)) != cudaSuccess)
+        break;
+      LaunchArgs a{s->d_mem_tune, nullptr, nt, s->consts.data(), bw, h, 0, s->st};
+      if ((e = s->ks.classic(a)) != cudaSuccess) break;  // warm-up
+      cudaEventRecord(e0, s->st);
+      for (int r = 0; r < 3; ++r) s->ks.classic(a);
+      cudaEventRecord(e1, s->st);
+      if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        bb = bw;
+        bh = h;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return e;
+  s->bw = bb;
+  s->h = bh;
+  s->ntiles = classic2d_tiles(nx, ny, bb, bh);
+  s->tuned = 1;
+  drop_graph(s);
+  return upload_member(s);
+}
+
+void free_bound(claw_solver* s) {
+  drop_graph(s);
+  if (s->work) cudaFree(s->work);
+  if (s->d_ctl) cudaFree(s->d_ctl);
+  if (s->d_mem) cudaFree(s->d_mem);
+  if (s->d_ctl_tune) cudaFree(s->d_ctl_tune);
+  if (s->d_mem_tune) cudaFree(s->d_mem_tune);
+  if (s->d_part) cudaFree(s->d_part);
+  if (s->h_ctl) cudaFreeHost(s->h_ctl);
+  if (s->h_part) cudaFreeHost(s->h_part);
+  s->work = nullptr;
+  s->d_ctl = nullptr;
+  s->d_mem = nullptr;
+  s->d_ctl_tune = nullptr;
+  s->d_mem_tune = nullptr;
+  s->d_part = nullptr;
+  s->h_ctl = nullptr;
+  s->h_part = nullptr;
+  s->bound = 0;
+}
+
+claw_status sync_state_impl(claw_solver* s) {
+  SCK(read_ctl(s));
+  if (s->h_ctl->cur != 0) {
+    const unsigned char* src = (const unsigned char*)s->h_mem.q[s->h_ctl->cur];
+    SCK(cudaMemcpyAsync(s->q_user, src, s->sbytes, cudaMemcpyDeviceToDevice, s->st));
+    SCK(launch_reset_cur(s->d_ctl, s->st));
+    SCK(read_ctl(s));
+  }
+  return CLAW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+claw_status claw_method_init(claw_method* m, int rp, int ndim) {
+  if (!m) return CLAW_EINVAL;
+  std::memset(m, 0, sizeof(*m));
+  if (ndim != 1 && ndim != 2) {
+    g_err = "ndim must be 1 or 2";
+    return CLAW_EINVAL;
+  }
+  if (rp < 0 || rp > 5 || num_eqn(rp, ndim) == 0) {
+    g_err = "unknown Riemann solver for this dimension";
+    return CLAW_EINVAL;
+  }
+  m->scheme = CLAW_CLASSIC;
+  m->rp = rp;
+  m->lim = CLAW_LIM_MC;
+  m->prec = CLAW_FP64;
+  m->order = 2;
+  m->transverse = ndim == 2 ? 2 : 0;
+  m->weno_order = 5;
+  m->char_decomp = rp == CLAW_RP_ELASTICITY_FWAVE ? 0 : 1;
+  m->entropy_fix = 1;
+  m->max_retries = 8;
+  m->cfl_desired = 0.9;
+  m->cfl_max = 1.0;
+  m->dt_initial = 0.0;
+  m->dt_max = 1e30;
+  m->weno_eps = 1e-6;
+  for (int d = 0; d < 3; ++d) m->bc_lower[d] = m->bc_upper[d] = CLAW_BC_PERIODIC;
+  switch (rp) {
+    case CLAW_RP_ADVECTION: m->params[0] = 1.0; m->params[1] = 1.0; break;
+    case CLAW_RP_ACOUSTICS: m->params[0] = 1.0; m->params[1] = 1.0; break;
+    case CLAW_RP_SW_ROE: m->params[0] = 1.0; break;
+    case CLAW_RP_EULER_ROE:
+    case CLAW_RP_EULER_HLLE: m->params[0] = 1.4; break;
+    default: break;
+  }
+  m->num_eqn = num_eqn(rp, ndim);
+  m->num_aux = rp == CLAW_RP_ELASTICITY_FWAVE ? 2 : 0;
+  return CLAW_OK;
+}
+
+claw_status claw_solver_create(const claw_method* m, const claw_grid* g, void* stream,
+                               claw_solver** out) {
+  if (!m || !g || !out) return fail(nullptr, "null argument");
+  *out = nullptr;
+  if (const char* why = check_grid(*g)) return fail(nullptr, why);
+  if (const char* why = check_method(*m, g->ndim)) return fail(nullptr, why);
+  KernelSet ks = kernels_for(m->rp, g->ndim, m->prec);
+  if (!ks.valid) return fail(nullptr, "no kernels for this solver/dimension/precision");
+  claw_solver* s = new claw_solver();
+  s->m = *m;
+  s->g = *g;
+  if (g->ndim == 1) s->g.n[1] = 1;
+  s->nd = g->ndim;
+  s->prec = m->prec;
+  s->nbuf = m->scheme == CLAW_SHARPCLAW ? 3 : 2;
+  s->ks = ks;
+  s->consts = make_consts(*m);
+  s->ustream = (cudaStream_t)stream;
+  s->sbytes = state_bytes_of(*m, s->g);
+  cudaError_t e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_a, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_b, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    claw_status st = fail(s, "stream/event creation", e);
+    claw_solver_destroy(s);
+    return st;
+  }
+  s->ntiles = tiles_of(m->scheme, s->nd, s->prec, (int)s->g.n[0], (int)s->g.n[1], s->bw, s->h);
+  *out = s;
+  return CLAW_OK;
+}
+
+claw_status claw_bind_state(claw_solver* s, void* q_dev, const void* aux_dev, double t0) {
+  if (!s) return fail(nullptr, "null solver");
+  if (!q_dev) return fail(s, "q_dev is NULL");
+  if (s->m.num_aux > 0 && !aux_dev) return fail(s, "this solver needs aux fields");
+  free_bound(s);
+  s->q_user = q_dev;
+  s->aux = aux_dev;
+  SCK(cudaMalloc(&s->work, s->sbytes * (s->nbuf - 1)));
+  SCK(cudaMalloc(&s->d_ctl, sizeof(DevCtl)));
+  SCK(cudaMalloc(&s->d_mem, sizeof(Member)));
+  SCK(cudaMallocHost(&s->h_ctl, sizeof(DevCtl)));
+  const long long ncell = (long long)s->g.n[0] * s->g.n[1];
+  s->npart = (int)std::min<long long>(1024, (ncell + kTotalsThreads - 1) / kTotalsThreads);
+  SCK(cudaMalloc(&s->d_part, sizeof(double) * 2 * s->npart * s->m.num_eqn));
+  SCK(cudaMallocHost(&s->h_part, sizeof(double) * 2 * s->npart * s->m.num_eqn));
+  std::memset(&s->h_mem, 0, sizeof(Member));
+  s->h_mem.q[0] = q_dev;
+  s->h_mem.q[1] = s->work;
+  s->h_mem.q[2] = s->nbuf == 3 ? (void*)((unsigned char*)s->work + s->sbytes) : nullptr;
+  s->h_mem.aux = aux_dev;
+  s->h_mem.nx = (int)s->g.n[0];
+  s->h_mem.ny = (int)s->g.n[1];
+  s->h_mem.ctl = s->d_ctl;
+  DevCtl c = make_ctl(s->m, s->g, s->nbuf, t0, INFINITY);
+  SCK(enter(s));
+  SCK(cudaMemcpyAsync(s->d_ctl, &c, sizeof(DevCtl), cudaMemcpyHostToDevice, s->st));
+  SCK(upload_member(s));
+  // first dt from the wave speeds of Q^0 (or dt_initial)
+  LaunchArgs a{s->d_mem, nullptr, maxspeed_tiles(s->h_mem.nx, s->h_mem.ny), s->consts.data(), 0,
+               0, 0, s->st};
+  SCK(s->ks.maxspeed(a));
+  SCK(launch_dt_init(s->d_ctl, 1, s->st));
+  SCK(leave(s));
+  SCK(cudaStreamSynchronize(s->st));
+  s->bound = 1;
+  return CLAW_OK;
+}
+
+claw_status claw_solver_tune(claw_solver* s, int mode, int* bw, int* h) {
+  if (!s || !s->bound) return fail(s, "solver not bound");
+  if (mode == 0) {
+    SCK(enter(s));
+    SCK(autotune(s));
+    SCK(leave(s));
+  } else {
+    if (!bw || !h || (*bw != 64 && *bw != 128) || *h < 1) return fail(s, "bad tile shape");
+    s->bw = *bw;
+    s->h = *h;
+    s->ntiles = tiles_of(s->m.scheme, s->nd, s->prec, (int)s->g.n[0], (int)s->g.n[1], s->bw, s->h);
+    s->tuned = 1;
+    drop_graph(s);
+    SCK(enter(s));
+    SCK(upload_member(s));
+    SCK(leave(s));
+  }
+  if (bw) *bw = s->bw;
+  if (h) *h = s->h;
+  SCK(cudaStreamSynchronize(s->st));
+  return CLAW_OK;
+}
+
+claw_status claw_set_t_end(claw_solver* s, double t_end, int64_t max_steps) {
+  if (!s || !s->bound) return fail(s, "solver not bound");
+  SCK(enter(s));
+  SCK(launch_set_t_end(s->d_ctl, 1, t_end, (long long)max_steps, s->st));
+  SCK(leave(s));
+  return CLAW_OK;
+}
+
+claw_status claw_advance(claw_solver* s, int n) {
+  if (!s || !s->bound) return fail(s, "solver not bound");
+  if (n < 0) return fail(s, "n must be >= 0");
+  SCK(enter(s));
+  for (int i = 0; i < n; ++i) SCK(solver_attempt(s, s->st));
+  SCK(leave(s));
+  return CLAW_OK;
+}
+
+claw_status claw_step(claw_solver* s, double dt, claw_step_info* info) {
+  if (!s || !s->bound) return fail(s, "solver not bound");
+  SCK(enter(s));
+  SCK(launch_set_t_end(s->d_ctl, 1, INFINITY, 0, s->st));
+  if (dt > 0) {
+    SCK(launch_force_dt(s->d_ctl, dt, s->st));
+    SCK(solver_attempt(s, s->st));
+    SCK(read_ctl(s));
+  } else {
+    for (int tries = 0; tries <= s->m.max_retries; ++tries) {
+      SCK(solver_attempt(s, s->st));
+      SCK(read_ctl(s));
+      if (s->h_ctl->accepted || s->h_ctl->done) break;
+    }
+  }
+  SCK(leave(s));
+  fill_info(*s->h_ctl, info);
+  return s->h_ctl->status;
+}
+
+claw_status claw_evolve_to_time(claw_solver* s, double t_end, int64_t max_steps, int use_graph,
+                                claw_step_info* info) {
+  if (!s || !s->bound) return fail(s, "solver not bound");
+  SCK(enter(s));
+  if (!s->tuned) SCK(autotune(s));
+  SCK(launch_set_t_end(s->d_ctl, 1, t_end, (long long)max_steps, s->st));
+  const int GK = 16;
+  if (use_graph && s->gk != GK) SCK(build_graph(s, GK));
+  long long launched = 0;
+  for (;;) {
+    SCK(read_ctl(s));
+    const DevCtl& c = *s->h_ctl;
+    if (c.done) break;
+    // attempts left: the steps to t_end at the current dt (at least one)
+    double left = (c.dt > 0) ? (c.t_end - c.t) / c.dt : 1.0;
+    long long k = (long long)std::ceil(std::min(left, 1e9)) + 1;
+    if (max_steps > 0) k = std::min<long long>(k, c.max_steps - c.steps);
+    k = std::max<long long>(1, std::min<long long>(k, 256));
+    if (use_graph) {
+      const long long reps = (k + GK - 1) / GK;
+      for (long long r = 0; r < reps; ++r) SCK(cudaGraphLaunch(s->gexec, s->st));
+      launched += reps * GK;
+    } else {
+      for (long long i = 0; i < k; ++i) SCK(solver_attempt(s, s->st));
+      launched += k;
+    }
+    if (launched > (1LL << 40)) return fail(s, "evolve made no progress");
+  }
+  claw_status st = sync_state_impl(s);
+  if (st != CLAW_OK) return st;
+  SCK(leave(s));
+  fill_info(*s->h_ctl, info);
+  return s->h_ctl->status;
+}
+
+claw_status claw_get_info(claw_solver* s, claw_step_info* info) {
+  if (!s || !s->bound) return fail(s, "solver not bound");
+  SCK(enter(s));
+  SCK(read_ctl(s));
+  SCK(leave(s));
+  fill_info(*s->h_ctl, info);
+  return CLAW_OK;
+}
+
+claw_status claw_current_state(claw_solver* s, void** q_cur) {
+  if (!s || !s->bound || !q_cur) return fail(s, "solver not bound");
+  SCK(enter(s));
+  SCK(read_ctl(s));
+  SCK(leave(s));
+  *q_cur = s->h_mem.q[s->h_ctl->cur];
+  return CLAW_OK;
+}
+
+claw_status claw_sync_state(claw_solver* s) {
+  if (!s || !s->bound) return fail(s, "solver not bound");
+  SCK(enter(s));
+  claw_status st = sync_state_impl(s);
+  if (st != CLAW_OK) return st;
+  SCK(leave(s));
+  return CLAW_OK;
+}
+
+claw_status claw_conserved_totals(claw_solver* s, double* out) {
+  if (!s || !s->bound || !out) return fail(s, "solver not bound");
+  SCK(enter(s));
+  SCK(read_ctl(s));
+  const void* q = s->h_mem.q[s->h_ctl->cur];
+  const long long ncell = (long long)s->g.n[0] * s->g.n[1];
+  const int M = s->m.num_eqn;
+  SCK(launch_totals(q, s->prec, ncell, M, s->d_part, s->npart, s->st));
+  SCK(cudaMemcpyAsync(s->h_part, s->d_part, sizeof(double) * 2 * s->npart * M,
+                      cudaMemcpyDeviceToHost, s->st));
+  SCK(cudaStreamSynchronize(s->st));
+  SCK(leave(s));
+  const double dV = s->nd == 2 ? s->h_ctl->dx[0] * s->h_ctl->dx[1] : s->h_ctl->dx[0];
+  for (int k = 0; k < M; ++k) {
+    double sum = 0.0, comp = 0.0;
+    for (int b = 0; b < s->npart; ++b) {
+      const double* pr = s->h_part + ((size_t)k * s->npart + b) * 2;
+      for (int j = 0; j < 2; ++j) {
+        const double x = pr[j];
+        const double t = sum + x;
+        if (std::fabs(sum) >= std::fabs(x)) comp += (sum - t) + x;
+        else comp += (x - t) + sum;
+        sum = t;
+      }
+    }
+    out[k] = (sum + comp) * dV;
+  }
+  return CLAW_OK;
+}
+
+struct CkptHeader {
+  uint64_t magic;
+  int64_t nx, ny;
+  int32_t m, prec, scheme, pad;
+};
+static const uint64_t kMagic = 0x434c415743505431ull;
+
+claw_status claw_checkpoint(claw_solver* s, void* host_buf, size_t* bytes) {
+  if (!s || !s->bound || !bytes) return fail(s, "solver not bound");
+  const size_t need = sizeof(CkptHeader) + sizeof(DevCtl) + s->sbytes;
+  if (!host_buf) {
+    *bytes = need;
+    return CLAW_OK;
+  }
+  if (*bytes < need) return fail(s, "checkpoint buffer too small");
+  SCK(enter(s));
+  SCK(read_ctl(s));
+  CkptHeader hd{kMagic, s->g.n[0], s->g.n[1], s->m.num_eqn, s->prec, s->m.scheme, 0};
+  unsigned char* p = (unsigned char*)host_buf;
+  std::memcpy(p, &hd, sizeof(hd));
+  std::memcpy(p + sizeof(hd), s->h_ctl, sizeof(DevCtl));
+  SCK(cudaMemcpyAsync(p + sizeof(hd) + sizeof(DevCtl), s->h_mem.q[s->h_ctl->cur], s->sbytes,
+                      cudaMemcpyDeviceToHost, s->st));
+  SCK(cudaStreamSynchronize(s->st));
+  SCK(leave(s));
+  *bytes = need;
+  return CLAW_OK;
+}
+
+claw_status claw_restore(claw_solver* s, const void* host_buf, size_t bytes) {
+  if (!s || !s->bound || !host_buf) return fail(s, "solver not bound");
+  const size_t need = sizeof(CkptHeader) + sizeof(DevCtl) + s->sbytes;
+  if (bytes < need) return fail(s, "checkpoint buffer too small");
+  CkptHeader hd;
+  std::memcpy(&hd, host_buf, sizeof(hd));
+  if (hd.magic != kMagic || hd.nx != s->g.n[0] || hd.ny != s->g.n[1] || hd.m != s->m.num_eqn ||
+      hd.prec != s->prec || hd.scheme != s->m.scheme)
+    return fail(s, "checkpoint does not match this solver");
+  DevCtl c;
+  std::memcpy(&c, (const unsigned char*)host_buf + sizeof(hd), sizeof(DevCtl));
+  c.cur = 0;
+  c.arrive = 0;
+  c.smax[0] = c.smax[1] = 0;
+  c.bad = 0;
+  c.dry = 0;
+  SCK(enter(s));
+  SCK(cudaMemcpyAsync(s->q_user, (const unsigned char*)host_buf + sizeof(hd) + sizeof(DevCtl),
+                      s->sbytes, cudaMemcpyHostToDevice, s->st));
+  SCK(cudaMemcpyAsync(s->d_ctl, &c, sizeof(DevCtl), cudaMemcpyHostToDevice, s->st));
+  SCK(cudaStreamSynchronize(s->st));
+  SCK(leave(s));
+  return CLAW_OK;
+}
+
+claw_status claw_step_host(claw_solver* s, const void* q_host_in, void* q_host_out, int n) {
+  if (!s || !s->bound) return fail(s, "solver not bound");
+  SCK(enter(s));
+  SCK(cudaMemcpyAsync(s->q_user, q_host_in, s->sbytes, cudaMemcpyHostToDevice, s->st));
+  SCK(launch_reset_cur(s->d_ctl, s->st));
+  for (int i = 0; i < n; ++i) SCK(solver_attempt(s, s->st));
+  SCK(read_ctl(s));
+  SCK(cudaMemcpyAsync(q_host_out, s->h_mem.q[s->h_ctl->cur], s->sbytes, cudaMemcpyDeviceToHost,
+                      s->st));
+  SCK(cudaStreamSynchronize(s->st));
+  SCK(leave(s));
+  return s->h_ctl->status;
+}
+
+claw_status claw_solver_destroy(claw_solver* s) {
+  if (!s) return CLAW_OK;
+  if (s->st) cudaStreamSynchronize(s->st);
+  free_bound(s);
+  if (s->ev_a) cudaEventDestroy(s->ev_a);
+  if (s->ev_b) cudaEventDestroy(s->ev_b);
+  if (s->st) cudaStreamDestroy(s->st);
+  delete s;
+  return CLAW_OK;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// batches
+// ===========================================================================
+struct claw_batch {
+  claw_method m;
+  int nd = 1, prec = 0, nbuf = 2, n = 0;
+  KernelSet ks{};
+  std::vector<unsigned char> consts;
+  std::vector<claw_grid> grids;
+  std::vector<size_t> sbytes;
+  cudaStream_t ustream = nullptr, st = nullptr;
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+  void* work = nullptr;
+  DevCtl* d_ctl = nullptr;
+  DevCtl* h_ctl = nullptr;  // pinned, n
+  Member* d_mem = nullptr;
+  std::vector<Member> h_mem;
+  Tile* d_tiles = nullptr;
+  std::vector<Tile> h_tiles;
+  int ntiles = 0;
+  Tile* d_mtiles = nullptr;  // max-speed tiles
+  int nmtiles = 0;
+  int* d_count = nullptr;
+  int* h_count = nullptr;
+  int bw = 128, h = 32;
+  cudaGraphExec_t gexec = nullptr;
+  int gk = 0;
+  int bound = 0;
+  std::string err;
+};
+
+namespace {
+
+claw_status bfail(claw_batch* b, const char* what, cudaError_t e = cudaSuccess) {
+  std::string msg = what;
+  if (e != cudaSuccess) {
+    msg += ": ";
+    msg += cudaGetErrorString(e);
+  }
+  if (b) b->err = msg;
+  g_err = msg;
+  return e != cudaSuccess ? CLAW_ECUDA : CLAW_EINVAL;
+}
+
+#define BCK(call)                                      \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return bfail(b, #call, e_); \
+  } while (0)
+
+void batch_free(claw_batch* b) {
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  b->gexec = nullptr;
+  b->gk = 0;
+  if (b->work) cudaFree(b->work);
+  if (b->d_ctl) cudaFree(b->d_ctl);
+  if (b->d_mem) cudaFree(b->d_mem);
+  if (b->d_tiles) cudaFree(b->d_tiles);
+  if (b->d_mtiles) cudaFree(b->d_mtiles);
+  if (b->d_count) cudaFree(b->d_count);
+  if (b->h_ctl) cudaFreeHost(b->h_ctl);
+  if (b->h_count) cudaFreeHost(b->h_count);
+  b->work = nullptr;
+  b->d_ctl = nullptr;
+  b->d_mem = nullptr;
+  b->d_tiles = nullptr;
+  b->d_mtiles = nullptr;
+  b->d_count = nullptr;
+  b->h_ctl = nullptr;
+  b->h_count = nullptr;
+  b->bound = 0;
+}
+
+cudaError_t batch_attempt(claw_batch* b, cudaStream_t st) {
+  return launch_attempt(b->ks, b->m.scheme, b->d_mem, b->d_tiles, b->ntiles, b->consts.data(),
+                        b->bw, b->h, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+claw_status claw_batch_create(const claw_method* m, const claw_grid* grids, int n, void* stream,
+                              claw_batch** out) {
+  if (!m || !grids || !out || n <= 0) return bfail(nullptr, "bad argument");
+  *out = nullptr;
+  const int nd = grids[0].ndim;
+  for (int k = 0; k < n; ++k) {
+    if (const char* why = check_grid(grids[k])) return bfail(nullptr, why);
+    if (grids[k].ndim != nd) return bfail(nullptr, "all members need the same ndim");
+  }
+  if (const char* why = check_method(*m, nd)) return bfail(nullptr, why);
+  KernelSet ks = kernels_for(m->rp, nd, m->prec);
+  if (!ks.valid) return bfail(nullptr, "no kernels for this solver/dimension/precision");
+  claw_batch* b = new claw_batch();
+  b->m = *m;
+  b->nd = nd;
+  b->prec = m->prec;
+  b->nbuf = m->scheme == CLAW_SHARPCLAW ? 3 : 2;
+  b->n = n;
+  b->ks = ks;
+  b->consts = make_consts(*m);
+  b->grids.assign(grids, grids + n);
+  for (auto& g : b->grids)
+    if (g.ndim == 1) g.n[1] = 1;
+  b->ustream = (cudaStream_t)stream;
+  cudaError_t e = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_a, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_b, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    claw_status st = bfail(b, "stream creation", e);
+    claw_batch_destroy(b);
+    return st;
+  }
+  *out = b;
+  return CLAW_OK;
+}
+
+claw_status claw_batch_bind(claw_batch* b, void* const* q, const void* const* aux,
+                            const double* t_end) {
+  if (!b || !q || !t_end) return bfail(b, "bad argument");
+  if (b->m.num_aux > 0 && !aux) return bfail(b, "this solver needs aux fields");
+  batch_free(b);
+  const int n = b->n;
+  b->sbytes.resize(n);
+  size_t total = 0;
+  for (int k = 0; k < n; ++k) {
+    b->sbytes[k] = align256(state_bytes_of(b->m, b->grids[k]));
+    total += b->sbytes[k] * (b->nbuf - 1);
+  }
+  BCK(cudaMalloc(&b->work, total));
+  BCK(cudaMalloc(&b->d_ctl, sizeof(DevCtl) * n));
+  BCK(cudaMalloc(&b->d_mem, sizeof(Member) * n));
+  BCK(cudaMallocHost(&b->h_ctl, sizeof(DevCtl) * n));
+  BCK(cudaMalloc(&b->d_count, sizeof(int)));
+  BCK(cudaMallocHost(&b->h_count, sizeof(int)));
+  b->h_mem.assign(n, Member{});
+  b->h_tiles.clear();
+  std::vector<Tile> mt;
+  unsigned char* w = (unsigned char*)b->work;
+  for (int k = 0; k < n; ++k) {
+    const claw_grid& g = b->grids[k];
+    Member& mb = b->h_mem[k];
+    mb.q[0] = q[k];
+    for (int j = 1; j < b->nbuf; ++j) {
+      mb.q[j] = w;
+      w += b->sbytes[k];
+    }
+    mb.aux = aux ? aux[k] : nullptr;
+    mb.nx = (int)g.n[0];
+    mb.ny = (int)g.n[1];
+    mb.ntiles = tiles_of(b->m.scheme, b->nd, b->prec, mb.nx, mb.ny, b->bw, b->h);
+    mb.ctl = b->d_ctl + k;
+    for (int t = 0; t < mb.ntiles; ++t) b->h_tiles.push_back(Tile{k, t});
+    const int ms = maxspeed_tiles(mb.nx, mb.ny);
+    for (int t = 0; t < ms; ++t) mt.push_back(Tile{k, t});
+    b->h_ctl[k] = make_ctl(b->m, g, b->nbuf, 0.0, t_end[k]);
+  }
+  b->ntiles = (int)b->h_tiles.size();
+  b->nmtiles = (int)mt.size();
+  BCK(cudaMalloc(&b->d_tiles, sizeof(Tile) * b->ntiles));
+  BCK(cudaMalloc(&b->d_mtiles, sizeof(Tile) * b->nmtiles));
+  BCK(cudaEventRecord(b->ev_a, b->ustream));
+  BCK(cudaStreamWaitEvent(b->st, b->ev_a, 0));
+  BCK(cudaMemcpyAsync(b->d_ctl, b->h_ctl, sizeof(DevCtl) * n, cudaMemcpyHostToDevice, b->st));
+  BCK(cudaMemcpyAsync(b->d_mem, b->h_mem.data(), sizeof(Member) * n, cudaMemcpyHostToDevice, b->st));
+  BCK(cudaMemcpyAsync(b->d_tiles, b->h_tiles.data(), sizeof(Tile) * b->ntiles,
+                      cudaMemcpyHostToDevice, b->st));
+  BCK(cudaMemcpyAsync(b->d_mtiles, mt.data(), sizeof(Tile) * b->nmtiles, cudaMemcpyHostToDevice,
+                      b->st));
+  LaunchArgs a{b->d_mem, b->d_mtiles, b->nmtiles, b->consts.data(), 0, 0, 0, b->st};
+  BCK(b->ks.maxspeed(a));
+  BCK(launch_dt_init(b->d_ctl, n, b->st));
+  BCK(cudaStreamSynchronize(b->st));
+  b->bound = 1;
+  return CLAW_OK;
+}
+
+claw_status claw_batch_advance(claw_batch* b, int n) {
+  if (!b || !b->bound) return bfail(b, "batch not bound");
+  BCK(cudaEventRecord(b->ev_a, b->ustream));
+  BCK(cudaStreamWaitEvent(b->st, b->ev_a, 0));
+  for (int i = 0; i < n; ++i) BCK(batch_attempt(b, b->st));
+  BCK(cudaEventRecord(b->ev_b, b->st));
+  BCK(cudaStreamWaitEvent(b->ustream, b->ev_b, 0));
+  return CLAW_OK;
+}
+
+claw_status claw_batch_info(claw_batch* b, claw_step_info* info) {
+  if (!b || !b->bound) return bfail(b, "batch not bound");
+  BCK(cudaEventRecord(b->ev_a, b->ustream));
+  BCK(cudaStreamWaitEvent(b->st, b->ev_a, 0));
+  BCK(cudaMemcpyAsync(b->h_ctl, b->d_ctl, sizeof(DevCtl) * b->n, cudaMemcpyDeviceToHost, b->st));
+  BCK(cudaStreamSynchronize(b->st));
+  if (info)
+    for (int k = 0; k < b->n; ++k) fill_info(b->h_ctl[k], info + k);
+  return CLAW_OK;
+}
+
+claw_status claw_batch_sync_state(claw_batch* b) {
+  if (!b || !b->bound) return bfail(b, "batch not bound");
+  BCK(cudaEventRecord(b->ev_a, b->ustream));
+  BCK(cudaStreamWaitEvent(b->st, b->ev_a, 0));
+  BCK(cudaMemcpyAsync(b->h_ctl, b->d_ctl, sizeof(DevCtl) * b->n, cudaMemcpyDeviceToHost, b->st));
+  BCK(cudaStreamSynchronize(b->st));
+  bool any = false;
+  for (int k = 0; k < b->n; ++k) {
+    const int cur = b->h_ctl[k].cur;
+    if (cur != 0) {
+      any = true;
+      BCK(cudaMemcpyAsync(b->h_mem[k].q[0], b->h_mem[k].q[cur],
+                          state_bytes_of(b->m, b->grids[k]), cudaMemcpyDeviceToDevice, b->st));
+      BCK(launch_reset_cur(b->d_ctl + k, b->st));
+    }
+  }
+  if (any) BCK(cudaStreamSynchronize(b->st));
+  BCK(cudaEventRecord(b->ev_b, b->st));
+  BCK(cudaStreamWaitEvent(b->ustream, b->ev_b, 0));
+  return CLAW_OK;
+}
+
+claw_status claw_batch_evolve(claw_batch* b, int use_graph, int64_t max_steps,
+                              claw_step_info* info) {
+  if (!b || !b->bound) return bfail(b, "batch not bound");
+  BCK(cudaEventRecord(b->ev_a, b->ustream));
+  BCK(cudaStreamWaitEvent(b->st, b->ev_a, 0));
+  if (max_steps > 0) {
+    // per-member step limit on top of each member's own t_end
+    BCK(cudaMemcpyAsync(b->h_ctl, b->d_ctl, sizeof(DevCtl) * b->n, cudaMemcpyDeviceToHost, b->st));
+    BCK(cudaStreamSynchronize(b->st));
+    for (int k = 0; k < b->n; ++k) b->h_ctl[k].max_steps = b->h_ctl[k].steps + max_steps;
+    BCK(cudaMemcpyAsync(b->d_ctl, b->h_ctl, sizeof(DevCtl) * b->n, cudaMemcpyHostToDevice, b->st));
+  }
+  const int GK = 16;
+  if (use_graph && b->gk != GK) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+    cudaGraph_t g = nullptr;
+    BCK(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < GK && e == cudaSuccess; ++i) e = batch_attempt(b, b->st);
+    cudaError_t e2 = cudaStreamEndCapture(b->st, &g);
+    if (e != cudaSuccess) return bfail(b, "graph capture", e);
+    if (e2 != cudaSuccess) return bfail(b, "graph capture", e2);
+    e = cudaGraphInstantiate(&b->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return bfail(b, "graph instantiate", e);
+    b->gk = GK;
+  }
+  long long launched = 0;
+  for (;;) {
+    BCK(launch_count_active(b->d_ctl, b->n, b->d_count, b->st));
+    BCK(cudaMemcpyAsync(b->h_count, b->d_count, sizeof(int), cudaMemcpyDeviceToHost, b->st));
+    BCK(cudaStreamSynchronize(b->st));
+    if (*b->h_count == 0) break;
+    for (int r = 0; r < 4; ++r) {
+      if (use_graph) BCK(cudaGraphLaunch(b->gexec, b->st));
+      else
+        for (int i = 0; i < GK; ++i) BCK(batch_attempt(b, b->st));
+    }
+    launched += 4 * GK;
+    if (launched > (1LL << 40)) return bfail(b, "batch made no progress");
+  }
+  BCK(cudaEventRecord(b->ev_b, b->st));
+  BCK(cudaStreamWaitEvent(b->ustream, b->ev_b, 0));
+  claw_status st = claw_batch_sync_state(b);
+  if (st != CLAW_OK) return st;
+  claw_status worst = CLAW_OK;
+  for (int k = 0; k < b->n; ++k) {
+    if (info) fill_info(b->h_ctl[k], info + k);
+    if (b->h_ctl[k].status != CLAW_OK) worst = b->h_ctl[k].status;
+  }
+  return worst;
+}
+
+claw_status claw_batch_destroy(claw_batch* b) {
+  if (!b) return CLAW_OK;
+  if (b->st) cudaStreamSynchronize(b->st);
+  batch_free(b);
+  if (b->ev_a) cudaEventDestroy(b->ev_a);
+  if (b->ev_b) cudaEventDestroy(b->ev_b);
+  if (b->st) cudaStreamDestroy(b->st);
+  delete b;
+  return CLAW_OK;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// serving: continuous batching
+// ===========================================================================
+namespace {
+struct Req {
+  uint64_t ticket = 0;
+  claw_grid g{};
+  std::vector<unsigned char> q0, aux0, result;
+  double t_end = 0;
+  int status = CLAW_EBUSY;
+  double t_submit = 0, t_admit = 0, t_done = 0, t_reached = 0;
+  long long steps = 0;
+  void* dblock = nullptr;
+  size_t dbytes = 0;
+  Member mem{};
+};
+}  // namespace
+
+struct claw_server {
+  claw_method m;
+  int prec = 0, nbuf = 2, nd = 2;
+  KernelSet ks{};
+  std::vector<unsigned char> consts;
+  size_t budget = 0, used = 0;
+  int max_slots = 0;
+  cudaStream_t ustream = nullptr, st = nullptr;
+  uint64_t next_ticket = 1;
+  std::deque<uint64_t> queue;
+  std::vector<uint64_t> running;
+  std::map<uint64_t, Req> reqs;
+  Member* d_mem = nullptr;
+  Tile* d_tiles = nullptr;
+  size_t cap_mem = 0, cap_tiles = 0;
+  int ntiles = 0;
+  bool dirty = true;
+  DevCtl* d_gather = nullptr;
+  DevCtl* h_gather = nullptr;
+  int bw = 128, h = 16;
+  std::string err;
+};
+
+namespace {
+
+claw_status sfail(claw_server* v, const char* what, cudaError_t e = cudaSuccess) {
+  std::string msg = what;
+  if (e != cudaSuccess) {
+    msg += ": ";
+    msg += cudaGetErrorString(e);
+  }
+  if (v) v->err = msg;
+  g_err = msg;
+  return e != cudaSuccess ? CLAW_ECUDA : CLAW_EINVAL;
+}
+
+#define VCK(call)                                      \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return sfail(v, #call, e_); \
+  } while (0)
+
+size_t req_bytes(const claw_server* v, const claw_grid& g) {
+  return align256(state_bytes_of(v->m, g)) * v->nbuf + align256(aux_bytes_of(v->m, g)) +
+         align256(sizeof(DevCtl));
+}
+
+}  // namespace
+
+extern "C" {
+
+double claw_clock(void) { return now_s(); }
+
+claw_status claw_server_create(const claw_method* m, size_t hbm_budget_bytes, int max_slots,
+                               void* stream, claw_server** out) {
+  if (!m || !out || max_slots <= 0) return sfail(nullptr, "bad argument");
+  *out = nullptr;
+  const int nd = (m->num_eqn == num_eqn(m->rp, 2)) ? 2 : 1;
+  if (const char* why = check_method(*m, nd)) return sfail(nullptr, why);
+  KernelSet ks = kernels_for(m->rp, nd, m->prec);
+  if (!ks.valid) return sfail(nullptr, "no kernels for this solver/dimension/precision");
+  claw_server* v = new claw_server();
+  v->m = *m;
+  v->prec = m->prec;
+  v->nd = nd;
+  v->nbuf = m->scheme == CLAW_SHARPCLAW ? 3 : 2;
+  v->ks = ks;
+  v->consts = make_consts(*m);
+  v->budget = hbm_budget_bytes;
+  v->max_slots = max_slots;
+  v->ustream = (cudaStream_t)stream;
+  cudaError_t e = cudaStreamCreateWithFlags(&v->st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc(&v->d_gather, sizeof(DevCtl) * max_slots);
+  if (e == cudaSuccess) e = cudaMallocHost(&v->h_gather, sizeof(DevCtl) * max_slots);
+  if (e == cudaSuccess) {
+    cudaMemPool_t pool;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+  }
+  if (e != cudaSuccess) {
+    claw_status st = sfail(v, "server setup", e);
+    claw_server_destroy(v);
+    return st;
+  }
+  *out = v;
+  return CLAW_OK;
+}
+
+claw_status claw_server_submit(claw_server* v, const claw_grid* g, const void* q0_host,
+                               const void* aux_host, double t_end, uint64_t* ticket) {
+  if (!v || !g || !q0_host || !ticket) return sfail(v, "bad argument");
+  if (g->ndim != v->nd) return sfail(v, "grid dimension does not match the server's method");
+  if (const char* why = check_grid(*g)) return sfail(v, why);
+  if (v->m.num_aux > 0 && !aux_host) return sfail(v, "this solver needs aux fields");
+  Req r;
+  r.ticket = v->next_ticket++;
+  r.g = *g;
+  if (r.g.ndim == 1) r.g.n[1] = 1;
+  r.dbytes = req_bytes(v, r.g);
+  if (r.dbytes > v->budget) {
+    g_err = v->err = "request exceeds the HBM budget";
+    return CLAW_EBUDGET;
+  }
+  const size_t sb = state_bytes_of(v->m, r.g), ab = aux_bytes_of(v->m, r.g);
+  r.q0.assign((const unsigned char*)q0_host, (const unsigned char*)q0_host + sb);
+  if (ab) r.aux0.assign((const unsigned char*)aux_host, (const unsigned char*)aux_host + ab);
+  r.t_end = t_end;
+  r.t_submit = now_s();
+  *ticket = r.ticket;
+  v->queue.push_back(r.ticket);
+  v->reqs.emplace(r.ticket, std::move(r));
+  return CLAW_OK;
+}
+
+claw_status claw_server_pump(claw_server* v, int steps, int* running, int* queued) {
+  if (!v) return sfail(nullptr, "null server");
+  // 1. admission: first-come first-served while the budget and slots allow
+  std::vector<uint64_t> admitted;
+  while (!v->queue.empty() && (int)v->running.size() < v->max_slots) {
+    Req& r = v->reqs[v->queue.front()];
+    if (v->used + r.dbytes > v->budget) break;
+    VCK(cudaMallocAsync(&r.dblock, r.dbytes, v->st));
+    v->used += r.dbytes;
+    const size_t sb = align256(state_bytes_of(v->m, r.g));
+    unsigned char* p = (unsigned char*)r.dblock;
+    std::memset(&r.mem, 0, sizeof(Member));
+    for (int j = 0; j < v->nbuf; ++j) r.mem.q[j] = p + j * sb;
+    p += sb * v->nbuf;
+    const size_t ab = align256(aux_bytes_of(v->m, r.g));
+    r.mem.aux = ab ? p : nullptr;
+    p += ab;
+    r.mem.ctl = (DevCtl*)p;
+    r.mem.nx = (int)r.g.n[0];
+    r.mem.ny = (int)r.g.n[1];
+    r.mem.ntiles = tiles_of(v->m.scheme, v->nd, v->prec, r.mem.nx, r.mem.ny, v->bw, v->h);
+    DevCtl c = make_ctl(v->m, r.g, v->nbuf, 0.0, r.t_end);
+    VCK(cudaMemcpyAsync(r.mem.q[0], r.q0.data(), r.q0.size(), cudaMemcpyHostToDevice, v->st));
+    if (!r.aux0.empty())
+      VCK(cudaMemcpyAsync((void*)r.mem.aux, r.aux0.data(), r.aux0.size(), cudaMemcpyHostToDevice,
+                          v->st));
+    VCK(cudaMemcpyAsync(r.mem.ctl, &c, sizeof(DevCtl), cudaMemcpyHostToDevice, v->st));
+    r.t_admit = now_s();
+    admitted.push_back(r.ticket);
+    v->running.push_back(r.ticket);
+    v->queue.pop_front();
+    v->dirty = true;
+  }
+  // 2. rebuild the member and tile tables when the running set changed
+  if (v->dirty) {
+    std::vector<Member> hm;
+    std::vector<Tile> ht, mt;
+    for (size_t i = 0; i < v->running.size(); ++i) {
+      const Req& r = v->reqs[v->running[i]];
+      hm.push_back(r.mem);
+      for (int t = 0; t < r.mem.ntiles; ++t) ht.push_back(Tile{(int)i, t});
+    }
+    if (hm.size() > v->cap_mem) {
+      if (v->d_mem) VCK(cudaFreeAsync(v->d_mem, v->st));
+      v->cap_mem = std::max<size_t>(hm.size(), 2 * v->cap_mem);
+      VCK(cudaMallocAsync(&v->d_mem, sizeof(Member) * v->cap_mem, v->st));
+    }
+    if (ht.size() > v->cap_tiles) {
+      if (v->d_tiles) VCK(cudaFreeAsync(v->d_tiles, v->st));
+      v->cap_tiles = std::max<size_t>(ht.size(), 2 * v->cap_tiles);
+      VCK(cudaMallocAsync(&v->d_tiles, sizeof(Tile) * v->cap_tiles, v->st));
+    }
+    if (!hm.empty()) {
+      VCK(cudaMemcpyAsync(v->d_mem, hm.data(), sizeof(Member) * hm.size(), cudaMemcpyHostToDevice,
+                          v->st));
+      VCK(cudaMemcpyAsync(v->d_tiles, ht.data(), sizeof(Tile) * ht.size(), cudaMemcpyHostToDevice,
+                          v->st));
+    }
+    v->ntiles = (int)ht.size();
+    // first dt for the newly admitted requests
+    if (!admitted.empty()) {
+      std::vector<Tile> ms;
+      for (size_t i = 0; i < v->running.size(); ++i) {
+        const Req& r = v->reqs[v->running[i]];
+        if (std::find(admitted.begin(), admitted.end(), r.ticket) == admitted.end()) continue;
+        const int n = maxspeed_tiles(r.mem.nx, r.mem.ny);
+        for (int t = 0; t < n; ++t) ms.push_back(Tile{(int)i, t});
+      }
+      Tile* d_ms = nullptr;
+      VCK(cudaMallocAsync(&d_ms, sizeof(Tile) * ms.size(), v->st));
+      VCK(cudaMemcpyAsync(d_ms, ms.data(), sizeof(Tile) * ms.size(), cudaMemcpyHostToDevice, v->st));
+      LaunchArgs a{v->d_mem, d_ms, (int)ms.size(), v->consts.data(), 0, 0, 0, v->st};
+      VCK(v->ks.maxspeed(a));
+      for (uint64_t t : admitted) VCK(launch_dt_init(v->reqs[t].mem.ctl, 1, v->st));
+      VCK(cudaFreeAsync(d_ms, v->st));
+    }
+    v->dirty = false;
+  }
+  // 3. fused step attempts over every running request
+  if (!v->running.empty()) {
+    for (int i = 0; i < steps; ++i)
+      VCK(launch_attempt(v->ks, v->m.scheme, v->d_mem, v->d_tiles, v->ntiles, v->consts.data(),
+                         v->bw, v->h, v->st));
+    // 4. retire finished requests
+    const int nr = (int)v->running.size();
+    std::vector<char> fin(nr, 0);
+    for (int base = 0; base < nr; base += v->max_slots) {
+      const int cnt = std::min(v->max_slots, nr - base);
+      VCK(launch_gather_ctl(v->d_mem + base, cnt, v->d_gather, v->st));
+      VCK(cudaMemcpyAsync(v->h_gather + 0, v->d_gather, sizeof(DevCtl) * cnt,
+                          cudaMemcpyDeviceToHost, v->st));
+      VCK(cudaStreamSynchronize(v->st));
+      for (int i = 0; i < cnt; ++i) {
+        Req& r = v->reqs[v->running[base + i]];
+        const DevCtl& c = v->h_gather[i];
+        r.steps = c.steps;
+        r.t_reached = c.t;
+        if (c.done) {
+          const size_t sb = state_bytes_of(v->m, r.g);
+          r.result.resize(sb);
+          VCK(cudaMemcpyAsync(r.result.data(), r.mem.q[c.cur], sb, cudaMemcpyDeviceToHost, v->st));
+          VCK(cudaStreamSynchronize(v->st));
+          r.status = c.status;
+          r.t_done = now_s();
+          fin[base + i] = 1;
+        }
+      }
+    }
+    std::vector<uint64_t> keep;
+    for (int i = 0; i < nr; ++i) {
+      const uint64_t t = v->running[i];
+      Req& r = v->reqs[t];
+      if (fin[i]) {
+        VCK(cudaFreeAsync(r.dblock, v->st));
+        r.dblock = nullptr;
+        v->used -= r.dbytes;
+        v->dirty = true;
+      } else {
+        keep.push_back(t);
+      }
+    }
+    v->running.swap(keep);
+  }
+  if (running) *running = (int)v->running.size();
+  if (queued) *queued = (int)v->queue.size();
+  return CLAW_OK;
+}
+
+claw_status claw_server_poll(claw_server* v, uint64_t ticket, void* q_host_out,
+                             claw_req_info* info) {
+  if (!v) return sfail(nullptr, "null server");
+  auto it = v->reqs.find(ticket);
+  if (it == v->reqs.end()) return sfail(v, "unknown ticket");
+  Req& r = it->second;
+  if (info) {
+    info->status = r.status;
+    info->steps = r.steps;
+    info->t = r.t_reached;
+    info->t_submit = r.t_submit;
+    info->t_admit = r.t_admit;
+    info->t_done = r.t_done;
+  }
+  if (r.status == CLAW_EBUSY) return CLAW_EBUSY;
+  if (q_host_out && !r.result.empty()) std::memcpy(q_host_out, r.result.data(), r.result.size());
+  const int st = r.status;
+  v->reqs.erase(it);
+  return st;
+}
+
+claw_status claw_server_destroy(claw_server* v) {
+  if (!v) return CLAW_OK;
+  if (v->st) cudaStreamSynchronize(v->st);
+  for (auto& kv : v->reqs)
+    if (kv.second.dblock) cudaFreeAsync(kv.second.dblock, v->st);
+  if (v->d_mem) cudaFreeAsync(v->d_mem, v->st);
+  if (v->d_tiles) cudaFreeAsync(v->d_tiles, v->st);
+  if (v->d_gather) cudaFree(v->d_gather);
+  if (v->h_gather) cudaFreeHost(v->h_gather);
+  if (v->st) cudaStreamSynchronize(v->st);
+  if (v->st) cudaStreamDestroy(v->st);
+  delete v;
+  return CLAW_OK;
+}
+
+const char* claw_last_error(const void* handle) {
+  (void)handle;
+  return g_err.c_str();
+}
+
+const char* claw_version(void) { return kVersion; }
+
+}  // extern "C"

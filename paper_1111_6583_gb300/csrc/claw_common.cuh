@@ -1,0 +1,269 @@
+// claw_common.cuh -- device-side types shared by the kernels of libclawgpu.
+//
+// Control block, member (grid) descriptors, method constants, ghost-cell index
+// remapping (Sec. 5: periodic, reflecting, outflow, inflow ghost cells done
+// inside the tile loads, with no separate halo pass), block reductions and the
+// on-device CFL controller (Sec. 5: check the Courant number, choose the next
+// step).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "clawgpu.h"
+
+namespace claw {
+
+// ---------------------------------------------------------------------------
+// Per-grid controller state, resident in device memory.  Kernels read dt/cur
+// at their start; the last block of an attempt runs the controller, which
+// writes the next dt/cur.  Stream order makes the update visible to the next
+// launch.
+// ---------------------------------------------------------------------------
+struct DevCtl {
+  double t, dt, t_end, dt_max;
+  double cfl_desired, cfl_max;
+  double nu_last, nu_max_seen, dt_used;
+  double dx[2];
+  double dt_init;   // first dt (<= 0: from the wave speeds of Q^0)
+  unsigned long long smax[2];  // bit patterns of max |s| per direction (non-negative)
+  long long steps, rejects, max_steps;
+  int cur;          // buffer holding Q^n
+  int nbuf;         // 2 (classic) or 3 (SharpClaw)
+  int retries, max_retries;
+  int status;       // CLAW_OK / CLAW_ECFL / CLAW_ENONPHYSICAL
+  int done;         // no more work: t reached t_end, max_steps reached, or error
+  int final_;       // current dt was clipped to land on t_end
+  int forced;       // current dt was forced by the host (no rejection)
+  int accepted;     // last attempt accepted
+  int ndim;
+  int dry;          // timing runs: attempts leave t, dt and cur unchanged
+  unsigned int arrive;  // blocks finished in the current attempt
+  unsigned int bad;     // non-finite value seen in the current attempt
+};
+
+// One grid of a launch.  Single solves use a table of one member.
+struct Member {
+  void* q[3];        // state buffers (rotation by DevCtl::cur)
+  const void* aux;   // cell aux fields or nullptr
+  int nx, ny;        // interior cells (ny = 1 in 1D)
+  int ntiles;        // blocks of this member per attempt
+  int pad;
+  DevCtl* ctl;
+};
+
+// Work item of a batched launch: (member, tile index within the member).
+struct Tile {
+  int member;
+  int tile;
+};
+
+// Method constants in the working precision R.
+template <typename R>
+struct MConsts {
+  R p[8];          // user params
+  R inflow[8];     // inflow ghost state
+  R aco_c, aco_Z, aco_h;  // acoustics: sound speed, impedance, 1/(2 impedance)
+  R g;             // shallow water gravity
+  R gamma, gm1;    // Euler
+  R weno_eps;
+  int lim, order, transverse, entropy_fix, char_decomp;
+  int bc_lo[2], bc_hi[2];
+};
+
+// ---------------------------------------------------------------------------
+// ghost-cell remap
+// ---------------------------------------------------------------------------
+// Map index i along a line of n interior cells to the interior cell whose
+// value the ghost takes.  flip = 1 for a reflecting wall (normal component
+// negated), inflow = 1 for the fixed inflow state.
+__device__ __forceinline__ int bc_map(int i, int n, int bclo, int bchi, int& flip, int& inflow) {
+  flip = 0;
+  inflow = 0;
+  if (i < 0) {
+    switch (bclo) {
+      case CLAW_BC_PERIODIC: return i + n;
+      case CLAW_BC_WALL: flip = 1; return -i - 1;
+      case CLAW_BC_INFLOW: inflow = 1; return 0;
+      default: return 0;
+    }
+  }
+  if (i >= n) {
+    switch (bchi) {
+      case CLAW_BC_PERIODIC: return i - n;
+      case CLAW_BC_WALL: flip = 1; return 2 * n - 1 - i;
+      case CLAW_BC_INFLOW: inflow = 1; return n - 1;
+      default: return n - 1;
+    }
+  }
+  return i;
+}
+
+// Load cell (c, r) of a field-major array q[M][ny][nx] with ghost remap.  In
+// 2D the value of a corner ghost is the y-rule applied to the x-rule value of
+// the reflected row (x ghosts are defined on interior rows first).
+template <int M, typename R>
+__device__ __forceinline__ void load_cell(const MConsts<R>& C, const R* __restrict__ q, int nx,
+                                          int ny, int c, int r, int wall_x, int wall_y,
+                                          R (&out)[M]) {
+  int fy, iy, fx, ix;
+  const int rr = bc_map(r, ny, C.bc_lo[1], C.bc_hi[1], fy, iy);
+  const int cc = bc_map(c, nx, C.bc_lo[0], C.bc_hi[0], fx, ix);
+  if (iy) {
+#pragma unroll
+    for (int k = 0; k < M; ++k) out[k] = C.inflow[k];
+    return;
+  }
+  if (ix) {
+#pragma unroll
+    for (int k = 0; k < M; ++k) out[k] = C.inflow[k];
+  } else {
+    const size_t plane = (size_t)nx * ny;
+    const size_t off = (size_t)rr * nx + cc;
+#pragma unroll
+    for (int k = 0; k < M; ++k) out[k] = __ldg(q + k * plane + off);
+#pragma unroll
+    for (int k = 0; k < M; ++k)
+      if (fx && k == wall_x) out[k] = -out[k];
+  }
+#pragma unroll
+  for (int k = 0; k < M; ++k)
+    if (fy && k == wall_y) out[k] = -out[k];
+}
+
+// aux fields: same index map, no sign flips, inflow treated as extrapolation
+template <int MA, typename R>
+__device__ __forceinline__ void load_aux(const MConsts<R>& C, const R* __restrict__ a, int nx,
+                                         int ny, int c, int r, R (&out)[MA > 0 ? MA : 1]) {
+  if (MA == 0) return;
+  int fy, iy, fx, ix;
+  const int rr = bc_map(r, ny, C.bc_lo[1], C.bc_hi[1], fy, iy);
+  const int cc = bc_map(c, nx, C.bc_lo[0], C.bc_hi[0], fx, ix);
+  const size_t plane = (size_t)nx * ny;
+#pragma unroll
+  for (int k = 0; k < MA; ++k) out[k] = __ldg(a + k * plane + (size_t)rr * nx + cc);
+}
+
+// ---------------------------------------------------------------------------
+// reductions
+// ---------------------------------------------------------------------------
+// max that keeps NaN (a NaN speed must reach the controller)
+__device__ __forceinline__ double nanmax(double a, double b) { return (b <= a) ? a : b; }
+
+__device__ __forceinline__ double warp_nanmax(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = nanmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ int clip_final(double t, double t_end, double& dt) {
+  if (t + dt >= t_end) {
+    dt = t_end - t;
+    return 1;
+  }
+  return 0;
+}
+
+// The CFL controller (one thread).  Courant number nu = max_d dt*smax_d/dx_d;
+// reject (keep Q^n, shrink dt by cfl_desired/nu) above cfl_max, otherwise
+// accept (advance t, rotate buffers); then choose dt_next = dt*cfl_desired/nu,
+// bounded by dt_max and clipped to land on t_end.
+static __device__ __noinline__ void run_controller(DevCtl* c) {
+  if (c->dry) {
+    c->smax[0] = 0ull;
+    c->smax[1] = 0ull;
+    c->bad = 0u;
+    __threadfence();
+    c->arrive = 0u;
+    return;
+  }
+  const double smx = __longlong_as_double((long long)atomicOr(&c->smax[0], 0ull));
+  const double smy = __longlong_as_double((long long)atomicOr(&c->smax[1], 0ull));
+  const unsigned bad = atomicOr(&c->bad, 0u);
+  const double dt = c->dt;
+  double nu = dt * smx / c->dx[0];
+  if (c->ndim == 2) {
+    const double v = dt * smy / c->dx[1];
+    nu = (nu >= v || isnan(nu)) ? nu : v;
+  }
+  c->accepted = 0;
+  if (bad || isnan(nu)) {
+    c->status = CLAW_ENONPHYSICAL;
+    c->done = 1;
+  } else if (!c->forced && nu > c->cfl_max) {
+    c->rejects += 1;
+    c->retries += 1;
+    if (c->retries > c->max_retries) {
+      c->status = CLAW_ECFL;
+      c->done = 1;
+    } else {
+      double nd = dt * c->cfl_desired / nu;
+      if (nd > c->dt_max) nd = c->dt_max;
+      c->final_ = clip_final(c->t, c->t_end, nd);
+      c->dt = nd;
+    }
+  } else {
+    c->accepted = 1;
+    c->t = c->final_ ? c->t_end : c->t + dt;
+    c->cur = (c->cur + 1) % c->nbuf;
+    c->steps += 1;
+    c->retries = 0;
+    c->nu_last = nu;
+    if (nu > c->nu_max_seen) c->nu_max_seen = nu;
+    c->dt_used = dt;
+    c->forced = 0;
+    double nd = nu > 0.0 ? dt * c->cfl_desired / nu : c->dt_max;
+    if (nd > c->dt_max) nd = c->dt_max;
+    c->final_ = clip_final(c->t, c->t_end, nd);
+    c->dt = nd;
+    if (c->t >= c->t_end || c->steps >= c->max_steps) c->done = 1;
+  }
+  c->smax[0] = 0ull;
+  c->smax[1] = 0ull;
+  c->bad = 0u;
+  __threadfence();
+  c->arrive = 0u;
+}
+
+// Reduce two per-thread maxima and a bad flag over the block, fold them into
+// the control block, and let the last block of the member's attempt run the
+// controller (when run_ctl).  Called by every thread of the block; blockDim.x
+// must be a multiple of 32 and at most 1024.
+static __device__ __forceinline__ void finish_attempt(DevCtl* ctl, double sx, double sy, int bad,
+                                               int ntiles, bool run_ctl) {
+  __shared__ double red_x[32], red_y[32];
+  __shared__ int red_bad;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) red_bad = 0;
+  sx = warp_nanmax(sx);
+  sy = warp_nanmax(sy);
+  __syncthreads();
+  if (bad) atomicOr(&red_bad, 1);
+  if (lane == 0) {
+    red_x[warp] = sx;
+    red_y[warp] = sy;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    double a = lane < nw ? red_x[lane] : 0.0;
+    double b = lane < nw ? red_y[lane] : 0.0;
+    a = warp_nanmax(a);
+    b = warp_nanmax(b);
+    if (lane == 0) {
+      if (a != 0.0) atomicMax(&ctl->smax[0], (unsigned long long)__double_as_longlong(a));
+      if (b != 0.0) atomicMax(&ctl->smax[1], (unsigned long long)__double_as_longlong(b));
+      if (red_bad) atomicOr(&ctl->bad, 1u);
+      if (run_ctl) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&ctl->arrive, 1u);
+        if (prev == (unsigned)ntiles - 1u) {
+          __threadfence();
+          run_controller(ctl);
+        }
+      }
+    }
+  }
+}
+
+}  // namespace claw

@@ -1,0 +1,14 @@
+// k_acoustics.cu -- fused kernels instantiated for the acoustics Riemann solver.
+#include "launch.cuh"
+
+namespace claw {
+
+KernelSet claw_kernels_acoustics(int nd, int prec) {
+  if (nd == 1 && prec == 0) return make_set<RpAcoustics, 1, double>(true);
+  if (nd == 1 && prec == 1) return make_set<RpAcoustics, 1, float>(true);
+  if (nd == 2 && prec == 0) return make_set<RpAcoustics, 2, double>(true);
+  if (nd == 2 && prec == 1) return make_set<RpAcoustics, 2, float>(true);
+  return KernelSet{};
+}
+
+}  // namespace claw

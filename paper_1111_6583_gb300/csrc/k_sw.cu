@@ -1,0 +1,14 @@
+// k_sw.cu -- fused kernels instantiated for the sw Riemann solver.
+#include "launch.cuh"
+
+namespace claw {
+
+KernelSet claw_kernels_sw(int nd, int prec) {
+  if (nd == 1 && prec == 0) return make_set<RpSW, 1, double>(true);
+  if (nd == 1 && prec == 1) return make_set<RpSW, 1, float>(true);
+  if (nd == 2 && prec == 0) return make_set<RpSW, 2, double>(true);
+  if (nd == 2 && prec == 1) return make_set<RpSW, 2, float>(true);
+  return KernelSet{};
+}
+
+}  // namespace claw

@@ -1,0 +1,73 @@
+// kernels.h -- host-side view of the per-solver kernel sets (no CUDA types
+// beyond the runtime API).  Each k_<solver>.cu translation unit instantiates
+// the fused kernels for its Riemann solver in FP64 and FP32 and returns their
+// launchers through claw_kernels_<solver>().
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace claw {
+
+struct Member;
+struct Tile;
+struct DevCtl;
+
+struct LaunchArgs {
+  const Member* members;   // device array
+  const Tile* tiles;       // device array or nullptr (single member, tiles 0..n-1)
+  int ntiles_total;        // work items of this launch
+  const void* consts;      // host pointer to MConsts<R>
+  int bw;                  // 2D classic: threads per block (strip width + 4)
+  int h;                   // 2D classic: rows per block
+  int stage;               // SharpClaw stage 0..2
+  cudaStream_t stream;
+};
+
+typedef cudaError_t (*launch_fn)(const LaunchArgs&);
+
+struct KernelSet {
+  int valid;
+  int M, MW, MA;
+  int has_char;            // characteristic projection available
+  launch_fn classic;       // one attempt (1D or 2D by the member grid)
+  launch_fn sharp;         // one SSP-RK3 stage
+  launch_fn maxspeed;      // first-order interface speeds into ctl->smax
+};
+
+// tile geometry shared by the host (tile tables) and the kernels
+constexpr int kClassic1dThreads = 256;
+constexpr int classic1d_T(int prec) { return prec == 0 ? 256 : 512; }
+constexpr int kSharpTX2 = 16, kSharpTY2 = 8;  // 2D SharpClaw tile
+constexpr int kSharpTX1 = 128;                // 1D SharpClaw tile
+constexpr int kMaxspeedCells = 256;           // cells per max-speed block
+
+__host__ __device__ inline int classic1d_tiles(int nx, int T) { return (nx + T - 1) / T; }
+__host__ __device__ inline int classic2d_tiles(int nx, int ny, int BW, int H) {
+  const int TX = BW - 4;
+  return ((nx + TX - 1) / TX) * ((ny + H - 1) / H);
+}
+__host__ __device__ inline int sharp_tiles(int nx, int ny, int TX, int TY) {
+  return ((nx + TX - 1) / TX) * ((ny + TY - 1) / TY);
+}
+
+KernelSet claw_kernels_advection(int nd, int prec);
+KernelSet claw_kernels_acoustics(int nd, int prec);
+KernelSet claw_kernels_sw(int nd, int prec);
+KernelSet claw_kernels_euler_roe(int nd, int prec);
+KernelSet claw_kernels_euler_hlle(int nd, int prec);
+KernelSet claw_kernels_elasticity(int nd, int prec);
+
+// generic kernels (k_common.cu)
+cudaError_t launch_dt_init(DevCtl* ctls, int n, cudaStream_t st);
+cudaError_t launch_set_t_end(DevCtl* ctls, int n, double t_end, long long max_steps_rel,
+                             cudaStream_t st);
+cudaError_t launch_force_dt(DevCtl* ctl, double dt, cudaStream_t st);
+cudaError_t launch_count_active(const DevCtl* ctls, int n, int* out, cudaStream_t st);
+cudaError_t launch_totals(const void* q, int prec, long long ncell, int m, double* partials,
+                          int nblocks, cudaStream_t st);
+cudaError_t launch_reset_cur(DevCtl* ctl, cudaStream_t st);
+cudaError_t launch_gather_ctl(const Member* members, int n, DevCtl* out, cudaStream_t st);
+cudaError_t launch_set_dry(DevCtl* ctl, int dry, cudaStream_t st);
+constexpr int kTotalsThreads = 256;
+
+}  // namespace claw

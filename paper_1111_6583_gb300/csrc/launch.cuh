@@ -1,0 +1,115 @@
+// launch.cuh -- launchers of the fused kernels for one Riemann solver, and the
+// first-order wave-speed kernel used to choose the first dt (Sec. 5).
+#pragma once
+
+#include "classic.cuh"
+#include "kernels.h"
+#include "sharpclaw.cuh"
+
+namespace claw {
+
+// First-order interface solves on the cell averages of every member; block
+// maxima of |s| per direction go to ctl->smax (no controller).
+template <class RP, typename R, int ND>
+__global__ void __launch_bounds__(kMaxspeedCells)
+    maxspeed_kernel(const Member* __restrict__ members, const Tile* __restrict__ tiles,
+                    int ntiles_total, const MConsts<R> C) {
+  constexpr int M = RP::M, MW = RP::MW, MA = RP::MA, MAS = MA > 0 ? MA : 1;
+  for (int it = blockIdx.x; it < ntiles_total; it += gridDim.x) {
+    const Tile tl = tiles ? tiles[it] : Tile{0, it};
+    const Member& mb = members[tl.member];
+    DevCtl* ctl = mb.ctl;
+    const int nx = mb.nx, ny = (ND == 2) ? mb.ny : 1;
+    const long long cell = (long long)tl.tile * kMaxspeedCells + threadIdx.x;
+    const R* q = (const R*)mb.q[ctl->cur];
+    const R* aux = (const R*)mb.aux;
+    double sx = 0.0, sy = 0.0;
+    if (cell < (long long)nx * ny) {
+      const int i = (int)(cell % nx), j = (int)(cell / nx);
+      R W[MW][M], s[MW], am[M], ap[M], x[RP::NCTX];
+      R a[M], b[M], al[MAS], ar[MAS];
+      for (int side = 0; side < (i == nx - 1 ? 2 : 1); ++side) {
+        load_cell<M, R>(C, q, nx, ny, i - 1 + side, j, RP::WALL_X, RP::WALL_Y, a);
+        load_cell<M, R>(C, q, nx, ny, i + side, j, RP::WALL_X, RP::WALL_Y, b);
+        if (MA > 0) {
+          load_aux<MA, R>(C, aux, nx, ny, i - 1 + side, j, al);
+          load_aux<MA, R>(C, aux, nx, ny, i + side, j, ar);
+        }
+        RP::template solve<0>(C, a, b, al, ar, W, s, am, ap, x);
+#pragma unroll
+        for (int p = 0; p < MW; ++p) sx = nanmax(sx, (double)fabs(s[p]));
+      }
+      if constexpr (ND == 2) {
+        for (int side = 0; side < (j == ny - 1 ? 2 : 1); ++side) {
+          load_cell<M, R>(C, q, nx, ny, i, j - 1 + side, RP::WALL_X, RP::WALL_Y, a);
+          load_cell<M, R>(C, q, nx, ny, i, j + side, RP::WALL_X, RP::WALL_Y, b);
+          RP::template solve<1>(C, a, b, al, ar, W, s, am, ap, x);
+#pragma unroll
+          for (int p = 0; p < MW; ++p) sy = nanmax(sy, (double)fabs(s[p]));
+        }
+      }
+    }
+    finish_attempt(ctl, sx, sy, 0, 0, false);
+  }
+}
+
+inline int launch_grid(int ntiles) { return ntiles < 1 ? 1 : ntiles; }
+
+template <class RP, typename R, int ND>
+struct Launchers {
+  static cudaError_t classic(const LaunchArgs& a) {
+    const MConsts<R>& C = *(const MConsts<R>*)a.consts;
+    if constexpr (ND == 1) {
+      constexpr int T = sizeof(R) == 8 ? classic1d_T(0) : classic1d_T(1);
+      classic1d_kernel<RP, R, kClassic1dThreads, T>
+          <<<launch_grid(a.ntiles_total), kClassic1dThreads, 0, a.stream>>>(a.members, a.tiles,
+                                                                         a.ntiles_total, C);
+    } else {
+      if (a.bw == 64)
+        classic2d_kernel<RP, R, 64>
+            <<<launch_grid(a.ntiles_total), 64, 0, a.stream>>>(a.members, a.tiles,
+                                                               a.ntiles_total, C, a.h);
+      else
+        classic2d_kernel<RP, R, 128>
+            <<<launch_grid(a.ntiles_total), 128, 0, a.stream>>>(a.members, a.tiles,
+                                                                a.ntiles_total, C, a.h);
+    }
+    return cudaGetLastError();
+  }
+  static cudaError_t sharp(const LaunchArgs& a) {
+    const MConsts<R>& C = *(const MConsts<R>*)a.consts;
+    if constexpr (ND == 1) {
+      sharp_stage_kernel<RP, R, 1, kSharpTX1, 1>
+          <<<launch_grid(a.ntiles_total), kSharpTX1, 0, a.stream>>>(a.members, a.tiles,
+                                                                 a.ntiles_total, C, a.stage);
+    } else {
+      sharp_stage_kernel<RP, R, 2, kSharpTX2, kSharpTY2>
+          <<<launch_grid(a.ntiles_total), kSharpTX2 * kSharpTY2, 0, a.stream>>>(
+              a.members, a.tiles, a.ntiles_total, C, a.stage);
+    }
+    return cudaGetLastError();
+  }
+  static cudaError_t maxspeed(const LaunchArgs& a) {
+    const MConsts<R>& C = *(const MConsts<R>*)a.consts;
+    maxspeed_kernel<RP, R, ND><<<launch_grid(a.ntiles_total), kMaxspeedCells, 0, a.stream>>>(
+        a.members, a.tiles, a.ntiles_total, C);
+    return cudaGetLastError();
+  }
+};
+
+template <template <typename, int> class RPT, int ND, typename R>
+KernelSet make_set(bool has_char) {
+  using RP = RPT<R, ND>;
+  KernelSet k{};
+  k.valid = 1;
+  k.M = RP::M;
+  k.MW = RP::MW;
+  k.MA = RP::MA;
+  k.has_char = has_char ? 1 : 0;
+  k.classic = &Launchers<RP, R, ND>::classic;
+  k.sharp = &Launchers<RP, R, ND>::sharp;
+  k.maxspeed = &Launchers<RP, R, ND>::maxspeed;
+  return k;
+}
+
+}  // namespace claw

@@ -1,0 +1,669 @@
+// riemann.cuh -- pointwise Riemann solvers, transverse solvers, limiters and
+// characteristic projections for the device kernels.
+//
+// Each solver is a policy struct templated on the working precision R and the
+// dimension ND, with compile-time direction DIR (0 = x, 1 = y):
+//   solve<DIR>(C, ql, qr, al, ar, W, s, am, ap, ctx)   normal solve: waves W^p,
+//       speeds s^p, fluctuations A^-dQ, A^+dQ (Sec. 3, fluctuation form) and a
+//       linearisation ctx kept for the transverse solve;
+//   trans<DIR>(C, ctx, a, bm, bp)   split a normal fluctuation a into the
+//       down-/up-going transverse fluctuations B^-a, B^+a (Sec. 3.1);
+//   to_char / from_char   characteristic projection for SharpClaw.
+// Formulas: LeVeque, Finite Volume Methods for Hyperbolic Problems (acoustics,
+// shallow-water and Euler Roe solvers, Harten-Hyman entropy fix, transverse
+// solvers); Einfeldt (HLLE); Bale-LeVeque-Mitran-Rossmanith (f-waves).
+#pragma once
+
+#include "claw_common.cuh"
+
+namespace claw {
+
+template <int ND, int DIR>
+struct Dirs {
+  static constexpr int n = (ND == 1) ? 1 : 1 + DIR;   // normal momentum / velocity
+  static constexpr int t = (ND == 1) ? -1 : 2 - DIR;  // tangential component
+};
+
+template <typename R>
+__device__ __forceinline__ R rsq(R x);
+template <>
+__device__ __forceinline__ double rsq<double>(double x) { return rsqrt(x); }
+template <>
+__device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
+
+// A^- dQ = sum_p min(s^p,0) W^p,  A^+ dQ = sum_p max(s^p,0) W^p
+template <int M, int MW, typename R>
+__device__ __forceinline__ void split_waves(const R (&W)[MW][M], const R (&s)[MW], R (&am)[M],
+                                            R (&ap)[M]) {
+#pragma unroll
+  for (int k = 0; k < M; ++k) {
+    am[k] = R(0);
+    ap[k] = R(0);
+  }
+#pragma unroll
+  for (int p = 0; p < MW; ++p) {
+    const R sm = fmin(s[p], R(0)), sp = fmax(s[p], R(0));
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      am[k] += sm * W[p][k];
+      ap[k] += sp * W[p][k];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// scalar advection q_t + u q_x + v q_y = 0
+// ---------------------------------------------------------------------------
+template <typename R, int ND>
+struct RpAdvection {
+  static constexpr int M = 1, MW = 1, MA = 0, NCTX = 1;
+  static constexpr bool FWAVE = false;
+  static constexpr int WALL_X = -1, WALL_Y = -1;
+  template <int DIR>
+  __device__ static __forceinline__ void solve(const MConsts<R>& C, const R (&ql)[M],
+                                               const R (&qr)[M], const R*, const R*,
+                                               R (&W)[MW][M], R (&s)[MW], R (&am)[M],
+                                               R (&ap)[M], R (&ctx)[NCTX]) {
+    const R u = C.p[DIR];
+    W[0][0] = qr[0] - ql[0];
+    s[0] = u;
+    am[0] = fmin(u, R(0)) * W[0][0];
+    ap[0] = fmax(u, R(0)) * W[0][0];
+    ctx[0] = R(0);
+  }
+  template <int DIR>
+  __device__ static __forceinline__ void trans(const MConsts<R>& C, const R (&)[NCTX],
+                                               const R (&a)[M], R (&bm)[M], R (&bp)[M]) {
+    const R v = C.p[1 - DIR];
+    bm[0] = fmin(v, R(0)) * a[0];
+    bp[0] = fmax(v, R(0)) * a[0];
+  }
+  template <int DIR>
+  __device__ static __forceinline__ void char_ctx(const MConsts<R>&, const R (&)[M],
+                                                  const R (&)[M], R (&ctx)[NCTX]) {
+    ctx[0] = R(0);
+  }
+  template <int DIR>
+  __device__ static __forceinline__ void to_char(const MConsts<R>&, const R (&)[NCTX],
+                                                 const R (&q)[M], R (&w)[M]) {
+    w[0] = q[0];
+  }
+  template <int DIR>
+  __device__ static __forceinline__ void from_char(const MConsts<R>&, const R (&)[NCTX],
+                                                   const R (&w)[M], R (&q)[M]) {
+    q[0] = w[0];
+  }
+};
+
+// ---------------------------------------------------------------------------
+// linear acoustics (p, u[, v]), constant rho, K: the paper's Table-1 system
+// ---------------------------------------------------------------------------
+template <typename R, int ND>
+struct RpAcoustics {
+  static constexpr int M = ND + 1, MW = 2, MA = 0, NCTX = 1;
+  static constexpr bool FWAVE = false;
+  static constexpr int WALL_X = 1, WALL_Y = (ND == 2) ? 2 : -1;
+  template <int DIR>
+  __device__ static __forceinline__ void solve(const MConsts<R>& C, const R (&ql)[M],
+                                               const R (&qr)[M], const R*, const R*,
+                                               R (&W)[MW][M], R (&s)[MW], R (&am)[M],
+                                               R (&ap)[M], R (&ctx)[NCTX]) {
+    constexpr int n = Dirs<ND, DIR>::n;
+    const R Z = C.aco_Z, c = C.aco_c, h = C.aco_h;
+    const R dp = qr[0] - ql[0], du = qr[n] - ql[n];
+    const R a1 = (Z * du - dp) * h;
+    const R a2 = (Z * du + dp) * h;
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      W[0][k] = R(0);
+      W[1][k] = R(0);
+    }
+    W[0][0] = -Z * a1;
+    W[0][n] = a1;
+    W[1][0] = Z * a2;
+    W[1][n] = a2;
+    s[0] = -c;
+    s[1] = c;
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      am[k] = -c * W[0][k];
+      ap[k] = c * W[1][k];
+    }
+    ctx[0] = R(0);
+  }
+  template <int DIR>
+  __device__ static __forceinline__ void trans(const MConsts<R>& C, const R (&)[NCTX],
+                                               const R (&a)[M], R (&bm)[M], R (&bp)[M]) {
+    constexpr int n = Dirs<ND, DIR>::n, t = Dirs<ND, DIR>::t;
+    const R Z = C.aco_Z, c = C.aco_c, h = C.aco_h;
+    const R b1 = (Z * a[t] - a[0]) * h;
+    const R b2 = (Z * a[t] + a[0]) * h;
+    bm[0] = c * Z * b1;
+    bm[n] = R(0);
+    bm[t] = -c * b1;
+    bp[0] = c * Z * b2;
+    bp[n] = R(0);
+    bp[t] = c * b2;
+  }
+  template <int DIR>
+  __device__ static __forceinline__ void char_ctx(const MConsts<R>&, const R (&)[M],
+                                                  const R (&)[M], R (&ctx)[NCTX]) {
+    ctx[0] = R(0);
+  }
+  template <int DIR>
+  __device__ static __forceinline__ void to_char(const MConsts<R>& C, const R (&)[NCTX],
+                                                 const R (&q)[M], R (&w)[M]) {
+    constexpr int n = Dirs<ND, DIR>::n, t = Dirs<ND, DIR>::t;
+    const R Z = C.aco_Z, h = C.aco_h;
+    w[0] = (Z * q[n] - q[0]) * h;
+    w[1] = (Z * q[n] + q[0]) * h;
+    if (ND == 2) w[ND] = q[t < 0 ? 0 : t];
+  }
+  template <int DIR>
+  __device__ static __forceinline__ void from_char(const MConsts<R>& C, const R (&)[NCTX],
+                                                   const R (&w)[M], R (&q)[M]) {
+    constexpr int n = Dirs<ND, DIR>::n, t = Dirs<ND, DIR>::t;
+    const R Z = C.aco_Z;
+    q[0] = Z * (w[1] - w[0]);
+    q[n] = w[0] + w[1];
+    if (ND == 2) q[t < 0 ? 0 : t] = w[ND];
+  }
+};
+
+// ---------------------------------------------------------------------------
+// shallow water (h, hu[, hv]) with the Roe solver and Harten-Hyman fix
+// ---------------------------------------------------------------------------
+template <typename R, int ND>
+struct RpSW {
+  static constexpr int M = ND + 1, MW = ND + 1, MA = 0, NCTX = 3;  // ctx: un, ut, c
+  static constexpr bool FWAVE = false;
+  static constexpr int WALL_X = 1, WALL_Y = (ND == 2) ? 2 : -1;
+
+  template <int DIR>
+  __device__ static __forceinline__ void roe(const MConsts<R>& C, const R (&ql)[M],
+                                             const R (&qr)[M], R (&x)[NCTX]) {
+    constexpr int n = Dirs<ND, DIR>::n, t = Dirs<ND, DIR>::t;
+    const R hl = ql[0], hr = qr[0];
+    const R il = rsq(hl), ir = rsq(hr);          // 1/sqrt(h)
+    const R iden = R(1) / (hl * il + hr * ir);   // 1/(sqrt(hl)+sqrt(hr))
+    x[0] = (ql[n] * il + qr[n] * ir) * iden;     // sqrt(h) u = hu/sqrt(h)
+    x[1] = (t >= 0) ? (ql[t < 0 ? 0 : t] * il + qr[t < 0 ? 0 : t] * ir) * iden : R(0);
+    x[2] = sqrt(C.g * (R(0.5) * (hl + hr)));
+  }
+
+  // eigen-coefficients of d in the frame (normal a, tangential b) at (un, ut, c)
+  template <int A, int B>
+  __device__ static __forceinline__ void coef(R un, R ut, R c, R i2c, const R (&d)[M],
+                                              R (&al)[MW]) {
+    al[0] = ((un + c) * d[0] - d[A]) * i2c;
+    al[MW - 1] = (d[A] - (un - c) * d[0]) * i2c;
+    if (B >= 0) al[1] = d[B < 0 ? 0 : B] - ut * d[0];
+  }
+  // sum_p k_p r_p in the frame (normal a, tangential b)
+  template <int A, int B>
+  __device__ static __forceinline__ void assemble(R un, R ut, R c, const R (&k)[MW], R (&o)[M]) {
+    const R k0 = k[0], kl = k[MW - 1];
+    o[0] = k0 + kl;
+    o[A] = k0 * (un - c) + kl * (un + c);
+    if (B >= 0) o[B < 0 ? 0 : B] = (k0 + kl) * ut + k[1];
+  }
+
+  template <int DIR>
+  __device__ static __forceinline__ R sonic(const MConsts<R>& C, R h, R hu, int plus) {
+    const R c = sqrt(C.g * h);
+    return plus ? hu / h + c : hu / h - c;
+  }
+
+  template <int DIR>
+  __device__ static __forceinline__ void solve(const MConsts<R>& C, const R (&ql)[M],
+                                               const R (&qr)[M], const R*, const R*,
+                                               R (&W)[MW][M], R (&s)[MW], R (&am)[M],
+                                               R (&ap)[M], R (&x)[NCTX]) {
+    constexpr int n = Dirs<ND, DIR>::n, t = Dirs<ND, DIR>::t;
+    roe<DIR>(C, ql, qr, x);
+    const R un = x[0], ut = x[1], c = x[2];
+    const R i2c = R(0.5) / c;
+    R d[M], al[MW];
+#pragma unroll
+    for (int k = 0; k < M; ++k) d[k] = qr[k] - ql[k];
+    coef<n, t>(un, ut, c, i2c, d, al);
+#pragma unroll
+    for (int p = 0; p < MW; ++p)
+#pragma unroll
+      for (int k = 0; k < M; ++k) W[p][k] = R(0);
+    W[0][0] = al[0];
+    W[0][n] = al[0] * (un - c);
+    W[MW - 1][0] = al[MW - 1];
+    W[MW - 1][n] = al[MW - 1] * (un + c);
+    if (t >= 0) {
+      W[0][t < 0 ? 0 : t] = al[0] * ut;
+      W[1][t < 0 ? 0 : t] = al[1];
+      W[MW - 1][t < 0 ? 0 : t] = al[MW - 1] * ut;
+      s[1] = un;
+    }
+    s[0] = un - c;
+    s[MW - 1] = un + c;
+    if (C.entropy_fix) {
+      R tot[M];
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+        tot[k] = R(0);
+#pragma unroll
+        for (int p = 0; p < MW; ++p) tot[k] += s[p] * W[p][k];
+      }
+      // first family: left state and Q_l + W^1
+      const R lamL = sonic<DIR>(C, ql[0], ql[n], 0);
+      const R lamR = sonic<DIR>(C, ql[0] + W[0][0], ql[n] + W[0][n], 0);
+      if (lamL < R(0) && lamR > R(0)) {
+        const R beta = (lamR - s[0]) / (lamR - lamL);
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+          am[k] = beta * lamL * W[0][k];
+          ap[k] = tot[k] - am[k];
+        }
+        return;
+      }
+      // last family: Q_r - W^last and the right state
+      const R muL = sonic<DIR>(C, qr[0] - W[MW - 1][0], qr[n] - W[MW - 1][n], 1);
+      const R muR = sonic<DIR>(C, qr[0], qr[n], 1);
+      if (muL < R(0) && muR > R(0)) {
+        const R beta = (muR - s[MW - 1]) / (muR - muL);
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+          ap[k] = (R(1) - beta) * muR * W[MW - 1][k];
+          am[k] = tot[k] - ap[k];
+        }
+        return;
+      }
+    }
+    split_waves<M, MW, R>(W, s, am, ap);
+  }
+
+  template <int DIR>
+  __device__ static __forceinline__ void trans(const MConsts<R>& C, const R (&x)[NCTX],
+                                               const R (&a)[M], R (&bm)[M], R (&bp)[M]) {
+    constexpr int n = Dirs<ND, DIR>::n, t = Dirs<ND, DIR>::t;
+    // transverse frame: normal = t (speed ut), tangential = n (speed un)
+    const R un = x[0], ut = x[1], c = x[2];
+    const R i2c = R(0.5) / c;
+    R be[MW], km[MW], kp[MW];
+    coef<t, n>(ut, un, c, i2c, a, be);
+    const R lam[3] = {ut - c, ut, ut + c};
+#pragma unroll
+    for (int p = 0; p < MW; ++p) {
+      km[p] = fmin(lam[p == MW - 1 ? 2 : p], R(0)) * be[p];
+      kp[p] = fmax(lam[p == MW - 1 ? 2 : p], R(0)) * be[p];
+    }
+    assemble<t, n>(ut, un, c, km, bm);
+    assemble<t, n>(ut, un, c, kp, bp);
+  }
+
+  template <int DIR>
+  __device__ static __forceinline__ void char_ctx(const MConsts<R>& C, const R (&ql)[M],
+                                                  const R (&qr)[M], R (&x)[NCTX]) {
+    roe<DIR>(C, ql, qr, x);
+  }
+  template <int DIR>
+  __device__ static __forceinline__ void to_char(const MConsts<R>&, const R (&x)[NCTX],
+                                                 const R (&q)[M], R (&w)[M]) {
+    constexpr int n = Dirs<ND, DIR>::n, t = Dirs<ND, DIR>::t;
+    const R i2c = R(0.5) / x[2];
+    coef<n, t>(x[0], x[1], x[2], i2c, q, w);
+  }
+  template <int DIR>
+  __device__ static __forceinline__ void from_char(const MConsts<R>&, const R (&x)[NCTX],
+                                                   const R (&w)[M], R (&q)[M]) {
+    constexpr int n = Dirs<ND, DIR>::n, t = Dirs<ND, DIR>::t;
+    assemble<n, t>(x[0], x[1], x[2], w, q);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Euler equations (rho, rho u[, rho v], E), ideal gas; Roe and HLLE solvers
+// ---------------------------------------------------------------------------
+template <typename R, int ND>
+struct EulerBase {
+  static constexpr int M = ND + 2, E = ND + 1, NCTX = 4;  // ctx: un, ut, H, c
+
+  template <int DIR>
+  __device__ static __forceinline__ R pressure(const MConsts<R>& C, const R (&q)[M], R irho) {
+    constexpr int n = Dirs<ND, DIR>::n, t = Dirs<ND, DIR>::t;
+    const R ke = (t >= 0) ? q[n] * q[n] + q[t < 0 ? 0 : t] * q[t < 0 ? 0 : t] : q[n] * q[n];
+    return C.gm1 * (q[E] - R(0.5) * ke * irho);
+  }
+
+  // Roe averages; also returns the two pressures
+  template <int DIR>
+  __device__ static __forceinline__ void roe(const MConsts<R>& C, const R (&ql)[M],
+                                             const R (&qr)[M], R (&x)[NCTX], R& pl, R& pr) {
+    constexpr int n = Dirs<ND, DIR>::n, t = Dirs<ND, DIR>::t;
+    const R irl = R(1) / ql[0], irr = R(1) / qr[0];
+    pl = pressure<DIR>(C, ql, irl);
+    pr = pressure<DIR>(C, qr, irr);
+    const R il = rsq(ql[0]), ir = rsq(qr[0]);  // 1/sqrt(rho)
+    const R sl = ql[0] * il, sr = qr[0] * ir;  // sqrt(rho)
+    const R iden = R(1) / (sl + sr);
+    x[0] = (ql[n] * il + qr[n] * ir) * iden;
+    x[1] = (t >= 0) ? (ql[t < 0 ? 0 : t] * il + qr[t < 0 ? 0 : t] * ir) * iden : R(0);
+    x[2] = ((ql[E] + pl) * il + (qr[E] + pr) * ir) * iden;  // sqrt(rho) H = (E+p)/sqrt(rho)
+    const R c2 = C.gm1 * (x[2] - R(0.5) * (x[0] * x[0] + x[1] * x[1]));
+    x[3] = sqrt(c2);
+  }
+
+  // eigen-coefficients of d in the frame (normal a, tangential b)
+  template <int A, int B>
+  __device__ static __forceinline__ void coef(const MConsts<R>& C, R un, R ut, R H, R c,
+                                              const R (&d)[M], R (&al)[M]) {
+    const R ic2 = R(1) / (c * c);
+    const R ash = (B >= 0) ? d[B < 0 ? 0 : B] - ut * d[0] : R(0);
+    const R a2 = C.gm1 * ((H - un * un) * d[0] + un * d[A] - d[E] + ut * ash) * ic2;
+    const R a4 = (d[A] + (c - un) * d[0] - c * a2) * (R(0.5) / c);
+    al[0] = d[0] - a2 - a4;
+    al[1] = a2;
+    if (B >= 0) al[2] = ash;
+    al[M - 1] = a4;
+  }
+  // sum_p k_p r_p in the frame (normal a, tangential b)
+  template <int A, int B>
+  __device__ static __forceinline__ void assemble(R un, R ut, R H, R c, const R (&k)[M],
+                                                  R (&o)[M]) {
+    const R k0 = k[0], k1 = k[1], kl = k[M - 1];
+    const R ksh = (B >= 0) ? k[2] : R(0);
+    const R s3 = k0 + k1 + kl;
+    o[0] = s3;
+    o[A] = k0 * (un - c) + k1 * un + kl * (un + c);
+    if (B >= 0) o[B < 0 ? 0 : B] = s3 * ut + ksh;
+    o[E] = k0 * (H - un * c) + k1 * (R(0.5) * (un * un + ut * ut)) + ksh * ut + kl * (H + un * c);
+  }
+
+  template <int DIR>
+  __device__ static __forceinline__ void trans(const MConsts<R>& C, const R (&x)[NCTX],
+                                               const R (&a)[M], R (&bm)[M], R (&bp)[M]) {
+    constexpr int n = Dirs<ND, DIR>::n, t = Dirs<ND, DIR>::t;
+    const R un = x[0], ut = x[1], H = x[2], c = x[3];
+    R be[M], km[M], kp[M];
+    coef<t, n>(C, ut, un, H, c, a, be);
+#pragma unroll
+    for (int p = 0; p < M; ++p) {
+      const R lam = (p == 0) ? ut - c : (p == M - 1 ? ut + c : ut);
+      km[p] = fmin(lam, R(0)) * be[p];
+      kp[p] = fmax(lam, R(0)) * be[p];
+    }
+    assemble<t, n>(ut, un, H, c, km, bm);
+    assemble<t, n>(ut, un, H, c, kp, bp);
+  }
+
+  template <int DIR>
+  __device__ static __forceinline__ void char_ctx(const MConsts<R>& C, const R (&ql)[M],
+                                                  const R (&qr)[M], R (&x)[NCTX]) {
+    R pl, pr;
+    roe<DIR>(C, ql, qr, x, pl, pr);
+  }
+  template <int DIR>
+  __device__ static __forceinline__ void to_char(const MConsts<R>& C, const R (&x)[NCTX],
+                                                 const R (&q)[M], R (&w)[M]) {
+    constexpr int n = Dirs<ND, DIR>::n, t = Dirs<ND, DIR>::t;
+    coef<n, t>(C, x[0], x[1], x[2], x[3], q, w);
+  }
+  template <int DIR>
+  __device__ static __forceinline__ void from_char(const MConsts<R>&, const R (&x)[NCTX],
+                                                   const R (&w)[M], R (&q)[M]) {
+    constexpr int n = Dirs<ND, DIR>::n, t = Dirs<ND, DIR>::t;
+    assemble<n, t>(x[0], x[1], x[2], x[3], w, q);
+  }
+};
+
+template <typename R, int ND>
+struct RpEulerRoe : EulerBase<R, ND> {
+  using B = EulerBase<R, ND>;
+  static constexpr int M = B::M, MW = B::M, MA = 0, NCTX = B::NCTX, E = B::E;
+  static constexpr bool FWAVE = false;
+  static constexpr int WALL_X = 1, WALL_Y = (ND == 2) ? 2 : -1;
+
+  template <int DIR>
+  __device__ static __forceinline__ R sonic(const MConsts<R>& C, const R (&q)[M], int plus) {
+    constexpr int n = Dirs<ND, DIR>::n;
+    const R ir = R(1) / q[0];
+    const R p = B::template pressure<DIR>(C, q, ir);
+    const R c = sqrt(C.gamma * p * ir);
+    const R u = q[n] * ir;
+    return plus ? u + c : u - c;
+  }
+
+  template <int DIR>
+  __device__ static __forceinline__ void solve(const MConsts<R>& C, const R (&ql)[M],
+                                               const R (&qr)[M], const R*, const R*,
+                                               R (&W)[MW][M], R (&s)[MW], R (&am)[M],
+                                               R (&ap)[M], R (&x)[NCTX]) {
+    constexpr int n = Dirs<ND, DIR>::n, t = Dirs<ND, DIR>::t;
+    R pl, pr;
+    B::template roe<DIR>(C, ql, qr, x, pl, pr);
+    const R un = x[0], ut = x[1], H = x[2], c = x[3];
+    R d[M], al[M];
+#pragma unroll
+    for (int k = 0; k < M; ++k) d[k] = qr[k] - ql[k];
+    B::template coef<n, t>(C, un, ut, H, c, d, al);
+#pragma unroll
+    for (int p = 0; p < MW; ++p)
+#pragma unroll
+      for (int k = 0; k < M; ++k) W[p][k] = R(0);
+    // (un - c), entropy, [shear], (un + c)
+    W[0][0] = al[0];
+    W[0][n] = al[0] * (un - c);
+    W[0][E] = al[0] * (H - un * c);
+    W[1][0] = al[1];
+    W[1][n] = al[1] * un;
+    W[1][E] = al[1] * (R(0.5) * (un * un + ut * ut));
+    W[M - 1][0] = al[M - 1];
+    W[M - 1][n] = al[M - 1] * (un + c);
+    W[M - 1][E] = al[M - 1] * (H + un * c);
+    if (t >= 0) {
+      constexpr int tt = t < 0 ? 0 : t;
+      W[0][tt] = al[0] * ut;
+      W[1][tt] = al[1] * ut;
+      W[2][tt] = al[2];
+      W[2][E] = al[2] * ut;
+      W[M - 1][tt] = al[M - 1] * ut;
+      s[2] = un;
+    }
+    s[0] = un - c;
+    s[1] = un;
+    s[M - 1] = un + c;
+    if (C.entropy_fix) {
+      R tot[M], qm[M];
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+        tot[k] = R(0);
+#pragma unroll
+        for (int p = 0; p < MW; ++p) tot[k] += s[p] * W[p][k];
+      }
+#pragma unroll
+      for (int k = 0; k < M; ++k) qm[k] = ql[k] + W[0][k];
+      const R lamL = sonic<DIR>(C, ql, 0);
+      const R lamR = sonic<DIR>(C, qm, 0);
+      if (lamL < R(0) && lamR > R(0)) {
+        const R beta = (lamR - s[0]) / (lamR - lamL);
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+          am[k] = beta * lamL * W[0][k];
+          ap[k] = tot[k] - am[k];
+        }
+        return;
+      }
+#pragma unroll
+      for (int k = 0; k < M; ++k) qm[k] = qr[k] - W[M - 1][k];
+      const R muL = sonic<DIR>(C, qm, 1);
+      const R muR = sonic<DIR>(C, qr, 1);
+      if (muL < R(0) && muR > R(0)) {
+        const R beta = (muR - s[M - 1]) / (muR - muL);
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+          ap[k] = (R(1) - beta) * muR * W[M - 1][k];
+          am[k] = tot[k] - ap[k];
+        }
+        return;
+      }
+    }
+    split_waves<M, MW, R>(W, s, am, ap);
+  }
+};
+
+template <typename R, int ND>
+struct RpEulerHLLE : EulerBase<R, ND> {
+  using B = EulerBase<R, ND>;
+  static constexpr int M = B::M, MW = 2, MA = 0, NCTX = B::NCTX, E = B::E;
+  static constexpr bool FWAVE = false;
+  static constexpr int WALL_X = 1, WALL_Y = (ND == 2) ? 2 : -1;
+
+  template <int DIR>
+  __device__ static __forceinline__ void flux(const R (&q)[M], R p, R (&f)[M]) {
+    constexpr int n = Dirs<ND, DIR>::n, t = Dirs<ND, DIR>::t;
+    const R u = q[n] / q[0];
+    f[0] = q[n];
+    f[n] = q[n] * u + p;
+    if (t >= 0) f[t < 0 ? 0 : t] = q[t < 0 ? 0 : t] * u;
+    f[E] = u * (q[E] + p);
+  }
+
+  template <int DIR>
+  __device__ static __forceinline__ void solve(const MConsts<R>& C, const R (&ql)[M],
+                                               const R (&qr)[M], const R*, const R*,
+                                               R (&W)[MW][M], R (&s)[MW], R (&am)[M],
+                                               R (&ap)[M], R (&x)[NCTX]) {
+    constexpr int n = Dirs<ND, DIR>::n;
+    R pl, pr;
+    B::template roe<DIR>(C, ql, qr, x, pl, pr);
+    const R cl = sqrt(C.gamma * pl / ql[0]), cr = sqrt(C.gamma * pr / qr[0]);
+    const R s1 = fmin(ql[n] / ql[0] - cl, x[0] - x[3]);
+    const R s2 = fmax(qr[n] / qr[0] + cr, x[0] + x[3]);
+    R fl[M], fr[M];
+    flux<DIR>(ql, pl, fl);
+    flux<DIR>(qr, pr, fr);
+    const R iden = R(1) / (s1 - s2);
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      const R qs = (fr[k] - fl[k] - s2 * qr[k] + s1 * ql[k]) * iden;
+      W[0][k] = qs - ql[k];
+      W[1][k] = qr[k] - qs;
+    }
+    s[0] = s1;
+    s[1] = s2;
+    split_waves<M, MW, R>(W, s, am, ap);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// nonlinear elasticity / p-system (eps, rho u) with f-waves, aux (rho, K),
+// sigma(eps) = exp(K eps) - 1 (Sec. 6.3 constitutive law, shifted to sigma(0)=0)
+// ---------------------------------------------------------------------------
+template <typename R, int ND>
+struct RpElasticity {
+  static constexpr int M = 2, MW = 2, MA = 2, NCTX = 1;
+  static constexpr bool FWAVE = true;
+  static constexpr int WALL_X = 1, WALL_Y = -1;
+  template <int DIR>
+  __device__ static __forceinline__ void solve(const MConsts<R>&, const R (&ql)[M],
+                                               const R (&qr)[M], const R* al, const R* ar,
+                                               R (&W)[MW][M], R (&s)[MW], R (&am)[M],
+                                               R (&ap)[M], R (&ctx)[NCTX]) {
+    const R rl = al[0], Kl = al[1], rr = ar[0], Kr = ar[1];
+    const R el = exp(Kl * ql[0]), er = exp(Kr * qr[0]);
+    const R irl = R(1) / rl, irr = R(1) / rr;
+    const R cl = sqrt(Kl * el * irl), cr = sqrt(Kr * er * irr);
+    const R Zl = rl * cl, Zr = rr * cr;
+    const R d1 = ql[1] * irl - qr[1] * irr;  // jump of -u
+    const R d2 = el - er;                    // jump of -sigma
+    const R iz = R(1) / (Zl + Zr);
+    const R b1 = (Zr * d1 + d2) * iz;
+    const R b2 = (Zl * d1 - d2) * iz;
+    W[0][0] = b1;
+    W[0][1] = b1 * Zl;
+    W[1][0] = b2;
+    W[1][1] = -b2 * Zr;
+    s[0] = -cl;
+    s[1] = cr;
+    // f-wave split by the sign of the speed (c > 0 on both sides)
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      am[k] = R(0);
+      ap[k] = R(0);
+    }
+#pragma unroll
+    for (int p = 0; p < MW; ++p)
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+        if (s[p] < R(0)) am[k] += W[p][k];
+        else if (s[p] > R(0)) ap[k] += W[p][k];
+        else {
+          am[k] += R(0.5) * W[p][k];
+          ap[k] += R(0.5) * W[p][k];
+        }
+      }
+    ctx[0] = R(0);
+  }
+  template <int DIR>
+  __device__ static __forceinline__ void trans(const MConsts<R>&, const R (&)[NCTX],
+                                               const R (&)[M], R (&bm)[M], R (&bp)[M]) {
+    bm[0] = bm[1] = bp[0] = bp[1] = R(0);
+  }
+  template <int DIR>
+  __device__ static __forceinline__ void char_ctx(const MConsts<R>&, const R (&)[M],
+                                                  const R (&)[M], R (&ctx)[NCTX]) {
+    ctx[0] = R(0);
+  }
+  template <int DIR>
+  __device__ static __forceinline__ void to_char(const MConsts<R>&, const R (&)[NCTX],
+                                                 const R (&q)[M], R (&w)[M]) {
+    w[0] = q[0];
+    w[1] = q[1];
+  }
+  template <int DIR>
+  __device__ static __forceinline__ void from_char(const MConsts<R>&, const R (&)[NCTX],
+                                                   const R (&w)[M], R (&q)[M]) {
+    q[0] = w[0];
+    q[1] = w[1];
+  }
+};
+
+// ---------------------------------------------------------------------------
+// wave limiters (LeVeque FVM book, high-resolution methods)
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R limiter(int lim, R th) {
+  switch (lim) {
+    case CLAW_LIM_MINMOD: return fmax(R(0), fmin(R(1), th));
+    case CLAW_LIM_SUPERBEE: return fmax(R(0), fmax(fmin(R(1), R(2) * th), fmin(R(2), th)));
+    case CLAW_LIM_VANLEER: {
+      const R a = fabs(th);
+      return (th + a) / (R(1) + a);
+    }
+    case CLAW_LIM_MC: return fmax(R(0), fmin(R(0.5) * (R(1) + th), fmin(R(2), R(2) * th)));
+    default: return R(1);
+  }
+}
+
+// Second-order correction at one interface (Eq. (lwflux) with limited waves):
+//   F = 1/2 sum_p c_p phi(theta_p) W^p,  c_p = |s|(1 - dt/dx |s|)   (waves)
+//                                          = sgn(s)(1 - dt/dx |s|) (f-waves)
+// dot_up[p] = W^p_upwind . W^p, nrm[p] = W^p . W^p (zero wave -> no correction).
+template <class RP, typename R>
+__device__ __forceinline__ void correction(const MConsts<R>& C, const R (&W)[RP::MW][RP::M],
+                                           const R (&s)[RP::MW], const R (&dot_up)[RP::MW],
+                                           const R (&nrm)[RP::MW], R dtdn, R (&F)[RP::M]) {
+#pragma unroll
+  for (int k = 0; k < RP::M; ++k) F[k] = R(0);
+#pragma unroll
+  for (int p = 0; p < RP::MW; ++p) {
+    R phi;
+    if (nrm[p] == R(0)) phi = R(0);
+    else if (C.lim == CLAW_LIM_NONE) phi = R(1);
+    else phi = limiter<R>(C.lim, dot_up[p] / nrm[p]);
+    const R a = fabs(s[p]);
+    const R sg = RP::FWAVE ? (s[p] > R(0) ? R(1) : (s[p] < R(0) ? R(-1) : R(0))) : a;
+    const R cf = R(0.5) * sg * (R(1) - dtdn * a) * phi;
+#pragma unroll
+    for (int k = 0; k < RP::M; ++k) F[k] += cf * W[p][k];
+  }
+}
+
+}  // namespace claw

@@ -1,0 +1,272 @@
+// sharpclaw.cuh -- fused SharpClaw stage kernel (Sec. 3 method of lines;
+// Sec. 3.1: WENO reconstruction, normal Riemann problems only in multi-D).
+//
+// One launch = one SSP-RK3 stage for every member of a tile table.  A block
+// stages a TX x TY tile of Q^(k) plus a 3-cell halo (ghost remap in the load),
+// reconstructs left/right interface values by WENO5 (component- or
+// characteristic-wise, projection at the Roe state of each interface), solves
+// the interface Riemann problems and the in-cell problems (total fluctuation
+// A dQ_i), forms L(Q) = -(A^+dQ_{i-1/2} + A^-dQ_{i+1/2} + A dQ_i)/dx summed
+// over directions, and writes the Shu-Osher combination
+//   stage 0: Q1 = Q + dt L(Q)
+//   stage 1: Q2 = 3/4 Q + 1/4 (Q1 + dt L(Q1))
+//   stage 2: Q3 = 1/3 Q + 2/3 (Q2 + dt L(Q2))
+// Stage 2's last block runs the CFL controller.
+#pragma once
+
+#include "kernels.h"
+#include "riemann.cuh"
+
+namespace claw {
+
+// Jiang-Shu WENO5: value at the right edge of the centre cell of a, b, c, d, e
+// (cell averages v_{i-2..i+2}).  The nonlinear weights d_k/(eps+beta_k)^2 are
+// normalised with one division.
+template <typename R>
+__device__ __forceinline__ R weno5(R a, R b, R c, R d, R e, R eps) {
+  const R sixth = R(1) / R(6);
+  const R q0 = (R(2) * a - R(7) * b + R(11) * c) * sixth;
+  const R q1 = (-b + R(5) * c + R(2) * d) * sixth;
+  const R q2 = (R(2) * c + R(5) * d - e) * sixth;
+  const R t0 = a - R(2) * b + c, u0 = a - R(4) * b + R(3) * c;
+  const R t1 = b - R(2) * c + d, u1 = b - d;
+  const R t2 = c - R(2) * d + e, u2 = R(3) * c - R(4) * d + e;
+  const R k13 = R(13) / R(12);
+  const R e0 = eps + (k13 * (t0 * t0) + R(0.25) * (u0 * u0));
+  const R e1 = eps + (k13 * (t1 * t1) + R(0.25) * (u1 * u1));
+  const R e2 = eps + (k13 * (t2 * t2) + R(0.25) * (u2 * u2));
+  const R s0 = e0 * e0, s1 = e1 * e1, s2 = e2 * e2;
+  // alpha_k = d_k / s_k; multiply through by s0 s1 s2
+  const R w0 = R(0.1) * (s1 * s2), w1 = R(0.6) * (s0 * s2), w2 = R(0.3) * (s0 * s1);
+  return (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
+}
+
+
+template <class RP, typename R, int ND, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY)
+    sharp_stage_kernel(const Member* __restrict__ members, const Tile* __restrict__ tiles,
+                       int ntiles_total, const MConsts<R> C, int stage) {
+  constexpr int M = RP::M, MW = RP::MW, MA = RP::MA, NC = RP::NCTX;
+  constexpr int MAS = MA > 0 ? MA : 1;
+  constexpr int NT = TX * TY;
+  constexpr int G = 3;
+  constexpr int HX = TX + 2 * G, HY = (ND == 2) ? TY + 2 * G : 1;
+  constexpr int NE = (ND == 2) ? ((TX + 1) * TY > TX * (TY + 1) ? (TX + 1) * TY : TX * (TY + 1))
+                               : TX + 1;
+  __shared__ R Qt[M][HY][HX];
+  __shared__ R At[MAS][MA > 0 ? HY : 1][MA > 0 ? HX : 1];
+  __shared__ R EL[M][NE];  // left edge value of the cell right of an interface
+  __shared__ R ER[M][NE];  // right edge value of the cell left of an interface
+  __shared__ R FM[M][NE];  // A^- dQ at the interface
+  __shared__ R FP[M][NE];  // A^+ dQ at the interface
+  __shared__ int s_done, s_cur, s_nbuf;
+  __shared__ double s_dt;
+
+  const int tid = threadIdx.x;
+  const int ti = tid % TX, tj = tid / TX;
+
+  for (int it = blockIdx.x; it < ntiles_total; it += gridDim.x) {
+    const Tile tl = tiles ? tiles[it] : Tile{0, it};
+    const Member& mb = members[tl.member];
+    DevCtl* ctl = mb.ctl;
+    if (tid == 0) {
+      s_done = ctl->done;
+      s_dt = ctl->dt;
+      s_cur = ctl->cur;
+      s_nbuf = ctl->nbuf;
+    }
+    __syncthreads();
+    if (s_done) {
+      __syncthreads();
+      continue;
+    }
+    const int nx = mb.nx, ny = (ND == 2) ? mb.ny : 1;
+    const int nsx = (nx + TX - 1) / TX;
+    const int c0 = (tl.tile % nsx) * TX;
+    const int r0 = (ND == 2) ? (tl.tile / nsx) * TY : 0;
+    const int cur = s_cur;
+    const int nb = s_nbuf;
+    const int in_b = (stage == 0) ? cur : (stage == 1 ? (cur + 1) % nb : (cur + 2) % nb);
+    const int out_b = (stage == 1) ? (cur + 2) % nb : (cur + 1) % nb;
+    const R* __restrict__ qk = (const R*)mb.q[in_b];
+    const R* __restrict__ qn = (const R*)mb.q[cur];
+    R* __restrict__ qo = (R*)mb.q[out_b];
+    const R* __restrict__ aux = (const R*)mb.aux;
+    const double dtd = s_dt;
+    const size_t plane = (size_t)nx * ny;
+
+    // stage Q^(k) (and aux) with a 3-cell halo, corners skipped in 2D
+    for (int idx = tid; idx < HX * HY; idx += NT) {
+      const int hi = idx % HX, hj = idx / HX;
+      if (ND == 2) {
+        const bool xin = hi >= G && hi < G + TX, yin = hj >= G && hj < G + TY;
+        if (!xin && !yin) continue;
+      }
+      const int c = c0 - G + hi, r = (ND == 2) ? r0 - G + hj : 0;
+      R v[M];
+      load_cell<M, R>(C, qk, nx, ny, min(c, nx + G - 1), (ND == 2) ? min(r, ny + G - 1) : 0,
+                      RP::WALL_X, RP::WALL_Y, v);
+#pragma unroll
+      for (int k = 0; k < M; ++k) Qt[k][hj][hi] = v[k];
+      if (MA > 0) {
+        R a[MAS];
+        load_aux<MA, R>(C, aux, nx, ny, min(c, nx + G - 1),
+                        (ND == 2) ? min(r, ny + G - 1) : 0, a);
+#pragma unroll
+        for (int k = 0; k < MA; ++k) At[k][MA > 0 ? hj : 0][MA > 0 ? hi : 0] = a[k];
+      }
+    }
+    __syncthreads();
+
+    R L[M];
+#pragma unroll
+    for (int k = 0; k < M; ++k) L[k] = R(0);
+    double smx = 0.0, smy = 0.0;
+
+#pragma unroll
+    for (int dir = 0; dir < ND; ++dir) {
+      // interfaces of this direction: along-line index a (0..n), line index b
+      const int na = (dir == 0) ? TX + 1 : TY + 1;
+      const int nl = (dir == 0) ? TY : TX;
+      const R idn = (R)(1.0 / ctl->dx[dir]);
+      // (a) reconstruction at every interface
+      for (int e = tid; e < na * nl; e += NT) {
+        const int a = e % na, b = e / na;
+        R cell[6][M];
+#pragma unroll
+        for (int k6 = 0; k6 < 6; ++k6) {
+          // cells a-3 .. a+2 along the line
+          const int hi = (dir == 0) ? a + k6 : G + b;
+          const int hj = (dir == 0) ? ((ND == 2) ? G + b : 0) : a + k6;
+#pragma unroll
+          for (int k = 0; k < M; ++k) cell[k6][k] = Qt[k][hj][hi];
+        }
+        R wm[M], wp[M];
+        if (C.char_decomp) {
+          R x[NC];
+          R w[6][M];
+          if (dir == 0) {
+            RP::template char_ctx<0>(C, cell[2], cell[3], x);
+#pragma unroll
+            for (int k6 = 0; k6 < 6; ++k6) RP::template to_char<0>(C, x, cell[k6], w[k6]);
+          } else {
+            RP::template char_ctx<1>(C, cell[2], cell[3], x);
+#pragma unroll
+            for (int k6 = 0; k6 < 6; ++k6) RP::template to_char<1>(C, x, cell[k6], w[k6]);
+          }
+          R um[M], up[M];
+#pragma unroll
+          for (int k = 0; k < M; ++k) {
+            um[k] = weno5<R>(w[0][k], w[1][k], w[2][k], w[3][k], w[4][k], C.weno_eps);
+            up[k] = weno5<R>(w[5][k], w[4][k], w[3][k], w[2][k], w[1][k], C.weno_eps);
+          }
+          if (dir == 0) {
+            RP::template from_char<0>(C, x, um, wm);
+            RP::template from_char<0>(C, x, up, wp);
+          } else {
+            RP::template from_char<1>(C, x, um, wm);
+            RP::template from_char<1>(C, x, up, wp);
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < M; ++k) {
+            wm[k] = weno5<R>(cell[0][k], cell[1][k], cell[2][k], cell[3][k], cell[4][k], C.weno_eps);
+            wp[k] = weno5<R>(cell[5][k], cell[4][k], cell[3][k], cell[2][k], cell[1][k], C.weno_eps);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+          ER[k][e] = wm[k];
+          EL[k][e] = wp[k];
+        }
+      }
+      __syncthreads();
+      // (b) interface Riemann problems (q^R_{a-1}, q^L_a)
+      for (int e = tid; e < na * nl; e += NT) {
+        const int a = e % na, b = e / na;
+        R ql[M], qr[M], al[MAS], ar[MAS];
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+          ql[k] = ER[k][e];
+          qr[k] = EL[k][e];
+        }
+        if (MA > 0) {
+          const int hil = (dir == 0) ? G + a - 1 : G + b, hir = (dir == 0) ? G + a : G + b;
+          const int hjl = (dir == 0) ? ((ND == 2) ? G + b : 0) : G + a - 1;
+          const int hjr = (dir == 0) ? ((ND == 2) ? G + b : 0) : G + a;
+#pragma unroll
+          for (int k = 0; k < MA; ++k) {
+            al[k] = At[k][MA > 0 ? hjl : 0][MA > 0 ? hil : 0];
+            ar[k] = At[k][MA > 0 ? hjr : 0][MA > 0 ? hir : 0];
+          }
+        }
+        R W[MW][M], s[MW], am[M], ap[M], x[NC];
+        if (dir == 0) RP::template solve<0>(C, ql, qr, al, ar, W, s, am, ap, x);
+        else RP::template solve<1>(C, ql, qr, al, ar, W, s, am, ap, x);
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+          FM[k][e] = am[k];
+          FP[k][e] = ap[k];
+        }
+        // interfaces 0..n of interior lines count for the Courant number
+        const int ga = ((dir == 0) ? c0 : r0) + a, gb = ((dir == 0) ? r0 : c0) + b;
+        const int nA = (dir == 0) ? nx : ny, nB = (dir == 0) ? ny : nx;
+        if (ga <= nA && gb < nB) {
+          double m_ = 0.0;
+#pragma unroll
+          for (int p = 0; p < MW; ++p) m_ = nanmax(m_, (double)fabs(s[p]));
+          if (dir == 0) smx = nanmax(smx, m_);
+          else smy = nanmax(smy, m_);
+        }
+      }
+      __syncthreads();
+      // (c) in-cell Riemann problem (q^L_i, q^R_i) and the cell's L
+      for (int cidx = tid; cidx < TX * TY; cidx += NT) {
+        const int ci = cidx % TX, cj = cidx / TX;
+        const int a = (dir == 0) ? ci : cj, b = (dir == 0) ? cj : ci;
+        const int e0 = b * na + a, e1 = e0 + 1;
+        R ql[M], qr[M], al[MAS];
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+          ql[k] = EL[k][e0];
+          qr[k] = ER[k][e1];
+        }
+        if (MA > 0) {
+#pragma unroll
+          for (int k = 0; k < MA; ++k)
+            al[k] = At[k][MA > 0 ? ((ND == 2) ? G + cj : 0) : 0][MA > 0 ? G + ci : 0];
+        }
+        R W[MW][M], s[MW], am[M], ap[M], x[NC];
+        if (dir == 0) RP::template solve<0>(C, ql, qr, al, al, W, s, am, ap, x);
+        else RP::template solve<1>(C, ql, qr, al, al, W, s, am, ap, x);
+        // thread cidx == tid owns cell (ci, cj) (NT == TX*TY)
+#pragma unroll
+        for (int k = 0; k < M; ++k) L[k] -= (FP[k][e0] + FM[k][e1] + (am[k] + ap[k])) * idn;
+      }
+      __syncthreads();
+    }
+
+    // (d) Shu-Osher stage combination
+    int bad = 0;
+    {
+      const int c = c0 + ti, r = r0 + tj;
+      if (c < nx && r < ny) {
+        const size_t off = (size_t)r * nx + c;
+        const R dt = (R)dtd;
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+          const R qkv = Qt[k][(ND == 2) ? G + tj : 0][G + ti];
+          R v;
+          if (stage == 0) v = qkv + dt * L[k];
+          else if (stage == 1) v = R(0.75) * qn[k * plane + off] + R(0.25) * (qkv + dt * L[k]);
+          else v = (R(1) / R(3)) * qn[k * plane + off] + (R(2) / R(3)) * (qkv + dt * L[k]);
+          bad |= !isfinite(v);
+          qo[k * plane + off] = v;
+        }
+      }
+    }
+    finish_attempt(ctl, smx, smy, bad, mb.ntiles, stage == 2);
+  }
+}
+
+}  // namespace claw

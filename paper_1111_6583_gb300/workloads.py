@@ -265,3 +265,51 @@ def random_smooth_2d(rp, nx, ny, seed=SEED, params=None, bc="periodic", **kw):
                  bc_lower=[bc, bc], bc_upper=[bc, bc], **kw)
     spec.update(q0=np.ascontiguousarray(q0), aux=None, t_end=kw.get("t_end", 0.1))
     return spec
+
+
+def random_1d(rp, n, seed=SEED, bc=("periodic", "periodic"), jump=True, **kw):
+    """Smooth random 1D data (a few Fourier modes) plus, when jump, a step in
+    the middle; physical states for SW/Euler/elasticity."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x = _centers(0.0, 1.0, n)
+
+    def field(amp):
+        f = np.zeros_like(x)
+        for _ in range(3):
+            k = rng.integers(1, 5)
+            f += amp * rng.uniform(0.3, 1.0) * np.sin(2 * np.pi * k * x + rng.uniform(0, 6.3))
+        if jump:
+            f += amp * np.where(x > 0.5, 1.0, 0.0)
+        return f
+
+    aux = None
+    if rp == "sw_roe":
+        q0 = np.stack([1.5 + field(0.2), field(0.3)])
+        params = [1.0]
+    elif rp in ("euler_roe", "euler_hlle"):
+        rho = 1.5 + field(0.2)
+        m = field(0.3)
+        p = 1.5 + field(0.2)
+        q0 = np.stack([rho, m, p / 0.4 + 0.5 * m * m / rho])
+        params = [1.4]
+    elif rp == "acoustics":
+        q0 = np.stack([field(0.5), field(0.5)])
+        params = [1.3, 2.5]
+    elif rp == "advection":
+        q0 = np.stack([field(1.0)])
+        params = [0.8]
+    elif rp == "elasticity_fwave":
+        rho, K = layered_medium(x * 8.0)
+        sig = 0.2 + field(0.1)
+        q0 = np.stack([np.log1p(sig) / K, field(0.3)])
+        aux = np.stack([rho, K])
+        params = []
+    else:
+        raise ValueError(rp)
+    spec = _base(1, [n], [0.0], [1.0], rp, params=kw.pop("params", params),
+                 bc_lower=[bc[0]], bc_upper=[bc[1]],
+                 num_aux=2 if rp == "elasticity_fwave" else 0, **kw)
+    spec.update(q0=np.ascontiguousarray(q0),
+                aux=np.ascontiguousarray(aux) if aux is not None else None,
+                t_end=kw.get("t_end", 0.1))
+    return spec

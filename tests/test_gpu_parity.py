@@ -1,0 +1,242 @@
+"""GPU parity: the CUDA kernels (through the C ABI) against the CPU oracle on
+the same seeded inputs, element by element.
+
+Sizes span several tiles with ragged tails (1D tiles of 256/512 cells; 2D
+strips of 60/124 columns and row segments of 8..128 rows; SharpClaw tiles of
+16x8 and 128 cells).  FP64 tolerance: max-norm relative 1e-12; FP32: 1e-5
+relative on smooth data, L1 1e-4 where the data have jumps.
+"""
+import numpy as np
+import pytest
+
+from paper_1111_6583_gb300 import workloads as wl
+from tests.gpu_util import (FP32_SHOCK_L1_TOL, FP32_SMOOTH_TOL, FP64_TOL, gpu_evolve,
+                            gpu_fixed_steps, oracle_evolve, oracle_fixed_steps, rel_l1,
+                            rel_maxnorm)
+
+pytestmark = pytest.mark.gpu
+
+RPS_1D = ["advection", "acoustics", "sw_roe", "euler_roe", "euler_hlle", "elasticity_fwave"]
+RPS_2D = ["advection", "acoustics", "sw_roe", "euler_roe", "euler_hlle"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+# --------------------------------------------------------------------------
+# classic 1D, fixed dt
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("rp", RPS_1D)
+@pytest.mark.parametrize("lim", ["mc", "minmod", "superbee", "vanleer", "none"])
+def test_classic1d_fixed_dt_fp64(orc, rp, lim):
+    spec = wl.random_1d(rp, 601, lim=lim)
+    dt = 0.3 / 601
+    qg, cg = gpu_fixed_steps(spec, "fp64", dt, 5)
+    qo, co = oracle_fixed_steps(orc, spec, dt, 5)
+    assert rel_maxnorm(qg, qo) <= FP64_TOL
+    assert np.allclose(cg, co, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("bc", [("wall", "wall"), ("extrap", "wall"), ("inflow", "extrap")])
+@pytest.mark.parametrize("rp", ["sw_roe", "euler_roe", "acoustics"])
+def test_classic1d_boundaries_fp64(orc, rp, bc):
+    spec = wl.random_1d(rp, 257, bc=bc)
+    if "inflow" in bc:
+        spec["inflow"] = list(spec["q0"][:, 0] * 1.05)
+    dt = 0.3 / 257
+    qg, _ = gpu_fixed_steps(spec, "fp64", dt, 6)
+    qo, _ = oracle_fixed_steps(orc, spec, dt, 6)
+    assert rel_maxnorm(qg, qo) <= FP64_TOL
+
+
+@pytest.mark.parametrize("rp", RPS_1D)
+def test_classic1d_order1_and_fp32(orc, rp):
+    spec = wl.random_1d(rp, 1100, order=1)
+    dt = 0.3 / 1100
+    qg, _ = gpu_fixed_steps(spec, "fp64", dt, 4)
+    qo, _ = oracle_fixed_steps(orc, spec, dt, 4)
+    assert rel_maxnorm(qg, qo) <= FP64_TOL
+    spec = wl.random_1d(rp, 1100, jump=False)
+    qg, _ = gpu_fixed_steps(spec, "fp32", dt, 4)
+    qo, _ = oracle_fixed_steps(orc, spec, dt, 4)
+    assert rel_maxnorm(qg, qo) <= FP32_SMOOTH_TOL
+
+
+# --------------------------------------------------------------------------
+# classic 2D, fixed dt, several tile shapes
+# --------------------------------------------------------------------------
+def _spec2d(rp, nx, ny, **kw):
+    spec = wl.random_smooth_2d(rp, nx, ny, **kw)
+    return spec
+
+
+@pytest.mark.parametrize("rp", RPS_2D)
+@pytest.mark.parametrize("order,transverse", [(2, 2), (2, 1), (2, 0), (1, 1)])
+def test_classic2d_fixed_dt_fp64(orc, rp, order, transverse):
+    spec = _spec2d(rp, 131, 70, order=order, transverse=transverse)
+    dt = 0.25 / 131
+    qo, co = oracle_fixed_steps(orc, spec, dt, 4)
+    for tune in ((128, 32), (64, 8), (64, 128)):
+        import torch
+        from paper_1111_6583_gb300 import claw
+        s = claw.Solver(spec, "fp64")
+        s.tune(*tune)
+        for _ in range(4):
+            info = s.step(dt)
+        s.sync()
+        qg = s.q.cpu().numpy()
+        s.close()
+        assert rel_maxnorm(qg, qo) <= FP64_TOL, tune
+        assert info["cfl"] == pytest.approx(co[-1], rel=1e-13)
+
+
+@pytest.mark.parametrize("rp", ["sw_roe", "euler_roe", "acoustics", "advection"])
+@pytest.mark.parametrize("bc", ["wall", "extrap"])
+def test_classic2d_boundaries_fp64(orc, rp, bc):
+    spec = _spec2d(rp, 67, 45, bc=bc)
+    spec["bc_lower"] = [bc, "wall"]
+    spec["bc_upper"] = ["extrap", bc]
+    dt = 0.25 / 67
+    qo, _ = oracle_fixed_steps(orc, spec, dt, 5)
+    qg, _ = gpu_fixed_steps(spec, "fp64", dt, 5)
+    assert rel_maxnorm(qg, qo) <= FP64_TOL
+
+
+def test_classic2d_inflow_fp64(orc):
+    spec = wl.shock_bubble_2d(nx=96, ny=48, scheme="classic")
+    dt = 0.2 / 96 / 3.0
+    qo, _ = oracle_fixed_steps(orc, spec, dt, 6)
+    qg, _ = gpu_fixed_steps(spec, "fp64", dt, 6)
+    assert rel_maxnorm(qg, qo) <= FP64_TOL
+
+
+@pytest.mark.parametrize("rp", RPS_2D)
+def test_classic2d_fp32(orc, rp):
+    spec = _spec2d(rp, 131, 70)
+    dt = 0.25 / 131
+    qo, _ = oracle_fixed_steps(orc, spec, dt, 4)
+    qg, _ = gpu_fixed_steps(spec, "fp32", dt, 4)
+    assert rel_maxnorm(qg, qo) <= FP32_SMOOTH_TOL
+
+
+# --------------------------------------------------------------------------
+# SharpClaw, fixed dt
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("rp", RPS_1D)
+@pytest.mark.parametrize("char", [0, 1])
+def test_sharpclaw1d_fp64(orc, rp, char):
+    if rp == "elasticity_fwave" and char:
+        pytest.skip("no characteristic projection for f-wave elasticity")
+    spec = wl.random_1d(rp, 300, scheme="sharpclaw", char_decomp=char)
+    dt = 0.15 / 300
+    qo, co = oracle_fixed_steps(orc, spec, dt, 3)
+    qg, cg = gpu_fixed_steps(spec, "fp64", dt, 3)
+    assert rel_maxnorm(qg, qo) <= FP64_TOL
+    assert np.allclose(cg, co, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("rp", RPS_2D)
+@pytest.mark.parametrize("char", [0, 1])
+def test_sharpclaw2d_fp64(orc, rp, char):
+    spec = _spec2d(rp, 70, 37, scheme="sharpclaw", char_decomp=char)
+    dt = 0.1 / 70
+    qo, _ = oracle_fixed_steps(orc, spec, dt, 3)
+    qg, _ = gpu_fixed_steps(spec, "fp64", dt, 3)
+    assert rel_maxnorm(qg, qo) <= FP64_TOL
+
+
+@pytest.mark.parametrize("rp", ["sw_roe", "euler_roe"])
+def test_sharpclaw2d_fp32(orc, rp):
+    spec = _spec2d(rp, 70, 37, scheme="sharpclaw", char_decomp=1)
+    dt = 0.1 / 70
+    qo, _ = oracle_fixed_steps(orc, spec, dt, 3)
+    qg, _ = gpu_fixed_steps(spec, "fp32", dt, 3)
+    assert rel_maxnorm(qg, qo) <= FP32_SMOOTH_TOL
+
+
+# --------------------------------------------------------------------------
+# controller runs (accept / reject / final-time clip) and the paper workloads
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_config_acoustics_1d_full_run(orc, use_graph):
+    """1D acoustics, 2000 cells, MC, CFL 0.9, t = 2 (about 4445 steps)."""
+    spec = wl.acoustics_1d(n=2000)
+    qo, io = oracle_evolve(orc, spec, 2.0)
+    qg, ig = gpu_evolve(spec, "fp64", 2.0, use_graph=use_graph)
+    assert ig["steps"] == io["steps"] and ig["t"] == io["t"] == 2.0
+    assert rel_maxnorm(qg, qo) <= FP64_TOL
+    q32, i32 = gpu_evolve(spec, "fp32", 2.0)
+    assert i32["t"] == 2.0 and rel_l1(q32, qo) <= FP32_SHOCK_L1_TOL
+
+
+def test_config_dambreak_256_full_run(orc):
+    """2D shallow-water dam break at the oracle size 256^2 to t = 1.5."""
+    spec = wl.sw_dambreak_2d(n=256)
+    qo, io = oracle_evolve(orc, spec, 1.5)
+    qg, ig = gpu_evolve(spec, "fp64", 1.5)
+    assert ig["steps"] == io["steps"] and ig["t"] == 1.5
+    assert rel_maxnorm(qg, qo) <= FP64_TOL
+    q32, i32 = gpu_evolve(spec, "fp32", 1.5)
+    assert rel_l1(q32, qo) <= FP32_SHOCK_L1_TOL
+
+
+def test_reject_and_retry_parity(orc):
+    spec = wl.random_1d("sw_roe", 400, dt_initial=0.02)
+    qo, io = oracle_evolve(orc, spec, 0.2)
+    qg, ig = gpu_evolve(spec, "fp64", 0.2)
+    assert io["rejects"] >= 1 and ig["rejects"] == io["rejects"]
+    assert ig["steps"] == io["steps"]
+    assert rel_maxnorm(qg, qo) <= FP64_TOL
+
+
+def test_nonphysical_status():
+    spec = wl.sw_dambreak_2d(n=64)
+    spec["q0"][0, 10, 10] = -1.0
+    qg, ig = gpu_evolve(spec, "fp64", 0.5)
+    assert ig["status"] == 6  # CLAW_ENONPHYSICAL
+
+
+def test_conserved_totals_drift():
+    import torch
+    from paper_1111_6583_gb300 import claw
+    spec = wl.random_smooth_2d("euler_roe", 200, 130)
+    for prec, tol in (("fp64", 1e-13), ("fp32", 1e-6)):
+        s = claw.Solver(spec, prec)
+        t0 = s.totals()
+        s.evolve(0.2)
+        t1 = s.totals()
+        ref = np.abs(spec["q0"]).reshape(4, -1).sum(axis=1) / (200 * 130)
+        assert (np.abs(t1 - t0) / ref).max() <= tol, prec
+        s.close()
+
+
+def test_totals_match_oracle(orc):
+    from paper_1111_6583_gb300 import claw
+    spec = wl.random_smooth_2d("sw_roe", 333, 77)
+    s = claw.Solver(spec, "fp64")
+    P = orc.make_problem(spec)
+    assert np.allclose(s.totals(), orc.totals(P, spec["q0"]), rtol=1e-15, atol=1e-15)
+    s.close()
+
+
+def test_checkpoint_restore_bitwise():
+    import torch
+    from paper_1111_6583_gb300 import claw
+    spec = wl.sw_dambreak_2d(n=128)
+    a = claw.Solver(spec, "fp64")
+    a.evolve(0.5)
+    blob = a.checkpoint()
+    a.evolve(1.0)
+    qa = a.q.cpu().numpy().copy()
+    b = claw.Solver(spec, "fp64")
+    b.restore(blob)
+    b.evolve(1.0)
+    assert np.array_equal(b.q.cpu().numpy(), qa)
+    a.close()
+    b.close()
