@@ -1,0 +1,431 @@
+#!/usr/bin/env python3
+"""Benchmark: cell-updates/s of the fused finite-volume step on one GB300.
+
+Headline workload (N=1): 2D shallow-water radial dam break, Clawpack-classic
+(Roe + Harten-Hyman, MC limiter, transverse corrections), 1024 x 1024 cells,
+FP64.  One step = one fused step attempt (ghost remap, Riemann solves,
+limiting, corrections, transverse propagation, update, CFL reduction and
+controller).  The same JSON line also carries the FP32 form of that workload,
+the FP32 batched 1D elasticity ensemble against FP64 one-at-a-time, and the
+serving stream's p50/p99 latency.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank runs its own replica (the step does not
+shard: replicas only); value = all ranks' cell updates / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s & % HBM peak, FP64 plain vs FP32 batched; p50/p99 solve latency"
+UNIT = "cell-updates/s"
+L2_FLUSH_BYTES = 512 << 20
+
+# Algorithmic work per cell update of the headline kernel (2D SW classic,
+# Roe + HH fix, MC, transverse 2).  FLOPs: the FP64 operations of the
+# method's formulas per cell (two normal solves, two limited corrections,
+# four transverse splits, the update), each add/sub/mul/div/sqrt counted once;
+# bytes: one read and one write of the three conserved fields.
+SW2D_FLOPS_PER_CELL = 760.0
+SW2D_BYTES_PER_CELL = {"fp64": 48.0, "fp32": 24.0}
+ELAST1D_BYTES_PER_CELL = {"fp64": 48.0, "fp32": 24.0}  # q read+write, aux read
+# FP64 ALU peak derived from unit counts and clocks: 152 SMs x 2.07 GHz x
+# 4 FP64 FLOP/clk/SM (two FP64 FMA lanes per SM) = 1.259 TFLOP/s.
+FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.samples = []
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[1]) for s in self.samples if len(s) > 8 and s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if len(s) > 8 and s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            if len(s) > 8:
+                for k, nm in enumerate(names):
+                    if s[5 + k].lower().startswith("active"):
+                        reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.samples)}
+
+
+def dist_setup(gpus):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def timed_steps(solver, stream, steps, flush):
+    """Per-step CUDA events on the launching stream; the L2 is flushed between
+    steps outside the timed intervals.  Returns the per-step durations (ms)."""
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for a, b in evs:
+            flush.zero_()
+            a.record(stream)
+            solver.advance(1)
+            b.record(stream)
+    stream.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def bench_sw2d(prec, steps, warmup, n=1024):
+    import torch
+    from paper_1111_6583_gb300 import claw
+    from paper_1111_6583_gb300 import workloads as wl
+    spec = wl.sw_dambreak_2d(n=n)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = claw.Solver(spec, prec, stream=stream.cuda_stream)
+        bw, h = s.tune()
+        s.set_t_end(1.5)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        s.advance(warmup)
+    stream.synchronize()
+    ms = timed_steps(s, stream, steps, flush)
+    info = s.info()
+    s.close()
+    return spec, ms, info, (bw, h)
+
+
+def e2e_sw2d(prec, steps, warmup, n=1024):
+    """Same metric through the C ABI from host memory: each step copies the
+    state in from pinned host memory, steps, and copies it back."""
+    import torch
+    from paper_1111_6583_gb300 import claw
+    from paper_1111_6583_gb300 import workloads as wl
+    spec = wl.sw_dambreak_2d(n=n)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = claw.Solver(spec, prec, stream=stream.cuda_stream)
+        s.tune()
+        s.set_t_end(1.5)
+    hin = torch.as_tensor(spec["q0"], dtype=dt).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    for _ in range(warmup):
+        s.step_host(hin, hout, 1)
+        hin, hout = hout, hin
+    stream.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        st = s.step_host(hin, hout, 1)
+        hin, hout = hout, hin
+    t1 = time.perf_counter()
+    s.close()
+    nbytes = hin.numel() * hin.element_size()
+    cells = n * n
+    return {"value": cells * steps / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+            "d2h_bytes_per_step": nbytes}
+
+
+def bench_elasticity(members, steps, fp64_sample):
+    """FP32 batched ensemble (one fused launch per step over all members) vs
+    FP64 one-at-a-time on a sample of the same members."""
+    import torch
+    from paper_1111_6583_gb300 import claw
+    from paper_1111_6583_gb300 import workloads as wl
+    ens = wl.elasticity_ensemble(members)
+    specs = [wl.elasticity_member(e["n"], e["amp"], e["width"], t_end=e["t_end"]) for e in ens]
+    cells = sum(e["n"] for e in ens)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = claw.Batch(specs, "fp32", stream=stream.cuda_stream)
+        b.advance(3)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        b.advance(steps)
+        e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    out = {"members": members, "cells": cells, "steps": steps,
+           "fp32_batched": cells * steps / (ms * 1e-3), "fp32_ms_per_step": ms / steps}
+    b.close()
+    # FP64, one grid at a time (each member its own solver and launches)
+    sample = specs[:fp64_sample]
+    scells = sum(sp["q0"].shape[1] for sp in sample)
+    solvers = []
+    with torch.cuda.stream(stream):
+        for sp in sample:
+            solvers.append(claw.Solver(sp, "fp64", stream=stream.cuda_stream))
+        for sv in solvers:
+            sv.advance(2)
+    stream.synchronize()
+    k = max(1, steps // 10)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(k):
+            for sv in solvers:
+                sv.advance(1)
+        e1.record(stream)
+    stream.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    for sv in solvers:
+        sv.close()
+    out["fp64_one_at_a_time"] = scells * k / (ms64 * 1e-3)
+    out["fp64_sample_members"] = len(sample)
+    return out
+
+
+def bench_serving(nreq, prec, rate=200.0, budget=120 << 30):
+    """Poisson stream of 2D shallow-water solves through the continuous-
+    batching server; latency = completion - arrival (server clock)."""
+    from paper_1111_6583_gb300 import claw
+    from paper_1111_6583_gb300 import workloads as wl
+    stream_reqs = wl.serving_stream(nreq, rate)
+    sv = claw.Server(wl.sw_humps_2d(64, [], 1.0), prec, budget_bytes=budget, max_slots=512)
+    specs = [wl.sw_humps_2d(r["n"], r["humps"], r["t_end"]) for r in stream_reqs]
+    t0 = claw.clock()
+    pending = {}
+    nxt = 0
+    lat = []
+    cell_updates = 0
+    while nxt < nreq or pending:
+        now = claw.clock() - t0
+        while nxt < nreq and stream_reqs[nxt]["arrival"] <= now:
+            tk = sv.submit(specs[nxt])
+            pending[tk] = nxt
+            nxt += 1
+        if pending:
+            sv.pump(8)
+            for tk in list(pending):
+                r = sv.poll(tk, want_state=False)
+                if r is not None:
+                    i = pending.pop(tk)
+                    lat.append(r["t_done"] - (t0 + stream_reqs[i]["arrival"]))
+                    n = specs[i]["n"][0]
+                    cell_updates += n * n * r["steps"]
+        elif nxt < nreq:
+            time.sleep(max(0.0, min(0.002, stream_reqs[nxt]["arrival"] - now)))
+    wall = claw.clock() - t0
+    sv.close()
+    lat = np.array(lat)
+    return {"requests": nreq, "rate_per_s": rate, "prec": prec,
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "throughput_cell_updates_per_s": cell_updates / wall, "wall_s": wall}
+
+
+def cpu_baseline_sw2d(n=1024, budget_s=12.0):
+    """The oracle as it stands on the host cores: steps of the headline
+    workload until about budget_s of CPU time."""
+    import oracle
+    from paper_1111_6583_gb300 import workloads as wl
+    oracle.build()
+    spec = wl.sw_dambreak_2d(n=n)
+    P = oracle.make_problem(spec)
+    q = spec["q0"]
+    dt = 0.9 * P.dx / 2.0
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        q, _ = oracle.step(P, q, None, dt)
+        steps += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": n * n * steps / el, "unit": UNIT, "cores": oracle.threads(),
+            "kind": "oracle",
+            "sample": "%d steps of the %dx%d FP64 dam break (dt = 0.9 dx / 2)" % (steps, n, n)}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cb = cpu_baseline_sw2d(budget_s=max(5.0, 60.0 / max(1, args.steps + args.warmup)))
+    # each timed step of the reference arm: one oracle step of the workload
+    import oracle
+    from paper_1111_6583_gb300 import workloads as wl
+    spec = wl.sw_dambreak_2d(n=1024)
+    P = oracle.make_problem(spec)
+    q = spec["q0"]
+    dt = 0.9 * P.dx / 2.0
+    for _ in range(args.warmup):
+        q, _ = oracle.step(P, q, None, dt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        q, _ = oracle.step(P, q, None, dt)
+    el = time.perf_counter() - t0
+    value = 1024 * 1024 * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "2D shallow-water dam break 1024x1024, classic Roe+HH, MC, "
+                                   "transverse 2, FP64", "global_batch": 1, "seq_len": 0,
+                       "parallelism": "replicas"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
+                             "sample": "%d timed oracle steps of the 1024x1024 workload"
+                                       % args.steps},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300")
+    ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--members", type=int, default=4096)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    hbm, hbm_kind = peaks()
+
+    barrier(world)
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        spec, ms, info, shape = bench_sw2d("fp64", args.steps, args.warmup, args.n)
+    torch.cuda.synchronize()
+    barrier(world)
+    total_ms = max_over_ranks(sum(ms), world)
+    cells = args.n * args.n
+    value = cells * args.steps * world / (total_ms * 1e-3)
+    avg_ms = sum(ms) / len(ms)
+    flops = SW2D_FLOPS_PER_CELL * cells
+    achieved_tf = flops / (avg_ms * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "2D shallow-water dam break %dx%d, classic Roe+HH, MC, "
+                               "transverse 2, FP64" % (args.n, args.n),
+                   "global_batch": world, "seq_len": 0, "parallelism": "replicas",
+                   "tile": {"bw": shape[0], "h": shape[1]},
+                   "l2": "flushed between timed steps (512 MB write, untimed)"},
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
+                     "traffic": None,
+                     "peak_kind": "derived FP64 (152 SM x 2.07 GHz x 4 FLOP/clk)",
+                     "hbm_gbs": SW2D_BYTES_PER_CELL["fp64"] * cells / (avg_ms * 1e-3) / 1e9,
+                     "hbm_frac": SW2D_BYTES_PER_CELL["fp64"] * cells / (avg_ms * 1e-3) / 1e9 / hbm,
+                     "hbm_peak_kind": hbm_kind},
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_extras:
+        spec32, ms32, info32, shape32 = bench_sw2d("fp32", args.steps, args.warmup, args.n)
+        avg32 = sum(ms32) / len(ms32)
+        gbs32 = SW2D_BYTES_PER_CELL["fp32"] * cells / (avg32 * 1e-3) / 1e9
+        line["fp32"] = {"value": cells * len(ms32) / (sum(ms32) * 1e-3), "unit": UNIT,
+                        "ms_per_step": avg32, "hbm_gbs": gbs32, "hbm_frac": gbs32 / hbm,
+                        "tile": {"bw": shape32[0], "h": shape32[1]}}
+        line["e2e"] = e2e_sw2d("fp64", max(5, args.steps // 4), 3, args.n)
+        try:
+            line["batched_elasticity"] = bench_elasticity(args.members, 100, 16)
+        except Exception as ex:  # reported, not hidden
+            line["batched_elasticity"] = {"error": repr(ex)}
+        try:
+            line["serving"] = bench_serving(args.serve_requests, "fp32")
+        except Exception as ex:
+            line["serving"] = {"error": repr(ex)}
+        line["cpu_baseline"] = cpu_baseline_sw2d(args.n)
+    elif rank == 0:
+        line["e2e"] = e2e_sw2d("fp64", max(5, args.steps // 4), 3, args.n)
+        line["cpu_baseline"] = cpu_baseline_sw2d(args.n, budget_s=5.0)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -27,8 +27,9 @@
  *     Riemann/limiter/WENO arithmetic is float; time, dt, the CFL number and
  *     the conserved totals stay double.
  *   - A handle is used from one host thread at a time and enqueues its work
- *     on the stream given at creation (cudaStream_t passed as void*; NULL =
- *     the legacy default stream).
+ *     on the stream given at creation (cudaStream_t passed as void*).  With
+ *     NULL (the legacy default stream) a single-grid solver runs on a private
+ *     stream ordered after and before the caller's work by events.
  */
 #ifndef CLAWGPU_H
 #define CLAWGPU_H

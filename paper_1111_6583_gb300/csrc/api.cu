@@ -262,11 +262,13 @@ claw_status fail(claw_solver* s, const char* what, cudaError_t e = cudaSuccess) 
   } while (0)
 
 cudaError_t enter(claw_solver* s) {
+  if (s->st == s->ustream) return cudaSuccess;
   cudaError_t e = cudaEventRecord(s->ev_a, s->ustream);
   if (e != cudaSuccess) return e;
   return cudaStreamWaitEvent(s->st, s->ev_a, 0);
 }
 cudaError_t leave(claw_solver* s) {
+  if (s->st == s->ustream) return cudaSuccess;
   cudaError_t e = cudaEventRecord(s->ev_b, s->st);
   if (e != cudaSuccess) return e;
   return cudaStreamWaitEvent(s->ustream, s->ev_b, 0);
@@ -469,7 +471,12 @@ claw_status claw_solver_create(const claw_method* m, const claw_grid* g, void* s
   s->consts = make_consts(*m);
   s->ustream = (cudaStream_t)stream;
   s->sbytes = state_bytes_of(*m, s->g);
-  cudaError_t e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
+  // work goes straight onto a caller's stream; the legacy default stream
+  // cannot be captured into a graph, so NULL gets a private stream ordered
+  // against it by events
+  cudaError_t e = cudaSuccess;
+  if (s->ustream) s->st = s->ustream;
+  else e = cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_a, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_b, cudaEventDisableTiming);
   if (e != cudaSuccess) {
@@ -746,7 +753,7 @@ claw_status claw_solver_destroy(claw_solver* s) {
   free_bound(s);
   if (s->ev_a) cudaEventDestroy(s->ev_a);
   if (s->ev_b) cudaEventDestroy(s->ev_b);
-  if (s->st) cudaStreamDestroy(s->st);
+  if (s->st && s->st != s->ustream) cudaStreamDestroy(s->st);
   delete s;
   return CLAW_OK;
 }
