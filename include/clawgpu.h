@@ -232,6 +232,30 @@ claw_status claw_server_poll(claw_server* sv, uint64_t ticket, void* q_host_out,
                              claw_req_info* info);
 claw_status claw_server_destroy(claw_server* sv);
 
+/* ---------------------------------------------------------------------- */
+/* Allocation-free step                                                     */
+/* ---------------------------------------------------------------------- */
+
+/* One SharpClaw SSP-RK3 step of size dt from q_in to q_out (caller device
+ * memory, layout as above; aux may be NULL when num_aux == 0), for callers
+ * that cannot let the library allocate device memory -- applications whose
+ * device memory is owned by their own allocator or fixed arena, or paths
+ * where cudaMalloc would synchronise the device or is not allowed.  The paper
+ * has no counterpart: it is a service of this library.  The two intermediate
+ * stage states, the control block and the grid descriptors live in one
+ * static device array of 8 MiB that every GPU loading the library keeps until
+ * exit; a grid whose two stage states do not fit (with 1 KiB of control
+ * data) is rejected with CLAW_EINVAL and a message from claw_last_error.  The
+ * first call on a device (that device current) looks up the array's address;
+ * make it before any stream capture.  Every call reuses the array, rewriting
+ * the control block first; calls that overlap on the GPU race.  Runs on
+ * stream (cudaStream_t, may be NULL) and synchronises it; *cfl (may be NULL)
+ * receives the Courant number.  Returns CLAW_ENONPHYSICAL on non-finite
+ * results. */
+claw_status claw_sharp_step_noalloc(const claw_method* m, const claw_grid* g, const void* q_in,
+                                    void* q_out, const void* aux, double dt, void* stream,
+                                    double* cfl);
+
 /* Seconds on the server's clock (monotonic). */
 double claw_clock(void);
 

@@ -103,6 +103,8 @@ _SIGS = {
     "claw_server_pump": (ctypes.c_int, [_VP, ctypes.c_int, _P(ctypes.c_int), _P(ctypes.c_int)]),
     "claw_server_poll": (ctypes.c_int, [_VP, ctypes.c_uint64, _VP, _P(claw_req_info)]),
     "claw_server_destroy": (ctypes.c_int, [_VP]),
+    "claw_sharp_step_noalloc": (ctypes.c_int, [_P(claw_method), _P(claw_grid), _VP, _VP, _VP,
+                                               ctypes.c_double, _VP, _P(ctypes.c_double)]),
     "claw_clock": (ctypes.c_double, []),
     "claw_last_error": (ctypes.c_char_p, [_VP]),
     "claw_version": (ctypes.c_char_p, []),

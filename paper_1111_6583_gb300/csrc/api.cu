@@ -210,6 +210,8 @@ double now_s() {
 
 }  // namespace
 
+void claw::set_last_error(const char* msg) { g_err = msg; }
+
 // ===========================================================================
 // single-grid solver
 // ===========================================================================

@@ -70,4 +70,7 @@ cudaError_t launch_gather_ctl(const Member* members, int n, DevCtl* out, cudaStr
 cudaError_t launch_set_dry(DevCtl* ctl, int dry, cudaStream_t st);
 constexpr int kTotalsThreads = 256;
 
+// record the message that claw_last_error returns (api.cu)
+void set_last_error(const char* msg);
+
 }  // namespace claw
