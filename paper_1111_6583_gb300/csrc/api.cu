@@ -137,7 +137,7 @@ const char* check_grid(const claw_grid& g) {
 
 int tiles_of(int scheme, int nd, int prec, int nx, int ny, int bw, int h) {
   if (scheme == CLAW_CLASSIC)
-    return nd == 1 ? classic1d_tiles(nx, classic1d_T(prec)) : classic2d_tiles(nx, ny, bw, h);
+    return nd == 1 ? classic1d_tiles(nx, prec) : classic2d_tiles(nx, ny, bw, h);
   return nd == 1 ? sharp_tiles(nx, 1, kSharpTX1, 1) : sharp_tiles(nx, ny, kSharpTX2, kSharpTY2);
 }
 

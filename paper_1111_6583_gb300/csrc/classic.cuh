@@ -14,23 +14,118 @@ namespace claw {
 
 
 // ---------------------------------------------------------------------------
-// 1D: a block loads T + 4 cells (2 ghosts each side) into shared memory,
-// solves T + 3 Riemann problems, limits T + 1 interfaces and updates T cells.
+// 1D: each thread owns K consecutive cells.  It loads them (16-byte vector
+// loads when the fields are aligned) plus two ghost/halo cells on each side,
+// prepares each cell once (CellPrep: the per-cell part of the Riemann solve),
+// then streams through its K + 3 interfaces with a three-interface register
+// window: solve interface j, limit interface j-1 with its neighbours, fold the
+// correction into the fluctuations and emit cell j-3.  No shared memory and no
+// barriers until the block's speed reduction.
 // ---------------------------------------------------------------------------
-template <class RP, typename R, int NT, int T>
+template <typename R, int K>
+struct VecIO;
+template <>
+struct VecIO<float, 8> {
+  __device__ static __forceinline__ void load(const float* p, float (&v)[8]) {
+    const float4 a = __ldg((const float4*)p), b = __ldg((const float4*)p + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  }
+  __device__ static __forceinline__ void store(float* p, const float (&v)[8]) {
+    ((float4*)p)[0] = make_float4(v[0], v[1], v[2], v[3]);
+    ((float4*)p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+  }
+};
+template <>
+struct VecIO<double, 4> {
+  __device__ static __forceinline__ void load(const double* p, double (&v)[4]) {
+    const double2 a = __ldg((const double2*)p), b = __ldg((const double2*)p + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
+  __device__ static __forceinline__ void store(double* p, const double (&v)[4]) {
+    ((double2*)p)[0] = make_double2(v[0], v[1]);
+    ((double2*)p)[1] = make_double2(v[2], v[3]);
+  }
+};
+
+// Per-cell preparation of a Riemann solve.  The default keeps the raw state
+// and aux; solvers with a cell-local part (RpElasticity: exp, sqrt and 1/rho)
+// specialise it so that each cell is prepared once instead of once per side.
+template <class RP, typename R>
+struct CellPrep {
+  static constexpr int MAS = RP::MA > 0 ? RP::MA : 1;
+  struct Cell {
+    R q[RP::M];
+    R a[MAS];
+  };
+  __device__ static __forceinline__ void prep(const MConsts<R>&, const R (&q)[RP::M],
+                                              const R (&a)[MAS], Cell& c) {
+#pragma unroll
+    for (int k = 0; k < RP::M; ++k) c.q[k] = q[k];
+#pragma unroll
+    for (int k = 0; k < MAS; ++k) c.a[k] = a[k];
+  }
+  __device__ static __forceinline__ void solve(const MConsts<R>& C, const Cell& l, const Cell& r,
+                                               R (&W)[RP::MW][RP::M], R (&s)[RP::MW],
+                                               R (&am)[RP::M], R (&ap)[RP::M]) {
+    R x[RP::NCTX];
+    RP::template solve<0>(C, l.q, r.q, l.a, r.a, W, s, am, ap, x);
+  }
+};
+
+template <typename R, int ND>
+struct RpElasticity;
+
+template <typename R>
+struct CellPrep<RpElasticity<R, 1>, R> {
+  static constexpr int MAS = 2;
+  struct Cell {
+    R e;   // exp(K eps) = sigma + 1
+    R u;   // m / rho
+    R c;   // sqrt(K exp(K eps) / rho)
+    R Z;   // rho c
+  };
+  __device__ static __forceinline__ void prep(const MConsts<R>&, const R (&q)[2],
+                                              const R (&a)[2], Cell& c) {
+    const R ir = FM<R>::rcp(a[0]);
+    c.e = FM<R>::exp(a[1] * q[0]);
+    c.u = q[1] * ir;
+    c.c = FM<R>::sqrt(a[1] * c.e * ir);
+    c.Z = a[0] * c.c;
+  }
+  // the f-wave solve of RpElasticity on prepared cells
+  __device__ static __forceinline__ void solve(const MConsts<R>&, const Cell& l, const Cell& r,
+                                               R (&W)[2][2], R (&s)[2], R (&am)[2], R (&ap)[2]) {
+    const R d1 = l.u - r.u;  // jump of -u
+    const R d2 = l.e - r.e;  // jump of -sigma
+    const R iz = FM<R>::rcp(l.Z + r.Z);
+    const R b1 = (r.Z * d1 + d2) * iz;
+    const R b2 = (l.Z * d1 - d2) * iz;
+    W[0][0] = b1;
+    W[0][1] = b1 * l.Z;
+    W[1][0] = b2;
+    W[1][1] = -b2 * r.Z;
+    s[0] = -l.c;
+    s[1] = r.c;
+    // speeds are -c_l < 0 < c_r: A^-dQ = Z^1, A^+dQ = Z^2
+    am[0] = b1;
+    am[1] = W[0][1];
+    ap[0] = b2;
+    ap[1] = W[1][1];
+  }
+};
+
+template <class RP, typename R, int NT, int K>
 __global__ void __launch_bounds__(NT)
     classic1d_kernel(const Member* __restrict__ members, const Tile* __restrict__ tiles,
                      int ntiles_total, const MConsts<R> C) {
   constexpr int M = RP::M, MW = RP::MW, MA = RP::MA;
   constexpr int MAS = MA > 0 ? MA : 1;
-  __shared__ R qs[M][T + 4];
-  __shared__ R as[MAS][MA > 0 ? T + 4 : 1];
-  __shared__ R Ws[MW][M][T + 3];
-  __shared__ R Ss[MW][T + 3];
-  __shared__ R Am[M][T + 1];
-  __shared__ R Ap[M][T + 1];
+  constexpr int T = NT * K;
+  using CP = CellPrep<RP, R>;
+  using Cell = typename CP::Cell;
   __shared__ int s_done, s_cur, s_nbuf;
-  __shared__ double s_dt;
+  __shared__ R s_dtdx;
 
   for (int it = blockIdx.x; it < ntiles_total; it += gridDim.x) {
     const Tile tl = tiles ? tiles[it] : Tile{0, it};
@@ -38,7 +133,7 @@ __global__ void __launch_bounds__(NT)
     DevCtl* ctl = mb.ctl;
     if (threadIdx.x == 0) {
       s_done = ctl->done;
-      s_dt = ctl->dt;
+      s_dtdx = (R)(ctl->dt / ctl->dx[0]);
       s_cur = ctl->cur;
       s_nbuf = ctl->nbuf;
     }
@@ -48,104 +143,148 @@ __global__ void __launch_bounds__(NT)
       continue;
     }
     const int nx = mb.nx;
-    const int i0 = tl.tile * T;
-    const int cnt = min(T, nx - i0);
+    const int base = tl.tile * T + threadIdx.x * K;
     const R* __restrict__ q = (const R*)mb.q[s_cur];
     R* __restrict__ qo = (R*)mb.q[(s_cur + 1) % s_nbuf];
     const R* __restrict__ aux = (const R*)mb.aux;
-    const R dtdx = (R)(s_dt / ctl->dx[0]);
-
-    // stage cells i0-2 .. i0+cnt+1 (ghosts by index remap)
-    for (int j = threadIdx.x; j < cnt + 4; j += NT) {
-      R v[M];
-      load_cell<M, R>(C, q, nx, 1, i0 - 2 + j, 0, RP::WALL_X, -1, v);
-#pragma unroll
-      for (int k = 0; k < M; ++k) qs[k][j] = v[k];
-      if (MA > 0) {
-        R a[MAS];
-        load_aux<MA, R>(C, aux, nx, 1, i0 - 2 + j, 0, a);
-#pragma unroll
-        for (int k = 0; k < MA; ++k) as[k][j] = a[k];
-      }
-    }
-    __syncthreads();
-
-    // Riemann problems at interfaces i0-1 .. i0+cnt+1 (index ii = i - i0 + 1)
-    double smax = 0.0;
-    for (int ii = threadIdx.x; ii < cnt + 3; ii += NT) {
-      R ql[M], qr[M], al[MAS], ar[MAS];
-#pragma unroll
-      for (int k = 0; k < M; ++k) {
-        ql[k] = qs[k][ii];
-        qr[k] = qs[k][ii + 1];
-      }
-#pragma unroll
-      for (int k = 0; k < MA; ++k) {
-        al[k] = as[k][ii];
-        ar[k] = as[k][ii + 1];
-      }
-      R W[MW][M], s[MW], am[M], ap[M], ctx[RP::NCTX];
-      RP::template solve<0>(C, ql, qr, al, ar, W, s, am, ap, ctx);
-#pragma unroll
-      for (int p = 0; p < MW; ++p) {
-        Ss[p][ii] = s[p];
-#pragma unroll
-        for (int k = 0; k < M; ++k) Ws[p][k][ii] = W[p][k];
-      }
-      if (ii >= 1 && ii <= cnt + 1) {
+    const R dtdx = s_dtdx;
+    R smax = R(0);
+    int bad = 0;
+    if (base < nx) {
+      // raw cells base-2 .. base+K+1 ; qa[c] is cell base-2+c
+      R qa[K + 4][M];
+      R aa[K + 4][MAS];
+      const bool full = base + K <= nx;
+      const bool rows16 = ((size_t)nx * sizeof(R)) % 16 == 0;  // every field 16-B aligned
+      const bool q_ok = ((((size_t)q) | ((size_t)qo)) & 15) == 0 && (M == 1 || rows16);
+      const bool a_ok = MA == 0 || ((((size_t)aux) & 15) == 0 && (MA == 1 || rows16));
+      const bool vec = full && q_ok && a_ok;
+      if (vec) {
 #pragma unroll
         for (int k = 0; k < M; ++k) {
-          Am[k][ii - 1] = am[k];
-          Ap[k][ii - 1] = ap[k];
+          R v[K];
+          VecIO<R, K>::load(q + (size_t)k * nx + base, v);
+#pragma unroll
+          for (int c = 0; c < K; ++c) qa[c + 2][k] = v[c];
         }
+        if (MA > 0) {
 #pragma unroll
-        for (int p = 0; p < MW; ++p) smax = nanmax(smax, (double)fabs(s[p]));
+          for (int k = 0; k < MA; ++k) {
+            R v[K];
+            VecIO<R, K>::load(aux + (size_t)k * nx + base, v);
+#pragma unroll
+            for (int c = 0; c < K; ++c) aa[c + 2][k] = v[c];
+          }
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+          load_cell<M, R>(C, q, nx, 1, min(base + c, nx + 1), 0, RP::WALL_X, -1, qa[c + 2]);
+          if (MA > 0) load_aux<MA, R>(C, aux, nx, 1, min(base + c, nx + 1), 0, aa[c + 2]);
+        }
       }
-    }
-    __syncthreads();
-
-    // limited corrections at interfaces i0 .. i0+cnt, folded into the
-    // fluctuations: cell i gets -dt/dx (A^+dQ_i - F_i) and -dt/dx (A^-dQ_{i+1} + F_{i+1})
-    if (C.order == 2) {
-      for (int jj = threadIdx.x; jj < cnt + 1; jj += NT) {
-        const int ii = jj + 1;
-        R W[MW][M], s[MW], dot[MW], nrm[MW], F[M];
 #pragma unroll
-        for (int p = 0; p < MW; ++p) {
-          s[p] = Ss[p][ii];
-          const int iu = s[p] > R(0) ? ii - 1 : ii + 1;
-          R d = R(0), n2 = R(0);
+      for (int h = 0; h < 4; ++h) {
+        const int c = h < 2 ? h : K + h;  // local slots 0,1 and K+2,K+3
+        const int gi = min(base - 2 + c, nx + 1);
+        load_cell<M, R>(C, q, nx, 1, gi, 0, RP::WALL_X, -1, qa[c]);
+        if (MA > 0) load_aux<MA, R>(C, aux, nx, 1, gi, 0, aa[c]);
+      }
+      // streaming window over interfaces jj = 0..K+2 (interface jj lies between
+      // qa[jj] and qa[jj+1], global index base-1+jj)
+      R W0[MW][M], W1[MW][M], W2[MW][M];  // interfaces jj-2, jj-1, jj
+      R s1[MW], s2[MW];
+      R am1[M], ap1[M], am2[M], ap2[M];
+      R Ap_prev[M];  // A^+ dQ - F of the interface left of the next cell
+      R qout[K][M];
+      Cell cl, cr;
+      CP::prep(C, qa[0], aa[0], cl);
+#pragma unroll
+      for (int jj = 0; jj < K + 3; ++jj) {
+        if (jj >= 1) {
+#pragma unroll
+          for (int p = 0; p < MW; ++p) {
+            s1[p] = s2[p];
+#pragma unroll
+            for (int k = 0; k < M; ++k) {
+              W0[p][k] = W1[p][k];
+              W1[p][k] = W2[p][k];
+            }
+          }
 #pragma unroll
           for (int k = 0; k < M; ++k) {
-            W[p][k] = Ws[p][k][ii];
-            d += Ws[p][k][iu] * W[p][k];
-            n2 += W[p][k] * W[p][k];
+            am1[k] = am2[k];
+            ap1[k] = ap2[k];
           }
-          dot[p] = d;
-          nrm[p] = n2;
         }
-        correction<RP, R>(C, W, s, dot, nrm, dtdx, F);
+        CP::prep(C, qa[jj + 1], aa[jj + 1], cr);
+        CP::solve(C, cl, cr, W2, s2, am2, ap2);
+        cl = cr;
+        {
+          const int gj = base - 1 + jj;
+          if (jj >= 1 && jj <= K + 1 && gj <= nx) {
+#pragma unroll
+            for (int p = 0; p < MW; ++p) smax = nanmax(smax, (R)fabs(s2[p]));
+          }
+        }
+        if (jj >= 2) {
+          // limit interface jj-1 with neighbours jj-2 and jj
+          R F[M];
+          if (C.order == 2) {
+            R dot[MW], nrm[MW];
+#pragma unroll
+            for (int p = 0; p < MW; ++p) {
+              R d = R(0), n2 = R(0);
+#pragma unroll
+              for (int k = 0; k < M; ++k) {
+                const R up = s1[p] > R(0) ? W0[p][k] : W2[p][k];
+                d += up * W1[p][k];
+                n2 += W1[p][k] * W1[p][k];
+              }
+              dot[p] = d;
+              nrm[p] = n2;
+            }
+            correction<RP, R>(C, W1, s1, dot, nrm, dtdx, F);
+          } else {
+#pragma unroll
+            for (int k = 0; k < M; ++k) F[k] = R(0);
+          }
+          // cell jj-3 (local) lies between interfaces jj-2 and jj-1
+          if (jj >= 3) {
+#pragma unroll
+            for (int k = 0; k < M; ++k)
+              qout[jj - 3][k] = qa[jj - 1][k] - dtdx * (Ap_prev[k] + (am1[k] + F[k]));
+          }
+#pragma unroll
+          for (int k = 0; k < M; ++k) Ap_prev[k] = ap1[k] - F[k];
+        }
+      }
+      // store cells base .. base+K-1
+      if (vec) {
 #pragma unroll
         for (int k = 0; k < M; ++k) {
-          Ap[k][jj] -= F[k];
-          Am[k][jj] += F[k];
+          R v[K];
+#pragma unroll
+          for (int c = 0; c < K; ++c) {
+            v[c] = qout[c][k];
+            bad |= !isfinite(v[c]);
+          }
+          VecIO<R, K>::store(qo + (size_t)k * nx + base, v);
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+          if (base + c < nx) {
+#pragma unroll
+            for (int k = 0; k < M; ++k) {
+              bad |= !isfinite(qout[c][k]);
+              qo[(size_t)k * nx + base + c] = qout[c][k];
+            }
+          }
         }
       }
-      __syncthreads();
     }
-
-    // conservative update of cells i0 .. i0+cnt-1
-    int bad = 0;
-    const size_t plane = (size_t)nx;
-    for (int j = threadIdx.x; j < cnt; j += NT) {
-#pragma unroll
-      for (int k = 0; k < M; ++k) {
-        const R v = qs[k][j + 2] - dtdx * (Ap[k][j] + Am[k][j + 1]);
-        bad |= !isfinite(v);
-        qo[k * plane + i0 + j] = v;
-      }
-    }
-    finish_attempt(ctl, smax, 0.0, bad, mb.ntiles, true);
+    finish_attempt<R>(ctl, smax, R(0), bad, mb.ntiles, true);
   }
 }
 
@@ -171,7 +310,7 @@ __global__ void __launch_bounds__(BW)
   __shared__ R mbl[4][M][BW];
   __shared__ R mbr[2][M][BW];
   __shared__ int s_done, s_cur, s_nbuf;
-  __shared__ double s_dt;
+  __shared__ R s_k[3];  // dt/dx, dt/dy, dt^2/(2 dx dy)
   const int l = threadIdx.x;
 
   for (int it = blockIdx.x; it < ntiles_total; it += gridDim.x) {
@@ -180,7 +319,10 @@ __global__ void __launch_bounds__(BW)
     DevCtl* ctl = mb.ctl;
     if (l == 0) {
       s_done = ctl->done;
-      s_dt = ctl->dt;
+      const double dtd = ctl->dt;
+      s_k[0] = (R)(dtd / ctl->dx[0]);
+      s_k[1] = (R)(dtd / ctl->dx[1]);
+      s_k[2] = (R)(0.5 * (dtd / ctl->dx[0]) * (dtd / ctl->dx[1]));
       s_cur = ctl->cur;
       s_nbuf = ctl->nbuf;
     }
@@ -202,10 +344,7 @@ __global__ void __launch_bounds__(BW)
     const bool ylim = (l >= 1) && (l <= BW - 2);
     const R* __restrict__ q = (const R*)mb.q[s_cur];
     R* __restrict__ qo = (R*)mb.q[(s_cur + 1) % s_nbuf];
-    const double dtd = s_dt;
-    const R dtdx = (R)(dtd / ctl->dx[0]);
-    const R dtdy = (R)(dtd / ctl->dx[1]);
-    const R kxy = (R)(0.5 * (dtd / ctl->dx[0]) * (dtd / ctl->dx[1]));
+    const R dtdx = s_k[0], dtdy = s_k[1], kxy = s_k[2];
     const size_t plane = (size_t)nx * ny;
 
     R qm2[M], qm1[M], qc[M];
@@ -227,7 +366,7 @@ __global__ void __launch_bounds__(BW)
     }
 #pragma unroll
     for (int k = 0; k < NC; ++k) yx[k] = R(0);
-    double smx = 0.0, smy = 0.0;
+    R smx = R(0), smy = R(0);
     int bad = 0;
 
     for (int Rw = r0 - 2; Rw <= rend + 2; ++Rw) {
@@ -259,7 +398,7 @@ __global__ void __launch_bounds__(BW)
         }
         if (col_in && Rw >= r0 && Rw <= rend + 1) {
 #pragma unroll
-          for (int p = 0; p < MW; ++p) smy = nanmax(smy, (double)fabs(ns[p]));
+          for (int p = 0; p < MW; ++p) smy = nanmax(smy, (R)fabs(ns[p]));
         }
       }
       __syncthreads();  // qs ready
@@ -318,7 +457,7 @@ __global__ void __launch_bounds__(BW)
         }
         if (xcfl && Rw >= r0 && Rw <= rend) {
 #pragma unroll
-          for (int p = 0; p < MW; ++p) smx = nanmax(smx, (double)fabs(xs[p]));
+          for (int p = 0; p < MW; ++p) smx = nanmax(smx, (R)fabs(xs[p]));
         }
         if (C.transverse) {
           R tp[M], tm[M], bmp[M], bpp[M], bmm[M], bpm[M];
@@ -444,7 +583,7 @@ __global__ void __launch_bounds__(BW)
         for (int k = 0; k < NC; ++k) yx[k] = nx_[k];
       }
     }
-    finish_attempt(ctl, smx, smy, bad, mb.ntiles, true);
+    finish_attempt<R>(ctl, smx, smy, bad, mb.ntiles, true);
   }
 }
 

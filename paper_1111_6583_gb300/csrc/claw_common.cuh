@@ -147,14 +147,11 @@ __device__ __forceinline__ void load_aux(const MConsts<R>& C, const R* __restric
 // ---------------------------------------------------------------------------
 // reductions
 // ---------------------------------------------------------------------------
-// max that keeps NaN (a NaN speed must reach the controller)
-__device__ __forceinline__ double nanmax(double a, double b) { return (b <= a) ? a : b; }
+// max that keeps NaN (a NaN speed must reach the controller); kept in the
+// working precision so FP32 kernels do no FP64 work per interface
+template <typename T>
+__device__ __forceinline__ T nanmax(T a, T b) { return (b <= a) ? a : b; }
 
-__device__ __forceinline__ double warp_nanmax(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = nanmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
 
 __device__ __forceinline__ int clip_final(double t, double t_end, double& dt) {
   if (t + dt >= t_end) {
@@ -225,18 +222,23 @@ static __device__ __noinline__ void run_controller(DevCtl* c) {
   c->arrive = 0u;
 }
 
-// Reduce two per-thread maxima and a bad flag over the block, fold them into
-// the control block, and let the last block of the member's attempt run the
+// Reduce two per-thread maxima and a bad flag over the block (in the working
+// precision T; one conversion to double at the end), fold them into the
+// control block, and let the last block of the member's attempt run the
 // controller (when run_ctl).  Called by every thread of the block; blockDim.x
 // must be a multiple of 32 and at most 1024.
-static __device__ __forceinline__ void finish_attempt(DevCtl* ctl, double sx, double sy, int bad,
-                                               int ntiles, bool run_ctl) {
-  __shared__ double red_x[32], red_y[32];
+template <typename T>
+static __device__ __forceinline__ void finish_attempt(DevCtl* ctl, T sx, T sy, int bad, int ntiles,
+                                                      bool run_ctl) {
+  __shared__ T red_x[32], red_y[32];
   __shared__ int red_bad;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) red_bad = 0;
-  sx = warp_nanmax(sx);
-  sy = warp_nanmax(sy);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sx = nanmax(sx, __shfl_xor_sync(0xffffffffu, sx, o));
+    sy = nanmax(sy, __shfl_xor_sync(0xffffffffu, sy, o));
+  }
   __syncthreads();
   if (bad) atomicOr(&red_bad, 1);
   if (lane == 0) {
@@ -246,13 +248,17 @@ static __device__ __forceinline__ void finish_attempt(DevCtl* ctl, double sx, do
   __syncthreads();
   if (warp == 0) {
     const int nw = blockDim.x >> 5;
-    double a = lane < nw ? red_x[lane] : 0.0;
-    double b = lane < nw ? red_y[lane] : 0.0;
-    a = warp_nanmax(a);
-    b = warp_nanmax(b);
+    T a = lane < nw ? red_x[lane] : T(0);
+    T b = lane < nw ? red_y[lane] : T(0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a = nanmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+      b = nanmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+    }
     if (lane == 0) {
-      if (a != 0.0) atomicMax(&ctl->smax[0], (unsigned long long)__double_as_longlong(a));
-      if (b != 0.0) atomicMax(&ctl->smax[1], (unsigned long long)__double_as_longlong(b));
+      const double ad = (double)a, bd = (double)b;
+      if (ad != 0.0) atomicMax(&ctl->smax[0], (unsigned long long)__double_as_longlong(ad));
+      if (bd != 0.0) atomicMax(&ctl->smax[1], (unsigned long long)__double_as_longlong(bd));
       if (red_bad) atomicOr(&ctl->bad, 1u);
       if (run_ctl) {
         __threadfence();

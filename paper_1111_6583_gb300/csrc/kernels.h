@@ -35,13 +35,16 @@ struct KernelSet {
 };
 
 // tile geometry shared by the host (tile tables) and the kernels
-constexpr int kClassic1dThreads = 256;
-constexpr int classic1d_T(int prec) { return prec == 0 ? 256 : 512; }
+constexpr int kClassic1dThreads = 128;
+constexpr int classic1d_K(int prec) { return prec == 0 ? 4 : 8; }  // cells per thread
+constexpr int classic1d_T(int prec) { return kClassic1dThreads * classic1d_K(prec); }
+inline int classic1d_tiles(int nx, int prec) {
+  return (nx + classic1d_T(prec) - 1) / classic1d_T(prec);
+}
 constexpr int kSharpTX2 = 16, kSharpTY2 = 8;  // 2D SharpClaw tile
 constexpr int kSharpTX1 = 128;                // 1D SharpClaw tile
 constexpr int kMaxspeedCells = 256;           // cells per max-speed block
 
-__host__ __device__ inline int classic1d_tiles(int nx, int T) { return (nx + T - 1) / T; }
 __host__ __device__ inline int classic2d_tiles(int nx, int ny, int BW, int H) {
   const int TX = BW - 4;
   return ((nx + TX - 1) / TX) * ((ny + H - 1) / H);

@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(kMaxspeedCells)
     const long long cell = (long long)tl.tile * kMaxspeedCells + threadIdx.x;
     const R* q = (const R*)mb.q[ctl->cur];
     const R* aux = (const R*)mb.aux;
-    double sx = 0.0, sy = 0.0;
+    R sx = R(0), sy = R(0);
     if (cell < (long long)nx * ny) {
       const int i = (int)(cell % nx), j = (int)(cell / nx);
       R W[MW][M], s[MW], am[M], ap[M], x[RP::NCTX];
@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(kMaxspeedCells)
         }
         RP::template solve<0>(C, a, b, al, ar, W, s, am, ap, x);
 #pragma unroll
-        for (int p = 0; p < MW; ++p) sx = nanmax(sx, (double)fabs(s[p]));
+        for (int p = 0; p < MW; ++p) sx = nanmax(sx, (R)fabs(s[p]));
       }
       if constexpr (ND == 2) {
         for (int side = 0; side < (j == ny - 1 ? 2 : 1); ++side) {
@@ -45,11 +45,11 @@ __global__ void __launch_bounds__(kMaxspeedCells)
           load_cell<M, R>(C, q, nx, ny, i, j + side, RP::WALL_X, RP::WALL_Y, b);
           RP::template solve<1>(C, a, b, al, ar, W, s, am, ap, x);
 #pragma unroll
-          for (int p = 0; p < MW; ++p) sy = nanmax(sy, (double)fabs(s[p]));
+          for (int p = 0; p < MW; ++p) sy = nanmax(sy, (R)fabs(s[p]));
         }
       }
     }
-    finish_attempt(ctl, sx, sy, 0, 0, false);
+    finish_attempt<R>(ctl, sx, sy, 0, 0, false);
   }
 }
 
@@ -60,8 +60,8 @@ struct Launchers {
   static cudaError_t classic(const LaunchArgs& a) {
     const MConsts<R>& C = *(const MConsts<R>*)a.consts;
     if constexpr (ND == 1) {
-      constexpr int T = sizeof(R) == 8 ? classic1d_T(0) : classic1d_T(1);
-      classic1d_kernel<RP, R, kClassic1dThreads, T>
+      constexpr int K = sizeof(R) == 8 ? classic1d_K(0) : classic1d_K(1);
+      classic1d_kernel<RP, R, kClassic1dThreads, K>
           <<<launch_grid(a.ntiles_total), kClassic1dThreads, 0, a.stream>>>(a.members, a.tiles,
                                                                          a.ntiles_total, C);
     } else {

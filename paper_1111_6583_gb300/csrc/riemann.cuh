@@ -24,12 +24,30 @@ struct Dirs {
   static constexpr int t = (ND == 1) ? -1 : 2 - DIR;  // tangential component
 };
 
+// Precision traits.  FP64 uses IEEE division and square root (parity with
+// the FP64 oracle to 1e-12); FP32 uses the hardware approximations (relative
+// error ~1e-7, well inside the FP32 tolerance of 1e-5).
 template <typename R>
-__device__ __forceinline__ R rsq(R x);
+struct FM;
 template <>
-__device__ __forceinline__ double rsq<double>(double x) { return rsqrt(x); }
+struct FM<double> {
+  __device__ static __forceinline__ double div(double a, double b) { return a / b; }
+  __device__ static __forceinline__ double rcp(double a) { return 1.0 / a; }
+  __device__ static __forceinline__ double sqrt(double a) { return ::sqrt(a); }
+  __device__ static __forceinline__ double rsqrt(double a) { return ::rsqrt(a); }
+  __device__ static __forceinline__ double exp(double a) { return ::exp(a); }
+};
 template <>
-__device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
+struct FM<float> {
+  __device__ static __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+  __device__ static __forceinline__ float rcp(float a) { return __fdividef(1.f, a); }
+  __device__ static __forceinline__ float sqrt(float a) { return a > 0.f ? a * rsqrtf(a) : sqrtf(a); }
+  __device__ static __forceinline__ float rsqrt(float a) { return rsqrtf(a); }
+  __device__ static __forceinline__ float exp(float a) { return __expf(a); }
+};
+
+template <typename R>
+__device__ __forceinline__ R rsq(R x) { return FM<R>::rsqrt(x); }
 
 // A^- dQ = sum_p min(s^p,0) W^p,  A^+ dQ = sum_p max(s^p,0) W^p
 template <int M, int MW, typename R>
@@ -175,7 +193,7 @@ struct RpAcoustics {
 // ---------------------------------------------------------------------------
 template <typename R, int ND>
 struct RpSW {
-  static constexpr int M = ND + 1, MW = ND + 1, MA = 0, NCTX = 3;  // ctx: un, ut, c
+  static constexpr int M = ND + 1, MW = ND + 1, MA = 0, NCTX = 4;  // ctx: un, ut, c, 1/(2c)
   static constexpr bool FWAVE = false;
   static constexpr int WALL_X = 1, WALL_Y = (ND == 2) ? 2 : -1;
 
@@ -185,10 +203,11 @@ struct RpSW {
     constexpr int n = Dirs<ND, DIR>::n, t = Dirs<ND, DIR>::t;
     const R hl = ql[0], hr = qr[0];
     const R il = rsq(hl), ir = rsq(hr);          // 1/sqrt(h)
-    const R iden = R(1) / (hl * il + hr * ir);   // 1/(sqrt(hl)+sqrt(hr))
+    const R iden = FM<R>::rcp(hl * il + hr * ir);   // 1/(sqrt(hl)+sqrt(hr))
     x[0] = (ql[n] * il + qr[n] * ir) * iden;     // sqrt(h) u = hu/sqrt(h)
     x[1] = (t >= 0) ? (ql[t < 0 ? 0 : t] * il + qr[t < 0 ? 0 : t] * ir) * iden : R(0);
-    x[2] = sqrt(C.g * (R(0.5) * (hl + hr)));
+    x[2] = FM<R>::sqrt(C.g * (R(0.5) * (hl + hr)));
+    x[3] = FM<R>::div(R(0.5), x[2]);
   }
 
   // eigen-coefficients of d in the frame (normal a, tangential b) at (un, ut, c)
@@ -210,8 +229,24 @@ struct RpSW {
 
   template <int DIR>
   __device__ static __forceinline__ R sonic(const MConsts<R>& C, R h, R hu, int plus) {
-    const R c = sqrt(C.g * h);
-    return plus ? hu / h + c : hu / h - c;
+    const R c = FM<R>::sqrt(C.g * h);
+    const R u = FM<R>::div(hu, h);
+    return plus ? u + c : u - c;
+  }
+  // Signs of u -/+ c for a state (h, hu) without square roots or divisions:
+  // with h > 0, u - c < 0  <=>  hu < 0 or hu^2 < g h^3, and u + c > 0  <=>
+  // hu > 0 or hu^2 < g h^3.  A state with h <= 0 satisfies none of them.
+  __device__ static __forceinline__ bool minus_neg(const MConsts<R>& C, R h, R hu) {
+    return h > R(0) && (hu < R(0) || hu * hu < C.g * (h * h * h));
+  }
+  __device__ static __forceinline__ bool minus_pos(const MConsts<R>& C, R h, R hu) {
+    return h > R(0) && hu > R(0) && hu * hu > C.g * (h * h * h);
+  }
+  __device__ static __forceinline__ bool plus_neg(const MConsts<R>& C, R h, R hu) {
+    return h > R(0) && hu < R(0) && hu * hu > C.g * (h * h * h);
+  }
+  __device__ static __forceinline__ bool plus_pos(const MConsts<R>& C, R h, R hu) {
+    return h > R(0) && (hu > R(0) || hu * hu < C.g * (h * h * h));
   }
 
   template <int DIR>
@@ -222,7 +257,7 @@ struct RpSW {
     constexpr int n = Dirs<ND, DIR>::n, t = Dirs<ND, DIR>::t;
     roe<DIR>(C, ql, qr, x);
     const R un = x[0], ut = x[1], c = x[2];
-    const R i2c = R(0.5) / c;
+    const R i2c = x[3];
     R d[M], al[MW];
 #pragma unroll
     for (int k = 0; k < M; ++k) d[k] = qr[k] - ql[k];
@@ -244,36 +279,41 @@ struct RpSW {
     s[0] = un - c;
     s[MW - 1] = un + c;
     if (C.entropy_fix) {
-      R tot[M];
+      // first family: transonic when u-c < 0 at Q_l and > 0 at Q_l + W^1
+      const R hm = ql[0] + W[0][0], hum = ql[n] + W[0][n];
+      if (minus_neg(C, ql[0], ql[n]) && minus_pos(C, hm, hum)) {
+        const R lamL = sonic<DIR>(C, ql[0], ql[n], 0);
+        const R lamR = sonic<DIR>(C, hm, hum, 0);
+        if (lamL < R(0) && lamR > R(0)) {
+          const R beta = FM<R>::div(lamR - s[0], lamR - lamL);
 #pragma unroll
-      for (int k = 0; k < M; ++k) {
-        tot[k] = R(0);
+          for (int k = 0; k < M; ++k) {
+            R tot = R(0);
 #pragma unroll
-        for (int p = 0; p < MW; ++p) tot[k] += s[p] * W[p][k];
-      }
-      // first family: left state and Q_l + W^1
-      const R lamL = sonic<DIR>(C, ql[0], ql[n], 0);
-      const R lamR = sonic<DIR>(C, ql[0] + W[0][0], ql[n] + W[0][n], 0);
-      if (lamL < R(0) && lamR > R(0)) {
-        const R beta = (lamR - s[0]) / (lamR - lamL);
-#pragma unroll
-        for (int k = 0; k < M; ++k) {
-          am[k] = beta * lamL * W[0][k];
-          ap[k] = tot[k] - am[k];
+            for (int p = 0; p < MW; ++p) tot += s[p] * W[p][k];
+            am[k] = beta * lamL * W[0][k];
+            ap[k] = tot - am[k];
+          }
+          return;
         }
-        return;
       }
-      // last family: Q_r - W^last and the right state
-      const R muL = sonic<DIR>(C, qr[0] - W[MW - 1][0], qr[n] - W[MW - 1][n], 1);
-      const R muR = sonic<DIR>(C, qr[0], qr[n], 1);
-      if (muL < R(0) && muR > R(0)) {
-        const R beta = (muR - s[MW - 1]) / (muR - muL);
+      // last family: u+c < 0 at Q_r - W^last and > 0 at Q_r
+      const R hm2 = qr[0] - W[MW - 1][0], hum2 = qr[n] - W[MW - 1][n];
+      if (plus_neg(C, hm2, hum2) && plus_pos(C, qr[0], qr[n])) {
+        const R muL = sonic<DIR>(C, hm2, hum2, 1);
+        const R muR = sonic<DIR>(C, qr[0], qr[n], 1);
+        if (muL < R(0) && muR > R(0)) {
+          const R beta = FM<R>::div(muR - s[MW - 1], muR - muL);
 #pragma unroll
-        for (int k = 0; k < M; ++k) {
-          ap[k] = (R(1) - beta) * muR * W[MW - 1][k];
-          am[k] = tot[k] - ap[k];
+          for (int k = 0; k < M; ++k) {
+            R tot = R(0);
+#pragma unroll
+            for (int p = 0; p < MW; ++p) tot += s[p] * W[p][k];
+            ap[k] = (R(1) - beta) * muR * W[MW - 1][k];
+            am[k] = tot - ap[k];
+          }
+          return;
         }
-        return;
       }
     }
     split_waves<M, MW, R>(W, s, am, ap);
@@ -285,7 +325,7 @@ struct RpSW {
     constexpr int n = Dirs<ND, DIR>::n, t = Dirs<ND, DIR>::t;
     // transverse frame: normal = t (speed ut), tangential = n (speed un)
     const R un = x[0], ut = x[1], c = x[2];
-    const R i2c = R(0.5) / c;
+    const R i2c = x[3];
     R be[MW], km[MW], kp[MW];
     coef<t, n>(ut, un, c, i2c, a, be);
     const R lam[3] = {ut - c, ut, ut + c};
@@ -307,8 +347,7 @@ struct RpSW {
   __device__ static __forceinline__ void to_char(const MConsts<R>&, const R (&x)[NCTX],
                                                  const R (&q)[M], R (&w)[M]) {
     constexpr int n = Dirs<ND, DIR>::n, t = Dirs<ND, DIR>::t;
-    const R i2c = R(0.5) / x[2];
-    coef<n, t>(x[0], x[1], x[2], i2c, q, w);
+    coef<n, t>(x[0], x[1], x[2], x[3], q, w);
   }
   template <int DIR>
   __device__ static __forceinline__ void from_char(const MConsts<R>&, const R (&x)[NCTX],
@@ -323,7 +362,7 @@ struct RpSW {
 // ---------------------------------------------------------------------------
 template <typename R, int ND>
 struct EulerBase {
-  static constexpr int M = ND + 2, E = ND + 1, NCTX = 4;  // ctx: un, ut, H, c
+  static constexpr int M = ND + 2, E = ND + 1, NCTX = 6;  // ctx: un, ut, H, c, 1/c^2, 1/(2c)
 
   template <int DIR>
   __device__ static __forceinline__ R pressure(const MConsts<R>& C, const R (&q)[M], R irho) {
@@ -337,27 +376,28 @@ struct EulerBase {
   __device__ static __forceinline__ void roe(const MConsts<R>& C, const R (&ql)[M],
                                              const R (&qr)[M], R (&x)[NCTX], R& pl, R& pr) {
     constexpr int n = Dirs<ND, DIR>::n, t = Dirs<ND, DIR>::t;
-    const R irl = R(1) / ql[0], irr = R(1) / qr[0];
+    const R irl = FM<R>::rcp(ql[0]), irr = FM<R>::rcp(qr[0]);
     pl = pressure<DIR>(C, ql, irl);
     pr = pressure<DIR>(C, qr, irr);
     const R il = rsq(ql[0]), ir = rsq(qr[0]);  // 1/sqrt(rho)
     const R sl = ql[0] * il, sr = qr[0] * ir;  // sqrt(rho)
-    const R iden = R(1) / (sl + sr);
+    const R iden = FM<R>::rcp(sl + sr);
     x[0] = (ql[n] * il + qr[n] * ir) * iden;
     x[1] = (t >= 0) ? (ql[t < 0 ? 0 : t] * il + qr[t < 0 ? 0 : t] * ir) * iden : R(0);
     x[2] = ((ql[E] + pl) * il + (qr[E] + pr) * ir) * iden;  // sqrt(rho) H = (E+p)/sqrt(rho)
     const R c2 = C.gm1 * (x[2] - R(0.5) * (x[0] * x[0] + x[1] * x[1]));
-    x[3] = sqrt(c2);
+    x[3] = FM<R>::sqrt(c2);
+    x[4] = FM<R>::rcp(c2);
+    x[5] = FM<R>::div(R(0.5), x[3]);
   }
 
   // eigen-coefficients of d in the frame (normal a, tangential b)
   template <int A, int B>
-  __device__ static __forceinline__ void coef(const MConsts<R>& C, R un, R ut, R H, R c,
-                                              const R (&d)[M], R (&al)[M]) {
-    const R ic2 = R(1) / (c * c);
+  __device__ static __forceinline__ void coef(const MConsts<R>& C, R un, R ut, R H, R c, R ic2,
+                                              R i2c, const R (&d)[M], R (&al)[M]) {
     const R ash = (B >= 0) ? d[B < 0 ? 0 : B] - ut * d[0] : R(0);
     const R a2 = C.gm1 * ((H - un * un) * d[0] + un * d[A] - d[E] + ut * ash) * ic2;
-    const R a4 = (d[A] + (c - un) * d[0] - c * a2) * (R(0.5) / c);
+    const R a4 = (d[A] + (c - un) * d[0] - c * a2) * i2c;
     al[0] = d[0] - a2 - a4;
     al[1] = a2;
     if (B >= 0) al[2] = ash;
@@ -382,7 +422,7 @@ struct EulerBase {
     constexpr int n = Dirs<ND, DIR>::n, t = Dirs<ND, DIR>::t;
     const R un = x[0], ut = x[1], H = x[2], c = x[3];
     R be[M], km[M], kp[M];
-    coef<t, n>(C, ut, un, H, c, a, be);
+    coef<t, n>(C, ut, un, H, c, x[4], x[5], a, be);
 #pragma unroll
     for (int p = 0; p < M; ++p) {
       const R lam = (p == 0) ? ut - c : (p == M - 1 ? ut + c : ut);
@@ -403,7 +443,7 @@ struct EulerBase {
   __device__ static __forceinline__ void to_char(const MConsts<R>& C, const R (&x)[NCTX],
                                                  const R (&q)[M], R (&w)[M]) {
     constexpr int n = Dirs<ND, DIR>::n, t = Dirs<ND, DIR>::t;
-    coef<n, t>(C, x[0], x[1], x[2], x[3], q, w);
+    coef<n, t>(C, x[0], x[1], x[2], x[3], x[4], x[5], q, w);
   }
   template <int DIR>
   __device__ static __forceinline__ void from_char(const MConsts<R>&, const R (&x)[NCTX],
@@ -420,12 +460,54 @@ struct RpEulerRoe : EulerBase<R, ND> {
   static constexpr bool FWAVE = false;
   static constexpr int WALL_X = 1, WALL_Y = (ND == 2) ? 2 : -1;
 
+  // Signs of u -/+ c without square roots or divisions: with rho > 0 and
+  // X = rho E - (m_n^2 + m_t^2)/2 > 0 (so p > 0), rho^2 c^2 = gamma (gamma-1) X
+  // and u - c < 0 <=> m_n < 0 or m_n^2 < gamma (gamma-1) X.
+  template <int DIR>
+  __device__ static __forceinline__ void sign_terms(const MConsts<R>& C, const R (&q)[M], R& mn,
+                                                    R& rc2, bool& phys) {
+    constexpr int n = Dirs<ND, DIR>::n, t = Dirs<ND, DIR>::t;
+    const R ke = (t >= 0) ? q[n] * q[n] + q[t < 0 ? 0 : t] * q[t < 0 ? 0 : t] : q[n] * q[n];
+    const R X = q[0] * q[E] - R(0.5) * ke;
+    mn = q[n];
+    rc2 = C.gamma * C.gm1 * X;
+    phys = q[0] > R(0) && X > R(0);
+  }
+  template <int DIR>
+  __device__ static __forceinline__ bool minus_neg(const MConsts<R>& C, const R (&q)[M]) {
+    R m, r;
+    bool ph;
+    sign_terms<DIR>(C, q, m, r, ph);
+    return ph && (m < R(0) || m * m < r);
+  }
+  template <int DIR>
+  __device__ static __forceinline__ bool minus_pos(const MConsts<R>& C, const R (&q)[M]) {
+    R m, r;
+    bool ph;
+    sign_terms<DIR>(C, q, m, r, ph);
+    return ph && m > R(0) && m * m > r;
+  }
+  template <int DIR>
+  __device__ static __forceinline__ bool plus_neg(const MConsts<R>& C, const R (&q)[M]) {
+    R m, r;
+    bool ph;
+    sign_terms<DIR>(C, q, m, r, ph);
+    return ph && m < R(0) && m * m > r;
+  }
+  template <int DIR>
+  __device__ static __forceinline__ bool plus_pos(const MConsts<R>& C, const R (&q)[M]) {
+    R m, r;
+    bool ph;
+    sign_terms<DIR>(C, q, m, r, ph);
+    return ph && (m > R(0) || m * m < r);
+  }
+
   template <int DIR>
   __device__ static __forceinline__ R sonic(const MConsts<R>& C, const R (&q)[M], int plus) {
     constexpr int n = Dirs<ND, DIR>::n;
-    const R ir = R(1) / q[0];
+    const R ir = FM<R>::rcp(q[0]);
     const R p = B::template pressure<DIR>(C, q, ir);
-    const R c = sqrt(C.gamma * p * ir);
+    const R c = FM<R>::sqrt(C.gamma * p * ir);
     const R u = q[n] * ir;
     return plus ? u + c : u - c;
   }
@@ -442,7 +524,7 @@ struct RpEulerRoe : EulerBase<R, ND> {
     R d[M], al[M];
 #pragma unroll
     for (int k = 0; k < M; ++k) d[k] = qr[k] - ql[k];
-    B::template coef<n, t>(C, un, ut, H, c, d, al);
+    B::template coef<n, t>(C, un, ut, H, c, x[4], x[5], d, al);
 #pragma unroll
     for (int p = 0; p < MW; ++p)
 #pragma unroll
@@ -470,38 +552,42 @@ struct RpEulerRoe : EulerBase<R, ND> {
     s[1] = un;
     s[M - 1] = un + c;
     if (C.entropy_fix) {
-      R tot[M], qm[M];
-#pragma unroll
-      for (int k = 0; k < M; ++k) {
-        tot[k] = R(0);
-#pragma unroll
-        for (int p = 0; p < MW; ++p) tot[k] += s[p] * W[p][k];
-      }
+      R qm[M];
 #pragma unroll
       for (int k = 0; k < M; ++k) qm[k] = ql[k] + W[0][k];
-      const R lamL = sonic<DIR>(C, ql, 0);
-      const R lamR = sonic<DIR>(C, qm, 0);
-      if (lamL < R(0) && lamR > R(0)) {
-        const R beta = (lamR - s[0]) / (lamR - lamL);
+      if (minus_neg<DIR>(C, ql) && minus_pos<DIR>(C, qm)) {
+        const R lamL = sonic<DIR>(C, ql, 0);
+        const R lamR = sonic<DIR>(C, qm, 0);
+        if (lamL < R(0) && lamR > R(0)) {
+          const R beta = FM<R>::div(lamR - s[0], lamR - lamL);
 #pragma unroll
-        for (int k = 0; k < M; ++k) {
-          am[k] = beta * lamL * W[0][k];
-          ap[k] = tot[k] - am[k];
+          for (int k = 0; k < M; ++k) {
+            R tot = R(0);
+#pragma unroll
+            for (int p = 0; p < MW; ++p) tot += s[p] * W[p][k];
+            am[k] = beta * lamL * W[0][k];
+            ap[k] = tot - am[k];
+          }
+          return;
         }
-        return;
       }
 #pragma unroll
       for (int k = 0; k < M; ++k) qm[k] = qr[k] - W[M - 1][k];
-      const R muL = sonic<DIR>(C, qm, 1);
-      const R muR = sonic<DIR>(C, qr, 1);
-      if (muL < R(0) && muR > R(0)) {
-        const R beta = (muR - s[M - 1]) / (muR - muL);
+      if (plus_neg<DIR>(C, qm) && plus_pos<DIR>(C, qr)) {
+        const R muL = sonic<DIR>(C, qm, 1);
+        const R muR = sonic<DIR>(C, qr, 1);
+        if (muL < R(0) && muR > R(0)) {
+          const R beta = FM<R>::div(muR - s[M - 1], muR - muL);
 #pragma unroll
-        for (int k = 0; k < M; ++k) {
-          ap[k] = (R(1) - beta) * muR * W[M - 1][k];
-          am[k] = tot[k] - ap[k];
+          for (int k = 0; k < M; ++k) {
+            R tot = R(0);
+#pragma unroll
+            for (int p = 0; p < MW; ++p) tot += s[p] * W[p][k];
+            ap[k] = (R(1) - beta) * muR * W[M - 1][k];
+            am[k] = tot - ap[k];
+          }
+          return;
         }
-        return;
       }
     }
     split_waves<M, MW, R>(W, s, am, ap);
@@ -518,7 +604,7 @@ struct RpEulerHLLE : EulerBase<R, ND> {
   template <int DIR>
   __device__ static __forceinline__ void flux(const R (&q)[M], R p, R (&f)[M]) {
     constexpr int n = Dirs<ND, DIR>::n, t = Dirs<ND, DIR>::t;
-    const R u = q[n] / q[0];
+    const R u = FM<R>::div(q[n], q[0]);
     f[0] = q[n];
     f[n] = q[n] * u + p;
     if (t >= 0) f[t < 0 ? 0 : t] = q[t < 0 ? 0 : t] * u;
@@ -533,13 +619,14 @@ struct RpEulerHLLE : EulerBase<R, ND> {
     constexpr int n = Dirs<ND, DIR>::n;
     R pl, pr;
     B::template roe<DIR>(C, ql, qr, x, pl, pr);
-    const R cl = sqrt(C.gamma * pl / ql[0]), cr = sqrt(C.gamma * pr / qr[0]);
-    const R s1 = fmin(ql[n] / ql[0] - cl, x[0] - x[3]);
-    const R s2 = fmax(qr[n] / qr[0] + cr, x[0] + x[3]);
+    const R cl = FM<R>::sqrt(C.gamma * FM<R>::div(pl, ql[0])),
+            cr = FM<R>::sqrt(C.gamma * FM<R>::div(pr, qr[0]));
+    const R s1 = fmin(FM<R>::div(ql[n], ql[0]) - cl, x[0] - x[3]);
+    const R s2 = fmax(FM<R>::div(qr[n], qr[0]) + cr, x[0] + x[3]);
     R fl[M], fr[M];
     flux<DIR>(ql, pl, fl);
     flux<DIR>(qr, pr, fr);
-    const R iden = R(1) / (s1 - s2);
+    const R iden = FM<R>::rcp(s1 - s2);
 #pragma unroll
     for (int k = 0; k < M; ++k) {
       const R qs = (fr[k] - fl[k] - s2 * qr[k] + s1 * ql[k]) * iden;
@@ -567,13 +654,13 @@ struct RpElasticity {
                                                R (&W)[MW][M], R (&s)[MW], R (&am)[M],
                                                R (&ap)[M], R (&ctx)[NCTX]) {
     const R rl = al[0], Kl = al[1], rr = ar[0], Kr = ar[1];
-    const R el = exp(Kl * ql[0]), er = exp(Kr * qr[0]);
-    const R irl = R(1) / rl, irr = R(1) / rr;
-    const R cl = sqrt(Kl * el * irl), cr = sqrt(Kr * er * irr);
+    const R el = FM<R>::exp(Kl * ql[0]), er = FM<R>::exp(Kr * qr[0]);
+    const R irl = FM<R>::rcp(rl), irr = FM<R>::rcp(rr);
+    const R cl = FM<R>::sqrt(Kl * el * irl), cr = FM<R>::sqrt(Kr * er * irr);
     const R Zl = rl * cl, Zr = rr * cr;
     const R d1 = ql[1] * irl - qr[1] * irr;  // jump of -u
     const R d2 = el - er;                    // jump of -sigma
-    const R iz = R(1) / (Zl + Zr);
+    const R iz = FM<R>::rcp(Zl + Zr);
     const R b1 = (Zr * d1 + d2) * iz;
     const R b2 = (Zl * d1 - d2) * iz;
     W[0][0] = b1;
@@ -635,7 +722,7 @@ __device__ __forceinline__ R limiter(int lim, R th) {
     case CLAW_LIM_SUPERBEE: return fmax(R(0), fmax(fmin(R(1), R(2) * th), fmin(R(2), th)));
     case CLAW_LIM_VANLEER: {
       const R a = fabs(th);
-      return (th + a) / (R(1) + a);
+      return FM<R>::div(th + a, R(1) + a);
     }
     case CLAW_LIM_MC: return fmax(R(0), fmin(R(0.5) * (R(1) + th), fmin(R(2), R(2) * th)));
     default: return R(1);
@@ -657,7 +744,7 @@ __device__ __forceinline__ void correction(const MConsts<R>& C, const R (&W)[RP:
     R phi;
     if (nrm[p] == R(0)) phi = R(0);
     else if (C.lim == CLAW_LIM_NONE) phi = R(1);
-    else phi = limiter<R>(C.lim, dot_up[p] / nrm[p]);
+    else phi = limiter<R>(C.lim, FM<R>::div(dot_up[p], nrm[p]));
     const R a = fabs(s[p]);
     const R sg = RP::FWAVE ? (s[p] > R(0) ? R(1) : (s[p] < R(0) ? R(-1) : R(0))) : a;
     const R cf = R(0.5) * sg * (R(1) - dtdn * a) * phi;

@@ -38,7 +38,7 @@ __device__ __forceinline__ R weno5(R a, R b, R c, R d, R e, R eps) {
   const R s0 = e0 * e0, s1 = e1 * e1, s2 = e2 * e2;
   // alpha_k = d_k / s_k; multiply through by s0 s1 s2
   const R w0 = R(0.1) * (s1 * s2), w1 = R(0.6) * (s0 * s2), w2 = R(0.3) * (s0 * s1);
-  return (w0 * q0 + w1 * q1 + w2 * q2) / (w0 + w1 + w2);
+  return FM<R>::div(w0 * q0 + w1 * q1 + w2 * q2, w0 + w1 + w2);
 }
 
 
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(TX * TY)
   __shared__ R FM[M][NE];  // A^- dQ at the interface
   __shared__ R FP[M][NE];  // A^+ dQ at the interface
   __shared__ int s_done, s_cur, s_nbuf;
-  __shared__ double s_dt;
+  __shared__ R s_dt, s_idn[2];
 
   const int tid = threadIdx.x;
   const int ti = tid % TX, tj = tid / TX;
@@ -71,7 +71,9 @@ __global__ void __launch_bounds__(TX * TY)
     DevCtl* ctl = mb.ctl;
     if (tid == 0) {
       s_done = ctl->done;
-      s_dt = ctl->dt;
+      s_dt = (R)ctl->dt;
+      s_idn[0] = (R)(1.0 / ctl->dx[0]);
+      s_idn[1] = (R)(1.0 / ctl->dx[1]);
       s_cur = ctl->cur;
       s_nbuf = ctl->nbuf;
     }
@@ -92,7 +94,6 @@ __global__ void __launch_bounds__(TX * TY)
     const R* __restrict__ qn = (const R*)mb.q[cur];
     R* __restrict__ qo = (R*)mb.q[out_b];
     const R* __restrict__ aux = (const R*)mb.aux;
-    const double dtd = s_dt;
     const size_t plane = (size_t)nx * ny;
 
     // stage Q^(k) (and aux) with a 3-cell halo, corners skipped in 2D
@@ -121,14 +122,14 @@ __global__ void __launch_bounds__(TX * TY)
     R L[M];
 #pragma unroll
     for (int k = 0; k < M; ++k) L[k] = R(0);
-    double smx = 0.0, smy = 0.0;
+    R smx = R(0), smy = R(0);
 
 #pragma unroll
     for (int dir = 0; dir < ND; ++dir) {
       // interfaces of this direction: along-line index a (0..n), line index b
       const int na = (dir == 0) ? TX + 1 : TY + 1;
       const int nl = (dir == 0) ? TY : TX;
-      const R idn = (R)(1.0 / ctl->dx[dir]);
+      const R idn = s_idn[dir];
       // (a) reconstruction at every interface
       for (int e = tid; e < na * nl; e += NT) {
         const int a = e % na, b = e / na;
@@ -212,9 +213,9 @@ __global__ void __launch_bounds__(TX * TY)
         const int ga = ((dir == 0) ? c0 : r0) + a, gb = ((dir == 0) ? r0 : c0) + b;
         const int nA = (dir == 0) ? nx : ny, nB = (dir == 0) ? ny : nx;
         if (ga <= nA && gb < nB) {
-          double m_ = 0.0;
+          R m_ = R(0);
 #pragma unroll
-          for (int p = 0; p < MW; ++p) m_ = nanmax(m_, (double)fabs(s[p]));
+          for (int p = 0; p < MW; ++p) m_ = nanmax(m_, (R)fabs(s[p]));
           if (dir == 0) smx = nanmax(smx, m_);
           else smy = nanmax(smy, m_);
         }
@@ -252,7 +253,7 @@ __global__ void __launch_bounds__(TX * TY)
       const int c = c0 + ti, r = r0 + tj;
       if (c < nx && r < ny) {
         const size_t off = (size_t)r * nx + c;
-        const R dt = (R)dtd;
+        const R dt = s_dt;
 #pragma unroll
         for (int k = 0; k < M; ++k) {
           const R qkv = Qt[k][(ND == 2) ? G + tj : 0][G + ti];
@@ -265,7 +266,7 @@ __global__ void __launch_bounds__(TX * TY)
         }
       }
     }
-    finish_attempt(ctl, smx, smy, bad, mb.ntiles, stage == 2);
+    finish_attempt<R>(ctl, smx, smy, bad, mb.ntiles, stage == 2);
   }
 }
 

@@ -1,0 +1,103 @@
+"""Batched and served solves: every member's result is the same alone and in
+the mix (same kernels, same per-member controller), and matches the oracle.
+"""
+import numpy as np
+import pytest
+
+from paper_1111_6583_gb300 import workloads as wl
+from tests.gpu_util import FP64_TOL, oracle_evolve, rel_maxnorm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _ensemble(sizes, t_end):
+    rng = np.random.Generator(np.random.PCG64(11))
+    specs = []
+    for k, n in enumerate(sizes):
+        sp = wl.elasticity_member(n, float(rng.uniform(0.1, 0.5)), float(rng.uniform(1, 5)),
+                                  t_end=t_end * (1.0 + 0.3 * k / len(sizes)))
+        specs.append(sp)
+    return specs
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batch_equals_alone(orc, prec, use_graph):
+    import torch
+    from paper_1111_6583_gb300 import claw
+    specs = _ensemble([64, 100, 1000, 4096, 5003, 9000], t_end=2.0)
+    b = claw.Batch(specs, prec)
+    infos = b.evolve(use_graph=use_graph)
+    torch.cuda.synchronize()
+    for k, sp in enumerate(specs):
+        s = claw.Solver(sp, prec)
+        ia = s.evolve(sp["t_end"])
+        qa = s.q.double().cpu().numpy()
+        qb = b.q[k].double().cpu().numpy()
+        assert infos[k]["steps"] == ia["steps"] and infos[k]["t"] == ia["t"] == sp["t_end"]
+        assert np.array_equal(qa, qb), k
+        s.close()
+        if prec == "fp64" and k < 3:
+            qo, io = oracle_evolve(orc, sp, sp["t_end"])
+            assert io["steps"] == ia["steps"]
+            assert rel_maxnorm(qb, qo) <= FP64_TOL
+    b.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("budget_mb", [4096, 3])
+def test_server_equals_alone(orc, prec, budget_mb):
+    """Requests of different sizes and final times through the continuous-
+    batching server (a 3 MB budget admits one or two at a time) give the
+    same states as solving each alone."""
+    import torch
+    from paper_1111_6583_gb300 import claw
+    reqs = [(48, [(0.5, 0.1, 0.4, 0.5)], 0.3), (96, [(0.3, 0.2, 0.6, 0.6)], 0.5),
+            (64, [(0.8, 0.05, 0.5, 0.3), (0.2, 0.3, 0.3, 0.7)], 0.2),
+            (120, [(0.4, 0.15, 0.5, 0.5)], 0.4)]
+    specs = [wl.sw_humps_2d(n, humps, t) for n, humps, t in reqs]
+    sv = claw.Server(specs[0], prec, budget_bytes=budget_mb << 20, max_slots=8)
+    tickets = [sv.submit(sp) for sp in specs]
+    results = {}
+    guard = 0
+    while len(results) < len(tickets):
+        sv.pump(4)
+        for t in tickets:
+            if t not in results:
+                r = sv.poll(t)
+                if r is not None:
+                    results[t] = r
+        guard += 1
+        assert guard < 100000
+    sv.close()
+    for t, sp in zip(tickets, specs):
+        r = results[t]
+        assert r["status"] == "ok" and r["t"] == sp["t_end"]
+        s = claw.Solver(sp, prec)
+        ia = s.evolve(sp["t_end"])
+        qa = s.q.double().cpu().numpy()
+        s.close()
+        assert ia["steps"] == r["steps"]
+        assert np.array_equal(qa, r["q"].astype(np.float64))
+        if prec == "fp64":
+            qo, io = oracle_evolve(orc, sp, sp["t_end"])
+            assert rel_maxnorm(r["q"], qo) <= FP64_TOL
+
+
+def test_server_rejects_request_beyond_budget():
+    from paper_1111_6583_gb300 import claw
+    sp = wl.sw_humps_2d(256, [(0.5, 0.1, 0.5, 0.5)], 0.1)
+    sv = claw.Server(sp, "fp32", budget_bytes=1 << 20, max_slots=4)
+    with pytest.raises(claw.ClawError) as ei:
+        sv.submit(sp)
+    assert ei.value.status == claw.CLAW_EBUDGET
+    sv.close()
