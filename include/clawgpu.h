@@ -21,7 +21,8 @@
  *     buffers (a second/third copy of the state, a control block) at
  *     claw_bind_state and frees them at destroy.
  *   - State layout: field-major, interior cells only, x fastest:
- *       q[m][ny][nx]  (2D),  q[m][nx]  (1D)   -- PyClaw's q[m, i, j] (Sec. 4.2).
+ *       q[m][nz][ny][nx] (3D), q[m][ny][nx] (2D), q[m][nx] (1D) -- PyClaw's
+ *       field-major q[m, i, j] (Sec. 4.2).  3D adds double-transverse terms.
  *     aux has the same layout with num_aux fields.
  *   - CLAW_FP64: q/aux are double.  CLAW_FP32: q/aux are float and the
  *     Riemann/limiter/WENO arithmetic is float; time, dt, the CFL number and
@@ -65,7 +66,7 @@ enum { CLAW_BC_PERIODIC = 0, CLAW_BC_WALL = 1, CLAW_BC_EXTRAP = 2, CLAW_BC_INFLO
 /* Domain (Sec. 4.2: tensor product of equispaced 1D grids).  n[d] cells on
  * [lower[d], upper[d]]; entries beyond ndim are ignored. */
 typedef struct {
-  int ndim;            /* 1 or 2 */
+  int ndim;            /* 1, 2 or 3 (3D: classic scheme, advection and acoustics) */
   int64_t n[3];
   double lower[3], upper[3];
 } claw_grid;

@@ -56,11 +56,12 @@ class _Prob(ctypes.Structure):
         ("order", ctypes.c_int), ("transverse", ctypes.c_int), ("char_decomp", ctypes.c_int),
         ("entropy_fix", ctypes.c_int),
         ("num_eqn", ctypes.c_int), ("num_aux", ctypes.c_int), ("num_waves", ctypes.c_int),
-        ("bc_lo", ctypes.c_int * 2), ("bc_hi", ctypes.c_int * 2),
+        ("bc_lo", ctypes.c_int * 3), ("bc_hi", ctypes.c_int * 3),
         ("inflow", ctypes.c_double * 8), ("params", ctypes.c_double * 8),
         ("cfl_desired", ctypes.c_double), ("cfl_max", ctypes.c_double),
         ("dt_initial", ctypes.c_double), ("dt_max", ctypes.c_double),
         ("max_retries", ctypes.c_int), ("weno_eps", ctypes.c_double),
+        ("nz", ctypes.c_int), ("dz", ctypes.c_double),
     ]
 
 
@@ -133,22 +134,24 @@ def make_problem(spec: dict):
     lo = list(spec["lower"]) + [0.0, 0.0]
     hi = list(spec["upper"]) + [1.0, 1.0]
     p.ndim = ndim
-    p.nx, p.ny = int(n[0]), (int(n[1]) if ndim == 2 else 1)
+    p.nx, p.ny = int(n[0]), (int(n[1]) if ndim >= 2 else 1)
+    p.nz = int(n[2]) if ndim == 3 else 1
     p.dx = (hi[0] - lo[0]) / n[0]
-    p.dy = (hi[1] - lo[1]) / n[1] if ndim == 2 else 1.0
+    p.dy = (hi[1] - lo[1]) / n[1] if ndim >= 2 else 1.0
+    p.dz = (hi[2] - lo[2]) / n[2] if ndim == 3 else 1.0
     p.rp = RP[spec["rp"]]
     p.scheme = SCHEME[spec.get("scheme", "classic")]
     p.lim = LIM[spec.get("lim", "mc")]
     p.order = int(spec.get("order", 2))
-    p.transverse = int(spec.get("transverse", 2)) if ndim == 2 else 0
+    p.transverse = int(spec.get("transverse", 2)) if ndim >= 2 else 0
     p.char_decomp = int(spec.get("char_decomp", 0))
     p.entropy_fix = int(spec.get("entropy_fix", 1))
     p.num_eqn = lib.orc_num_eqn(p.rp, ndim)
     p.num_aux = int(spec.get("num_aux", 2 if spec["rp"] == "elasticity_fwave" else 0))
     p.num_waves = lib.orc_num_waves(p.rp, ndim)
-    bl = list(spec.get("bc_lower", ["periodic"] * ndim)) + ["periodic"]
-    bh = list(spec.get("bc_upper", ["periodic"] * ndim)) + ["periodic"]
-    for d in range(2):
+    bl = list(spec.get("bc_lower", ["periodic"] * ndim)) + ["periodic"] * 2
+    bh = list(spec.get("bc_upper", ["periodic"] * ndim)) + ["periodic"] * 2
+    for d in range(3):
         p.bc_lo[d] = BC[bl[d]]
         p.bc_hi[d] = BC[bh[d]]
     inflow = list(spec.get("inflow", [])) + [0.0] * 8
@@ -166,6 +169,8 @@ def make_problem(spec: dict):
 
 
 def _shape(p):
+    if p.ndim == 3:
+        return (p.num_eqn, p.nz, p.ny, p.nx)
     return (p.num_eqn, p.ny, p.nx) if p.ndim == 2 else (p.num_eqn, p.nx)
 
 
@@ -258,7 +263,7 @@ def ssp_rk3_linear(lam, dt, q0) -> float:
 
 
 def max_speeds(p, q, aux=None):
-    smax = np.zeros(2)
+    smax = np.zeros(3)
     _load().orc_max_speeds(ctypes.byref(p), _ptr(_arr(q, _shape(p))),
                            _ptr(_arr(aux) if aux is not None else None), _ptr(smax))
     return smax

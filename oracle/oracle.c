@@ -28,11 +28,11 @@
 int orc_num_eqn(int rp, int ndim) {
   switch (rp) {
     case ORC_RP_ADVECTION: return 1;
-    case ORC_RP_ACOUSTICS: return ndim == 1 ? 2 : 3;
-    case ORC_RP_SW_ROE: return ndim == 1 ? 2 : 3;
+    case ORC_RP_ACOUSTICS: return ndim + 1;
+    case ORC_RP_SW_ROE: return ndim == 1 ? 2 : (ndim == 2 ? 3 : 0);
     case ORC_RP_EULER_ROE:
-    case ORC_RP_EULER_HLLE: return ndim == 1 ? 3 : 4;
-    case ORC_RP_ELASTICITY_FWAVE: return 2;
+    case ORC_RP_EULER_HLLE: return ndim <= 2 ? ndim + 2 : 0;
+    case ORC_RP_ELASTICITY_FWAVE: return ndim == 1 ? 2 : 0;
   }
   return 0;
 }
@@ -791,9 +791,270 @@ static int classic2d(const orc_prob* P, double* q, const double* aux, double dt,
   return ORC_OK;
 }
 
+static int classic3d(const orc_prob* P, double* q, double dt, double* cfl);
+
 int orc_classic_step(const orc_prob* P, double* q, const double* aux, double dt, double* cfl) {
   if (P->ndim == 1) return classic1d(P, q, aux, dt, cfl);
+  if (P->ndim == 3) return classic3d(P, q, dt, cfl);
   return classic2d(P, q, aux, dt, cfl);
+}
+
+
+/* ------------------------------------------------------------------------ */
+/* classic 3D unsplit step with transverse and double-transverse propagation */
+/* (LeVeque 1997): advection and linear acoustics                            */
+/* ------------------------------------------------------------------------ */
+
+/* cell (i,j,k) of a ghosted 3D array with ghost width 2, ncomp fields */
+typedef struct {
+  const double* a;
+  int m, NX, NY, NZ;
+} g3arr;
+
+static void g3cell(const g3arr* G, int i, int j, int k, double* out) {
+  size_t plane = (size_t)G->NX * G->NY * G->NZ;
+  size_t off = ((size_t)(k + 2) * G->NY + (j + 2)) * G->NX + (i + 2);
+  for (int c = 0; c < G->m; ++c) out[c] = G->a[c * plane + off];
+}
+
+/* ghost cells of a 3D array: x ghosts on interior (y,z) rows, then y ghosts on
+ * all x for interior z, then z ghosts everywhere */
+static void fill_ghost3(const orc_prob* P, const double* q, double* qg) {
+  const int nx = P->nx, ny = P->ny, nz = P->nz, m = P->num_eqn, g = 2;
+  const int NX = nx + 2 * g, NY = ny + 2 * g, NZ = nz + 2 * g;
+  const size_t plane = (size_t)NX * NY * NZ;
+#define QG(c, i, j, k) qg[(c) * plane + ((size_t)((k) + g) * NY + ((j) + g)) * NX + ((i) + g)]
+  for (int c = 0; c < m; ++c)
+    for (int k = 0; k < nz; ++k)
+      for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i)
+          QG(c, i, j, k) = q[(size_t)c * nx * ny * nz + ((size_t)k * ny + j) * nx + i];
+  const int n3[3] = {nx, ny, nz};
+  for (int d = 0; d < 3; ++d) {
+    /* ranges: directions before d include ghosts, after d interior only */
+    int lo[3], hi[3];
+    for (int e = 0; e < 3; ++e) {
+      lo[e] = e < d ? -g : 0;
+      hi[e] = e < d ? n3[e] + g : n3[e];
+    }
+    for (int side = 0; side < 2; ++side)
+      for (int kk = 1; kk <= g; ++kk) {
+        int gi = side == 0 ? -kk : n3[d] - 1 + kk;
+        int bc = side == 0 ? P->bc_lo[d] : P->bc_hi[d];
+        int src, mir;
+        ghost_source(bc, n3[d], gi, &src, &mir);
+        int wall = wall_comp(P, d);
+        for (int a = lo[(d + 1) % 3]; a < hi[(d + 1) % 3]; ++a)
+          for (int b = lo[(d + 2) % 3]; b < hi[(d + 2) % 3]; ++b) {
+            int idx[3], sidx[3];
+            idx[d] = gi;
+            idx[(d + 1) % 3] = a;
+            idx[(d + 2) % 3] = b;
+            sidx[0] = idx[0]; sidx[1] = idx[1]; sidx[2] = idx[2];
+            sidx[d] = src;
+            for (int c = 0; c < m; ++c) {
+              double v = QG(c, sidx[0], sidx[1], sidx[2]);
+              if (bc == ORC_BC_INFLOW) v = P->inflow[c];
+              else if (mir && c == wall) v = -v;
+              QG(c, idx[0], idx[1], idx[2]) = v;
+            }
+          }
+      }
+  }
+#undef QG
+}
+
+/* normal solve of a 3D problem in direction d */
+static void rp3(const orc_prob* P, int d, const double* ql, const double* qr, double* W,
+                double* s, double* amdq, double* apdq) {
+  int m = P->num_eqn;
+  if (P->rp == ORC_RP_ADVECTION) {
+    W[0] = qr[0] - ql[0];
+    s[0] = P->params[d];
+  } else {
+    /* acoustics (p, u, v, w): the two waves of the normal velocity 1+d */
+    double alpha[MAXW], r[MAXW * MAXM], d_[MAXM];
+    int n = 1 + d;
+    for (int k = 0; k < m; ++k) d_[k] = qr[k] - ql[k];
+    acoustics_eig(P, n, -1, 0, d_, alpha, r, s);
+    for (int p = 0; p < 2; ++p)
+      for (int k = 0; k < m; ++k) W[p * m + k] = alpha[p] * r[p * m + k];
+  }
+  split_by_speed(m, orc_num_waves(P->rp, 3), W, s, amdq, apdq);
+}
+
+/* split a (a fluctuation of a d-normal solve) in direction e */
+static void trans3(const orc_prob* P, int e, const double* a, double* em, double* ep) {
+  int m = P->num_eqn;
+  for (int k = 0; k < m; ++k) { em[k] = 0.0; ep[k] = 0.0; }
+  if (P->rp == ORC_RP_ADVECTION) {
+    double v = P->params[e];
+    em[0] = fmin(v, 0.0) * a[0];
+    ep[0] = fmax(v, 0.0) * a[0];
+    return;
+  }
+  double beta[MAXW], r[MAXW * MAXM], lam[MAXW];
+  acoustics_eig(P, 1 + e, -1, 0, a, beta, r, lam);
+  for (int p = 0; p < 2; ++p)
+    for (int k = 0; k < m; ++k) {
+      em[k] += fmin(lam[p], 0.0) * beta[p] * r[p * m + k];
+      ep[k] += fmax(lam[p], 0.0) * beta[p] * r[p * m + k];
+    }
+}
+
+/* add coef*v to the flux correction of the face (f0,f1,f2) in direction e
+ * when that face bounds an interior cell */
+static void add_face(const orc_prob* P, double* Fe, int e, const int* f, double coef,
+                     const double* v) {
+  const int n3[3] = {P->nx, P->ny, P->nz};
+  for (int d = 0; d < 3; ++d) {
+    int hi = (d == e) ? n3[d] : n3[d] - 1;
+    if (f[d] < 0 || f[d] > hi) return;
+  }
+  const int NXF = P->nx + (e == 0), NYF = P->ny + (e == 1);
+  size_t off = (((size_t)f[2] * NYF + f[1]) * NXF + f[0]) * P->num_eqn;
+  for (int k = 0; k < P->num_eqn; ++k) Fe[off + k] += coef * v[k];
+}
+
+static int classic3d(const orc_prob* P, double* q, double dt, double* cfl) {
+  const int nx = P->nx, ny = P->ny, nz = P->nz, m = P->num_eqn;
+  const int nw = orc_num_waves(P->rp, 3);
+  const double dxs[3] = {P->dx, P->dy, P->dz};
+  const int n3[3] = {nx, ny, nz};
+  g3arr Q;
+  Q.m = m; Q.NX = nx + 4; Q.NY = ny + 4; Q.NZ = nz + 4;
+  double* qb = (double*)malloc(sizeof(double) * (size_t)m * Q.NX * Q.NY * Q.NZ);
+  fill_ghost3(P, q, qb);
+  Q.a = qb;
+  /* per direction: fluctuations and total flux corrections on interior faces */
+  double* AM[3];
+  double* AP[3];
+  double* FC[3];
+  for (int e = 0; e < 3; ++e) {
+    size_t nf = (size_t)(nx + (e == 0)) * (ny + (e == 1)) * (nz + (e == 2)) * m;
+    AM[e] = (double*)calloc(nf, sizeof(double));
+    AP[e] = (double*)calloc(nf, sizeof(double));
+    FC[e] = (double*)calloc(nf, sizeof(double));
+  }
+  double smax[3] = {0.0, 0.0, 0.0};
+  for (int d = 0; d < 3; ++d) {
+    const int e1 = (d + 1) % 3, e2 = (d + 2) % 3;
+    const double dtdn = dt / dxs[d];
+    const int n = n3[d];
+    double* W = (double*)malloc(sizeof(double) * (n + 3) * nw * m);
+    double* S = (double*)malloc(sizeof(double) * (n + 3) * nw);
+    double* AMl = (double*)malloc(sizeof(double) * (n + 3) * m);
+    double* APl = (double*)malloc(sizeof(double) * (n + 3) * m);
+    /* lines along d, one ghost layer in each transverse direction */
+    for (int a = -1; a <= n3[e1]; ++a)
+      for (int b = -1; b <= n3[e2]; ++b) {
+        const int interior_line = a >= 0 && a < n3[e1] && b >= 0 && b < n3[e2];
+        for (int i = -1; i <= n + 1; ++i) {
+          int il[3], ir[3];
+          il[d] = i - 1; ir[d] = i;
+          il[e1] = ir[e1] = a;
+          il[e2] = ir[e2] = b;
+          double ql[MAXM], qr[MAXM];
+          g3cell(&Q, il[0], il[1], il[2], ql);
+          g3cell(&Q, ir[0], ir[1], ir[2], qr);
+          int ii = i + 1;
+          rp3(P, d, ql, qr, W + ii * nw * m, S + ii * nw, AMl + ii * m, APl + ii * m);
+          if (interior_line && i >= 0 && i <= n)
+            for (int p = 0; p < nw; ++p) {
+              double v = fabs(S[ii * nw + p]);
+              if (!(v <= smax[d])) smax[d] = v;
+            }
+        }
+        for (int i = 0; i <= n; ++i) {
+          int ii = i + 1;
+          double F[MAXM] = {0};
+          if (P->order == 2)
+            correction_flux(P, m, nw, W + (ii - 1) * nw * m, W + ii * nw * m,
+                            W + (ii + 1) * nw * m, S + ii * nw, dtdn, F);
+          int f[3];
+          f[d] = i; f[e1] = a; f[e2] = b;
+          /* normal fluctuations and correction on this face */
+          add_face(P, AM[d], d, f, 1.0, AMl + ii * m);
+          add_face(P, AP[d], d, f, 1.0, APl + ii * m);
+          add_face(P, FC[d], d, f, 1.0, F);
+          if (!P->transverse) continue;
+          double apq[MAXM], amq[MAXM];
+          for (int k = 0; k < m; ++k) {
+            apq[k] = APl[ii * m + k] - (P->transverse == 2 ? F[k] : 0.0);
+            amq[k] = AMl[ii * m + k] + (P->transverse == 2 ? F[k] : 0.0);
+          }
+          for (int side = 0; side < 2; ++side) {
+            /* a+ goes into the cell at d-index i, a- into the cell at i-1 */
+            const double* av = side == 0 ? apq : amq;
+            int c[3];
+            c[d] = side == 0 ? i : i - 1; c[e1] = a; c[e2] = b;
+            for (int t = 0; t < 2; ++t) {
+              const int e = t == 0 ? e1 : e2, g2 = t == 0 ? e2 : e1;
+              double em[MAXM], ep[MAXM];
+              trans3(P, e, av, em, ep);
+              /* transverse: faces of cell c in direction e */
+              int fu[3] = {c[0], c[1], c[2]};
+              fu[e] = c[e] + 1;
+              add_face(P, FC[e], e, fu, -0.5 * dtdn, ep);
+              add_face(P, FC[e], e, c, -0.5 * dtdn, em);
+              /* double transverse: the part E^+-a of the fluctuation has moved on
+                 into cell c +- 1 in e, so its share of the third-direction (g2)
+                 transverse flux moves from the g2-faces of c to those of c +- 1:
+                 +1/6 (dt/dx_d)(dt/dx_e) G^+-E^+-a at c's faces, -1/6 at the
+                 shifted cell's faces (six orderings of the three directions
+                 make the corner-transport-upwind triple term) */
+              const double dte = dt / dxs[e];
+              for (int sgn = 0; sgn < 2; ++sgn) {
+                /* E^+ a moves up in e (positive speeds), E^- a down (negative
+                   speeds, so the moved amount is -E^- a) */
+                const double* bv = sgn == 0 ? ep : em;
+                const double k6 = (sgn == 0 ? 1.0 : -1.0) * dtdn * dte / 6.0;
+                int c2[3] = {c[0], c[1], c[2]};
+                c2[e] += sgn == 0 ? 1 : -1;
+                double gm[MAXM], gp[MAXM];
+                trans3(P, g2, bv, gm, gp);
+                int fu1[3] = {c[0], c[1], c[2]};
+                fu1[g2] = c[g2] + 1;
+                add_face(P, FC[g2], g2, fu1, k6, gp);
+                add_face(P, FC[g2], g2, c, k6, gm);
+                int fu2[3] = {c2[0], c2[1], c2[2]};
+                fu2[g2] = c2[g2] + 1;
+                add_face(P, FC[g2], g2, fu2, -k6, gp);
+                add_face(P, FC[g2], g2, c2, -k6, gm);
+              }
+            }
+          }
+        }
+      }
+    free(W); free(S); free(AMl); free(APl);
+  }
+  /* conservative update */
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i)
+        for (int c = 0; c < m; ++c) {
+          double* qc = q + (size_t)c * nx * ny * nz + ((size_t)k * ny + j) * nx + i;
+          double upd = *qc;
+          for (int d = 0; d < 3; ++d) {
+            const int NXF = nx + (d == 0), NYF = ny + (d == 1);
+            int lo[3] = {i, j, k}, hi[3] = {i, j, k};
+            hi[d] += 1;
+            size_t ol = (((size_t)lo[2] * NYF + lo[1]) * NXF + lo[0]) * m + c;
+            size_t oh = (((size_t)hi[2] * NYF + hi[1]) * NXF + hi[0]) * m + c;
+            const double dtdn = dt / dxs[d];
+            upd = upd - dtdn * (AP[d][ol] + AM[d][oh]) - dtdn * (FC[d][oh] - FC[d][ol]);
+          }
+          *qc = upd;
+        }
+  double nu = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    double v = dt * smax[d] / dxs[d];
+    if (!(v <= nu)) nu = v;
+  }
+  *cfl = nu;
+  free(qb);
+  for (int e = 0; e < 3; ++e) { free(AM[e]); free(AP[e]); free(FC[e]); }
+  return ORC_OK;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -960,7 +1221,39 @@ int orc_sharp_step(const orc_prob* P, double* q, const double* aux, double dt, d
 /* CFL control (Sec. 5: check the Courant number, choose the next step)      */
 /* ------------------------------------------------------------------------ */
 
+static void max_speeds3(const orc_prob* P, const double* q, double* smax) {
+  const int nx = P->nx, ny = P->ny, nz = P->nz, m = P->num_eqn, nw = orc_num_waves(P->rp, 3);
+  const int n3[3] = {nx, ny, nz};
+  g3arr Q;
+  Q.m = m; Q.NX = nx + 4; Q.NY = ny + 4; Q.NZ = nz + 4;
+  double* qb = (double*)malloc(sizeof(double) * (size_t)m * Q.NX * Q.NY * Q.NZ);
+  fill_ghost3(P, q, qb);
+  Q.a = qb;
+  for (int d = 0; d < 3; ++d) {
+    smax[d] = 0.0;
+    const int e1 = (d + 1) % 3, e2 = (d + 2) % 3;
+    for (int a = 0; a < n3[e1]; ++a)
+      for (int b = 0; b < n3[e2]; ++b)
+        for (int i = 0; i <= n3[d]; ++i) {
+          int il[3], ir[3];
+          il[d] = i - 1; ir[d] = i;
+          il[e1] = ir[e1] = a;
+          il[e2] = ir[e2] = b;
+          double ql[MAXM], qr[MAXM], W[MAXW * MAXM], S[MAXW], am[MAXM], ap[MAXM];
+          g3cell(&Q, il[0], il[1], il[2], ql);
+          g3cell(&Q, ir[0], ir[1], ir[2], qr);
+          rp3(P, d, ql, qr, W, S, am, ap);
+          for (int p = 0; p < nw; ++p) {
+            double v = fabs(S[p]);
+            if (!(v <= smax[d])) smax[d] = v;
+          }
+        }
+  }
+  free(qb);
+}
+
 void orc_max_speeds(const orc_prob* P, const double* q, const double* aux, double* smax) {
+  if (P->ndim == 3) { max_speeds3(P, q, smax); return; }
   int m = P->num_eqn, ma = P->num_aux, nw = orc_num_waves(P->rp, P->ndim);
   int nx = P->nx, ny = (P->ndim == 2) ? P->ny : 1;
   garr Q, A;
@@ -1002,8 +1295,9 @@ static int all_finite(const double* q, size_t n) {
 
 int orc_evolve(const orc_prob* P, double* q, const double* aux, double t0, double t_end,
                int max_steps, orc_run_info* info) {
-  int ny = (P->ndim == 2) ? P->ny : 1;
-  size_t ntot = (size_t)P->nx * ny * P->num_eqn;
+  int ny = (P->ndim >= 2) ? P->ny : 1;
+  int nz = (P->ndim == 3) ? P->nz : 1;
+  size_t ntot = (size_t)P->nx * ny * nz * P->num_eqn;
   double* qold = (double*)malloc(sizeof(double) * ntot);
   double t = t0, dt;
   int steps = 0, rejects = 0, retries = 0, status = ORC_OK;
@@ -1011,10 +1305,11 @@ int orc_evolve(const orc_prob* P, double* q, const double* aux, double t0, doubl
   if (P->dt_initial > 0.0) {
     dt = P->dt_initial;
   } else {
-    double smax[2], rate = 0.0;
+    double smax[3], rate = 0.0;
+    const double dxs[3] = {P->dx, P->dy, P->dz};
     orc_max_speeds(P, q, aux, smax);
     for (int d = 0; d < P->ndim; ++d) {
-      double v = smax[d] / (d == 0 ? P->dx : P->dy);
+      double v = smax[d] / dxs[d];
       if (v > rate) rate = v;
     }
     dt = rate > 0.0 ? P->cfl_desired / rate : P->dt_max;
@@ -1064,9 +1359,11 @@ int orc_evolve(const orc_prob* P, double* q, const double* aux, double t0, doubl
 /* ------------------------------------------------------------------------ */
 
 void orc_totals(const orc_prob* P, const double* q, double* out) {
-  int ny = (P->ndim == 2) ? P->ny : 1;
-  size_t n = (size_t)P->nx * ny;
-  double dV = (P->ndim == 2) ? P->dx * P->dy : P->dx;
+  int ny = (P->ndim >= 2) ? P->ny : 1;
+  int nz = (P->ndim == 3) ? P->nz : 1;
+  size_t n = (size_t)P->nx * ny * nz;
+  double dV = (P->ndim == 3) ? P->dx * P->dy * P->dz
+                             : ((P->ndim == 2) ? P->dx * P->dy : P->dx);
   for (int k = 0; k < P->num_eqn; ++k) {
     double s = 0.0, c = 0.0;
     for (size_t i = 0; i < n; ++i) {

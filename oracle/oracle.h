@@ -12,7 +12,7 @@
  * fix; Ketcheson-Parsani-LeVeque for SharpClaw; Jiang-Shu WENO5; Shu-Osher
  * SSP-RK3; Einfeldt HLLE; Bale-LeVeque-Mitran-Rossmanith f-waves).
  *
- * Layout: q is field-major, interior cells only: q[m][ny][nx] (x fastest),
+ * Layout: q is field-major, interior cells only: q[m][nz][ny][nx] (x fastest),
  * matching PyClaw's q[m,i,j] field-major arrays (Sec. 4.2).  1D uses ny = 1.
  */
 #ifndef CLAW_ORACLE_H
@@ -36,7 +36,7 @@ enum { ORC_CLASSIC = 0, ORC_SHARPCLAW = 1 };
 enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ECFL = 5, ORC_ENONPHYSICAL = 6 };
 
 typedef struct {
-  int ndim;             /* 1 or 2 */
+  int ndim;             /* 1, 2 or 3 (3D: classic, advection and acoustics) */
   int nx, ny;           /* interior cells (ny = 1 in 1D) */
   double dx, dy;        /* cell widths */
   int rp;               /* ORC_RP_* */
@@ -47,12 +47,14 @@ typedef struct {
   int char_decomp;      /* SharpClaw: 0 component-wise, 1 characteristic-wise */
   int entropy_fix;      /* Harten-Hyman on Roe solvers */
   int num_eqn, num_aux, num_waves;
-  int bc_lo[2], bc_hi[2];
+  int bc_lo[3], bc_hi[3];
   double inflow[8];     /* fixed ghost state for ORC_BC_INFLOW */
   double params[8];     /* advection: u,v | acoustics: rho,K | SW: g | Euler: gamma */
   double cfl_desired, cfl_max, dt_initial, dt_max;
   int max_retries;
   double weno_eps;      /* WENO5 epsilon (Jiang-Shu) */
+  int nz;               /* 3D: cells in z (1 otherwise) */
+  double dz;            /* 3D: cell width in z */
 } orc_prob;
 
 typedef struct {

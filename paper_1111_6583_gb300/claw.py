@@ -184,7 +184,7 @@ def method_from_spec(spec, prec="fp64") -> claw_method:
     m.lim = LIM[spec.get("lim", "mc")]
     m.prec = FP32 if prec in ("fp32", FP32) else FP64
     m.order = int(spec.get("order", 2))
-    m.transverse = int(spec.get("transverse", 2)) if ndim == 2 else 0
+    m.transverse = int(spec.get("transverse", 2)) if ndim >= 2 else 0
     m.char_decomp = int(spec.get("char_decomp", 0))
     m.entropy_fix = int(spec.get("entropy_fix", 1))
     m.max_retries = int(spec.get("max_retries", 8))

@@ -62,7 +62,7 @@ void fill_consts(const claw_method& m, MConsts<R>& C) {
   C.transverse = m.transverse;
   C.entropy_fix = m.entropy_fix;
   C.char_decomp = m.char_decomp;
-  for (int d = 0; d < 2; ++d) {
+  for (int d = 0; d < 3; ++d) {
     C.bc_lo[d] = m.bc_lower[d];
     C.bc_hi[d] = m.bc_upper[d];
   }
@@ -84,9 +84,9 @@ int num_eqn(int rp, int nd) {
   switch (rp) {
     case CLAW_RP_ADVECTION: return 1;
     case CLAW_RP_ACOUSTICS: return nd + 1;
-    case CLAW_RP_SW_ROE: return nd + 1;
+    case CLAW_RP_SW_ROE: return nd <= 2 ? nd + 1 : 0;
     case CLAW_RP_EULER_ROE:
-    case CLAW_RP_EULER_HLLE: return nd + 2;
+    case CLAW_RP_EULER_HLLE: return nd <= 2 ? nd + 2 : 0;
     case CLAW_RP_ELASTICITY_FWAVE: return nd == 1 ? 2 : 0;
   }
   return 0;
@@ -94,7 +94,8 @@ int num_eqn(int rp, int nd) {
 
 // validate a method against a dimension; returns an error message or nullptr
 const char* check_method(const claw_method& m, int nd) {
-  if (nd != 1 && nd != 2) return "ndim must be 1 or 2";
+  if (nd < 1 || nd > 3) return "ndim must be 1, 2 or 3";
+  if (nd == 3 && m.scheme != CLAW_CLASSIC) return "3D grids use the classic scheme";
   if (m.rp < 0 || m.rp > 5) return "unknown Riemann solver";
   if (num_eqn(m.rp, nd) == 0) return "solver not available in this dimension";
   if (m.num_eqn != num_eqn(m.rp, nd)) return "num_eqn does not match the Riemann solver";
@@ -126,7 +127,7 @@ const char* check_method(const claw_method& m, int nd) {
 }
 
 const char* check_grid(const claw_grid& g) {
-  if (g.ndim != 1 && g.ndim != 2) return "ndim must be 1 or 2";
+  if (g.ndim < 1 || g.ndim > 3) return "ndim must be 1, 2 or 3";
   for (int d = 0; d < g.ndim; ++d) {
     if (g.n[d] < 4) return "each direction needs at least 4 cells";
     if (g.n[d] > (int64_t)INT_MAX / 2) return "too many cells in one direction";
@@ -155,7 +156,8 @@ DevCtl make_ctl(const claw_method& m, const claw_grid& g, int nbuf, double t0, d
   c.cfl_desired = m.cfl_desired;
   c.cfl_max = m.cfl_max;
   c.dx[0] = (g.upper[0] - g.lower[0]) / (double)g.n[0];
-  c.dx[1] = g.ndim == 2 ? (g.upper[1] - g.lower[1]) / (double)g.n[1] : 1.0;
+  c.dx[1] = g.ndim >= 2 ? (g.upper[1] - g.lower[1]) / (double)g.n[1] : 1.0;
+  c.dx[2] = g.ndim == 3 ? (g.upper[2] - g.lower[2]) / (double)g.n[2] : 1.0;
   c.dt_init = m.dt_initial;
   c.max_steps = LLONG_MAX;
   c.nbuf = nbuf;
@@ -165,15 +167,16 @@ DevCtl make_ctl(const claw_method& m, const claw_grid& g, int nbuf, double t0, d
   return c;
 }
 
+size_t cells_of(const claw_grid& g) {
+  return (size_t)g.n[0] * (g.ndim >= 2 ? (size_t)g.n[1] : 1) * (g.ndim == 3 ? (size_t)g.n[2] : 1);
+}
 size_t state_bytes_of(const claw_method& m, const claw_grid& g) {
   const size_t es = m.prec == CLAW_FP64 ? 8 : 4;
-  size_t cells = (size_t)g.n[0] * (g.ndim == 2 ? (size_t)g.n[1] : 1);
-  return cells * m.num_eqn * es;
+  return cells_of(g) * m.num_eqn * es;
 }
 size_t aux_bytes_of(const claw_method& m, const claw_grid& g) {
   const size_t es = m.prec == CLAW_FP64 ? 8 : 4;
-  size_t cells = (size_t)g.n[0] * (g.ndim == 2 ? (size_t)g.n[1] : 1);
-  return cells * m.num_aux * es;
+  return cells_of(g) * m.num_aux * es;
 }
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -238,6 +241,8 @@ struct claw_solver {
   int npart = 0;
   int ntiles = 0, bw = 128, h = 32;
   int tuned = 0;
+  void* work3 = nullptr;  // 3D per-face arrays
+  size_t work3_bytes = 0;
   cudaGraphExec_t gexec = nullptr;
   int gk = 0;
   int bound = 0;
@@ -277,6 +282,11 @@ cudaError_t leave(claw_solver* s) {
 }
 
 cudaError_t solver_attempt(claw_solver* s, cudaStream_t st) {
+  if (s->nd == 3) {
+    LaunchArgs a{s->d_mem, nullptr, s->ntiles, s->consts.data(), 0, 0, 0, st,
+                 {(int)s->g.n[0], (int)s->g.n[1], (int)s->g.n[2]}, s->work3, s->work3_bytes};
+    return s->ks.classic(a);
+  }
   return launch_attempt(s->ks, s->m.scheme, s->d_mem, nullptr, s->ntiles, s->consts.data(), s->bw,
                         s->h, st);
 }
@@ -381,6 +391,8 @@ cudaError_t autotune(claw_solver* s) {
 void free_bound(claw_solver* s) {
   drop_graph(s);
   if (s->work) cudaFree(s->work);
+  if (s->work3) cudaFree(s->work3);
+  s->work3 = nullptr;
   if (s->d_ctl) cudaFree(s->d_ctl);
   if (s->d_mem) cudaFree(s->d_mem);
   if (s->d_ctl_tune) cudaFree(s->d_ctl_tune);
@@ -417,8 +429,8 @@ extern "C" {
 claw_status claw_method_init(claw_method* m, int rp, int ndim) {
   if (!m) return CLAW_EINVAL;
   std::memset(m, 0, sizeof(*m));
-  if (ndim != 1 && ndim != 2) {
-    g_err = "ndim must be 1 or 2";
+  if (ndim < 1 || ndim > 3) {
+    g_err = "ndim must be 1, 2 or 3";
     return CLAW_EINVAL;
   }
   if (rp < 0 || rp > 5 || num_eqn(rp, ndim) == 0) {
@@ -430,7 +442,7 @@ claw_status claw_method_init(claw_method* m, int rp, int ndim) {
   m->lim = CLAW_LIM_MC;
   m->prec = CLAW_FP64;
   m->order = 2;
-  m->transverse = ndim == 2 ? 2 : 0;
+  m->transverse = ndim >= 2 ? 2 : 0;
   m->weno_order = 5;
   m->char_decomp = rp == CLAW_RP_ELASTICITY_FWAVE ? 0 : 1;
   m->entropy_fix = 1;
@@ -466,6 +478,7 @@ claw_status claw_solver_create(const claw_method* m, const claw_grid* g, void* s
   s->m = *m;
   s->g = *g;
   if (g->ndim == 1) s->g.n[1] = 1;
+  if (g->ndim <= 2) s->g.n[2] = 1;
   s->nd = g->ndim;
   s->prec = m->prec;
   s->nbuf = m->scheme == CLAW_SHARPCLAW ? 3 : 2;
@@ -486,7 +499,9 @@ claw_status claw_solver_create(const claw_method* m, const claw_grid* g, void* s
     claw_solver_destroy(s);
     return st;
   }
-  s->ntiles = tiles_of(m->scheme, s->nd, s->prec, (int)s->g.n[0], (int)s->g.n[1], s->bw, s->h);
+  s->ntiles = s->nd == 3 ? (int)((cells_of(s->g) + 255) / 256)
+                         : tiles_of(m->scheme, s->nd, s->prec, (int)s->g.n[0], (int)s->g.n[1],
+                                    s->bw, s->h);
   *out = s;
   return CLAW_OK;
 }
@@ -499,10 +514,15 @@ claw_status claw_bind_state(claw_solver* s, void* q_dev, const void* aux_dev, do
   s->q_user = q_dev;
   s->aux = aux_dev;
   SCK(cudaMalloc(&s->work, s->sbytes * (s->nbuf - 1)));
+  if (s->nd == 3) {
+    s->work3_bytes = classic3d_work_bytes((int)s->g.n[0], (int)s->g.n[1], (int)s->g.n[2],
+                                          s->m.num_eqn, s->prec);
+    SCK(cudaMalloc(&s->work3, s->work3_bytes));
+  }
   SCK(cudaMalloc(&s->d_ctl, sizeof(DevCtl)));
   SCK(cudaMalloc(&s->d_mem, sizeof(Member)));
   SCK(cudaMallocHost(&s->h_ctl, sizeof(DevCtl)));
-  const long long ncell = (long long)s->g.n[0] * s->g.n[1];
+  const long long ncell = (long long)cells_of(s->g);
   s->npart = (int)std::min<long long>(1024, (ncell + kTotalsThreads - 1) / kTotalsThreads);
   SCK(cudaMalloc(&s->d_part, sizeof(double) * 2 * s->npart * s->m.num_eqn));
   SCK(cudaMallocHost(&s->h_part, sizeof(double) * 2 * s->npart * s->m.num_eqn));
@@ -513,6 +533,8 @@ claw_status claw_bind_state(claw_solver* s, void* q_dev, const void* aux_dev, do
   s->h_mem.aux = aux_dev;
   s->h_mem.nx = (int)s->g.n[0];
   s->h_mem.ny = (int)s->g.n[1];
+  s->h_mem.nz = (int)s->g.n[2];
+  s->h_mem.work3 = s->work3;
   s->h_mem.ctl = s->d_ctl;
   DevCtl c = make_ctl(s->m, s->g, s->nbuf, t0, INFINITY);
   SCK(enter(s));
@@ -520,7 +542,7 @@ claw_status claw_bind_state(claw_solver* s, void* q_dev, const void* aux_dev, do
   SCK(upload_member(s));
   // first dt from the wave speeds of Q^0 (or dt_initial)
   LaunchArgs a{s->d_mem, nullptr, maxspeed_tiles(s->h_mem.nx, s->h_mem.ny), s->consts.data(), 0,
-               0, 0, s->st};
+               0, 0, s->st, {(int)s->g.n[0], (int)s->g.n[1], (int)s->g.n[2]}, nullptr, 0};
   SCK(s->ks.maxspeed(a));
   SCK(launch_dt_init(s->d_ctl, 1, s->st));
   SCK(leave(s));
@@ -539,7 +561,9 @@ claw_status claw_solver_tune(claw_solver* s, int mode, int* bw, int* h) {
     if (!bw || !h || (*bw != 64 && *bw != 128) || *h < 1) return fail(s, "bad tile shape");
     s->bw = *bw;
     s->h = *h;
-    s->ntiles = tiles_of(s->m.scheme, s->nd, s->prec, (int)s->g.n[0], (int)s->g.n[1], s->bw, s->h);
+    if (s->nd != 3)
+      s->ntiles = tiles_of(s->m.scheme, s->nd, s->prec, (int)s->g.n[0], (int)s->g.n[1], s->bw,
+                           s->h);
     s->tuned = 1;
     drop_graph(s);
     SCK(enter(s));
@@ -656,14 +680,15 @@ claw_status claw_conserved_totals(claw_solver* s, double* out) {
   SCK(enter(s));
   SCK(read_ctl(s));
   const void* q = s->h_mem.q[s->h_ctl->cur];
-  const long long ncell = (long long)s->g.n[0] * s->g.n[1];
+  const long long ncell = (long long)cells_of(s->g);
   const int M = s->m.num_eqn;
   SCK(launch_totals(q, s->prec, ncell, M, s->d_part, s->npart, s->st));
   SCK(cudaMemcpyAsync(s->h_part, s->d_part, sizeof(double) * 2 * s->npart * M,
                       cudaMemcpyDeviceToHost, s->st));
   SCK(cudaStreamSynchronize(s->st));
   SCK(leave(s));
-  const double dV = s->nd == 2 ? s->h_ctl->dx[0] * s->h_ctl->dx[1] : s->h_ctl->dx[0];
+  double dV = s->h_ctl->dx[0];
+  for (int d = 1; d < s->nd; ++d) dV *= s->h_ctl->dx[d];
   for (int k = 0; k < M; ++k) {
     double sum = 0.0, comp = 0.0;
     for (int b = 0; b < s->npart; ++b) {
@@ -849,6 +874,7 @@ claw_status claw_batch_create(const claw_method* m, const claw_grid* grids, int 
   if (!m || !grids || !out || n <= 0) return bfail(nullptr, "bad argument");
   *out = nullptr;
   const int nd = grids[0].ndim;
+  if (nd == 3) return bfail(nullptr, "batches take 1D or 2D grids");
   for (int k = 0; k < n; ++k) {
     if (const char* why = check_grid(grids[k])) return bfail(nullptr, why);
     if (grids[k].ndim != nd) return bfail(nullptr, "all members need the same ndim");

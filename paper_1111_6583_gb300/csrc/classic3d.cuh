@@ -1,0 +1,363 @@
+// classic3d.cuh -- 3D unsplit Clawpack-classic step (LeVeque 1997): normal
+// solves, limited corrections, transverse and double-transverse propagation,
+// for scalar advection and linear acoustics.
+//
+// One attempt = a zero fill of the per-face arrays, three face sweeps (one per
+// direction; a thread per face, its limiter neighbours solved again in the
+// thread) that accumulate fluctuations and correction fluxes on the faces of
+// interior cells, and an update kernel whose last block runs the controller.
+// Transverse pieces: a fluctuation a that enters cell c across a d-face adds
+// -dt/(2 dx_d) E^+-a to the e-faces of c; the part E^+-a has moved on into
+// cell c +- e, so its third-direction split F^+-E^+-a moves 1/6 (dt/dx_d)
+// (dt/dx_e) of flux correction from the f-faces of c to those of c +- e
+// (six orderings of the directions give the corner-transport-upwind term).
+#pragma once
+
+#include "riemann.cuh"
+
+namespace claw {
+
+// cell (i, j, k) of q[M][nz][ny][nx] with ghost remap: x rule, then y rule on
+// the x-remapped value, then z rule (corners defined as x, y, z fills in turn)
+template <int M, typename R>
+__device__ __forceinline__ void load_cell3(const MConsts<R>& C, const R* __restrict__ q, int nx,
+                                           int ny, int nz, int i, int j, int k, int wall0,
+                                           int wall1, int wall2, R (&out)[M]) {
+  int fz, iz, fy, iy, fx, ix;
+  const int kk = bc_map(k, nz, C.bc_lo[2], C.bc_hi[2], fz, iz);
+  const int jj = bc_map(j, ny, C.bc_lo[1], C.bc_hi[1], fy, iy);
+  const int ii = bc_map(i, nx, C.bc_lo[0], C.bc_hi[0], fx, ix);
+  if (iz || iy || ix) {
+    // an inflow rule at any level replaces the value below it
+#pragma unroll
+    for (int c = 0; c < M; ++c) out[c] = C.inflow[c];
+    if (iz) return;
+    if (iy) {
+#pragma unroll
+      for (int c = 0; c < M; ++c)
+        if (fz && c == wall2) out[c] = -out[c];
+      return;
+    }
+  } else {
+    const size_t plane = (size_t)nx * ny * nz;
+    const size_t off = ((size_t)kk * ny + jj) * nx + ii;
+#pragma unroll
+    for (int c = 0; c < M; ++c) out[c] = __ldg(q + c * plane + off);
+#pragma unroll
+    for (int c = 0; c < M; ++c)
+      if (fx && c == wall0) out[c] = -out[c];
+  }
+#pragma unroll
+  for (int c = 0; c < M; ++c) {
+    if (fy && c == wall1) out[c] = -out[c];
+    if (fz && c == wall2) out[c] = -out[c];
+  }
+}
+
+// 3D transverse split in direction E of a fluctuation a
+template <class RP, typename R, int E>
+struct Trans3;
+
+template <typename R, int E>
+struct Trans3<RpAdvection<R, 3>, R, E> {
+  __device__ static __forceinline__ void split(const MConsts<R>& C, const R (&a)[1], R (&em)[1],
+                                               R (&ep)[1]) {
+    const R v = C.p[E];
+    em[0] = fmin(v, R(0)) * a[0];
+    ep[0] = fmax(v, R(0)) * a[0];
+  }
+};
+
+template <typename R, int E>
+struct Trans3<RpAcoustics<R, 3>, R, E> {
+  __device__ static __forceinline__ void split(const MConsts<R>& C, const R (&a)[4], R (&em)[4],
+                                               R (&ep)[4]) {
+    constexpr int e = 1 + E;
+    const R Z = C.aco_Z, c = C.aco_c, h = C.aco_h;
+    const R b1 = (Z * a[e] - a[0]) * h;
+    const R b2 = (Z * a[e] + a[0]) * h;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      em[k] = R(0);
+      ep[k] = R(0);
+    }
+    em[0] = c * Z * b1;
+    em[e] = -c * b1;
+    ep[0] = c * Z * b2;
+    ep[e] = c * b2;
+  }
+};
+
+// per-face arrays: for direction d, faces (nx+[d==0]) x (ny+[d==1]) x (nz+[d==2]),
+// each with M values of A^-dQ, A^+dQ and the total correction flux
+struct Faces3 {
+  size_t n[3];       // faces per direction
+  size_t off_am[3], off_ap[3], off_fc[3];  // element offsets into the work array
+};
+
+__host__ __device__ inline void faces3_layout(int nx, int ny, int nz, int M, Faces3& f) {
+  size_t o = 0;
+  for (int d = 0; d < 3; ++d) {
+    f.n[d] = (size_t)(nx + (d == 0)) * (ny + (d == 1)) * (nz + (d == 2));
+    f.off_am[d] = o;
+    o += f.n[d] * M;
+    f.off_ap[d] = o;
+    o += f.n[d] * M;
+    f.off_fc[d] = o;
+    o += f.n[d] * M;
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ size_t face_index(int e, int nx, int ny, const int (&f)[3]) {
+  const int NXF = nx + (e == 0), NYF = ny + (e == 1);
+  return ((size_t)f[2] * NYF + f[1]) * NXF + f[0];
+}
+
+// add coef * v to the correction flux of face f in direction e when it bounds an
+// interior cell
+template <int M, typename R>
+__device__ __forceinline__ void add_fc(R* __restrict__ work, const Faces3& L, int e, int nx,
+                                       int ny, int nz, const int (&f)[3], R coef,
+                                       const R (&v)[M]) {
+  const int n3[3] = {nx, ny, nz};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int hi = (d == e) ? n3[d] : n3[d] - 1;
+    if (f[d] < 0 || f[d] > hi) return;
+  }
+  const size_t fi = face_index<R>(e, nx, ny, f);
+  R* base = work + L.off_fc[e] + fi * M;
+#pragma unroll
+  for (int c = 0; c < M; ++c) atomicAdd(base + c, coef * v[c]);
+}
+
+template <class RP, typename R, int D>
+__global__ void __launch_bounds__(256)
+    classic3d_sweep(const Member* __restrict__ members, const MConsts<R> C) {
+  constexpr int M = RP::M, MW = RP::MW;
+  constexpr int E1 = (D + 1) % 3, E2 = (D + 2) % 3;
+  const Member& mb = members[0];
+  DevCtl* ctl = mb.ctl;
+  __shared__ int s_done, s_cur;
+  __shared__ R s_k[3];  // dt/dx_d for d = 0, 1, 2
+  if (threadIdx.x == 0) {
+    s_done = ctl->done;
+    s_cur = ctl->cur;
+    for (int d = 0; d < 3; ++d) s_k[d] = (R)(ctl->dt / ctl->dx[d]);
+  }
+  __syncthreads();
+  if (s_done) return;
+  const int nx = mb.nx, ny = mb.ny, nz = mb.nz;
+  const int n3[3] = {nx, ny, nz};
+  const int nd = n3[D], ne1 = n3[E1], ne2 = n3[E2];
+  // faces i = 0..nd in D, lines a = -1..ne1, b = -1..ne2
+  const long long total = (long long)(nd + 1) * (ne1 + 2) * (ne2 + 2);
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  R smax = R(0);
+  if (id < total) {
+    const int i = (int)(id % (nd + 1));
+    const int a = (int)((id / (nd + 1)) % (ne1 + 2)) - 1;
+    const int b = (int)(id / ((long long)(nd + 1) * (ne1 + 2))) - 1;
+    const R* __restrict__ q = (const R*)mb.q[s_cur];
+    R* __restrict__ work = (R*)mb.work3;
+    Faces3 L;
+    faces3_layout(nx, ny, nz, M, L);
+    const R dtdn = s_k[D];
+    // cells i-2 .. i+1 along D on line (a, b)
+    R cell[4][M];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      int c3[3];
+      c3[D] = i - 2 + t;
+      c3[E1] = a;
+      c3[E2] = b;
+      load_cell3<M, R>(C, q, nx, ny, nz, c3[0], c3[1], c3[2], RP::WALL_X, 2, 3, cell[t]);
+    }
+    // faces i-1, i, i+1 (solves of cell pairs (t, t+1))
+    R W[3][MW][M], s[3][MW], am[M], ap[M];
+    {
+      R x[RP::NCTX], amt[M], apt[M];
+      RP::template solve<D>(C, cell[0], cell[1], nullptr, nullptr, W[0], s[0], amt, apt, x);
+      RP::template solve<D>(C, cell[1], cell[2], nullptr, nullptr, W[1], s[1], am, ap, x);
+      RP::template solve<D>(C, cell[2], cell[3], nullptr, nullptr, W[2], s[2], amt, apt, x);
+    }
+    // (cell[2] is cell i, cell[1] is cell i-1: face i solved into W[1])
+    const bool interior_line = a >= 0 && a < ne1 && b >= 0 && b < ne2;
+    if (interior_line) {
+#pragma unroll
+      for (int p = 0; p < MW; ++p) smax = nanmax(smax, (R)fabs(s[1][p]));
+    }
+    R F[M];
+    if (C.order == 2) {
+      R dot[MW], nrm[MW];
+#pragma unroll
+      for (int p = 0; p < MW; ++p) {
+        R d_ = R(0), n2 = R(0);
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+          const R up = s[1][p] > R(0) ? W[0][p][c] : W[2][p][c];
+          d_ += up * W[1][p][c];
+          n2 += W[1][p][c] * W[1][p][c];
+        }
+        dot[p] = d_;
+        nrm[p] = n2;
+      }
+      correction<RP, R>(C, W[1], s[1], dot, nrm, dtdn, F);
+    } else {
+#pragma unroll
+      for (int c = 0; c < M; ++c) F[c] = R(0);
+    }
+    int f[3];
+    f[D] = i;
+    f[E1] = a;
+    f[E2] = b;
+    if (interior_line) {
+      const size_t fi = face_index<R>(D, nx, ny, f);
+#pragma unroll
+      for (int c = 0; c < M; ++c) {
+        work[L.off_am[D] + fi * M + c] = am[c];
+        work[L.off_ap[D] + fi * M + c] = ap[c];
+      }
+      add_fc<M, R>(work, L, D, nx, ny, nz, f, R(1), F);
+    }
+    if (C.transverse) {
+      R apq[M], amq[M];
+#pragma unroll
+      for (int c = 0; c < M; ++c) {
+        apq[c] = ap[c] - (C.transverse == 2 ? F[c] : R(0));
+        amq[c] = am[c] + (C.transverse == 2 ? F[c] : R(0));
+      }
+#pragma unroll
+      for (int side = 0; side < 2; ++side) {
+        const R(&av)[M] = side == 0 ? apq : amq;
+        int c0[3];
+        c0[D] = side == 0 ? i : i - 1;
+        c0[E1] = a;
+        c0[E2] = b;
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          // transverse direction e and third direction g
+          R em[M], ep[M];
+          if (t == 0) Trans3<RP, R, E1>::split(C, av, em, ep);
+          else Trans3<RP, R, E2>::split(C, av, em, ep);
+          const int e = t == 0 ? E1 : E2;
+          int fu[3] = {c0[0], c0[1], c0[2]};
+          fu[e] = c0[e] + 1;
+          add_fc<M, R>(work, L, e, nx, ny, nz, fu, R(-0.5) * dtdn, ep);
+          add_fc<M, R>(work, L, e, nx, ny, nz, c0, R(-0.5) * dtdn, em);
+          const R dte = s_k[e];
+#pragma unroll
+          for (int sg = 0; sg < 2; ++sg) {
+            const R(&bv)[M] = sg == 0 ? ep : em;
+            const R k6 = (sg == 0 ? R(1) : R(-1)) * dtdn * dte * (R(1) / R(6));
+            R gm[M], gp[M];
+            const int g = t == 0 ? E2 : E1;
+            if (t == 0) Trans3<RP, R, E2>::split(C, bv, gm, gp);
+            else Trans3<RP, R, E1>::split(C, bv, gm, gp);
+            int c2[3] = {c0[0], c0[1], c0[2]};
+            c2[e] += sg == 0 ? 1 : -1;
+            int fu1[3] = {c0[0], c0[1], c0[2]};
+            fu1[g] = c0[g] + 1;
+            add_fc<M, R>(work, L, g, nx, ny, nz, fu1, k6, gp);
+            add_fc<M, R>(work, L, g, nx, ny, nz, c0, k6, gm);
+            int fu2[3] = {c2[0], c2[1], c2[2]};
+            fu2[g] = c2[g] + 1;
+            add_fc<M, R>(work, L, g, nx, ny, nz, fu2, -k6, gp);
+            add_fc<M, R>(work, L, g, nx, ny, nz, c2, -k6, gm);
+          }
+        }
+      }
+    }
+  }
+  R sx = D == 0 ? smax : R(0), sy = D == 1 ? smax : R(0), sz = D == 2 ? smax : R(0);
+  finish_attempt<R>(ctl, sx, sy, 0, 0, false, sz);
+}
+
+template <class RP, typename R>
+__global__ void __launch_bounds__(256)
+    classic3d_update(const Member* __restrict__ members, const MConsts<R> C) {
+  constexpr int M = RP::M;
+  const Member& mb = members[0];
+  DevCtl* ctl = mb.ctl;
+  __shared__ int s_done, s_cur, s_nbuf;
+  __shared__ R s_k[3];
+  if (threadIdx.x == 0) {
+    s_done = ctl->done;
+    s_cur = ctl->cur;
+    s_nbuf = ctl->nbuf;
+    for (int d = 0; d < 3; ++d) s_k[d] = (R)(ctl->dt / ctl->dx[d]);
+  }
+  __syncthreads();
+  if (s_done) return;
+  const int nx = mb.nx, ny = mb.ny, nz = mb.nz;
+  const long long ncell = (long long)nx * ny * nz;
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  int bad = 0;
+  if (id < ncell) {
+    const int i = (int)(id % nx), j = (int)((id / nx) % ny), k = (int)(id / ((long long)nx * ny));
+    const R* __restrict__ q = (const R*)mb.q[s_cur];
+    R* __restrict__ qo = (R*)mb.q[(s_cur + 1) % s_nbuf];
+    const R* __restrict__ work = (const R*)mb.work3;
+    Faces3 L;
+    faces3_layout(nx, ny, nz, M, L);
+    R v[M];
+#pragma unroll
+    for (int c = 0; c < M; ++c) v[c] = q[(size_t)c * ncell + id];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      int lo[3] = {i, j, k}, hi[3] = {i, j, k};
+      hi[d] += 1;
+      const size_t fl = face_index<R>(d, nx, ny, lo), fh = face_index<R>(d, nx, ny, hi);
+      const R dtdn = s_k[d];
+#pragma unroll
+      for (int c = 0; c < M; ++c) {
+        v[c] = v[c] - dtdn * (work[L.off_ap[d] + fl * M + c] + work[L.off_am[d] + fh * M + c]) -
+               dtdn * (work[L.off_fc[d] + fh * M + c] - work[L.off_fc[d] + fl * M + c]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+      bad |= !isfinite(v[c]);
+      qo[(size_t)c * ncell + id] = v[c];
+    }
+  }
+  finish_attempt<R>(ctl, R(0), R(0), bad, mb.ntiles, true, R(0));
+}
+
+template <class RP, typename R>
+__global__ void __launch_bounds__(256)
+    maxspeed3_kernel(const Member* __restrict__ members, const MConsts<R> C) {
+  constexpr int M = RP::M, MW = RP::MW;
+  const Member& mb = members[0];
+  DevCtl* ctl = mb.ctl;
+  const int nx = mb.nx, ny = mb.ny, nz = mb.nz;
+  const long long ncell = (long long)nx * ny * nz;
+  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  R sm[3] = {R(0), R(0), R(0)};
+  if (id < ncell) {
+    const int i = (int)(id % nx), j = (int)((id / nx) % ny), k = (int)(id / ((long long)nx * ny));
+    const R* q = (const R*)mb.q[ctl->cur];
+    const int c3[3] = {i, j, k};
+    const int n3[3] = {nx, ny, nz};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      for (int side = 0; side < (c3[d] == n3[d] - 1 ? 2 : 1); ++side) {
+        int l[3] = {i, j, k}, r[3] = {i, j, k};
+        l[d] += side - 1;
+        r[d] += side;
+        R a[M], b[M], W[MW][M], s[MW], am[M], ap[M], x[RP::NCTX];
+        load_cell3<M, R>(C, q, nx, ny, nz, l[0], l[1], l[2], RP::WALL_X, 2, 3, a);
+        load_cell3<M, R>(C, q, nx, ny, nz, r[0], r[1], r[2], RP::WALL_X, 2, 3, b);
+        if (d == 0) RP::template solve<0>(C, a, b, nullptr, nullptr, W, s, am, ap, x);
+        else if (d == 1) RP::template solve<1>(C, a, b, nullptr, nullptr, W, s, am, ap, x);
+        else RP::template solve<2>(C, a, b, nullptr, nullptr, W, s, am, ap, x);
+#pragma unroll
+        for (int p = 0; p < MW; ++p) sm[d] = nanmax(sm[d], (R)fabs(s[p]));
+      }
+    }
+  }
+  finish_attempt<R>(ctl, sm[0], sm[1], 0, 0, false, sm[2]);
+}
+
+}  // namespace claw

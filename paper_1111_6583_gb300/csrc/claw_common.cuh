@@ -24,9 +24,9 @@ struct DevCtl {
   double t, dt, t_end, dt_max;
   double cfl_desired, cfl_max;
   double nu_last, nu_max_seen, dt_used;
-  double dx[2];
+  double dx[3];
   double dt_init;   // first dt (<= 0: from the wave speeds of Q^0)
-  unsigned long long smax[2];  // bit patterns of max |s| per direction (non-negative)
+  unsigned long long smax[3];  // bit patterns of max |s| per direction (non-negative)
   long long steps, rejects, max_steps;
   int cur;          // buffer holding Q^n
   int nbuf;         // 2 (classic) or 3 (SharpClaw)
@@ -48,8 +48,9 @@ struct Member {
   const void* aux;   // cell aux fields or nullptr
   int nx, ny;        // interior cells (ny = 1 in 1D)
   int ntiles;        // blocks of this member per attempt
-  int pad;
+  int nz;            // 3D: cells in z (1 otherwise)
   DevCtl* ctl;
+  void* work3;       // 3D: per-face fluctuation / correction arrays
 };
 
 // Work item of a batched launch: (member, tile index within the member).
@@ -68,7 +69,7 @@ struct MConsts {
   R gamma, gm1;    // Euler
   R weno_eps;
   int lim, order, transverse, entropy_fix, char_decomp;
-  int bc_lo[2], bc_hi[2];
+  int bc_lo[3], bc_hi[3];
 };
 
 // ---------------------------------------------------------------------------
@@ -169,18 +170,17 @@ static __device__ __noinline__ void run_controller(DevCtl* c) {
   if (c->dry) {
     c->smax[0] = 0ull;
     c->smax[1] = 0ull;
+    c->smax[2] = 0ull;
     c->bad = 0u;
     __threadfence();
     c->arrive = 0u;
     return;
   }
-  const double smx = __longlong_as_double((long long)atomicOr(&c->smax[0], 0ull));
-  const double smy = __longlong_as_double((long long)atomicOr(&c->smax[1], 0ull));
   const unsigned bad = atomicOr(&c->bad, 0u);
   const double dt = c->dt;
-  double nu = dt * smx / c->dx[0];
-  if (c->ndim == 2) {
-    const double v = dt * smy / c->dx[1];
+  double nu = dt * __longlong_as_double((long long)atomicOr(&c->smax[0], 0ull)) / c->dx[0];
+  for (int d = 1; d < c->ndim; ++d) {
+    const double v = dt * __longlong_as_double((long long)atomicOr(&c->smax[d], 0ull)) / c->dx[d];
     nu = (nu >= v || isnan(nu)) ? nu : v;
   }
   c->accepted = 0;
@@ -217,6 +217,7 @@ static __device__ __noinline__ void run_controller(DevCtl* c) {
   }
   c->smax[0] = 0ull;
   c->smax[1] = 0ull;
+  c->smax[2] = 0ull;
   c->bad = 0u;
   __threadfence();
   c->arrive = 0u;
@@ -229,8 +230,8 @@ static __device__ __noinline__ void run_controller(DevCtl* c) {
 // must be a multiple of 32 and at most 1024.
 template <typename T>
 static __device__ __forceinline__ void finish_attempt(DevCtl* ctl, T sx, T sy, int bad, int ntiles,
-                                                      bool run_ctl) {
-  __shared__ T red_x[32], red_y[32];
+                                                      bool run_ctl, T sz = T(0)) {
+  __shared__ T red_x[32], red_y[32], red_z[32];
   __shared__ int red_bad;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) red_bad = 0;
@@ -238,27 +239,32 @@ static __device__ __forceinline__ void finish_attempt(DevCtl* ctl, T sx, T sy, i
   for (int o = 16; o > 0; o >>= 1) {
     sx = nanmax(sx, __shfl_xor_sync(0xffffffffu, sx, o));
     sy = nanmax(sy, __shfl_xor_sync(0xffffffffu, sy, o));
+    sz = nanmax(sz, __shfl_xor_sync(0xffffffffu, sz, o));
   }
   __syncthreads();
   if (bad) atomicOr(&red_bad, 1);
   if (lane == 0) {
     red_x[warp] = sx;
     red_y[warp] = sy;
+    red_z[warp] = sz;
   }
   __syncthreads();
   if (warp == 0) {
     const int nw = blockDim.x >> 5;
     T a = lane < nw ? red_x[lane] : T(0);
     T b = lane < nw ? red_y[lane] : T(0);
+    T z = lane < nw ? red_z[lane] : T(0);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       a = nanmax(a, __shfl_xor_sync(0xffffffffu, a, o));
       b = nanmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+      z = nanmax(z, __shfl_xor_sync(0xffffffffu, z, o));
     }
     if (lane == 0) {
-      const double ad = (double)a, bd = (double)b;
+      const double ad = (double)a, bd = (double)b, zd = (double)z;
       if (ad != 0.0) atomicMax(&ctl->smax[0], (unsigned long long)__double_as_longlong(ad));
       if (bd != 0.0) atomicMax(&ctl->smax[1], (unsigned long long)__double_as_longlong(bd));
+      if (zd != 0.0) atomicMax(&ctl->smax[2], (unsigned long long)__double_as_longlong(zd));
       if (red_bad) atomicOr(&ctl->bad, 1u);
       if (run_ctl) {
         __threadfence();

@@ -8,6 +8,8 @@ KernelSet claw_kernels_acoustics(int nd, int prec) {
   if (nd == 1 && prec == 1) return make_set<RpAcoustics, 1, float>(true);
   if (nd == 2 && prec == 0) return make_set<RpAcoustics, 2, double>(true);
   if (nd == 2 && prec == 1) return make_set<RpAcoustics, 2, float>(true);
+  if (nd == 3 && prec == 0) return make_set<RpAcoustics, 3, double>(false);
+  if (nd == 3 && prec == 1) return make_set<RpAcoustics, 3, float>(false);
   return KernelSet{};
 }
 

@@ -27,6 +27,7 @@ __global__ void dt_init_kernel(DevCtl* ctls, int n) {
   c->dt = dt;
   c->smax[0] = 0ull;
   c->smax[1] = 0ull;
+  c->smax[2] = 0ull;
   c->bad = 0u;
   c->arrive = 0u;
 }

@@ -21,6 +21,9 @@ struct LaunchArgs {
   int h;                   // 2D classic: rows per block
   int stage;               // SharpClaw stage 0..2
   cudaStream_t stream;
+  int n3[3];               // 3D: cells per direction
+  void* work3;             // 3D: per-face arrays (device)
+  size_t work3_bytes;
 };
 
 typedef cudaError_t (*launch_fn)(const LaunchArgs&);
@@ -51,6 +54,11 @@ __host__ __device__ inline int classic2d_tiles(int nx, int ny, int BW, int H) {
 }
 __host__ __device__ inline int sharp_tiles(int nx, int ny, int TX, int TY) {
   return ((nx + TX - 1) / TX) * ((ny + TY - 1) / TY);
+}
+
+inline size_t classic3d_work_bytes(int nx, int ny, int nz, int M, int prec) {
+  size_t faces = (size_t)(nx + 1) * ny * nz + (size_t)nx * (ny + 1) * nz + (size_t)nx * ny * (nz + 1);
+  return faces * 3 * M * (prec == 0 ? 8 : 4);
 }
 
 KernelSet claw_kernels_advection(int nd, int prec);

@@ -3,6 +3,7 @@
 #pragma once
 
 #include "classic.cuh"
+#include "classic3d.cuh"
 #include "kernels.h"
 #include "sharpclaw.cuh"
 
@@ -59,7 +60,18 @@ template <class RP, typename R, int ND>
 struct Launchers {
   static cudaError_t classic(const LaunchArgs& a) {
     const MConsts<R>& C = *(const MConsts<R>*)a.consts;
-    if constexpr (ND == 1) {
+    if constexpr (ND == 3) {
+      const long long nx = a.n3[0], ny = a.n3[1], nz = a.n3[2];
+      cudaError_t e = cudaMemsetAsync(a.work3, 0, a.work3_bytes, a.stream);
+      if (e != cudaSuccess) return e;
+      const long long f0 = (nx + 1) * (ny + 2) * (nz + 2), f1 = (ny + 1) * (nz + 2) * (nx + 2),
+                      f2 = (nz + 1) * (nx + 2) * (ny + 2);
+      classic3d_sweep<RP, R, 0><<<(unsigned)((f0 + 255) / 256), 256, 0, a.stream>>>(a.members, C);
+      classic3d_sweep<RP, R, 1><<<(unsigned)((f1 + 255) / 256), 256, 0, a.stream>>>(a.members, C);
+      classic3d_sweep<RP, R, 2><<<(unsigned)((f2 + 255) / 256), 256, 0, a.stream>>>(a.members, C);
+      classic3d_update<RP, R><<<a.ntiles_total, 256, 0, a.stream>>>(a.members, C);
+      return cudaGetLastError();
+    } else if constexpr (ND == 1) {
       constexpr int K = sizeof(R) == 8 ? classic1d_K(0) : classic1d_K(1);
       classic1d_kernel<RP, R, kClassic1dThreads, K>
           <<<launch_grid(a.ntiles_total), kClassic1dThreads, 0, a.stream>>>(a.members, a.tiles,
@@ -78,7 +90,10 @@ struct Launchers {
   }
   static cudaError_t sharp(const LaunchArgs& a) {
     const MConsts<R>& C = *(const MConsts<R>*)a.consts;
-    if constexpr (ND == 1) {
+    if constexpr (ND == 3) {
+      (void)C;
+      return cudaErrorNotSupported;
+    } else if constexpr (ND == 1) {
       sharp_stage_kernel<RP, R, 1, kSharpTX1, 1>
           <<<launch_grid(a.ntiles_total), kSharpTX1, 0, a.stream>>>(a.members, a.tiles,
                                                                  a.ntiles_total, C, a.stage);
@@ -91,8 +106,13 @@ struct Launchers {
   }
   static cudaError_t maxspeed(const LaunchArgs& a) {
     const MConsts<R>& C = *(const MConsts<R>*)a.consts;
-    maxspeed_kernel<RP, R, ND><<<launch_grid(a.ntiles_total), kMaxspeedCells, 0, a.stream>>>(
-        a.members, a.tiles, a.ntiles_total, C);
+    if constexpr (ND == 3) {
+      const long long n = (long long)a.n3[0] * a.n3[1] * a.n3[2];
+      maxspeed3_kernel<RP, R><<<(unsigned)((n + 255) / 256), 256, 0, a.stream>>>(a.members, C);
+    } else {
+      maxspeed_kernel<RP, R, ND><<<launch_grid(a.ntiles_total), kMaxspeedCells, 0, a.stream>>>(
+          a.members, a.tiles, a.ntiles_total, C);
+    }
     return cudaGetLastError();
   }
 };

@@ -89,6 +89,13 @@ struct RpAdvection {
     ap[0] = fmax(u, R(0)) * W[0][0];
     ctx[0] = R(0);
   }
+  // physical flux in direction DIR (A^-dQ + A^+dQ of every solve equals the
+  // flux jump, so the in-cell total fluctuation is a flux difference)
+  template <int DIR>
+  __device__ static __forceinline__ void flux(const MConsts<R>& C, const R (&q)[M], const R*,
+                                              R (&f)[M]) {
+    f[0] = C.p[DIR] * q[0];
+  }
   template <int DIR>
   __device__ static __forceinline__ void trans(const MConsts<R>& C, const R (&)[NCTX],
                                                const R (&a)[M], R (&bm)[M], R (&bp)[M]) {
@@ -148,6 +155,15 @@ struct RpAcoustics {
       ap[k] = c * W[1][k];
     }
     ctx[0] = R(0);
+  }
+  template <int DIR>
+  __device__ static __forceinline__ void flux(const MConsts<R>& C, const R (&q)[M], const R*,
+                                              R (&f)[M]) {
+    constexpr int n = Dirs<ND, DIR>::n;
+#pragma unroll
+    for (int k = 0; k < M; ++k) f[k] = R(0);
+    f[0] = C.p[1] * q[n];
+    f[n] = FM<R>::div(q[0], C.p[0]);
   }
   template <int DIR>
   __device__ static __forceinline__ void trans(const MConsts<R>& C, const R (&)[NCTX],
@@ -320,6 +336,15 @@ struct RpSW {
   }
 
   template <int DIR>
+  __device__ static __forceinline__ void flux(const MConsts<R>& C, const R (&q)[M], const R*,
+                                              R (&f)[M]) {
+    constexpr int n = Dirs<ND, DIR>::n, t = Dirs<ND, DIR>::t;
+    const R u = FM<R>::div(q[n], q[0]);
+    f[0] = q[n];
+    f[n] = q[n] * u + R(0.5) * C.g * (q[0] * q[0]);
+    if (t >= 0) f[t < 0 ? 0 : t] = q[t < 0 ? 0 : t] * u;
+  }
+  template <int DIR>
   __device__ static __forceinline__ void trans(const MConsts<R>& C, const R (&x)[NCTX],
                                                const R (&a)[M], R (&bm)[M], R (&bp)[M]) {
     constexpr int n = Dirs<ND, DIR>::n, t = Dirs<ND, DIR>::t;
@@ -416,6 +441,18 @@ struct EulerBase {
     o[E] = k0 * (H - un * c) + k1 * (R(0.5) * (un * un + ut * ut)) + ksh * ut + kl * (H + un * c);
   }
 
+  template <int DIR>
+  __device__ static __forceinline__ void flux(const MConsts<R>& C, const R (&q)[M], const R*,
+                                              R (&f)[M]) {
+    constexpr int n = Dirs<ND, DIR>::n, t = Dirs<ND, DIR>::t;
+    const R ir = FM<R>::rcp(q[0]);
+    const R p = pressure<DIR>(C, q, ir);
+    const R u = q[n] * ir;
+    f[0] = q[n];
+    f[n] = q[n] * u + p;
+    if (t >= 0) f[t < 0 ? 0 : t] = q[t < 0 ? 0 : t] * u;
+    f[E] = u * (q[E] + p);
+  }
   template <int DIR>
   __device__ static __forceinline__ void trans(const MConsts<R>& C, const R (&x)[NCTX],
                                                const R (&a)[M], R (&bm)[M], R (&bp)[M]) {
@@ -602,7 +639,7 @@ struct RpEulerHLLE : EulerBase<R, ND> {
   static constexpr int WALL_X = 1, WALL_Y = (ND == 2) ? 2 : -1;
 
   template <int DIR>
-  __device__ static __forceinline__ void flux(const R (&q)[M], R p, R (&f)[M]) {
+  __device__ static __forceinline__ void flux_p(const R (&q)[M], R p, R (&f)[M]) {
     constexpr int n = Dirs<ND, DIR>::n, t = Dirs<ND, DIR>::t;
     const R u = FM<R>::div(q[n], q[0]);
     f[0] = q[n];
@@ -624,8 +661,8 @@ struct RpEulerHLLE : EulerBase<R, ND> {
     const R s1 = fmin(FM<R>::div(ql[n], ql[0]) - cl, x[0] - x[3]);
     const R s2 = fmax(FM<R>::div(qr[n], qr[0]) + cr, x[0] + x[3]);
     R fl[M], fr[M];
-    flux<DIR>(ql, pl, fl);
-    flux<DIR>(qr, pr, fr);
+    flux_p<DIR>(ql, pl, fl);
+    flux_p<DIR>(qr, pr, fr);
     const R iden = FM<R>::rcp(s1 - s2);
 #pragma unroll
     for (int k = 0; k < M; ++k) {
@@ -687,6 +724,12 @@ struct RpElasticity {
         }
       }
     ctx[0] = R(0);
+  }
+  template <int DIR>
+  __device__ static __forceinline__ void flux(const MConsts<R>&, const R (&q)[M], const R* a,
+                                              R (&f)[M]) {
+    f[0] = -FM<R>::div(q[1], a[0]);
+    f[1] = R(1) - FM<R>::exp(a[1] * q[0]);
   }
   template <int DIR>
   __device__ static __forceinline__ void trans(const MConsts<R>&, const R (&)[NCTX],

@@ -313,3 +313,33 @@ def random_1d(rp, n, seed=SEED, bc=("periodic", "periodic"), jump=True, **kw):
                 aux=np.ascontiguousarray(aux) if aux is not None else None,
                 t_end=kw.get("t_end", 0.1))
     return spec
+
+
+def random_3d(rp, nx, ny, nz, seed=SEED, bc="periodic", **kw):
+    """Smooth random 3D data for advection (u, v, w) or acoustics (p, u, v, w)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    z = _centers(0.0, 1.0, nz)
+    y = _centers(0.0, 1.0, ny)
+    x = _centers(0.0, 1.0, nx)
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+
+    def field(amp):
+        f = np.zeros_like(X)
+        for _ in range(3):
+            k = rng.integers(1, 3, 3)
+            f += amp * rng.uniform(0.3, 1.0) * np.sin(
+                2 * np.pi * (k[0] * X + k[1] * Y + k[2] * Z) + rng.uniform(0, 6.3))
+        return f
+
+    if rp == "advection":
+        q0 = np.stack([field(1.0)])
+        params = kw.pop("params", [0.7, -0.5, 0.4])
+    elif rp == "acoustics":
+        q0 = np.stack([field(0.5), field(0.5), field(0.5), field(0.5)])
+        params = kw.pop("params", [1.3, 2.5])
+    else:
+        raise ValueError(rp)
+    spec = _base(3, [nx, ny, nz], [0.0, 0.0, 0.0], [1.0, 1.0, 1.0], rp, params=params,
+                 bc_lower=[bc] * 3, bc_upper=[bc] * 3, **kw)
+    spec.update(q0=np.ascontiguousarray(q0), aux=None, t_end=kw.get("t_end", 0.1))
+    return spec

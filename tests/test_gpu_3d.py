@@ -1,0 +1,59 @@
+"""3D classic step (transverse + double-transverse terms) on the GPU against
+the CPU oracle."""
+import numpy as np
+import pytest
+
+from paper_1111_6583_gb300 import workloads as wl
+from tests.gpu_util import (FP32_SMOOTH_TOL, FP64_TOL, gpu_evolve, gpu_fixed_steps,
+                            oracle_evolve, oracle_fixed_steps, rel_maxnorm)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+@pytest.mark.parametrize("rp", ["advection", "acoustics"])
+@pytest.mark.parametrize("order,transverse", [(2, 2), (2, 1), (1, 1), (2, 0)])
+def test_3d_fixed_dt_fp64(orc, rp, order, transverse):
+    spec = wl.random_3d(rp, 13, 11, 9, order=order, transverse=transverse)
+    dt = 0.25 / 13
+    qo, co = oracle_fixed_steps(orc, spec, dt, 4)
+    qg, cg = gpu_fixed_steps(spec, "fp64", dt, 4)
+    assert rel_maxnorm(qg, qo) <= FP64_TOL
+    assert np.allclose(cg, co, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("bc", ["wall", "extrap"])
+def test_3d_acoustics_boundaries(orc, bc):
+    spec = wl.random_3d("acoustics", 12, 10, 14, bc=bc)
+    spec["bc_lower"] = [bc, "periodic", "wall"]
+    spec["bc_upper"] = ["extrap", "periodic", bc]
+    dt = 0.2 / 14
+    qo, _ = oracle_fixed_steps(orc, spec, dt, 5)
+    qg, _ = gpu_fixed_steps(spec, "fp64", dt, 5)
+    assert rel_maxnorm(qg, qo) <= FP64_TOL
+    q32, _ = gpu_fixed_steps(spec, "fp32", dt, 5)
+    assert rel_maxnorm(q32, qo) <= FP32_SMOOTH_TOL
+
+
+def test_3d_diagonal_shift():
+    n = 16
+    spec = wl.random_3d("advection", n, n, n, params=[1.0, 1.0, 1.0], order=2, transverse=2)
+    qg, cg = gpu_fixed_steps(spec, "fp64", 1.0 / n, 1)
+    assert cg[0] == 1.0
+    assert np.abs(qg - np.roll(spec["q0"], (1, 1, 1), axis=(1, 2, 3))).max() <= 1e-14
+
+
+def test_3d_controller_run(orc):
+    spec = wl.random_3d("acoustics", 16, 12, 10, bc="wall")
+    qo, io = oracle_evolve(orc, spec, 0.15)
+    qg, ig = gpu_evolve(spec, "fp64", 0.15)
+    assert ig["steps"] == io["steps"] and ig["t"] == 0.15
+    assert rel_maxnorm(qg, qo) <= FP64_TOL

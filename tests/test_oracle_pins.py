@@ -646,3 +646,90 @@ def test_paper_listing_euler_quadrants(orc):
     rho = qT[0]
     p = 0.4 * (qT[3] - 0.5 * (qT[1] ** 2 + qT[2] ** 2) / rho)
     assert rho.min() > 0 and p.min() > 0
+
+
+# --------------------------------------------------------------------------
+# 3D classic (transverse + double-transverse propagation)
+# --------------------------------------------------------------------------
+def _prob3(orc, rp, n, params, order=2, transverse=2, lim="mc", bc="periodic", **kw):
+    spec = dict(ndim=3, n=list(n), lower=[0, 0, 0], upper=[1, 1, 1], rp=rp, params=params,
+                order=order, transverse=transverse, lim=lim,
+                bc_lower=[bc] * 3, bc_upper=[bc] * 3)
+    spec.update(kw)
+    return orc.make_problem(spec)
+
+
+def test_3d_ctu_exact_and_formula(orc):
+    """3D advection: at Courant number 1 in every direction the step is an
+    exact diagonal shift; below 1, first order with transverse and
+    double-transverse terms is the corner-transport-upwind product
+    prod_d [(1 - nu_d) + nu_d S_d] Q."""
+    n = 12
+    q0 = RNG.uniform(-1, 1, (1, n, n, n))
+    for order, tr in ((1, 1), (2, 2), (2, 1)):
+        q1, cfl = orc.step(_prob3(orc, "advection", (n, n, n), [1.0, 1.0, 1.0], order, tr), q0,
+                           dt=1.0 / n)
+        assert cfl == 1.0
+        assert np.abs(q1 - np.roll(q0, (1, 1, 1), axis=(1, 2, 3))).max() <= 1e-14
+    u, v, w = 1.0, 0.6, -0.35
+    dt = 0.8 / n
+    nus = [abs(u) * dt * n, abs(v) * dt * n, abs(w) * dt * n]
+    q1, _ = orc.step(_prob3(orc, "advection", (n, n, n), [u, v, w], 1, 1), q0, dt=dt)
+    Q = q0[0]
+    # axes of Q: (z, y, x); upwind shift +1 for positive speed, -1 for negative
+    out = Q
+    for ax, vel, nu in ((2, u, nus[0]), (1, v, nus[1]), (0, w, nus[2])):
+        sh = 1 if vel > 0 else -1
+        out = (1 - nu) * out + nu * np.roll(out, sh, axis=ax)
+    assert np.abs(q1[0] - out).max() <= 1e-14
+
+
+@pytest.mark.parametrize("rp,params", [("advection", [0.7, -0.4, 0.3]), ("acoustics", [1.3, 2.5])])
+def test_3d_conservation(orc, rp, params):
+    n = (10, 9, 8)
+    m = 1 if rp == "advection" else 4
+    q0 = RNG.uniform(-1, 1, (m, n[2], n[1], n[0]))
+    P = _prob3(orc, rp, n, params)
+    q = q0.copy()
+    for _ in range(5):
+        q, cfl = orc.step(P, q, dt=0.3 / 10)
+    t0, t1 = orc.totals(P, q0), orc.totals(P, q)
+    ref = np.abs(q0).reshape(m, -1).sum(axis=1) * P.dx * P.dy * P.dz
+    assert (np.abs(t1 - t0) / ref).max() <= 1e-13
+
+
+def test_3d_acoustics_axis_symmetry(orc):
+    """A pressure pulse symmetric under axis permutations stays symmetric, with
+    the velocity components permuted along; walls keep mirror symmetry."""
+    n = 16
+    x = (np.arange(n) + 0.5) / n - 0.5
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    p = np.exp(-40 * (X * X + Y * Y + Z * Z))
+    q0 = np.stack([p, np.zeros_like(p), np.zeros_like(p), np.zeros_like(p)])
+    P = _prob3(orc, "acoustics", (n, n, n), [1.0, 4.0], bc="wall")
+    q = q0.copy()
+    for _ in range(8):
+        q, _ = orc.step(P, q, dt=0.4 / n / 2.0)
+    pp, u, v, w = q
+    tol = 1e-13
+    assert np.abs(pp - pp.transpose(0, 2, 1)).max() <= tol  # x <-> y
+    assert np.abs(u - v.transpose(0, 2, 1)).max() <= tol
+    assert np.abs(pp - pp.transpose(2, 1, 0)).max() <= tol  # x <-> z
+    assert np.abs(u - w.transpose(2, 1, 0)).max() <= tol
+    assert np.abs(pp - pp[:, :, ::-1]).max() <= tol and np.abs(u + u[:, :, ::-1]).max() <= tol
+
+
+def test_3d_second_order(orc):
+    ns = [8, 16, 32]
+    errs = []
+    for n in ns:
+        dx = 1.0 / n
+        xe = np.arange(n + 1) * dx
+        c1 = (np.cos(2 * np.pi * xe[:-1]) - np.cos(2 * np.pi * xe[1:])) / (2 * np.pi * dx)
+        q0 = np.einsum("k,j,i->kji", c1, c1, c1)[None]
+        P = _prob3(orc, "advection", (n, n, n), [1.0, 1.0, 1.0], 2, 2, lim="none",
+                   cfl_desired=0.8)
+        qT, info = orc.evolve(P, q0, t_end=1.0)
+        errs.append(np.abs(qT - q0).sum() * dx ** 3)
+    ords = _order(errs, ns)
+    assert min(ords[1:]) >= 1.85, ords
