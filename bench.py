@@ -370,6 +370,33 @@ def reference_arm(args):
     print(json.dumps(line))
 
 
+def profile_case(case):
+    """A short fixed launch sequence of one kernel for ncu captures (untimed):
+    sw2d64/sw2d32 -- 2048^2 dam break, autotune (40 launches) then 3 steps;
+    elast -- 1024-member FP32 elasticity batch, 5 fused steps;
+    sharp -- 1024x512 shock-bubble FP64, 2 SharpClaw steps (6 stage launches)."""
+    import torch
+    from paper_1111_6583_gb300 import claw
+    from paper_1111_6583_gb300 import workloads as wl
+    if case in ("sw2d64", "sw2d32"):
+        s = claw.Solver(wl.sw_dambreak_2d(n=2048), "fp64" if case == "sw2d64" else "fp32")
+        print("tile", s.tune())
+        s.set_t_end(1.5)
+        s.advance(3)
+    elif case == "elast":
+        ens = wl.elasticity_ensemble(1024)
+        b = claw.Batch([wl.elasticity_member(e["n"], e["amp"], e["width"]) for e in ens], "fp32")
+        b.advance(5)
+    elif case == "sharp":
+        s = claw.Solver(wl.shock_bubble_2d(nx=1024, ny=512), "fp64")
+        s.set_t_end(0.2)
+        s.advance(2)
+    else:
+        raise SystemExit("unknown case " + case)
+    torch.cuda.synchronize()
+    print("ok")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -380,7 +407,14 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--members", type=int, default=4096)
+    ap.add_argument("--case", default=None,
+                    help="run one short launch sequence for a profiler (sw2d64, sw2d32, elast, sharp)")
     args = ap.parse_args()
+    if args.case:
+        import __graft_entry__
+        __graft_entry__.build()
+        profile_case(args.case)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

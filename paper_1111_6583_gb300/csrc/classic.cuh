@@ -116,7 +116,7 @@ struct CellPrep<RpElasticity<R, 1>, R> {
 };
 
 template <class RP, typename R, int NT, int K>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? 7 : 1)
     classic1d_kernel(const Member* __restrict__ members, const Tile* __restrict__ tiles,
                      int ntiles_total, const MConsts<R> C) {
   constexpr int M = RP::M, MW = RP::MW, MA = RP::MA;
@@ -183,12 +183,25 @@ __global__ void __launch_bounds__(NT)
           if (MA > 0) load_aux<MA, R>(C, aux, nx, 1, min(base + c, nx + 1), 0, aa[c + 2]);
         }
       }
+      if (base >= 2 && base + K + 2 <= nx) {
+        // halo cells inside the grid: plain loads
 #pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        const int c = h < 2 ? h : K + h;  // local slots 0,1 and K+2,K+3
-        const int gi = min(base - 2 + c, nx + 1);
-        load_cell<M, R>(C, q, nx, 1, gi, 0, RP::WALL_X, -1, qa[c]);
-        if (MA > 0) load_aux<MA, R>(C, aux, nx, 1, gi, 0, aa[c]);
+        for (int h = 0; h < 4; ++h) {
+          const int c = h < 2 ? h : K + h;  // local slots 0,1 and K+2,K+3
+          const size_t gi = (size_t)(base - 2 + c);
+#pragma unroll
+          for (int k = 0; k < M; ++k) qa[c][k] = __ldg(q + (size_t)k * nx + gi);
+#pragma unroll
+          for (int k = 0; k < MA; ++k) aa[c][k] = __ldg(aux + (size_t)k * nx + gi);
+        }
+      } else {
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const int c = h < 2 ? h : K + h;
+          const int gi = min(base - 2 + c, nx + 1);
+          load_cell<M, R>(C, q, nx, 1, gi, 0, RP::WALL_X, -1, qa[c]);
+          if (MA > 0) load_aux<MA, R>(C, aux, nx, 1, gi, 0, aa[c]);
+        }
       }
       // streaming window over interfaces jj = 0..K+2 (interface jj lies between
       // qa[jj] and qa[jj+1], global index base-1+jj)
