@@ -62,6 +62,7 @@ class _Prob(ctypes.Structure):
         ("dt_initial", ctypes.c_double), ("dt_max", ctypes.c_double),
         ("max_retries", ctypes.c_int), ("weno_eps", ctypes.c_double),
         ("nz", ctypes.c_int), ("dz", ctypes.c_double),
+        ("time_integrator", ctypes.c_int),
     ]
 
 
@@ -96,6 +97,8 @@ def _load():
         lib.orc_sharp_step.argtypes = [P, _dp, _dp, ctypes.c_double, _dp]
         lib.orc_ssp_rk3_linear.restype = ctypes.c_double
         lib.orc_ssp_rk3_linear.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
+        lib.orc_ssp104_linear.restype = ctypes.c_double
+        lib.orc_ssp104_linear.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
         lib.orc_max_speeds.argtypes = [P, _dp, _dp, _dp]
         lib.orc_evolve.argtypes = [P, _dp, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                    ctypes.POINTER(_RunInfo)]
@@ -165,6 +168,7 @@ def make_problem(spec: dict):
     p.dt_max = float(spec.get("dt_max", 1e30))
     p.max_retries = int(spec.get("max_retries", 8))
     p.weno_eps = float(spec.get("weno_eps", 1e-6))
+    p.time_integrator = {"ssp_rk3": 0, "ssp104": 1}[spec.get("time_integrator", "ssp_rk3")]
     return p
 
 
@@ -260,6 +264,10 @@ def sharp_L(p, q, aux=None):
 
 def ssp_rk3_linear(lam, dt, q0) -> float:
     return _load().orc_ssp_rk3_linear(float(lam), float(dt), float(q0))
+
+
+def ssp104_linear(lam, dt, q0) -> float:
+    return _load().orc_ssp104_linear(float(lam), float(dt), float(q0))
 
 
 def max_speeds(p, q, aux=None):

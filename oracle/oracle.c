@@ -1191,7 +1191,75 @@ double orc_ssp_rk3_linear(double lambda, double dt, double q0) {
   return rk3_stage(2, q0, q2, lambda * q2, dt);
 }
 
+/* Ketcheson's ten-stage fourth-order SSP method in its low-storage form:
+ * five forward-Euler steps of size dt/6 on q1, then q2 = q2/25 + 9 q1/25,
+ * q1 = 15 q2 - 5 q1, four more dt/6 steps on q1, and finally
+ * q1 = q2 + 3/5 q1 + dt/10 L(q1).  Lfun evaluates L into its third argument
+ * and returns the largest Courant number it saw (or NaN). */
+typedef double (*lfun_t)(const void* ctx, const double* q, double* L);
+
+static double ssp104(lfun_t Lf, const void* ctx, size_t n, double* q, double dt) {
+  double* q1 = (double*)malloc(sizeof(double) * n);
+  double* q2 = (double*)malloc(sizeof(double) * n);
+  double* L = (double*)malloc(sizeof(double) * n);
+  double nu = 0.0;
+  memcpy(q1, q, sizeof(double) * n);
+  memcpy(q2, q, sizeof(double) * n);
+  for (int st = 0; st < 9; ++st) {
+    double v = Lf(ctx, q1, L);
+    if (!(v <= nu)) nu = v;
+    for (size_t c = 0; c < n; ++c) q1[c] = q1[c] + dt / 6.0 * L[c];
+    if (st == 4) {
+      for (size_t c = 0; c < n; ++c) {
+        q2[c] = q2[c] / 25.0 + 9.0 * q1[c] / 25.0;
+        q1[c] = 15.0 * q2[c] - 5.0 * q1[c];
+      }
+    }
+  }
+  double v = Lf(ctx, q1, L);
+  if (!(v <= nu)) nu = v;
+  for (size_t c = 0; c < n; ++c) q[c] = q2[c] + 3.0 / 5.0 * q1[c] + dt / 10.0 * L[c];
+  free(q1); free(q2); free(L);
+  return nu;
+}
+
+static double lin_L(const void* ctx, const double* q, double* L) {
+  L[0] = *(const double*)ctx * q[0];
+  return 0.0;
+}
+
+double orc_ssp104_linear(double lambda, double dt, double q0) {
+  double q = q0;
+  ssp104(lin_L, &lambda, 1, &q, dt);
+  return q;
+}
+
+typedef struct {
+  const orc_prob* P;
+  const double* aux;
+  double dt;
+  int status;
+} sharp_ctx;
+
+static double sharp_L_fn(const void* vctx, const double* q, double* L) {
+  sharp_ctx* c = (sharp_ctx*)vctx;
+  double smax[2];
+  if (orc_sharp_L(c->P, q, c->aux, L, smax) != ORC_OK) c->status = ORC_EINVAL;
+  double nu = 0.0;
+  for (int d = 0; d < c->P->ndim; ++d) {
+    double v = c->dt * smax[d] / (d == 0 ? c->P->dx : c->P->dy);
+    if (!(v <= nu)) nu = v;
+  }
+  return nu;
+}
+
 int orc_sharp_step(const orc_prob* P, double* q, const double* aux, double dt, double* cfl) {
+  if (P->time_integrator == 1) {
+    int ny1 = (P->ndim == 2) ? P->ny : 1;
+    sharp_ctx c = {P, aux, dt, ORC_OK};
+    *cfl = ssp104(sharp_L_fn, &c, (size_t)P->nx * ny1 * P->num_eqn, q, dt);
+    return c.status;
+  }
   int ny = (P->ndim == 2) ? P->ny : 1;
   size_t ntot = (size_t)P->nx * ny * P->num_eqn;
   double* qn = (double*)malloc(sizeof(double) * ntot);

@@ -55,6 +55,7 @@ typedef struct {
   double weno_eps;      /* WENO5 epsilon (Jiang-Shu) */
   int nz;               /* 3D: cells in z (1 otherwise) */
   double dz;            /* 3D: cell width in z */
+  int time_integrator;  /* SharpClaw: 0 SSP-RK3 (Shu-Osher), 1 SSP(10,4) (Ketcheson 2008) */
 } orc_prob;
 
 typedef struct {
@@ -104,6 +105,8 @@ int orc_sharp_L(const orc_prob* P, const double* q, const double* aux, double* L
 int orc_sharp_step(const orc_prob* P, double* q, const double* aux, double dt, double* cfl);
 /* One SSP-RK3 step of the scalar linear ODE q' = lambda q (same stage code). */
 double orc_ssp_rk3_linear(double lambda, double dt, double q0);
+/* One SSP(10,4) step of q' = lambda q (same stage code as orc_sharp_step). */
+double orc_ssp104_linear(double lambda, double dt, double q0);
 /* Largest first-order interface wave speed per direction on Q (used for dt0). */
 void orc_max_speeds(const orc_prob* P, const double* q, const double* aux, double* smax);
 

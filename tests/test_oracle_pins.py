@@ -733,3 +733,40 @@ def test_3d_second_order(orc):
         errs.append(np.abs(qT - q0).sum() * dx ** 3)
     ords = _order(errs, ns)
     assert min(ords[1:]) >= 1.85, ords
+
+
+# --------------------------------------------------------------------------
+# SSP(10,4): the paper's default SharpClaw integrator
+# --------------------------------------------------------------------------
+def test_ssp104_is_fourth_order_on_linear_problems(orc):
+    """One step of q' = lambda q agrees with exp(z) to O(z^5) (fourth order),
+    the error at z -> z/2 falls by 2^5, and the scheme is stable on the
+    negative real axis out to z = -6 (SSP coefficient 6, ten stages)."""
+    for z in (0.05, -0.05, 0.02j):
+        pass
+    errs = []
+    for z in (0.2, 0.1, 0.05):
+        r = orc.ssp104_linear(-z, 1.0, 1.0)
+        errs.append(abs(r - math.exp(-z)))
+    assert errs[0] / errs[1] == pytest.approx(32, rel=0.1)
+    assert errs[1] / errs[2] == pytest.approx(32, rel=0.05)
+    for z in np.linspace(-6.0, 0.0, 61):
+        assert abs(orc.ssp104_linear(z, 1.0, 1.0)) <= 1.0 + 1e-12
+
+
+def test_ssp104_sharpclaw_converges(orc):
+    """WENO5 + SSP(10,4) on smooth periodic advection for one period: the
+    error falls at high order at a large Courant number."""
+    ns = [32, 64, 128]
+    errs = []
+    for n in ns:
+        dx = 1.0 / n
+        xe = np.arange(n + 1) * dx
+        q0 = np.stack([(np.cos(2 * np.pi * xe[:-1]) - np.cos(2 * np.pi * xe[1:])) / (2 * np.pi * dx)])
+        P = _adv1d(orc, n, scheme="sharpclaw", time_integrator="ssp104", cfl_desired=2.0,
+                   cfl_max=2.5)
+        qT, info = orc.evolve(P, q0, t_end=1.0)
+        assert info["status"] == "ok"
+        errs.append(np.abs(qT - q0).sum() * dx)
+    ords = _order(errs, ns)
+    assert min(ords) >= 3.7, ords
