@@ -49,6 +49,56 @@ ELAST1D_BYTES_PER_CELL = {"fp64": 48.0, "fp32": 24.0}  # q read+write, aux read
 FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12
 
 
+TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "traffic_classic2d_sw_fp64_1024.json")
+KERNEL_SOURCES = ["claw_common.cuh", "riemann.cuh", "classic.cuh", "launch.cuh", "kernels.h",
+                  "k_sw.cu"]
+
+
+def kernel_sha():
+    """Hash of the sources that define the headline kernel."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1111_6583_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic():
+    """DRAM bytes per launch of the headline kernel from the last ncu capture,
+    or None when the kernel sources changed since it was taken."""
+    if not os.path.exists(TRAFFIC_RECORD):
+        return None
+    rec = json.load(open(TRAFFIC_RECORD))
+    return rec["dram_bytes_per_launch"] if rec.get("sources_sha256") == kernel_sha() else None
+
+
+def record_traffic(csv_path):
+    """Write the traffic record from an ncu --csv launch list of the bench
+    command (metrics dram__bytes_read.sum, dram__bytes_write.sum; the last
+    `steps` classic2d launches are the timed ones)."""
+    import csv
+    rows = list(csv.reader(open(csv_path)))
+    hi = [i for i, r in enumerate(rows) if "Kernel Name" in r][0]
+    hdr = rows[hi]
+    mi, vi, ii = hdr.index("Metric Name"), hdr.index("Metric Value"), hdr.index("ID")
+    by = {}
+    for r in rows[hi + 1:]:
+        if len(r) > vi:
+            by.setdefault(r[ii], {})[r[mi]] = float(r[vi].replace(",", ""))
+    timed = list(by.values())[-4:]
+    b = sum(v["dram__bytes_read.sum"] + v["dram__bytes_write.sum"] for v in timed) / len(timed)
+    rec = {"kernel": "classic2d_kernel<RpSW<double,2>>", "workload": "dam break 1024x1024 FP64",
+           "dram_bytes_per_launch": b, "sources_sha256": kernel_sha(),
+           "command": "python bench.py --steps 4 --warmup 3 --no-extras > gpurun_out/plain.log "
+                      "2>&1 && ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,"
+                      "dram__bytes_write.sum --clock-control none -k regex:classic2d --csv "
+                      "--log-file gpurun_out/traffic_sw2d.csv python bench.py --steps 4 "
+                      "--warmup 3 --no-extras"}
+    json.dump(rec, open(TRAFFIC_RECORD, "w"), indent=1)
+    print(json.dumps(rec))
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -407,9 +457,14 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--members", type=int, default=4096)
+    ap.add_argument("--record-traffic", default=None,
+                    help="write the headline kernel's traffic record from an ncu csv")
     ap.add_argument("--case", default=None,
                     help="run one short launch sequence for a profiler (sw2d64, sw2d32, elast, sharp)")
     args = ap.parse_args()
+    if args.record_traffic:
+        record_traffic(args.record_traffic)
+        return
     if args.case:
         import __graft_entry__
         __graft_entry__.build()
@@ -451,7 +506,7 @@ def main():
         "gpu_launches": args.steps,
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
-                     "traffic": None,
+                     "traffic": recorded_traffic(),
                      "peak_kind": "derived FP64 (152 SM x 2.07 GHz x 4 FLOP/clk)",
                      "hbm_gbs": SW2D_BYTES_PER_CELL["fp64"] * cells / (avg_ms * 1e-3) / 1e9,
                      "hbm_frac": SW2D_BYTES_PER_CELL["fp64"] * cells / (avg_ms * 1e-3) / 1e9 / hbm,

@@ -62,6 +62,11 @@ enum { CLAW_RP_ADVECTION = 0, CLAW_RP_ACOUSTICS = 1, CLAW_RP_SW_ROE = 2,
 enum { CLAW_LIM_NONE = 0, CLAW_LIM_MINMOD = 1, CLAW_LIM_SUPERBEE = 2, CLAW_LIM_VANLEER = 3,
        CLAW_LIM_MC = 4 };
 enum { CLAW_BC_PERIODIC = 0, CLAW_BC_WALL = 1, CLAW_BC_EXTRAP = 2, CLAW_BC_INFLOW = 3 };
+/* SharpClaw time integrators (Sec. 3.1): Shu-Osher three-stage SSP-RK3, and
+ * Ketcheson's ten-stage fourth-order SSP(10,4) in its two-register low-storage
+ * form (SSP coefficient 6, so the CFL limit is about six times that of one
+ * forward-Euler stage spread over ten stages). */
+enum { CLAW_SSP_RK3 = 0, CLAW_SSP104 = 1 };
 
 /* Domain (Sec. 4.2: tensor product of equispaced 1D grids).  n[d] cells on
  * [lower[d], upper[d]]; entries beyond ndim are ignored. */
@@ -94,6 +99,7 @@ typedef struct {
   double params[8];    /* advection u,v | acoustics rho,K | SW g | Euler gamma    */
   int num_eqn;         /* filled in by claw_method_init / validated by create     */
   int num_aux;         /* elasticity: 2 (rho, K per cell); others 0               */
+  int time_integrator; /* SharpClaw: CLAW_SSP_RK3 (default) | CLAW_SSP104          */
 } claw_method;
 
 typedef struct {

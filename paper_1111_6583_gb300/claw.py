@@ -26,6 +26,7 @@ RP = {"advection": 0, "acoustics": 1, "sw_roe": 2, "euler_roe": 3, "euler_hlle":
       "elasticity_fwave": 5}
 LIM = {"none": 0, "minmod": 1, "superbee": 2, "vanleer": 3, "mc": 4}
 BC = {"periodic": 0, "wall": 1, "extrap": 2, "inflow": 3}
+TIME_INTEGRATOR = {"ssp_rk3": 0, "ssp104": 1}
 
 
 class ClawError(RuntimeError):
@@ -49,7 +50,7 @@ class claw_method(ctypes.Structure):
                 ("weno_eps", ctypes.c_double), ("bc_lower", ctypes.c_int * 3),
                 ("bc_upper", ctypes.c_int * 3), ("inflow", ctypes.c_double * 8),
                 ("params", ctypes.c_double * 8), ("num_eqn", ctypes.c_int),
-                ("num_aux", ctypes.c_int)]
+                ("num_aux", ctypes.c_int), ("time_integrator", ctypes.c_int)]
 
 
 class claw_step_info(ctypes.Structure):
@@ -193,6 +194,7 @@ def method_from_spec(spec, prec="fp64") -> claw_method:
     m.dt_initial = float(spec.get("dt_initial", 0.0))
     m.dt_max = float(spec.get("dt_max", 1e30))
     m.weno_eps = float(spec.get("weno_eps", 1e-6))
+    m.time_integrator = TIME_INTEGRATOR[spec.get("time_integrator", "ssp_rk3")]
     bl = list(spec.get("bc_lower", ["periodic"] * ndim)) + ["periodic"] * 2
     bh = list(spec.get("bc_upper", ["periodic"] * ndim)) + ["periodic"] * 2
     for d in range(3):

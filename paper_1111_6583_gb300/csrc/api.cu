@@ -107,6 +107,9 @@ const char* check_method(const claw_method& m, int nd) {
   if (m.scheme == CLAW_CLASSIC && m.order != 1 && m.order != 2) return "order must be 1 or 2";
   if (m.transverse < 0 || m.transverse > 2) return "transverse must be 0, 1 or 2";
   if (m.scheme == CLAW_SHARPCLAW && m.weno_order != 5) return "weno_order must be 5";
+  if (m.scheme == CLAW_SHARPCLAW && m.time_integrator != CLAW_SSP_RK3 &&
+      m.time_integrator != CLAW_SSP104)
+    return "unknown time integrator";
   if (m.scheme == CLAW_SHARPCLAW && m.char_decomp && m.rp == CLAW_RP_ELASTICITY_FWAVE)
     return "no characteristic projection for the f-wave elasticity solver";
   if (!(m.cfl_desired > 0) || !(m.cfl_max >= m.cfl_desired)) return "need 0 < cfl_desired <= cfl_max";
@@ -147,6 +150,13 @@ int maxspeed_tiles(int nx, int ny) {
   return (int)((n + kMaxspeedCells - 1) / kMaxspeedCells);
 }
 
+// state buffers a scheme rotates through: classic Q^n, Q^{n+1}; SSP-RK3 adds
+// one stage state; SSP(10,4) two (its two low-storage registers)
+int nbuf_of(const claw_method& m) {
+  if (m.scheme == CLAW_CLASSIC) return 2;
+  return m.time_integrator == CLAW_SSP104 ? 4 : 3;
+}
+
 DevCtl make_ctl(const claw_method& m, const claw_grid& g, int nbuf, double t0, double t_end) {
   DevCtl c;
   std::memset(&c, 0, sizeof(c));
@@ -161,6 +171,7 @@ DevCtl make_ctl(const claw_method& m, const claw_grid& g, int nbuf, double t0, d
   c.dt_init = m.dt_initial;
   c.max_steps = LLONG_MAX;
   c.nbuf = nbuf;
+  c.accept_shift = (m.scheme == CLAW_SHARPCLAW && m.time_integrator == CLAW_SSP104) ? 2 : 1;
   c.max_retries = m.max_retries;
   c.ndim = g.ndim;
   c.done = (t0 >= t_end) ? 1 : 0;
@@ -194,12 +205,16 @@ void fill_info(const DevCtl& c, claw_step_info* info) {
 }
 
 // Launch one attempt (classic: one kernel; SharpClaw: three stage kernels).
-cudaError_t launch_attempt(const KernelSet& ks, int scheme, const Member* mem, const Tile* tiles,
-                           int ntiles, const void* consts, int bw, int h, cudaStream_t st) {
+cudaError_t launch_attempt(const KernelSet& ks, const claw_method& m, const Member* mem,
+                           const Tile* tiles, int ntiles, const void* consts, int bw, int h,
+                           cudaStream_t st) {
   LaunchArgs a{mem, tiles, ntiles, consts, bw, h, 0, st};
-  if (scheme == CLAW_CLASSIC) return ks.classic(a);
-  for (int s = 0; s < 3; ++s) {
+  if (m.scheme == CLAW_CLASSIC) return ks.classic(a);
+  const StageOp* ops;
+  const int ns = stage_table(m.time_integrator, &ops);
+  for (int s = 0; s < ns; ++s) {
     a.stage = s;
+    a.stage_op = ops + s;
     cudaError_t e = ks.sharp(a);
     if (e != cudaSuccess) return e;
   }
@@ -287,7 +302,7 @@ cudaError_t solver_attempt(claw_solver* s, cudaStream_t st) {
                  {(int)s->g.n[0], (int)s->g.n[1], (int)s->g.n[2]}, s->work3, s->work3_bytes};
     return s->ks.classic(a);
   }
-  return launch_attempt(s->ks, s->m.scheme, s->d_mem, nullptr, s->ntiles, s->consts.data(), s->bw,
+  return launch_attempt(s->ks, s->m, s->d_mem, nullptr, s->ntiles, s->consts.data(), s->bw,
                         s->h, st);
 }
 
@@ -481,7 +496,7 @@ claw_status claw_solver_create(const claw_method* m, const claw_grid* g, void* s
   if (g->ndim <= 2) s->g.n[2] = 1;
   s->nd = g->ndim;
   s->prec = m->prec;
-  s->nbuf = m->scheme == CLAW_SHARPCLAW ? 3 : 2;
+  s->nbuf = nbuf_of(*m);
   s->ks = ks;
   s->consts = make_consts(*m);
   s->ustream = (cudaStream_t)stream;
@@ -529,7 +544,8 @@ claw_status claw_bind_state(claw_solver* s, void* q_dev, const void* aux_dev, do
   std::memset(&s->h_mem, 0, sizeof(Member));
   s->h_mem.q[0] = q_dev;
   s->h_mem.q[1] = s->work;
-  s->h_mem.q[2] = s->nbuf == 3 ? (void*)((unsigned char*)s->work + s->sbytes) : nullptr;
+  for (int j = 2; j < s->nbuf; ++j)
+    s->h_mem.q[j] = (void*)((unsigned char*)s->work + (size_t)(j - 1) * s->sbytes);
   s->h_mem.aux = aux_dev;
   s->h_mem.nx = (int)s->g.n[0];
   s->h_mem.ny = (int)s->g.n[1];
@@ -747,6 +763,8 @@ claw_status claw_restore(claw_solver* s, const void* host_buf, size_t bytes) {
   DevCtl c;
   std::memcpy(&c, (const unsigned char*)host_buf + sizeof(hd), sizeof(DevCtl));
   c.cur = 0;
+  c.nbuf = s->nbuf;
+  c.accept_shift = make_ctl(s->m, s->g, s->nbuf, 0.0, 0.0).accept_shift;
   c.arrive = 0;
   c.smax[0] = c.smax[1] = 0;
   c.bad = 0;
@@ -861,7 +879,7 @@ void batch_free(claw_batch* b) {
 }
 
 cudaError_t batch_attempt(claw_batch* b, cudaStream_t st) {
-  return launch_attempt(b->ks, b->m.scheme, b->d_mem, b->d_tiles, b->ntiles, b->consts.data(),
+  return launch_attempt(b->ks, b->m, b->d_mem, b->d_tiles, b->ntiles, b->consts.data(),
                         b->bw, b->h, st);
 }
 
@@ -886,7 +904,7 @@ claw_status claw_batch_create(const claw_method* m, const claw_grid* grids, int 
   b->m = *m;
   b->nd = nd;
   b->prec = m->prec;
-  b->nbuf = m->scheme == CLAW_SHARPCLAW ? 3 : 2;
+  b->nbuf = nbuf_of(*m);
   b->n = n;
   b->ks = ks;
   b->consts = make_consts(*m);
@@ -1159,7 +1177,7 @@ claw_status claw_server_create(const claw_method* m, size_t hbm_budget_bytes, in
   v->m = *m;
   v->prec = m->prec;
   v->nd = nd;
-  v->nbuf = m->scheme == CLAW_SHARPCLAW ? 3 : 2;
+  v->nbuf = nbuf_of(*m);
   v->ks = ks;
   v->consts = make_consts(*m);
   v->budget = hbm_budget_bytes;
@@ -1293,7 +1311,7 @@ claw_status claw_server_pump(claw_server* v, int steps, int* running, int* queue
   // 3. fused step attempts over every running request
   if (!v->running.empty()) {
     for (int i = 0; i < steps; ++i)
-      VCK(launch_attempt(v->ks, v->m.scheme, v->d_mem, v->d_tiles, v->ntiles, v->consts.data(),
+      VCK(launch_attempt(v->ks, v->m, v->d_mem, v->d_tiles, v->ntiles, v->consts.data(),
                          v->bw, v->h, v->st));
     // 4. retire finished requests
     const int nr = (int)v->running.size();

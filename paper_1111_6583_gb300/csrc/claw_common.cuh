@@ -29,7 +29,8 @@ struct DevCtl {
   unsigned long long smax[3];  // bit patterns of max |s| per direction (non-negative)
   long long steps, rejects, max_steps;
   int cur;          // buffer holding Q^n
-  int nbuf;         // 2 (classic) or 3 (SharpClaw)
+  int nbuf;         // 2 (classic), 3 (SharpClaw SSP-RK3) or 4 (SharpClaw SSP(10,4))
+  int accept_shift; // buffer rotation on acceptance (slot of the new state)
   int retries, max_retries;
   int status;       // CLAW_OK / CLAW_ECFL / CLAW_ENONPHYSICAL
   int done;         // no more work: t reached t_end, max_steps reached, or error
@@ -44,13 +45,22 @@ struct DevCtl {
 
 // One grid of a launch.  Single solves use a table of one member.
 struct Member {
-  void* q[3];        // state buffers (rotation by DevCtl::cur)
+  void* q[4];        // state buffers (rotation by DevCtl::cur)
   const void* aux;   // cell aux fields or nullptr
   int nx, ny;        // interior cells (ny = 1 in 1D)
   int ntiles;        // blocks of this member per attempt
   int nz;            // 3D: cells in z (1 otherwise)
   DevCtl* ctl;
   void* work3;       // 3D: per-face fluctuation / correction arrays
+};
+
+// One stage of a SharpClaw Runge-Kutta method.  Buffer slots are relative to
+// DevCtl::cur (slot 0 holds Q^n).  With v = Q[in] + g dt L(Q[in]):
+//   Q[out] = a0 Q[sa] + a1 v,   and when out2 >= 0:   Q[out2] = b0 Q[sb] + b1 v.
+// The stage marked last runs the CFL controller.
+struct StageOp {
+  int in, out, out2, sa, sb, last;
+  double g, a0, a1, b0, b1;
 };
 
 // Work item of a batched launch: (member, tile index within the member).
@@ -202,7 +212,7 @@ static __device__ __noinline__ void run_controller(DevCtl* c) {
   } else {
     c->accepted = 1;
     c->t = c->final_ ? c->t_end : c->t + dt;
-    c->cur = (c->cur + 1) % c->nbuf;
+    c->cur = (c->cur + c->accept_shift) % c->nbuf;
     c->steps += 1;
     c->retries = 0;
     c->nu_last = nu;

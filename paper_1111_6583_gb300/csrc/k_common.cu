@@ -125,6 +125,39 @@ cudaError_t launch_set_dry(DevCtl* ctl, int dry, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Shu-Osher SSP-RK3: Q1 = Q + dt L(Q); Q2 = 3/4 Q + 1/4 (Q1 + dt L(Q1));
+// Q3 = 1/3 Q + 2/3 (Q2 + dt L(Q2)).  Slots: Q^n 0, Q1 1, Q2 2, Q3 1.
+static const StageOp kRK3[3] = {
+    {0, 1, -1, 0, 0, 0, 1.0, 0.0, 1.0, 0.0, 0.0},
+    {1, 2, -1, 0, 0, 0, 1.0, 0.75, 0.25, 0.0, 0.0},
+    {2, 1, -1, 0, 0, 1, 1.0, 1.0 / 3.0, 2.0 / 3.0, 0.0, 0.0},
+};
+// Ketcheson's SSP(10,4), low-storage form: q1 = q1 + dt/6 L(q1) five times;
+// q2 = q2/25 + 9 q1/25 and q1 = 15 q2 - 5 q1 = 3/5 Q^n + 2/5 q1 (folded into
+// stage 5); four more dt/6 steps; q1 = q2 + 3/5 (q1 + dt/6 L(q1)).  Slots:
+// Q^n 0, q1 alternating 1/2, q2 3; the new state lands in slot 2.
+static const StageOp kSSP104[10] = {
+    {0, 1, -1, 0, 0, 0, 1.0 / 6.0, 0.0, 1.0, 0.0, 0.0},
+    {1, 2, -1, 0, 0, 0, 1.0 / 6.0, 0.0, 1.0, 0.0, 0.0},
+    {2, 1, -1, 0, 0, 0, 1.0 / 6.0, 0.0, 1.0, 0.0, 0.0},
+    {1, 2, -1, 0, 0, 0, 1.0 / 6.0, 0.0, 1.0, 0.0, 0.0},
+    {2, 3, 1, 0, 0, 0, 1.0 / 6.0, 1.0 / 25.0, 9.0 / 25.0, 3.0 / 5.0, 2.0 / 5.0},
+    {1, 2, -1, 0, 0, 0, 1.0 / 6.0, 0.0, 1.0, 0.0, 0.0},
+    {2, 1, -1, 0, 0, 0, 1.0 / 6.0, 0.0, 1.0, 0.0, 0.0},
+    {1, 2, -1, 0, 0, 0, 1.0 / 6.0, 0.0, 1.0, 0.0, 0.0},
+    {2, 1, -1, 0, 0, 0, 1.0 / 6.0, 0.0, 1.0, 0.0, 0.0},
+    {1, 2, -1, 3, 0, 1, 1.0 / 6.0, 1.0, 3.0 / 5.0, 0.0, 0.0},
+};
+
+int stage_table(int integrator, const StageOp** ops) {
+  if (integrator == 1) {
+    *ops = kSSP104;
+    return 10;
+  }
+  *ops = kRK3;
+  return 3;
+}
+
 cudaError_t launch_dt_init(DevCtl* ctls, int n, cudaStream_t st) {
   dt_init_kernel<<<(n + 127) / 128, 128, 0, st>>>(ctls, n);
   return cudaGetLastError();

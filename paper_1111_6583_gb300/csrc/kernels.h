@@ -11,6 +11,7 @@ namespace claw {
 struct Member;
 struct Tile;
 struct DevCtl;
+struct StageOp;
 
 struct LaunchArgs {
   const Member* members;   // device array
@@ -19,12 +20,16 @@ struct LaunchArgs {
   const void* consts;      // host pointer to MConsts<R>
   int bw;                  // 2D classic: threads per block (strip width + 4)
   int h;                   // 2D classic: rows per block
-  int stage;               // SharpClaw stage 0..2
+  int stage;               // SharpClaw SSP-RK3 stage 0..2 (used when stage_op is null)
   cudaStream_t stream;
   int n3[3];               // 3D: cells per direction
   void* work3;             // 3D: per-face arrays (device)
   size_t work3_bytes;
+  const StageOp* stage_op; // SharpClaw: explicit stage (host pointer) or null
 };
+
+// stage tables of the SharpClaw time integrators
+int stage_table(int integrator, const StageOp** ops);  // returns the number of stages
 
 typedef cudaError_t (*launch_fn)(const LaunchArgs&);
 

@@ -93,14 +93,24 @@ struct Launchers {
     if constexpr (ND == 3) {
       (void)C;
       return cudaErrorNotSupported;
-    } else if constexpr (ND == 1) {
-      sharp_stage_kernel<RP, R, 1, kSharpTX1, 1>
-          <<<launch_grid(a.ntiles_total), kSharpTX1, 0, a.stream>>>(a.members, a.tiles,
-                                                                 a.ntiles_total, C, a.stage);
     } else {
-      sharp_stage_kernel<RP, R, 2, kSharpTX2, kSharpTY2>
-          <<<launch_grid(a.ntiles_total), kSharpTX2 * kSharpTY2, 0, a.stream>>>(
-              a.members, a.tiles, a.ntiles_total, C, a.stage);
+      StageOp op;
+      if (a.stage_op) {
+        op = *a.stage_op;
+      } else {
+        const StageOp* rk3;
+        stage_table(0, &rk3);
+        op = rk3[a.stage];
+      }
+      if constexpr (ND == 1) {
+        sharp_stage_kernel<RP, R, 1, kSharpTX1, 1>
+            <<<launch_grid(a.ntiles_total), kSharpTX1, 0, a.stream>>>(a.members, a.tiles,
+                                                                   a.ntiles_total, C, op);
+      } else {
+        sharp_stage_kernel<RP, R, 2, kSharpTX2, kSharpTY2>
+            <<<launch_grid(a.ntiles_total), kSharpTX2 * kSharpTY2, 0, a.stream>>>(
+                a.members, a.tiles, a.ntiles_total, C, op);
+      }
     }
     return cudaGetLastError();
   }

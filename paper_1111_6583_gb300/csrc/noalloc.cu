@@ -160,6 +160,7 @@ claw_status claw_sharp_step_noalloc(const claw_method* m, const claw_grid* g, co
   c.dx[1] = g->ndim == 2 ? (g->upper[1] - g->lower[1]) / (double)ny : 1.0;
   c.max_steps = 0x7fffffffffffffffLL;
   c.nbuf = 3;
+  c.accept_shift = 1;
   c.forced = 1;
   c.ndim = g->ndim;
   // stages 0 and 1: Q^n -> Q1 -> Q2 in scratch; stage 2 reads Q2, writes q_out

@@ -45,7 +45,7 @@ __device__ __forceinline__ R weno5(R a, R b, R c, R d, R e, R eps) {
 template <class RP, typename R, int ND, int TX, int TY>
 __global__ void __launch_bounds__(TX * TY)
     sharp_stage_kernel(const Member* __restrict__ members, const Tile* __restrict__ tiles,
-                       int ntiles_total, const MConsts<R> C, int stage) {
+                       int ntiles_total, const MConsts<R> C, const StageOp op) {
   constexpr int M = RP::M, MW = RP::MW, MA = RP::MA, NC = RP::NCTX;
   constexpr int MAS = MA > 0 ? MA : 1;
   constexpr int NT = TX * TY;
@@ -88,11 +88,11 @@ __global__ void __launch_bounds__(TX * TY)
     const int r0 = (ND == 2) ? (tl.tile / nsx) * TY : 0;
     const int cur = s_cur;
     const int nb = s_nbuf;
-    const int in_b = (stage == 0) ? cur : (stage == 1 ? (cur + 1) % nb : (cur + 2) % nb);
-    const int out_b = (stage == 1) ? (cur + 2) % nb : (cur + 1) % nb;
-    const R* __restrict__ qk = (const R*)mb.q[in_b];
-    const R* __restrict__ qn = (const R*)mb.q[cur];
-    R* __restrict__ qo = (R*)mb.q[out_b];
+    const R* __restrict__ qk = (const R*)mb.q[(cur + op.in) % nb];
+    const R* __restrict__ qa = (const R*)mb.q[(cur + op.sa) % nb];
+    const R* __restrict__ qb = (const R*)mb.q[(cur + op.sb) % nb];
+    R* __restrict__ qo = (R*)mb.q[(cur + op.out) % nb];
+    R* __restrict__ qo2 = op.out2 >= 0 ? (R*)mb.q[(cur + op.out2) % nb] : nullptr;
     const R* __restrict__ aux = (const R*)mb.aux;
     const size_t plane = (size_t)nx * ny;
 
@@ -254,26 +254,30 @@ __global__ void __launch_bounds__(TX * TY)
       __syncthreads();
     }
 
-    // (d) Shu-Osher stage combination
+    // (d) Runge-Kutta stage combination: v = Q^(k) + g dt L, then up to two
+    // linear combinations with earlier states
     int bad = 0;
     {
       const int c = c0 + ti, r = r0 + tj;
       if (c < nx && r < ny) {
         const size_t off = (size_t)r * nx + c;
-        const R dt = s_dt;
+        const R gdt = (R)op.g * s_dt;
+        const R a0 = (R)op.a0, a1 = (R)op.a1, b0 = (R)op.b0, b1 = (R)op.b1;
 #pragma unroll
         for (int k = 0; k < M; ++k) {
           const R qkv = Qt[k][(ND == 2) ? G + tj : 0][G + ti];
-          R v;
-          if (stage == 0) v = qkv + dt * L[k];
-          else if (stage == 1) v = R(0.75) * qn[k * plane + off] + R(0.25) * (qkv + dt * L[k]);
-          else v = (R(1) / R(3)) * qn[k * plane + off] + (R(2) / R(3)) * (qkv + dt * L[k]);
-          bad |= !isfinite(v);
-          qo[k * plane + off] = v;
+          const R v = qkv + gdt * L[k];
+          const R o = (op.a0 != 0.0) ? a0 * qa[k * plane + off] + a1 * v : a1 * v;
+          bad |= !isfinite(o);
+          qo[k * plane + off] = o;
+          if (qo2) {
+            const R o2 = (op.b0 != 0.0) ? b0 * qb[k * plane + off] + b1 * v : b1 * v;
+            qo2[k * plane + off] = o2;
+          }
         }
       }
     }
-    finish_attempt<R>(ctl, smx, smy, bad, mb.ntiles, stage == 2);
+    finish_attempt<R>(ctl, smx, smy, bad, mb.ntiles, op.last != 0);
   }
 }
 
