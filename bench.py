@@ -76,7 +76,9 @@ def recorded_traffic():
 def record_traffic(csv_path):
     """Write the traffic record from an ncu --csv launch list of the bench
     command (metrics dram__bytes_read.sum, dram__bytes_write.sum; the last
-    `steps` classic2d launches are the timed ones)."""
+    four classic2d launches of `--case sw2d1024` are its four steps; ncu
+    flushes the caches before each launch it captures, so these are the
+    bytes of a launch that starts with a cold L2, as the timed steps do)."""
     import csv
     rows = list(csv.reader(open(csv_path)))
     hi = [i for i, r in enumerate(rows) if "Kernel Name" in r][0]
@@ -90,11 +92,10 @@ def record_traffic(csv_path):
     b = sum(v["dram__bytes_read.sum"] + v["dram__bytes_write.sum"] for v in timed) / len(timed)
     rec = {"kernel": "classic2d_kernel<RpSW<double,2>>", "workload": "dam break 1024x1024 FP64",
            "dram_bytes_per_launch": b, "sources_sha256": kernel_sha(),
-           "command": "python bench.py --steps 4 --warmup 3 --no-extras > gpurun_out/plain.log "
-                      "2>&1 && ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,"
+           "command": "python bench.py --case sw2d1024 > gpurun_out/plain.log 2>&1 && "
+                      "ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,"
                       "dram__bytes_write.sum --clock-control none -k regex:classic2d --csv "
-                      "--log-file gpurun_out/traffic_sw2d.csv python bench.py --steps 4 "
-                      "--warmup 3 --no-extras"}
+                      "--log-file gpurun_out/traffic_sw2d.csv python bench.py --case sw2d1024"}
     json.dump(rec, open(TRAFFIC_RECORD, "w"), indent=1)
     print(json.dumps(rec))
 
@@ -424,7 +425,8 @@ def profile_case(case):
     """A short fixed launch sequence of one kernel for ncu captures (untimed):
     sw2d64/sw2d32 -- 2048^2 dam break, autotune (40 launches) then 3 steps;
     elast -- 1024-member FP32 elasticity batch, 5 fused steps;
-    sharp -- 1024x512 shock-bubble FP64, 2 SharpClaw steps (6 stage launches)."""
+    sharp -- 1024x512 shock-bubble FP64, 2 SharpClaw steps (6 stage launches);
+    sw2d1024 -- the headline 1024^2 FP64 dam break, autotune then 4 steps."""
     import torch
     from paper_1111_6583_gb300 import claw
     from paper_1111_6583_gb300 import workloads as wl
@@ -433,6 +435,11 @@ def profile_case(case):
         print("tile", s.tune())
         s.set_t_end(1.5)
         s.advance(3)
+    elif case == "sw2d1024":
+        s = claw.Solver(wl.sw_dambreak_2d(n=1024), "fp64")
+        print("tile", s.tune())
+        s.set_t_end(1.5)
+        s.advance(4)
     elif case == "elast":
         ens = wl.elasticity_ensemble(1024)
         b = claw.Batch([wl.elasticity_member(e["n"], e["amp"], e["width"]) for e in ens], "fp32")
