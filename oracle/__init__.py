@@ -22,6 +22,8 @@ import subprocess
 
 import numpy as np
 
+from .weno_coeffs import weno_tables
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liboracle.so")
 _SRC = os.path.join(_HERE, "oracle.c")
@@ -63,6 +65,10 @@ class _Prob(ctypes.Structure):
         ("max_retries", ctypes.c_int), ("weno_eps", ctypes.c_double),
         ("nz", ctypes.c_int), ("dz", ctypes.c_double),
         ("time_integrator", ctypes.c_int),
+        ("weno_r", ctypes.c_int),
+        ("weno_c", ctypes.c_double * 81),
+        ("weno_d", ctypes.c_double * 9),
+        ("weno_b", ctypes.c_double * 729),
     ]
 
 
@@ -90,6 +96,8 @@ def _load():
         lib.orc_phi.argtypes = [ctypes.c_int, ctypes.c_double]
         lib.orc_weno5.restype = ctypes.c_double
         lib.orc_weno5.argtypes = [_dp, ctypes.c_double]
+        lib.orc_weno_r.restype = ctypes.c_double
+        lib.orc_weno_r.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp, ctypes.c_double]
         lib.orc_char_matrices.argtypes = [P, ctypes.c_int, _dp, _dp, _dp, _dp]
         lib.orc_fill_ghost.argtypes = [P, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
         lib.orc_classic_step.argtypes = [P, _dp, _dp, ctypes.c_double, _dp]
@@ -169,6 +177,15 @@ def make_problem(spec: dict):
     p.max_retries = int(spec.get("max_retries", 8))
     p.weno_eps = float(spec.get("weno_eps", 1e-6))
     p.time_integrator = {"ssp_rk3": 0, "ssp104": 1}[spec.get("time_integrator", "ssp_rk3")]
+    order = int(spec.get("weno_order", 5))
+    if order % 2 == 0 or not 5 <= order <= 17:
+        raise ValueError("weno_order must be odd, 5..17")
+    p.weno_r = (order + 1) // 2
+    if p.weno_r > 3:
+        cf, df, bf = weno_tables(p.weno_r)
+        p.weno_c[:len(cf)] = cf
+        p.weno_d[:len(df)] = df
+        p.weno_b[:len(bf)] = bf
     return p
 
 
@@ -211,6 +228,18 @@ def transverse(p, direction, ql, qr, asdq, auxl=None, auxr=None):
 
 def phi(lim: str, theta: float) -> float:
     return _load().orc_phi(LIM[lim], float(theta))
+
+
+def weno_r(r, v, eps=1e-6) -> float:
+    """WENO of order 2r-1: left-biased value at the right edge of the centre
+    cell of v[0..2r-2], coefficients from oracle.weno_coeffs."""
+    cf, df, bf = weno_tables(r)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    assert v.shape == (2 * r - 1,)
+    c = np.array(cf)
+    d = np.array(df)
+    b = np.array(bf)
+    return _load().orc_weno_r(int(r), _ptr(c), _ptr(d), _ptr(b), _ptr(v), float(eps))
 
 
 def weno5(v, eps=1e-6) -> float:

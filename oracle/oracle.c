@@ -1079,13 +1079,41 @@ double orc_weno5(const double* v, double eps) {
   return (a0 * q0 + a1 * q1 + a2 * q2) / sum;
 }
 
+/* WENO of order 2r-1 (Jiang-Shu weights d_k / (eps + beta_k)^2 normalised to
+ * sum 1): candidate values q_k = sum_j c[k][j] v[k+j], smoothness beta_k =
+ * v_k^T B[k] v_k over the stencil's r cells. */
+double orc_weno_r(int r, const double* c, const double* d, const double* B, const double* v,
+                  double eps) {
+  double qk[9], alpha[9], sum = 0.0;
+  for (int k = 0; k < r; ++k) {
+    double q = 0.0, beta = 0.0;
+    for (int j = 0; j < r; ++j) q += c[k * r + j] * v[k + j];
+    for (int a = 0; a < r; ++a)
+      for (int b = 0; b < r; ++b) beta += B[(k * r + a) * r + b] * v[k + a] * v[k + b];
+    qk[k] = q;
+    alpha[k] = d[k] / ((eps + beta) * (eps + beta));
+    sum += alpha[k];
+  }
+  double out = 0.0;
+  for (int k = 0; k < r; ++k) out += (alpha[k] / sum) * qk[k];
+  return out;
+}
+
+/* left-biased edge value of the problem's WENO order from v[0..2r-2] */
+static double weno_edge(const orc_prob* P, int r, const double* v) {
+  if (r == 3) return orc_weno5(v, P->weno_eps);
+  return orc_weno_r(r, P->weno_c, P->weno_d, P->weno_b, v, P->weno_eps);
+}
+
 int orc_sharp_L(const orc_prob* P, const double* q, const double* aux, double* L, double* smax) {
   int m = P->num_eqn, ma = P->num_aux;
   int nx = P->nx, ny = (P->ndim == 2) ? P->ny : 1;
   size_t ncell = (size_t)nx * ny;
+  const int r = P->weno_r > 3 ? P->weno_r : 3;  /* ghost width and stencil half-width */
+  if (r > 9) return ORC_EINVAL;
   garr Q, A;
-  double* qb = ghosted(P, q, m, 3, 0, &Q);
-  double* ab = ghosted(P, aux, ma, 3, 1, &A);
+  double* qb = ghosted(P, q, m, r, 0, &Q);
+  double* ab = ghosted(P, aux, ma, r, 1, &A);
   if (P->char_decomp && P->rp == ORC_RP_ELASTICITY_FWAVE) { free(qb); free(ab); return ORC_EINVAL; }
   for (size_t c = 0; c < ncell * m; ++c) L[c] = 0.0;
   smax[0] = 0.0; smax[1] = 0.0;
@@ -1103,31 +1131,32 @@ int orc_sharp_L(const orc_prob* P, const double* q, const double* aux, double* L
       double sm = 0.0;
       /* reconstruction at every interface i - 1/2, i = 0..n */
       for (int i = 0; i <= n; ++i) {
-        double cells[6][MAXM], w[6][MAXM];
+        /* the 2r cells i-r .. i+r-1 around interface i - 1/2 */
+        double cells[18][MAXM], w[18][MAXM];
         double Lm[MAXM * MAXM], Rm[MAXM * MAXM];
-        for (int k6 = 0; k6 < 6; ++k6) {
-          int ci = i - 3 + k6;
+        for (int k6 = 0; k6 < 2 * r; ++k6) {
+          int ci = i - r + k6;
           if (dir == 0) gcell(&Q, ci, l, cells[k6]); else gcell(&Q, l, ci, cells[k6]);
         }
         if (P->char_decomp) {
-          orc_char_matrices(P, dir, cells[2], cells[3], Lm, Rm);
-          for (int k6 = 0; k6 < 6; ++k6)
+          orc_char_matrices(P, dir, cells[r - 1], cells[r], Lm, Rm);
+          for (int k6 = 0; k6 < 2 * r; ++k6)
             for (int p = 0; p < m; ++p) {
               double acc = 0.0;
               for (int k = 0; k < m; ++k) acc += Lm[p * m + k] * cells[k6][k];
               w[k6][p] = acc;
             }
         } else {
-          for (int k6 = 0; k6 < 6; ++k6)
+          for (int k6 = 0; k6 < 2 * r; ++k6)
             for (int p = 0; p < m; ++p) w[k6][p] = cells[k6][p];
         }
         double wm[MAXM], wp[MAXM];
         for (int p = 0; p < m; ++p) {
-          double v[5];
-          for (int k = 0; k < 5; ++k) v[k] = w[k][p];        /* cells i-3..i+1 */
-          wm[p] = orc_weno5(v, P->weno_eps);                  /* right edge of cell i-1 */
-          for (int k = 0; k < 5; ++k) v[k] = w[5 - k][p];    /* cells i+2..i-2 */
-          wp[p] = orc_weno5(v, P->weno_eps);                  /* left edge of cell i */
+          double v[17];
+          for (int k = 0; k < 2 * r - 1; ++k) v[k] = w[k][p];          /* cells i-r..i+r-2 */
+          wm[p] = weno_edge(P, r, v);                                   /* right edge of cell i-1 */
+          for (int k = 0; k < 2 * r - 1; ++k) v[k] = w[2 * r - 1 - k][p]; /* cells i+r-1..i-r+1 */
+          wp[p] = weno_edge(P, r, v);                                   /* left edge of cell i */
         }
         for (int k = 0; k < m; ++k) {
           if (P->char_decomp) {

@@ -56,6 +56,11 @@ typedef struct {
   int nz;               /* 3D: cells in z (1 otherwise) */
   double dz;            /* 3D: cell width in z */
   int time_integrator;  /* SharpClaw: 0 SSP-RK3 (Shu-Osher), 1 SSP(10,4) (Ketcheson 2008) */
+  int weno_r;           /* SharpClaw: WENO order 2r-1; 0 or 3 = WENO5 (Jiang-Shu) */
+  /* for weno_r > 3: coefficients from their definitions (oracle/weno_coeffs.py):
+   * weno_c[k*r+j] reconstruction, weno_d[k] optimal weights,
+   * weno_b[(k*r+a)*r+b] smoothness quadratic forms */
+  double weno_c[81], weno_d[9], weno_b[729];
 } orc_prob;
 
 typedef struct {
@@ -86,6 +91,10 @@ void orc_transverse(const orc_prob* P, int dir, const double* ql, const double* 
 double orc_phi(int lim, double theta);
 /* WENO5 left-biased value at x_{i+1/2} from v[0..4] = v_{i-2..i+2} */
 double orc_weno5(const double* v, double eps);
+/* WENO of order 2r-1: left-biased value at x_{i+1/2} from v[0..2r-2] =
+ * v_{i-r+1..i+r-1}, with the coefficient layout of orc_prob */
+double orc_weno_r(int r, const double* c, const double* d, const double* B, const double* v,
+                  double eps);
 /* characteristic matrices at the interface (ql, qr): Lmat (meqn x meqn,
  * rows = left eigenvectors), Rmat (columns = right eigenvectors), row-major. */
 int orc_char_matrices(const orc_prob* P, int dir, const double* ql, const double* qr,
