@@ -1081,7 +1081,9 @@ double orc_weno5(const double* v, double eps) {
 
 /* WENO of order 2r-1 (Jiang-Shu weights d_k / (eps + beta_k)^2 normalised to
  * sum 1): candidate values q_k = sum_j c[k][j] v[k+j], smoothness beta_k =
- * v_k^T B[k] v_k over the stencil's r cells. */
+ * v_k^T B[k] v_k over the stencil's r cells.  beta measures derivatives only,
+ * so it is unchanged when a constant is subtracted from the data; the form is
+ * evaluated on v - v[k] to keep its rounding relative to the variation. */
 double orc_weno_r(int r, const double* c, const double* d, const double* B, const double* v,
                   double eps) {
   double qk[9], alpha[9], sum = 0.0;
@@ -1089,7 +1091,8 @@ double orc_weno_r(int r, const double* c, const double* d, const double* B, cons
     double q = 0.0, beta = 0.0;
     for (int j = 0; j < r; ++j) q += c[k * r + j] * v[k + j];
     for (int a = 0; a < r; ++a)
-      for (int b = 0; b < r; ++b) beta += B[(k * r + a) * r + b] * v[k + a] * v[k + b];
+      for (int b = 0; b < r; ++b)
+        beta += B[(k * r + a) * r + b] * (v[k + a] - v[k]) * (v[k + b] - v[k]);
     qk[k] = q;
     alpha[k] = d[k] / ((eps + beta) * (eps + beta));
     sum += alpha[k];
