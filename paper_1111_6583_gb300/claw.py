@@ -194,6 +194,7 @@ def method_from_spec(spec, prec="fp64") -> claw_method:
     m.dt_initial = float(spec.get("dt_initial", 0.0))
     m.dt_max = float(spec.get("dt_max", 1e30))
     m.weno_eps = float(spec.get("weno_eps", 1e-6))
+    m.weno_order = int(spec.get("weno_order", 5))
     m.time_integrator = TIME_INTEGRATOR[spec.get("time_integrator", "ssp_rk3")]
     bl = list(spec.get("bc_lower", ["periodic"] * ndim)) + ["periodic"] * 2
     bh = list(spec.get("bc_upper", ["periodic"] * ndim)) + ["periodic"] * 2

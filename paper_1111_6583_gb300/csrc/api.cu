@@ -57,6 +57,7 @@ void fill_consts(const claw_method& m, MConsts<R>& C) {
   C.gamma = (R)m.params[0];
   C.gm1 = (R)(m.params[0] - 1.0);
   C.weno_eps = (R)m.weno_eps;
+  C.weno_r = (m.weno_order + 1) / 2;
   C.lim = m.lim;
   C.order = m.order;
   C.transverse = m.transverse;
@@ -106,7 +107,9 @@ const char* check_method(const claw_method& m, int nd) {
   if (m.lim < 0 || m.lim > 4) return "unknown limiter";
   if (m.scheme == CLAW_CLASSIC && m.order != 1 && m.order != 2) return "order must be 1 or 2";
   if (m.transverse < 0 || m.transverse > 2) return "transverse must be 0, 1 or 2";
-  if (m.scheme == CLAW_SHARPCLAW && m.weno_order != 5) return "weno_order must be 5";
+  if (m.scheme == CLAW_SHARPCLAW && m.weno_order != 5 && m.weno_order != 7 &&
+      m.weno_order != 9)
+    return "weno_order must be 5, 7 or 9";
   if (m.scheme == CLAW_SHARPCLAW && m.time_integrator != CLAW_SSP_RK3 &&
       m.time_integrator != CLAW_SSP104)
     return "unknown time integrator";
@@ -129,10 +132,12 @@ const char* check_method(const claw_method& m, int nd) {
   return nullptr;
 }
 
-const char* check_grid(const claw_grid& g) {
+const char* check_grid(const claw_grid& g, const claw_method& m) {
   if (g.ndim < 1 || g.ndim > 3) return "ndim must be 1, 2 or 3";
+  // the ghost layer (WENO half-width for SharpClaw) must fit in the grid
+  const int need = m.scheme == CLAW_SHARPCLAW ? std::max(4, (m.weno_order + 1) / 2) : 4;
   for (int d = 0; d < g.ndim; ++d) {
-    if (g.n[d] < 4) return "each direction needs at least 4 cells";
+    if (g.n[d] < need) return "too few cells in a direction for the ghost layer";
     if (g.n[d] > (int64_t)INT_MAX / 2) return "too many cells in one direction";
     if (!(g.upper[d] > g.lower[d])) return "upper must exceed lower";
   }
@@ -485,7 +490,7 @@ claw_status claw_solver_create(const claw_method* m, const claw_grid* g, void* s
                                claw_solver** out) {
   if (!m || !g || !out) return fail(nullptr, "null argument");
   *out = nullptr;
-  if (const char* why = check_grid(*g)) return fail(nullptr, why);
+  if (const char* why = check_grid(*g, *m)) return fail(nullptr, why);
   if (const char* why = check_method(*m, g->ndim)) return fail(nullptr, why);
   KernelSet ks = kernels_for(m->rp, g->ndim, m->prec);
   if (!ks.valid) return fail(nullptr, "no kernels for this solver/dimension/precision");
@@ -894,7 +899,7 @@ claw_status claw_batch_create(const claw_method* m, const claw_grid* grids, int 
   const int nd = grids[0].ndim;
   if (nd == 3) return bfail(nullptr, "batches take 1D or 2D grids");
   for (int k = 0; k < n; ++k) {
-    if (const char* why = check_grid(grids[k])) return bfail(nullptr, why);
+    if (const char* why = check_grid(grids[k], *m)) return bfail(nullptr, why);
     if (grids[k].ndim != nd) return bfail(nullptr, "all members need the same ndim");
   }
   if (const char* why = check_method(*m, nd)) return bfail(nullptr, why);
@@ -1208,7 +1213,7 @@ claw_status claw_server_submit(claw_server* v, const claw_grid* g, const void* q
                                const void* aux_host, double t_end, uint64_t* ticket) {
   if (!v || !g || !q0_host || !ticket) return sfail(v, "bad argument");
   if (g->ndim != v->nd) return sfail(v, "grid dimension does not match the server's method");
-  if (const char* why = check_grid(*g)) return sfail(v, why);
+  if (const char* why = check_grid(*g, v->m)) return sfail(v, why);
   if (v->m.num_aux > 0 && !aux_host) return sfail(v, "this solver needs aux fields");
   Req r;
   r.ticket = v->next_ticket++;

@@ -78,6 +78,7 @@ struct MConsts {
   R g;             // shallow water gravity
   R gamma, gm1;    // Euler
   R weno_eps;
+  int weno_r;      // SharpClaw: WENO order 2 weno_r - 1 (0 means 3, WENO5)
   int lim, order, transverse, entropy_fix, char_decomp;
   int bc_lo[3], bc_hi[3];
 };

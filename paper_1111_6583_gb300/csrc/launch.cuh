@@ -102,17 +102,27 @@ struct Launchers {
         stage_table(0, &rk3);
         op = rk3[a.stage];
       }
-      if constexpr (ND == 1) {
-        sharp_stage_kernel<RP, R, 1, kSharpTX1, 1>
-            <<<launch_grid(a.ntiles_total), kSharpTX1, 0, a.stream>>>(a.members, a.tiles,
-                                                                   a.ntiles_total, C, op);
-      } else {
-        sharp_stage_kernel<RP, R, 2, kSharpTX2, kSharpTY2>
-            <<<launch_grid(a.ntiles_total), kSharpTX2 * kSharpTY2, 0, a.stream>>>(
-                a.members, a.tiles, a.ntiles_total, C, op);
+      switch (C.weno_r) {
+        case 0:
+        case 3: sharp_launch<3>(a, C, op); break;
+        case 4: sharp_launch<4>(a, C, op); break;
+        case 5: sharp_launch<5>(a, C, op); break;
+        default: return cudaErrorInvalidValue;
       }
     }
     return cudaGetLastError();
+  }
+  template <int RW>
+  static void sharp_launch(const LaunchArgs& a, const MConsts<R>& C, const StageOp& op) {
+    if constexpr (ND == 1) {
+      sharp_stage_kernel<RP, R, 1, kSharpTX1, 1, RW>
+          <<<launch_grid(a.ntiles_total), kSharpTX1, 0, a.stream>>>(a.members, a.tiles,
+                                                                 a.ntiles_total, C, op);
+    } else if constexpr (ND == 2) {
+      sharp_stage_kernel<RP, R, 2, kSharpTX2, kSharpTY2, RW>
+          <<<launch_grid(a.ntiles_total), kSharpTX2 * kSharpTY2, 0, a.stream>>>(
+              a.members, a.tiles, a.ntiles_total, C, op);
+    }
   }
   static cudaError_t maxspeed(const LaunchArgs& a) {
     const MConsts<R>& C = *(const MConsts<R>*)a.consts;

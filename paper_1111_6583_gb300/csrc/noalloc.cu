@@ -119,6 +119,7 @@ claw_status claw_sharp_step_noalloc(const claw_method* m, const claw_grid* g, co
   if (g->ndim != 1 && g->ndim != 2) return nfail("ndim must be 1 or 2");
   const int nx = (int)g->n[0], ny = g->ndim == 2 ? (int)g->n[1] : 1;
   if (g->n[0] < 4 || (g->ndim == 2 && g->n[1] < 4)) return nfail("each direction needs >= 4 cells");
+  if (m->weno_order != 5) return nfail("the allocation-free step takes WENO5 only");
   if (!(dt > 0)) return nfail("dt must be positive");
   if (m->num_aux > 0 && !aux) return nfail("this solver needs aux fields");
   if (m->char_decomp && m->rp == CLAW_RP_ELASTICITY_FWAVE)

@@ -1,21 +1,21 @@
 // sharpclaw.cuh -- fused SharpClaw stage kernel (Sec. 3 method of lines;
 // Sec. 3.1: WENO reconstruction, normal Riemann problems only in multi-D).
 //
-// One launch = one SSP-RK3 stage for every member of a tile table.  A block
-// stages a TX x TY tile of Q^(k) plus a 3-cell halo (ghost remap in the load),
-// reconstructs left/right interface values by WENO5 (component- or
+// One launch = one Runge-Kutta stage for every member of a tile table.  A
+// block stages a TX x TY tile of Q^(k) plus an RW-cell halo (ghost remap in
+// the load), reconstructs left/right interface values by WENO of order
+// 2 RW - 1 (component- or
 // characteristic-wise, projection at the Roe state of each interface), solves
 // the interface Riemann problems and the in-cell problems (total fluctuation
 // A dQ_i), forms L(Q) = -(A^+dQ_{i-1/2} + A^-dQ_{i+1/2} + A dQ_i)/dx summed
-// over directions, and writes the Shu-Osher combination
-//   stage 0: Q1 = Q + dt L(Q)
-//   stage 1: Q2 = 3/4 Q + 1/4 (Q1 + dt L(Q1))
-//   stage 2: Q3 = 1/3 Q + 2/3 (Q2 + dt L(Q2))
-// Stage 2's last block runs the CFL controller.
+// over directions, and writes the stage's linear combinations (StageOp: the
+// Shu-Osher SSP-RK3 or the low-storage SSP(10,4) stages).  The last stage's
+// last block runs the CFL controller.
 #pragma once
 
 #include "kernels.h"
 #include "riemann.cuh"
+#include "weno_hi.cuh"
 
 namespace claw {
 
@@ -41,15 +41,29 @@ __device__ __forceinline__ R weno5(R a, R b, R c, R d, R e, R eps) {
   return FM<R>::div(w0 * q0 + w1 * q1 + w2 * q2, w0 + w1 + w2);
 }
 
+// WENO of order 2 RW - 1: left-biased value at the right edge of cell
+// v[o + RW - 1] from v[o .. o + 2 RW - 2] (REV: the mirrored stencil, value at
+// the left edge of cell v[o + RW], read from v[o + 2 RW - 1] downwards).
+template <int RW, bool REV, typename R, int NV>
+__device__ __forceinline__ R weno_edge(const R (&w)[NV], R eps) {
+  constexpr int n = 2 * RW - 1;
+  R v[n];
+#pragma unroll
+  for (int j = 0; j < n; ++j) v[j] = REV ? w[n - j] : w[j];
+  if constexpr (RW == 3) return weno5<R>(v[0], v[1], v[2], v[3], v[4], eps);
+  else if constexpr (RW == 4) return weno7<R>(v, eps);
+  else return weno9<R>(v, eps);
+}
 
-template <class RP, typename R, int ND, int TX, int TY>
+template <class RP, typename R, int ND, int TX, int TY, int RW>
 __global__ void __launch_bounds__(TX * TY)
     sharp_stage_kernel(const Member* __restrict__ members, const Tile* __restrict__ tiles,
                        int ntiles_total, const MConsts<R> C, const StageOp op) {
   constexpr int M = RP::M, MW = RP::MW, MA = RP::MA, NC = RP::NCTX;
   constexpr int MAS = MA > 0 ? MA : 1;
   constexpr int NT = TX * TY;
-  constexpr int G = 3;
+  constexpr int G = RW;        // ghost / halo width
+  constexpr int NS = 2 * RW;   // cells around an interface
   constexpr int HX = TX + 2 * G, HY = (ND == 2) ? TY + 2 * G : 1;
   constexpr int NE = (ND == 2) ? ((TX + 1) * TY > TX * (TY + 1) ? (TX + 1) * TY : TX * (TY + 1))
                                : TX + 1;
@@ -96,7 +110,7 @@ __global__ void __launch_bounds__(TX * TY)
     const R* __restrict__ aux = (const R*)mb.aux;
     const size_t plane = (size_t)nx * ny;
 
-    // stage Q^(k) (and aux) with a 3-cell halo, corners skipped in 2D
+    // stage Q^(k) (and aux) with a G-cell halo, corners skipped in 2D
     for (int idx = tid; idx < HX * HY; idx += NT) {
       const int hi = idx % HX, hj = idx / HX;
       if (ND == 2) {
@@ -133,10 +147,10 @@ __global__ void __launch_bounds__(TX * TY)
       // (a) reconstruction at every interface
       for (int e = tid; e < na * nl; e += NT) {
         const int a = e % na, b = e / na;
-        R cell[6][M];
+        R cell[NS][M];
 #pragma unroll
-        for (int k6 = 0; k6 < 6; ++k6) {
-          // cells a-3 .. a+2 along the line
+        for (int k6 = 0; k6 < NS; ++k6) {
+          // cells a-RW .. a+RW-1 along the line
           const int hi = (dir == 0) ? a + k6 : G + b;
           const int hj = (dir == 0) ? ((ND == 2) ? G + b : 0) : a + k6;
 #pragma unroll
@@ -145,21 +159,24 @@ __global__ void __launch_bounds__(TX * TY)
         R wm[M], wp[M];
         if (C.char_decomp) {
           R x[NC];
-          R w[6][M];
+          R w[NS][M];
           if (dir == 0) {
-            RP::template char_ctx<0>(C, cell[2], cell[3], x);
+            RP::template char_ctx<0>(C, cell[RW - 1], cell[RW], x);
 #pragma unroll
-            for (int k6 = 0; k6 < 6; ++k6) RP::template to_char<0>(C, x, cell[k6], w[k6]);
+            for (int k6 = 0; k6 < NS; ++k6) RP::template to_char<0>(C, x, cell[k6], w[k6]);
           } else {
-            RP::template char_ctx<1>(C, cell[2], cell[3], x);
+            RP::template char_ctx<1>(C, cell[RW - 1], cell[RW], x);
 #pragma unroll
-            for (int k6 = 0; k6 < 6; ++k6) RP::template to_char<1>(C, x, cell[k6], w[k6]);
+            for (int k6 = 0; k6 < NS; ++k6) RP::template to_char<1>(C, x, cell[k6], w[k6]);
           }
           R um[M], up[M];
 #pragma unroll
           for (int k = 0; k < M; ++k) {
-            um[k] = weno5<R>(w[0][k], w[1][k], w[2][k], w[3][k], w[4][k], C.weno_eps);
-            up[k] = weno5<R>(w[5][k], w[4][k], w[3][k], w[2][k], w[1][k], C.weno_eps);
+            R line[NS];
+#pragma unroll
+            for (int k6 = 0; k6 < NS; ++k6) line[k6] = w[k6][k];
+            um[k] = weno_edge<RW, false>(line, C.weno_eps);
+            up[k] = weno_edge<RW, true>(line, C.weno_eps);
           }
           if (dir == 0) {
             RP::template from_char<0>(C, x, um, wm);
@@ -171,8 +188,11 @@ __global__ void __launch_bounds__(TX * TY)
         } else {
 #pragma unroll
           for (int k = 0; k < M; ++k) {
-            wm[k] = weno5<R>(cell[0][k], cell[1][k], cell[2][k], cell[3][k], cell[4][k], C.weno_eps);
-            wp[k] = weno5<R>(cell[5][k], cell[4][k], cell[3][k], cell[2][k], cell[1][k], C.weno_eps);
+            R line[NS];
+#pragma unroll
+            for (int k6 = 0; k6 < NS; ++k6) line[k6] = cell[k6][k];
+            wm[k] = weno_edge<RW, false>(line, C.weno_eps);
+            wp[k] = weno_edge<RW, true>(line, C.weno_eps);
           }
         }
 #pragma unroll

@@ -59,7 +59,7 @@ def test_method_init_and_validation_without_gpu(lib_path):
     h = ctypes.c_void_p()
     assert lib.claw_solver_create(ctypes.byref(m), ctypes.byref(g), None,
                                   ctypes.byref(h)) == claw.CLAW_EINVAL
-    assert b"at least 4" in lib.claw_last_error(None)
+    assert b"too few cells" in lib.claw_last_error(None)
     g.n[0] = 64
     m.bc_lower[0] = claw.BC["periodic"]
     m.bc_upper[0] = claw.BC["wall"]
@@ -72,4 +72,23 @@ def test_method_init_and_validation_without_gpu(lib_path):
     g.ndim = 1
     assert lib.claw_solver_create(ctypes.byref(m), ctypes.byref(g), None,
                                   ctypes.byref(h)) == claw.CLAW_EINVAL
+    # SharpClaw options: WENO orders 5/7/9, the two SSP integrators, and a
+    # grid at least as wide as the WENO ghost layer
+    lib.claw_method_init(ctypes.byref(m), claw.RP["euler_roe"], 1)
+    m.scheme = claw.SHARPCLAW
+    g.n[0] = 64
+    m.weno_order = 11
+    assert lib.claw_solver_create(ctypes.byref(m), ctypes.byref(g), None,
+                                  ctypes.byref(h)) == claw.CLAW_EINVAL
+    assert b"weno_order" in lib.claw_last_error(None)
+    m.weno_order = 9
+    m.time_integrator = 2
+    assert lib.claw_solver_create(ctypes.byref(m), ctypes.byref(g), None,
+                                  ctypes.byref(h)) == claw.CLAW_EINVAL
+    assert b"time integrator" in lib.claw_last_error(None)
+    m.time_integrator = 1
+    g.n[0] = 4
+    assert lib.claw_solver_create(ctypes.byref(m), ctypes.byref(g), None,
+                                  ctypes.byref(h)) == claw.CLAW_EINVAL
+    assert b"too few cells" in lib.claw_last_error(None)
     assert lib.claw_version().startswith(b"clawgpu")
