@@ -32,7 +32,7 @@ int orc_num_eqn(int rp, int ndim) {
     case ORC_RP_SW_ROE: return ndim == 1 ? 2 : (ndim == 2 ? 3 : 0);
     case ORC_RP_EULER_ROE:
     case ORC_RP_EULER_HLLE: return ndim <= 2 ? ndim + 2 : 0;
-    case ORC_RP_ELASTICITY_FWAVE: return ndim == 1 ? 2 : 0;
+    case ORC_RP_ELASTICITY_FWAVE: return ndim == 1 ? 2 : (ndim == 2 ? 3 : 0);
   }
   return 0;
 }
@@ -345,19 +345,24 @@ void orc_riemann(const orc_prob* P, int dir, const double* ql, const double* qr,
       break;
     }
     case ORC_RP_ELASTICITY_FWAVE: {
-      /* sigma(eps) = exp(K eps) - 1, u = m / rho, flux f = (-u, -sigma) */
+      /* p-system (Sec. 6.3): sigma(eps) = exp(K eps) - 1, normal velocity
+       * u_n = m_n / rho, normal flux (-u_n, -sigma) in the (eps, m_n)
+       * components; the tangential momentum has no normal flux (2D) */
+      int n = comp_n(P, dir), t = comp_t(P, dir);
       double rl = auxl[0], Kl = auxl[1], rr = auxr[0], Kr = auxr[1];
       double el = exp(Kl * ql[0]), er = exp(Kr * qr[0]);
       double sigl = el - 1.0, sigr = er - 1.0;
-      double ul = ql[1] / rl, ur = qr[1] / rr;
+      double ul = ql[n] / rl, ur = qr[n] / rr;
       double cl = sqrt(Kl * el / rl), cr = sqrt(Kr * er / rr);
       double Zl = rl * cl, Zr = rr * cr;
       double d1 = ul - ur;       /* (-u_r) - (-u_l) */
       double d2 = sigl - sigr;   /* (-sigma_r) - (-sigma_l) */
       double b1 = (Zr * d1 + d2) / (Zl + Zr);
       double b2 = (Zl * d1 - d2) / (Zl + Zr);
-      wave[0] = b1; wave[1] = b1 * Zl; s[0] = -cl;
-      wave[2] = b2; wave[3] = -b2 * Zr; s[1] = cr;
+      for (int k = 0; k < 2 * m; ++k) wave[k] = 0.0;
+      wave[0] = b1; wave[n] = b1 * Zl; s[0] = -cl;
+      wave[m] = b2; wave[m + n] = -b2 * Zr; s[1] = cr;
+      (void)t;
       break;
     }
   }
@@ -795,6 +800,8 @@ static int classic3d(const orc_prob* P, double* q, double dt, double* cfl);
 
 int orc_classic_step(const orc_prob* P, double* q, const double* aux, double dt, double* cfl) {
   if (P->ndim == 1) return classic1d(P, q, aux, dt, cfl);
+  /* the 2D p-system is solved with SharpClaw only (normal solves, Sec. 6.3) */
+  if (P->ndim == 2 && P->rp == ORC_RP_ELASTICITY_FWAVE) return ORC_EINVAL;
   if (P->ndim == 3) return classic3d(P, q, dt, cfl);
   return classic2d(P, q, aux, dt, cfl);
 }

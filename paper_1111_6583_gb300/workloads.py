@@ -190,6 +190,41 @@ def elasticity_ensemble(members=4096, seed=SEED, lo_exp=12, hi_exp=16, t_end=50.
 # --------------------------------------------------------------------------
 # serving stream: 2D shallow-water humps
 # --------------------------------------------------------------------------
+def checkerboard_medium(x, y, k_hi=5.0, rho_hi=5.0):
+    """(rho, K) of the checkerboard crystal of Sec. 6.3: (1, 1) where
+    (x - floor(x) - 1/2)(y - floor(y) - 1/2) < 0, (rho_hi, k_hi) where > 0
+    (lengths in material periods)."""
+    s = (x - np.floor(x) - 0.5) * (y - np.floor(y) - 0.5)
+    hi = s > 0
+    return np.where(hi, rho_hi, 1.0), np.where(hi, k_hi, 1.0)
+
+
+def psystem_checkerboard_2d(periods=32, cells_per_period=64, amp=5.0, var=5.0, t_end=20.0,
+                            weno_order=5, integrator="ssp104", cfl=(1.0, 1.2)):
+    """2D p-system in the checkerboard medium (Sec. 6.3) at reduced size:
+    the positive quadrant [0, periods]^2, walls at x = 0 and y = 0 (the
+    problem's mirror symmetry), zero-order extrapolation at the far sides,
+    Gaussian stress pulse sigma_0 = amp exp(-(x^2 + y^2) / (2 var)) at the
+    origin, zero velocity; eps_0 = ln(1 + sigma_0) / K.  Cell centres never lie
+    on a material edge when cells_per_period is even, so the centre values
+    are the cell averages of (rho, K).  SharpClaw WENO, component-wise."""
+    assert cells_per_period % 2 == 0
+    n = periods * cells_per_period
+    c = _centers(0.0, float(periods), n)
+    Y, X = np.meshgrid(c, c, indexing="ij")
+    rho, K = checkerboard_medium(X, Y)
+    sig0 = amp * np.exp(-(X * X + Y * Y) / (2.0 * var))
+    eps0 = np.log1p(sig0) / K
+    q0 = np.stack([eps0, np.zeros_like(eps0), np.zeros_like(eps0)])
+    aux = np.stack([rho, K])
+    spec = _base(2, [n, n], [0.0, 0.0], [float(periods)] * 2, "elasticity_fwave",
+                 scheme="sharpclaw", char_decomp=0, weno_order=weno_order,
+                 time_integrator=integrator, cfl_desired=cfl[0], cfl_max=cfl[1], num_aux=2,
+                 bc_lower=["wall", "wall"], bc_upper=["extrap", "extrap"])
+    spec.update(q0=np.ascontiguousarray(q0), aux=np.ascontiguousarray(aux), t_end=t_end)
+    return spec
+
+
 def sw_humps_2d(n, humps, t_end):
     """[0,1]^2, depth 1 plus Gaussian humps (a, w, cx, cy), walls, g = 1."""
     x = _centers(0.0, 1.0, n)
@@ -259,11 +294,27 @@ def random_smooth_2d(rp, nx, ny, seed=SEED, params=None, bc="periodic", **kw):
     elif rp == "advection":
         q0 = np.stack([field(1.0)])
         params = params or [1.0, 0.5]
+    elif rp == "elasticity_fwave":
+        # checkerboard medium of period 1/4 (material edges on cell edges when
+        # 8 divides nx and ny; otherwise cells take the centre's material)
+        rho, K = checkerboard_medium(4.0 * X, 4.0 * Y, k_hi=3.0, rho_hi=2.0)
+        sig = 0.3 + field(0.1)
+        q0 = np.stack([np.log1p(sig) / K, field(0.2), field(0.2)])
+        aux = np.stack([rho, K])
+        params = []
     else:
         raise ValueError(rp)
+    if rp == "elasticity_fwave":
+        kw.setdefault("scheme", "sharpclaw")
+        kw.setdefault("char_decomp", 0)
+        kw.setdefault("num_aux", 2)
+    else:
+        aux = None
     spec = _base(2, [nx, ny], [0.0, 0.0], [1.0, 1.0], rp, params=params,
                  bc_lower=[bc, bc], bc_upper=[bc, bc], **kw)
-    spec.update(q0=np.ascontiguousarray(q0), aux=None, t_end=kw.get("t_end", 0.1))
+    spec.update(q0=np.ascontiguousarray(q0),
+                aux=np.ascontiguousarray(aux) if aux is not None else None,
+                t_end=kw.get("t_end", 0.1))
     return spec
 
 
