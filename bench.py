@@ -371,6 +371,30 @@ def bench_shockbubble(prec, steps, warmup, nx=2048, ny=1024, weno_order=5,
                            prec.upper())}
 
 
+def bench_psystem(prec, steps, warmup, periods=32, cells_per_period=64):
+    """2D p-system in the checkerboard medium (Sec. 6.3), SharpClaw WENO5
+    component-wise + SSP(10,4): one step = ten fused stage launches."""
+    import torch
+    from paper_1111_6583_gb300 import claw
+    from paper_1111_6583_gb300 import workloads as wl
+    spec = wl.psystem_checkerboard_2d(periods=periods, cells_per_period=cells_per_period)
+    n = spec["n"][0]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = claw.Solver(spec, prec, stream=stream.cuda_stream)
+        s.set_t_end(spec["t_end"])
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        s.advance(warmup)
+    stream.synchronize()
+    ms = timed_steps(s, stream, steps, flush)
+    s.close()
+    avg = sum(ms) / len(ms)
+    return {"value": n * n * len(ms) / (sum(ms) * 1e-3), "unit": UNIT, "ms_per_step": avg,
+            "workload": "2D p-system checkerboard %dx%d (%d periods, dx = 1/%d), SharpClaw "
+                        "WENO5 + SSP(10,4), %s" % (n, n, periods, cells_per_period,
+                                                   prec.upper())}
+
+
 def cpu_baseline_sw2d(n=1024, budget_s=12.0):
     """The oracle as it stands on the host cores: steps of the headline
     workload until about budget_s of CPU time."""
@@ -538,6 +562,7 @@ def main():
         line["shock_bubble"] = {p: bench_shockbubble(p, 5, 3) for p in ("fp64", "fp32")}
         line["shock_bubble"]["fp64_weno7_ssp104"] = bench_shockbubble("fp64", 3, 3, weno_order=7,
                                                                       integrator="ssp104")
+        line["psystem_checkerboard"] = {p: bench_psystem(p, 3, 3) for p in ("fp64", "fp32")}
         try:
             line["batched_elasticity"] = bench_elasticity(args.members, 100, 16)
         except Exception as ex:  # reported, not hidden

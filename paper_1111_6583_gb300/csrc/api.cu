@@ -88,7 +88,7 @@ int num_eqn(int rp, int nd) {
     case CLAW_RP_SW_ROE: return nd <= 2 ? nd + 1 : 0;
     case CLAW_RP_EULER_ROE:
     case CLAW_RP_EULER_HLLE: return nd <= 2 ? nd + 2 : 0;
-    case CLAW_RP_ELASTICITY_FWAVE: return nd == 1 ? 2 : 0;
+    case CLAW_RP_ELASTICITY_FWAVE: return nd <= 2 ? nd + 1 : 0;
   }
   return 0;
 }
@@ -115,6 +115,8 @@ const char* check_method(const claw_method& m, int nd) {
     return "unknown time integrator";
   if (m.scheme == CLAW_SHARPCLAW && m.char_decomp && m.rp == CLAW_RP_ELASTICITY_FWAVE)
     return "no characteristic projection for the f-wave elasticity solver";
+  if (m.scheme == CLAW_CLASSIC && nd == 2 && m.rp == CLAW_RP_ELASTICITY_FWAVE)
+    return "the 2D p-system has normal solves only: use SharpClaw";
   if (!(m.cfl_desired > 0) || !(m.cfl_max >= m.cfl_desired)) return "need 0 < cfl_desired <= cfl_max";
   if (!(m.dt_max > 0)) return "dt_max must be positive";
   if (m.max_retries < 0) return "max_retries must be >= 0";
@@ -457,7 +459,8 @@ claw_status claw_method_init(claw_method* m, int rp, int ndim) {
     g_err = "unknown Riemann solver for this dimension";
     return CLAW_EINVAL;
   }
-  m->scheme = CLAW_CLASSIC;
+  // the 2D p-system has normal solves only (Sec. 6.3 uses SharpClaw)
+  m->scheme = (rp == CLAW_RP_ELASTICITY_FWAVE && ndim == 2) ? CLAW_SHARPCLAW : CLAW_CLASSIC;
   m->rp = rp;
   m->lim = CLAW_LIM_MC;
   m->prec = CLAW_FP64;

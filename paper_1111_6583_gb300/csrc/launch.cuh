@@ -44,6 +44,10 @@ __global__ void __launch_bounds__(kMaxspeedCells)
         for (int side = 0; side < (j == ny - 1 ? 2 : 1); ++side) {
           load_cell<M, R>(C, q, nx, ny, i, j - 1 + side, RP::WALL_X, RP::WALL_Y, a);
           load_cell<M, R>(C, q, nx, ny, i, j + side, RP::WALL_X, RP::WALL_Y, b);
+          if (MA > 0) {
+            load_aux<MA, R>(C, aux, nx, ny, i, j - 1 + side, al);
+            load_aux<MA, R>(C, aux, nx, ny, i, j + side, ar);
+          }
           RP::template solve<1>(C, a, b, al, ar, W, s, am, ap, x);
 #pragma unroll
           for (int p = 0; p < MW; ++p) sy = nanmax(sy, (R)fabs(s[p]));
@@ -71,6 +75,10 @@ struct Launchers {
       classic3d_sweep<RP, R, 2><<<(unsigned)((f2 + 255) / 256), 256, 0, a.stream>>>(a.members, C);
       classic3d_update<RP, R><<<a.ntiles_total, 256, 0, a.stream>>>(a.members, C);
       return cudaGetLastError();
+    } else if constexpr (ND == 2 && RP::MA > 0) {
+      // 2D solvers with aux fields have normal solves only (SharpClaw)
+      (void)C;
+      return cudaErrorNotSupported;
     } else if constexpr (ND == 1) {
       constexpr int K = sizeof(R) == 8 ? classic1d_K(0) : classic1d_K(1);
       classic1d_kernel<RP, R, kClassic1dThreads, K>

@@ -680,30 +680,41 @@ struct RpEulerHLLE : EulerBase<R, ND> {
 // nonlinear elasticity / p-system (eps, rho u) with f-waves, aux (rho, K),
 // sigma(eps) = exp(K eps) - 1 (Sec. 6.3 constitutive law, shifted to sigma(0)=0)
 // ---------------------------------------------------------------------------
+// Nonlinear elasticity / p-system with f-waves (Sec. 6.3; Bale-LeVeque-
+// Mitran-Rossmanith f-wave splitting): q = (eps, m_x[, m_y]), aux (rho, K) per
+// cell, sigma = exp(K eps) - 1, normal flux (-m_n/rho, -sigma) in the
+// (eps, m_n) components and none in the tangential momentum.  Each side uses
+// its own impedance Z = rho c, c = sqrt(K exp(K eps) / rho).  In 2D only the
+// normal solves exist (SharpClaw), so there is no transverse solver.
 template <typename R, int ND>
 struct RpElasticity {
-  static constexpr int M = 2, MW = 2, MA = 2, NCTX = 1;
+  static constexpr int M = ND + 1, MW = 2, MA = 2, NCTX = 1;
   static constexpr bool FWAVE = true;
-  static constexpr int WALL_X = 1, WALL_Y = -1;
+  static constexpr int WALL_X = 1, WALL_Y = (ND == 2) ? 2 : -1;
   template <int DIR>
   __device__ static __forceinline__ void solve(const MConsts<R>&, const R (&ql)[M],
                                                const R (&qr)[M], const R* al, const R* ar,
                                                R (&W)[MW][M], R (&s)[MW], R (&am)[M],
                                                R (&ap)[M], R (&ctx)[NCTX]) {
+    constexpr int n = (ND == 1) ? 1 : 1 + DIR;
     const R rl = al[0], Kl = al[1], rr = ar[0], Kr = ar[1];
     const R el = FM<R>::exp(Kl * ql[0]), er = FM<R>::exp(Kr * qr[0]);
     const R irl = FM<R>::rcp(rl), irr = FM<R>::rcp(rr);
     const R cl = FM<R>::sqrt(Kl * el * irl), cr = FM<R>::sqrt(Kr * er * irr);
     const R Zl = rl * cl, Zr = rr * cr;
-    const R d1 = ql[1] * irl - qr[1] * irr;  // jump of -u
+    const R d1 = ql[n] * irl - qr[n] * irr;  // jump of -u_n
     const R d2 = el - er;                    // jump of -sigma
     const R iz = FM<R>::rcp(Zl + Zr);
     const R b1 = (Zr * d1 + d2) * iz;
     const R b2 = (Zl * d1 - d2) * iz;
+#pragma unroll
+    for (int p = 0; p < MW; ++p)
+#pragma unroll
+      for (int k = 0; k < M; ++k) W[p][k] = R(0);
     W[0][0] = b1;
-    W[0][1] = b1 * Zl;
+    W[0][n] = b1 * Zl;
     W[1][0] = b2;
-    W[1][1] = -b2 * Zr;
+    W[1][n] = -b2 * Zr;
     s[0] = -cl;
     s[1] = cr;
     // f-wave split by the sign of the speed (c > 0 on both sides)
@@ -728,13 +739,17 @@ struct RpElasticity {
   template <int DIR>
   __device__ static __forceinline__ void flux(const MConsts<R>&, const R (&q)[M], const R* a,
                                               R (&f)[M]) {
-    f[0] = -FM<R>::div(q[1], a[0]);
-    f[1] = R(1) - FM<R>::exp(a[1] * q[0]);
+    constexpr int n = (ND == 1) ? 1 : 1 + DIR;
+#pragma unroll
+    for (int k = 0; k < M; ++k) f[k] = R(0);
+    f[0] = -FM<R>::div(q[n], a[0]);
+    f[n] = R(1) - FM<R>::exp(a[1] * q[0]);
   }
   template <int DIR>
   __device__ static __forceinline__ void trans(const MConsts<R>&, const R (&)[NCTX],
                                                const R (&)[M], R (&bm)[M], R (&bp)[M]) {
-    bm[0] = bm[1] = bp[0] = bp[1] = R(0);
+#pragma unroll
+    for (int k = 0; k < M; ++k) bm[k] = bp[k] = R(0);
   }
   template <int DIR>
   __device__ static __forceinline__ void char_ctx(const MConsts<R>&, const R (&)[M],
@@ -744,14 +759,14 @@ struct RpElasticity {
   template <int DIR>
   __device__ static __forceinline__ void to_char(const MConsts<R>&, const R (&)[NCTX],
                                                  const R (&q)[M], R (&w)[M]) {
-    w[0] = q[0];
-    w[1] = q[1];
+#pragma unroll
+    for (int k = 0; k < M; ++k) w[k] = q[k];
   }
   template <int DIR>
   __device__ static __forceinline__ void from_char(const MConsts<R>&, const R (&)[NCTX],
                                                    const R (&w)[M], R (&q)[M]) {
-    q[0] = w[0];
-    q[1] = w[1];
+#pragma unroll
+    for (int k = 0; k < M; ++k) q[k] = w[k];
   }
 };
 

@@ -48,7 +48,10 @@ def test_method_init_and_validation_without_gpu(lib_path):
     m = claw.claw_method()
     assert lib.claw_method_init(ctypes.byref(m), claw.RP["sw_roe"], 2) == claw.CLAW_OK
     assert m.num_eqn == 3 and m.transverse == 2 and m.lim == claw.LIM["mc"]
-    assert lib.claw_method_init(ctypes.byref(m), claw.RP["elasticity_fwave"], 2) == claw.CLAW_EINVAL
+    assert lib.claw_method_init(ctypes.byref(m), claw.RP["elasticity_fwave"], 3) == claw.CLAW_EINVAL
+    # the 2D p-system defaults to SharpClaw (normal solves only)
+    assert lib.claw_method_init(ctypes.byref(m), claw.RP["elasticity_fwave"], 2) == claw.CLAW_OK
+    assert m.scheme == claw.SHARPCLAW and m.num_eqn == 3 and m.num_aux == 2
     assert lib.claw_method_init(ctypes.byref(m), 99, 1) == claw.CLAW_EINVAL
     g = claw.claw_grid()
     g.ndim = 2
@@ -66,6 +69,12 @@ def test_method_init_and_validation_without_gpu(lib_path):
     assert lib.claw_solver_create(ctypes.byref(m), ctypes.byref(g), None,
                                   ctypes.byref(h)) == claw.CLAW_EINVAL
     assert b"paired" in lib.claw_last_error(None)
+    lib.claw_method_init(ctypes.byref(m), claw.RP["elasticity_fwave"], 2)
+    m.scheme = claw.CLASSIC
+    m.bc_upper[0] = claw.BC["periodic"]
+    assert lib.claw_solver_create(ctypes.byref(m), ctypes.byref(g), None,
+                                  ctypes.byref(h)) == claw.CLAW_EINVAL
+    assert b"SharpClaw" in lib.claw_last_error(None)
     lib.claw_method_init(ctypes.byref(m), claw.RP["elasticity_fwave"], 1)
     m.scheme = claw.SHARPCLAW
     m.char_decomp = 1
