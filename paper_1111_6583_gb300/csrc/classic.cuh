@@ -312,13 +312,30 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? 7 : 1)
 // (own column in registers, neighbour columns through shared-memory
 // mailboxes).  Row R-2 is then complete and is written out.
 // ---------------------------------------------------------------------------
+// normal solve between two cells, with the solver's per-cell prep when it
+// has one (computed once per cell instead of once per interface side)
+template <class RP, int DIR, typename R>
+__device__ __forceinline__ void solve_cells(const MConsts<R>& C, const R (&ql)[RP::M],
+                                            const R (&qr)[RP::M], const R* pcl, const R* pcr,
+                                            R (&W)[RP::MW][RP::M], R (&s)[RP::MW],
+                                            R (&am)[RP::M], R (&ap)[RP::M], R (&x)[RP::NCTX]) {
+  if constexpr (RP::NPC > 0)
+    RP::template solve_pc<DIR>(C, ql, qr, pcl[0], pcr[0], W, s, am, ap, x);
+  else
+    RP::template solve<DIR>(C, ql, qr, nullptr, nullptr, W, s, am, ap, x);
+}
+
 template <class RP, typename R, int BW>
 __global__ void __launch_bounds__(BW)
     classic2d_kernel(const Member* __restrict__ members, const Tile* __restrict__ tiles,
                      int ntiles_total, const MConsts<R> C, int H) {
   constexpr int M = RP::M, MW = RP::MW, NC = RP::NCTX;
+  constexpr int NP = RP::NPC > 0 ? RP::NPC : 1;
+  using NZX = typename RP::template NZ<0>;
+  using NZY = typename RP::template NZ<1>;
   constexpr int TX = BW - 4;
   __shared__ R qs[M][BW];
+  __shared__ R pcs[NP][BW];
   __shared__ R xws[MW][M][BW];
   __shared__ R mbl[4][M][BW];
   __shared__ R mbr[2][M][BW];
@@ -361,6 +378,9 @@ __global__ void __launch_bounds__(BW)
     const size_t plane = (size_t)nx * ny;
 
     R qm2[M], qm1[M], qc[M];
+    R pm1[NP], pcc[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) pm1[k] = pcc[k] = R(0);
     R acc0[M], acc1[M], acc2[M], acc3[M];
     // y-interface R-1 (previous): waves, speeds, fluctuations, linearisation,
     // norms and dot products with the interface below it
@@ -392,17 +412,25 @@ __global__ void __launch_bounds__(BW)
       load_cell<M, R>(C, q, nx, ny, cload, Rw, RP::WALL_X, RP::WALL_Y, qc);
 #pragma unroll
       for (int k = 0; k < M; ++k) qs[k][l] = qc[k];
+      if constexpr (RP::NPC > 0) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) pm1[k] = pcc[k];
+        RP::cell_pc(C, qc, pcc);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) pcs[k][l] = pcc[k];
+      }
 
       // (2) y-interface Rw (rows Rw-1, Rw)
       R nW[MW][M], ns[MW], nam[M], nap[M], nx_[NC], nnrm[MW], ndot[MW];
       const bool yrow = Rw >= r0 - 1;
       if (yrow) {
-        RP::template solve<1>(C, qm1, qc, nullptr, nullptr, nW, ns, nam, nap, nx_);
+        solve_cells<RP, 1, R>(C, qm1, qc, pm1, pcc, nW, ns, nam, nap, nx_);
 #pragma unroll
         for (int p = 0; p < MW; ++p) {
           R a = R(0), b = R(0);
 #pragma unroll
           for (int k = 0; k < M; ++k) {
+            if (!NZY::f(p, k)) continue;
             a += nW[p][k] * nW[p][k];
             b += nW[p][k] * yW[p][k];
           }
@@ -411,7 +439,7 @@ __global__ void __launch_bounds__(BW)
         }
         if (col_in && Rw >= r0 && Rw <= rend + 1) {
 #pragma unroll
-          for (int p = 0; p < MW; ++p) smy = nanmax(smy, (R)fabs(ns[p]));
+          for (int p = 0; p < MW; ++p) smy = max_nonneg(smy, (R)fabs(ns[p]));
         }
       }
       __syncthreads();  // qs ready
@@ -420,14 +448,17 @@ __global__ void __launch_bounds__(BW)
       const bool xrow = (Rw >= r0 - 1) && (Rw <= rend + 1);
       R xW[MW][M], xs[MW], xam[M], xap[M], xx[NC];
       if (xrow && l >= 1) {
-        R ql[M];
+        R ql[M], pl[NP];
 #pragma unroll
         for (int k = 0; k < M; ++k) ql[k] = qs[k][l - 1];
-        RP::template solve<0>(C, ql, qc, nullptr, nullptr, xW, xs, xam, xap, xx);
+#pragma unroll
+        for (int k = 0; k < NP; ++k) pl[k] = RP::NPC > 0 ? pcs[k][l - 1] : R(0);
+        solve_cells<RP, 0, R>(C, ql, qc, pl, pcc, xW, xs, xam, xap, xx);
 #pragma unroll
         for (int p = 0; p < MW; ++p)
 #pragma unroll
-          for (int k = 0; k < M; ++k) xws[p][k][l] = xW[p][k];
+          for (int k = 0; k < M; ++k)
+            if (NZX::f(p, k)) xws[p][k][l] = xW[p][k];
       }
       __syncthreads();  // x waves ready
 
@@ -445,17 +476,18 @@ __global__ void __launch_bounds__(BW)
           R dot[MW], nrm[MW];
 #pragma unroll
           for (int p = 0; p < MW; ++p) {
-            const int lu = xs[p] > R(0) ? l - 1 : l + 1;
+            const int lu = gt0(xs[p]) ? l - 1 : l + 1;
             R a = R(0), b = R(0);
 #pragma unroll
             for (int k = 0; k < M; ++k) {
+              if (!NZX::f(p, k)) continue;
               b += xws[p][k][lu] * xW[p][k];
               a += xW[p][k] * xW[p][k];
             }
             dot[p] = b;
             nrm[p] = a;
           }
-          correction<RP, R>(C, xW, xs, dot, nrm, dtdx, F);
+          correction<RP, R, 0>(C, xW, xs, dot, nrm, dtdx, F);
         } else {
 #pragma unroll
           for (int k = 0; k < M; ++k) F[k] = R(0);
@@ -470,7 +502,7 @@ __global__ void __launch_bounds__(BW)
         }
         if (xcfl && Rw >= r0 && Rw <= rend) {
 #pragma unroll
-          for (int p = 0; p < MW; ++p) smx = nanmax(smx, (R)fabs(xs[p]));
+          for (int p = 0; p < MW; ++p) smx = max_nonneg(smx, (R)fabs(xs[p]));
         }
         if (C.transverse) {
           R tp[M], tm[M], bmp[M], bpp[M], bmm[M], bpm[M];
@@ -499,8 +531,8 @@ __global__ void __launch_bounds__(BW)
         if (C.order == 2) {
           R dot[MW];
 #pragma unroll
-          for (int p = 0; p < MW; ++p) dot[p] = ys[p] > R(0) ? ydot[p] : ndot[p];
-          correction<RP, R>(C, yW, ys, dot, ynrm, dtdy, G);
+          for (int p = 0; p < MW; ++p) dot[p] = gt0(ys[p]) ? ydot[p] : ndot[p];
+          correction<RP, R, 1>(C, yW, ys, dot, ynrm, dtdy, G);
         } else {
 #pragma unroll
           for (int k = 0; k < M; ++k) G[k] = R(0);

@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(256)
         dot[p] = d_;
         nrm[p] = n2;
       }
-      correction<RP, R>(C, W[1], s[1], dot, nrm, dtdn, F);
+      correction<RP, R, D>(C, W[1], s[1], dot, nrm, dtdn, F);
     } else {
 #pragma unroll
       for (int c = 0; c < M; ++c) F[c] = R(0);

@@ -49,8 +49,38 @@ struct FM<float> {
 template <typename R>
 __device__ __forceinline__ R rsq(R x) { return FM<R>::rsqrt(x); }
 
-// A^- dQ = sum_p min(s^p,0) W^p,  A^+ dQ = sum_p max(s^p,0) W^p
-template <int M, int MW, typename R>
+// Sign tests and maxima on the bit patterns (integer pipe; the FP64 pipe is
+// the scarce unit).  gt0(x) == (x > 0) and lt0(x) == (x < 0) for every
+// non-NaN x (+0 and -0 are neither); a NaN counts by its sign bit.
+__device__ __forceinline__ long long fbits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ int fbits(float x) { return __float_as_int(x); }
+template <typename R>
+__device__ __forceinline__ bool gt0(R x) { return fbits(x) > 0; }
+template <typename R>
+__device__ __forceinline__ bool lt0(R x) {
+  return fbits(x) < 0 && (fbits(x) << 1) != 0;
+}
+// larger of two non-negative values (or NaNs with clear sign bit, which win:
+// their bit patterns lie above +inf)
+template <typename R>
+__device__ __forceinline__ R max_nonneg(R a, R b) { return fbits(b) > fbits(a) ? b : a; }
+// x is a positive normal finite number
+__device__ __forceinline__ bool pos_normal(double x) {
+  const long long b = fbits(x);
+  return b >= 0x0010000000000000LL && b < 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool pos_normal(float x) {
+  const int b = fbits(x);
+  return b >= 0x00800000 && b < 0x7f800000;
+}
+
+// A^- dQ = sum_p min(s^p,0) W^p,  A^+ dQ = sum_p max(s^p,0) W^p.  NZ(p, k)
+// tells which wave components can be non-zero (the rest are structural
+// zeros of the solver and are skipped).
+struct AllNZ {
+  __device__ static constexpr bool f(int, int) { return true; }
+};
+template <int M, int MW, typename R, class NZ = AllNZ>
 __device__ __forceinline__ void split_waves(const R (&W)[MW][M], const R (&s)[MW], R (&am)[M],
                                             R (&ap)[M]) {
 #pragma unroll
@@ -58,11 +88,32 @@ __device__ __forceinline__ void split_waves(const R (&W)[MW][M], const R (&s)[MW
     am[k] = R(0);
     ap[k] = R(0);
   }
+  if (lt0(s[0]) && gt0(s[MW - 1])) {
+    // first family left-going, last right-going (every subsonic state)
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      if (NZ::f(0, k)) am[k] = s[0] * W[0][k];
+      if (NZ::f(MW - 1, k)) ap[k] = s[MW - 1] * W[MW - 1][k];
+    }
+#pragma unroll
+    for (int p = 1; p < MW - 1; ++p) {
+      const bool neg = lt0(s[p]);
+      const R sm = neg ? s[p] : R(0), sp = neg ? R(0) : s[p];
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+        if (!NZ::f(p, k)) continue;
+        am[k] += sm * W[p][k];
+        ap[k] += sp * W[p][k];
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int p = 0; p < MW; ++p) {
     const R sm = fmin(s[p], R(0)), sp = fmax(s[p], R(0));
 #pragma unroll
     for (int k = 0; k < M; ++k) {
+      if (!NZ::f(p, k)) continue;
       am[k] += sm * W[p][k];
       ap[k] += sp * W[p][k];
     }
@@ -74,7 +125,9 @@ __device__ __forceinline__ void split_waves(const R (&W)[MW][M], const R (&s)[MW
 // ---------------------------------------------------------------------------
 template <typename R, int ND>
 struct RpAdvection {
-  static constexpr int M = 1, MW = 1, MA = 0, NCTX = 1;
+  static constexpr int M = 1, MW = 1, MA = 0, NCTX = 1, NPC = 0;
+  template <int DIR>
+  struct NZ : AllNZ {};
   static constexpr bool FWAVE = false;
   static constexpr int WALL_X = -1, WALL_Y = -1;
   template <int DIR>
@@ -125,7 +178,12 @@ struct RpAdvection {
 // ---------------------------------------------------------------------------
 template <typename R, int ND>
 struct RpAcoustics {
-  static constexpr int M = ND + 1, MW = 2, MA = 0, NCTX = 1;
+  static constexpr int M = ND + 1, MW = 2, MA = 0, NCTX = 1, NPC = 0;
+  // waves live in the pressure and normal-velocity components
+  template <int DIR>
+  struct NZ {
+    __device__ static constexpr bool f(int, int k) { return k == 0 || k == 1 + DIR; }
+  };
   static constexpr bool FWAVE = false;
   static constexpr int WALL_X = 1, WALL_Y = (ND == 2) ? 2 : -1;
   template <int DIR>
@@ -210,20 +268,41 @@ struct RpAcoustics {
 template <typename R, int ND>
 struct RpSW {
   static constexpr int M = ND + 1, MW = ND + 1, MA = 0, NCTX = 4;  // ctx: un, ut, c, 1/(2c)
+  static constexpr int NPC = 1;  // per-cell prep: 1/sqrt(h)
   static constexpr bool FWAVE = false;
   static constexpr int WALL_X = 1, WALL_Y = (ND == 2) ? 2 : -1;
-
+  // the shear wave (2D) has only the tangential component
   template <int DIR>
-  __device__ static __forceinline__ void roe(const MConsts<R>& C, const R (&ql)[M],
-                                             const R (&qr)[M], R (&x)[NCTX]) {
+  struct NZ {
+    __device__ static constexpr bool f(int p, int k) {
+      return ND == 1 || p != 1 || k == 2 - DIR;
+    }
+  };
+  __device__ static __forceinline__ void cell_pc(const MConsts<R>&, const R (&q)[M],
+                                                 R (&pc)[NPC]) {
+    pc[0] = rsq(q[0]);
+  }
+
+  // Roe averages from the cells' 1/sqrt(h): u^ = (hu_l/sqrt(h_l) +
+  // hu_r/sqrt(h_r)) / (sqrt(h_l) + sqrt(h_r)); c^ = sqrt(g h^) and 1/(2 c^)
+  // from one reciprocal square root.
+  template <int DIR>
+  __device__ static __forceinline__ void roe_pc(const MConsts<R>& C, const R (&ql)[M],
+                                                const R (&qr)[M], R il, R ir, R (&x)[NCTX]) {
     constexpr int n = Dirs<ND, DIR>::n, t = Dirs<ND, DIR>::t;
     const R hl = ql[0], hr = qr[0];
-    const R il = rsq(hl), ir = rsq(hr);          // 1/sqrt(h)
     const R iden = FM<R>::rcp(hl * il + hr * ir);   // 1/(sqrt(hl)+sqrt(hr))
     x[0] = (ql[n] * il + qr[n] * ir) * iden;     // sqrt(h) u = hu/sqrt(h)
     x[1] = (t >= 0) ? (ql[t < 0 ? 0 : t] * il + qr[t < 0 ? 0 : t] * ir) * iden : R(0);
-    x[2] = FM<R>::sqrt(C.g * (R(0.5) * (hl + hr)));
-    x[3] = FM<R>::div(R(0.5), x[2]);
+    const R gh = C.g * (R(0.5) * (hl + hr));
+    const R rc = rsq(gh);
+    x[2] = gh * rc;
+    x[3] = R(0.5) * rc;
+  }
+  template <int DIR>
+  __device__ static __forceinline__ void roe(const MConsts<R>& C, const R (&ql)[M],
+                                             const R (&qr)[M], R (&x)[NCTX]) {
+    roe_pc<DIR>(C, ql, qr, rsq(ql[0]), rsq(qr[0]), x);
   }
 
   // eigen-coefficients of d in the frame (normal a, tangential b) at (un, ut, c)
@@ -267,11 +346,19 @@ struct RpSW {
 
   template <int DIR>
   __device__ static __forceinline__ void solve(const MConsts<R>& C, const R (&ql)[M],
-                                               const R (&qr)[M], const R*, const R*,
+                                               const R (&qr)[M], const R* al, const R* ar,
                                                R (&W)[MW][M], R (&s)[MW], R (&am)[M],
                                                R (&ap)[M], R (&x)[NCTX]) {
+    solve_pc<DIR>(C, ql, qr, rsq(ql[0]), rsq(qr[0]), W, s, am, ap, x);
+  }
+  // the normal solve with the cells' 1/sqrt(h) given
+  template <int DIR>
+  __device__ static __forceinline__ void solve_pc(const MConsts<R>& C, const R (&ql)[M],
+                                                  const R (&qr)[M], R il, R ir,
+                                                  R (&W)[MW][M], R (&s)[MW], R (&am)[M],
+                                                  R (&ap)[M], R (&x)[NCTX]) {
     constexpr int n = Dirs<ND, DIR>::n, t = Dirs<ND, DIR>::t;
-    roe<DIR>(C, ql, qr, x);
+    roe_pc<DIR>(C, ql, qr, il, ir, x);
     const R un = x[0], ut = x[1], c = x[2];
     const R i2c = x[3];
     R d[M], al[MW];
@@ -332,7 +419,7 @@ struct RpSW {
         }
       }
     }
-    split_waves<M, MW, R>(W, s, am, ap);
+    split_waves<M, MW, R, NZ<DIR>>(W, s, am, ap);
   }
 
   template <int DIR>
@@ -353,7 +440,23 @@ struct RpSW {
     const R i2c = x[3];
     R be[MW], km[MW], kp[MW];
     coef<t, n>(ut, un, c, i2c, a, be);
-    const R lam[3] = {ut - c, ut, ut + c};
+    const R lm = ut - c, lp = ut + c;
+    if (ND == 2 && lt0(lm) && gt0(lp)) {
+      // subsonic in the transverse direction: the first family goes down,
+      // the last up, the shear wave by the sign of ut
+      const R k0 = lm * be[0], k2 = lp * be[MW - 1];
+      const R k1 = ut * be[1];
+      const bool neg = lt0(ut);
+      constexpr int tt = t < 0 ? 0 : t;
+      bm[0] = k0;
+      bm[tt] = k0 * lm;
+      bm[n] = k0 * un + (neg ? k1 : R(0));
+      bp[0] = k2;
+      bp[tt] = k2 * lp;
+      bp[n] = k2 * un + (neg ? R(0) : k1);
+      return;
+    }
+    const R lam[3] = {lm, ut, lp};
 #pragma unroll
     for (int p = 0; p < MW; ++p) {
       km[p] = fmin(lam[p == MW - 1 ? 2 : p], R(0)) * be[p];
@@ -493,7 +596,9 @@ struct EulerBase {
 template <typename R, int ND>
 struct RpEulerRoe : EulerBase<R, ND> {
   using B = EulerBase<R, ND>;
-  static constexpr int M = B::M, MW = B::M, MA = 0, NCTX = B::NCTX, E = B::E;
+  static constexpr int M = B::M, MW = B::M, MA = 0, NCTX = B::NCTX, E = B::E, NPC = 0;
+  template <int DIR>
+  struct NZ : AllNZ {};
   static constexpr bool FWAVE = false;
   static constexpr int WALL_X = 1, WALL_Y = (ND == 2) ? 2 : -1;
 
@@ -634,7 +739,9 @@ struct RpEulerRoe : EulerBase<R, ND> {
 template <typename R, int ND>
 struct RpEulerHLLE : EulerBase<R, ND> {
   using B = EulerBase<R, ND>;
-  static constexpr int M = B::M, MW = 2, MA = 0, NCTX = B::NCTX, E = B::E;
+  static constexpr int M = B::M, MW = 2, MA = 0, NCTX = B::NCTX, E = B::E, NPC = 0;
+  template <int DIR>
+  struct NZ : AllNZ {};
   static constexpr bool FWAVE = false;
   static constexpr int WALL_X = 1, WALL_Y = (ND == 2) ? 2 : -1;
 
@@ -688,7 +795,12 @@ struct RpEulerHLLE : EulerBase<R, ND> {
 // normal solves exist (SharpClaw), so there is no transverse solver.
 template <typename R, int ND>
 struct RpElasticity {
-  static constexpr int M = ND + 1, MW = 2, MA = 2, NCTX = 1;
+  static constexpr int M = ND + 1, MW = 2, MA = 2, NCTX = 1, NPC = 0;
+  // f-waves live in the strain and normal-momentum components
+  template <int DIR>
+  struct NZ {
+    __device__ static constexpr bool f(int, int k) { return k == 0 || k == (ND == 1 ? 1 : 1 + DIR); }
+  };
   static constexpr bool FWAVE = true;
   static constexpr int WALL_X = 1, WALL_Y = (ND == 2) ? 2 : -1;
   template <int DIR>
@@ -787,27 +899,69 @@ __device__ __forceinline__ R limiter(int lim, R th) {
   }
 }
 
+// MC limiter max(0, min((1+th)/2, 2, 2 th)) with the branch chosen on the bit
+// pattern of th (2 th below th = 1/3, (1+th)/2 up to th = 3, then 2).
+template <typename R>
+__device__ __forceinline__ R limiter_mc(R th) {
+  if (!gt0(th)) return R(0);
+  const R two_th = R(2) * th, mid = R(0.5) * (R(1) + th);
+  const auto b = fbits(th);
+  return b < fbits(R(1) / R(3)) ? two_th : (b <= fbits(R(3)) ? mid : R(2));
+}
+
 // Second-order correction at one interface (Eq. (lwflux) with limited waves):
 //   F = 1/2 sum_p c_p phi(theta_p) W^p,  c_p = |s|(1 - dt/dx |s|)   (waves)
 //                                          = sgn(s)(1 - dt/dx |s|) (f-waves)
 // dot_up[p] = W^p_upwind . W^p, nrm[p] = W^p . W^p (zero wave -> no correction).
-template <class RP, typename R>
+// theta_p = dot_up[p] / nrm[p]; with three or more waves, when the product
+// of the norms is a normal number, the reciprocals come from one division
+// (1/n_p = prod_{q != p} n_q / prod_q n_q).  DIR selects the solver's
+// structural zeros.
+template <class RP, typename R, int DIR = 0>
 __device__ __forceinline__ void correction(const MConsts<R>& C, const R (&W)[RP::MW][RP::M],
                                            const R (&s)[RP::MW], const R (&dot_up)[RP::MW],
                                            const R (&nrm)[RP::MW], R dtdn, R (&F)[RP::M]) {
+  using NZ = typename RP::template NZ<DIR>;
+  constexpr int MW = RP::MW;
 #pragma unroll
   for (int k = 0; k < RP::M; ++k) F[k] = R(0);
+  R inv[MW];
+  bool batched = false;
+  if (MW >= 3 && C.lim != CLAW_LIM_NONE) {
+    R pre[MW];
+    R prod = nrm[0];
+    pre[0] = R(1);
 #pragma unroll
-  for (int p = 0; p < RP::MW; ++p) {
+    for (int p = 1; p < MW; ++p) {
+      pre[p] = prod;
+      prod = prod * nrm[p];
+    }
+    if (pos_normal(prod)) {
+      const R r = FM<R>::rcp(prod);
+      R suf = r;
+#pragma unroll
+      for (int p = MW - 1; p >= 0; --p) {
+        inv[p] = p == 0 ? suf : suf * pre[p];
+        suf = suf * nrm[p];
+      }
+      batched = true;
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < MW; ++p) {
     R phi;
-    if (nrm[p] == R(0)) phi = R(0);
+    if (fbits(nrm[p]) == 0) phi = R(0);
     else if (C.lim == CLAW_LIM_NONE) phi = R(1);
-    else phi = limiter<R>(C.lim, FM<R>::div(dot_up[p], nrm[p]));
+    else {
+      const R th = batched ? dot_up[p] * inv[p] : FM<R>::div(dot_up[p], nrm[p]);
+      phi = C.lim == CLAW_LIM_MC ? limiter_mc<R>(th) : limiter<R>(C.lim, th);
+    }
     const R a = fabs(s[p]);
-    const R sg = RP::FWAVE ? (s[p] > R(0) ? R(1) : (s[p] < R(0) ? R(-1) : R(0))) : a;
+    const R sg = RP::FWAVE ? (gt0(s[p]) ? R(1) : (lt0(s[p]) ? R(-1) : R(0))) : a;
     const R cf = R(0.5) * sg * (R(1) - dtdn * a) * phi;
 #pragma unroll
-    for (int k = 0; k < RP::M; ++k) F[k] += cf * W[p][k];
+    for (int k = 0; k < RP::M; ++k)
+      if (NZ::f(p, k)) F[k] += cf * W[p][k];
   }
 }
 
