@@ -314,13 +314,14 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? 7 : 1)
 // ---------------------------------------------------------------------------
 // normal solve between two cells, with the solver's per-cell prep when it
 // has one (computed once per cell instead of once per interface side)
-template <class RP, int DIR, typename R>
+template <class RP, int DIR, typename R, int NP>
 __device__ __forceinline__ void solve_cells(const MConsts<R>& C, const R (&ql)[RP::M],
-                                            const R (&qr)[RP::M], const R* pcl, const R* pcr,
-                                            R (&W)[RP::MW][RP::M], R (&s)[RP::MW],
-                                            R (&am)[RP::M], R (&ap)[RP::M], R (&x)[RP::NCTX]) {
+                                            const R (&qr)[RP::M], const R (&pcl)[NP],
+                                            const R (&pcr)[NP], R (&W)[RP::MW][RP::M],
+                                            R (&s)[RP::MW], R (&am)[RP::M], R (&ap)[RP::M],
+                                            R (&x)[RP::NCTX]) {
   if constexpr (RP::NPC > 0)
-    RP::template solve_pc<DIR>(C, ql, qr, pcl[0], pcr[0], W, s, am, ap, x);
+    RP::template solve_pc<DIR>(C, ql, qr, pcl, pcr, W, s, am, ap, x);
   else
     RP::template solve<DIR>(C, ql, qr, nullptr, nullptr, W, s, am, ap, x);
 }
@@ -424,7 +425,7 @@ __global__ void __launch_bounds__(BW)
       R nW[MW][M], ns[MW], nam[M], nap[M], nx_[NC], nnrm[MW], ndot[MW];
       const bool yrow = Rw >= r0 - 1;
       if (yrow) {
-        solve_cells<RP, 1, R>(C, qm1, qc, pm1, pcc, nW, ns, nam, nap, nx_);
+        solve_cells<RP, 1, R, NP>(C, qm1, qc, pm1, pcc, nW, ns, nam, nap, nx_);
 #pragma unroll
         for (int p = 0; p < MW; ++p) {
           R a = R(0), b = R(0);
@@ -453,7 +454,7 @@ __global__ void __launch_bounds__(BW)
         for (int k = 0; k < M; ++k) ql[k] = qs[k][l - 1];
 #pragma unroll
         for (int k = 0; k < NP; ++k) pl[k] = RP::NPC > 0 ? pcs[k][l - 1] : R(0);
-        solve_cells<RP, 0, R>(C, ql, qc, pl, pcc, xW, xs, xam, xap, xx);
+        solve_cells<RP, 0, R, NP>(C, ql, qc, pl, pcc, xW, xs, xam, xap, xx);
 #pragma unroll
         for (int p = 0; p < MW; ++p)
 #pragma unroll

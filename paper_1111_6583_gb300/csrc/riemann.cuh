@@ -268,7 +268,7 @@ struct RpAcoustics {
 template <typename R, int ND>
 struct RpSW {
   static constexpr int M = ND + 1, MW = ND + 1, MA = 0, NCTX = 4;  // ctx: un, ut, c, 1/(2c)
-  static constexpr int NPC = 1;  // per-cell prep: 1/sqrt(h)
+  static constexpr int NPC = 2;  // per-cell prep: 1/sqrt(h), g h^3
   static constexpr bool FWAVE = false;
   static constexpr int WALL_X = 1, WALL_Y = (ND == 2) ? 2 : -1;
   // the shear wave (2D) has only the tangential component
@@ -278,9 +278,10 @@ struct RpSW {
       return ND == 1 || p != 1 || k == 2 - DIR;
     }
   };
-  __device__ static __forceinline__ void cell_pc(const MConsts<R>&, const R (&q)[M],
+  __device__ static __forceinline__ void cell_pc(const MConsts<R>& C, const R (&q)[M],
                                                  R (&pc)[NPC]) {
     pc[0] = rsq(q[0]);
+    pc[1] = C.g * (q[0] * q[0] * q[0]);
   }
 
   // Roe averages from the cells' 1/sqrt(h): u^ = (hu_l/sqrt(h_l) +
@@ -303,6 +304,14 @@ struct RpSW {
   __device__ static __forceinline__ void roe(const MConsts<R>& C, const R (&ql)[M],
                                              const R (&qr)[M], R (&x)[NCTX]) {
     roe_pc<DIR>(C, ql, qr, rsq(ql[0]), rsq(qr[0]), x);
+  }
+  // the sign tests below with g h^3 given (gh3 = C.g * (h * h * h)); the
+  // comparisons of non-negative values run on their bit patterns
+  __device__ static __forceinline__ bool minus_neg_c(R h, R hu, R gh3) {
+    return gt0(h) && (lt0(hu) || fbits(hu * hu) < fbits(gh3));
+  }
+  __device__ static __forceinline__ bool plus_pos_c(R h, R hu, R gh3) {
+    return gt0(h) && (gt0(hu) || fbits(hu * hu) < fbits(gh3));
   }
 
   // eigen-coefficients of d in the frame (normal a, tangential b) at (un, ut, c)
@@ -335,10 +344,10 @@ struct RpSW {
     return h > R(0) && (hu < R(0) || hu * hu < C.g * (h * h * h));
   }
   __device__ static __forceinline__ bool minus_pos(const MConsts<R>& C, R h, R hu) {
-    return h > R(0) && hu > R(0) && hu * hu > C.g * (h * h * h);
+    return gt0(h) && gt0(hu) && fbits(hu * hu) > fbits(C.g * (h * h * h));
   }
   __device__ static __forceinline__ bool plus_neg(const MConsts<R>& C, R h, R hu) {
-    return h > R(0) && hu < R(0) && hu * hu > C.g * (h * h * h);
+    return gt0(h) && lt0(hu) && fbits(hu * hu) > fbits(C.g * (h * h * h));
   }
   __device__ static __forceinline__ bool plus_pos(const MConsts<R>& C, R h, R hu) {
     return h > R(0) && (hu > R(0) || hu * hu < C.g * (h * h * h));
@@ -349,16 +358,19 @@ struct RpSW {
                                                const R (&qr)[M], const R* al, const R* ar,
                                                R (&W)[MW][M], R (&s)[MW], R (&am)[M],
                                                R (&ap)[M], R (&x)[NCTX]) {
-    solve_pc<DIR>(C, ql, qr, rsq(ql[0]), rsq(qr[0]), W, s, am, ap, x);
+    R pl[NPC], pr[NPC];
+    cell_pc(C, ql, pl);
+    cell_pc(C, qr, pr);
+    solve_pc<DIR>(C, ql, qr, pl, pr, W, s, am, ap, x);
   }
-  // the normal solve with the cells' 1/sqrt(h) given
+  // the normal solve with the cells' prep (1/sqrt(h), g h^3) given
   template <int DIR>
   __device__ static __forceinline__ void solve_pc(const MConsts<R>& C, const R (&ql)[M],
-                                                  const R (&qr)[M], R il, R ir,
-                                                  R (&W)[MW][M], R (&s)[MW], R (&am)[M],
-                                                  R (&ap)[M], R (&x)[NCTX]) {
+                                                  const R (&qr)[M], const R (&pl)[NPC],
+                                                  const R (&pr)[NPC], R (&W)[MW][M], R (&s)[MW],
+                                                  R (&am)[M], R (&ap)[M], R (&x)[NCTX]) {
     constexpr int n = Dirs<ND, DIR>::n, t = Dirs<ND, DIR>::t;
-    roe_pc<DIR>(C, ql, qr, il, ir, x);
+    roe_pc<DIR>(C, ql, qr, pl[0], pr[0], x);
     const R un = x[0], ut = x[1], c = x[2];
     const R i2c = x[3];
     R d[M], al[MW];
@@ -384,7 +396,7 @@ struct RpSW {
     if (C.entropy_fix) {
       // first family: transonic when u-c < 0 at Q_l and > 0 at Q_l + W^1
       const R hm = ql[0] + W[0][0], hum = ql[n] + W[0][n];
-      if (minus_neg(C, ql[0], ql[n]) && minus_pos(C, hm, hum)) {
+      if (minus_neg_c(ql[0], ql[n], pl[1]) && minus_pos(C, hm, hum)) {
         const R lamL = sonic<DIR>(C, ql[0], ql[n], 0);
         const R lamR = sonic<DIR>(C, hm, hum, 0);
         if (lamL < R(0) && lamR > R(0)) {
@@ -402,7 +414,7 @@ struct RpSW {
       }
       // last family: u+c < 0 at Q_r - W^last and > 0 at Q_r
       const R hm2 = qr[0] - W[MW - 1][0], hum2 = qr[n] - W[MW - 1][n];
-      if (plus_neg(C, hm2, hum2) && plus_pos(C, qr[0], qr[n])) {
+      if (plus_pos_c(qr[0], qr[n], pr[1]) && plus_neg(C, hm2, hum2)) {
         const R muL = sonic<DIR>(C, hm2, hum2, 1);
         const R muR = sonic<DIR>(C, qr[0], qr[n], 1);
         if (muL < R(0) && muR > R(0)) {
