@@ -30,7 +30,7 @@ _SRC = os.path.join(_HERE, "oracle.c")
 _HDR = os.path.join(_HERE, "oracle.h")
 
 RP = {"advection": 0, "acoustics": 1, "sw_roe": 2, "euler_roe": 3, "euler_hlle": 4,
-      "elasticity_fwave": 5}
+      "elasticity_fwave": 5, "euler_tracer": 6}
 LIM = {"none": 0, "minmod": 1, "superbee": 2, "vanleer": 3, "mc": 4}
 BC = {"periodic": 0, "wall": 1, "extrap": 2, "inflow": 3}
 SCHEME = {"classic": 0, "sharpclaw": 1}
@@ -69,6 +69,9 @@ class _Prob(ctypes.Structure):
         ("weno_c", ctypes.c_double * 81),
         ("weno_d", ctypes.c_double * 9),
         ("weno_b", ctypes.c_double * 729),
+        ("source", ctypes.c_int),
+        ("dim_split", ctypes.c_int),
+        ("lower", ctypes.c_double * 2),
     ]
 
 
@@ -108,6 +111,8 @@ def _load():
         lib.orc_ssp104_linear.restype = ctypes.c_double
         lib.orc_ssp104_linear.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
         lib.orc_max_speeds.argtypes = [P, _dp, _dp, _dp]
+        lib.orc_source_step.restype = None
+        lib.orc_source_step.argtypes = [P, _dp, ctypes.c_double]
         lib.orc_evolve.argtypes = [P, _dp, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                    ctypes.POINTER(_RunInfo)]
         lib.orc_totals.argtypes = [P, _dp, _dp]
@@ -186,6 +191,10 @@ def make_problem(spec: dict):
         p.weno_c[:len(cf)] = cf
         p.weno_d[:len(df)] = df
         p.weno_b[:len(bf)] = bf
+    p.source = {"none": 0, "axisymmetric": 1}[spec.get("source", "none")]
+    p.dim_split = int(spec.get("dim_split", 0))
+    p.lower[0] = float(lo[0])
+    p.lower[1] = float(lo[1])
     return p
 
 
@@ -289,6 +298,13 @@ def sharp_L(p, q, aux=None):
     if st != 0:
         raise ValueError("oracle L failed: %s" % STATUS.get(st, st))
     return L, smax
+
+
+def source_step(p, q, dt):
+    """One source step (the problem's source term over dt), returns a copy."""
+    q = _arr(q, _shape(p)).copy()
+    _load().orc_source_step(ctypes.byref(p), _ptr(q), float(dt))
+    return q
 
 
 def ssp_rk3_linear(lam, dt, q0) -> float:

@@ -33,6 +33,7 @@ int orc_num_eqn(int rp, int ndim) {
     case ORC_RP_EULER_ROE:
     case ORC_RP_EULER_HLLE: return ndim <= 2 ? ndim + 2 : 0;
     case ORC_RP_ELASTICITY_FWAVE: return ndim == 1 ? 2 : (ndim == 2 ? 3 : 0);
+    case ORC_RP_EULER_TRACER: return ndim <= 2 ? ndim + 3 : 0;
   }
   return 0;
 }
@@ -45,6 +46,7 @@ int orc_num_waves(int rp, int ndim) {
     case ORC_RP_EULER_ROE: return ndim == 1 ? 3 : 4;
     case ORC_RP_EULER_HLLE: return 2;
     case ORC_RP_ELASTICITY_FWAVE: return 2;
+    case ORC_RP_EULER_TRACER: return ndim == 1 ? 4 : 5;
   }
   return 0;
 }
@@ -64,6 +66,11 @@ static int comp_t(const orc_prob* P, int dir) { return P->ndim == 1 ? -1 : 2 - d
 /* index of the energy component of the Euler equations */
 static int comp_e(const orc_prob* P) { return P->ndim == 1 ? 2 : 3; }
 static int is_fwave(const orc_prob* P) { return P->rp == ORC_RP_ELASTICITY_FWAVE; }
+/* index of the tracer of the Euler-with-tracer system (last component) */
+static int comp_tr(const orc_prob* P) { return P->ndim + 2; }
+static int is_euler(const orc_prob* P) {
+  return P->rp == ORC_RP_EULER_ROE || P->rp == ORC_RP_EULER_HLLE || P->rp == ORC_RP_EULER_TRACER;
+}
 
 /* ------------------------------------------------------------------------ */
 /* eigen-decompositions (LeVeque FVM book: acoustics, shallow water, Euler)  */
@@ -142,6 +149,25 @@ static int euler_eig(const orc_prob* P, int a, int b, double un, double ut, doub
   r[last * m + 0] = 1.0; r[last * m + a] = un + c; r[last * m + e] = H + un * c;
   lam[last] = un + c;
   return nw;
+}
+
+/* Euler with a passive tracer phi (phi_t + u . grad phi = 0, Sec. 6.2): the
+ * Euler waves with a zero tracer component, and a tracer wave (jump of phi
+ * alone) moving with the normal velocity, placed before the u + c wave so
+ * that the first and last waves stay the acoustic ones. */
+static int euler_tracer_eig(const orc_prob* P, int a, int b, double un, double ut, double H,
+                            double c, double c2, const double* d, double* alpha, double* r,
+                            double* lam) {
+  int m = P->num_eqn, tr = comp_tr(P);
+  int nwe = euler_eig(P, a, b, un, ut, H, c, c2, d, alpha, r, lam);
+  int last = nwe;  /* acoustic u + c wave moves one slot up */
+  alpha[last] = alpha[nwe - 1];
+  lam[last] = lam[nwe - 1];
+  for (int k = 0; k < m; ++k) r[last * m + k] = r[(nwe - 1) * m + k];
+  alpha[nwe - 1] = d[tr];
+  lam[nwe - 1] = un;
+  for (int k = 0; k < m; ++k) r[(nwe - 1) * m + k] = (k == tr) ? 1.0 : 0.0;
+  return nwe + 1;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -326,6 +352,14 @@ void orc_riemann(const orc_prob* P, int dir, const double* ql, const double* qr,
         for (int k = 0; k < m; ++k) wave[p * m + k] = alpha[p] * r[p * m + k];
       break;
     }
+    case ORC_RP_EULER_TRACER: {
+      double un, ut, H, c, c2;
+      euler_roe_avg(P, dir, ql, qr, &un, &ut, &H, &c, &c2);
+      euler_tracer_eig(P, n, t, un, ut, H, c, c2, d, alpha, r, s);
+      for (int p = 0; p < nw; ++p)
+        for (int k = 0; k < m; ++k) wave[p * m + k] = alpha[p] * r[p * m + k];
+      break;
+    }
     case ORC_RP_EULER_HLLE: {
       double un, ut, H, c, c2;
       double fl[MAXM], fr[MAXM], qs[MAXM];
@@ -370,7 +404,8 @@ void orc_riemann(const orc_prob* P, int dir, const double* ql, const double* qr,
     split_fwaves(m, nw, wave, s, amdq, apdq);
     return;
   }
-  if (P->entropy_fix && (P->rp == ORC_RP_SW_ROE || P->rp == ORC_RP_EULER_ROE)) {
+  if (P->entropy_fix &&
+      (P->rp == ORC_RP_SW_ROE || P->rp == ORC_RP_EULER_ROE || P->rp == ORC_RP_EULER_TRACER)) {
     if (harten_hyman(P, dir, m, nw, ql, qr, wave, s, amdq, apdq)) return;
   }
   split_by_speed(m, nw, wave, s, amdq, apdq);
@@ -414,6 +449,12 @@ void orc_transverse(const orc_prob* P, int dir, const double* ql, const double* 
       nw = euler_eig(P, t, n, ut, un, H, c, c2, asdq, beta, r, lam);
       break;
     }
+    case ORC_RP_EULER_TRACER: {
+      double un, ut, H, c, c2;
+      euler_roe_avg(P, dir, ql, qr, &un, &ut, &H, &c, &c2);
+      nw = euler_tracer_eig(P, t, n, ut, un, H, c, c2, asdq, beta, r, lam);
+      break;
+    }
     default:
       return;
   }
@@ -436,14 +477,14 @@ int orc_char_matrices(const orc_prob* P, int dir, const double* ql, const double
   double un = 0, ut = 0, H = 0, c = 0, c2 = 0;
   if (P->rp == ORC_RP_ELASTICITY_FWAVE) return ORC_EINVAL;
   if (P->rp == ORC_RP_SW_ROE) sw_roe_avg(P, dir, ql, qr, &un, &ut, &c);
-  if (P->rp == ORC_RP_EULER_ROE || P->rp == ORC_RP_EULER_HLLE)
-    euler_roe_avg(P, dir, ql, qr, &un, &ut, &H, &c, &c2);
+  if (is_euler(P)) euler_roe_avg(P, dir, ql, qr, &un, &ut, &H, &c, &c2);
   for (int col = 0; col < m; ++col) {
     for (int k = 0; k < m; ++k) e[k] = (k == col) ? 1.0 : 0.0;
     switch (P->rp) {
       case ORC_RP_ADVECTION: alpha[0] = e[0]; r[0] = 1.0; break;
       case ORC_RP_ACOUSTICS: acoustics_eig(P, n, t, 1, e, alpha, r, lam); break;
       case ORC_RP_SW_ROE: sw_eig(P, n, t, un, ut, c, e, alpha, r, lam); break;
+      case ORC_RP_EULER_TRACER: euler_tracer_eig(P, n, t, un, ut, H, c, c2, e, alpha, r, lam); break;
       default: euler_eig(P, n, t, un, ut, H, c, c2, e, alpha, r, lam); break;
     }
     /* column col of L is L e_col = alpha */
@@ -734,9 +775,12 @@ static void sweep(const orc_prob* P, int dir, const garr* Q, const garr* A, doub
   }
 }
 
-static int classic2d(const orc_prob* P, double* q, const double* aux, double dt, double* cfl) {
+/* mask: 1 x-interfaces only, 2 y-interfaces only (one sweep of the
+ * dimensionally split method, no transverse terms), 3 the unsplit step */
+static int classic2d(const orc_prob* P, double* q, const double* aux, double dt, double* cfl,
+                     int mask) {
   int nx = P->nx, ny = P->ny, m = P->num_eqn, ma = P->num_aux;
-  double dtdx = dt / P->dx, dtdy = dt / P->dy;
+  double dtdx = (mask & 1) ? dt / P->dx : 0.0, dtdy = (mask & 2) ? dt / P->dy : 0.0;
   garr Q, A;
   double* qb = ghosted(P, q, m, 2, 0, &Q);
   double* ab = ghosted(P, aux, ma, 2, 1, &A);
@@ -745,8 +789,10 @@ static int classic2d(const orc_prob* P, double* q, const double* aux, double dt,
   iface_rec* Y = (iface_rec*)malloc(sizeof(iface_rec) * (size_t)(nx + 2) * (ny + 1));
   double* smx = (double*)malloc(sizeof(double) * (ny + 2));
   double* smy = (double*)malloc(sizeof(double) * (nx + 2));
-  sweep(P, 0, &Q, &A, dtdx, X, smx);
-  sweep(P, 1, &Q, &A, dtdy, Y, smy);
+  orc_prob Ps = *P;
+  if (mask != 3) Ps.transverse = 0;
+  sweep(&Ps, 0, &Q, &A, dtdx, X, smx);
+  sweep(&Ps, 1, &Q, &A, dtdy, Y, smy);
 #define XR(i, j) (X + (size_t)((j) + 1) * (nx + 1) + (i))
 #define YR(i, j) (Y + (size_t)((i) + 1) * (ny + 1) + (j))
   /* total correction fluxes: normal part plus transverse contributions */
@@ -790,7 +836,7 @@ static int classic2d(const orc_prob* P, double* q, const double* aux, double dt,
   double sx = 0.0, sy = 0.0;
   for (int l = 0; l < ny + 2; ++l) if (!(smx[l] <= sx)) sx = smx[l];
   for (int l = 0; l < nx + 2; ++l) if (!(smy[l] <= sy)) sy = smy[l];
-  double nx_ = dt * sx / P->dx, ny_ = dt * sy / P->dy;
+  double nx_ = (mask & 1) ? dt * sx / P->dx : 0.0, ny_ = (mask & 2) ? dt * sy / P->dy : 0.0;
   *cfl = (nx_ >= ny_ || isnan(nx_)) ? nx_ : ny_;
   free(qb); free(ab); free(X); free(Y); free(smx); free(smy); free(Ft); free(Gt);
   return ORC_OK;
@@ -798,12 +844,64 @@ static int classic2d(const orc_prob* P, double* q, const double* aux, double dt,
 
 static int classic3d(const orc_prob* P, double* q, double dt, double* cfl);
 
+/* ------------------------------------------------------------------------ */
+/* source terms by fractional steps (Sec. 3, Eq. (conslaw) right-hand side;  */
+/* Sec. 6.2 axisymmetric Euler)                                              */
+/* ------------------------------------------------------------------------ */
+
+/* axisymmetric geometric source of the Euler equations in (z, r) = (x, y):
+ * psi = -(1/r) (rho v, rho u v, rho v^2, (E + p) v) with v the radial
+ * velocity; the tracer has none */
+static void axisym_source(const orc_prob* P, const double* q, double r, double* f) {
+  int m = P->num_eqn;
+  double rho = q[0], u = q[1] / rho, v = q[2] / rho;
+  double p = euler_pressure(P, q);
+  for (int k = 0; k < m; ++k) f[k] = 0.0;
+  f[0] = -(rho * v) / r;
+  f[1] = -(rho * u * v) / r;
+  f[2] = -(rho * v * v) / r;
+  f[3] = -((q[3] + p) * v) / r;
+}
+
+/* the source ODE q' = psi(q) over dt in every cell by the two-stage
+ * second-order Runge-Kutta method (Heun): q1 = q + dt psi(q),
+ * q <- (q + q1 + dt psi(q1)) / 2 */
+void orc_source_step(const orc_prob* P, double* q, double dt) {
+  if (P->source != 1) return;
+  int nx = P->nx, ny = P->ny, m = P->num_eqn;
+  size_t plane = (size_t)nx * ny;
+  #pragma omp parallel for schedule(static)
+  for (int j = 0; j < ny; ++j) {
+    double r = P->lower[1] + (j + 0.5) * P->dy;
+    for (int i = 0; i < nx; ++i) {
+      double q0[MAXM], q1[MAXM], f0[MAXM], f1[MAXM];
+      size_t off = (size_t)j * nx + i;
+      for (int k = 0; k < m; ++k) q0[k] = q[k * plane + off];
+      axisym_source(P, q0, r, f0);
+      for (int k = 0; k < m; ++k) q1[k] = q0[k] + dt * f0[k];
+      axisym_source(P, q1, r, f1);
+      for (int k = 0; k < m; ++k) q[k * plane + off] = 0.5 * (q0[k] + (q1[k] + dt * f1[k]));
+    }
+  }
+}
+
 int orc_classic_step(const orc_prob* P, double* q, const double* aux, double dt, double* cfl) {
   if (P->ndim == 1) return classic1d(P, q, aux, dt, cfl);
   /* the 2D p-system is solved with SharpClaw only (normal solves, Sec. 6.3) */
   if (P->ndim == 2 && P->rp == ORC_RP_ELASTICITY_FWAVE) return ORC_EINVAL;
   if (P->ndim == 3) return classic3d(P, q, dt, cfl);
-  return classic2d(P, q, aux, dt, cfl);
+  int st;
+  if (P->dim_split) {
+    /* Godunov dimensional splitting: x sweeps over dt, then y sweeps over dt */
+    double c1, c2;
+    st = classic2d(P, q, aux, dt, &c1, 1);
+    if (st == ORC_OK) st = classic2d(P, q, aux, dt, &c2, 2);
+    *cfl = (c1 >= c2 || isnan(c1)) ? c1 : c2;
+  } else {
+    st = classic2d(P, q, aux, dt, cfl, 3);
+  }
+  if (st == ORC_OK) orc_source_step(P, q, dt);
+  return st;
 }
 
 
@@ -1297,6 +1395,7 @@ int orc_sharp_step(const orc_prob* P, double* q, const double* aux, double dt, d
     int ny1 = (P->ndim == 2) ? P->ny : 1;
     sharp_ctx c = {P, aux, dt, ORC_OK};
     *cfl = ssp104(sharp_L_fn, &c, (size_t)P->nx * ny1 * P->num_eqn, q, dt);
+    if (c.status == ORC_OK && P->ndim == 2) orc_source_step(P, q, dt);
     return c.status;
   }
   int ny = (P->ndim == 2) ? P->ny : 1;
@@ -1321,6 +1420,7 @@ int orc_sharp_step(const orc_prob* P, double* q, const double* aux, double dt, d
   memcpy(q, qk, sizeof(double) * ntot);
   *cfl = nu;
   free(qn); free(qk); free(L);
+  if (st == ORC_OK && P->ndim == 2) orc_source_step(P, q, dt);
   return st;
 }
 

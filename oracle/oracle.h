@@ -24,7 +24,8 @@ extern "C" {
 
 /* Riemann solver ids */
 enum { ORC_RP_ADVECTION = 0, ORC_RP_ACOUSTICS = 1, ORC_RP_SW_ROE = 2,
-       ORC_RP_EULER_ROE = 3, ORC_RP_EULER_HLLE = 4, ORC_RP_ELASTICITY_FWAVE = 5 };
+       ORC_RP_EULER_ROE = 3, ORC_RP_EULER_HLLE = 4, ORC_RP_ELASTICITY_FWAVE = 5,
+       ORC_RP_EULER_TRACER = 6 };
 /* wave limiters */
 enum { ORC_LIM_NONE = 0, ORC_LIM_MINMOD = 1, ORC_LIM_SUPERBEE = 2,
        ORC_LIM_VANLEER = 3, ORC_LIM_MC = 4 };
@@ -61,6 +62,11 @@ typedef struct {
    * weno_c[k*r+j] reconstruction, weno_d[k] optimal weights,
    * weno_b[(k*r+a)*r+b] smoothness quadratic forms */
   double weno_c[81], weno_d[9], weno_b[729];
+  int source;           /* 0 none; 1 axisymmetric Euler geometric source about y = 0
+                           (r = y; Sec. 6.2), by Godunov splitting after each step */
+  int dim_split;        /* classic 2D: 0 unsplit; 1 dimensional splitting (x sweeps,
+                           then y sweeps, Godunov) */
+  double lower[2];      /* lower corner of the grid (cell centres for the source) */
 } orc_prob;
 
 typedef struct {
@@ -116,6 +122,8 @@ int orc_sharp_step(const orc_prob* P, double* q, const double* aux, double dt, d
 double orc_ssp_rk3_linear(double lambda, double dt, double q0);
 /* One SSP(10,4) step of q' = lambda q (same stage code as orc_sharp_step). */
 double orc_ssp104_linear(double lambda, double dt, double q0);
+/* Apply the source step of the problem (P->source) for time dt to q in place. */
+void orc_source_step(const orc_prob* P, double* q, double dt);
 /* Largest first-order interface wave speed per direction on Q (used for dt0). */
 void orc_max_speeds(const orc_prob* P, const double* q, const double* aux, double* smax);
 

@@ -129,6 +129,53 @@ def shock_bubble_2d(nx=2048, ny=1024, t_end=0.2, scheme="sharpclaw", gamma=1.4,
     return spec
 
 
+def post_shock_state_from_pressure(p2, gamma=1.4, rho1=1.0, p1=1.0):
+    """Rankine-Hugoniot state behind the shock whose post-shock pressure is
+    p2 (gas at rest ahead): Mach^2 = 1 + (gamma+1)/(2 gamma) (p2/p1 - 1)."""
+    mach = math.sqrt(1.0 + (gamma + 1.0) / (2.0 * gamma) * (p2 / p1 - 1.0))
+    return post_shock_state(mach, gamma, rho1, p1)
+
+
+def shock_bubble_axisym(nx=1280, ny=320, t_end=0.6, scheme="classic", gamma=1.4, sub=16,
+                        dim_split=0, cfl=(0.8, 1.0)):
+    """The shock-bubble interaction of Sec. 6.2 in its axisymmetric form:
+    (z, r) = (x, y) on [0, 2] x [0, 0.5], Euler with a passive tracer and the
+    geometric source -(1/r)(rho v, rho u v, rho v^2, (E + p) v) by Godunov
+    splitting.  Ahead of the shock rho = p = 1 at rest; a sphere of rho = 0.1
+    (p = 1), radius 0.2, centred on the axis at z = 0.5, carries tracer 1
+    (cell fractions from a sub x sub point sample); the shock at z = 0.2 has
+    the paper's post-shock pressure 5 (rho and u by Rankine-Hugoniot, about
+    2.82 and 1.61), which also enters at the left.  Reflecting axis r = 0,
+    extrapolation at r = 0.5 and z = 2.  Classic unsplit with full
+    transverse corrections, MC limiter, CFL 0.8."""
+    x = _centers(0.0, 2.0, nx)
+    y = _centers(0.0, 0.5, ny)
+    dx, dy = 2.0 / nx, 0.5 / ny
+    off = (np.arange(sub) + 0.5) / sub - 0.5
+    frac = np.zeros((ny, nx))
+    X, Y = np.meshgrid(x, y, indexing="xy")
+    for a in off:
+        for b in off:
+            frac += ((X + a * dx - 0.5) ** 2 + (Y + b * dy) ** 2 < 0.04)
+    frac /= sub * sub
+    rho = frac * 0.1 + (1.0 - frac) * 1.0
+    E = np.full_like(rho, 1.0 / (gamma - 1.0))
+    rho2, u2, p2 = post_shock_state_from_pressure(5.0, gamma)
+    E2 = p2 / (gamma - 1.0) + 0.5 * rho2 * u2 * u2
+    left = X < 0.2
+    rho = np.where(left, rho2, rho)
+    mx = np.where(left, rho2 * u2, 0.0)
+    E = np.where(left, E2, E)
+    tracer = np.where(left, 0.0, frac)
+    q0 = np.stack([rho, mx, np.zeros_like(rho), E, tracer])
+    spec = _base(2, [nx, ny], [0.0, 0.0], [2.0, 0.5], "euler_tracer", scheme=scheme,
+                 params=[gamma], source="axisymmetric", dim_split=dim_split,
+                 bc_lower=["inflow", "wall"], bc_upper=["extrap", "extrap"],
+                 inflow=[rho2, rho2 * u2, 0.0, E2, 0.0], cfl_desired=cfl[0], cfl_max=cfl[1])
+    spec.update(q0=np.ascontiguousarray(q0), aux=None, t_end=t_end)
+    return spec
+
+
 # --------------------------------------------------------------------------
 # Listing 1: 2D Euler Riemann problem (Lax-Liu case 6), the paper's hello world
 # --------------------------------------------------------------------------
@@ -281,12 +328,14 @@ def random_smooth_2d(rp, nx, ny, seed=SEED, params=None, bc="periodic", **kw):
     if rp == "sw_roe":
         q0 = np.stack([1.0 + field(0.1), field(0.1), field(0.1)])
         params = params or [1.0]
-    elif rp in ("euler_roe", "euler_hlle"):
+    elif rp in ("euler_roe", "euler_hlle", "euler_tracer"):
         rho = 1.0 + field(0.1)
         mx, my = field(0.2), field(0.2)
         p = 1.0 + field(0.1)
         E = p / 0.4 + 0.5 * (mx * mx + my * my) / rho
         q0 = np.stack([rho, mx, my, E])
+        if rp == "euler_tracer":
+            q0 = np.concatenate([q0, (0.5 + field(0.5))[None]])
         params = params or [1.4]
     elif rp == "acoustics":
         q0 = np.stack([field(0.5), field(0.5), field(0.5)])
@@ -337,11 +386,13 @@ def random_1d(rp, n, seed=SEED, bc=("periodic", "periodic"), jump=True, **kw):
     if rp == "sw_roe":
         q0 = np.stack([1.5 + field(0.2), field(0.3)])
         params = [1.0]
-    elif rp in ("euler_roe", "euler_hlle"):
+    elif rp in ("euler_roe", "euler_hlle", "euler_tracer"):
         rho = 1.5 + field(0.2)
         m = field(0.3)
         p = 1.5 + field(0.2)
         q0 = np.stack([rho, m, p / 0.4 + 0.5 * m * m / rho])
+        if rp == "euler_tracer":
+            q0 = np.concatenate([q0, (0.5 + field(0.5))[None]])
         params = [1.4]
     elif rp == "acoustics":
         q0 = np.stack([field(0.5), field(0.5)])
