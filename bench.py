@@ -371,6 +371,36 @@ def bench_shockbubble(prec, steps, warmup, nx=2048, ny=1024, weno_order=5,
                            prec.upper())}
 
 
+def bench_axisym(prec, steps, warmup, nx=1280, ny=320, dim_split=0):
+    """The axisymmetric shock-bubble of Sec. 6.2 at the paper's 1280 x 320:
+    Euler + tracer, classic unsplit with full transverse corrections (or
+    dimensionally split), geometric source by Godunov splitting; one step =
+    the step kernel (two when split) + the source kernel + its marker."""
+    import torch
+    from paper_1111_6583_gb300 import claw
+    from paper_1111_6583_gb300 import workloads as wl
+    spec = wl.shock_bubble_axisym(nx=nx, ny=ny, dim_split=dim_split)
+    if dim_split:
+        spec["transverse"] = 0
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = claw.Solver(spec, prec, stream=stream.cuda_stream)
+        tile = s.tune()
+        s.set_t_end(spec["t_end"])
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        s.advance(warmup)
+    stream.synchronize()
+    ms = timed_steps(s, stream, steps, flush)
+    s.close()
+    avg = sum(ms) / len(ms)
+    return {"value": nx * ny * len(ms) / (sum(ms) * 1e-3), "unit": UNIT, "ms_per_step": avg,
+            "tile": list(tile) if tile else None,
+            "workload": "axisymmetric shock-bubble %dx%d, Euler + tracer, classic %s, "
+                        "geometric source (Godunov), %s"
+                        % (nx, ny, "dimensionally split" if dim_split else "unsplit full "
+                           "transverse", prec.upper())}
+
+
 def bench_psystem(prec, steps, warmup, periods=32, cells_per_period=64):
     """2D p-system in the checkerboard medium (Sec. 6.3), SharpClaw WENO5
     component-wise + SSP(10,4): one step = ten fused stage launches."""
@@ -563,6 +593,8 @@ def main():
         line["shock_bubble"]["fp64_weno7_ssp104"] = bench_shockbubble("fp64", 3, 3, weno_order=7,
                                                                       integrator="ssp104")
         line["psystem_checkerboard"] = {p: bench_psystem(p, 3, 3) for p in ("fp64", "fp32")}
+        line["axisym_shock_bubble"] = {p: bench_axisym(p, 20, 3) for p in ("fp64", "fp32")}
+        line["axisym_shock_bubble"]["fp64_split"] = bench_axisym("fp64", 20, 3, dim_split=1)
         try:
             line["batched_elasticity"] = bench_elasticity(args.members, 100, 16)
         except Exception as ex:  # reported, not hidden

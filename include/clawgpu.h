@@ -58,7 +58,14 @@ enum {
 enum { CLAW_FP64 = 0, CLAW_FP32 = 1 };
 enum { CLAW_CLASSIC = 0, CLAW_SHARPCLAW = 1 };
 enum { CLAW_RP_ADVECTION = 0, CLAW_RP_ACOUSTICS = 1, CLAW_RP_SW_ROE = 2,
-       CLAW_RP_EULER_ROE = 3, CLAW_RP_EULER_HLLE = 4, CLAW_RP_ELASTICITY_FWAVE = 5 };
+       CLAW_RP_EULER_ROE = 3, CLAW_RP_EULER_HLLE = 4, CLAW_RP_ELASTICITY_FWAVE = 5,
+       CLAW_RP_EULER_TRACER = 6 };
+/* Source terms (Eq. (conslaw) right-hand side), by Godunov splitting after
+ * every accepted step: CLAW_SOURCE_AXISYMMETRIC is the geometric source of
+ * the Euler equations in cylindrical symmetry about y = 0 (Sec. 6.2:
+ * (z, r) = (x, y); -(1/r)(rho v, rho u v, rho v^2, (E + p) v), tracer none),
+ * integrated over the step by a two-stage second-order Runge-Kutta method. */
+enum { CLAW_SOURCE_NONE = 0, CLAW_SOURCE_AXISYMMETRIC = 1 };
 enum { CLAW_LIM_NONE = 0, CLAW_LIM_MINMOD = 1, CLAW_LIM_SUPERBEE = 2, CLAW_LIM_VANLEER = 3,
        CLAW_LIM_MC = 4 };
 enum { CLAW_BC_PERIODIC = 0, CLAW_BC_WALL = 1, CLAW_BC_EXTRAP = 2, CLAW_BC_INFLOW = 3 };
@@ -100,6 +107,9 @@ typedef struct {
   int num_eqn;         /* filled in by claw_method_init / validated by create     */
   int num_aux;         /* elasticity: 2 (rho, K per cell); others 0               */
   int time_integrator; /* SharpClaw: CLAW_SSP_RK3 (default) | CLAW_SSP104          */
+  int source;          /* CLAW_SOURCE_*; axisymmetric: 2D Euler systems, y >= 0    */
+  int dim_split;       /* classic 2D: 0 unsplit (default); 1 dimensional splitting
+                          (x sweeps then y sweeps over dt, no transverse terms)    */
 } claw_method;
 
 typedef struct {

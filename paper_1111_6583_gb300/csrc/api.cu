@@ -35,6 +35,7 @@ KernelSet kernels_for(int rp, int nd, int prec) {
     case CLAW_RP_EULER_ROE: return claw_kernels_euler_roe(nd, prec);
     case CLAW_RP_EULER_HLLE: return claw_kernels_euler_hlle(nd, prec);
     case CLAW_RP_ELASTICITY_FWAVE: return claw_kernels_elasticity(nd, prec);
+    case CLAW_RP_EULER_TRACER: return claw_kernels_euler_tracer(nd, prec);
   }
   return KernelSet{};
 }
@@ -60,7 +61,7 @@ void fill_consts(const claw_method& m, MConsts<R>& C) {
   C.weno_r = (m.weno_order + 1) / 2;
   C.lim = m.lim;
   C.order = m.order;
-  C.transverse = m.transverse;
+  C.transverse = m.dim_split ? 0 : m.transverse;
   C.entropy_fix = m.entropy_fix;
   C.char_decomp = m.char_decomp;
   for (int d = 0; d < 3; ++d) {
@@ -89,6 +90,7 @@ int num_eqn(int rp, int nd) {
     case CLAW_RP_EULER_ROE:
     case CLAW_RP_EULER_HLLE: return nd <= 2 ? nd + 2 : 0;
     case CLAW_RP_ELASTICITY_FWAVE: return nd <= 2 ? nd + 1 : 0;
+    case CLAW_RP_EULER_TRACER: return nd <= 2 ? nd + 3 : 0;
   }
   return 0;
 }
@@ -97,7 +99,7 @@ int num_eqn(int rp, int nd) {
 const char* check_method(const claw_method& m, int nd) {
   if (nd < 1 || nd > 3) return "ndim must be 1, 2 or 3";
   if (nd == 3 && m.scheme != CLAW_CLASSIC) return "3D grids use the classic scheme";
-  if (m.rp < 0 || m.rp > 5) return "unknown Riemann solver";
+  if (m.rp < 0 || m.rp > 6) return "unknown Riemann solver";
   if (num_eqn(m.rp, nd) == 0) return "solver not available in this dimension";
   if (m.num_eqn != num_eqn(m.rp, nd)) return "num_eqn does not match the Riemann solver";
   const int na = m.rp == CLAW_RP_ELASTICITY_FWAVE ? 2 : 0;
@@ -117,6 +119,15 @@ const char* check_method(const claw_method& m, int nd) {
     return "no characteristic projection for the f-wave elasticity solver";
   if (m.scheme == CLAW_CLASSIC && nd == 2 && m.rp == CLAW_RP_ELASTICITY_FWAVE)
     return "the 2D p-system has normal solves only: use SharpClaw";
+  if (m.source != CLAW_SOURCE_NONE && m.source != CLAW_SOURCE_AXISYMMETRIC)
+    return "unknown source term";
+  if (m.source == CLAW_SOURCE_AXISYMMETRIC &&
+      !(nd == 2 && (m.rp == CLAW_RP_EULER_ROE || m.rp == CLAW_RP_EULER_HLLE ||
+                    m.rp == CLAW_RP_EULER_TRACER)))
+    return "the axisymmetric source needs a 2D Euler system";
+  if (m.dim_split != 0 && m.dim_split != 1) return "dim_split must be 0 or 1";
+  if (m.dim_split && !(m.scheme == CLAW_CLASSIC && nd == 2))
+    return "dimensional splitting is for the classic 2D scheme";
   if (!(m.cfl_desired > 0) || !(m.cfl_max >= m.cfl_desired)) return "need 0 < cfl_desired <= cfl_max";
   if (!(m.dt_max > 0)) return "dt_max must be positive";
   if (m.max_retries < 0) return "max_retries must be >= 0";
@@ -143,6 +154,8 @@ const char* check_grid(const claw_grid& g, const claw_method& m) {
     if (g.n[d] > (int64_t)INT_MAX / 2) return "too many cells in one direction";
     if (!(g.upper[d] > g.lower[d])) return "upper must exceed lower";
   }
+  if (m.source == CLAW_SOURCE_AXISYMMETRIC && !(g.ndim == 2 && g.lower[1] >= 0.0))
+    return "the axisymmetric source needs r = y >= 0 on the grid";
   return nullptr;
 }
 
@@ -160,7 +173,7 @@ int maxspeed_tiles(int nx, int ny) {
 // state buffers a scheme rotates through: classic Q^n, Q^{n+1}; SSP-RK3 adds
 // one stage state; SSP(10,4) two (its two low-storage registers)
 int nbuf_of(const claw_method& m) {
-  if (m.scheme == CLAW_CLASSIC) return 2;
+  if (m.scheme == CLAW_CLASSIC) return m.dim_split ? 3 : 2;
   return m.time_integrator == CLAW_SSP104 ? 4 : 3;
 }
 
@@ -178,7 +191,11 @@ DevCtl make_ctl(const claw_method& m, const claw_grid& g, int nbuf, double t0, d
   c.dt_init = m.dt_initial;
   c.max_steps = LLONG_MAX;
   c.nbuf = nbuf;
-  c.accept_shift = (m.scheme == CLAW_SHARPCLAW && m.time_integrator == CLAW_SSP104) ? 2 : 1;
+  c.accept_shift = ((m.scheme == CLAW_SHARPCLAW && m.time_integrator == CLAW_SSP104) ||
+                    (m.scheme == CLAW_CLASSIC && m.dim_split))
+                       ? 2
+                       : 1;
+  for (int d = 0; d < 3; ++d) c.lo[d] = d < g.ndim ? g.lower[d] : 0.0;
   c.max_retries = m.max_retries;
   c.ndim = g.ndim;
   c.done = (t0 >= t_end) ? 1 : 0;
@@ -212,20 +229,35 @@ void fill_info(const DevCtl& c, claw_step_info* info) {
 }
 
 // Launch one attempt (classic: one kernel; SharpClaw: three stage kernels).
+// Launch one attempt: classic, one kernel (two sweeps when dimensionally
+// split); SharpClaw, one kernel per stage; then the source step over the
+// cell tiles (mtiles) when the method has one.
 cudaError_t launch_attempt(const KernelSet& ks, const claw_method& m, const Member* mem,
                            const Tile* tiles, int ntiles, const void* consts, int bw, int h,
-                           cudaStream_t st) {
+                           cudaStream_t st, const Tile* mtiles = nullptr, int nmtiles = 0,
+                           int nmembers = 1) {
   LaunchArgs a{mem, tiles, ntiles, consts, bw, h, 0, st};
-  if (m.scheme == CLAW_CLASSIC) return ks.classic(a);
-  const StageOp* ops;
-  const int ns = stage_table(m.time_integrator, &ops);
-  for (int s = 0; s < ns; ++s) {
-    a.stage = s;
-    a.stage_op = ops + s;
-    cudaError_t e = ks.sharp(a);
-    if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
+  if (m.scheme == CLAW_CLASSIC) {
+    if (m.dim_split) {
+      a.sweep = 1;
+      if ((e = ks.classic(a)) != cudaSuccess) return e;
+      a.sweep = 2;
+    }
+    e = ks.classic(a);
+  } else {
+    const StageOp* ops;
+    const int ns = stage_table(m.time_integrator, &ops);
+    for (int s = 0; s < ns && e == cudaSuccess; ++s) {
+      a.stage = s;
+      a.stage_op = ops + s;
+      e = ks.sharp(a);
+    }
   }
-  return cudaSuccess;
+  if (e != cudaSuccess || m.source == CLAW_SOURCE_NONE) return e;
+  LaunchArgs b{mem, mtiles, nmtiles, consts, 0, 0, 0, st};
+  if ((e = ks.source(b)) != cudaSuccess) return e;
+  return launch_source_mark(mem, nmembers, st);
 }
 
 double now_s() {
@@ -310,7 +342,7 @@ cudaError_t solver_attempt(claw_solver* s, cudaStream_t st) {
     return s->ks.classic(a);
   }
   return launch_attempt(s->ks, s->m, s->d_mem, nullptr, s->ntiles, s->consts.data(), s->bw,
-                        s->h, st);
+                        s->h, st, nullptr, maxspeed_tiles(s->h_mem.nx, s->h_mem.ny), 1);
 }
 
 cudaError_t read_ctl(claw_solver* s) {
@@ -375,11 +407,11 @@ cudaError_t autotune(claw_solver* s) {
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   float best = 1e30f;
-  int bb = 128, bh = 32;
+  int bb = s->ks.max_bw, bh = 32;
   for (int ib = 0; ib < 2; ++ib)
     for (int ih = 0; ih < 5; ++ih) {
       const int bw = bws[ib], h = hs[ih];
-      if (h > 2 * ny) continue;
+      if (h > 2 * ny || bw > s->ks.max_bw) continue;
       const int nt = classic2d_tiles(nx, ny, bw, h);
       mt.ntiles = nt;
       if ((e = cudaMemcpyAsync(s->d_mem_tune, &mt, sizeof(Member), cudaMemcpyHostToDevice,
@@ -455,7 +487,7 @@ claw_status claw_method_init(claw_method* m, int rp, int ndim) {
     g_err = "ndim must be 1, 2 or 3";
     return CLAW_EINVAL;
   }
-  if (rp < 0 || rp > 5 || num_eqn(rp, ndim) == 0) {
+  if (rp < 0 || rp > 6 || num_eqn(rp, ndim) == 0) {
     g_err = "unknown Riemann solver for this dimension";
     return CLAW_EINVAL;
   }
@@ -506,6 +538,7 @@ claw_status claw_solver_create(const claw_method* m, const claw_grid* g, void* s
   s->prec = m->prec;
   s->nbuf = nbuf_of(*m);
   s->ks = ks;
+  s->bw = std::min(s->bw, ks.max_bw);
   s->consts = make_consts(*m);
   s->ustream = (cudaStream_t)stream;
   s->sbytes = state_bytes_of(*m, s->g);
@@ -582,7 +615,8 @@ claw_status claw_solver_tune(claw_solver* s, int mode, int* bw, int* h) {
     SCK(autotune(s));
     SCK(leave(s));
   } else {
-    if (!bw || !h || (*bw != 64 && *bw != 128) || *h < 1) return fail(s, "bad tile shape");
+    if (!bw || !h || (*bw != 64 && *bw != 128) || *h < 1 || *bw > s->ks.max_bw)
+      return fail(s, "bad tile shape");
     s->bw = *bw;
     s->h = *h;
     if (s->nd != 3)
@@ -888,7 +922,7 @@ void batch_free(claw_batch* b) {
 
 cudaError_t batch_attempt(claw_batch* b, cudaStream_t st) {
   return launch_attempt(b->ks, b->m, b->d_mem, b->d_tiles, b->ntiles, b->consts.data(),
-                        b->bw, b->h, st);
+                        b->bw, b->h, st, b->d_mtiles, b->nmtiles, b->n);
 }
 
 }  // namespace
@@ -915,6 +949,7 @@ claw_status claw_batch_create(const claw_method* m, const claw_grid* grids, int 
   b->nbuf = nbuf_of(*m);
   b->n = n;
   b->ks = ks;
+  b->bw = std::min(b->bw, ks.max_bw);
   b->consts = make_consts(*m);
   b->grids.assign(grids, grids + n);
   for (auto& g : b->grids)
@@ -1179,6 +1214,8 @@ claw_status claw_server_create(const claw_method* m, size_t hbm_budget_bytes, in
   *out = nullptr;
   const int nd = (m->num_eqn == num_eqn(m->rp, 2)) ? 2 : 1;
   if (const char* why = check_method(*m, nd)) return sfail(nullptr, why);
+  if (m->source != CLAW_SOURCE_NONE)
+    return sfail(nullptr, "the server takes methods without source terms");
   KernelSet ks = kernels_for(m->rp, nd, m->prec);
   if (!ks.valid) return sfail(nullptr, "no kernels for this solver/dimension/precision");
   claw_server* v = new claw_server();
@@ -1187,6 +1224,7 @@ claw_status claw_server_create(const claw_method* m, size_t hbm_budget_bytes, in
   v->nd = nd;
   v->nbuf = nbuf_of(*m);
   v->ks = ks;
+  v->bw = std::min(v->bw, ks.max_bw);
   v->consts = make_consts(*m);
   v->budget = hbm_budget_bytes;
   v->max_slots = max_slots;

@@ -326,10 +326,13 @@ __device__ __forceinline__ void solve_cells(const MConsts<R>& C, const R (&ql)[R
     RP::template solve<DIR>(C, ql, qr, nullptr, nullptr, W, s, am, ap, x);
 }
 
+// sweep: 0 the unsplit step (Q^n in slot 0 -> slot 1, runs the controller);
+// dimensional splitting (Godunov) as two launches: 1 the x sweeps (slot 0 ->
+// slot 1), 2 the y sweeps (slot 1 -> slot 2, runs the controller).
 template <class RP, typename R, int BW>
 __global__ void __launch_bounds__(BW)
     classic2d_kernel(const Member* __restrict__ members, const Tile* __restrict__ tiles,
-                     int ntiles_total, const MConsts<R> C, int H) {
+                     int ntiles_total, const MConsts<R> C, int H, int sweep) {
   constexpr int M = RP::M, MW = RP::MW, NC = RP::NCTX;
   constexpr int NP = RP::NPC > 0 ? RP::NPC : 1;
   using NZX = typename RP::template NZ<0>;
@@ -373,8 +376,9 @@ __global__ void __launch_bounds__(BW)
     const bool xlim = (l >= 2) && (l <= BW - 2);
     const bool xcfl = xlim && (c <= nx);
     const bool ylim = (l >= 1) && (l <= BW - 2);
-    const R* __restrict__ q = (const R*)mb.q[s_cur];
-    R* __restrict__ qo = (R*)mb.q[(s_cur + 1) % s_nbuf];
+    const bool dox = sweep != 2, doy = sweep != 1;
+    const R* __restrict__ q = (const R*)mb.q[(s_cur + (sweep == 2 ? 1 : 0)) % s_nbuf];
+    R* __restrict__ qo = (R*)mb.q[(s_cur + (sweep == 2 ? 2 : 1)) % s_nbuf];
     const R dtdx = s_k[0], dtdy = s_k[1], kxy = s_k[2];
     const size_t plane = (size_t)nx * ny;
 
@@ -423,7 +427,7 @@ __global__ void __launch_bounds__(BW)
 
       // (2) y-interface Rw (rows Rw-1, Rw)
       R nW[MW][M], ns[MW], nam[M], nap[M], nx_[NC], nnrm[MW], ndot[MW];
-      const bool yrow = Rw >= r0 - 1;
+      const bool yrow = doy && Rw >= r0 - 1;
       if (yrow) {
         solve_cells<RP, 1, R, NP>(C, qm1, qc, pm1, pcc, nW, ns, nam, nap, nx_);
 #pragma unroll
@@ -446,7 +450,7 @@ __global__ void __launch_bounds__(BW)
       __syncthreads();  // qs ready
 
       // (3) x-interface (c, Rw)
-      const bool xrow = (Rw >= r0 - 1) && (Rw <= rend + 1);
+      const bool xrow = dox && (Rw >= r0 - 1) && (Rw <= rend + 1);
       R xW[MW][M], xs[MW], xam[M], xap[M], xx[NC];
       if (xrow && l >= 1) {
         R ql[M], pl[NP];
@@ -527,7 +531,7 @@ __global__ void __launch_bounds__(BW)
       }
 
       // (5) y-limiting of interface Rw-1, corrections, transverse propagation
-      if (ylim && Rw - 1 >= r0 && Rw - 1 <= rend + 1) {
+      if (doy && ylim && Rw - 1 >= r0 && Rw - 1 <= rend + 1) {
         R G[M];
         if (C.order == 2) {
           R dot[MW];
@@ -629,7 +633,7 @@ __global__ void __launch_bounds__(BW)
         for (int k = 0; k < NC; ++k) yx[k] = nx_[k];
       }
     }
-    finish_attempt<R>(ctl, smx, smy, bad, mb.ntiles, true);
+    finish_attempt<R>(ctl, smx, smy, bad, mb.ntiles, sweep != 1);
   }
 }
 

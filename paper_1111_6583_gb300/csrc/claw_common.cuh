@@ -25,9 +25,11 @@ struct DevCtl {
   double cfl_desired, cfl_max;
   double nu_last, nu_max_seen, dt_used;
   double dx[3];
+  double lo[3];     // lower corner of the grid (cell centres for source terms)
   double dt_init;   // first dt (<= 0: from the wave speeds of Q^0)
   unsigned long long smax[3];  // bit patterns of max |s| per direction (non-negative)
   long long steps, rejects, max_steps;
+  long long src_mark;  // accepted steps whose source step has been applied
   int cur;          // buffer holding Q^n
   int nbuf;         // 2 (classic), 3 (SharpClaw SSP-RK3) or 4 (SharpClaw SSP(10,4))
   int accept_shift; // buffer rotation on acceptance (slot of the new state)

@@ -158,6 +158,19 @@ int stage_table(int integrator, const StageOp** ops) {
   return 3;
 }
 
+__global__ void source_mark_kernel(const Member* __restrict__ members, int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) {
+    DevCtl* c = members[k].ctl;
+    c->src_mark = c->steps;
+  }
+}
+
+cudaError_t launch_source_mark(const Member* members, int n, cudaStream_t st) {
+  source_mark_kernel<<<(n + 127) / 128, 128, 0, st>>>(members, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_dt_init(DevCtl* ctls, int n, cudaStream_t st) {
   dt_init_kernel<<<(n + 127) / 128, 128, 0, st>>>(ctls, n);
   return cudaGetLastError();

@@ -26,6 +26,7 @@ struct LaunchArgs {
   void* work3;             // 3D: per-face arrays (device)
   size_t work3_bytes;
   const StageOp* stage_op; // SharpClaw: explicit stage (host pointer) or null
+  int sweep;               // 2D classic: 0 unsplit, 1 / 2 the x / y sweeps of a split step
 };
 
 // stage tables of the SharpClaw time integrators
@@ -40,6 +41,8 @@ struct KernelSet {
   launch_fn classic;       // one attempt (1D or 2D by the member grid)
   launch_fn sharp;         // one SSP-RK3 stage
   launch_fn maxspeed;      // first-order interface speeds into ctl->smax
+  launch_fn source;        // axisymmetric Euler source step (2D Euler systems)
+  int max_bw;              // 2D classic: widest block whose static shared memory fits
 };
 
 // tile geometry shared by the host (tile tables) and the kernels
@@ -72,9 +75,13 @@ KernelSet claw_kernels_sw(int nd, int prec);
 KernelSet claw_kernels_euler_roe(int nd, int prec);
 KernelSet claw_kernels_euler_hlle(int nd, int prec);
 KernelSet claw_kernels_elasticity(int nd, int prec);
+KernelSet claw_kernels_euler_tracer(int nd, int prec);
 
 // generic kernels (k_common.cu)
 cudaError_t launch_dt_init(DevCtl* ctls, int n, cudaStream_t st);
+// after a source launch: record that every member's accepted steps have had
+// their source step (members[k].ctl->src_mark = steps)
+cudaError_t launch_source_mark(const Member* members, int n, cudaStream_t st);
 cudaError_t launch_set_t_end(DevCtl* ctls, int n, double t_end, long long max_steps_rel,
                              cudaStream_t st);
 cudaError_t launch_force_dt(DevCtl* ctl, double dt, cudaStream_t st);

@@ -60,6 +60,68 @@ __global__ void __launch_bounds__(kMaxspeedCells)
 
 inline int launch_grid(int ntiles) { return ntiles < 1 ? 1 : ntiles; }
 
+// Axisymmetric Euler geometric source (Sec. 6.2), Godunov-split after an
+// accepted step: with r = y (cell centre) and v the radial velocity,
+// psi(q) = -(1/r) (rho v, rho u v, rho v^2, (E + p) v, 0 for a tracer), over the
+// step's dt by the two-stage Runge-Kutta method q1 = q + dt psi(q),
+// q <- (q + q1 + dt psi(q1)) / 2.  A member whose accepted-step count equals
+// its source mark has nothing pending (rejected or skipped attempt).
+template <class RP, typename R>
+__device__ __forceinline__ void axisym_psi(const MConsts<R>& C, const R (&q)[RP::M], R r,
+                                           R (&f)[RP::M]) {
+  const R rho = q[0], u = FM<R>::div(q[1], rho), v = FM<R>::div(q[2], rho);
+  const R ke = q[1] * q[1] + q[2] * q[2];
+  const R p = C.gm1 * (q[3] - R(0.5) * ke / rho);
+#pragma unroll
+  for (int k = 0; k < RP::M; ++k) f[k] = R(0);
+  f[0] = -FM<R>::div(rho * v, r);
+  f[1] = -FM<R>::div(rho * u * v, r);
+  f[2] = -FM<R>::div(rho * v * v, r);
+  f[3] = -FM<R>::div((q[3] + p) * v, r);
+}
+
+template <class RP, typename R>
+__global__ void __launch_bounds__(kMaxspeedCells)
+    axisym_source_kernel(const Member* __restrict__ members, const Tile* __restrict__ tiles,
+                         int ntiles_total, const MConsts<R> C) {
+  constexpr int M = RP::M;
+  for (int it = blockIdx.x; it < ntiles_total; it += gridDim.x) {
+    const Tile tl = tiles ? tiles[it] : Tile{0, it};
+    const Member& mb = members[tl.member];
+    const DevCtl* ctl = mb.ctl;
+    if (ctl->steps == ctl->src_mark) continue;
+    const int nx = mb.nx, ny = mb.ny;
+    const long long cell = (long long)tl.tile * kMaxspeedCells + threadIdx.x;
+    if (cell >= (long long)nx * ny) continue;
+    const int j = (int)(cell / nx);
+    R* q = (R*)mb.q[ctl->cur];
+    const size_t plane = (size_t)nx * ny;
+    const R dt = (R)ctl->dt_used;
+    const R r = (R)(ctl->lo[1] + ((double)j + 0.5) * ctl->dx[1]);
+    R q0[M], q1[M], f0[M], f1[M];
+#pragma unroll
+    for (int k = 0; k < M; ++k) q0[k] = q[k * plane + cell];
+    axisym_psi<RP, R>(C, q0, r, f0);
+#pragma unroll
+    for (int k = 0; k < M; ++k) q1[k] = q0[k] + dt * f0[k];
+    axisym_psi<RP, R>(C, q1, r, f1);
+#pragma unroll
+    for (int k = 0; k < M; ++k) q[k * plane + cell] = R(0.5) * (q0[k] + (q1[k] + dt * f1[k]));
+  }
+}
+
+// static shared memory of classic2d_kernel<RP, R, BW> (its arrays; the block
+// reduction adds under 1 KB); a block may declare at most 48 KB statically
+template <class RP, typename R>
+constexpr size_t classic2d_smem(int bw) {
+  return sizeof(R) * (size_t)bw *
+         (size_t)(RP::M + RP::MW * RP::M + 6 * RP::M + (RP::NPC > 0 ? RP::NPC : 1));
+}
+template <class RP, typename R>
+constexpr bool classic2d_fits(int bw) {
+  return classic2d_smem<RP, R>(bw) + 1024 <= 48 * 1024;
+}
+
 template <class RP, typename R, int ND>
 struct Launchers {
   static cudaError_t classic(const LaunchArgs& a) {
@@ -85,14 +147,16 @@ struct Launchers {
           <<<launch_grid(a.ntiles_total), kClassic1dThreads, 0, a.stream>>>(a.members, a.tiles,
                                                                          a.ntiles_total, C);
     } else {
-      if (a.bw == 64)
-        classic2d_kernel<RP, R, 64>
-            <<<launch_grid(a.ntiles_total), 64, 0, a.stream>>>(a.members, a.tiles,
-                                                               a.ntiles_total, C, a.h);
-      else
-        classic2d_kernel<RP, R, 128>
-            <<<launch_grid(a.ntiles_total), 128, 0, a.stream>>>(a.members, a.tiles,
-                                                                a.ntiles_total, C, a.h);
+      if constexpr (classic2d_fits<RP, R>(128)) {
+        if (a.bw == 128) {
+          classic2d_kernel<RP, R, 128><<<launch_grid(a.ntiles_total), 128, 0, a.stream>>>(
+              a.members, a.tiles, a.ntiles_total, C, a.h, a.sweep);
+          return cudaGetLastError();
+        }
+      }
+      if (a.bw != 64) return cudaErrorInvalidValue;
+      classic2d_kernel<RP, R, 64><<<launch_grid(a.ntiles_total), 64, 0, a.stream>>>(
+          a.members, a.tiles, a.ntiles_total, C, a.h, a.sweep);
     }
     return cudaGetLastError();
   }
@@ -132,6 +196,17 @@ struct Launchers {
               a.members, a.tiles, a.ntiles_total, C, op);
     }
   }
+  static cudaError_t source(const LaunchArgs& a) {
+    const MConsts<R>& C = *(const MConsts<R>*)a.consts;
+    if constexpr (ND == 2 && is_euler_rp<RP>::value) {
+      axisym_source_kernel<RP, R><<<launch_grid(a.ntiles_total), kMaxspeedCells, 0, a.stream>>>(
+          a.members, a.tiles, a.ntiles_total, C);
+      return cudaGetLastError();
+    } else {
+      (void)C;
+      return cudaErrorNotSupported;
+    }
+  }
   static cudaError_t maxspeed(const LaunchArgs& a) {
     const MConsts<R>& C = *(const MConsts<R>*)a.consts;
     if constexpr (ND == 3) {
@@ -157,6 +232,8 @@ KernelSet make_set(bool has_char) {
   k.classic = &Launchers<RP, R, ND>::classic;
   k.sharp = &Launchers<RP, R, ND>::sharp;
   k.maxspeed = &Launchers<RP, R, ND>::maxspeed;
+  k.source = &Launchers<RP, R, ND>::source;
+  k.max_bw = classic2d_fits<RP, R>(128) ? 128 : 64;
   return k;
 }
 

@@ -895,6 +895,149 @@ struct RpElasticity {
 };
 
 // ---------------------------------------------------------------------------
+// Euler with a passive tracer phi (phi_t + u . grad phi = 0; Sec. 6.2): the
+// Euler Roe solver on the first ND + 2 components and a tracer wave (the jump
+// of phi alone) moving with the normal Roe velocity, placed before the u + c
+// wave.  The tracer equation is not in conservation form, so SharpClaw's
+// in-cell fluctuation comes from a Riemann solve (INCELL_SOLVE), not from a
+// flux difference.
+// ---------------------------------------------------------------------------
+template <typename R, int ND>
+struct RpEulerTracer {
+  using EU = RpEulerRoe<R, ND>;
+  static constexpr int ME = EU::M;                 // Euler components
+  static constexpr int M = ME + 1, MW = ME + 1, MA = 0, NCTX = EU::NCTX, NPC = 0;
+  static constexpr int TR = ME;                    // tracer component
+  static constexpr int E = EU::E;                  // energy component
+  static constexpr bool FWAVE = false, INCELL_SOLVE = true;
+  static constexpr int WALL_X = 1, WALL_Y = (ND == 2) ? 2 : -1;
+  template <int DIR>
+  struct NZ {
+    // Euler waves carry no tracer; the tracer wave carries nothing else
+    __device__ static constexpr bool f(int p, int k) {
+      return (p == ME - 1) ? k == TR : k != TR;
+    }
+  };
+  // wave slot of Euler wave e (the last Euler wave moves one slot up)
+  __device__ static constexpr int slot(int e) { return e == ME - 1 ? ME : e; }
+
+  template <int DIR>
+  __device__ static __forceinline__ void solve(const MConsts<R>& C, const R (&ql)[M],
+                                               const R (&qr)[M], const R*, const R*,
+                                               R (&W)[MW][M], R (&s)[MW], R (&am)[M],
+                                               R (&ap)[M], R (&x)[NCTX]) {
+    R el[ME], er[ME], We[ME][ME], se[ME], ame[ME], ape[ME];
+#pragma unroll
+    for (int k = 0; k < ME; ++k) {
+      el[k] = ql[k];
+      er[k] = qr[k];
+    }
+    EU::template solve<DIR>(C, el, er, nullptr, nullptr, We, se, ame, ape, x);
+#pragma unroll
+    for (int e = 0; e < ME; ++e) {
+#pragma unroll
+      for (int k = 0; k < ME; ++k) W[slot(e)][k] = We[e][k];
+      W[slot(e)][TR] = R(0);
+      s[slot(e)] = se[e];
+    }
+    const R dphi = qr[TR] - ql[TR];
+    const R un = x[0];
+#pragma unroll
+    for (int k = 0; k < ME; ++k) W[ME - 1][k] = R(0);
+    W[ME - 1][TR] = dphi;
+    s[ME - 1] = un;
+#pragma unroll
+    for (int k = 0; k < ME; ++k) {
+      am[k] = ame[k];
+      ap[k] = ape[k];
+    }
+    am[TR] = fmin(un, R(0)) * dphi;
+    ap[TR] = fmax(un, R(0)) * dphi;
+  }
+  template <int DIR>
+  __device__ static __forceinline__ void flux(const MConsts<R>& C, const R (&q)[M], const R*,
+                                              R (&f)[M]) {
+    // the conservative part only (the tracer has no flux); SharpClaw uses
+    // the Riemann solve for the in-cell fluctuation of this system
+    R e[ME], fe[ME];
+#pragma unroll
+    for (int k = 0; k < ME; ++k) e[k] = q[k];
+    EU::template flux<DIR>(C, e, nullptr, fe);
+#pragma unroll
+    for (int k = 0; k < ME; ++k) f[k] = fe[k];
+    f[TR] = R(0);
+  }
+  template <int DIR>
+  __device__ static __forceinline__ void trans(const MConsts<R>& C, const R (&x)[NCTX],
+                                               const R (&a)[M], R (&bm)[M], R (&bp)[M]) {
+    R ae[ME], bme[ME], bpe[ME];
+#pragma unroll
+    for (int k = 0; k < ME; ++k) ae[k] = a[k];
+    EU::template trans<DIR>(C, x, ae, bme, bpe);
+#pragma unroll
+    for (int k = 0; k < ME; ++k) {
+      bm[k] = bme[k];
+      bp[k] = bpe[k];
+    }
+    const R ut = x[1];  // transverse Roe velocity carries the tracer
+    bm[TR] = fmin(ut, R(0)) * a[TR];
+    bp[TR] = fmax(ut, R(0)) * a[TR];
+  }
+  template <int DIR>
+  __device__ static __forceinline__ void char_ctx(const MConsts<R>& C, const R (&ql)[M],
+                                                  const R (&qr)[M], R (&x)[NCTX]) {
+    R el[ME], er[ME];
+#pragma unroll
+    for (int k = 0; k < ME; ++k) {
+      el[k] = ql[k];
+      er[k] = qr[k];
+    }
+    EU::template char_ctx<DIR>(C, el, er, x);
+  }
+  template <int DIR>
+  __device__ static __forceinline__ void to_char(const MConsts<R>& C, const R (&x)[NCTX],
+                                                 const R (&q)[M], R (&w)[M]) {
+    R e[ME], we[ME];
+#pragma unroll
+    for (int k = 0; k < ME; ++k) e[k] = q[k];
+    EU::template to_char<DIR>(C, x, e, we);
+#pragma unroll
+    for (int k = 0; k < ME; ++k) w[k] = we[k];
+    w[TR] = q[TR];
+  }
+  template <int DIR>
+  __device__ static __forceinline__ void from_char(const MConsts<R>& C, const R (&x)[NCTX],
+                                                   const R (&w)[M], R (&q)[M]) {
+    R we[ME], e[ME];
+#pragma unroll
+    for (int k = 0; k < ME; ++k) we[k] = w[k];
+    EU::template from_char<DIR>(C, x, we, e);
+#pragma unroll
+    for (int k = 0; k < ME; ++k) q[k] = e[k];
+    q[TR] = w[TR];
+  }
+};
+
+// policy traits with defaults: Euler-family systems (axisymmetric source),
+// and systems whose SharpClaw in-cell fluctuation needs a Riemann solve
+template <class RP, class = void>
+struct is_euler_rp {
+  static constexpr bool value = false;
+};
+template <class RP>
+struct is_euler_rp<RP, decltype((void)RP::E, void())> {
+  static constexpr bool value = true;
+};
+template <class RP, class = void>
+struct incell_solve {
+  static constexpr bool value = false;
+};
+template <class RP>
+struct incell_solve<RP, decltype((void)RP::INCELL_SOLVE, void())> {
+  static constexpr bool value = RP::INCELL_SOLVE;
+};
+
+// ---------------------------------------------------------------------------
 // wave limiters (LeVeque FVM book, high-resolution methods)
 // ---------------------------------------------------------------------------
 template <typename R>

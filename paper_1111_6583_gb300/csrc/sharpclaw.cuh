@@ -258,18 +258,31 @@ __global__ void __launch_bounds__(TX * TY)
             al[k] = At[k][MA > 0 ? ((ND == 2) ? G + cj : 0) : 0][MA > 0 ? G + ci : 0];
         }
         // total fluctuation A dQ_i = A^- + A^+ of the solve (q^L_i, q^R_i), which
-        // for every solver here equals the flux jump f(q^R_i) - f(q^L_i)
-        R fl[M], fr[M];
-        if (dir == 0) {
-          RP::template flux<0>(C, ql, al, fl);
-          RP::template flux<0>(C, qr, al, fr);
+        // for every conservative solver here equals the flux jump
+        // f(q^R_i) - f(q^L_i); systems with a non-conservative component
+        // (the advected tracer) take the solve itself
+        R adq[M];
+        if constexpr (incell_solve<RP>::value) {
+          R W[MW][M], s_[MW], am[M], ap[M], x[NC];
+          if (dir == 0) RP::template solve<0>(C, ql, qr, al, al, W, s_, am, ap, x);
+          else RP::template solve<1>(C, ql, qr, al, al, W, s_, am, ap, x);
+#pragma unroll
+          for (int k = 0; k < M; ++k) adq[k] = am[k] + ap[k];
         } else {
-          RP::template flux<1>(C, ql, al, fl);
-          RP::template flux<1>(C, qr, al, fr);
+          R fl[M], fr[M];
+          if (dir == 0) {
+            RP::template flux<0>(C, ql, al, fl);
+            RP::template flux<0>(C, qr, al, fr);
+          } else {
+            RP::template flux<1>(C, ql, al, fl);
+            RP::template flux<1>(C, qr, al, fr);
+          }
+#pragma unroll
+          for (int k = 0; k < M; ++k) adq[k] = fr[k] - fl[k];
         }
         // thread cidx == tid owns cell (ci, cj) (NT == TX*TY)
 #pragma unroll
-        for (int k = 0; k < M; ++k) L[k] -= (FP[k][e0] + FM[k][e1] + (fr[k] - fl[k])) * idn;
+        for (int k = 0; k < M; ++k) L[k] -= (FP[k][e0] + FM[k][e1] + adq[k]) * idn;
       }
       __syncthreads();
     }

@@ -1,0 +1,129 @@
+"""GPU parity of the axisymmetric shock-bubble pieces (Sec. 6.2) against the
+oracle: the Euler Roe solver with a passive tracer (classic and SharpClaw),
+dimensionally split classic steps, and the geometric source applied after
+accepted steps only (Godunov splitting), alone and in batches.
+"""
+import numpy as np
+import pytest
+
+from paper_1111_6583_gb300 import workloads as wl
+from tests.gpu_util import (FP32_SHOCK_L1_TOL, FP64_TOL, gpu_evolve, gpu_fixed_steps,
+                            oracle_evolve, oracle_fixed_steps, rel_l1, rel_maxnorm)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+@pytest.mark.parametrize("transverse", [0, 1, 2])
+def test_tracer_classic2d_fixed_dt(orc, transverse):
+    spec = wl.random_smooth_2d("euler_tracer", 131, 70, transverse=transverse)
+    dt = 0.25 / 131
+    qo, co = oracle_fixed_steps(orc, spec, dt, 4)
+    qg, cg = gpu_fixed_steps(spec, "fp64", dt, 4)
+    assert rel_maxnorm(qg, qo) <= FP64_TOL
+    assert np.allclose(cg, co, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("scheme,char", [("classic", 0), ("sharpclaw", 0), ("sharpclaw", 1)])
+def test_tracer_1d(orc, scheme, char):
+    spec = wl.random_1d("euler_tracer", 300, scheme=scheme, char_decomp=char)
+    dt = 0.15 / 300
+    qo, _ = oracle_fixed_steps(orc, spec, dt, 3)
+    qg, _ = gpu_fixed_steps(spec, "fp64", dt, 3)
+    assert rel_maxnorm(qg, qo) <= FP64_TOL
+
+
+@pytest.mark.parametrize("char", [0, 1])
+def test_tracer_sharpclaw2d(orc, char):
+    spec = wl.random_smooth_2d("euler_tracer", 70, 37, scheme="sharpclaw", char_decomp=char)
+    dt = 0.1 / 70
+    qo, _ = oracle_fixed_steps(orc, spec, dt, 3)
+    qg, _ = gpu_fixed_steps(spec, "fp64", dt, 3)
+    assert rel_maxnorm(qg, qo) <= FP64_TOL
+
+
+@pytest.mark.parametrize("rp", ["advection", "acoustics", "sw_roe", "euler_roe", "euler_tracer"])
+@pytest.mark.parametrize("order", [1, 2])
+def test_dimensional_splitting_fixed_dt(orc, rp, order):
+    spec = wl.random_smooth_2d(rp, 131, 70, order=order, dim_split=1, transverse=0)
+    dt = 0.25 / 131
+    qo, co = oracle_fixed_steps(orc, spec, dt, 4)
+    qg, cg = gpu_fixed_steps(spec, "fp64", dt, 4)
+    assert rel_maxnorm(qg, qo) <= FP64_TOL
+    assert np.allclose(cg, co, rtol=1e-13, atol=0)
+
+
+def test_dimensional_splitting_controller(orc):
+    """Split steps through the controller (three state buffers, the result
+    two slots on): the dam break to t = 0.4."""
+    spec = wl.sw_dambreak_2d(n=128, t_end=0.4)
+    spec.update(dim_split=1, transverse=0)
+    qo, io = oracle_evolve(orc, spec, 0.4)
+    for graph in (True, False):
+        qg, ig = gpu_evolve(spec, "fp64", 0.4, use_graph=graph)
+        assert ig["steps"] == io["steps"] and ig["t"] == io["t"] == 0.4
+        assert rel_maxnorm(qg, qo) <= FP64_TOL
+
+
+@pytest.mark.parametrize("dim_split", [0, 1])
+def test_axisymmetric_shock_bubble(orc, dim_split):
+    spec = wl.shock_bubble_axisym(nx=160, ny=40, t_end=0.1, sub=4, dim_split=dim_split)
+    if dim_split:
+        spec["transverse"] = 0
+    qo, io = oracle_evolve(orc, spec, 0.1)
+    assert io["status"] == "ok"
+    for graph in (True, False):
+        qg, ig = gpu_evolve(spec, "fp64", 0.1, use_graph=graph)
+        assert ig["status"] == 0 and ig["steps"] == io["steps"] and ig["t"] == 0.1
+        assert rel_maxnorm(qg, qo) <= FP64_TOL
+    q32, i32 = gpu_evolve(spec, "fp32", 0.1)
+    assert i32["status"] == 0 and rel_l1(q32, qo) <= FP32_SHOCK_L1_TOL
+
+
+def test_source_follows_accepted_steps_only(orc):
+    """A first dt far above the stable one is rejected and retried; the
+    source step runs once per accepted step (steps, rejects and state as the
+    oracle's)."""
+    spec = wl.shock_bubble_axisym(nx=80, ny=20, t_end=0.05, sub=4)
+    spec["dt_initial"] = 0.02
+    qo, io = oracle_evolve(orc, spec, 0.05)
+    qg, ig = gpu_evolve(spec, "fp64", 0.05)
+    assert io["rejects"] >= 1 and ig["rejects"] == io["rejects"]
+    assert ig["steps"] == io["steps"]
+    assert rel_maxnorm(qg, qo) <= FP64_TOL
+
+
+def test_axisymmetric_batch_equals_alone(orc):
+    import torch
+    from paper_1111_6583_gb300 import claw
+    specs = [wl.shock_bubble_axisym(nx=nx, ny=ny, t_end=t, sub=4)
+             for nx, ny, t in ((80, 20, 0.05), (120, 30, 0.04), (64, 16, 0.06))]
+    b = claw.Batch(specs, "fp64")
+    infos = b.evolve()
+    torch.cuda.synchronize()
+    for k, sp in enumerate(specs):
+        s = claw.Solver(sp, "fp64")
+        ia = s.evolve(sp["t_end"])
+        qa = s.q.double().cpu().numpy()
+        s.close()
+        assert infos[k]["steps"] == ia["steps"] and infos[k]["t"] == sp["t_end"]
+        assert np.array_equal(qa, b.q[k].double().cpu().numpy())
+        if k == 0:
+            qo, io = oracle_evolve(orc, sp, sp["t_end"])
+            assert io["steps"] == ia["steps"] and rel_maxnorm(qa, qo) <= FP64_TOL
+    b.close()
+
+
+def test_server_rejects_source_terms():
+    from paper_1111_6583_gb300 import claw
+    sp = wl.shock_bubble_axisym(nx=64, ny=16, t_end=0.01, sub=2)
+    with pytest.raises(claw.ClawError):
+        claw.Server(sp, "fp64", budget_bytes=1 << 26, max_slots=2)
