@@ -1068,10 +1068,10 @@ __device__ __forceinline__ R limiter_mc(R th) {
 //   F = 1/2 sum_p c_p phi(theta_p) W^p,  c_p = |s|(1 - dt/dx |s|)   (waves)
 //                                          = sgn(s)(1 - dt/dx |s|) (f-waves)
 // dot_up[p] = W^p_upwind . W^p, nrm[p] = W^p . W^p (zero wave -> no correction).
-// theta_p = dot_up[p] / nrm[p]; with three or more waves, when the product
-// of the norms is a normal number, the reciprocals come from one division
-// (1/n_p = prod_{q != p} n_q / prod_q n_q).  DIR selects the solver's
-// structural zeros.
+// theta_p = dot_up[p] / nrm[p]; with three or more waves, when every partial
+// product of the norms is a normal number, the reciprocals come from one
+// division (1/n_p = prod_{q != p} n_q / prod_q n_q).  DIR selects the
+// solver's structural zeros.
 template <class RP, typename R, int DIR = 0>
 __device__ __forceinline__ void correction(const MConsts<R>& C, const R (&W)[RP::MW][RP::M],
                                            const R (&s)[RP::MW], const R (&dot_up)[RP::MW],
@@ -1083,15 +1083,19 @@ __device__ __forceinline__ void correction(const MConsts<R>& C, const R (&W)[RP:
   R inv[MW];
   bool batched = false;
   if (MW >= 3 && C.lim != CLAW_LIM_NONE) {
+    // every partial product must be a normal number: a subnormal one (a tiny
+    // wave next to large ones) would lose precision in the reciprocals
     R pre[MW];
     R prod = nrm[0];
+    bool normal = pos_normal(prod);
     pre[0] = R(1);
 #pragma unroll
     for (int p = 1; p < MW; ++p) {
       pre[p] = prod;
       prod = prod * nrm[p];
+      normal = normal && pos_normal(prod);
     }
-    if (pos_normal(prod)) {
+    if (normal) {
       const R r = FM<R>::rcp(prod);
       R suf = r;
 #pragma unroll
