@@ -30,7 +30,7 @@ _SRC = os.path.join(_HERE, "oracle.c")
 _HDR = os.path.join(_HERE, "oracle.h")
 
 RP = {"advection": 0, "acoustics": 1, "sw_roe": 2, "euler_roe": 3, "euler_hlle": 4,
-      "elasticity_fwave": 5, "euler_tracer": 6}
+      "elasticity_fwave": 5, "euler_tracer": 6, "acoustics_vc": 7}
 LIM = {"none": 0, "minmod": 1, "superbee": 2, "vanleer": 3, "mc": 4}
 BC = {"periodic": 0, "wall": 1, "extrap": 2, "inflow": 3}
 SCHEME = {"classic": 0, "sharpclaw": 1}
@@ -72,6 +72,7 @@ class _Prob(ctypes.Structure):
         ("source", ctypes.c_int),
         ("dim_split", ctypes.c_int),
         ("lower", ctypes.c_double * 2),
+        ("capa_index", ctypes.c_int),
     ]
 
 
@@ -111,6 +112,8 @@ def _load():
         lib.orc_ssp104_linear.restype = ctypes.c_double
         lib.orc_ssp104_linear.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
         lib.orc_max_speeds.argtypes = [P, _dp, _dp, _dp]
+        lib.orc_transverse_vc.restype = None
+        lib.orc_transverse_vc.argtypes = [P, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
         lib.orc_source_step.restype = None
         lib.orc_source_step.argtypes = [P, _dp, ctypes.c_double]
         lib.orc_evolve.argtypes = [P, _dp, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
@@ -163,7 +166,8 @@ def make_problem(spec: dict):
     p.char_decomp = int(spec.get("char_decomp", 0))
     p.entropy_fix = int(spec.get("entropy_fix", 1))
     p.num_eqn = lib.orc_num_eqn(p.rp, ndim)
-    p.num_aux = int(spec.get("num_aux", 2 if spec["rp"] == "elasticity_fwave" else 0))
+    p.num_aux = int(spec.get("num_aux", 2 if spec["rp"] in ("elasticity_fwave", "acoustics_vc")
+                                 else 0))
     p.num_waves = lib.orc_num_waves(p.rp, ndim)
     bl = list(spec.get("bc_lower", ["periodic"] * ndim)) + ["periodic"] * 2
     bh = list(spec.get("bc_upper", ["periodic"] * ndim)) + ["periodic"] * 2
@@ -195,6 +199,7 @@ def make_problem(spec: dict):
     p.dim_split = int(spec.get("dim_split", 0))
     p.lower[0] = float(lo[0])
     p.lower[1] = float(lo[1])
+    p.capa_index = int(spec.get("capa_index", -1))
     return p
 
 
@@ -232,6 +237,15 @@ def transverse(p, direction, ql, qr, asdq, auxl=None, auxr=None):
     bm = np.zeros(m); bp = np.zeros(m)
     _load().orc_transverse(ctypes.byref(p), direction, _ptr(ql), _ptr(qr), _ptr(al), _ptr(ar),
                            _ptr(asdq), _ptr(bm), _ptr(bp))
+    return bm, bp
+
+
+def transverse_vc(p, direction, a_m, a_c, a_p, asdq):
+    """Varying-medium acoustics transverse split: (bm, bp)."""
+    m = p.num_eqn
+    bm, bp = np.zeros(m), np.zeros(m)
+    _load().orc_transverse_vc(ctypes.byref(p), direction, _ptr(_arr(a_m)), _ptr(_arr(a_c)),
+                              _ptr(_arr(a_p)), _ptr(_arr(asdq)), _ptr(bm), _ptr(bp))
     return bm, bp
 
 

@@ -34,6 +34,7 @@ int orc_num_eqn(int rp, int ndim) {
     case ORC_RP_EULER_HLLE: return ndim <= 2 ? ndim + 2 : 0;
     case ORC_RP_ELASTICITY_FWAVE: return ndim == 1 ? 2 : (ndim == 2 ? 3 : 0);
     case ORC_RP_EULER_TRACER: return ndim <= 2 ? ndim + 3 : 0;
+    case ORC_RP_ACOUSTICS_VC: return ndim <= 2 ? ndim + 1 : 0;
   }
   return 0;
 }
@@ -47,6 +48,7 @@ int orc_num_waves(int rp, int ndim) {
     case ORC_RP_EULER_HLLE: return 2;
     case ORC_RP_ELASTICITY_FWAVE: return 2;
     case ORC_RP_EULER_TRACER: return ndim == 1 ? 4 : 5;
+    case ORC_RP_ACOUSTICS_VC: return 2;
   }
   return 0;
 }
@@ -360,6 +362,18 @@ void orc_riemann(const orc_prob* P, int dir, const double* ql, const double* qr,
         for (int k = 0; k < m; ++k) wave[p * m + k] = alpha[p] * r[p * m + k];
       break;
     }
+    case ORC_RP_ACOUSTICS_VC: {
+      /* linear acoustics in a varying medium, aux (rho, c) per cell: the
+       * left-going wave carries the left impedance, the right-going the
+       * right one (LeVeque FVM book, heterogeneous media) */
+      double Zl = auxl[0] * auxl[1], Zr = auxr[0] * auxr[1];
+      double a1 = (-d[0] + Zr * d[n]) / (Zl + Zr);
+      double a2 = (d[0] + Zl * d[n]) / (Zl + Zr);
+      for (int k = 0; k < 2 * m; ++k) wave[k] = 0.0;
+      wave[0] = -a1 * Zl; wave[n] = a1; s[0] = -auxl[1];
+      wave[m] = a2 * Zr; wave[m + n] = a2; s[1] = auxr[1];
+      break;
+    }
     case ORC_RP_EULER_HLLE: {
       double un, ut, H, c, c2;
       double fl[MAXM], fr[MAXM], qs[MAXM];
@@ -414,6 +428,23 @@ void orc_riemann(const orc_prob* P, int dir, const double* ql, const double* qr,
 /* ------------------------------------------------------------------------ */
 /* transverse solvers (2D)                                                   */
 /* ------------------------------------------------------------------------ */
+
+/* Transverse split of asdq in a varying acoustic medium: the down-going part
+ * is the left-going wave of the transverse Riemann problem between the cell
+ * below (aux a_m) and the cell holding the fluctuation (a_c); the up-going
+ * part the right-going wave between a_c and the cell above (a_p). */
+void orc_transverse_vc(const orc_prob* P, int dir, const double* a_m, const double* a_c,
+                       const double* a_p, const double* asdq, double* bm, double* bp) {
+  int m = P->num_eqn, t = comp_t(P, dir);
+  double Zm = a_m[0] * a_m[1], Zc = a_c[0] * a_c[1], Zp = a_p[0] * a_p[1];
+  for (int k = 0; k < m; ++k) { bm[k] = 0.0; bp[k] = 0.0; }
+  double b1 = (-asdq[0] + Zc * asdq[t]) / (Zm + Zc);
+  double b2 = (asdq[0] + Zc * asdq[t]) / (Zc + Zp);
+  bm[0] = a_m[1] * b1 * Zm;
+  bm[t] = -a_m[1] * b1;
+  bp[0] = a_p[1] * b2 * Zp;
+  bp[t] = a_p[1] * b2;
+}
 
 void orc_transverse(const orc_prob* P, int dir, const double* ql, const double* qr,
                     const double* auxl, const double* auxr, const double* asdq,
@@ -661,6 +692,7 @@ static int classic1d(const orc_prob* P, double* q, const double* aux, double dt,
   double* AP = (double*)malloc(sizeof(double) * nint * m);
   double* F = (double*)calloc((size_t)(N + 1) * m, sizeof(double));
   double smax = 0.0;
+  const int capa = P->capa_index;
   for (int i = -1; i <= N + 1; ++i) {
     double ql[MAXM], qr[MAXM], al[MAXM] = {0}, ar[MAXM] = {0};
     gcell(&Q, i - 1, 0, ql);
@@ -670,22 +702,39 @@ static int classic1d(const orc_prob* P, double* q, const double* aux, double dt,
     orc_riemann(P, 0, ql, qr, al, ar, W + ii * nw * m, S + ii * nw, AM + ii * m, AP + ii * m);
     if (i >= 0 && i <= N)
       for (int p = 0; p < nw; ++p) {
-        double a = fabs(S[ii * nw + p]);
+        double sp = S[ii * nw + p];
+        /* with a capacity the Courant number of a wave uses the capacity of
+         * the cell it moves into */
+        double a = capa < 0 ? fabs(sp)
+                            : (sp > 0.0 ? sp / ar[capa] : (sp < 0.0 ? -sp / al[capa] : 0.0));
         if (!(a <= smax)) smax = a; /* NaN propagates */
       }
   }
   if (P->order == 2)
     for (int i = 0; i <= N; ++i) {
       int ii = i + 1;
+      double dtc = dtdx;
+      if (capa >= 0) {
+        double al[MAXM], ar[MAXM];
+        gcell(&A, i - 1, 0, al); gcell(&A, i, 0, ar);
+        dtc = 0.5 * (dtdx / al[capa] + dtdx / ar[capa]);
+      }
       correction_flux(P, m, nw, W + (ii - 1) * nw * m, W + ii * nw * m, W + (ii + 1) * nw * m,
-                      S + ii * nw, dtdx, F + i * m);
+                      S + ii * nw, dtc, F + i * m);
     }
-  for (int i = 0; i < N; ++i)
+  for (int i = 0; i < N; ++i) {
+    double dti = dtdx;
+    if (capa >= 0) {
+      double ac[MAXM];
+      gcell(&A, i, 0, ac);
+      dti = dtdx / ac[capa];
+    }
     for (int k = 0; k < m; ++k) {
       double* qk = q + (size_t)k * N + i;
-      *qk = *qk - dtdx * (AP[(i + 1) * m + k] + AM[(i + 2) * m + k]) -
-            dtdx * (F[(i + 1) * m + k] - F[i * m + k]);
+      *qk = *qk - dti * (AP[(i + 1) * m + k] + AM[(i + 2) * m + k]) -
+            dti * (F[(i + 1) * m + k] - F[i * m + k]);
     }
+  }
   *cfl = dt * smax / P->dx;
   free(qb); free(ab); free(W); free(S); free(AM); free(AP); free(F);
   return ORC_OK;
@@ -729,7 +778,11 @@ static void sweep(const orc_prob* P, int dir, const garr* Q, const garr* A, doub
       orc_riemann(P, dir, ql, qr, al, ar, W + ii * nw * m, S + ii * nw, AM + ii * m, AP + ii * m);
       if (i >= 0 && i <= n && l >= 0 && l < nl)
         for (int p = 0; p < nw; ++p) {
-          double a = fabs(S[ii * nw + p]);
+          double sp = S[ii * nw + p];
+          double a = P->capa_index < 0
+                         ? fabs(sp)
+                         : (sp > 0.0 ? sp / ar[P->capa_index]
+                                     : (sp < 0.0 ? -sp / al[P->capa_index] : 0.0));
           if (!(a <= smax)) smax = a;
         }
     }
@@ -742,9 +795,18 @@ static void sweep(const orc_prob* P, int dir, const garr* Q, const garr* A, doub
         R->apdq[k] = AP[ii * m + k];
         R->F[k] = 0.0;
       }
+      double kl = 1.0, kr = 1.0;  /* capacities of the two cells */
+      if (P->capa_index >= 0) {
+        double al[MAXM], ar[MAXM];
+        if (dir == 0) { gcell(A, i - 1, l, al); gcell(A, i, l, ar); }
+        else { gcell(A, l, i - 1, al); gcell(A, l, i, ar); }
+        kl = al[P->capa_index];
+        kr = ar[P->capa_index];
+      }
       if (P->order == 2)
         correction_flux(P, m, nw, W + (ii - 1) * nw * m, W + ii * nw * m,
-                        W + (ii + 1) * nw * m, S + ii * nw, dtdn, R->F);
+                        W + (ii + 1) * nw * m, S + ii * nw,
+                        P->capa_index < 0 ? dtdn : 0.5 * (dtdn / kl + dtdn / kr), R->F);
       if (P->transverse) {
         double ql[MAXM], qr[MAXM], al[MAXM] = {0}, ar[MAXM] = {0};
         double ap[MAXM], am[MAXM];
@@ -763,8 +825,29 @@ static void sweep(const orc_prob* P, int dir, const garr* Q, const garr* A, doub
             am[k] = R->amdq[k];
           }
         }
-        orc_transverse(P, dir, ql, qr, al, ar, ap, R->bm_ap, R->bp_ap);
-        orc_transverse(P, dir, ql, qr, al, ar, am, R->bm_am, R->bp_am);
+        if (P->rp == ORC_RP_ACOUSTICS_VC) {
+          /* the transverse neighbours of the cell each fluctuation enters */
+          double m_r[MAXM], p_r[MAXM], m_l[MAXM], p_l[MAXM];
+          if (dir == 0) {
+            gcell(A, i, l - 1, m_r); gcell(A, i, l + 1, p_r);
+            gcell(A, i - 1, l - 1, m_l); gcell(A, i - 1, l + 1, p_l);
+          } else {
+            gcell(A, l - 1, i, m_r); gcell(A, l + 1, i, p_r);
+            gcell(A, l - 1, i - 1, m_l); gcell(A, l + 1, i - 1, p_l);
+          }
+          orc_transverse_vc(P, dir, m_r, ar, p_r, ap, R->bm_ap, R->bp_ap);
+          orc_transverse_vc(P, dir, m_l, al, p_l, am, R->bm_am, R->bp_am);
+        } else {
+          orc_transverse(P, dir, ql, qr, al, ar, ap, R->bm_ap, R->bp_ap);
+          orc_transverse(P, dir, ql, qr, al, ar, am, R->bm_am, R->bp_am);
+        }
+        if (P->capa_index >= 0)
+          /* transverse parts scaled by the capacity of the cell their
+           * fluctuation enters (right cell for A^+, left for A^-) */
+          for (int k = 0; k < m; ++k) {
+            R->bm_ap[k] /= kr; R->bp_ap[k] /= kr;
+            R->bm_am[k] /= kl; R->bp_am[k] /= kl;
+          }
       } else {
         for (int k = 0; k < m; ++k) {
           R->bm_ap[k] = 0.0; R->bp_ap[k] = 0.0; R->bm_am[k] = 0.0; R->bp_am[k] = 0.0;
@@ -820,17 +903,26 @@ static int classic2d(const orc_prob* P, double* q, const double* aux, double dt,
       }
   #pragma omp parallel for schedule(static)
   for (int j = 0; j < ny; ++j)
-    for (int i = 0; i < nx; ++i)
+    for (int i = 0; i < nx; ++i) {
+      /* capacity-form differencing: the cell's updates divided by its kappa */
+      double cx = dtdx, cy = dtdy;
+      if (P->capa_index >= 0) {
+        double ac[MAXM];
+        gcell(&A, i, j, ac);
+        cx = dtdx / ac[P->capa_index];
+        cy = dtdy / ac[P->capa_index];
+      }
       for (int k = 0; k < m; ++k) {
         double* qk = q + (size_t)k * nx * ny + (size_t)j * nx + i;
         double fl = Ft[((size_t)j * (nx + 1) + i) * m + k];
         double fr = Ft[((size_t)j * (nx + 1) + i + 1) * m + k];
         double gb = Gt[((size_t)i * (ny + 1) + j) * m + k];
         double gtp = Gt[((size_t)i * (ny + 1) + j + 1) * m + k];
-        *qk = *qk - dtdx * (XR(i, j)->apdq[k] + XR(i + 1, j)->amdq[k]) -
-              dtdy * (YR(i, j)->apdq[k] + YR(i, j + 1)->amdq[k]) - dtdx * (fr - fl) -
-              dtdy * (gtp - gb);
+        *qk = *qk - cx * (XR(i, j)->apdq[k] + XR(i + 1, j)->amdq[k]) -
+              cy * (YR(i, j)->apdq[k] + YR(i, j + 1)->amdq[k]) - cx * (fr - fl) -
+              cy * (gtp - gb);
       }
+    }
 #undef XR
 #undef YR
   double sx = 0.0, sy = 0.0;
@@ -1288,7 +1380,11 @@ int orc_sharp_L(const orc_prob* P, const double* q, const double* aux, double* L
         }
         orc_riemann(P, dir, qR + i * m, qL + i * m, al, ar, W, S, AM + i * m, AP + i * m);
         for (int p = 0; p < orc_num_waves(P->rp, P->ndim); ++p) {
-          double a = fabs(S[p]);
+          double sp = S[p];
+          double a = P->capa_index < 0
+                         ? fabs(sp)
+                         : (sp > 0.0 ? sp / ar[P->capa_index]
+                                     : (sp < 0.0 ? -sp / al[P->capa_index] : 0.0));
           if (!(a <= sm)) sm = a;
         }
       }
@@ -1299,10 +1395,12 @@ int orc_sharp_L(const orc_prob* P, const double* q, const double* aux, double* L
         if (ma) { if (dir == 0) gcell(&A, i, l, al); else gcell(&A, l, i, al); }
         orc_riemann(P, dir, qL + i * m, qR + (i + 1) * m, al, al, W, S, am, ap);
         size_t cell = dir == 0 ? (size_t)l * nx + i : (size_t)i * nx + l;
+        /* with a capacity: -(1/(kappa_i dx)) (...) */
+        double dnk = P->capa_index < 0 ? dn : dn * al[P->capa_index];
         for (int k = 0; k < m; ++k) {
           double adq = am[k] + ap[k];
           L[(size_t)k * ncell + cell] =
-              L[(size_t)k * ncell + cell] - (AP[i * m + k] + AM[(i + 1) * m + k] + adq) / dn;
+              L[(size_t)k * ncell + cell] - (AP[i * m + k] + AM[(i + 1) * m + k] + adq) / dnk;
         }
       }
       lmax[l] = sm;
@@ -1481,7 +1579,11 @@ void orc_max_speeds(const orc_prob* P, const double* q, const double* aux, doubl
         }
         orc_riemann(P, dir, ql, qr, al, ar, W, S, am, ap);
         for (int p = 0; p < nw; ++p) {
-          double a = fabs(S[p]);
+          double sp = S[p];
+          double a = P->capa_index < 0
+                         ? fabs(sp)
+                         : (sp > 0.0 ? sp / ar[P->capa_index]
+                                     : (sp < 0.0 ? -sp / al[P->capa_index] : 0.0));
           if (!(a <= smax[dir])) smax[dir] = a;
         }
       }

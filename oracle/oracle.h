@@ -25,7 +25,7 @@ extern "C" {
 /* Riemann solver ids */
 enum { ORC_RP_ADVECTION = 0, ORC_RP_ACOUSTICS = 1, ORC_RP_SW_ROE = 2,
        ORC_RP_EULER_ROE = 3, ORC_RP_EULER_HLLE = 4, ORC_RP_ELASTICITY_FWAVE = 5,
-       ORC_RP_EULER_TRACER = 6 };
+       ORC_RP_EULER_TRACER = 6, ORC_RP_ACOUSTICS_VC = 7 };
 /* wave limiters */
 enum { ORC_LIM_NONE = 0, ORC_LIM_MINMOD = 1, ORC_LIM_SUPERBEE = 2,
        ORC_LIM_VANLEER = 3, ORC_LIM_MC = 4 };
@@ -67,6 +67,7 @@ typedef struct {
   int dim_split;        /* classic 2D: 0 unsplit; 1 dimensional splitting (x sweeps,
                            then y sweeps, Godunov) */
   double lower[2];      /* lower corner of the grid (cell centres for the source) */
+  int capa_index;       /* aux field holding the capacity kappa (Eq. (conslaw)); -1 none */
 } orc_prob;
 
 typedef struct {
@@ -93,6 +94,10 @@ void orc_riemann(const orc_prob* P, int dir, const double* ql, const double* qr,
 void orc_transverse(const orc_prob* P, int dir, const double* ql, const double* qr,
                     const double* auxl, const double* auxr, const double* asdq,
                     double* bmasdq, double* bpasdq);
+/* Varying-medium acoustics (aux rho, c): transverse split of asdq held by the
+ * cell with aux a_c between its neighbours a_m (below) and a_p (above). */
+void orc_transverse_vc(const orc_prob* P, int dir, const double* a_m, const double* a_c,
+                       const double* a_p, const double* asdq, double* bm, double* bp);
 /* limiter function phi(theta) */
 double orc_phi(int lim, double theta);
 /* WENO5 left-biased value at x_{i+1/2} from v[0..4] = v_{i-2..i+2} */

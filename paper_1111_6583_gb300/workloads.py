@@ -272,6 +272,34 @@ def psystem_checkerboard_2d(periods=32, cells_per_period=64, amp=5.0, var=5.0, t
     return spec
 
 
+def acoustics_vc_2d(n=1024, t_end=0.6, capacity=True, cfl=(0.9, 1.0)):
+    """2D acoustics in a heterogeneous medium (the Table 1 acoustics system
+    with spatially varying coefficients): [-1, 1]^2, (rho, c) = (1, 1) for
+    x < 0.3 and (4, 0.5) beyond (an impedance jump of 2), a circular pressure
+    pulse p = exp(-80 r^2) at (-0.4, 0), at rest, walls; with capacity, the
+    medium sits on a grid stretched in x (x = xi + 0.1 sin(pi xi)), entering
+    as kappa = dx/dxi = 1 + 0.1 pi cos(pi xi) on the uniform xi grid.  Classic,
+    MC, full transverse corrections, CFL 0.9."""
+    xi = _centers(-1.0, 1.0, n)
+    XI, Y = np.meshgrid(xi, xi, indexing="xy")
+    X = XI + 0.1 * np.sin(np.pi * XI) if capacity else XI
+    rho = np.where(X < 0.3, 1.0, 4.0)
+    c = np.where(X < 0.3, 1.0, 0.5)
+    p = np.exp(-80.0 * ((X + 0.4) ** 2 + Y ** 2))
+    q0 = np.stack([p, np.zeros_like(p), np.zeros_like(p)])
+    auxl = [rho, c]
+    kw = {}
+    if capacity:
+        auxl.append(1.0 + 0.1 * np.pi * np.cos(np.pi * XI))
+        kw["capa_index"] = 2
+    aux = np.stack(auxl)
+    spec = _base(2, [n, n], [-1.0, -1.0], [1.0, 1.0], "acoustics_vc", num_aux=len(auxl),
+                 bc_lower=["wall", "wall"], bc_upper=["wall", "wall"], cfl_desired=cfl[0],
+                 cfl_max=cfl[1], **kw)
+    spec.update(q0=np.ascontiguousarray(q0), aux=np.ascontiguousarray(aux), t_end=t_end)
+    return spec
+
+
 def sw_humps_2d(n, humps, t_end):
     """[0,1]^2, depth 1 plus Gaussian humps (a, w, cx, cy), walls, g = 1."""
     x = _centers(0.0, 1.0, n)
@@ -343,6 +371,14 @@ def random_smooth_2d(rp, nx, ny, seed=SEED, params=None, bc="periodic", **kw):
     elif rp == "advection":
         q0 = np.stack([field(1.0)])
         params = params or [1.0, 0.5]
+    elif rp == "acoustics_vc":
+        # layered medium (rho, c) with a smooth capacity field as a third aux
+        rho = np.where(X < 0.5, 1.0, 2.5) * (1.0 + 0.2 * np.sin(2 * np.pi * Y))
+        c = np.where(X < 0.5, 1.0, 0.6) * (1.0 + 0.1 * np.cos(2 * np.pi * Y))
+        kap = 1.0 + 0.3 * np.sin(2 * np.pi * X) * np.sin(2 * np.pi * Y)
+        q0 = np.stack([field(0.5), field(0.5), field(0.5)])
+        aux = np.stack([rho, c, kap])
+        params = []
     elif rp == "elasticity_fwave":
         # checkerboard medium of period 1/4 (material edges on cell edges when
         # 8 divides nx and ny; otherwise cells take the centre's material)
@@ -357,6 +393,9 @@ def random_smooth_2d(rp, nx, ny, seed=SEED, params=None, bc="periodic", **kw):
         kw.setdefault("scheme", "sharpclaw")
         kw.setdefault("char_decomp", 0)
         kw.setdefault("num_aux", 2)
+    elif rp == "acoustics_vc":
+        kw.setdefault("num_aux", 3)
+        kw.setdefault("char_decomp", 0)
     else:
         aux = None
     spec = _base(2, [nx, ny], [0.0, 0.0], [1.0, 1.0], rp, params=params,
@@ -406,11 +445,21 @@ def random_1d(rp, n, seed=SEED, bc=("periodic", "periodic"), jump=True, **kw):
         q0 = np.stack([np.log1p(sig) / K, field(0.3)])
         aux = np.stack([rho, K])
         params = []
+    elif rp == "acoustics_vc":
+        rho = np.where(x < 0.5, 1.0, 2.5)
+        c = np.where(x < 0.5, 1.0, 0.6)
+        kap = 1.0 + 0.3 * np.sin(2 * np.pi * x)
+        q0 = np.stack([field(0.5), field(0.5)])
+        aux = np.stack([rho, c, kap])
+        params = []
     else:
         raise ValueError(rp)
+    if rp == "acoustics_vc":
+        kw.setdefault("char_decomp", 0)
     spec = _base(1, [n], [0.0], [1.0], rp, params=kw.pop("params", params),
                  bc_lower=[bc[0]], bc_upper=[bc[1]],
-                 num_aux=2 if rp == "elasticity_fwave" else 0, **kw)
+                 num_aux=kw.pop("num_aux", 2 if rp == "elasticity_fwave" else
+                                (3 if rp == "acoustics_vc" else 0)), **kw)
     spec.update(q0=np.ascontiguousarray(q0),
                 aux=np.ascontiguousarray(aux) if aux is not None else None,
                 t_end=kw.get("t_end", 0.1))
