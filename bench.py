@@ -401,6 +401,29 @@ def bench_axisym(prec, steps, warmup, nx=1280, ny=320, dim_split=0):
                            "transverse", prec.upper())}
 
 
+def bench_acoustics_vc(prec, steps, warmup, n=1024):
+    """2D acoustics in a heterogeneous medium on a stretched grid (capacity):
+    classic with full transverse corrections on the per-face path (two face
+    sweeps + the update per step)."""
+    import torch
+    from paper_1111_6583_gb300 import claw
+    from paper_1111_6583_gb300 import workloads as wl
+    spec = wl.acoustics_vc_2d(n=n)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = claw.Solver(spec, prec, stream=stream.cuda_stream)
+        s.set_t_end(spec["t_end"])
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        s.advance(warmup)
+    stream.synchronize()
+    ms = timed_steps(s, stream, steps, flush)
+    s.close()
+    avg = sum(ms) / len(ms)
+    return {"value": n * n * len(ms) / (sum(ms) * 1e-3), "unit": UNIT, "ms_per_step": avg,
+            "workload": "2D acoustics, varying medium + capacity %dx%d, classic full "
+                        "transverse (per-face path), %s" % (n, n, prec.upper())}
+
+
 def bench_psystem(prec, steps, warmup, periods=32, cells_per_period=64):
     """2D p-system in the checkerboard medium (Sec. 6.3), SharpClaw WENO5
     component-wise + SSP(10,4): one step = ten fused stage launches."""
@@ -595,6 +618,7 @@ def main():
         line["psystem_checkerboard"] = {p: bench_psystem(p, 3, 3) for p in ("fp64", "fp32")}
         line["axisym_shock_bubble"] = {p: bench_axisym(p, 20, 3) for p in ("fp64", "fp32")}
         line["axisym_shock_bubble"]["fp64_split"] = bench_axisym("fp64", 20, 3, dim_split=1)
+        line["acoustics_vc_capacity"] = {p: bench_acoustics_vc(p, 10, 3) for p in ("fp64", "fp32")}
         try:
             line["batched_elasticity"] = bench_elasticity(args.members, 100, 16)
         except Exception as ex:  # reported, not hidden

@@ -59,7 +59,7 @@ enum { CLAW_FP64 = 0, CLAW_FP32 = 1 };
 enum { CLAW_CLASSIC = 0, CLAW_SHARPCLAW = 1 };
 enum { CLAW_RP_ADVECTION = 0, CLAW_RP_ACOUSTICS = 1, CLAW_RP_SW_ROE = 2,
        CLAW_RP_EULER_ROE = 3, CLAW_RP_EULER_HLLE = 4, CLAW_RP_ELASTICITY_FWAVE = 5,
-       CLAW_RP_EULER_TRACER = 6 };
+       CLAW_RP_EULER_TRACER = 6, CLAW_RP_ACOUSTICS_VC = 7 };
 /* Source terms (Eq. (conslaw) right-hand side), by Godunov splitting after
  * every accepted step: CLAW_SOURCE_AXISYMMETRIC is the geometric source of
  * the Euler equations in cylindrical symmetry about y = 0 (Sec. 6.2:
@@ -105,11 +105,15 @@ typedef struct {
   double inflow[8];    /* ghost state for CLAW_BC_INFLOW                          */
   double params[8];    /* advection u,v | acoustics rho,K | SW g | Euler gamma    */
   int num_eqn;         /* filled in by claw_method_init / validated by create     */
-  int num_aux;         /* elasticity: 2 (rho, K per cell); others 0               */
+  int num_aux;         /* elasticity: 2 (rho, K); acoustics_vc: 2 (rho, c); others
+                          0; one more when a capacity field follows them           */
   int time_integrator; /* SharpClaw: CLAW_SSP_RK3 (default) | CLAW_SSP104          */
   int source;          /* CLAW_SOURCE_*; axisymmetric: 2D Euler systems, y >= 0    */
   int dim_split;       /* classic 2D: 0 unsplit (default); 1 dimensional splitting
                           (x sweeps then y sweeps over dt, no transverse terms)    */
+  int capa_index;      /* -1 (default): no capacity; else the aux field holding the
+                          capacity kappa of Eq. (conslaw), which must be the field
+                          after the solver's own (num_aux = solver's + 1); 1D/2D   */
 } claw_method;
 
 typedef struct {

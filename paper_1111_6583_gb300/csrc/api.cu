@@ -36,6 +36,7 @@ KernelSet kernels_for(int rp, int nd, int prec) {
     case CLAW_RP_EULER_HLLE: return claw_kernels_euler_hlle(nd, prec);
     case CLAW_RP_ELASTICITY_FWAVE: return claw_kernels_elasticity(nd, prec);
     case CLAW_RP_EULER_TRACER: return claw_kernels_euler_tracer(nd, prec);
+    case CLAW_RP_ACOUSTICS_VC: return claw_kernels_acoustics_vc(nd, prec);
   }
   return KernelSet{};
 }
@@ -59,6 +60,7 @@ void fill_consts(const claw_method& m, MConsts<R>& C) {
   C.gm1 = (R)(m.params[0] - 1.0);
   C.weno_eps = (R)m.weno_eps;
   C.weno_r = (m.weno_order + 1) / 2;
+  C.capa = m.capa_index;
   C.lim = m.lim;
   C.order = m.order;
   C.transverse = m.dim_split ? 0 : m.transverse;
@@ -91,19 +93,35 @@ int num_eqn(int rp, int nd) {
     case CLAW_RP_EULER_HLLE: return nd <= 2 ? nd + 2 : 0;
     case CLAW_RP_ELASTICITY_FWAVE: return nd <= 2 ? nd + 1 : 0;
     case CLAW_RP_EULER_TRACER: return nd <= 2 ? nd + 3 : 0;
+    case CLAW_RP_ACOUSTICS_VC: return nd <= 2 ? nd + 1 : 0;
   }
   return 0;
+}
+
+// aux fields the Riemann solver reads
+int solver_aux(int rp) {
+  return (rp == CLAW_RP_ELASTICITY_FWAVE || rp == CLAW_RP_ACOUSTICS_VC) ? 2 : 0;
 }
 
 // validate a method against a dimension; returns an error message or nullptr
 const char* check_method(const claw_method& m, int nd) {
   if (nd < 1 || nd > 3) return "ndim must be 1, 2 or 3";
   if (nd == 3 && m.scheme != CLAW_CLASSIC) return "3D grids use the classic scheme";
-  if (m.rp < 0 || m.rp > 6) return "unknown Riemann solver";
+  if (m.rp < 0 || m.rp > 7) return "unknown Riemann solver";
   if (num_eqn(m.rp, nd) == 0) return "solver not available in this dimension";
   if (m.num_eqn != num_eqn(m.rp, nd)) return "num_eqn does not match the Riemann solver";
-  const int na = m.rp == CLAW_RP_ELASTICITY_FWAVE ? 2 : 0;
-  if (m.num_aux != na) return "num_aux does not match the Riemann solver";
+  const int na = solver_aux(m.rp);
+  if (m.capa_index != -1 && m.capa_index != na)
+    return "capa_index must be -1 or the aux field after the solver's own";
+  if (m.num_aux != na + (m.capa_index >= 0 ? 1 : 0))
+    return "num_aux does not match the Riemann solver (and capacity field)";
+  if (m.capa_index >= 0 && nd == 3) return "capacity is for 1D and 2D grids";
+  if (m.capa_index >= 0 && m.scheme == CLAW_CLASSIC && m.dim_split)
+    return "capacity with dimensional splitting is not supported";
+  if (m.rp == CLAW_RP_ACOUSTICS_VC && m.scheme == CLAW_CLASSIC && nd == 2 && m.dim_split)
+    return "the varying-medium solver runs unsplit";
+  if (m.scheme == CLAW_SHARPCLAW && m.char_decomp && m.rp == CLAW_RP_ACOUSTICS_VC)
+    return "no characteristic projection for the varying-medium acoustics solver";
   if (m.scheme != CLAW_CLASSIC && m.scheme != CLAW_SHARPCLAW) return "unknown scheme";
   if (m.prec != CLAW_FP64 && m.prec != CLAW_FP32) return "unknown precision";
   if (m.lim < 0 || m.lim > 4) return "unknown limiter";
@@ -235,8 +253,16 @@ void fill_info(const DevCtl& c, claw_step_info* info) {
 cudaError_t launch_attempt(const KernelSet& ks, const claw_method& m, const Member* mem,
                            const Tile* tiles, int ntiles, const void* consts, int bw, int h,
                            cudaStream_t st, const Tile* mtiles = nullptr, int nmtiles = 0,
-                           int nmembers = 1) {
+                           int nmembers = 1, const int* n3 = nullptr, void* work3 = nullptr,
+                           size_t work3_bytes = 0) {
   LaunchArgs a{mem, tiles, ntiles, consts, bw, h, 0, st};
+  if (n3) {
+    a.n3[0] = n3[0];
+    a.n3[1] = n3[1];
+    a.n3[2] = n3[2];
+  }
+  a.work3 = work3;
+  a.work3_bytes = work3_bytes;
   cudaError_t e = cudaSuccess;
   if (m.scheme == CLAW_CLASSIC) {
     if (m.dim_split) {
@@ -276,6 +302,7 @@ struct claw_solver {
   claw_method m;
   claw_grid g;
   int nd = 1, prec = 0, nbuf = 2;
+  int faces = 0;  // classic step on the per-face path (capacity / media-aware transverse)
   KernelSet ks{};
   std::vector<unsigned char> consts;
   cudaStream_t ustream = nullptr, st = nullptr;
@@ -341,8 +368,10 @@ cudaError_t solver_attempt(claw_solver* s, cudaStream_t st) {
                  {(int)s->g.n[0], (int)s->g.n[1], (int)s->g.n[2]}, s->work3, s->work3_bytes};
     return s->ks.classic(a);
   }
+  const int n3[3] = {(int)s->g.n[0], (int)s->g.n[1], (int)s->g.n[2]};
   return launch_attempt(s->ks, s->m, s->d_mem, nullptr, s->ntiles, s->consts.data(), s->bw,
-                        s->h, st, nullptr, maxspeed_tiles(s->h_mem.nx, s->h_mem.ny), 1);
+                        s->h, st, nullptr, maxspeed_tiles(s->h_mem.nx, s->h_mem.ny), 1, n3,
+                        s->work3, s->work3_bytes);
 }
 
 cudaError_t read_ctl(claw_solver* s) {
@@ -384,7 +413,7 @@ cudaError_t build_graph(claw_solver* s, int k) {
 // with a dry control block (attempts leave t, dt and the state untouched) and
 // keep the fastest.
 cudaError_t autotune(claw_solver* s) {
-  if (s->m.scheme != CLAW_CLASSIC || s->nd != 2) {
+  if (s->m.scheme != CLAW_CLASSIC || s->nd != 2 || s->faces) {
     s->tuned = 1;
     return cudaSuccess;
   }
@@ -487,7 +516,7 @@ claw_status claw_method_init(claw_method* m, int rp, int ndim) {
     g_err = "ndim must be 1, 2 or 3";
     return CLAW_EINVAL;
   }
-  if (rp < 0 || rp > 6 || num_eqn(rp, ndim) == 0) {
+  if (rp < 0 || rp > 7 || num_eqn(rp, ndim) == 0) {
     g_err = "unknown Riemann solver for this dimension";
     return CLAW_EINVAL;
   }
@@ -499,7 +528,7 @@ claw_status claw_method_init(claw_method* m, int rp, int ndim) {
   m->order = 2;
   m->transverse = ndim >= 2 ? 2 : 0;
   m->weno_order = 5;
-  m->char_decomp = rp == CLAW_RP_ELASTICITY_FWAVE ? 0 : 1;
+  m->char_decomp = (rp == CLAW_RP_ELASTICITY_FWAVE || rp == CLAW_RP_ACOUSTICS_VC) ? 0 : 1;
   m->entropy_fix = 1;
   m->max_retries = 8;
   m->cfl_desired = 0.9;
@@ -517,7 +546,8 @@ claw_status claw_method_init(claw_method* m, int rp, int ndim) {
     default: break;
   }
   m->num_eqn = num_eqn(rp, ndim);
-  m->num_aux = rp == CLAW_RP_ELASTICITY_FWAVE ? 2 : 0;
+  m->num_aux = solver_aux(rp);
+  m->capa_index = -1;
   return CLAW_OK;
 }
 
@@ -555,7 +585,12 @@ claw_status claw_solver_create(const claw_method* m, const claw_grid* g, void* s
     claw_solver_destroy(s);
     return st;
   }
-  s->ntiles = s->nd == 3 ? (int)((cells_of(s->g) + 255) / 256)
+  s->faces = (m->scheme == CLAW_CLASSIC && s->nd <= 2 &&
+              (m->capa_index >= 0 || (s->nd == 2 && m->rp == CLAW_RP_ACOUSTICS_VC)))
+                 ? 1
+                 : 0;
+  if (s->faces) s->tuned = 1;  // no tile shapes to choose
+  s->ntiles = (s->nd == 3 || s->faces) ? (int)((cells_of(s->g) + 255) / 256)
                          : tiles_of(m->scheme, s->nd, s->prec, (int)s->g.n[0], (int)s->g.n[1],
                                     s->bw, s->h);
   *out = s;
@@ -570,6 +605,11 @@ claw_status claw_bind_state(claw_solver* s, void* q_dev, const void* aux_dev, do
   s->q_user = q_dev;
   s->aux = aux_dev;
   SCK(cudaMalloc(&s->work, s->sbytes * (s->nbuf - 1)));
+  if (s->faces) {
+    s->work3_bytes = faces_work_bytes(s->nd, (int)s->g.n[0], (int)s->g.n[1], s->m.num_eqn,
+                                      s->prec);
+    SCK(cudaMalloc(&s->work3, s->work3_bytes));
+  }
   if (s->nd == 3) {
     s->work3_bytes = classic3d_work_bytes((int)s->g.n[0], (int)s->g.n[1], (int)s->g.n[2],
                                           s->m.num_eqn, s->prec);
@@ -619,7 +659,7 @@ claw_status claw_solver_tune(claw_solver* s, int mode, int* bw, int* h) {
       return fail(s, "bad tile shape");
     s->bw = *bw;
     s->h = *h;
-    if (s->nd != 3)
+    if (s->nd != 3 && !s->faces)
       s->ntiles = tiles_of(s->m.scheme, s->nd, s->prec, (int)s->g.n[0], (int)s->g.n[1], s->bw,
                            s->h);
     s->tuned = 1;
@@ -935,6 +975,9 @@ claw_status claw_batch_create(const claw_method* m, const claw_grid* grids, int 
   *out = nullptr;
   const int nd = grids[0].ndim;
   if (nd == 3) return bfail(nullptr, "batches take 1D or 2D grids");
+  if (m->scheme == CLAW_CLASSIC &&
+      (m->capa_index >= 0 || (nd == 2 && m->rp == CLAW_RP_ACOUSTICS_VC)))
+    return bfail(nullptr, "batches run the row kernels: no capacity or varying-medium 2D classic");
   for (int k = 0; k < n; ++k) {
     if (const char* why = check_grid(grids[k], *m)) return bfail(nullptr, why);
     if (grids[k].ndim != nd) return bfail(nullptr, "all members need the same ndim");
@@ -1216,6 +1259,9 @@ claw_status claw_server_create(const claw_method* m, size_t hbm_budget_bytes, in
   if (const char* why = check_method(*m, nd)) return sfail(nullptr, why);
   if (m->source != CLAW_SOURCE_NONE)
     return sfail(nullptr, "the server takes methods without source terms");
+  if (m->scheme == CLAW_CLASSIC &&
+      (m->capa_index >= 0 || (nd == 2 && m->rp == CLAW_RP_ACOUSTICS_VC)))
+    return sfail(nullptr, "the server runs the row kernels: no capacity or varying-medium 2D classic");
   KernelSet ks = kernels_for(m->rp, nd, m->prec);
   if (!ks.valid) return sfail(nullptr, "no kernels for this solver/dimension/precision");
   claw_server* v = new claw_server();

@@ -81,6 +81,7 @@ struct MConsts {
   R gamma, gm1;    // Euler
   R weno_eps;
   int weno_r;      // SharpClaw: WENO order 2 weno_r - 1 (0 means 3, WENO5)
+  int capa;        // aux field holding the capacity kappa, or -1
   int lim, order, transverse, entropy_fix, char_decomp;
   int bc_lo[3], bc_hi[3];
 };
@@ -156,6 +157,16 @@ __device__ __forceinline__ void load_aux(const MConsts<R>& C, const R* __restric
   const size_t plane = (size_t)nx * ny;
 #pragma unroll
   for (int k = 0; k < MA; ++k) out[k] = __ldg(a + k * plane + (size_t)rr * nx + cc);
+}
+
+// one aux field (runtime index) of cell (c, r) with ghost remap
+template <typename R>
+__device__ __forceinline__ R load_aux_field(const MConsts<R>& C, const R* __restrict__ a, int nx,
+                                            int ny, int c, int r, int field) {
+  int fy, iy, fx, ix;
+  const int rr = bc_map(r, ny, C.bc_lo[1], C.bc_hi[1], fy, iy);
+  const int cc = bc_map(c, nx, C.bc_lo[0], C.bc_hi[0], fx, ix);
+  return __ldg(a + (size_t)field * nx * ny + (size_t)rr * nx + cc);
 }
 
 // ---------------------------------------------------------------------------

@@ -166,6 +166,12 @@ __global__ void source_mark_kernel(const Member* __restrict__ members, int n) {
   }
 }
 
+size_t faces_work_bytes(int nd, int nx, int ny, int m, int prec) {
+  const size_t nf = nd == 1 ? (size_t)nx + 1
+                            : (size_t)(nx + 1) * (ny + 2) + (size_t)(ny + 1) * (nx + 2);
+  return nf * 7 * (size_t)m * (prec == 0 ? 8 : 4);
+}
+
 cudaError_t launch_source_mark(const Member* members, int n, cudaStream_t st) {
   source_mark_kernel<<<(n + 127) / 128, 128, 0, st>>>(members, n);
   return cudaGetLastError();

@@ -76,6 +76,9 @@ KernelSet claw_kernels_euler_roe(int nd, int prec);
 KernelSet claw_kernels_euler_hlle(int nd, int prec);
 KernelSet claw_kernels_elasticity(int nd, int prec);
 KernelSet claw_kernels_euler_tracer(int nd, int prec);
+KernelSet claw_kernels_acoustics_vc(int nd, int prec);
+// bytes of the per-face records of the per-face classic path
+size_t faces_work_bytes(int nd, int nx, int ny, int m, int prec);
 
 // generic kernels (k_common.cu)
 cudaError_t launch_dt_init(DevCtl* ctls, int n, cudaStream_t st);

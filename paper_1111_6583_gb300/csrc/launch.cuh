@@ -4,6 +4,7 @@
 
 #include "classic.cuh"
 #include "classic3d.cuh"
+#include "classic_faces.cuh"
 #include "kernels.h"
 #include "sharpclaw.cuh"
 
@@ -37,8 +38,17 @@ __global__ void __launch_bounds__(kMaxspeedCells)
           load_aux<MA, R>(C, aux, nx, ny, i + side, j, ar);
         }
         RP::template solve<0>(C, a, b, al, ar, W, s, am, ap, x);
+        if (C.capa < 0) {
 #pragma unroll
-        for (int p = 0; p < MW; ++p) sx = nanmax(sx, (R)fabs(s[p]));
+          for (int p = 0; p < MW; ++p) sx = nanmax(sx, (R)fabs(s[p]));
+        } else {
+          const R kl = load_aux_field<R>(C, aux, nx, ny, i - 1 + side, j, C.capa);
+          const R kr = load_aux_field<R>(C, aux, nx, ny, i + side, j, C.capa);
+#pragma unroll
+          for (int p = 0; p < MW; ++p)
+            sx = nanmax(sx, gt0(s[p]) ? FM<R>::div(s[p], kr)
+                                      : (lt0(s[p]) ? FM<R>::div(-s[p], kl) : R(0)));
+        }
       }
       if constexpr (ND == 2) {
         for (int side = 0; side < (j == ny - 1 ? 2 : 1); ++side) {
@@ -49,8 +59,17 @@ __global__ void __launch_bounds__(kMaxspeedCells)
             load_aux<MA, R>(C, aux, nx, ny, i, j + side, ar);
           }
           RP::template solve<1>(C, a, b, al, ar, W, s, am, ap, x);
+          if (C.capa < 0) {
 #pragma unroll
-          for (int p = 0; p < MW; ++p) sy = nanmax(sy, (R)fabs(s[p]));
+            for (int p = 0; p < MW; ++p) sy = nanmax(sy, (R)fabs(s[p]));
+          } else {
+            const R kl = load_aux_field<R>(C, aux, nx, ny, i, j - 1 + side, C.capa);
+            const R kr = load_aux_field<R>(C, aux, nx, ny, i, j + side, C.capa);
+#pragma unroll
+            for (int p = 0; p < MW; ++p)
+              sy = nanmax(sy, gt0(s[p]) ? FM<R>::div(s[p], kr)
+                                        : (lt0(s[p]) ? FM<R>::div(-s[p], kl) : R(0)));
+          }
         }
       }
     }
@@ -122,10 +141,32 @@ constexpr bool classic2d_fits(int bw) {
   return classic2d_smem<RP, R>(bw) + 1024 <= 48 * 1024;
 }
 
+// the classic step runs on the per-face path with a capacity, and in 2D for
+// solvers whose transverse split needs the neighbouring cells' media
+template <class RP, int ND>
+inline bool uses_faces(int capa) {
+  return ND <= 2 && (capa >= 0 || (ND == 2 && trans_aux_rp<RP>::value));
+}
+
 template <class RP, typename R, int ND>
 struct Launchers {
   static cudaError_t classic(const LaunchArgs& a) {
     const MConsts<R>& C = *(const MConsts<R>*)a.consts;
+    if constexpr (ND <= 2) {
+      if (uses_faces<RP, ND>(C.capa)) {
+        const int nx = a.n3[0], ny = ND == 2 ? a.n3[1] : 1;
+        const size_t fx = faces_count(ND, nx, ny, 0), fy = faces_count(ND, nx, ny, 1);
+        faces_sweep<RP, R, 0><<<(unsigned)((fx + kFacesThreads - 1) / kFacesThreads),
+                                kFacesThreads, 0, a.stream>>>(a.members, C, ND);
+        if (ND == 2)
+          faces_sweep<RP, R, 1><<<(unsigned)((fy + kFacesThreads - 1) / kFacesThreads),
+                                  kFacesThreads, 0, a.stream>>>(a.members, C, ND);
+        const long long nc = (long long)nx * ny;
+        faces_update<RP, R><<<(unsigned)((nc + kFacesThreads - 1) / kFacesThreads),
+                              kFacesThreads, 0, a.stream>>>(a.members, C, ND);
+        return cudaGetLastError();
+      }
+    }
     if constexpr (ND == 3) {
       const long long nx = a.n3[0], ny = a.n3[1], nz = a.n3[2];
       cudaError_t e = cudaMemsetAsync(a.work3, 0, a.work3_bytes, a.stream);

@@ -895,6 +895,110 @@ struct RpElasticity {
 };
 
 // ---------------------------------------------------------------------------
+// linear acoustics in a varying medium: aux (rho, c) per cell (LeVeque FVM
+// book, heterogeneous media).  The left-going wave carries the left cell's
+// impedance and speed, the right-going one the right cell's; the transverse
+// split of a fluctuation held by a cell solves the transverse Riemann
+// problems with its neighbours below and above (TRANS_AUX: it needs their
+// media, so 2D classic steps with this solver run the per-face path).
+// ---------------------------------------------------------------------------
+template <typename R, int ND>
+struct RpAcousticsVC {
+  static constexpr int M = ND + 1, MW = 2, MA = 2, NCTX = 1, NPC = 0;
+  static constexpr bool FWAVE = false, TRANS_AUX = true;
+  static constexpr int WALL_X = 1, WALL_Y = (ND == 2) ? 2 : -1;
+  template <int DIR>
+  struct NZ {
+    __device__ static constexpr bool f(int, int k) { return k == 0 || k == 1 + DIR; }
+  };
+  template <int DIR>
+  __device__ static __forceinline__ void solve(const MConsts<R>&, const R (&ql)[M],
+                                               const R (&qr)[M], const R* al, const R* ar,
+                                               R (&W)[MW][M], R (&s)[MW], R (&am)[M],
+                                               R (&ap)[M], R (&ctx)[NCTX]) {
+    constexpr int n = Dirs<ND, DIR>::n;
+    const R Zl = al[0] * al[1], Zr = ar[0] * ar[1];
+    const R dp = qr[0] - ql[0], du = qr[n] - ql[n];
+    const R iz = FM<R>::rcp(Zl + Zr);
+    const R a1 = (-dp + Zr * du) * iz;
+    const R a2 = (dp + Zl * du) * iz;
+#pragma unroll
+    for (int k = 0; k < M; ++k) W[0][k] = W[1][k] = R(0);
+    W[0][0] = -a1 * Zl;
+    W[0][n] = a1;
+    W[1][0] = a2 * Zr;
+    W[1][n] = a2;
+    s[0] = -al[1];
+    s[1] = ar[1];
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      am[k] = s[0] * W[0][k];
+      ap[k] = s[1] * W[1][k];
+    }
+    ctx[0] = R(0);
+  }
+  // flux (rho c^2 u_n, p / rho) in the (p, u_n) components with one cell's medium
+  template <int DIR>
+  __device__ static __forceinline__ void flux(const MConsts<R>&, const R (&q)[M], const R* a,
+                                              R (&f)[M]) {
+    constexpr int n = Dirs<ND, DIR>::n;
+#pragma unroll
+    for (int k = 0; k < M; ++k) f[k] = R(0);
+    f[0] = a[0] * a[1] * a[1] * q[n];
+    f[n] = FM<R>::div(q[0], a[0]);
+  }
+  template <int DIR>
+  __device__ static __forceinline__ void trans(const MConsts<R>&, const R (&)[NCTX],
+                                               const R (&)[M], R (&bm)[M], R (&bp)[M]) {
+#pragma unroll
+    for (int k = 0; k < M; ++k) bm[k] = bp[k] = R(0);
+  }
+  // B^- a: down-going wave between the cell below (am_) and the cell (ac);
+  // B^+ a: up-going wave between the cell and the one above (ap_)
+  template <int DIR>
+  __device__ static __forceinline__ void trans_aux(const MConsts<R>&, const R* am_, const R* ac,
+                                                   const R* ap_, const R (&a)[M], R (&bm)[M],
+                                                   R (&bp)[M]) {
+    constexpr int t = Dirs<ND, DIR>::t < 0 ? 0 : Dirs<ND, DIR>::t;
+    const R Zm = am_[0] * am_[1], Zc = ac[0] * ac[1], Zp = ap_[0] * ap_[1];
+#pragma unroll
+    for (int k = 0; k < M; ++k) bm[k] = bp[k] = R(0);
+    const R b1 = FM<R>::div(-a[0] + Zc * a[t], Zm + Zc);
+    const R b2 = FM<R>::div(a[0] + Zc * a[t], Zc + Zp);
+    bm[0] = am_[1] * b1 * Zm;
+    bm[t] = -am_[1] * b1;
+    bp[0] = ap_[1] * b2 * Zp;
+    bp[t] = ap_[1] * b2;
+  }
+  template <int DIR>
+  __device__ static __forceinline__ void char_ctx(const MConsts<R>&, const R (&)[M],
+                                                  const R (&)[M], R (&ctx)[NCTX]) {
+    ctx[0] = R(0);
+  }
+  template <int DIR>
+  __device__ static __forceinline__ void to_char(const MConsts<R>&, const R (&)[NCTX],
+                                                 const R (&q)[M], R (&w)[M]) {
+#pragma unroll
+    for (int k = 0; k < M; ++k) w[k] = q[k];
+  }
+  template <int DIR>
+  __device__ static __forceinline__ void from_char(const MConsts<R>&, const R (&)[NCTX],
+                                                   const R (&w)[M], R (&q)[M]) {
+#pragma unroll
+    for (int k = 0; k < M; ++k) q[k] = w[k];
+  }
+};
+
+template <class RP, class = void>
+struct trans_aux_rp {
+  static constexpr bool value = false;
+};
+template <class RP>
+struct trans_aux_rp<RP, decltype((void)RP::TRANS_AUX, void())> {
+  static constexpr bool value = RP::TRANS_AUX;
+};
+
+// ---------------------------------------------------------------------------
 // Euler with a passive tracer phi (phi_t + u . grad phi = 0; Sec. 6.2): the
 // Euler Roe solver on the first ND + 2 components and a tracer wave (the jump
 // of phi alone) moving with the normal Roe velocity, placed before the u + c

@@ -69,6 +69,7 @@ __global__ void __launch_bounds__(TX * TY)
                                : TX + 1;
   __shared__ R Qt[M][HY][HX];
   __shared__ R At[MAS][MA > 0 ? HY : 1][MA > 0 ? HX : 1];
+  __shared__ R Kt[HY][HX];  // capacity kappa (when the method has one)
   __shared__ R EL[M][NE];  // left edge value of the cell right of an interface
   __shared__ R ER[M][NE];  // right edge value of the cell left of an interface
   __shared__ R FM[M][NE];  // A^- dQ at the interface
@@ -130,6 +131,9 @@ __global__ void __launch_bounds__(TX * TY)
 #pragma unroll
         for (int k = 0; k < MA; ++k) At[k][MA > 0 ? hj : 0][MA > 0 ? hi : 0] = a[k];
       }
+      if (C.capa >= 0)
+        Kt[hj][hi] = load_aux_field<R>(C, aux, nx, ny, min(c, nx + G - 1),
+                                       (ND == 2) ? min(r, ny + G - 1) : 0, C.capa);
     }
     __syncthreads();
 
@@ -234,8 +238,20 @@ __global__ void __launch_bounds__(TX * TY)
         const int nA = (dir == 0) ? nx : ny, nB = (dir == 0) ? ny : nx;
         if (ga <= nA && gb < nB) {
           R m_ = R(0);
+          if (C.capa < 0) {
 #pragma unroll
-          for (int p = 0; p < MW; ++p) m_ = nanmax(m_, (R)fabs(s[p]));
+            for (int p = 0; p < MW; ++p) m_ = nanmax(m_, (R)fabs(s[p]));
+          } else {
+            // a wave's Courant number uses the capacity of the cell it enters
+            const int hil = (dir == 0) ? G + a - 1 : G + b, hir = (dir == 0) ? G + a : G + b;
+            const int hjl = (dir == 0) ? ((ND == 2) ? G + b : 0) : G + a - 1;
+            const int hjr = (dir == 0) ? ((ND == 2) ? G + b : 0) : G + a;
+            const R kl = Kt[hjl][hil], kr = Kt[hjr][hir];
+#pragma unroll
+            for (int p = 0; p < MW; ++p)
+              m_ = nanmax(m_, gt0(s[p]) ? ::claw::FM<R>::div(s[p], kr)
+                                        : (lt0(s[p]) ? ::claw::FM<R>::div(-s[p], kl) : R(0)));
+          }
           if (dir == 0) smx = nanmax(smx, m_);
           else smy = nanmax(smy, m_);
         }
@@ -280,9 +296,12 @@ __global__ void __launch_bounds__(TX * TY)
 #pragma unroll
           for (int k = 0; k < M; ++k) adq[k] = fr[k] - fl[k];
         }
-        // thread cidx == tid owns cell (ci, cj) (NT == TX*TY)
+        // thread cidx == tid owns cell (ci, cj) (NT == TX*TY); with a capacity
+        // the cell's L is -(1/(kappa_i dx)) (...)
+        const R idk = C.capa < 0 ? idn
+                                 : ::claw::FM<R>::div(idn, Kt[(ND == 2) ? G + cj : 0][G + ci]);
 #pragma unroll
-        for (int k = 0; k < M; ++k) L[k] -= (FP[k][e0] + FM[k][e1] + adq[k]) * idn;
+        for (int k = 0; k < M; ++k) L[k] -= (FP[k][e0] + FM[k][e1] + adq[k]) * idk;
       }
       __syncthreads();
     }

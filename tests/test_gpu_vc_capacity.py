@@ -1,0 +1,116 @@
+"""GPU parity of acoustics in a varying medium and of the capacity function
+kappa (Eq. (conslaw)) against the oracle: the 1D row kernel, the per-face
+classic path (capacity; 2D media-aware transverse splits), SharpClaw, and a
+controller run of the heterogeneous 2D acoustics workload.
+"""
+import numpy as np
+import pytest
+
+from paper_1111_6583_gb300 import workloads as wl
+from tests.gpu_util import (FP32_SHOCK_L1_TOL, FP32_SMOOTH_TOL, FP64_TOL, gpu_evolve,
+                            gpu_fixed_steps, oracle_evolve, oracle_fixed_steps, rel_l1,
+                            rel_maxnorm)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+@pytest.mark.parametrize("bc", [("periodic", "periodic"), ("wall", "extrap")])
+@pytest.mark.parametrize("capa", [-1, 2])
+def test_vc_1d_classic(orc, bc, capa):
+    kw = {"capa_index": 2} if capa >= 0 else {"num_aux": 2}
+    spec = wl.random_1d("acoustics_vc", 700, bc=bc, **kw)
+    if capa < 0:
+        spec["aux"] = spec["aux"][:2].copy()
+    dt = 0.4 / 700
+    qo, co = oracle_fixed_steps(orc, spec, dt, 5)
+    qg, cg = gpu_fixed_steps(spec, "fp64", dt, 5)
+    assert rel_maxnorm(qg, qo) <= FP64_TOL
+    assert np.allclose(cg, co, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("transverse", [0, 1, 2])
+@pytest.mark.parametrize("capa", [-1, 2])
+def test_vc_2d_classic_faces(orc, transverse, capa):
+    kw = {"capa_index": 2} if capa >= 0 else {"num_aux": 2}
+    spec = wl.random_smooth_2d("acoustics_vc", 131, 70, transverse=transverse, **kw)
+    if capa < 0:
+        spec["aux"] = spec["aux"][:2].copy()
+    dt = 0.3 / 131
+    qo, co = oracle_fixed_steps(orc, spec, dt, 4)
+    qg, cg = gpu_fixed_steps(spec, "fp64", dt, 4)
+    assert rel_maxnorm(qg, qo) <= FP64_TOL
+    assert np.allclose(cg, co, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("ndim", [1, 2])
+@pytest.mark.parametrize("rp", ["sw_roe", "euler_roe"])
+def test_capacity_classic_conservative_systems(orc, ndim, rp):
+    if ndim == 1:
+        spec = wl.random_1d(rp, 400, bc=("wall", "extrap"))
+        x = (np.arange(400) + 0.5) / 400
+        kap = (1.0 + 0.4 * np.sin(2 * np.pi * x))[None]
+    else:
+        spec = wl.random_smooth_2d(rp, 90, 61, bc="wall")
+        X, Y = np.meshgrid((np.arange(90) + 0.5) / 90, (np.arange(61) + 0.5) / 61,
+                           indexing="xy")
+        kap = (1.0 + 0.4 * np.sin(2 * np.pi * X) * np.cos(2 * np.pi * Y))[None]
+    spec.update(num_aux=1, capa_index=0, aux=np.ascontiguousarray(kap))
+    dt = 0.2 / spec["n"][0]
+    qo, co = oracle_fixed_steps(orc, spec, dt, 4)
+    qg, cg = gpu_fixed_steps(spec, "fp64", dt, 4)
+    assert rel_maxnorm(qg, qo) <= FP64_TOL
+    assert np.allclose(cg, co, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("ndim", [1, 2])
+@pytest.mark.parametrize("capa", [-1, 2])
+def test_vc_sharpclaw(orc, ndim, capa):
+    kw = {"capa_index": 2} if capa >= 0 else {"num_aux": 2}
+    if ndim == 1:
+        spec = wl.random_1d("acoustics_vc", 300, scheme="sharpclaw", **kw)
+    else:
+        spec = wl.random_smooth_2d("acoustics_vc", 70, 37, scheme="sharpclaw", **kw)
+    if capa < 0:
+        spec["aux"] = spec["aux"][:2].copy()
+    dt = 0.15 / spec["n"][0]
+    qo, co = oracle_fixed_steps(orc, spec, dt, 3)
+    qg, cg = gpu_fixed_steps(spec, "fp64", dt, 3)
+    assert rel_maxnorm(qg, qo) <= FP64_TOL
+    assert np.allclose(cg, co, rtol=1e-13, atol=0)
+
+
+def test_vc_2d_workload_controller(orc):
+    """The heterogeneous 2D acoustics workload (impedance jump, stretched
+    grid as a capacity, walls) through the controller."""
+    spec = wl.acoustics_vc_2d(n=128, t_end=0.3)
+    qo, io = oracle_evolve(orc, spec, 0.3)
+    for graph in (True, False):
+        qg, ig = gpu_evolve(spec, "fp64", 0.3, use_graph=graph)
+        assert ig["steps"] == io["steps"] and ig["t"] == io["t"] == 0.3
+        assert rel_maxnorm(qg, qo) <= FP64_TOL
+    q32, i32 = gpu_evolve(spec, "fp32", 0.3)
+    assert i32["t"] == 0.3 and rel_l1(q32, qo) <= FP32_SHOCK_L1_TOL
+
+
+def test_vc_2d_fp32(orc):
+    spec = wl.random_smooth_2d("acoustics_vc", 131, 70, capa_index=2)
+    dt = 0.3 / 131
+    qo, _ = oracle_fixed_steps(orc, spec, dt, 4)
+    qg, _ = gpu_fixed_steps(spec, "fp32", dt, 4)
+    assert rel_maxnorm(qg, qo) <= FP32_SMOOTH_TOL
+
+
+def test_batches_reject_the_per_face_path():
+    from paper_1111_6583_gb300 import claw
+    spec = wl.random_smooth_2d("acoustics_vc", 32, 32, capa_index=2)
+    with pytest.raises(claw.ClawError):
+        claw.Batch([spec, spec], "fp64")
