@@ -86,6 +86,7 @@ void noalloc_consts(const claw_method& m, MConsts<R>& C) {
   C.gamma = (R)m.params[0];
   C.gm1 = (R)(m.params[0] - 1.0);
   C.weno_eps = (R)m.weno_eps;
+  C.capa = -1;  // no capacity field on this path
   C.lim = m.lim;
   C.order = m.order;
   C.transverse = m.transverse;
@@ -120,6 +121,8 @@ claw_status claw_sharp_step_noalloc(const claw_method* m, const claw_grid* g, co
   const int nx = (int)g->n[0], ny = g->ndim == 2 ? (int)g->n[1] : 1;
   if (g->n[0] < 4 || (g->ndim == 2 && g->n[1] < 4)) return nfail("each direction needs >= 4 cells");
   if (m->weno_order != 5) return nfail("the allocation-free step takes WENO5 only");
+  if (m->capa_index != -1 || m->source != 0)
+    return nfail("the allocation-free step takes no capacity or source term");
   if (!(dt > 0)) return nfail("dt must be positive");
   if (m->num_aux > 0 && !aux) return nfail("this solver needs aux fields");
   if (m->char_decomp && m->rp == CLAW_RP_ELASTICITY_FWAVE)
