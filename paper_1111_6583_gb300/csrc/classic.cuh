@@ -338,11 +338,20 @@ __global__ void __launch_bounds__(BW)
   using NZX = typename RP::template NZ<0>;
   using NZY = typename RP::template NZ<1>;
   constexpr int TX = BW - 4;
+  // neighbour contributions: systems of up to three fields publish the raw
+  // vectors (the receiver multiplies and adds them, saving the sender's pass
+  // into a zeroed sum); larger systems publish per-row sums (mailboxes)
+  constexpr bool GATHER = (M <= 3);
   __shared__ R qs[M][BW];
   __shared__ R pcs[NP][BW];
   __shared__ R xws[MW][M][BW];
-  __shared__ R mbl[4][M][BW];
-  __shared__ R mbr[2][M][BW];
+  constexpr int MM = GATHER ? 1 : M, BM = GATHER ? 1 : BW;  // mailbox extents
+  constexpr int GM = GATHER ? M : 1, BG = GATHER ? BW : 1;  // raw-vector extents
+  __shared__ R mbl[4][MM][BM];
+  __shared__ R mbr[2][MM][BM];
+  __shared__ R gxv[3][GM][BG];  // A^-dQ + F, B^+ and B^- of it (x-interface)
+  __shared__ R gyv[4][GM][BG];  // x-splits of the y-fluctuations: A^- (B^+..),
+                                // A^- (B^-..), A^+ (B^+..), A^+ (B^-..)
   __shared__ int s_done, s_cur, s_nbuf;
   __shared__ R s_k[3];  // dt/dx, dt/dy, dt^2/(2 dx dy)
   const int l = threadIdx.x;
@@ -468,10 +477,13 @@ __global__ void __launch_bounds__(BW)
       __syncthreads();  // x waves ready
 
       R tl_[4][M], tr_[2][M];
+      R gx[3][M], gy[4][M];
 #pragma unroll
       for (int k = 0; k < M; ++k) {
         tl_[0][k] = tl_[1][k] = tl_[2][k] = tl_[3][k] = R(0);
         tr_[0][k] = tr_[1][k] = R(0);
+        gx[0][k] = gx[1][k] = gx[2][k] = R(0);
+        gy[0][k] = gy[1][k] = gy[2][k] = gy[3][k] = R(0);
       }
 
       // (4) x-limiting, corrections, transverse propagation
@@ -503,7 +515,8 @@ __global__ void __launch_bounds__(BW)
           ap_[k] = xap[k] - F[k];
           am_[k] = xam[k] + F[k];
           acc2[k] -= dtdx * ap_[k];
-          tl_[2][k] -= dtdx * am_[k];
+          if constexpr (GATHER) gx[0][k] = am_[k];
+          else tl_[2][k] -= dtdx * am_[k];
         }
         if (xcfl && Rw >= r0 && Rw <= rend) {
 #pragma unroll
@@ -523,9 +536,14 @@ __global__ void __launch_bounds__(BW)
             acc2[k] += kxy * (bpp[k] - bmp[k]);
             acc3[k] -= kxy * bpp[k];
             acc1[k] += kxy * bmp[k];
-            tl_[2][k] += kxy * (bpm[k] - bmm[k]);
-            tl_[3][k] -= kxy * bpm[k];
-            tl_[1][k] += kxy * bmm[k];
+            if constexpr (GATHER) {
+              gx[1][k] = bpm[k];
+              gx[2][k] = bmm[k];
+            } else {
+              tl_[2][k] += kxy * (bpm[k] - bmm[k]);
+              tl_[3][k] -= kxy * bpm[k];
+              tl_[1][k] += kxy * bmm[k];
+            }
           }
         }
       }
@@ -563,21 +581,38 @@ __global__ void __launch_bounds__(BW)
           for (int k = 0; k < M; ++k) {
             acc1[k] += kxy * (app[k] - amp[k]);
             acc0[k] += kxy * (apm[k] - amm[k]);
-            tr_[1][k] -= kxy * app[k];
-            tr_[0][k] -= kxy * apm[k];
-            tl_[1][k] += kxy * amp[k];
-            tl_[0][k] += kxy * amm[k];
+            if constexpr (GATHER) {
+              gy[0][k] = amp[k];
+              gy[1][k] = amm[k];
+              gy[2][k] = app[k];
+              gy[3][k] = apm[k];
+            } else {
+              tr_[1][k] -= kxy * app[k];
+              tr_[0][k] -= kxy * apm[k];
+              tl_[1][k] += kxy * amp[k];
+              tl_[0][k] += kxy * amm[k];
+            }
           }
         }
       }
 #pragma unroll
       for (int k = 0; k < M; ++k) {
-        mbl[0][k][l] = tl_[0][k];
-        mbl[1][k][l] = tl_[1][k];
-        mbl[2][k][l] = tl_[2][k];
-        mbl[3][k][l] = tl_[3][k];
-        mbr[0][k][l] = tr_[0][k];
-        mbr[1][k][l] = tr_[1][k];
+        if constexpr (GATHER) {
+          gxv[0][k][l] = gx[0][k];
+          gxv[1][k][l] = gx[1][k];
+          gxv[2][k][l] = gx[2][k];
+          gyv[0][k][l] = gy[0][k];
+          gyv[1][k][l] = gy[1][k];
+          gyv[2][k][l] = gy[2][k];
+          gyv[3][k][l] = gy[3][k];
+        } else {
+          mbl[0][k][l] = tl_[0][k];
+          mbl[1][k][l] = tl_[1][k];
+          mbl[2][k][l] = tl_[2][k];
+          mbl[3][k][l] = tl_[3][k];
+          mbr[0][k][l] = tr_[0][k];
+          mbr[1][k][l] = tr_[1][k];
+        }
       }
       __syncthreads();  // mailboxes ready
 
@@ -585,17 +620,34 @@ __global__ void __launch_bounds__(BW)
       if (l + 1 < BW) {
 #pragma unroll
         for (int k = 0; k < M; ++k) {
-          acc0[k] += mbl[0][k][l + 1];
-          acc1[k] += mbl[1][k][l + 1];
-          acc2[k] += mbl[2][k][l + 1];
-          acc3[k] += mbl[3][k][l + 1];
+          if constexpr (GATHER) {
+            // the right neighbour's x-interface is this column's right face
+            const R am_n = gxv[0][k][l + 1], bpm_n = gxv[1][k][l + 1],
+                    bmm_n = gxv[2][k][l + 1];
+            acc2[k] -= dtdx * am_n;
+            acc2[k] += kxy * (bpm_n - bmm_n);
+            acc3[k] -= kxy * bpm_n;
+            acc1[k] += kxy * bmm_n;
+            acc1[k] += kxy * gyv[0][k][l + 1];
+            acc0[k] += kxy * gyv[1][k][l + 1];
+          } else {
+            acc0[k] += mbl[0][k][l + 1];
+            acc1[k] += mbl[1][k][l + 1];
+            acc2[k] += mbl[2][k][l + 1];
+            acc3[k] += mbl[3][k][l + 1];
+          }
         }
       }
       if (l >= 1) {
 #pragma unroll
         for (int k = 0; k < M; ++k) {
-          acc0[k] += mbr[0][k][l - 1];
-          acc1[k] += mbr[1][k][l - 1];
+          if constexpr (GATHER) {
+            acc1[k] -= kxy * gyv[2][k][l - 1];
+            acc0[k] -= kxy * gyv[3][k][l - 1];
+          } else {
+            acc0[k] += mbr[0][k][l - 1];
+            acc1[k] += mbr[1][k][l - 1];
+          }
         }
       }
       const int Rf = Rw - 2;

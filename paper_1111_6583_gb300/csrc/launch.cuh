@@ -133,8 +133,11 @@ __global__ void __launch_bounds__(kMaxspeedCells)
 // reduction adds under 1 KB); a block may declare at most 48 KB statically
 template <class RP, typename R>
 constexpr size_t classic2d_smem(int bw) {
+  // qs, xws, neighbour exchange (mailboxes 6 M or raw vectors 7 M plus the
+  // one-row placeholders of the unused form), per-cell prep
   return sizeof(R) * (size_t)bw *
-         (size_t)(RP::M + RP::MW * RP::M + 6 * RP::M + (RP::NPC > 0 ? RP::NPC : 1));
+         (size_t)(RP::M + RP::MW * RP::M + (RP::M <= 3 ? 7 : 6) * RP::M +
+                  (RP::NPC > 0 ? RP::NPC : 1));
 }
 template <class RP, typename R>
 constexpr bool classic2d_fits(int bw) {
