@@ -1167,6 +1167,16 @@ __device__ __forceinline__ R limiter_mc(R th) {
   const auto b = fbits(th);
   return b < fbits(R(1) / R(3)) ? two_th : (b <= fbits(R(3)) ? mid : R(2));
 }
+// the same as one fused multiply-add, a th + b with (a, b) chosen by the
+// branch: (2, 0), (1/2, 1/2) or (0, 2); the middle branch rounds once
+template <typename R>
+__device__ __forceinline__ R limiter_mc_fma(R th) {
+  const auto b = fbits(th);
+  const bool pos = gt0(th), lo = b < fbits(R(1) / R(3)), mid = b <= fbits(R(3));
+  const R a = !pos ? R(0) : (lo ? R(2) : (mid ? R(0.5) : R(0)));
+  const R c = !pos ? R(0) : (lo ? R(0) : (mid ? R(0.5) : R(2)));
+  return a * th + c;
+}
 
 // Second-order correction at one interface (Eq. (lwflux) with limited waves):
 //   F = 1/2 sum_p c_p phi(theta_p) W^p,  c_p = |s|(1 - dt/dx |s|)   (waves)
@@ -1210,6 +1220,7 @@ __device__ __forceinline__ void correction(const MConsts<R>& C, const R (&W)[RP:
       batched = true;
     }
   }
+  const R hd = R(0.5) * dtdn;
 #pragma unroll
   for (int p = 0; p < MW; ++p) {
     R phi;
@@ -1217,11 +1228,20 @@ __device__ __forceinline__ void correction(const MConsts<R>& C, const R (&W)[RP:
     else if (C.lim == CLAW_LIM_NONE) phi = R(1);
     else {
       const R th = batched ? dot_up[p] * inv[p] : FM<R>::div(dot_up[p], nrm[p]);
-      phi = C.lim == CLAW_LIM_MC ? limiter_mc<R>(th) : limiter<R>(C.lim, th);
+      // systems of three or more waves take the fused forms (one rounding
+      // less per wave; the long linear runs of two-wave systems keep the
+      // oracle's order)
+      phi = C.lim == CLAW_LIM_MC ? (MW >= 3 ? limiter_mc_fma<R>(th) : limiter_mc<R>(th))
+                                 : limiter<R>(C.lim, th);
     }
     const R a = fabs(s[p]);
-    const R sg = RP::FWAVE ? (gt0(s[p]) ? R(1) : (lt0(s[p]) ? R(-1) : R(0))) : a;
-    const R cf = R(0.5) * sg * (R(1) - dtdn * a) * phi;
+    R cf;
+    if (MW >= 3 && !RP::FWAVE) {
+      cf = (R(0.5) - hd * a) * a * phi;  // 1/2 |s| (1 - dt/dx |s|) phi
+    } else {
+      const R sg = RP::FWAVE ? (gt0(s[p]) ? R(1) : (lt0(s[p]) ? R(-1) : R(0))) : a;
+      cf = R(0.5) * sg * (R(1) - dtdn * a) * phi;
+    }
 #pragma unroll
     for (int k = 0; k < RP::M; ++k)
       if (NZ::f(p, k)) F[k] += cf * W[p][k];
