@@ -510,7 +510,9 @@ def profile_case(case):
     sw2d64/sw2d32 -- 2048^2 dam break, autotune (40 launches) then 3 steps;
     elast -- 1024-member FP32 elasticity batch, 5 fused steps;
     sharp -- 1024x512 shock-bubble FP64, 2 SharpClaw steps (6 stage launches);
-    sw2d1024 -- the headline 1024^2 FP64 dam break, autotune then 4 steps."""
+    sw2d1024 -- the headline 1024^2 FP64 dam break, autotune then 4 steps;
+    axisym -- 1280x320 axisymmetric shock-bubble FP64, tune then 3 steps;
+    vc -- 1024^2 varying-medium acoustics with capacity FP64, 3 steps."""
     import torch
     from paper_1111_6583_gb300 import claw
     from paper_1111_6583_gb300 import workloads as wl
@@ -524,6 +526,17 @@ def profile_case(case):
         print("tile", s.tune())
         s.set_t_end(1.5)
         s.advance(4)
+    elif case == "axisym":
+        sp = wl.shock_bubble_axisym()
+        s = claw.Solver(sp, "fp64")
+        print("tile", s.tune())
+        s.set_t_end(sp["t_end"])
+        s.advance(3)
+    elif case == "vc":
+        sp = wl.acoustics_vc_2d(n=1024)
+        s = claw.Solver(sp, "fp64")
+        s.set_t_end(sp["t_end"])
+        s.advance(3)
     elif case == "elast":
         ens = wl.elasticity_ensemble(1024)
         b = claw.Batch([wl.elasticity_member(e["n"], e["amp"], e["width"]) for e in ens], "fp32")
@@ -551,7 +564,8 @@ def main():
     ap.add_argument("--record-traffic", default=None,
                     help="write the headline kernel's traffic record from an ncu csv")
     ap.add_argument("--case", default=None,
-                    help="run one short launch sequence for a profiler (sw2d64, sw2d32, elast, sharp)")
+                    help="run one short launch sequence for a profiler (sw2d64, sw2d32, sw2d1024, "
+                         "elast, sharp, axisym, vc)")
     args = ap.parse_args()
     if args.record_traffic:
         record_traffic(args.record_traffic)
