@@ -516,19 +516,21 @@ struct EulerBase {
   __device__ static __forceinline__ void roe(const MConsts<R>& C, const R (&ql)[M],
                                              const R (&qr)[M], R (&x)[NCTX], R& pl, R& pr) {
     constexpr int n = Dirs<ND, DIR>::n, t = Dirs<ND, DIR>::t;
-    const R irl = FM<R>::rcp(ql[0]), irr = FM<R>::rcp(qr[0]);
+    const R il = rsq(ql[0]), ir = rsq(qr[0]);  // 1/sqrt(rho)
+    const R irl = il * il, irr = ir * ir;      // 1/rho
     pl = pressure<DIR>(C, ql, irl);
     pr = pressure<DIR>(C, qr, irr);
-    const R il = rsq(ql[0]), ir = rsq(qr[0]);  // 1/sqrt(rho)
     const R sl = ql[0] * il, sr = qr[0] * ir;  // sqrt(rho)
     const R iden = FM<R>::rcp(sl + sr);
     x[0] = (ql[n] * il + qr[n] * ir) * iden;
     x[1] = (t >= 0) ? (ql[t < 0 ? 0 : t] * il + qr[t < 0 ? 0 : t] * ir) * iden : R(0);
     x[2] = ((ql[E] + pl) * il + (qr[E] + pr) * ir) * iden;  // sqrt(rho) H = (E+p)/sqrt(rho)
     const R c2 = C.gm1 * (x[2] - R(0.5) * (x[0] * x[0] + x[1] * x[1]));
-    x[3] = FM<R>::sqrt(c2);
-    x[4] = FM<R>::rcp(c2);
-    x[5] = FM<R>::div(R(0.5), x[3]);
+    // c, 1/c^2 and 1/(2c) from one reciprocal square root
+    const R rc = rsq(c2);
+    x[3] = c2 * rc;
+    x[4] = rc * rc;
+    x[5] = R(0.5) * rc;
   }
 
   // eigen-coefficients of d in the frame (normal a, tangential b)
@@ -609,8 +611,13 @@ template <typename R, int ND>
 struct RpEulerRoe : EulerBase<R, ND> {
   using B = EulerBase<R, ND>;
   static constexpr int M = B::M, MW = B::M, MA = 0, NCTX = B::NCTX, E = B::E, NPC = 0;
+  // the shear wave (2D) lives in the tangential momentum and the energy
   template <int DIR>
-  struct NZ : AllNZ {};
+  struct NZ {
+    __device__ static constexpr bool f(int p, int k) {
+      return ND == 1 || p != 2 || k == 2 - DIR || k == E;
+    }
+  };
   static constexpr bool FWAVE = false;
   static constexpr int WALL_X = 1, WALL_Y = (ND == 2) ? 2 : -1;
 
@@ -625,35 +632,36 @@ struct RpEulerRoe : EulerBase<R, ND> {
     const R X = q[0] * q[E] - R(0.5) * ke;
     mn = q[n];
     rc2 = C.gamma * C.gm1 * X;
-    phys = q[0] > R(0) && X > R(0);
+    phys = gt0(q[0]) && gt0(X);
   }
+  // (comparisons of the non-negative m^2 and rho^2 c^2 on their bit patterns)
   template <int DIR>
   __device__ static __forceinline__ bool minus_neg(const MConsts<R>& C, const R (&q)[M]) {
     R m, r;
     bool ph;
     sign_terms<DIR>(C, q, m, r, ph);
-    return ph && (m < R(0) || m * m < r);
+    return ph && (lt0(m) || fbits(m * m) < fbits(r));
   }
   template <int DIR>
   __device__ static __forceinline__ bool minus_pos(const MConsts<R>& C, const R (&q)[M]) {
     R m, r;
     bool ph;
     sign_terms<DIR>(C, q, m, r, ph);
-    return ph && m > R(0) && m * m > r;
+    return ph && gt0(m) && fbits(m * m) > fbits(r);
   }
   template <int DIR>
   __device__ static __forceinline__ bool plus_neg(const MConsts<R>& C, const R (&q)[M]) {
     R m, r;
     bool ph;
     sign_terms<DIR>(C, q, m, r, ph);
-    return ph && m < R(0) && m * m > r;
+    return ph && lt0(m) && fbits(m * m) > fbits(r);
   }
   template <int DIR>
   __device__ static __forceinline__ bool plus_pos(const MConsts<R>& C, const R (&q)[M]) {
     R m, r;
     bool ph;
     sign_terms<DIR>(C, q, m, r, ph);
-    return ph && (m > R(0) || m * m < r);
+    return ph && (gt0(m) || fbits(m * m) < fbits(r));
   }
 
   template <int DIR>
@@ -744,7 +752,7 @@ struct RpEulerRoe : EulerBase<R, ND> {
         }
       }
     }
-    split_waves<M, MW, R>(W, s, am, ap);
+    split_waves<M, MW, R, NZ<DIR>>(W, s, am, ap);
   }
 };
 
