@@ -160,15 +160,21 @@ class Clocks:
                 "samples": len(self.samples)}
 
 
-def dist_setup(gpus):
+def dist_setup(gpus, backend=None):
+    """One process per GPU (torchrun environment).  Replicas only: the ranks
+    share no data; the process group carries the barrier and the max of the
+    timings.  backend defaults to NCCL with a GPU, gloo without."""
     import torch
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if backend is None:
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
     return rank, world, local
 
 
@@ -183,9 +189,16 @@ def max_over_ranks(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_value(units_per_rank, total_ms_max, world):
+    """Whole-job throughput of N replicas: every rank processes the same
+    units; the job takes the slowest rank's time."""
+    return units_per_rank * world / (total_ms_max * 1e-3)
 
 
 def timed_steps(solver, stream, steps, flush):
@@ -595,7 +608,7 @@ def main():
     barrier(world)
     total_ms = max_over_ranks(sum(ms), world)
     cells = args.n * args.n
-    value = cells * args.steps * world / (total_ms * 1e-3)
+    value = replica_value(cells * args.steps, total_ms, world)
     avg_ms = sum(ms) / len(ms)
     flops = SW2D_FLOPS_PER_CELL * cells
     achieved_tf = flops / (avg_ms * 1e-3) / 1e12
