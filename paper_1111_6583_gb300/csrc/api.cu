@@ -256,6 +256,7 @@ cudaError_t launch_attempt(const KernelSet& ks, const claw_method& m, const Memb
                            int nmembers = 1, const int* n3 = nullptr, void* work3 = nullptr,
                            size_t work3_bytes = 0) {
   LaunchArgs a{mem, tiles, ntiles, consts, bw, h, 0, st};
+  a.nmembers = nmembers;
   if (n3) {
     a.n3[0] = n3[0];
     a.n3[1] = n3[1];
@@ -1404,7 +1405,7 @@ claw_status claw_server_pump(claw_server* v, int steps, int* running, int* queue
   if (!v->running.empty()) {
     for (int i = 0; i < steps; ++i)
       VCK(launch_attempt(v->ks, v->m, v->d_mem, v->d_tiles, v->ntiles, v->consts.data(),
-                         v->bw, v->h, v->st));
+                         v->bw, v->h, v->st, nullptr, 0, (int)v->running.size()));
     // 4. retire finished requests
     const int nr = (int)v->running.size();
     std::vector<char> fin(nr, 0);

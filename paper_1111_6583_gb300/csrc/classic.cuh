@@ -297,7 +297,9 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? 7 : 1)
         }
       }
     }
-    finish_attempt<R>(ctl, smax, R(0), bad, mb.ntiles, true);
+    // per-warp atomics; the controllers run in the next launch
+    fold_warp<R>(ctl, smax, bad);
+    __syncthreads();  // s_* are rewritten by the next tile
   }
 }
 

@@ -302,4 +302,22 @@ static __device__ __forceinline__ void finish_attempt(DevCtl* ctl, T sx, T sy, i
   }
 }
 
+// Fold a per-thread maximum speed (direction 0) and bad flag into the control
+// block with one atomic per warp: no block barrier and no arrival count.  The
+// controller then runs in a separate launch (launch_controllers) once the
+// attempt's kernel has finished.  Called by every thread of a full warp.
+template <typename T>
+static __device__ __forceinline__ void fold_warp(DevCtl* ctl, T sx, int bad) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sx = nanmax(sx, __shfl_xor_sync(0xffffffffu, sx, o));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    const double d = (double)sx;
+    if (d != 0.0) atomicMax(&ctl->smax[0], (unsigned long long)__double_as_longlong(d));
+    if (bad) atomicOr(&ctl->bad, 1u);
+  }
+}
+
 }  // namespace claw

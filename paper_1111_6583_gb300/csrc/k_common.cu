@@ -172,6 +172,19 @@ size_t faces_work_bytes(int nd, int nx, int ny, int m, int prec) {
   return nf * 7 * (size_t)m * (prec == 0 ? 8 : 4);
 }
 
+__global__ void controllers_kernel(const Member* __restrict__ members, int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) {
+    DevCtl* c = members[k].ctl;
+    if (!c->done) run_controller(c);
+  }
+}
+
+cudaError_t launch_controllers(const Member* members, int n, cudaStream_t st) {
+  controllers_kernel<<<(n + 127) / 128, 128, 0, st>>>(members, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_source_mark(const Member* members, int n, cudaStream_t st) {
   source_mark_kernel<<<(n + 127) / 128, 128, 0, st>>>(members, n);
   return cudaGetLastError();

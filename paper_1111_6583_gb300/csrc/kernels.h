@@ -27,6 +27,7 @@ struct LaunchArgs {
   size_t work3_bytes;
   const StageOp* stage_op; // SharpClaw: explicit stage (host pointer) or null
   int sweep;               // 2D classic: 0 unsplit, 1 / 2 the x / y sweeps of a split step
+  int nmembers;            // members of the table (1D classic runs their controllers after)
 };
 
 // stage tables of the SharpClaw time integrators
@@ -85,6 +86,8 @@ cudaError_t launch_dt_init(DevCtl* ctls, int n, cudaStream_t st);
 // after a source launch: record that every member's accepted steps have had
 // their source step (members[k].ctl->src_mark = steps)
 cudaError_t launch_source_mark(const Member* members, int n, cudaStream_t st);
+// the CFL controller of every member that took part in the attempt (not done)
+cudaError_t launch_controllers(const Member* members, int n, cudaStream_t st);
 cudaError_t launch_set_t_end(DevCtl* ctls, int n, double t_end, long long max_steps_rel,
                              cudaStream_t st);
 cudaError_t launch_force_dt(DevCtl* ctl, double dt, cudaStream_t st);

@@ -190,6 +190,9 @@ struct Launchers {
       classic1d_kernel<RP, R, kClassic1dThreads, K>
           <<<launch_grid(a.ntiles_total), kClassic1dThreads, 0, a.stream>>>(a.members, a.tiles,
                                                                          a.ntiles_total, C);
+      const cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      return launch_controllers(a.members, a.nmembers > 0 ? a.nmembers : 1, a.stream);
     } else {
       if constexpr (classic2d_fits<RP, R>(128)) {
         if (a.bw == 128) {
