@@ -431,36 +431,52 @@ cudaError_t autotune(claw_solver* s) {
   Member mt = s->h_mem;
   mt.ctl = s->d_ctl_tune;
   const int nx = (int)s->g.n[0], ny = (int)s->g.n[1];
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int bws[2] = {64, 128};
-  const int hs[5] = {8, 16, 32, 64, 128};
+  // fixed heights, plus for each k the lowest height whose tile count fits in
+  // k x (number of SMs), k = 1..8: whole waves at any residency
+  std::vector<std::pair<int, int>> cand;
+  for (int bw : bws) {
+    if (bw > s->ks.max_bw) continue;
+    for (int h : {8, 16, 32, 64, 128})
+      if (h <= 2 * ny) cand.push_back({bw, h});
+    for (int k = 1; k <= 8; ++k) {
+      if (nsm <= 0) break;
+      int h = 4;
+      while (h < ny && classic2d_tiles(nx, ny, bw, h) > k * nsm) ++h;
+      bool seen = false;
+      for (auto& pr : cand) seen |= (pr.first == bw && pr.second == h);
+      if (!seen) cand.push_back({bw, h});
+    }
+  }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   float best = 1e30f;
   int bb = s->ks.max_bw, bh = 32;
-  for (int ib = 0; ib < 2; ++ib)
-    for (int ih = 0; ih < 5; ++ih) {
-      const int bw = bws[ib], h = hs[ih];
-      if (h > 2 * ny || bw > s->ks.max_bw) continue;
-      const int nt = classic2d_tiles(nx, ny, bw, h);
-      mt.ntiles = nt;
-      if ((e = cudaMemcpyAsync(s->d_mem_tune, &mt, sizeof(Member), cudaMemcpyHostToDevice,
-                               s->st)) != cudaSuccess)
-        break;
-      LaunchArgs a{s->d_mem_tune, nullptr, nt, s->consts.data(), bw, h, 0, s->st};
-      if ((e = s->ks.classic(a)) != cudaSuccess) break;  // warm-up
-      cudaEventRecord(e0, s->st);
-      for (int r = 0; r < 3; ++r) s->ks.classic(a);
-      cudaEventRecord(e1, s->st);
-      if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best) {
-        best = ms;
-        bb = bw;
-        bh = h;
-      }
+  for (const auto& pr : cand) {
+    const int bw = pr.first, h = pr.second;
+    const int nt = classic2d_tiles(nx, ny, bw, h);
+    mt.ntiles = nt;
+    if ((e = cudaMemcpyAsync(s->d_mem_tune, &mt, sizeof(Member), cudaMemcpyHostToDevice,
+                             s->st)) != cudaSuccess)
+      break;
+    LaunchArgs a{s->d_mem_tune, nullptr, nt, s->consts.data(), bw, h, 0, s->st};
+    if ((e = s->ks.classic(a)) != cudaSuccess) break;  // warm-up
+    cudaEventRecord(e0, s->st);
+    for (int r = 0; r < 3; ++r) s->ks.classic(a);
+    cudaEventRecord(e1, s->st);
+    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      bb = bw;
+      bh = h;
     }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (e != cudaSuccess) return e;

@@ -8,6 +8,7 @@
 // controller (Sec. 5).
 #pragma once
 
+#include "kernels.h"
 #include "riemann.cuh"
 
 namespace claw {
@@ -34,6 +35,16 @@ struct VecIO<float, 8> {
   __device__ static __forceinline__ void store(float* p, const float (&v)[8]) {
     ((float4*)p)[0] = make_float4(v[0], v[1], v[2], v[3]);
     ((float4*)p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+  }
+};
+template <>
+struct VecIO<float, 4> {
+  __device__ static __forceinline__ void load(const float* p, float (&v)[4]) {
+    const float4 a = __ldg((const float4*)p);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  }
+  __device__ static __forceinline__ void store(float* p, const float (&v)[4]) {
+    ((float4*)p)[0] = make_float4(v[0], v[1], v[2], v[3]);
   }
 };
 template <>
@@ -116,7 +127,7 @@ struct CellPrep<RpElasticity<R, 1>, R> {
 };
 
 template <class RP, typename R, int NT, int K>
-__global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? 7 : 1)
+__global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? 8 : 1)
     classic1d_kernel(const Member* __restrict__ members, const Tile* __restrict__ tiles,
                      int ntiles_total, const MConsts<R> C) {
   constexpr int M = RP::M, MW = RP::MW, MA = RP::MA;
@@ -377,10 +388,14 @@ __global__ void __launch_bounds__(BW)
       continue;
     }
     const int nx = mb.nx, ny = mb.ny;
-    const int nsx = (nx + TX - 1) / TX;
-    const int c0 = (tl.tile % nsx) * TX;
-    const int r0 = (tl.tile / nsx) * H;
-    const int rend = min(r0 + H, ny) - 1;
+    const Classic2dLayout L = classic2d_layout(nx, ny, BW, H);
+    const int c0 = (tl.tile % L.nsx) * TX;
+    const int ch = tl.tile / L.nsx;
+    const int r0 = (int)(((long long)ch * ny) / L.nch);
+    const int rend = (int)(((long long)(ch + 1) * ny) / L.nch) - 1;
+    // a warp whose columns all lie past the second ghost column feeds no
+    // stored cell, speed or flag: it only keeps the block's barriers
+    const bool live = c0 - 2 + (l & ~31) <= nx + 1;
     const int c = c0 - 2 + l;
     const int cload = min(c, nx + 1);
     const bool col_in = (l >= 2) && (l < BW - 2) && (c < nx);
@@ -425,20 +440,22 @@ __global__ void __launch_bounds__(BW)
         qm2[k] = qm1[k];
         qm1[k] = qc[k];
       }
-      load_cell<M, R>(C, q, nx, ny, cload, Rw, RP::WALL_X, RP::WALL_Y, qc);
+      if (live) {
+        load_cell<M, R>(C, q, nx, ny, cload, Rw, RP::WALL_X, RP::WALL_Y, qc);
 #pragma unroll
-      for (int k = 0; k < M; ++k) qs[k][l] = qc[k];
-      if constexpr (RP::NPC > 0) {
+        for (int k = 0; k < M; ++k) qs[k][l] = qc[k];
+        if constexpr (RP::NPC > 0) {
 #pragma unroll
-        for (int k = 0; k < NP; ++k) pm1[k] = pcc[k];
-        RP::cell_pc(C, qc, pcc);
+          for (int k = 0; k < NP; ++k) pm1[k] = pcc[k];
+          RP::cell_pc(C, qc, pcc);
 #pragma unroll
-        for (int k = 0; k < NP; ++k) pcs[k][l] = pcc[k];
+          for (int k = 0; k < NP; ++k) pcs[k][l] = pcc[k];
+        }
       }
 
       // (2) y-interface Rw (rows Rw-1, Rw)
       R nW[MW][M], ns[MW], nam[M], nap[M], nx_[NC], nnrm[MW], ndot[MW];
-      const bool yrow = doy && Rw >= r0 - 1;
+      const bool yrow = live && doy && Rw >= r0 - 1;
       if (yrow) {
         solve_cells<RP, 1, R, NP>(C, qm1, qc, pm1, pcc, nW, ns, nam, nap, nx_);
 #pragma unroll
@@ -461,7 +478,7 @@ __global__ void __launch_bounds__(BW)
       __syncthreads();  // qs ready
 
       // (3) x-interface (c, Rw)
-      const bool xrow = dox && (Rw >= r0 - 1) && (Rw <= rend + 1);
+      const bool xrow = live && dox && (Rw >= r0 - 1) && (Rw <= rend + 1);
       R xW[MW][M], xs[MW], xam[M], xap[M], xx[NC];
       if (xrow && l >= 1) {
         R ql[M], pl[NP];
@@ -551,7 +568,7 @@ __global__ void __launch_bounds__(BW)
       }
 
       // (5) y-limiting of interface Rw-1, corrections, transverse propagation
-      if (doy && ylim && Rw - 1 >= r0 && Rw - 1 <= rend + 1) {
+      if (live && doy && ylim && Rw - 1 >= r0 && Rw - 1 <= rend + 1) {
         R G[M];
         if (C.order == 2) {
           R dot[MW];
@@ -597,29 +614,31 @@ __global__ void __launch_bounds__(BW)
           }
         }
       }
+      if (live) {
 #pragma unroll
-      for (int k = 0; k < M; ++k) {
-        if constexpr (GATHER) {
-          gxv[0][k][l] = gx[0][k];
-          gxv[1][k][l] = gx[1][k];
-          gxv[2][k][l] = gx[2][k];
-          gyv[0][k][l] = gy[0][k];
-          gyv[1][k][l] = gy[1][k];
-          gyv[2][k][l] = gy[2][k];
-          gyv[3][k][l] = gy[3][k];
-        } else {
-          mbl[0][k][l] = tl_[0][k];
-          mbl[1][k][l] = tl_[1][k];
-          mbl[2][k][l] = tl_[2][k];
-          mbl[3][k][l] = tl_[3][k];
-          mbr[0][k][l] = tr_[0][k];
-          mbr[1][k][l] = tr_[1][k];
+        for (int k = 0; k < M; ++k) {
+          if constexpr (GATHER) {
+            gxv[0][k][l] = gx[0][k];
+            gxv[1][k][l] = gx[1][k];
+            gxv[2][k][l] = gx[2][k];
+            gyv[0][k][l] = gy[0][k];
+            gyv[1][k][l] = gy[1][k];
+            gyv[2][k][l] = gy[2][k];
+            gyv[3][k][l] = gy[3][k];
+          } else {
+            mbl[0][k][l] = tl_[0][k];
+            mbl[1][k][l] = tl_[1][k];
+            mbl[2][k][l] = tl_[2][k];
+            mbl[3][k][l] = tl_[3][k];
+            mbr[0][k][l] = tr_[0][k];
+            mbr[1][k][l] = tr_[1][k];
+          }
         }
       }
       __syncthreads();  // mailboxes ready
 
       // (6) gather neighbour contributions, (7) finish row Rw-2
-      if (l + 1 < BW) {
+      if (live && l + 1 < BW) {
 #pragma unroll
         for (int k = 0; k < M; ++k) {
           if constexpr (GATHER) {
@@ -640,7 +659,7 @@ __global__ void __launch_bounds__(BW)
           }
         }
       }
-      if (l >= 1) {
+      if (live && l >= 1) {
 #pragma unroll
         for (int k = 0; k < M; ++k) {
           if constexpr (GATHER) {

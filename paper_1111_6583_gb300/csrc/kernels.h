@@ -48,7 +48,7 @@ struct KernelSet {
 
 // tile geometry shared by the host (tile tables) and the kernels
 constexpr int kClassic1dThreads = 128;
-constexpr int classic1d_K(int prec) { return prec == 0 ? 4 : 8; }  // cells per thread
+constexpr int classic1d_K(int prec) { return prec == 0 ? 4 : 4; }  // cells per thread
 constexpr int classic1d_T(int prec) { return kClassic1dThreads * classic1d_K(prec); }
 inline int classic1d_tiles(int nx, int prec) {
   return (nx + classic1d_T(prec) - 1) / classic1d_T(prec);
@@ -57,9 +57,26 @@ constexpr int kSharpTX2 = 16, kSharpTY2 = 8;  // 2D SharpClaw tile
 constexpr int kSharpTX1 = 128;                // 1D SharpClaw tile
 constexpr int kMaxspeedCells = 256;           // cells per max-speed block
 
+// Tiles of the 2D classic kernel.  A block of BW threads owns a strip of
+// TX = BW - 4 interior columns and a chunk of rows; the ny rows are spread
+// evenly over nch = ceil(ny / H) chunks (no short last chunk).  Tile t is
+// strip t % nsx, chunk t / nsx.  In a narrow last strip the warps that hold
+// only columns past the second ghost column skip all work; its chunks keep
+// the common height, since a tile's time is set by the rows each of its warps
+// walks, not by the number of warps.
+struct Classic2dLayout {
+  int TX, nsx, nch;
+};
+__host__ __device__ inline Classic2dLayout classic2d_layout(int nx, int ny, int BW, int H) {
+  Classic2dLayout L;
+  L.TX = BW - 4;
+  L.nsx = (nx + L.TX - 1) / L.TX;
+  L.nch = (ny + H - 1) / H;
+  return L;
+}
 __host__ __device__ inline int classic2d_tiles(int nx, int ny, int BW, int H) {
-  const int TX = BW - 4;
-  return ((nx + TX - 1) / TX) * ((ny + H - 1) / H);
+  const Classic2dLayout L = classic2d_layout(nx, ny, BW, H);
+  return L.nsx * L.nch;
 }
 __host__ __device__ inline int sharp_tiles(int nx, int ny, int TX, int TY) {
   return ((nx + TX - 1) / TX) * ((ny + TY - 1) / TY);

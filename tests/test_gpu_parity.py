@@ -96,6 +96,32 @@ def test_classic2d_fixed_dt_fp64(orc, rp, order, transverse):
         assert info["cfl"] == pytest.approx(co[-1], rel=1e-13)
 
 
+@pytest.mark.parametrize("rp,nx,ny", [("sw_roe", 131, 70), ("euler_roe", 250, 61),
+                                       ("sw_roe", 372, 33)])
+def test_classic2d_tile_shapes_bitwise(rp, nx, ny):
+    """Every tile shape gives the same bits: narrow last strips whose upper
+    warps sit idle (131 and 250 columns), a last strip exactly full (372 =
+    3 x 124), chunk heights that do not divide the rows (29, 13, 7), one
+    chunk for all rows, and the autotuned shape."""
+    from paper_1111_6583_gb300 import claw
+    spec = _spec2d(rp, nx, ny, order=2, transverse=2)
+    dt = 0.25 / nx
+    out = []
+    for tune in ((128, 32), (128, 29), (64, 13), (128, 7), (64, 128), None):
+        s = claw.Solver(spec, "fp64")
+        if tune is None:
+            s.tune()
+        else:
+            s.tune(*tune)
+        for _ in range(3):
+            s.step(dt)
+        s.sync()
+        out.append(s.q.cpu().numpy())
+        s.close()
+    for k in range(1, len(out)):
+        assert np.array_equal(out[k], out[0]), k
+
+
 @pytest.mark.parametrize("rp", ["sw_roe", "euler_roe", "acoustics", "advection"])
 @pytest.mark.parametrize("bc", ["wall", "extrap"])
 def test_classic2d_boundaries_fp64(orc, rp, bc):
