@@ -64,16 +64,19 @@ def kernel_sha():
     return h.hexdigest()
 
 
-def recorded_traffic():
+def recorded_traffic(tile):
     """DRAM bytes per launch of the headline kernel from the last ncu capture,
-    or None when the kernel sources changed since it was taken."""
+    or None when the kernel sources changed since it was taken or the capture
+    ran another tile shape."""
     if not os.path.exists(TRAFFIC_RECORD):
         return None
     rec = json.load(open(TRAFFIC_RECORD))
-    return rec["dram_bytes_per_launch"] if rec.get("sources_sha256") == kernel_sha() else None
+    if rec.get("sources_sha256") != kernel_sha() or rec.get("tile") != list(tile):
+        return None
+    return rec["dram_bytes_per_launch"]
 
 
-def record_traffic(csv_path):
+def record_traffic(csv_path, tile):
     """Write the traffic record from an ncu --csv launch list of the bench
     command (metrics dram__bytes_read.sum, dram__bytes_write.sum; the last
     four classic2d launches of `--case sw2d1024` are its four steps; ncu
@@ -90,12 +93,14 @@ def record_traffic(csv_path):
             by.setdefault(r[ii], {})[r[mi]] = float(r[vi].replace(",", ""))
     timed = list(by.values())[-4:]
     b = sum(v["dram__bytes_read.sum"] + v["dram__bytes_write.sum"] for v in timed) / len(timed)
+    t = "%d,%d" % tuple(tile)
     rec = {"kernel": "classic2d_kernel<RpSW<double,2>>", "workload": "dam break 1024x1024 FP64",
-           "dram_bytes_per_launch": b, "sources_sha256": kernel_sha(),
-           "command": "python bench.py --case sw2d1024 > gpurun_out/plain.log 2>&1 && "
+           "tile": list(tile), "dram_bytes_per_launch": b, "sources_sha256": kernel_sha(),
+           "command": "python bench.py --case sw2d1024 --tile %s > gpurun_out/plain.log 2>&1 && "
                       "ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,"
                       "dram__bytes_write.sum --clock-control none -k regex:classic2d --csv "
-                      "--log-file gpurun_out/traffic_sw2d.csv python bench.py --case sw2d1024"}
+                      "--log-file gpurun_out/traffic_sw2d.csv python bench.py --case sw2d1024 "
+                      "--tile %s" % (t, t)}
     json.dump(rec, open(TRAFFIC_RECORD, "w"), indent=1)
     print(json.dumps(rec))
 
@@ -518,12 +523,12 @@ def reference_arm(args):
     print(json.dumps(line))
 
 
-def profile_case(case):
+def profile_case(case, tile=None):
     """A short fixed launch sequence of one kernel for ncu captures (untimed):
     sw2d64/sw2d32 -- 2048^2 dam break, autotune (40 launches) then 3 steps;
     elast -- 1024-member FP32 elasticity batch, 5 fused steps;
     sharp -- 1024x512 shock-bubble FP64, 2 SharpClaw steps (6 stage launches);
-    sw2d1024 -- the headline 1024^2 FP64 dam break, autotune then 4 steps;
+    sw2d1024 -- the headline 1024^2 FP64 dam break, autotune (or --tile) then 4 steps;
     axisym -- 1280x320 axisymmetric shock-bubble FP64, tune then 3 steps;
     vc -- 1024^2 varying-medium acoustics with capacity FP64, 3 steps."""
     import torch
@@ -536,7 +541,7 @@ def profile_case(case):
         s.advance(3)
     elif case == "sw2d1024":
         s = claw.Solver(wl.sw_dambreak_2d(n=1024), "fp64")
-        print("tile", s.tune())
+        print("tile", s.tune(*tile) if tile else s.tune())
         s.set_t_end(1.5)
         s.advance(4)
     elif case == "axisym":
@@ -576,17 +581,21 @@ def main():
     ap.add_argument("--members", type=int, default=4096)
     ap.add_argument("--record-traffic", default=None,
                     help="write the headline kernel's traffic record from an ncu csv")
+    ap.add_argument("--tile", default=None,
+                    help="BW,H: fixed 2D tile shape for --case sw2d1024 and --record-traffic")
     ap.add_argument("--case", default=None,
                     help="run one short launch sequence for a profiler (sw2d64, sw2d32, sw2d1024, "
                          "elast, sharp, axisym, vc)")
     args = ap.parse_args()
     if args.record_traffic:
-        record_traffic(args.record_traffic)
+        if not args.tile:
+            raise SystemExit("--record-traffic needs the --tile the capture ran")
+        record_traffic(args.record_traffic, [int(v) for v in args.tile.split(",")])
         return
     if args.case:
         import __graft_entry__
         __graft_entry__.build()
-        profile_case(args.case)
+        profile_case(args.case, [int(v) for v in args.tile.split(",")] if args.tile else None)
         return
     if args.warmup < 3:
         args.warmup = 3
@@ -624,7 +633,7 @@ def main():
         "gpu_launches": args.steps,
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
-                     "traffic": recorded_traffic(),
+                     "traffic": recorded_traffic(shape),
                      "peak_kind": "derived FP64 (152 SM x 2.07 GHz x 4 FLOP/clk)",
                      "hbm_gbs": SW2D_BYTES_PER_CELL["fp64"] * cells / (avg_ms * 1e-3) / 1e9,
                      "hbm_frac": SW2D_BYTES_PER_CELL["fp64"] * cells / (avg_ms * 1e-3) / 1e9 / hbm,

@@ -26,18 +26,6 @@ namespace claw {
 template <typename R, int K>
 struct VecIO;
 template <>
-struct VecIO<float, 8> {
-  __device__ static __forceinline__ void load(const float* p, float (&v)[8]) {
-    const float4 a = __ldg((const float4*)p), b = __ldg((const float4*)p + 1);
-    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-  }
-  __device__ static __forceinline__ void store(float* p, const float (&v)[8]) {
-    ((float4*)p)[0] = make_float4(v[0], v[1], v[2], v[3]);
-    ((float4*)p)[1] = make_float4(v[4], v[5], v[6], v[7]);
-  }
-};
-template <>
 struct VecIO<float, 4> {
   __device__ static __forceinline__ void load(const float* p, float (&v)[4]) {
     const float4 a = __ldg((const float4*)p);

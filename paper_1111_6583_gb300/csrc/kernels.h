@@ -48,7 +48,7 @@ struct KernelSet {
 
 // tile geometry shared by the host (tile tables) and the kernels
 constexpr int kClassic1dThreads = 128;
-constexpr int classic1d_K(int prec) { return prec == 0 ? 4 : 4; }  // cells per thread
+constexpr int classic1d_K(int) { return 4; }  // cells per thread (FP64 and FP32)
 constexpr int classic1d_T(int prec) { return kClassic1dThreads * classic1d_K(prec); }
 inline int classic1d_tiles(int nx, int prec) {
   return (nx + classic1d_T(prec) - 1) / classic1d_T(prec);
