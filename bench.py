@@ -389,15 +389,16 @@ def bench_shockbubble(prec, steps, warmup, nx=2048, ny=1024, weno_order=5,
                            prec.upper())}
 
 
-def bench_axisym(prec, steps, warmup, nx=1280, ny=320, dim_split=0):
+def bench_axisym(prec, steps, warmup, nx=1280, ny=320, dim_split=0, source_split="godunov"):
     """The axisymmetric shock-bubble of Sec. 6.2 at the paper's 1280 x 320:
     Euler + tracer, classic unsplit with full transverse corrections (or
-    dimensionally split), geometric source by Godunov splitting; one step =
-    the step kernel (two when split) + the source kernel + its marker."""
+    dimensionally split), geometric source by Godunov (or Strang) splitting;
+    one step = the step kernel (two when split) + the source kernel (two for
+    Strang) + its marker."""
     import torch
     from paper_1111_6583_gb300 import claw
     from paper_1111_6583_gb300 import workloads as wl
-    spec = wl.shock_bubble_axisym(nx=nx, ny=ny, dim_split=dim_split)
+    spec = wl.shock_bubble_axisym(nx=nx, ny=ny, dim_split=dim_split, source_split=source_split)
     if dim_split:
         spec["transverse"] = 0
     stream = torch.cuda.Stream()
@@ -414,9 +415,9 @@ def bench_axisym(prec, steps, warmup, nx=1280, ny=320, dim_split=0):
     return {"value": nx * ny * len(ms) / (sum(ms) * 1e-3), "unit": UNIT, "ms_per_step": avg,
             "tile": list(tile) if tile else None,
             "workload": "axisymmetric shock-bubble %dx%d, Euler + tracer, classic %s, "
-                        "geometric source (Godunov), %s"
+                        "geometric source (%s), %s"
                         % (nx, ny, "dimensionally split" if dim_split else "unsplit full "
-                           "transverse", prec.upper())}
+                           "transverse", source_split.capitalize(), prec.upper())}
 
 
 def bench_acoustics_vc(prec, steps, warmup, n=1024):
@@ -654,6 +655,8 @@ def main():
         line["psystem_checkerboard"] = {p: bench_psystem(p, 3, 3) for p in ("fp64", "fp32")}
         line["axisym_shock_bubble"] = {p: bench_axisym(p, 20, 3) for p in ("fp64", "fp32")}
         line["axisym_shock_bubble"]["fp64_split"] = bench_axisym("fp64", 20, 3, dim_split=1)
+        line["axisym_shock_bubble"]["fp64_strang"] = bench_axisym("fp64", 20, 3,
+                                                                  source_split="strang")
         line["acoustics_vc_capacity"] = {p: bench_acoustics_vc(p, 10, 3) for p in ("fp64", "fp32")}
         try:
             line["batched_elasticity"] = bench_elasticity(args.members, 100, 16)

@@ -60,12 +60,17 @@ enum { CLAW_CLASSIC = 0, CLAW_SHARPCLAW = 1 };
 enum { CLAW_RP_ADVECTION = 0, CLAW_RP_ACOUSTICS = 1, CLAW_RP_SW_ROE = 2,
        CLAW_RP_EULER_ROE = 3, CLAW_RP_EULER_HLLE = 4, CLAW_RP_ELASTICITY_FWAVE = 5,
        CLAW_RP_EULER_TRACER = 6, CLAW_RP_ACOUSTICS_VC = 7 };
-/* Source terms (Eq. (conslaw) right-hand side), by Godunov splitting after
- * every accepted step: CLAW_SOURCE_AXISYMMETRIC is the geometric source of
- * the Euler equations in cylindrical symmetry about y = 0 (Sec. 6.2:
- * (z, r) = (x, y); -(1/r)(rho v, rho u v, rho v^2, (E + p) v), tracer none),
- * integrated over the step by a two-stage second-order Runge-Kutta method. */
+/* Source terms (Eq. (conslaw) right-hand side) by fractional steps (Sec. 3;
+ * Sec. 6.1 uses Strang's splitting): CLAW_SOURCE_AXISYMMETRIC is the
+ * geometric source of the Euler equations in cylindrical symmetry about
+ * y = 0 (Sec. 6.2: (z, r) = (x, y); -(1/r)(rho v, rho u v, rho v^2,
+ * (E + p) v), tracer none), integrated over each fractional step by a
+ * two-stage second-order Runge-Kutta method.  CLAW_SPLIT_GODUNOV: the source
+ * over dt after every accepted step; CLAW_SPLIT_STRANG: over dt/2 before the
+ * step (into an extra state buffer, so a rejected attempt leaves Q^n as it
+ * was) and over dt/2 after every accepted step. */
 enum { CLAW_SOURCE_NONE = 0, CLAW_SOURCE_AXISYMMETRIC = 1 };
+enum { CLAW_SPLIT_GODUNOV = 1, CLAW_SPLIT_STRANG = 2 };
 enum { CLAW_LIM_NONE = 0, CLAW_LIM_MINMOD = 1, CLAW_LIM_SUPERBEE = 2, CLAW_LIM_VANLEER = 3,
        CLAW_LIM_MC = 4 };
 enum { CLAW_BC_PERIODIC = 0, CLAW_BC_WALL = 1, CLAW_BC_EXTRAP = 2, CLAW_BC_INFLOW = 3 };
@@ -114,6 +119,7 @@ typedef struct {
   int capa_index;      /* -1 (default): no capacity; else the aux field holding the
                           capacity kappa of Eq. (conslaw), which must be the field
                           after the solver's own (num_aux = solver's + 1); 1D/2D   */
+  int source_split;    /* CLAW_SPLIT_GODUNOV (default) | CLAW_SPLIT_STRANG        */
 } claw_method;
 
 typedef struct {

@@ -73,6 +73,7 @@ class _Prob(ctypes.Structure):
         ("dim_split", ctypes.c_int),
         ("lower", ctypes.c_double * 2),
         ("capa_index", ctypes.c_int),
+        ("source_split", ctypes.c_int),
     ]
 
 
@@ -200,6 +201,7 @@ def make_problem(spec: dict):
     p.lower[0] = float(lo[0])
     p.lower[1] = float(lo[1])
     p.capa_index = int(spec.get("capa_index", -1))
+    p.source_split = {"godunov": 1, "strang": 2}[spec.get("source_split", "godunov")]
     return p
 
 

@@ -977,12 +977,24 @@ void orc_source_step(const orc_prob* P, double* q, double dt) {
   }
 }
 
+/* the source before the hyperbolic step: a half step for Strang splitting,
+ * nothing for Godunov */
+static void source_before(const orc_prob* P, double* q, double dt) {
+  if (P->ndim == 2 && P->source_split == 2) orc_source_step(P, q, 0.5 * dt);
+}
+/* the source after an accepted hyperbolic step: the other Strang half step,
+ * or the whole step for Godunov */
+static void source_after(const orc_prob* P, double* q, double dt) {
+  if (P->ndim == 2) orc_source_step(P, q, P->source_split == 2 ? 0.5 * dt : dt);
+}
+
 int orc_classic_step(const orc_prob* P, double* q, const double* aux, double dt, double* cfl) {
   if (P->ndim == 1) return classic1d(P, q, aux, dt, cfl);
   /* the 2D p-system is solved with SharpClaw only (normal solves, Sec. 6.3) */
   if (P->ndim == 2 && P->rp == ORC_RP_ELASTICITY_FWAVE) return ORC_EINVAL;
   if (P->ndim == 3) return classic3d(P, q, dt, cfl);
   int st;
+  source_before(P, q, dt);
   if (P->dim_split) {
     /* Godunov dimensional splitting: x sweeps over dt, then y sweeps over dt */
     double c1, c2;
@@ -992,7 +1004,7 @@ int orc_classic_step(const orc_prob* P, double* q, const double* aux, double dt,
   } else {
     st = classic2d(P, q, aux, dt, cfl, 3);
   }
-  if (st == ORC_OK) orc_source_step(P, q, dt);
+  if (st == ORC_OK) source_after(P, q, dt);
   return st;
 }
 
@@ -1489,11 +1501,12 @@ static double sharp_L_fn(const void* vctx, const double* q, double* L) {
 }
 
 int orc_sharp_step(const orc_prob* P, double* q, const double* aux, double dt, double* cfl) {
+  source_before(P, q, dt);
   if (P->time_integrator == 1) {
     int ny1 = (P->ndim == 2) ? P->ny : 1;
     sharp_ctx c = {P, aux, dt, ORC_OK};
     *cfl = ssp104(sharp_L_fn, &c, (size_t)P->nx * ny1 * P->num_eqn, q, dt);
-    if (c.status == ORC_OK && P->ndim == 2) orc_source_step(P, q, dt);
+    if (c.status == ORC_OK) source_after(P, q, dt);
     return c.status;
   }
   int ny = (P->ndim == 2) ? P->ny : 1;
@@ -1518,7 +1531,7 @@ int orc_sharp_step(const orc_prob* P, double* q, const double* aux, double dt, d
   memcpy(q, qk, sizeof(double) * ntot);
   *cfl = nu;
   free(qn); free(qk); free(L);
-  if (st == ORC_OK && P->ndim == 2) orc_source_step(P, q, dt);
+  if (st == ORC_OK) source_after(P, q, dt);
   return st;
 }
 

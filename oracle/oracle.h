@@ -63,11 +63,14 @@ typedef struct {
    * weno_b[(k*r+a)*r+b] smoothness quadratic forms */
   double weno_c[81], weno_d[9], weno_b[729];
   int source;           /* 0 none; 1 axisymmetric Euler geometric source about y = 0
-                           (r = y; Sec. 6.2), by Godunov splitting after each step */
+                           (r = y; Sec. 6.2), by fractional steps (source_split) */
   int dim_split;        /* classic 2D: 0 unsplit; 1 dimensional splitting (x sweeps,
                            then y sweeps, Godunov) */
   double lower[2];      /* lower corner of the grid (cell centres for the source) */
   int capa_index;       /* aux field holding the capacity kappa (Eq. (conslaw)); -1 none */
+  int source_split;     /* fractional steps for the source (Sec. 3; Sec. 6.1 uses Strang):
+                           1 Godunov, S(dt) after the step; 2 Strang, S(dt/2) before
+                           and after it */
 } orc_prob;
 
 typedef struct {

@@ -25,6 +25,7 @@ CLASSIC, SHARPCLAW = 0, 1
 RP = {"advection": 0, "acoustics": 1, "sw_roe": 2, "euler_roe": 3, "euler_hlle": 4,
       "elasticity_fwave": 5, "euler_tracer": 6, "acoustics_vc": 7}
 SOURCE = {"none": 0, "axisymmetric": 1}
+SOURCE_SPLIT = {"godunov": 1, "strang": 2}
 LIM = {"none": 0, "minmod": 1, "superbee": 2, "vanleer": 3, "mc": 4}
 BC = {"periodic": 0, "wall": 1, "extrap": 2, "inflow": 3}
 TIME_INTEGRATOR = {"ssp_rk3": 0, "ssp104": 1}
@@ -53,7 +54,7 @@ class claw_method(ctypes.Structure):
                 ("params", ctypes.c_double * 8), ("num_eqn", ctypes.c_int),
                 ("num_aux", ctypes.c_int), ("time_integrator", ctypes.c_int),
                 ("source", ctypes.c_int), ("dim_split", ctypes.c_int),
-                ("capa_index", ctypes.c_int)]
+                ("capa_index", ctypes.c_int), ("source_split", ctypes.c_int)]
 
 
 class claw_step_info(ctypes.Structure):
@@ -202,6 +203,7 @@ def method_from_spec(spec, prec="fp64") -> claw_method:
     m.source = SOURCE[spec.get("source", "none")]
     m.dim_split = int(spec.get("dim_split", 0))
     m.capa_index = int(spec.get("capa_index", -1))
+    m.source_split = SOURCE_SPLIT[spec.get("source_split", "godunov")]
     m.num_aux = int(spec.get("num_aux", m.num_aux))
     bl = list(spec.get("bc_lower", ["periodic"] * ndim)) + ["periodic"] * 2
     bh = list(spec.get("bc_upper", ["periodic"] * ndim)) + ["periodic"] * 2

@@ -143,6 +143,8 @@ const char* check_method(const claw_method& m, int nd) {
       !(nd == 2 && (m.rp == CLAW_RP_EULER_ROE || m.rp == CLAW_RP_EULER_HLLE ||
                     m.rp == CLAW_RP_EULER_TRACER)))
     return "the axisymmetric source needs a 2D Euler system";
+  if (m.source_split != CLAW_SPLIT_GODUNOV && m.source_split != CLAW_SPLIT_STRANG)
+    return "source_split must be CLAW_SPLIT_GODUNOV or CLAW_SPLIT_STRANG";
   if (m.dim_split != 0 && m.dim_split != 1) return "dim_split must be 0 or 1";
   if (m.dim_split && !(m.scheme == CLAW_CLASSIC && nd == 2))
     return "dimensional splitting is for the classic 2D scheme";
@@ -193,6 +195,10 @@ int maxspeed_tiles(int nx, int ny) {
 int nbuf_of(const claw_method& m) {
   if (m.scheme == CLAW_CLASSIC) return m.dim_split ? 3 : 2;
   return m.time_integrator == CLAW_SSP104 ? 4 : 3;
+}
+// a Strang-split source needs one more state: Q^n after the first half step
+int pre_buffers(const claw_method& m) {
+  return (m.source != CLAW_SOURCE_NONE && m.source_split == CLAW_SPLIT_STRANG) ? 1 : 0;
 }
 
 DevCtl make_ctl(const claw_method& m, const claw_grid& g, int nbuf, double t0, double t_end) {
@@ -246,10 +252,10 @@ void fill_info(const DevCtl& c, claw_step_info* info) {
   info->status = c.status;
 }
 
-// Launch one attempt (classic: one kernel; SharpClaw: three stage kernels).
 // Launch one attempt: classic, one kernel (two sweeps when dimensionally
-// split); SharpClaw, one kernel per stage; then the source step over the
-// cell tiles (mtiles) when the method has one.
+// split); SharpClaw, one kernel per stage; with a source, its fractional
+// steps over the cell tiles (mtiles): Godunov, after the step; Strang, half
+// before the step (into Member::qpre) and half after it.
 cudaError_t launch_attempt(const KernelSet& ks, const claw_method& m, const Member* mem,
                            const Tile* tiles, int ntiles, const void* consts, int bw, int h,
                            cudaStream_t st, const Tile* mtiles = nullptr, int nmtiles = 0,
@@ -265,6 +271,12 @@ cudaError_t launch_attempt(const KernelSet& ks, const claw_method& m, const Memb
   a.work3 = work3;
   a.work3_bytes = work3_bytes;
   cudaError_t e = cudaSuccess;
+  const bool strang = m.source != CLAW_SOURCE_NONE && m.source_split == CLAW_SPLIT_STRANG;
+  LaunchArgs b{mem, mtiles, nmtiles, consts, 0, 0, 0, st};
+  if (strang) {
+    b.src_phase = 1;  // S(dt/2) Q^n into the pre-source buffer the step reads
+    if ((e = ks.source(b)) != cudaSuccess) return e;
+  }
   if (m.scheme == CLAW_CLASSIC) {
     if (m.dim_split) {
       a.sweep = 1;
@@ -282,7 +294,7 @@ cudaError_t launch_attempt(const KernelSet& ks, const claw_method& m, const Memb
     }
   }
   if (e != cudaSuccess || m.source == CLAW_SOURCE_NONE) return e;
-  LaunchArgs b{mem, mtiles, nmtiles, consts, 0, 0, 0, st};
+  b.src_phase = strang ? 2 : 0;
   if ((e = ks.source(b)) != cudaSuccess) return e;
   return launch_source_mark(mem, nmembers, st);
 }
@@ -430,6 +442,7 @@ cudaError_t autotune(claw_solver* s) {
   if ((e = launch_set_t_end(s->d_ctl_tune, 1, INFINITY, 0, s->st)) != cudaSuccess) return e;
   Member mt = s->h_mem;
   mt.ctl = s->d_ctl_tune;
+  mt.qpre = nullptr;  // trial launches read Q^n itself
   const int nx = (int)s->g.n[0], ny = (int)s->g.n[1];
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
@@ -565,6 +578,7 @@ claw_status claw_method_init(claw_method* m, int rp, int ndim) {
   m->num_eqn = num_eqn(rp, ndim);
   m->num_aux = solver_aux(rp);
   m->capa_index = -1;
+  m->source_split = CLAW_SPLIT_GODUNOV;
   return CLAW_OK;
 }
 
@@ -621,7 +635,8 @@ claw_status claw_bind_state(claw_solver* s, void* q_dev, const void* aux_dev, do
   free_bound(s);
   s->q_user = q_dev;
   s->aux = aux_dev;
-  SCK(cudaMalloc(&s->work, s->sbytes * (s->nbuf - 1)));
+  const int npre = pre_buffers(s->m);
+  SCK(cudaMalloc(&s->work, s->sbytes * (s->nbuf - 1 + npre)));
   if (s->faces) {
     s->work3_bytes = faces_work_bytes(s->nd, (int)s->g.n[0], (int)s->g.n[1], s->m.num_eqn,
                                       s->prec);
@@ -644,6 +659,7 @@ claw_status claw_bind_state(claw_solver* s, void* q_dev, const void* aux_dev, do
   s->h_mem.q[1] = s->work;
   for (int j = 2; j < s->nbuf; ++j)
     s->h_mem.q[j] = (void*)((unsigned char*)s->work + (size_t)(j - 1) * s->sbytes);
+  if (npre) s->h_mem.qpre = (void*)((unsigned char*)s->work + (size_t)(s->nbuf - 1) * s->sbytes);
   s->h_mem.aux = aux_dev;
   s->h_mem.nx = (int)s->g.n[0];
   s->h_mem.ny = (int)s->g.n[1];
@@ -1037,7 +1053,7 @@ claw_status claw_batch_bind(claw_batch* b, void* const* q, const void* const* au
   size_t total = 0;
   for (int k = 0; k < n; ++k) {
     b->sbytes[k] = align256(state_bytes_of(b->m, b->grids[k]));
-    total += b->sbytes[k] * (b->nbuf - 1);
+    total += b->sbytes[k] * (b->nbuf - 1 + pre_buffers(b->m));
   }
   BCK(cudaMalloc(&b->work, total));
   BCK(cudaMalloc(&b->d_ctl, sizeof(DevCtl) * n));
@@ -1055,6 +1071,10 @@ claw_status claw_batch_bind(claw_batch* b, void* const* q, const void* const* au
     mb.q[0] = q[k];
     for (int j = 1; j < b->nbuf; ++j) {
       mb.q[j] = w;
+      w += b->sbytes[k];
+    }
+    if (pre_buffers(b->m)) {
+      mb.qpre = w;
       w += b->sbytes[k];
     }
     mb.aux = aux ? aux[k] : nullptr;

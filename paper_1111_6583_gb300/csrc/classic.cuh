@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(BW)
     const bool xcfl = xlim && (c <= nx);
     const bool ylim = (l >= 1) && (l <= BW - 2);
     const bool dox = sweep != 2, doy = sweep != 1;
-    const R* __restrict__ q = (const R*)mb.q[(s_cur + (sweep == 2 ? 1 : 0)) % s_nbuf];
+    const R* __restrict__ q = (const R*)step_input(mb, s_cur, s_nbuf, sweep == 2 ? 1 : 0);
     R* __restrict__ qo = (R*)mb.q[(s_cur + (sweep == 2 ? 2 : 1)) % s_nbuf];
     const R dtdx = s_k[0], dtdy = s_k[1], kxy = s_k[2];
     const size_t plane = (size_t)nx * ny;

@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(kFacesThreads)
   const int lines = (nd == 2) ? nl + 2 : 1;
   const long long nf = (long long)(n + 1) * lines;
   const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const R* __restrict__ q = (const R*)mb.q[s_cur];
+  const R* __restrict__ q = (const R*)step_input(mb, s_cur, 0, 0);
   const R* __restrict__ aux = (const R*)mb.aux;
   R smax = R(0);
   if (id < nf) {
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kFacesThreads)
   int bad = 0;
   if (id < (long long)nx * ny) {
     const int i = (int)(id % nx), j = (int)(id / nx);
-    const R* __restrict__ q = (const R*)mb.q[s_cur];
+    const R* __restrict__ q = (const R*)step_input(mb, s_cur, s_nbuf, 0);
     R* __restrict__ qo = (R*)mb.q[(s_cur + 1) % s_nbuf];
     const R* __restrict__ aux = (const R*)mb.aux;
     const size_t NX = faces_count(nd, nx, ny, 0), NY = faces_count(nd, nx, ny, 1);

@@ -54,7 +54,16 @@ struct Member {
   int nz;            // 3D: cells in z (1 otherwise)
   DevCtl* ctl;
   void* work3;       // 3D: per-face fluctuation / correction arrays
+  void* qpre;        // Strang-split source: Q^n after the first half source
+                     // step, which the step reads in place of slot cur; else null
 };
+
+// The step's input in slot cur + rel: Q^n, or with a Strang-split source the
+// state after the first half source step.
+__device__ __forceinline__ const void* step_input(const Member& mb, int cur, int nbuf, int rel) {
+  if (rel == 0) return mb.qpre ? mb.qpre : mb.q[cur];
+  return mb.q[(cur + rel) % nbuf];
+}
 
 // One stage of a SharpClaw Runge-Kutta method.  Buffer slots are relative to
 // DevCtl::cur (slot 0 holds Q^n).  With v = Q[in] + g dt L(Q[in]):

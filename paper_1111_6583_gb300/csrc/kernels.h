@@ -28,6 +28,9 @@ struct LaunchArgs {
   const StageOp* stage_op; // SharpClaw: explicit stage (host pointer) or null
   int sweep;               // 2D classic: 0 unsplit, 1 / 2 the x / y sweeps of a split step
   int nmembers;            // members of the table (1D classic runs their controllers after)
+  int src_phase;           // source step: 0 Godunov (dt after an accepted step), 1 Strang
+                           // pre (dt/2 of the attempt, slot cur -> qpre), 2 Strang post
+                           // (dt/2 after an accepted step)
 };
 
 // stage tables of the SharpClaw time integrators

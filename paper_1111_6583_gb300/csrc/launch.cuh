@@ -79,11 +79,11 @@ __global__ void __launch_bounds__(kMaxspeedCells)
 
 inline int launch_grid(int ntiles) { return ntiles < 1 ? 1 : ntiles; }
 
-// Axisymmetric Euler geometric source (Sec. 6.2), Godunov-split after an
-// accepted step: with r = y (cell centre) and v the radial velocity,
-// psi(q) = -(1/r) (rho v, rho u v, rho v^2, (E + p) v, 0 for a tracer), over the
-// step's dt by the two-stage Runge-Kutta method q1 = q + dt psi(q),
-// q <- (q + q1 + dt psi(q1)) / 2.  A member whose accepted-step count equals
+// Axisymmetric Euler geometric source (Sec. 6.2) by fractional steps: with
+// r = y (cell centre) and v the radial velocity,
+// psi(q) = -(1/r) (rho v, rho u v, rho v^2, (E + p) v, 0 for a tracer), over a
+// time h by the two-stage Runge-Kutta method q1 = q + h psi(q),
+// q <- (q + q1 + h psi(q1)) / 2.  A member whose accepted-step count equals
 // its source mark has nothing pending (rejected or skipped attempt).
 template <class RP, typename R>
 __device__ __forceinline__ void axisym_psi(const MConsts<R>& C, const R (&q)[RP::M], R r,
@@ -99,33 +99,39 @@ __device__ __forceinline__ void axisym_psi(const MConsts<R>& C, const R (&q)[RP:
   f[3] = -FM<R>::div((q[3] + p) * v, r);
 }
 
+// The source ODE over one fractional step by Heun's method, cell by cell.
+// phase 0 (Godunov): dt_used in place on the new slot cur, after an accepted
+// step only; phase 1 (Strang, before the step): dt/2 of the attempt from slot
+// cur into Member::qpre, which the step then reads; phase 2 (Strang, after):
+// dt_used/2 in place on the new slot cur, after an accepted step only.
 template <class RP, typename R>
 __global__ void __launch_bounds__(kMaxspeedCells)
     axisym_source_kernel(const Member* __restrict__ members, const Tile* __restrict__ tiles,
-                         int ntiles_total, const MConsts<R> C) {
+                         int ntiles_total, const MConsts<R> C, int phase) {
   constexpr int M = RP::M;
   for (int it = blockIdx.x; it < ntiles_total; it += gridDim.x) {
     const Tile tl = tiles ? tiles[it] : Tile{0, it};
     const Member& mb = members[tl.member];
     const DevCtl* ctl = mb.ctl;
-    if (ctl->steps == ctl->src_mark) continue;
+    if (phase == 1 ? (ctl->done != 0) : (ctl->steps == ctl->src_mark)) continue;
     const int nx = mb.nx, ny = mb.ny;
     const long long cell = (long long)tl.tile * kMaxspeedCells + threadIdx.x;
     if (cell >= (long long)nx * ny) continue;
     const int j = (int)(cell / nx);
-    R* q = (R*)mb.q[ctl->cur];
+    const R* qi = (const R*)mb.q[ctl->cur];
+    R* qo = phase == 1 ? (R*)mb.qpre : (R*)mb.q[ctl->cur];
     const size_t plane = (size_t)nx * ny;
-    const R dt = (R)ctl->dt_used;
+    const R dt = (R)(phase == 1 ? 0.5 * ctl->dt : (phase == 2 ? 0.5 * ctl->dt_used : ctl->dt_used));
     const R r = (R)(ctl->lo[1] + ((double)j + 0.5) * ctl->dx[1]);
     R q0[M], q1[M], f0[M], f1[M];
 #pragma unroll
-    for (int k = 0; k < M; ++k) q0[k] = q[k * plane + cell];
+    for (int k = 0; k < M; ++k) q0[k] = qi[k * plane + cell];
     axisym_psi<RP, R>(C, q0, r, f0);
 #pragma unroll
     for (int k = 0; k < M; ++k) q1[k] = q0[k] + dt * f0[k];
     axisym_psi<RP, R>(C, q1, r, f1);
 #pragma unroll
-    for (int k = 0; k < M; ++k) q[k * plane + cell] = R(0.5) * (q0[k] + (q1[k] + dt * f1[k]));
+    for (int k = 0; k < M; ++k) qo[k * plane + cell] = R(0.5) * (q0[k] + (q1[k] + dt * f1[k]));
   }
 }
 
@@ -247,7 +253,7 @@ struct Launchers {
     const MConsts<R>& C = *(const MConsts<R>*)a.consts;
     if constexpr (ND == 2 && is_euler_rp<RP>::value) {
       axisym_source_kernel<RP, R><<<launch_grid(a.ntiles_total), kMaxspeedCells, 0, a.stream>>>(
-          a.members, a.tiles, a.ntiles_total, C);
+          a.members, a.tiles, a.ntiles_total, C, a.src_phase);
       return cudaGetLastError();
     } else {
       (void)C;

@@ -103,9 +103,9 @@ __global__ void __launch_bounds__(TX * TY)
     const int r0 = (ND == 2) ? (tl.tile / nsx) * TY : 0;
     const int cur = s_cur;
     const int nb = s_nbuf;
-    const R* __restrict__ qk = (const R*)mb.q[(cur + op.in) % nb];
-    const R* __restrict__ qa = (const R*)mb.q[(cur + op.sa) % nb];
-    const R* __restrict__ qb = (const R*)mb.q[(cur + op.sb) % nb];
+    const R* __restrict__ qk = (const R*)step_input(mb, cur, nb, op.in);
+    const R* __restrict__ qa = (const R*)step_input(mb, cur, nb, op.sa);
+    const R* __restrict__ qb = (const R*)step_input(mb, cur, nb, op.sb);
     R* __restrict__ qo = (R*)mb.q[(cur + op.out) % nb];
     R* __restrict__ qo2 = op.out2 >= 0 ? (R*)mb.q[(cur + op.out2) % nb] : nullptr;
     const R* __restrict__ aux = (const R*)mb.aux;

@@ -137,11 +137,11 @@ def post_shock_state_from_pressure(p2, gamma=1.4, rho1=1.0, p1=1.0):
 
 
 def shock_bubble_axisym(nx=1280, ny=320, t_end=0.6, scheme="classic", gamma=1.4, sub=16,
-                        dim_split=0, cfl=(0.8, 1.0)):
+                        dim_split=0, cfl=(0.8, 1.0), source_split="godunov"):
     """The shock-bubble interaction of Sec. 6.2 in its axisymmetric form:
     (z, r) = (x, y) on [0, 2] x [0, 0.5], Euler with a passive tracer and the
     geometric source -(1/r)(rho v, rho u v, rho v^2, (E + p) v) by Godunov
-    splitting.  Ahead of the shock rho = p = 1 at rest; a sphere of rho = 0.1
+    (or Strang) splitting.  Ahead of the shock rho = p = 1 at rest; a sphere of rho = 0.1
     (p = 1), radius 0.2, centred on the axis at z = 0.5, carries tracer 1
     (cell fractions from a sub x sub point sample); the shock at z = 0.2 has
     the paper's post-shock pressure 5 (rho and u by Rankine-Hugoniot, about
@@ -169,7 +169,8 @@ def shock_bubble_axisym(nx=1280, ny=320, t_end=0.6, scheme="classic", gamma=1.4,
     tracer = np.where(left, 0.0, frac)
     q0 = np.stack([rho, mx, np.zeros_like(rho), E, tracer])
     spec = _base(2, [nx, ny], [0.0, 0.0], [2.0, 0.5], "euler_tracer", scheme=scheme,
-                 params=[gamma], source="axisymmetric", dim_split=dim_split,
+                 params=[gamma], source="axisymmetric", source_split=source_split,
+                 dim_split=dim_split,
                  bc_lower=["inflow", "wall"], bc_upper=["extrap", "extrap"],
                  inflow=[rho2, rho2 * u2, 0.0, E2, 0.0], cfl_desired=cfl[0], cfl_max=cfl[1])
     spec.update(q0=np.ascontiguousarray(q0), aux=None, t_end=t_end)

@@ -100,4 +100,14 @@ def test_method_init_and_validation_without_gpu(lib_path):
     assert lib.claw_solver_create(ctypes.byref(m), ctypes.byref(g), None,
                                   ctypes.byref(h)) == claw.CLAW_EINVAL
     assert b"too few cells" in lib.claw_last_error(None)
+    # source splitting: Godunov by default, Strang on request, nothing else
+    lib.claw_method_init(ctypes.byref(m), claw.RP["euler_tracer"], 2)
+    assert m.source_split == claw.SOURCE_SPLIT["godunov"]
+    m.source = claw.SOURCE["axisymmetric"]
+    m.source_split = 3
+    g.ndim = 2
+    g.n[0] = g.n[1] = 64
+    assert lib.claw_solver_create(ctypes.byref(m), ctypes.byref(g), None,
+                                  ctypes.byref(h)) == claw.CLAW_EINVAL
+    assert b"source_split" in lib.claw_last_error(None)
     assert lib.claw_version().startswith(b"clawgpu")

@@ -127,3 +127,88 @@ def test_server_rejects_source_terms():
     sp = wl.shock_bubble_axisym(nx=64, ny=16, t_end=0.01, sub=2)
     with pytest.raises(claw.ClawError):
         claw.Server(sp, "fp64", budget_bytes=1 << 26, max_slots=2)
+
+
+# --------------------------------------------------------------------------
+# Strang splitting of the source: half before the step, half after it
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("dim_split", [0, 1])
+def test_strang_axisymmetric_shock_bubble(orc, dim_split):
+    spec = wl.shock_bubble_axisym(nx=160, ny=40, t_end=0.1, sub=4, dim_split=dim_split,
+                                  source_split="strang")
+    if dim_split:
+        spec["transverse"] = 0
+    qo, io = oracle_evolve(orc, spec, 0.1)
+    assert io["status"] == "ok"
+    for graph in (True, False):
+        qg, ig = gpu_evolve(spec, "fp64", 0.1, use_graph=graph)
+        assert ig["status"] == 0 and ig["steps"] == io["steps"] and ig["t"] == 0.1
+        assert rel_maxnorm(qg, qo) <= FP64_TOL
+    q32, i32 = gpu_evolve(spec, "fp32", 0.1)
+    assert i32["status"] == 0 and rel_l1(q32, qo) <= FP32_SHOCK_L1_TOL
+
+
+def test_strang_fixed_dt_differs_from_godunov(orc):
+    """Fixed steps, long enough for the shock to reach the bubble (before
+    that the radial momentum is at rounding level and a per-field relative
+    norm means nothing): each splitting matches its own oracle run, and the
+    two differ (the source is active)."""
+    out = {}
+    for split in ("godunov", "strang"):
+        spec = wl.shock_bubble_axisym(nx=96, ny=24, t_end=0.05, sub=4, source_split=split)
+        dt = 0.2 / 96
+        qo, co = oracle_fixed_steps(orc, spec, dt, 40)
+        qg, cg = gpu_fixed_steps(spec, "fp64", dt, 40)
+        assert rel_maxnorm(qg, qo) <= FP64_TOL
+        assert np.allclose(cg, co, rtol=1e-13, atol=0)
+        out[split] = qg
+    assert np.abs(out["godunov"] - out["strang"]).max() > 1e-3
+
+
+def test_strang_rejected_attempt_keeps_qn(orc):
+    """A first dt far above the stable one: the rejected attempt has already
+    written the half-source state, but into its own buffer, so the retry
+    starts from Q^n (steps, rejects and state as the oracle's)."""
+    spec = wl.shock_bubble_axisym(nx=80, ny=20, t_end=0.05, sub=4, source_split="strang")
+    spec["dt_initial"] = 0.02
+    qo, io = oracle_evolve(orc, spec, 0.05)
+    for graph in (True, False):
+        qg, ig = gpu_evolve(spec, "fp64", 0.05, use_graph=graph)
+        assert io["rejects"] >= 1 and ig["rejects"] == io["rejects"]
+        assert ig["steps"] == io["steps"]
+        assert rel_maxnorm(qg, qo) <= FP64_TOL
+
+
+@pytest.mark.parametrize("integrator", ["ssp_rk3", "ssp104"])
+def test_strang_sharpclaw(orc, integrator):
+    """SharpClaw stages read the half-source state wherever they read Q^n
+    (run until the shock has reached the bubble, so that every field is well
+    above rounding level)."""
+    spec = wl.shock_bubble_axisym(nx=96, ny=24, t_end=0.06, sub=4, scheme="sharpclaw",
+                                  source_split="strang")
+    spec.update(char_decomp=1, time_integrator=integrator, cfl_desired=0.5, cfl_max=0.6)
+    qo, io = oracle_evolve(orc, spec, 0.06)
+    qg, ig = gpu_evolve(spec, "fp64", 0.06)
+    assert ig["status"] == 0 and ig["steps"] == io["steps"]
+    assert rel_maxnorm(qg, qo) <= FP64_TOL
+
+
+def test_strang_batch_equals_alone(orc):
+    import torch
+    from paper_1111_6583_gb300 import claw
+    specs = [wl.shock_bubble_axisym(nx=nx, ny=ny, t_end=t, sub=4, source_split="strang")
+             for nx, ny, t in ((80, 20, 0.07), (120, 30, 0.06))]
+    b = claw.Batch(specs, "fp64")
+    infos = b.evolve()
+    torch.cuda.synchronize()
+    for k, sp in enumerate(specs):
+        s = claw.Solver(sp, "fp64")
+        ia = s.evolve(sp["t_end"])
+        qa = s.q.double().cpu().numpy()
+        s.close()
+        assert infos[k]["steps"] == ia["steps"] and infos[k]["t"] == sp["t_end"]
+        assert np.array_equal(qa, b.q[k].double().cpu().numpy())
+        if k == 0:
+            qo, io = oracle_evolve(orc, sp, sp["t_end"])
+            assert io["steps"] == ia["steps"] and rel_maxnorm(qa, qo) <= FP64_TOL
+    b.close()

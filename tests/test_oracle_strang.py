@@ -1,0 +1,98 @@
+"""Pins for the source term by Strang splitting (Sec. 3 operator splitting;
+Sec. 6.1 uses Strang's method): half a source step, the hyperbolic step,
+half a source step.
+
+Pinned by orders of accuracy and controller behaviour, not by the oracle's
+composition: on a smooth axisymmetric Euler flow with the second-order
+(unlimited) classic scheme, grid and step refined together, Strang splitting
+converges at second order while Godunov splitting (a whole source step
+after the hyperbolic step) stays first order; without a source the choice
+changes nothing; a rejected attempt leaves the state where it was (the
+pre-step half source is undone), so a run that rejects its first step
+equals a run started at the retried step.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1111_6583_gb300 import workloads as wl
+
+
+def _smooth_axisym(split, n, source="axisymmetric"):
+    """(z, r) on [0, 1] x [1, 2], periodic in z, extrapolation in r; a smooth
+    subsonic flow with a radial velocity (the source is active everywhere)."""
+    x = (np.arange(n) + 0.5) / n
+    y = 1.0 + (np.arange(n) + 0.5) / n
+    X, Y = np.meshgrid(x, y, indexing="xy")
+    g = 1.4
+    rho = 1.0 + 0.2 * np.sin(2 * np.pi * X) * np.cos(np.pi * (Y - 1.5))
+    u = 0.2 + 0.1 * np.cos(2 * np.pi * X)
+    v = 0.5 + 0.1 * np.sin(2 * np.pi * X)
+    p = 1.0 + 0.1 * np.cos(2 * np.pi * X)
+    E = p / (g - 1) + 0.5 * rho * (u * u + v * v)
+    sp = wl._base(2, [n, n], [0.0, 1.0], [1.0, 2.0], "euler_roe", params=[g], lim="none",
+                  source=source, source_split=split,
+                  bc_lower=["periodic", "extrap"], bc_upper=["periodic", "extrap"])
+    sp.update(q0=np.ascontiguousarray(np.stack([rho, rho * u, rho * v, E])), aux=None)
+    return sp
+
+
+def _run(split, n, T=0.1):
+    sp = _smooth_axisym(split, n)
+    P = oracle.make_problem(sp)
+    q = sp["q0"]
+    nsteps = int(round(2 * T * n))  # Courant number about 0.9
+    for _ in range(nsteps):
+        q, _ = oracle.step(P, q, None, T / nsteps)
+    return q
+
+
+def _coarsen(q, f):
+    m, ny, nx = q.shape
+    return q.reshape(m, ny // f, f, nx // f, f).mean(axis=(2, 4))
+
+
+def test_strang_second_order_godunov_first_order():
+    nref = 256
+    ref = _run("strang", nref)
+    ratios = {}
+    for split in ("godunov", "strang"):
+        err = []
+        for n in (32, 64):
+            d = np.abs(_run(split, n) - _coarsen(ref, nref // n))
+            # rows r in [1.3, 1.7]: the extrapolated r-boundaries stay out of reach
+            err.append(d[:, int(0.3 * n):int(0.7 * n), :].mean())
+        ratios[split] = err[0] / err[1]
+    assert ratios["strang"] > 3.4, ratios
+    assert ratios["godunov"] < 3.0, ratios
+
+
+def test_split_choice_is_inert_without_source():
+    sa = _smooth_axisym("godunov", 32, source="none")
+    sb = _smooth_axisym("strang", 32, source="none")
+    Pa, Pb = oracle.make_problem(sa), oracle.make_problem(sb)
+    qa, qb = sa["q0"], sb["q0"]
+    for _ in range(4):
+        qa, _ = oracle.step(Pa, qa, None, 0.01)
+        qb, _ = oracle.step(Pb, qb, None, 0.01)
+    assert np.array_equal(qa, qb)
+
+
+@pytest.mark.parametrize("scheme", ["classic", "sharpclaw"])
+def test_strang_reject_and_retry(scheme):
+    """The first attempt (dt far above the stable one) is rejected: the state
+    it restarts from is Q^n, not Q^n after the first half source step."""
+    sp = wl.shock_bubble_axisym(nx=64, ny=16, t_end=0.03, sub=2, scheme=scheme,
+                                source_split="strang")
+    if scheme == "sharpclaw":
+        sp.update(cfl_desired=0.5, cfl_max=0.6, char_decomp=0)
+    P = oracle.make_problem(dict(sp, dt_initial=0.02))
+    qa, ia = oracle.evolve(P, sp["q0"], t_end=0.03, max_steps=1)
+    assert ia["rejects"] == 1 and ia["steps"] == 1 and ia["status"] == "ok"
+    # the retried step: dt = 0.02 * cfl_desired / nu of the rejected attempt
+    qr, nu = oracle.step(oracle.make_problem(sp), sp["q0"], None, 0.02)
+    dt2 = 0.02 * sp["cfl_desired"] / nu
+    qb, ib = oracle.evolve(oracle.make_problem(dict(sp, dt_initial=dt2)), sp["q0"], t_end=0.03,
+                           max_steps=1)
+    assert ib["rejects"] == 0 and ib["steps"] == 1
+    assert np.array_equal(qa, qb)
