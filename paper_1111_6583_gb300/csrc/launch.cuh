@@ -85,18 +85,20 @@ inline int launch_grid(int ntiles) { return ntiles < 1 ? 1 : ntiles; }
 // time h by the two-stage Runge-Kutta method q1 = q + h psi(q),
 // q <- (q + q1 + h psi(q1)) / 2.  A member whose accepted-step count equals
 // its source mark has nothing pending (rejected or skipped attempt).
+// psi from the conserved variables with one reciprocal of rho (ir = 1/r is
+// the caller's): rho v = q2, rho u v = q1 v, rho v^2 = q2 v.
 template <class RP, typename R>
-__device__ __forceinline__ void axisym_psi(const MConsts<R>& C, const R (&q)[RP::M], R r,
+__device__ __forceinline__ void axisym_psi(const MConsts<R>& C, const R (&q)[RP::M], R ir,
                                            R (&f)[RP::M]) {
-  const R rho = q[0], u = FM<R>::div(q[1], rho), v = FM<R>::div(q[2], rho);
-  const R ke = q[1] * q[1] + q[2] * q[2];
-  const R p = C.gm1 * (q[3] - R(0.5) * ke / rho);
+  const R irho = R(1) / q[0];
+  const R v = q[2] * irho;
+  const R p = C.gm1 * (q[3] - R(0.5) * ((q[1] * q[1] + q[2] * q[2]) * irho));
 #pragma unroll
   for (int k = 0; k < RP::M; ++k) f[k] = R(0);
-  f[0] = -FM<R>::div(rho * v, r);
-  f[1] = -FM<R>::div(rho * u * v, r);
-  f[2] = -FM<R>::div(rho * v * v, r);
-  f[3] = -FM<R>::div((q[3] + p) * v, r);
+  f[0] = -(q[2] * ir);
+  f[1] = -((q[1] * v) * ir);
+  f[2] = -((q[2] * v) * ir);
+  f[3] = -(((q[3] + p) * v) * ir);
 }
 
 // The source ODE over one fractional step by Heun's method, cell by cell.
@@ -122,14 +124,14 @@ __global__ void __launch_bounds__(kMaxspeedCells)
     R* qo = phase == 1 ? (R*)mb.qpre : (R*)mb.q[ctl->cur];
     const size_t plane = (size_t)nx * ny;
     const R dt = (R)(phase == 1 ? 0.5 * ctl->dt : (phase == 2 ? 0.5 * ctl->dt_used : ctl->dt_used));
-    const R r = (R)(ctl->lo[1] + ((double)j + 0.5) * ctl->dx[1]);
+    const R ir = R(1) / (R)(ctl->lo[1] + ((double)j + 0.5) * ctl->dx[1]);
     R q0[M], q1[M], f0[M], f1[M];
 #pragma unroll
     for (int k = 0; k < M; ++k) q0[k] = qi[k * plane + cell];
-    axisym_psi<RP, R>(C, q0, r, f0);
+    axisym_psi<RP, R>(C, q0, ir, f0);
 #pragma unroll
     for (int k = 0; k < M; ++k) q1[k] = q0[k] + dt * f0[k];
-    axisym_psi<RP, R>(C, q1, r, f1);
+    axisym_psi<RP, R>(C, q1, ir, f1);
 #pragma unroll
     for (int k = 0; k < M; ++k) qo[k * plane + cell] = R(0.5) * (q0[k] + (q1[k] + dt * f1[k]));
   }
