@@ -41,6 +41,72 @@ __device__ __forceinline__ R weno5(R a, R b, R c, R d, R e, R eps) {
   return FM<R>::div(w0 * q0 + w1 * q1 + w2 * q2, w0 + w1 + w2);
 }
 
+// Both Jiang-Shu WENO5 values at the interface between cells c and d of the
+// six cell averages a..f: the left-biased one at the right edge of c (um)
+// and the right-biased one at the left edge of d (up), as numerator and
+// denominator.  The two use the same candidates from stencils (b, c, d) and
+// (c, d, e) and the same second differences of those stencils, computed
+// once here; candidates are kept times 6 (the 6 moves to the denominator).
+template <typename R>
+__device__ __forceinline__ void weno5_pair(R a, R b, R c, R d, R e, R f, R eps, R& nm, R& dm,
+                                           R& np, R& dp) {
+  const R p0 = R(2) * a - R(7) * b + R(11) * c;   // (a, b, c) at the right edge of c
+  const R p1 = R(2) * d + R(5) * c - b;           // (b, c, d) at the c|d edge
+  const R p2 = R(2) * c + R(5) * d - e;           // (c, d, e) at the c|d edge
+  const R p3 = R(2) * f - R(7) * e + R(11) * d;   // (d, e, f) at the left edge of d
+  const R k13 = R(13) / R(12);
+  const R t0 = a - R(2) * b + c, t1 = b - R(2) * c + d, t2 = c - R(2) * d + e,
+          t3 = d - R(2) * e + f;
+  const R h0 = k13 * (t0 * t0), h1 = k13 * (t1 * t1), h2 = k13 * (t2 * t2),
+          h3 = k13 * (t3 * t3);
+  const R u0 = a - R(4) * b + R(3) * c, u1 = b - d, u2 = R(3) * c - R(4) * d + e;
+  const R v0 = f - R(4) * e + R(3) * d, v1 = e - c, v2 = R(3) * d - R(4) * c + b;
+  const R e0 = eps + (h0 + R(0.25) * (u0 * u0)), e1 = eps + (h1 + R(0.25) * (u1 * u1)),
+          e2 = eps + (h2 + R(0.25) * (u2 * u2));
+  const R g0 = eps + (h3 + R(0.25) * (v0 * v0)), g1 = eps + (h2 + R(0.25) * (v1 * v1)),
+          g2 = eps + (h1 + R(0.25) * (v2 * v2));
+  // alpha_k = d_k / beta_k^2 multiplied through by the product of the three
+  const R s0 = e0 * e0, s1 = e1 * e1, s2 = e2 * e2;
+  const R w0 = R(0.1) * (s1 * s2), w1 = R(0.6) * (s0 * s2), w2 = R(0.3) * (s0 * s1);
+  nm = w0 * p0 + w1 * p1 + w2 * p2;
+  dm = R(6) * (w0 + w1 + w2);
+  const R z0 = g0 * g0, z1 = g1 * g1, z2 = g2 * g2;
+  const R y0 = R(0.1) * (z1 * z2), y1 = R(0.6) * (z0 * z2), y2 = R(0.3) * (z0 * z1);
+  np = y0 * p3 + y1 * p2 + y2 * p1;
+  dp = R(6) * (y0 + y1 + y2);
+}
+
+// n / d for N pairs.  In FP64 with one division: 1/d_i = (prod_{j<i} d_j)
+// (prod_{j>i} d_j) / prod_j d_j, taken only when every partial product is a
+// positive normal number (no overflow, underflow or lost precision), else N
+// divisions.
+template <typename R, int N>
+__device__ __forceinline__ void div_many(const R (&n)[N], const R (&d)[N], R (&q)[N]) {
+  if constexpr (sizeof(R) == 8 && N > 1) {
+    R pre[N];
+    R prod = d[0];
+    bool normal = pos_normal(prod);
+    pre[0] = R(1);
+#pragma unroll
+    for (int i = 1; i < N; ++i) {
+      pre[i] = prod;
+      prod = prod * d[i];
+      normal = normal && pos_normal(prod);
+    }
+    if (normal) {
+      R suf = FM<R>::rcp(prod);
+#pragma unroll
+      for (int i = N - 1; i >= 0; --i) {
+        q[i] = n[i] * (i == 0 ? suf : suf * pre[i]);
+        suf = suf * d[i];
+      }
+      return;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < N; ++i) q[i] = FM<R>::div(n[i], d[i]);
+}
+
 // WENO of order 2 RW - 1: left-biased value at the right edge of cell
 // v[o + RW - 1] from v[o .. o + 2 RW - 2] (REV: the mirrored stencil, value at
 // the left edge of cell v[o + RW], read from v[o + 2 RW - 1] downwards).
@@ -174,13 +240,27 @@ __global__ void __launch_bounds__(TX * TY)
             for (int k6 = 0; k6 < NS; ++k6) RP::template to_char<1>(C, x, cell[k6], w[k6]);
           }
           R um[M], up[M];
+          if constexpr (RW == 3) {
+            R nn[2 * M], dd[2 * M], vv[2 * M];
 #pragma unroll
-          for (int k = 0; k < M; ++k) {
-            R line[NS];
+            for (int k = 0; k < M; ++k)
+              weno5_pair<R>(w[0][k], w[1][k], w[2][k], w[3][k], w[4][k], w[5][k], C.weno_eps,
+                            nn[k], dd[k], nn[M + k], dd[M + k]);
+            div_many<R, 2 * M>(nn, dd, vv);
 #pragma unroll
-            for (int k6 = 0; k6 < NS; ++k6) line[k6] = w[k6][k];
-            um[k] = weno_edge<RW, false>(line, C.weno_eps);
-            up[k] = weno_edge<RW, true>(line, C.weno_eps);
+            for (int k = 0; k < M; ++k) {
+              um[k] = vv[k];
+              up[k] = vv[M + k];
+            }
+          } else {
+#pragma unroll
+            for (int k = 0; k < M; ++k) {
+              R line[NS];
+#pragma unroll
+              for (int k6 = 0; k6 < NS; ++k6) line[k6] = w[k6][k];
+              um[k] = weno_edge<RW, false>(line, C.weno_eps);
+              up[k] = weno_edge<RW, true>(line, C.weno_eps);
+            }
           }
           if (dir == 0) {
             RP::template from_char<0>(C, x, um, wm);
@@ -188,6 +268,18 @@ __global__ void __launch_bounds__(TX * TY)
           } else {
             RP::template from_char<1>(C, x, um, wm);
             RP::template from_char<1>(C, x, up, wp);
+          }
+        } else if constexpr (RW == 3) {
+          R nn[2 * M], dd[2 * M], vv[2 * M];
+#pragma unroll
+          for (int k = 0; k < M; ++k)
+            weno5_pair<R>(cell[0][k], cell[1][k], cell[2][k], cell[3][k], cell[4][k], cell[5][k],
+                          C.weno_eps, nn[k], dd[k], nn[M + k], dd[M + k]);
+          div_many<R, 2 * M>(nn, dd, vv);
+#pragma unroll
+          for (int k = 0; k < M; ++k) {
+            wm[k] = vv[k];
+            wp[k] = vv[M + k];
           }
         } else {
 #pragma unroll
