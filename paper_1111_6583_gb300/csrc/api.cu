@@ -212,6 +212,7 @@ DevCtl make_ctl(const claw_method& m, const claw_grid& g, int nbuf, double t0, d
   c.dx[0] = (g.upper[0] - g.lower[0]) / (double)g.n[0];
   c.dx[1] = g.ndim >= 2 ? (g.upper[1] - g.lower[1]) / (double)g.n[1] : 1.0;
   c.dx[2] = g.ndim == 3 ? (g.upper[2] - g.lower[2]) / (double)g.n[2] : 1.0;
+  for (int d = 0; d < 3; ++d) c.idx[d] = 1.0 / c.dx[d];
   c.dt_init = m.dt_initial;
   c.max_steps = LLONG_MAX;
   c.nbuf = nbuf;

@@ -132,7 +132,10 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? 8 : 1)
     DevCtl* ctl = mb.ctl;
     if (threadIdx.x == 0) {
       s_done = ctl->done;
-      s_dtdx = (R)(ctl->dt / ctl->dx[0]);
+      // FP32: one multiply by the stored 1/dx (an FP64 division here would
+      // hold every thread of the block at the barrier below)
+      if constexpr (sizeof(R) == 4) s_dtdx = (R)(ctl->dt * ctl->idx[0]);
+      else s_dtdx = ctl->dt / ctl->dx[0];
       s_cur = ctl->cur;
       s_nbuf = ctl->nbuf;
     }

@@ -25,6 +25,7 @@ struct DevCtl {
   double cfl_desired, cfl_max;
   double nu_last, nu_max_seen, dt_used;
   double dx[3];
+  double idx[3];    // 1 / dx
   double lo[3];     // lower corner of the grid (cell centres for source terms)
   double dt_init;   // first dt (<= 0: from the wave speeds of Q^0)
   unsigned long long smax[3];  // bit patterns of max |s| per direction (non-negative)

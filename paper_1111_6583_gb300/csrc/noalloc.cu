@@ -162,6 +162,8 @@ claw_status claw_sharp_step_noalloc(const claw_method* m, const claw_grid* g, co
   c.cfl_max = INFINITY;
   c.dx[0] = (g->upper[0] - g->lower[0]) / (double)nx;
   c.dx[1] = g->ndim == 2 ? (g->upper[1] - g->lower[1]) / (double)ny : 1.0;
+  c.dx[2] = 1.0;
+  for (int d = 0; d < 3; ++d) c.idx[d] = 1.0 / c.dx[d];
   c.max_steps = 0x7fffffffffffffffLL;
   c.nbuf = 3;
   c.accept_shift = 1;
