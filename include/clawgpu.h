@@ -189,8 +189,9 @@ claw_status claw_current_state(claw_solver* s, void** q_cur);
 /* Copy the current state into q_dev if it lives in a work buffer. */
 claw_status claw_sync_state(claw_solver* s);
 
-/* Conserved totals (sum_i Q_i) * dV per field, FP64 with compensated
- * summation, into host out[num_eqn] (synchronises). */
+/* Conserved totals (sum_i kappa_i Q_i) * dV per field (kappa = 1 without a
+ * capacity field), FP64 with compensated summation, into host
+ * out[num_eqn] (synchronises). */
 claw_status claw_conserved_totals(claw_solver* s, double* out);
 
 /* Checkpoint: state + controller into a host buffer.  With host_buf NULL,

@@ -814,7 +814,13 @@ claw_status claw_conserved_totals(claw_solver* s, double* out) {
   const void* q = s->h_mem.q[s->h_ctl->cur];
   const long long ncell = (long long)cells_of(s->g);
   const int M = s->m.num_eqn;
-  SCK(launch_totals(q, s->prec, ncell, M, s->d_part, s->npart, s->st));
+  // capacity-form differencing conserves sum_i kappa_i Q_i
+  const void* kappa =
+      s->m.capa_index >= 0
+          ? (const void*)((const unsigned char*)s->aux +
+                          (size_t)s->m.capa_index * ncell * (s->prec == CLAW_FP64 ? 8 : 4))
+          : nullptr;
+  SCK(launch_totals(q, kappa, s->prec, ncell, M, s->d_part, s->npart, s->st));
   SCK(cudaMemcpyAsync(s->h_part, s->d_part, sizeof(double) * 2 * s->npart * M,
                       cudaMemcpyDeviceToHost, s->st));
   SCK(cudaStreamSynchronize(s->st));

@@ -77,12 +77,13 @@ __device__ __forceinline__ void two_sum_add(double& s, double& c, double s2, dou
 
 template <typename R>
 __global__ void __launch_bounds__(kTotalsThreads)
-    totals_kernel(const R* __restrict__ q, long long ncell, double* partials) {
+    totals_kernel(const R* __restrict__ q, const R* __restrict__ kappa, long long ncell,
+                  double* partials) {
   const R* f = q + (size_t)blockIdx.y * ncell;
   double s = 0.0, c = 0.0;
   for (long long i = (long long)blockIdx.x * kTotalsThreads + threadIdx.x; i < ncell;
        i += (long long)gridDim.x * kTotalsThreads) {
-    const double x = (double)f[i];
+    const double x = kappa ? (double)f[i] * (double)kappa[i] : (double)f[i];
     const double t = s + x;
     if (fabs(s) >= fabs(x)) c += (s - t) + x;
     else c += (x - t) + s;
@@ -211,11 +212,15 @@ cudaError_t launch_count_active(const DevCtl* ctls, int n, int* out, cudaStream_
   count_active_kernel<<<1, 256, 0, st>>>(ctls, n, out);
   return cudaGetLastError();
 }
-cudaError_t launch_totals(const void* q, int prec, long long ncell, int m, double* partials,
-                          int nblocks, cudaStream_t st) {
+cudaError_t launch_totals(const void* q, const void* kappa, int prec, long long ncell, int m,
+                          double* partials, int nblocks, cudaStream_t st) {
   dim3 grid(nblocks, m);
-  if (prec == 0) totals_kernel<double><<<grid, kTotalsThreads, 0, st>>>((const double*)q, ncell, partials);
-  else totals_kernel<float><<<grid, kTotalsThreads, 0, st>>>((const float*)q, ncell, partials);
+  if (prec == 0)
+    totals_kernel<double><<<grid, kTotalsThreads, 0, st>>>((const double*)q, (const double*)kappa,
+                                                           ncell, partials);
+  else
+    totals_kernel<float><<<grid, kTotalsThreads, 0, st>>>((const float*)q, (const float*)kappa,
+                                                          ncell, partials);
   return cudaGetLastError();
 }
 

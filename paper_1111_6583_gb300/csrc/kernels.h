@@ -112,8 +112,8 @@ cudaError_t launch_set_t_end(DevCtl* ctls, int n, double t_end, long long max_st
                              cudaStream_t st);
 cudaError_t launch_force_dt(DevCtl* ctl, double dt, cudaStream_t st);
 cudaError_t launch_count_active(const DevCtl* ctls, int n, int* out, cudaStream_t st);
-cudaError_t launch_totals(const void* q, int prec, long long ncell, int m, double* partials,
-                          int nblocks, cudaStream_t st);
+cudaError_t launch_totals(const void* q, const void* kappa, int prec, long long ncell, int m,
+                          double* partials, int nblocks, cudaStream_t st);
 cudaError_t launch_reset_cur(DevCtl* ctl, cudaStream_t st);
 cudaError_t launch_gather_ctl(const Member* members, int n, DevCtl* out, cudaStream_t st);
 cudaError_t launch_set_dry(DevCtl* ctl, int dry, cudaStream_t st);

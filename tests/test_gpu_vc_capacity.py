@@ -114,3 +114,35 @@ def test_batches_reject_the_per_face_path():
     spec = wl.random_smooth_2d("acoustics_vc", 32, 32, capa_index=2)
     with pytest.raises(claw.ClawError):
         claw.Batch([spec, spec], "fp64")
+
+
+@pytest.mark.parametrize("ndim,scheme", [(1, "classic"), (2, "classic"), (2, "sharpclaw")])
+def test_conserved_totals_weight_the_capacity(ndim, scheme):
+    """claw_conserved_totals returns (sum_i kappa_i Q_i) dV: equal to the sum
+    formed here from the initial data, and unchanged by periodic steps
+    (shallow water, a conservation law, with a varying capacity)."""
+    import torch
+    from paper_1111_6583_gb300 import claw
+    if ndim == 1:
+        spec = wl.random_1d("sw_roe", 150, scheme=scheme, char_decomp=0)
+        x = (np.arange(150) + 0.5) / 150
+        kap = (1.0 + 0.4 * np.sin(2 * np.pi * x))[None]
+    else:
+        spec = wl.random_smooth_2d("sw_roe", 48, 36, scheme=scheme, char_decomp=0)
+        X, Y = np.meshgrid((np.arange(48) + 0.5) / 48, (np.arange(36) + 0.5) / 36, indexing="xy")
+        kap = (1.0 + 0.4 * np.sin(2 * np.pi * X) * np.cos(2 * np.pi * Y))[None]
+    spec.update(num_aux=1, capa_index=0, aux=np.ascontiguousarray(kap))
+    dV = np.prod([(spec["upper"][d] - spec["lower"][d]) / spec["n"][d] for d in range(ndim)])
+    q0 = spec["q0"]
+    want = (q0 * spec["aux"][0]).reshape(q0.shape[0], -1).sum(axis=1) * dV
+    s = claw.Solver(spec, "fp64")
+    t0 = np.array(s.totals())
+    assert np.allclose(t0, want, rtol=1e-14, atol=1e-14 * np.abs(want).max())
+    for _ in range(6):
+        s.step(0.3 / spec["n"][0])
+    s.sync()
+    torch.cuda.synchronize()
+    t1 = np.array(s.totals())
+    scale = (np.abs(q0) * spec["aux"][0]).reshape(q0.shape[0], -1).sum(axis=1).max() * dV
+    assert np.abs(t1 - t0).max() <= 1e-12 * scale
+    s.close()
