@@ -19,28 +19,6 @@
 
 namespace claw {
 
-// Jiang-Shu WENO5: value at the right edge of the centre cell of a, b, c, d, e
-// (cell averages v_{i-2..i+2}).  The nonlinear weights d_k/(eps+beta_k)^2 are
-// normalised with one division.
-template <typename R>
-__device__ __forceinline__ R weno5(R a, R b, R c, R d, R e, R eps) {
-  const R sixth = R(1) / R(6);
-  const R q0 = (R(2) * a - R(7) * b + R(11) * c) * sixth;
-  const R q1 = (-b + R(5) * c + R(2) * d) * sixth;
-  const R q2 = (R(2) * c + R(5) * d - e) * sixth;
-  const R t0 = a - R(2) * b + c, u0 = a - R(4) * b + R(3) * c;
-  const R t1 = b - R(2) * c + d, u1 = b - d;
-  const R t2 = c - R(2) * d + e, u2 = R(3) * c - R(4) * d + e;
-  const R k13 = R(13) / R(12);
-  const R e0 = eps + (k13 * (t0 * t0) + R(0.25) * (u0 * u0));
-  const R e1 = eps + (k13 * (t1 * t1) + R(0.25) * (u1 * u1));
-  const R e2 = eps + (k13 * (t2 * t2) + R(0.25) * (u2 * u2));
-  const R s0 = e0 * e0, s1 = e1 * e1, s2 = e2 * e2;
-  // alpha_k = d_k / s_k; multiply through by s0 s1 s2
-  const R w0 = R(0.1) * (s1 * s2), w1 = R(0.6) * (s0 * s2), w2 = R(0.3) * (s0 * s1);
-  return FM<R>::div(w0 * q0 + w1 * q1 + w2 * q2, w0 + w1 + w2);
-}
-
 // Both Jiang-Shu WENO5 values at the interface between cells c and d of the
 // six cell averages a..f: the left-biased one at the right edge of c (um)
 // and the right-biased one at the left edge of d (up), as numerator and
@@ -107,7 +85,7 @@ __device__ __forceinline__ void div_many(const R (&n)[N], const R (&d)[N], R (&q
   for (int i = 0; i < N; ++i) q[i] = FM<R>::div(n[i], d[i]);
 }
 
-// WENO of order 2 RW - 1: left-biased value at the right edge of cell
+// WENO of order 2 RW - 1 (7 or 9; WENO5 takes weno5_pair): left-biased value at the right edge of cell
 // v[o + RW - 1] from v[o .. o + 2 RW - 2] (REV: the mirrored stencil, value at
 // the left edge of cell v[o + RW], read from v[o + 2 RW - 1] downwards).
 template <int RW, bool REV, typename R, int NV>
@@ -116,8 +94,7 @@ __device__ __forceinline__ R weno_edge(const R (&w)[NV], R eps) {
   R v[n];
 #pragma unroll
   for (int j = 0; j < n; ++j) v[j] = REV ? w[n - j] : w[j];
-  if constexpr (RW == 3) return weno5<R>(v[0], v[1], v[2], v[3], v[4], eps);
-  else if constexpr (RW == 4) return weno7<R>(v, eps);
+  if constexpr (RW == 4) return weno7<R>(v, eps);
   else return weno9<R>(v, eps);
 }
 
