@@ -38,12 +38,11 @@ __global__ void __launch_bounds__(kFacesThreads)
   const Member& mb = members[0];
   DevCtl* ctl = mb.ctl;
   __shared__ int s_done, s_cur;
-  __shared__ double s_dt, s_dx;
+  __shared__ R s_dtdn;
   if (threadIdx.x == 0) {
     s_done = ctl->done;
     s_cur = ctl->cur;
-    s_dt = ctl->dt;
-    s_dx = ctl->dx[D];
+    s_dtdn = (R)(ctl->dt / ctl->dx[D]);
   }
   __syncthreads();
   if (s_done) return;
@@ -58,7 +57,7 @@ __global__ void __launch_bounds__(kFacesThreads)
   if (id < nf) {
     const int f = (int)(id % (n + 1));
     const int l = (nd == 2) ? (int)(id / (n + 1)) - 1 : 0;
-    const R dtdn = (R)(s_dt / s_dx);
+    const R dtdn = s_dtdn;
     R cell[4][M], au[4][MAS];
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
@@ -67,10 +66,13 @@ __global__ void __launch_bounds__(kFacesThreads)
       load_cell<M, R>(C, q, nx, ny, i, j, RP::WALL_X, RP::WALL_Y, cell[t]);
       if (MA > 0) load_aux<MA, R>(C, aux, nx, ny, i, j, au[t]);
     }
-    R kl = R(1), kr = R(1);
+    // 1/kappa of the face's two cells (one reciprocal each; every capacity
+    // scaling below multiplies by them)
+    R ikl = R(1), ikr = R(1);
     if (C.capa >= 0) {
-      kl = load_aux_field<R>(C, aux, nx, ny, D == 0 ? f - 1 : l, D == 0 ? l : f - 1, C.capa);
-      kr = load_aux_field<R>(C, aux, nx, ny, D == 0 ? f : l, D == 0 ? l : f, C.capa);
+      ikl = FM<R>::rcp(
+          load_aux_field<R>(C, aux, nx, ny, D == 0 ? f - 1 : l, D == 0 ? l : f - 1, C.capa));
+      ikr = FM<R>::rcp(load_aux_field<R>(C, aux, nx, ny, D == 0 ? f : l, D == 0 ? l : f, C.capa));
     }
     R W[3][MW][M], s[3][MW], am[M], ap[M], x[NC], amx[M], apx[M], xx[NC];
     RP::template solve<D>(C, cell[0], cell[1], au[0], au[1], W[0], s[0], amx, apx, xx);
@@ -82,8 +84,7 @@ __global__ void __launch_bounds__(kFacesThreads)
       for (int p = 0; p < MW; ++p) {
         const R sp = s[1][p];
         const R a = C.capa < 0 ? (R)fabs(sp)
-                               : (gt0(sp) ? FM<R>::div(sp, kr)
-                                          : (lt0(sp) ? FM<R>::div(-sp, kl) : R(0)));
+                               : (gt0(sp) ? sp * ikr : (lt0(sp) ? -sp * ikl : R(0)));
         smax = nanmax(smax, a);
       }
     }
@@ -103,8 +104,7 @@ __global__ void __launch_bounds__(kFacesThreads)
         dot[p] = dd;
         nrm[p] = n2;
       }
-      const R dtc = C.capa < 0 ? dtdn
-                               : R(0.5) * (FM<R>::div(dtdn, kl) + FM<R>::div(dtdn, kr));
+      const R dtc = C.capa < 0 ? dtdn : R(0.5) * (dtdn * ikl + dtdn * ikr);
       correction<RP, R, D>(C, W[1], s[1], dot, nrm, dtc, F);
     } else {
 #pragma unroll
@@ -147,10 +147,10 @@ __global__ void __launch_bounds__(kFacesThreads)
       if (C.capa >= 0) {
 #pragma unroll
         for (int k = 0; k < M; ++k) {
-          bma[k] = FM<R>::div(bma[k], kr);
-          bpa[k] = FM<R>::div(bpa[k], kr);
-          bmb[k] = FM<R>::div(bmb[k], kl);
-          bpb[k] = FM<R>::div(bpb[k], kl);
+          bma[k] *= ikr;
+          bpa[k] *= ikr;
+          bmb[k] *= ikl;
+          bpb[k] *= ikl;
         }
       }
     }
@@ -175,14 +175,13 @@ __global__ void __launch_bounds__(kFacesThreads)
   const Member& mb = members[0];
   DevCtl* ctl = mb.ctl;
   __shared__ int s_done, s_cur, s_nbuf;
-  __shared__ double s_dt, s_dx[2];
+  __shared__ R s_dtd[2];  // dt/dx, dt/dy
   if (threadIdx.x == 0) {
     s_done = ctl->done;
     s_cur = ctl->cur;
     s_nbuf = ctl->nbuf;
-    s_dt = ctl->dt;
-    s_dx[0] = ctl->dx[0];
-    s_dx[1] = ctl->dx[1];
+    s_dtd[0] = (R)(ctl->dt / ctl->dx[0]);
+    s_dtd[1] = nd == 2 ? (R)(ctl->dt / ctl->dx[1]) : R(0);
   }
   __syncthreads();
   if (s_done) return;
@@ -197,12 +196,12 @@ __global__ void __launch_bounds__(kFacesThreads)
     const size_t NX = faces_count(nd, nx, ny, 0), NY = faces_count(nd, nx, ny, 1);
     const R* X = (const R*)mb.work3;
     const R* Y = X + 7 * (size_t)M * NX;
-    const R dtdx = (R)(s_dt / s_dx[0]), dtdy = nd == 2 ? (R)(s_dt / s_dx[1]) : R(0);
+    const R dtdx = s_dtd[0], dtdy = s_dtd[1];
     R cx = dtdx, cy = dtdy;
     if (C.capa >= 0) {
-      const R kap = load_aux_field<R>(C, aux, nx, ny, i, j, C.capa);
-      cx = FM<R>::div(dtdx, kap);
-      cy = FM<R>::div(dtdy, kap);
+      const R ik = FM<R>::rcp(load_aux_field<R>(C, aux, nx, ny, i, j, C.capa));
+      cx = dtdx * ik;
+      cy = dtdy * ik;
     }
     // x-face (a, row r) and y-face (b, column c) record indices
     auto xf = [&](int a, int r) -> size_t {

@@ -971,8 +971,12 @@ struct RpAcousticsVC {
     const R Zm = am_[0] * am_[1], Zc = ac[0] * ac[1], Zp = ap_[0] * ap_[1];
 #pragma unroll
     for (int k = 0; k < M; ++k) bm[k] = bp[k] = R(0);
-    const R b1 = FM<R>::div(-a[0] + Zc * a[t], Zm + Zc);
-    const R b2 = FM<R>::div(a[0] + Zc * a[t], Zc + Zp);
+    // one reciprocal for both impedance sums (positive, of the media's scale,
+    // so their product stays in range)
+    const R sm = Zm + Zc, sp = Zc + Zp;
+    const R inv = FM<R>::rcp(sm * sp);
+    const R b1 = (-a[0] + Zc * a[t]) * (sp * inv);
+    const R b2 = (a[0] + Zc * a[t]) * (sm * inv);
     bm[0] = am_[1] * b1 * Zm;
     bm[t] = -am_[1] * b1;
     bp[0] = ap_[1] * b2 * Zp;
