@@ -4,8 +4,9 @@
 // ghost-cell remap in the loads, Riemann solve at every interface, wave
 // limiting, second-order corrections (Eq. (lwflux)), transverse corrections in
 // 2D (Sec. 3.1; LeVeque 1997), conservative update (Eq. (fluxdiff)) and the
-// per-block maximum wave speed; the last block of a member runs the CFL
-// controller (Sec. 5).
+// maximum wave speed.  In 2D the last block of a member to finish runs the
+// CFL controller (Sec. 5); in 1D each warp folds its speed into the control
+// block by atomics and a controller launch follows the step kernel.
 #pragma once
 
 #include "kernels.h"
@@ -13,15 +14,14 @@
 
 namespace claw {
 
-
 // ---------------------------------------------------------------------------
 // 1D: each thread owns K consecutive cells.  It loads them (16-byte vector
 // loads when the fields are aligned) plus two ghost/halo cells on each side,
 // prepares each cell once (CellPrep: the per-cell part of the Riemann solve),
 // then streams through its K + 3 interfaces with a three-interface register
 // window: solve interface j, limit interface j-1 with its neighbours, fold the
-// correction into the fluctuations and emit cell j-3.  No shared memory and no
-// barriers until the block's speed reduction.
+// correction into the fluctuations and emit cell j-3.  No shared memory but
+// the control values thread 0 reads for the tile (two barriers per tile).
 // ---------------------------------------------------------------------------
 template <typename R, int K>
 struct VecIO;

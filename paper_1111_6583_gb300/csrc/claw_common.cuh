@@ -16,9 +16,9 @@ namespace claw {
 
 // ---------------------------------------------------------------------------
 // Per-grid controller state, resident in device memory.  Kernels read dt/cur
-// at their start; the last block of an attempt runs the controller, which
-// writes the next dt/cur.  Stream order makes the update visible to the next
-// launch.
+// at their start; the last block of an attempt (or, for the 1D row kernel, a
+// controller launch after it) runs the controller, which writes the next
+// dt/cur.  Stream order makes the update visible to the next launch.
 // ---------------------------------------------------------------------------
 struct DevCtl {
   double t, dt, t_end, dt_max;
