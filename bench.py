@@ -443,6 +443,35 @@ def bench_acoustics_vc(prec, steps, warmup, n=1024):
                         "transverse (per-face path), %s" % (n, n, prec.upper())}
 
 
+def bench_acoustics_table1(prec, steps, warmup, nd, n):
+    """The paper's Table 1 acoustics system, constant medium: 2D on n^2 (row
+    kernel, autotuned tiles) or 3D on n^3 (a memset, three face sweeps with
+    transverse and double-transverse terms, the update)."""
+    import torch
+    from paper_1111_6583_gb300 import claw
+    from paper_1111_6583_gb300 import workloads as wl
+    spec = wl.acoustics_2d(n=n) if nd == 2 else wl.acoustics_3d(n=n)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = claw.Solver(spec, prec, stream=stream.cuda_stream)
+        tile = s.tune() if nd == 2 else None
+        s.set_t_end(spec["t_end"])
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        s.advance(warmup)
+    stream.synchronize()
+    ms = timed_steps(s, stream, steps, flush)
+    s.close()
+    avg = sum(ms) / len(ms)
+    cells = n ** nd
+    out = {"value": cells * len(ms) / (sum(ms) * 1e-3), "unit": UNIT, "ms_per_step": avg,
+           "workload": "%dD acoustics, constant medium %s, classic MC full transverse%s, %s"
+                       % (nd, "x".join([str(n)] * nd),
+                          " + double transverse" if nd == 3 else "", prec.upper())}
+    if tile:
+        out["tile"] = list(tile)
+    return out
+
+
 def bench_psystem(prec, steps, warmup, periods=32, cells_per_period=64):
     """2D p-system in the checkerboard medium (Sec. 6.3), SharpClaw WENO5
     component-wise + SSP(10,4): one step = ten fused stage launches."""
@@ -531,7 +560,8 @@ def profile_case(case, tile=None):
     sharp -- 1024x512 shock-bubble FP64, 2 SharpClaw steps (6 stage launches);
     sw2d1024 -- the headline 1024^2 FP64 dam break, autotune (or --tile) then 4 steps;
     axisym -- 1280x320 axisymmetric shock-bubble FP64, tune then 3 steps;
-    vc -- 1024^2 varying-medium acoustics with capacity FP64, 3 steps."""
+    vc -- 1024^2 varying-medium acoustics with capacity FP64, 3 steps;
+    acou3d -- 256^3 constant-medium acoustics FP64, 3 steps."""
     import torch
     from paper_1111_6583_gb300 import claw
     from paper_1111_6583_gb300 import workloads as wl
@@ -549,6 +579,11 @@ def profile_case(case, tile=None):
         sp = wl.shock_bubble_axisym()
         s = claw.Solver(sp, "fp64")
         print("tile", s.tune())
+        s.set_t_end(sp["t_end"])
+        s.advance(3)
+    elif case == "acou3d":
+        sp = wl.acoustics_3d(n=256)
+        s = claw.Solver(sp, "fp64")
         s.set_t_end(sp["t_end"])
         s.advance(3)
     elif case == "vc":
@@ -586,7 +621,7 @@ def main():
                     help="BW,H: fixed 2D tile shape for --case sw2d1024 and --record-traffic")
     ap.add_argument("--case", default=None,
                     help="run one short launch sequence for a profiler (sw2d64, sw2d32, sw2d1024, "
-                         "elast, sharp, axisym, vc)")
+                         "elast, sharp, axisym, vc, acou3d)")
     args = ap.parse_args()
     if args.record_traffic:
         if not args.tile:
@@ -657,6 +692,10 @@ def main():
         line["axisym_shock_bubble"]["fp64_split"] = bench_axisym("fp64", 20, 3, dim_split=1)
         line["axisym_shock_bubble"]["fp64_strang"] = bench_axisym("fp64", 20, 3,
                                                                   source_split="strang")
+        line["acoustics_table1"] = {
+            "2d_" + p: bench_acoustics_table1(p, 20, 3, 2, 1024) for p in ("fp64", "fp32")}
+        line["acoustics_table1"].update({
+            "3d_" + p: bench_acoustics_table1(p, 5, 3, 3, 256) for p in ("fp64", "fp32")})
         line["acoustics_vc_capacity"] = {p: bench_acoustics_vc(p, 10, 3) for p in ("fp64", "fp32")}
         try:
             line["batched_elasticity"] = bench_elasticity(args.members, 100, 16)

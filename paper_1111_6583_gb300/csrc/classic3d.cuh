@@ -132,6 +132,23 @@ __device__ __forceinline__ void add_fc(R* __restrict__ work, const Faces3& L, in
   for (int c = 0; c < M; ++c) atomicAdd(base + c, coef * v[c]);
 }
 
+// add coef * v to the correction flux of a face this thread alone updates in
+// the current launch (a plain read-modify-write; earlier launches' sums are
+// already in place by stream order)
+template <int M, typename R>
+__device__ __forceinline__ void add_fc_own(R* __restrict__ work, const Faces3& L, int e, int nx,
+                                           int ny, int nz, const int (&f)[3], const R (&v)[M]) {
+  const int n3[3] = {nx, ny, nz};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int hi = (d == e) ? n3[d] : n3[d] - 1;
+    if (f[d] < 0 || f[d] > hi) return;
+  }
+  R* base = work + L.off_fc[e] + face_index<R>(e, nx, ny, f) * M;
+#pragma unroll
+  for (int c = 0; c < M; ++c) base[c] += v[c];
+}
+
 template <class RP, typename R, int D>
 __global__ void __launch_bounds__(256)
     classic3d_sweep(const Member* __restrict__ members, const MConsts<R> C) {
@@ -156,9 +173,17 @@ __global__ void __launch_bounds__(256)
   const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   R smax = R(0);
   if (id < total) {
-    const int i = (int)(id % (nd + 1));
-    const int a = (int)((id / (nd + 1)) % (ne1 + 2)) - 1;
-    const int b = (int)(id / ((long long)(nd + 1) * (ne1 + 2))) - 1;
+    // x varies fastest across threads in every sweep (coalesced loads and
+    // face-array updates); coordinates along D run 0..nd, across it -1..n
+    int ext[3], v[3];
+    ext[D] = nd + 1;
+    ext[E1] = ne1 + 2;
+    ext[E2] = ne2 + 2;
+    const long long q01 = (long long)ext[0] * ext[1];
+    v[0] = (int)(id % ext[0]);
+    v[1] = (int)((id / ext[0]) % ext[1]);
+    v[2] = (int)(id / q01);
+    const int i = v[D], a = v[E1] - 1, b = v[E2] - 1;
     const R* __restrict__ q = (const R*)mb.q[s_cur];
     R* __restrict__ work = (R*)mb.work3;
     Faces3 L;
@@ -219,7 +244,8 @@ __global__ void __launch_bounds__(256)
         work[L.off_am[D] + fi * M + c] = am[c];
         work[L.off_ap[D] + fi * M + c] = ap[c];
       }
-      add_fc<M, R>(work, L, D, nx, ny, nz, f, R(1), F);
+      // within this sweep only this thread touches the D-face's correction
+      add_fc_own<M, R>(work, L, D, nx, ny, nz, f, F);
     }
     if (C.transverse) {
       R apq[M], amq[M];
@@ -235,6 +261,11 @@ __global__ void __launch_bounds__(256)
         c0[D] = side == 0 ? i : i - 1;
         c0[E1] = a;
         c0[E2] = b;
+        // the four transverse faces of c0 (lower / upper in E1 and E2) take
+        // two pieces each: summed here, one update per face
+        R lo1[M], hi1[M], lo2[M], hi2[M];
+#pragma unroll
+        for (int c = 0; c < M; ++c) lo1[c] = hi1[c] = lo2[c] = hi2[c] = R(0);
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
           // transverse direction e and third direction g
@@ -242,31 +273,47 @@ __global__ void __launch_bounds__(256)
           if (t == 0) Trans3<RP, R, E1>::split(C, av, em, ep);
           else Trans3<RP, R, E2>::split(C, av, em, ep);
           const int e = t == 0 ? E1 : E2;
-          int fu[3] = {c0[0], c0[1], c0[2]};
-          fu[e] = c0[e] + 1;
-          add_fc<M, R>(work, L, e, nx, ny, nz, fu, R(-0.5) * dtdn, ep);
-          add_fc<M, R>(work, L, e, nx, ny, nz, c0, R(-0.5) * dtdn, em);
+          const int g = t == 0 ? E2 : E1;
+          R(&elo)[M] = t == 0 ? lo1 : lo2;
+          R(&ehi)[M] = t == 0 ? hi1 : hi2;
+          R(&glo)[M] = t == 0 ? lo2 : lo1;
+          R(&ghi)[M] = t == 0 ? hi2 : hi1;
+          const R h = R(-0.5) * dtdn;
+#pragma unroll
+          for (int c = 0; c < M; ++c) {
+            ehi[c] += h * ep[c];
+            elo[c] += h * em[c];
+          }
           const R dte = s_k[e];
 #pragma unroll
           for (int sg = 0; sg < 2; ++sg) {
             const R(&bv)[M] = sg == 0 ? ep : em;
             const R k6 = (sg == 0 ? R(1) : R(-1)) * dtdn * dte * (R(1) / R(6));
             R gm[M], gp[M];
-            const int g = t == 0 ? E2 : E1;
             if (t == 0) Trans3<RP, R, E2>::split(C, bv, gm, gp);
             else Trans3<RP, R, E1>::split(C, bv, gm, gp);
+#pragma unroll
+            for (int c = 0; c < M; ++c) {
+              ghi[c] += k6 * gp[c];
+              glo[c] += k6 * gm[c];
+            }
+            // the g-faces of the cell the piece moved on to, c0 +- e
             int c2[3] = {c0[0], c0[1], c0[2]};
             c2[e] += sg == 0 ? 1 : -1;
-            int fu1[3] = {c0[0], c0[1], c0[2]};
-            fu1[g] = c0[g] + 1;
-            add_fc<M, R>(work, L, g, nx, ny, nz, fu1, k6, gp);
-            add_fc<M, R>(work, L, g, nx, ny, nz, c0, k6, gm);
             int fu2[3] = {c2[0], c2[1], c2[2]};
             fu2[g] = c2[g] + 1;
             add_fc<M, R>(work, L, g, nx, ny, nz, fu2, -k6, gp);
             add_fc<M, R>(work, L, g, nx, ny, nz, c2, -k6, gm);
           }
         }
+        int u1[3] = {c0[0], c0[1], c0[2]};
+        u1[E1] = c0[E1] + 1;
+        int u2[3] = {c0[0], c0[1], c0[2]};
+        u2[E2] = c0[E2] + 1;
+        add_fc<M, R>(work, L, E1, nx, ny, nz, u1, R(1), hi1);
+        add_fc<M, R>(work, L, E1, nx, ny, nz, c0, R(1), lo1);
+        add_fc<M, R>(work, L, E2, nx, ny, nz, u2, R(1), hi2);
+        add_fc<M, R>(work, L, E2, nx, ny, nz, c0, R(1), lo2);
       }
     }
   }

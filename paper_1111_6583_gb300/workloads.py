@@ -59,6 +59,40 @@ def acoustics_1d(n=2000, t_end=2.0, lim="mc"):
 
 
 # --------------------------------------------------------------------------
+# 2D and 3D linear acoustics, constant medium (Table 1 acoustics workload)
+# --------------------------------------------------------------------------
+def acoustics_2d(n=1024, t_end=0.5, lim="mc"):
+    """[-1,1]^2, rho = 1, K = 4 (c = 2), p0 = exp(-100 r^2) + 1 on the square
+    [0.3,0.5]^2, u0 = v0 = 0, walls, MC limiter, full transverse corrections,
+    CFL 0.9."""
+    x = _centers(-1.0, 1.0, n)
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    sq = ((X >= 0.3) & (X <= 0.5) & (Y >= 0.3) & (Y <= 0.5)).astype(np.float64)
+    p = np.exp(-100.0 * (X * X + Y * Y)) + sq
+    z = np.zeros_like(p)
+    spec = _base(2, [n, n], [-1.0, -1.0], [1.0, 1.0], "acoustics", lim=lim, params=[1.0, 4.0],
+                 bc_lower=["wall", "wall"], bc_upper=["wall", "wall"])
+    spec.update(q0=np.ascontiguousarray(np.stack([p, z, z])), aux=None, t_end=t_end)
+    return spec
+
+
+def acoustics_3d(n=256, t_end=0.25, lim="mc"):
+    """The 3D form on [-1,1]^3: same medium, p0 = exp(-100 r^2) + 1 on the
+    cube [0.3,0.5]^3, zero velocity, walls, MC, transverse and
+    double-transverse corrections, CFL 0.9."""
+    x = _centers(-1.0, 1.0, n)
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    cube = ((X >= 0.3) & (X <= 0.5) & (Y >= 0.3) & (Y <= 0.5) & (Z >= 0.3) &
+            (Z <= 0.5)).astype(np.float64)
+    p = np.exp(-100.0 * (X * X + Y * Y + Z * Z)) + cube
+    z = np.zeros_like(p)
+    spec = _base(3, [n, n, n], [-1.0] * 3, [1.0] * 3, "acoustics", lim=lim, params=[1.0, 4.0],
+                 bc_lower=["wall"] * 3, bc_upper=["wall"] * 3)
+    spec.update(q0=np.ascontiguousarray(np.stack([p, z, z, z])), aux=None, t_end=t_end)
+    return spec
+
+
+# --------------------------------------------------------------------------
 # 2D shallow-water radial dam break (Table 1 shallow-water workload)
 # --------------------------------------------------------------------------
 def sw_dambreak_2d(n=1024, t_end=1.5, transverse=2, lim="mc"):

@@ -7,7 +7,8 @@ oracle finishes a few steps of these sizes in seconds).
 - 2D Euler shock-bubble, 2048 x 1024, SharpClaw WENO5-char + SSP-RK3, FP64 and FP32;
 - axisymmetric shock-bubble, 1280 x 320, classic + source, FP64;
 - the 4096-member FP32 elasticity ensemble (90.7 M cells, one batch), sampled
-  members compared with the oracle run of that member alone.
+  members compared with the oracle run of that member alone;
+- the Table 1 acoustics system: 2D at 1024^2, 3D at 64^3.
 FP32 runs are compared with the FP64 oracle (L1 where the data have jumps).
 """
 import numpy as np
@@ -91,3 +92,28 @@ def test_elasticity_ensemble_4096_sampled(orc):
         assert infos[k]["steps"] == io["steps"] == 30
         assert rel_maxnorm(q[k].double().cpu().numpy(), qo) <= FP32_SMOOTH_TOL, k
     b.close()
+
+
+@pytest.mark.parametrize("nd,n,steps", [(2, 1024, 6), (3, 64, 4)])
+def test_table1_acoustics(orc, nd, n, steps):
+    """The paper's Table 1 acoustics system in the bench's configuration: 2D at
+    the bench size, 3D at 64^3 (the oracle's 3D step is slow at 256^3)."""
+    spec = wl.acoustics_2d(n=n) if nd == 2 else wl.acoustics_3d(n=n)
+    qo, io = oracle_evolve(orc, spec, spec["t_end"], max_steps=steps)
+    run = _gpu_steps if nd == 2 else _gpu_steps_untuned
+    qg, ig = run(spec, "fp64", spec["t_end"], steps)
+    assert ig["status"] == 0 and ig["steps"] == io["steps"] == steps
+    assert rel_maxnorm(qg, qo) <= FP64_TOL
+    q32, i32 = run(spec, "fp32", spec["t_end"], steps)
+    assert i32["status"] == 0 and rel_l1(q32, qo) <= FP32_SHOCK_L1_TOL
+
+
+def _gpu_steps_untuned(spec, prec, t_end, steps):
+    import torch
+    from paper_1111_6583_gb300 import claw
+    s = claw.Solver(spec, prec)
+    info = s.evolve(t_end, max_steps=steps, use_graph=True)
+    torch.cuda.synchronize()
+    q = s.q.double().cpu().numpy()
+    s.close()
+    return q, info
