@@ -79,6 +79,23 @@ __global__ void __launch_bounds__(kMaxspeedCells)
 
 inline int launch_grid(int ntiles) { return ntiles < 1 ? 1 : ntiles; }
 
+// Persistent grid: no more blocks than fit on the GPU at once (SMs x resident
+// blocks per SM of this kernel); each block walks the tile table with a
+// grid stride.  Queried once per kernel (one instantiation per kernel).
+template <auto Kern>
+inline int persistent_grid(int threads, int ntiles) {
+  static int cap = 0;
+  if (cap == 0) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, Kern, threads, 0);
+    cap = sms * (per > 0 ? per : 1);
+    if (cap < 1) cap = 1;
+  }
+  return ntiles < 1 ? 1 : (ntiles < cap ? ntiles : cap);
+}
+
 // Axisymmetric Euler geometric source (Sec. 6.2) by fractional steps: with
 // r = y (cell centre) and v the radial velocity,
 // psi(q) = -(1/r) (rho v, rho u v, rho v^2, (E + p) v, 0 for a tracer), over a
@@ -195,9 +212,9 @@ struct Launchers {
       return cudaErrorNotSupported;
     } else if constexpr (ND == 1) {
       constexpr int K = sizeof(R) == 8 ? classic1d_K(0) : classic1d_K(1);
-      classic1d_kernel<RP, R, kClassic1dThreads, K>
-          <<<launch_grid(a.ntiles_total), kClassic1dThreads, 0, a.stream>>>(a.members, a.tiles,
-                                                                         a.ntiles_total, C);
+      constexpr auto kern = classic1d_kernel<RP, R, kClassic1dThreads, K>;
+      kern<<<persistent_grid<kern>(kClassic1dThreads, a.ntiles_total), kClassic1dThreads, 0,
+             a.stream>>>(a.members, a.tiles, a.ntiles_total, C);
       const cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
       return launch_controllers(a.members, a.nmembers > 0 ? a.nmembers : 1, a.stream);
