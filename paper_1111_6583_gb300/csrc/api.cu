@@ -1256,8 +1256,9 @@ struct claw_server {
   std::map<uint64_t, Req> reqs;
   Member* d_mem = nullptr;
   Tile* d_tiles = nullptr;
-  size_t cap_mem = 0, cap_tiles = 0;
-  int ntiles = 0;
+  Tile* d_stiles = nullptr;  // cell tiles of the source step (methods with a source)
+  size_t cap_mem = 0, cap_tiles = 0, cap_stiles = 0;
+  int ntiles = 0, nstiles = 0;
   bool dirty = true;
   DevCtl* d_gather = nullptr;
   DevCtl* h_gather = nullptr;
@@ -1285,8 +1286,8 @@ claw_status sfail(claw_server* v, const char* what, cudaError_t e = cudaSuccess)
   } while (0)
 
 size_t req_bytes(const claw_server* v, const claw_grid& g) {
-  return align256(state_bytes_of(v->m, g)) * v->nbuf + align256(aux_bytes_of(v->m, g)) +
-         align256(sizeof(DevCtl));
+  return align256(state_bytes_of(v->m, g)) * (v->nbuf + pre_buffers(v->m)) +
+         align256(aux_bytes_of(v->m, g)) + align256(sizeof(DevCtl));
 }
 
 }  // namespace
@@ -1301,8 +1302,6 @@ claw_status claw_server_create(const claw_method* m, size_t hbm_budget_bytes, in
   *out = nullptr;
   const int nd = (m->num_eqn == num_eqn(m->rp, 2)) ? 2 : 1;
   if (const char* why = check_method(*m, nd)) return sfail(nullptr, why);
-  if (m->source != CLAW_SOURCE_NONE)
-    return sfail(nullptr, "the server takes methods without source terms");
   if (m->scheme == CLAW_CLASSIC &&
       (m->capa_index >= 0 || (nd == 2 && m->rp == CLAW_RP_ACOUSTICS_VC)))
     return sfail(nullptr, "the server runs the row kernels: no capacity or varying-medium 2D classic");
@@ -1380,6 +1379,10 @@ claw_status claw_server_pump(claw_server* v, int steps, int* running, int* queue
     std::memset(&r.mem, 0, sizeof(Member));
     for (int j = 0; j < v->nbuf; ++j) r.mem.q[j] = p + j * sb;
     p += sb * v->nbuf;
+    if (pre_buffers(v->m)) {  // Strang: Q^n after the first half source step
+      r.mem.qpre = p;
+      p += sb;
+    }
     const size_t ab = align256(aux_bytes_of(v->m, r.g));
     r.mem.aux = ab ? p : nullptr;
     p += ab;
@@ -1402,12 +1405,23 @@ claw_status claw_server_pump(claw_server* v, int steps, int* running, int* queue
   // 2. rebuild the member and tile tables when the running set changed
   if (v->dirty) {
     std::vector<Member> hm;
-    std::vector<Tile> ht, mt;
+    std::vector<Tile> ht, mt, hs;
     for (size_t i = 0; i < v->running.size(); ++i) {
       const Req& r = v->reqs[v->running[i]];
       hm.push_back(r.mem);
       for (int t = 0; t < r.mem.ntiles; ++t) ht.push_back(Tile{(int)i, t});
+      if (v->m.source != CLAW_SOURCE_NONE)
+        for (int t = 0; t < maxspeed_tiles(r.mem.nx, r.mem.ny); ++t) hs.push_back(Tile{(int)i, t});
     }
+    if (hs.size() > v->cap_stiles) {
+      if (v->d_stiles) VCK(cudaFreeAsync(v->d_stiles, v->st));
+      v->cap_stiles = std::max<size_t>(hs.size(), 2 * v->cap_stiles);
+      VCK(cudaMallocAsync(&v->d_stiles, sizeof(Tile) * v->cap_stiles, v->st));
+    }
+    if (!hs.empty())
+      VCK(cudaMemcpyAsync(v->d_stiles, hs.data(), sizeof(Tile) * hs.size(),
+                          cudaMemcpyHostToDevice, v->st));
+    v->nstiles = (int)hs.size();
     if (hm.size() > v->cap_mem) {
       if (v->d_mem) VCK(cudaFreeAsync(v->d_mem, v->st));
       v->cap_mem = std::max<size_t>(hm.size(), 2 * v->cap_mem);
@@ -1448,7 +1462,8 @@ claw_status claw_server_pump(claw_server* v, int steps, int* running, int* queue
   if (!v->running.empty()) {
     for (int i = 0; i < steps; ++i)
       VCK(launch_attempt(v->ks, v->m, v->d_mem, v->d_tiles, v->ntiles, v->consts.data(),
-                         v->bw, v->h, v->st, nullptr, 0, (int)v->running.size()));
+                         v->bw, v->h, v->st, v->d_stiles, v->nstiles,
+                         (int)v->running.size()));
     // 4. retire finished requests
     const int nr = (int)v->running.size();
     std::vector<char> fin(nr, 0);
@@ -1522,6 +1537,7 @@ claw_status claw_server_destroy(claw_server* v) {
     if (kv.second.dblock) cudaFreeAsync(kv.second.dblock, v->st);
   if (v->d_mem) cudaFreeAsync(v->d_mem, v->st);
   if (v->d_tiles) cudaFreeAsync(v->d_tiles, v->st);
+  if (v->d_stiles) cudaFreeAsync(v->d_stiles, v->st);
   if (v->d_gather) cudaFree(v->d_gather);
   if (v->h_gather) cudaFreeHost(v->h_gather);
   if (v->st) cudaStreamSynchronize(v->st);

@@ -122,11 +122,42 @@ def test_axisymmetric_batch_equals_alone(orc):
     b.close()
 
 
-def test_server_rejects_source_terms():
+@pytest.mark.parametrize("split", ["godunov", "strang"])
+@pytest.mark.parametrize("budget_kb", [512 << 10, 300])
+def test_server_with_source_equals_alone(orc, split, budget_kb):
+    """Axisymmetric shock-bubble requests of different sizes and final times
+    through the continuous-batching server (a 300 KB budget admits about one
+    at a time; Strang requests carry their half-step buffer) give the same
+    states as solving each alone."""
     from paper_1111_6583_gb300 import claw
-    sp = wl.shock_bubble_axisym(nx=64, ny=16, t_end=0.01, sub=2)
-    with pytest.raises(claw.ClawError):
-        claw.Server(sp, "fp64", budget_bytes=1 << 26, max_slots=2)
+    specs = [wl.shock_bubble_axisym(nx=nx, ny=ny, t_end=t, sub=2, source_split=split)
+             for nx, ny, t in ((64, 16, 0.06), (96, 24, 0.05), (80, 20, 0.07))]
+    sv = claw.Server(specs[0], "fp64", budget_bytes=budget_kb << 10, max_slots=4)
+    tickets = [sv.submit(sp) for sp in specs]
+    results = {}
+    guard = 0
+    while len(results) < len(tickets):
+        sv.pump(4)
+        for t in tickets:
+            if t not in results:
+                r = sv.poll(t)
+                if r is not None:
+                    results[t] = r
+        guard += 1
+        assert guard < 100000
+    sv.close()
+    for k, (t, sp) in enumerate(zip(tickets, specs)):
+        r = results[t]
+        assert r["status"] == "ok" and r["t"] == sp["t_end"]
+        s = claw.Solver(sp, "fp64")
+        ia = s.evolve(sp["t_end"])
+        qa = s.q.double().cpu().numpy()
+        s.close()
+        assert ia["steps"] == r["steps"]
+        assert np.array_equal(qa, r["q"].astype(np.float64))
+        if k == 0:
+            qo, io = oracle_evolve(orc, sp, sp["t_end"])
+            assert rel_maxnorm(r["q"], qo) <= FP64_TOL
 
 
 # --------------------------------------------------------------------------
