@@ -228,6 +228,17 @@ def test_nonphysical_status():
     assert ig["status"] == 6  # CLAW_ENONPHYSICAL
 
 
+def test_cfl_failure_status_keeps_qn():
+    """A first dt far above the stable one and no retries allowed: the run
+    stops with CLAW_ECFL and the state is still Q^n (the rejected attempt
+    wrote only a work buffer)."""
+    spec = wl.random_smooth_2d("sw_roe", 96, 64, dt_initial=0.5, max_retries=0)
+    qg, ig = gpu_evolve(spec, "fp64", 0.3)
+    assert ig["status"] == 5  # CLAW_ECFL
+    assert ig["steps"] == 0 and ig["t"] == 0.0
+    assert np.array_equal(qg, spec["q0"])
+
+
 def test_conserved_totals_drift():
     import torch
     from paper_1111_6583_gb300 import claw
