@@ -561,6 +561,9 @@ def profile_case(case, tile=None):
     sw2d1024 -- the headline 1024^2 FP64 dam break, autotune (or --tile) then 4 steps;
     axisym -- 1280x320 axisymmetric shock-bubble FP64, tune then 3 steps;
     vc -- 1024^2 varying-medium acoustics with capacity FP64, 3 steps;
+    acou2d -- 1024^2 constant-medium acoustics FP64, tile 128 x 32, 3 steps;
+    psystem -- 1024^2 p-system checkerboard FP64, one SSP(10,4) step (10 stages);
+    weno7 -- 1024x512 shock-bubble FP64, WENO7 + SSP(10,4), one step;
     acou3d -- 256^3 constant-medium acoustics FP64, 3 steps."""
     import torch
     from paper_1111_6583_gb300 import claw
@@ -581,6 +584,23 @@ def profile_case(case, tile=None):
         print("tile", s.tune())
         s.set_t_end(sp["t_end"])
         s.advance(3)
+    elif case == "acou2d":
+        sp = wl.acoustics_2d(n=1024)
+        s = claw.Solver(sp, "fp64")
+        s.tune(128, 32)
+        s.set_t_end(sp["t_end"])
+        s.advance(3)
+    elif case == "psystem":
+        sp = wl.psystem_checkerboard_2d(periods=16, cells_per_period=64)
+        s = claw.Solver(sp, "fp64")
+        s.set_t_end(sp["t_end"])
+        s.advance(1)
+    elif case == "weno7":
+        sp = wl.shock_bubble_2d(nx=1024, ny=512)
+        sp.update(weno_order=7, time_integrator="ssp104", cfl_desired=2.0, cfl_max=2.5)
+        s = claw.Solver(sp, "fp64")
+        s.set_t_end(0.2)
+        s.advance(1)
     elif case == "acou3d":
         sp = wl.acoustics_3d(n=256)
         s = claw.Solver(sp, "fp64")
@@ -621,7 +641,7 @@ def main():
                     help="BW,H: fixed 2D tile shape for --case sw2d1024 and --record-traffic")
     ap.add_argument("--case", default=None,
                     help="run one short launch sequence for a profiler (sw2d64, sw2d32, sw2d1024, "
-                         "elast, sharp, axisym, vc, acou3d)")
+                         "elast, sharp, axisym, vc, acou2d, psystem, weno7, acou3d)")
     args = ap.parse_args()
     if args.record_traffic:
         if not args.tile:
