@@ -101,3 +101,64 @@ def test_server_rejects_request_beyond_budget():
         sv.submit(sp)
     assert ei.value.status == claw.CLAW_EBUDGET
     sv.close()
+
+
+def _host_pair(spec, prec):
+    import torch
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    hin = torch.as_tensor(spec["q0"], dtype=dt).pin_memory()
+    return hin, torch.empty_like(hin).pin_memory()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("shape", [(64, 41), (128, 7), (64, 3)])
+def test_step_host_equals_device_steps(prec, shape):
+    """claw_step_host from host buffers: two calls of one attempt give the same
+    bits as one call of two attempts and as the device-resident solver."""
+    import torch
+    from paper_1111_6583_gb300 import claw
+    spec = wl.random_smooth_2d("sw_roe", 131, 29 if shape[1] == 3 else 70)
+    a = claw.Solver(spec, prec)
+    a.tune(*shape)
+    b = claw.Solver(spec, prec)
+    b.tune(*shape)
+    c = claw.Solver(spec, prec)
+    c.tune(*shape)
+    ain, aout = _host_pair(spec, prec)
+    bin_, bout = _host_pair(spec, prec)
+    for _ in range(3):
+        assert a.step_host(ain, aout, 1) == 0
+        assert a.step_host(aout, ain, 1) == 0
+        assert b.step_host(bin_, bout, 2) == 0
+        bin_, bout = bout, bin_
+        c.step()
+        c.step()
+    c.sync()
+    torch.cuda.synchronize()
+    assert np.array_equal(ain.numpy(), bin_.numpy())
+    assert np.array_equal(ain.numpy(), c.q.cpu().numpy())
+    for s in (a, b, c):
+        s.close()
+
+
+def test_step_host_rejected_attempt():
+    """A first dt far above the stable one: the single attempt is rejected and
+    the output is the input; the next call takes the shrunk dt.  Two calls
+    equal one call of two attempts."""
+    from paper_1111_6583_gb300 import claw
+    spec = wl.random_smooth_2d("sw_roe", 131, 70, dt_initial=0.5)
+    a = claw.Solver(spec, "fp64")
+    a.tune(64, 41)
+    b = claw.Solver(spec, "fp64")
+    b.tune(64, 41)
+    ain, aout = _host_pair(spec, "fp64")
+    bin_, bout = _host_pair(spec, "fp64")
+    assert a.step_host(ain, aout, 1) == 0
+    assert np.array_equal(aout.numpy(), ain.numpy())
+    assert a.info()["rejects"] == 1 and a.info()["steps"] == 0
+    assert a.step_host(aout, ain, 1) == 0
+    assert b.step_host(bin_, bout, 2) == 0
+    assert np.array_equal(ain.numpy(), bout.numpy())
+    assert a.info()["steps"] == 1
+    a.close()
+    b.close()
