@@ -211,8 +211,11 @@ claw_status claw_solver_destroy(claw_solver* s);
 /* launch per step over a table of tiles (each grid keeps its own t, dt).  */
 /* ---------------------------------------------------------------------- */
 
-/* grids[n]: one per member (same ndim and method).  tile: cells per tile
- * along x (1D) or columns x rows (2D) chosen by the autotuner if 0. */
+/* grids[n]: one per member (same ndim and method; 1D or 2D).  Row-kernel
+ * methods run one fused launch per step over all members' tiles; methods on
+ * the per-face classic path (a capacity field, or 2D varying-medium
+ * acoustics) run its kernels member by member inside each attempt, and take
+ * no source term (CLAW_EINVAL). */
 claw_status claw_batch_create(const claw_method* m, const claw_grid* grids, int n, void* stream,
                               claw_batch** out);
 /* q[k], aux[k]: device pointers of member k (caller-owned); t_end[k]. */

@@ -952,6 +952,9 @@ struct claw_batch {
   int* d_count = nullptr;
   int* h_count = nullptr;
   int bw = 128, h = 32;
+  int faces = 0;              // per-face classic path (capacity / media-aware transverse)
+  void* work3 = nullptr;      // the members' face arrays, one allocation
+  std::vector<size_t> work3_bytes;
   cudaGraphExec_t gexec = nullptr;
   int gk = 0;
   int bound = 0;
@@ -982,6 +985,8 @@ void batch_free(claw_batch* b) {
   b->gexec = nullptr;
   b->gk = 0;
   if (b->work) cudaFree(b->work);
+  if (b->work3) cudaFree(b->work3);
+  b->work3 = nullptr;
   if (b->d_ctl) cudaFree(b->d_ctl);
   if (b->d_mem) cudaFree(b->d_mem);
   if (b->d_tiles) cudaFree(b->d_tiles);
@@ -1001,6 +1006,17 @@ void batch_free(claw_batch* b) {
 }
 
 cudaError_t batch_attempt(claw_batch* b, cudaStream_t st) {
+  if (b->faces) {
+    // the per-face kernels take one member: sweeps and update member by member
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < b->n && e == cudaSuccess; ++k) {
+      const Member& mb = b->h_mem[k];
+      const int n3[3] = {mb.nx, mb.ny, 1};
+      e = launch_attempt(b->ks, b->m, b->d_mem + k, nullptr, mb.ntiles, b->consts.data(), b->bw,
+                         b->h, st, nullptr, 0, 1, n3, mb.work3, b->work3_bytes[k]);
+    }
+    return e;
+  }
   return launch_attempt(b->ks, b->m, b->d_mem, b->d_tiles, b->ntiles, b->consts.data(),
                         b->bw, b->h, st, b->d_mtiles, b->nmtiles, b->n);
 }
@@ -1015,9 +1031,10 @@ claw_status claw_batch_create(const claw_method* m, const claw_grid* grids, int 
   *out = nullptr;
   const int nd = grids[0].ndim;
   if (nd == 3) return bfail(nullptr, "batches take 1D or 2D grids");
-  if (m->scheme == CLAW_CLASSIC &&
-      (m->capa_index >= 0 || (nd == 2 && m->rp == CLAW_RP_ACOUSTICS_VC)))
-    return bfail(nullptr, "batches run the row kernels: no capacity or varying-medium 2D classic");
+  const int faces = m->scheme == CLAW_CLASSIC && nd <= 2 &&
+                    (m->capa_index >= 0 || (nd == 2 && m->rp == CLAW_RP_ACOUSTICS_VC));
+  if (faces && m->source != CLAW_SOURCE_NONE)
+    return bfail(nullptr, "batches on the per-face path take no source term");
   for (int k = 0; k < n; ++k) {
     if (const char* why = check_grid(grids[k], *m)) return bfail(nullptr, why);
     if (grids[k].ndim != nd) return bfail(nullptr, "all members need the same ndim");
@@ -1032,6 +1049,7 @@ claw_status claw_batch_create(const claw_method* m, const claw_grid* grids, int 
   b->nbuf = nbuf_of(*m);
   b->n = n;
   b->ks = ks;
+  b->faces = faces;
   b->bw = std::min(b->bw, ks.max_bw);
   b->consts = make_consts(*m);
   b->grids.assign(grids, grids + n);
@@ -1063,6 +1081,16 @@ claw_status claw_batch_bind(claw_batch* b, void* const* q, const void* const* au
     total += b->sbytes[k] * (b->nbuf - 1 + pre_buffers(b->m));
   }
   BCK(cudaMalloc(&b->work, total));
+  if (b->faces) {
+    size_t w3 = 0;
+    b->work3_bytes.assign(n, 0);
+    for (int k = 0; k < n; ++k) {
+      b->work3_bytes[k] = align256(faces_work_bytes(b->nd, (int)b->grids[k].n[0],
+                                                    (int)b->grids[k].n[1], b->m.num_eqn, b->prec));
+      w3 += b->work3_bytes[k];
+    }
+    BCK(cudaMalloc(&b->work3, w3));
+  }
   BCK(cudaMalloc(&b->d_ctl, sizeof(DevCtl) * n));
   BCK(cudaMalloc(&b->d_mem, sizeof(Member) * n));
   BCK(cudaMallocHost(&b->h_ctl, sizeof(DevCtl) * n));
@@ -1072,6 +1100,7 @@ claw_status claw_batch_bind(claw_batch* b, void* const* q, const void* const* au
   b->h_tiles.clear();
   std::vector<Tile> mt;
   unsigned char* w = (unsigned char*)b->work;
+  unsigned char* w3p = (unsigned char*)b->work3;
   for (int k = 0; k < n; ++k) {
     const claw_grid& g = b->grids[k];
     Member& mb = b->h_mem[k];
@@ -1087,23 +1116,31 @@ claw_status claw_batch_bind(claw_batch* b, void* const* q, const void* const* au
     mb.aux = aux ? aux[k] : nullptr;
     mb.nx = (int)g.n[0];
     mb.ny = (int)g.n[1];
-    mb.ntiles = tiles_of(b->m.scheme, b->nd, b->prec, mb.nx, mb.ny, b->bw, b->h);
     mb.ctl = b->d_ctl + k;
-    for (int t = 0; t < mb.ntiles; ++t) b->h_tiles.push_back(Tile{k, t});
+    if (b->faces) {
+      // the update's blocks (256 cells each) count the arrivals
+      mb.ntiles = (int)((cells_of(g) + 255) / 256);
+      mb.work3 = w3p;
+      w3p += b->work3_bytes[k];
+    } else {
+      mb.ntiles = tiles_of(b->m.scheme, b->nd, b->prec, mb.nx, mb.ny, b->bw, b->h);
+      for (int t = 0; t < mb.ntiles; ++t) b->h_tiles.push_back(Tile{k, t});
+    }
     const int ms = maxspeed_tiles(mb.nx, mb.ny);
     for (int t = 0; t < ms; ++t) mt.push_back(Tile{k, t});
     b->h_ctl[k] = make_ctl(b->m, g, b->nbuf, 0.0, t_end[k]);
   }
   b->ntiles = (int)b->h_tiles.size();
   b->nmtiles = (int)mt.size();
-  BCK(cudaMalloc(&b->d_tiles, sizeof(Tile) * b->ntiles));
+  BCK(cudaMalloc(&b->d_tiles, sizeof(Tile) * std::max(b->ntiles, 1)));
   BCK(cudaMalloc(&b->d_mtiles, sizeof(Tile) * b->nmtiles));
   BCK(cudaEventRecord(b->ev_a, b->ustream));
   BCK(cudaStreamWaitEvent(b->st, b->ev_a, 0));
   BCK(cudaMemcpyAsync(b->d_ctl, b->h_ctl, sizeof(DevCtl) * n, cudaMemcpyHostToDevice, b->st));
   BCK(cudaMemcpyAsync(b->d_mem, b->h_mem.data(), sizeof(Member) * n, cudaMemcpyHostToDevice, b->st));
-  BCK(cudaMemcpyAsync(b->d_tiles, b->h_tiles.data(), sizeof(Tile) * b->ntiles,
-                      cudaMemcpyHostToDevice, b->st));
+  if (b->ntiles > 0)
+    BCK(cudaMemcpyAsync(b->d_tiles, b->h_tiles.data(), sizeof(Tile) * b->ntiles,
+                        cudaMemcpyHostToDevice, b->st));
   BCK(cudaMemcpyAsync(b->d_mtiles, mt.data(), sizeof(Tile) * b->nmtiles, cudaMemcpyHostToDevice,
                       b->st));
   LaunchArgs a{b->d_mem, b->d_mtiles, b->nmtiles, b->consts.data(), 0, 0, 0, b->st};

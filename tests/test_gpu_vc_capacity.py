@@ -109,11 +109,54 @@ def test_vc_2d_fp32(orc):
     assert rel_maxnorm(qg, qo) <= FP32_SMOOTH_TOL
 
 
-def test_batches_reject_the_per_face_path():
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batches_on_the_per_face_path(orc, prec):
+    """Uneven members of the varying-medium, capacity workload in one batch
+    (the per-face kernels run member by member inside each captured
+    attempt): the same bits as solving each alone; the first against the
+    oracle."""
+    import torch
     from paper_1111_6583_gb300 import claw
-    spec = wl.random_smooth_2d("acoustics_vc", 32, 32, capa_index=2)
-    with pytest.raises(claw.ClawError):
-        claw.Batch([spec, spec], "fp64")
+    specs = [wl.acoustics_vc_2d(n=n, t_end=t) for n, t in ((48, 0.2), (64, 0.15), (40, 0.25))]
+    b = claw.Batch(specs, prec)
+    infos = b.evolve()
+    torch.cuda.synchronize()
+    for k, sp in enumerate(specs):
+        s = claw.Solver(sp, prec)
+        ia = s.evolve(sp["t_end"])
+        qa = s.q.double().cpu().numpy()
+        s.close()
+        assert infos[k]["status"] == 0 and infos[k]["t"] == sp["t_end"]
+        assert infos[k]["steps"] == ia["steps"]
+        assert np.array_equal(qa, b.q[k].double().cpu().numpy())
+        if k == 0:
+            qo, io = oracle_evolve(orc, sp, sp["t_end"])
+            if prec == "fp64":
+                assert io["steps"] == ia["steps"]
+                assert rel_maxnorm(qa, qo) <= FP64_TOL
+            else:
+                assert rel_l1(qa, qo) <= FP32_SHOCK_L1_TOL
+    b.close()
+
+
+def test_batches_with_capacity_in_1d(orc):
+    import torch
+    from paper_1111_6583_gb300 import claw
+    specs = []
+    for n in (300, 457):
+        sp = wl.random_1d("sw_roe", n, char_decomp=0)
+        x = (np.arange(n) + 0.5) / n
+        sp.update(num_aux=1, capa_index=0, t_end=0.05,
+                  aux=np.ascontiguousarray((1.0 + 0.4 * np.sin(2 * np.pi * x))[None]))
+        specs.append(sp)
+    b = claw.Batch(specs, "fp64")
+    infos = b.evolve()
+    torch.cuda.synchronize()
+    for k, sp in enumerate(specs):
+        qo, io = oracle_evolve(orc, sp, sp["t_end"])
+        assert infos[k]["steps"] == io["steps"]
+        assert rel_maxnorm(b.q[k].double().cpu().numpy(), qo) <= FP64_TOL
+    b.close()
 
 
 @pytest.mark.parametrize("ndim,scheme", [(1, "classic"), (2, "classic"), (2, "sharpclaw")])
