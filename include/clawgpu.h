@@ -246,10 +246,11 @@ typedef struct {
 
 /* hbm_budget_bytes bounds the device memory of admitted requests (state,
  * work buffers, aux, control blocks; with a Strang-split source one more
- * state buffer).  max_slots bounds concurrent requests.  Any method the
- * row-kernel paths run (classic 1D/2D without a capacity, SharpClaw), with
- * or without a source term.  CLAW_EINVAL for capacity or 2D varying-medium
- * classic methods (per-face path). */
+ * state buffer; on the per-face classic path its face arrays).  max_slots
+ * bounds concurrent requests.  Classic 1D/2D and SharpClaw methods, with or
+ * without a source term; on the per-face path (a capacity field, or 2D
+ * varying-medium acoustics) the kernels run request by request and there is
+ * no source term (CLAW_EINVAL). */
 claw_status claw_server_create(const claw_method* m, size_t hbm_budget_bytes, int max_slots,
                                void* stream, claw_server** out);
 /* Submit one solve: grid, initial state (host memory, the method's precision

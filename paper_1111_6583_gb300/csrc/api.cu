@@ -1275,6 +1275,7 @@ struct Req {
   long long steps = 0;
   void* dblock = nullptr;
   size_t dbytes = 0;
+  size_t w3bytes = 0;  // per-face path: the request's face arrays
   Member mem{};
 };
 }  // namespace
@@ -1300,6 +1301,7 @@ struct claw_server {
   DevCtl* d_gather = nullptr;
   DevCtl* h_gather = nullptr;
   int bw = 128, h = 16;
+  int faces = 0;  // per-face classic path: kernels run request by request
   std::string err;
 };
 
@@ -1322,9 +1324,15 @@ claw_status sfail(claw_server* v, const char* what, cudaError_t e = cudaSuccess)
     if (e_ != cudaSuccess) return sfail(v, #call, e_); \
   } while (0)
 
+size_t req_faces_bytes(const claw_server* v, const claw_grid& g) {
+  return v->faces ? align256(faces_work_bytes(v->nd, (int)g.n[0], (int)g.n[1], v->m.num_eqn,
+                                              v->prec))
+                  : 0;
+}
+
 size_t req_bytes(const claw_server* v, const claw_grid& g) {
   return align256(state_bytes_of(v->m, g)) * (v->nbuf + pre_buffers(v->m)) +
-         align256(aux_bytes_of(v->m, g)) + align256(sizeof(DevCtl));
+         align256(aux_bytes_of(v->m, g)) + align256(sizeof(DevCtl)) + req_faces_bytes(v, g);
 }
 
 }  // namespace
@@ -1339,9 +1347,10 @@ claw_status claw_server_create(const claw_method* m, size_t hbm_budget_bytes, in
   *out = nullptr;
   const int nd = (m->num_eqn == num_eqn(m->rp, 2)) ? 2 : 1;
   if (const char* why = check_method(*m, nd)) return sfail(nullptr, why);
-  if (m->scheme == CLAW_CLASSIC &&
-      (m->capa_index >= 0 || (nd == 2 && m->rp == CLAW_RP_ACOUSTICS_VC)))
-    return sfail(nullptr, "the server runs the row kernels: no capacity or varying-medium 2D classic");
+  const int faces = m->scheme == CLAW_CLASSIC && nd <= 2 &&
+                    (m->capa_index >= 0 || (nd == 2 && m->rp == CLAW_RP_ACOUSTICS_VC));
+  if (faces && m->source != CLAW_SOURCE_NONE)
+    return sfail(nullptr, "the per-face path serves no source term");
   KernelSet ks = kernels_for(m->rp, nd, m->prec);
   if (!ks.valid) return sfail(nullptr, "no kernels for this solver/dimension/precision");
   claw_server* v = new claw_server();
@@ -1350,6 +1359,7 @@ claw_status claw_server_create(const claw_method* m, size_t hbm_budget_bytes, in
   v->nd = nd;
   v->nbuf = nbuf_of(*m);
   v->ks = ks;
+  v->faces = faces;
   v->bw = std::min(v->bw, ks.max_bw);
   v->consts = make_consts(*m);
   v->budget = hbm_budget_bytes;
@@ -1424,9 +1434,17 @@ claw_status claw_server_pump(claw_server* v, int steps, int* running, int* queue
     r.mem.aux = ab ? p : nullptr;
     p += ab;
     r.mem.ctl = (DevCtl*)p;
+    p += align256(sizeof(DevCtl));
     r.mem.nx = (int)r.g.n[0];
     r.mem.ny = (int)r.g.n[1];
-    r.mem.ntiles = tiles_of(v->m.scheme, v->nd, v->prec, r.mem.nx, r.mem.ny, v->bw, v->h);
+    if (v->faces) {
+      // face arrays; the update's blocks (256 cells each) count the arrivals
+      r.w3bytes = req_faces_bytes(v, r.g);
+      r.mem.work3 = p;
+      r.mem.ntiles = (int)((cells_of(r.g) + 255) / 256);
+    } else {
+      r.mem.ntiles = tiles_of(v->m.scheme, v->nd, v->prec, r.mem.nx, r.mem.ny, v->bw, v->h);
+    }
     DevCtl c = make_ctl(v->m, r.g, v->nbuf, 0.0, r.t_end);
     VCK(cudaMemcpyAsync(r.mem.q[0], r.q0.data(), r.q0.size(), cudaMemcpyHostToDevice, v->st));
     if (!r.aux0.empty())
@@ -1446,7 +1464,8 @@ claw_status claw_server_pump(claw_server* v, int steps, int* running, int* queue
     for (size_t i = 0; i < v->running.size(); ++i) {
       const Req& r = v->reqs[v->running[i]];
       hm.push_back(r.mem);
-      for (int t = 0; t < r.mem.ntiles; ++t) ht.push_back(Tile{(int)i, t});
+      if (!v->faces)
+        for (int t = 0; t < r.mem.ntiles; ++t) ht.push_back(Tile{(int)i, t});
       if (v->m.source != CLAW_SOURCE_NONE)
         for (int t = 0; t < maxspeed_tiles(r.mem.nx, r.mem.ny); ++t) hs.push_back(Tile{(int)i, t});
     }
@@ -1472,8 +1491,9 @@ claw_status claw_server_pump(claw_server* v, int steps, int* running, int* queue
     if (!hm.empty()) {
       VCK(cudaMemcpyAsync(v->d_mem, hm.data(), sizeof(Member) * hm.size(), cudaMemcpyHostToDevice,
                           v->st));
-      VCK(cudaMemcpyAsync(v->d_tiles, ht.data(), sizeof(Tile) * ht.size(), cudaMemcpyHostToDevice,
-                          v->st));
+      if (!ht.empty())
+        VCK(cudaMemcpyAsync(v->d_tiles, ht.data(), sizeof(Tile) * ht.size(),
+                            cudaMemcpyHostToDevice, v->st));
     }
     v->ntiles = (int)ht.size();
     // first dt for the newly admitted requests
@@ -1497,10 +1517,22 @@ claw_status claw_server_pump(claw_server* v, int steps, int* running, int* queue
   }
   // 3. fused step attempts over every running request
   if (!v->running.empty()) {
-    for (int i = 0; i < steps; ++i)
-      VCK(launch_attempt(v->ks, v->m, v->d_mem, v->d_tiles, v->ntiles, v->consts.data(),
-                         v->bw, v->h, v->st, v->d_stiles, v->nstiles,
-                         (int)v->running.size()));
+    for (int i = 0; i < steps; ++i) {
+      if (v->faces) {
+        // the per-face kernels take one member: request by request
+        for (size_t k = 0; k < v->running.size(); ++k) {
+          const Req& r = v->reqs[v->running[k]];
+          const int n3[3] = {r.mem.nx, r.mem.ny, 1};
+          VCK(launch_attempt(v->ks, v->m, v->d_mem + k, nullptr, r.mem.ntiles,
+                             v->consts.data(), v->bw, v->h, v->st, nullptr, 0, 1, n3,
+                             r.mem.work3, r.w3bytes));
+        }
+      } else {
+        VCK(launch_attempt(v->ks, v->m, v->d_mem, v->d_tiles, v->ntiles, v->consts.data(),
+                           v->bw, v->h, v->st, v->d_stiles, v->nstiles,
+                           (int)v->running.size()));
+      }
+    }
     // 4. retire finished requests
     const int nr = (int)v->running.size();
     std::vector<char> fin(nr, 0);

@@ -189,3 +189,34 @@ def test_conserved_totals_weight_the_capacity(ndim, scheme):
     scale = (np.abs(q0) * spec["aux"][0]).reshape(q0.shape[0], -1).sum(axis=1).max() * dV
     assert np.abs(t1 - t0).max() <= 1e-12 * scale
     s.close()
+
+
+def test_server_on_the_per_face_path(orc):
+    """Varying-medium, capacity requests through the continuous-batching
+    server (a budget that admits one or two at a time): the same bits as
+    solving each alone."""
+    from paper_1111_6583_gb300 import claw
+    specs = [wl.acoustics_vc_2d(n=n, t_end=t) for n, t in ((48, 0.2), (64, 0.15), (40, 0.25))]
+    sv = claw.Server(specs[0], "fp64", budget_bytes=3 << 20, max_slots=4)
+    tickets = [sv.submit(sp) for sp in specs]
+    results = {}
+    guard = 0
+    while len(results) < len(tickets):
+        sv.pump(4)
+        for t in tickets:
+            if t not in results:
+                r = sv.poll(t)
+                if r is not None:
+                    results[t] = r
+        guard += 1
+        assert guard < 100000
+    sv.close()
+    for t, sp in zip(tickets, specs):
+        r = results[t]
+        assert r["status"] == "ok" and r["t"] == sp["t_end"]
+        s = claw.Solver(sp, "fp64")
+        ia = s.evolve(sp["t_end"])
+        qa = s.q.double().cpu().numpy()
+        s.close()
+        assert ia["steps"] == r["steps"]
+        assert np.array_equal(qa, r["q"].astype(np.float64))
