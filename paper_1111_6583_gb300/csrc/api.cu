@@ -116,10 +116,6 @@ const char* check_method(const claw_method& m, int nd) {
   if (m.num_aux != na + (m.capa_index >= 0 ? 1 : 0))
     return "num_aux does not match the Riemann solver (and capacity field)";
   if (m.capa_index >= 0 && nd == 3) return "capacity is for 1D and 2D grids";
-  if (m.capa_index >= 0 && m.scheme == CLAW_CLASSIC && m.dim_split)
-    return "capacity with dimensional splitting is not supported";
-  if (m.rp == CLAW_RP_ACOUSTICS_VC && m.scheme == CLAW_CLASSIC && nd == 2 && m.dim_split)
-    return "the varying-medium solver runs unsplit";
   if (m.scheme == CLAW_SHARPCLAW && m.char_decomp && m.rp == CLAW_RP_ACOUSTICS_VC)
     return "no characteristic projection for the varying-medium acoustics solver";
   if (m.scheme != CLAW_CLASSIC && m.scheme != CLAW_SHARPCLAW) return "unknown scheme";

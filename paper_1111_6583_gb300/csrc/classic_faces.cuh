@@ -31,17 +31,18 @@ __host__ __device__ inline size_t faces_count(int nd, int nx, int ny, int dir) {
 
 template <class RP, typename R, int D>
 __global__ void __launch_bounds__(kFacesThreads)
-    faces_sweep(const Member* __restrict__ members, const MConsts<R> C, int nd) {
+    faces_sweep(const Member* __restrict__ members, const MConsts<R> C, int nd, int in_rel) {
   constexpr int M = RP::M, MW = RP::MW, MA = RP::MA, NC = RP::NCTX;
   constexpr int MAS = MA > 0 ? MA : 1;
   using NZ = typename RP::template NZ<D>;
   const Member& mb = members[0];
   DevCtl* ctl = mb.ctl;
-  __shared__ int s_done, s_cur;
+  __shared__ int s_done, s_cur, s_nbuf;
   __shared__ R s_dtdn;
   if (threadIdx.x == 0) {
     s_done = ctl->done;
     s_cur = ctl->cur;
+    s_nbuf = ctl->nbuf;
     s_dtdn = (R)(ctl->dt / ctl->dx[D]);
   }
   __syncthreads();
@@ -51,7 +52,8 @@ __global__ void __launch_bounds__(kFacesThreads)
   const int lines = (nd == 2) ? nl + 2 : 1;
   const long long nf = (long long)(n + 1) * lines;
   const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const R* __restrict__ q = (const R*)step_input(mb, s_cur, 0, 0);
+  // in_rel 0: Q^n; 1: the x-swept state (second sweep of a split step)
+  const R* __restrict__ q = (const R*)step_input(mb, s_cur, s_nbuf, in_rel);
   const R* __restrict__ aux = (const R*)mb.aux;
   R smax = R(0);
   if (id < nf) {
@@ -170,7 +172,7 @@ __global__ void __launch_bounds__(kFacesThreads)
 
 template <class RP, typename R>
 __global__ void __launch_bounds__(kFacesThreads)
-    faces_update(const Member* __restrict__ members, const MConsts<R> C, int nd) {
+    faces_update(const Member* __restrict__ members, const MConsts<R> C, int nd, int sweep) {
   constexpr int M = RP::M;
   const Member& mb = members[0];
   DevCtl* ctl = mb.ctl;
@@ -190,8 +192,11 @@ __global__ void __launch_bounds__(kFacesThreads)
   int bad = 0;
   if (id < (long long)nx * ny) {
     const int i = (int)(id % nx), j = (int)(id / nx);
-    const R* __restrict__ q = (const R*)step_input(mb, s_cur, s_nbuf, 0);
-    R* __restrict__ qo = (R*)mb.q[(s_cur + 1) % s_nbuf];
+    // sweep 0: the unsplit step (slot 0 -> 1); dimensional splitting
+    // (Godunov): 1 the x-faces only (slot 0 -> 1), 2 the y-faces only
+    // (slot 1 -> 2), without transverse terms
+    const R* __restrict__ q = (const R*)step_input(mb, s_cur, s_nbuf, sweep == 2 ? 1 : 0);
+    R* __restrict__ qo = (R*)mb.q[(s_cur + (sweep == 2 ? 2 : 1)) % s_nbuf];
     const R* __restrict__ aux = (const R*)mb.aux;
     const size_t NX = faces_count(nd, nx, ny, 0), NY = faces_count(nd, nx, ny, 1);
     const R* X = (const R*)mb.work3;
@@ -218,6 +223,13 @@ __global__ void __launch_bounds__(kFacesThreads)
       if (nd == 1) {
         v = qv - cx * (XR(1, xf(i, 0)) + XR(0, xf(i + 1, 0))) -
             cx * (XR(2, xf(i + 1, 0)) - XR(2, xf(i, 0)));
+      } else if (sweep == 1) {
+        // x-faces only: the y-face records are not written in this sweep
+        v = qv - cx * (XR(1, xf(i, j)) + XR(0, xf(i + 1, j))) -
+            cx * (XR(2, xf(i + 1, j)) - XR(2, xf(i, j)));
+      } else if (sweep == 2) {
+        v = qv - cy * (YR(1, yf(i, j)) + YR(0, yf(i, j + 1))) -
+            cy * (YR(2, yf(i, j + 1)) - YR(2, yf(i, j)));
       } else {
         // total correction fluxes: normal part and the transverse pieces that
         // reach the face (order of the terms as in the serial definition)
@@ -239,7 +251,7 @@ __global__ void __launch_bounds__(kFacesThreads)
       qo[k * plane + (size_t)j * nx + i] = v;
     }
   }
-  finish_attempt<R>(ctl, R(0), R(0), bad, mb.ntiles, true);
+  finish_attempt<R>(ctl, R(0), R(0), bad, mb.ntiles, sweep != 1);
 }
 
 }  // namespace claw

@@ -184,14 +184,17 @@ struct Launchers {
       if (uses_faces<RP, ND>(C.capa)) {
         const int nx = a.n3[0], ny = ND == 2 ? a.n3[1] : 1;
         const size_t fx = faces_count(ND, nx, ny, 0), fy = faces_count(ND, nx, ny, 1);
-        faces_sweep<RP, R, 0><<<(unsigned)((fx + kFacesThreads - 1) / kFacesThreads),
-                                kFacesThreads, 0, a.stream>>>(a.members, C, ND);
-        if (ND == 2)
+        // a.sweep: 0 unsplit; 1 / 2 the x / y sweep of a dimensionally split step
+        if (a.sweep != 2)
+          faces_sweep<RP, R, 0><<<(unsigned)((fx + kFacesThreads - 1) / kFacesThreads),
+                                  kFacesThreads, 0, a.stream>>>(a.members, C, ND, 0);
+        if (ND == 2 && a.sweep != 1)
           faces_sweep<RP, R, 1><<<(unsigned)((fy + kFacesThreads - 1) / kFacesThreads),
-                                  kFacesThreads, 0, a.stream>>>(a.members, C, ND);
+                                  kFacesThreads, 0, a.stream>>>(a.members, C, ND,
+                                                                a.sweep == 2 ? 1 : 0);
         const long long nc = (long long)nx * ny;
         faces_update<RP, R><<<(unsigned)((nc + kFacesThreads - 1) / kFacesThreads),
-                              kFacesThreads, 0, a.stream>>>(a.members, C, ND);
+                              kFacesThreads, 0, a.stream>>>(a.members, C, ND, a.sweep);
         return cudaGetLastError();
       }
     }

@@ -220,3 +220,31 @@ def test_server_on_the_per_face_path(orc):
         s.close()
         assert ia["steps"] == r["steps"]
         assert np.array_equal(qa, r["q"].astype(np.float64))
+
+
+@pytest.mark.parametrize("case", ["sw_capacity", "vc_capacity", "vc"])
+def test_dimensional_splitting_on_the_per_face_path(orc, case):
+    """Godunov dimensional splitting on the per-face path (x sweeps over dt
+    from Q^n, then y sweeps over dt from that state): a capacity field, and
+    the varying-medium solver with or without one; fixed steps and a
+    controller run against the oracle."""
+    if case == "sw_capacity":
+        spec = wl.random_smooth_2d("sw_roe", 70, 45, char_decomp=0, transverse=0)
+        X, Y = np.meshgrid((np.arange(70) + 0.5) / 70, (np.arange(45) + 0.5) / 45, indexing="xy")
+        kap = (1.0 + 0.4 * np.sin(2 * np.pi * X) * np.cos(2 * np.pi * Y))[None]
+        spec.update(num_aux=1, capa_index=0, aux=np.ascontiguousarray(kap))
+    else:
+        spec = wl.acoustics_vc_2d(n=64, t_end=0.2, capacity=(case == "vc_capacity"))
+        spec["transverse"] = 0
+    spec["dim_split"] = 1
+    dt = 0.3 / spec["n"][0]
+    qo, co = oracle_fixed_steps(orc, spec, dt, 4)
+    qg, cg = gpu_fixed_steps(spec, "fp64", dt, 4)
+    assert rel_maxnorm(qg, qo) <= FP64_TOL
+    assert np.allclose(cg, co, rtol=1e-13, atol=0)
+    t_end = 0.1
+    qo, io = oracle_evolve(orc, spec, t_end)
+    for graph in (True, False):
+        qg, ig = gpu_evolve(spec, "fp64", t_end, use_graph=graph)
+        assert ig["status"] == 0 and ig["steps"] == io["steps"] and ig["t"] == t_end
+        assert rel_maxnorm(qg, qo) <= FP64_TOL
