@@ -98,11 +98,13 @@ def test_transmission_and_reflection_at_an_impedance_jump():
     assert abs(Rf - (Zr - Zl) / (Zl + Zr)) < 0.02
 
 
-@pytest.mark.parametrize("ndim,scheme", [(1, "classic"), (2, "classic"), (1, "sharpclaw"),
-                                         (2, "sharpclaw")])
-def test_uniform_capacity_is_a_stretched_grid(ndim, scheme):
+@pytest.mark.parametrize("ndim,scheme,split", [(1, "classic", 0), (2, "classic", 0),
+                                               (2, "classic", 1), (1, "sharpclaw", 0),
+                                               (2, "sharpclaw", 0)])
+def test_uniform_capacity_is_a_stretched_grid(ndim, scheme, split):
     """kappa q_t + f(q)_x = 0 with kappa = k everywhere is the problem on a
-    grid k times wider: same states, same Courant numbers."""
+    grid k times wider: same states, same Courant numbers (unsplit, and with
+    dimensional splitting)."""
     k = 1.6
     if ndim == 1:
         s1 = wl.random_1d("sw_roe", 96, scheme=scheme, char_decomp=0)
@@ -110,9 +112,10 @@ def test_uniform_capacity_is_a_stretched_grid(ndim, scheme):
         s2 = wl.random_1d("sw_roe", 96, scheme=scheme, char_decomp=0)
         s2["upper"] = [k]
     else:
-        s1 = wl.random_smooth_2d("sw_roe", 40, 30, scheme=scheme, char_decomp=0)
+        kw = {"dim_split": 1, "transverse": 0} if split else {}
+        s1 = wl.random_smooth_2d("sw_roe", 40, 30, scheme=scheme, char_decomp=0, **kw)
         s1.update(num_aux=1, capa_index=0, aux=np.full((1, 30, 40), k))
-        s2 = wl.random_smooth_2d("sw_roe", 40, 30, scheme=scheme, char_decomp=0)
+        s2 = wl.random_smooth_2d("sw_roe", 40, 30, scheme=scheme, char_decomp=0, **kw)
         s2["upper"] = [k, k]
     P1, P2 = oracle.make_problem(s1), oracle.make_problem(s2)
     q1, q2 = s1["q0"], s2["q0"]
