@@ -214,8 +214,7 @@ claw_status claw_solver_destroy(claw_solver* s);
 /* grids[n]: one per member (same ndim and method; 1D or 2D).  Row-kernel
  * methods run one fused launch per step over all members' tiles; methods on
  * the per-face classic path (a capacity field, or 2D varying-medium
- * acoustics) run its kernels member by member inside each attempt, and take
- * no source term (CLAW_EINVAL). */
+ * acoustics) run its kernels member by member inside each attempt. */
 claw_status claw_batch_create(const claw_method* m, const claw_grid* grids, int n, void* stream,
                               claw_batch** out);
 /* q[k], aux[k]: device pointers of member k (caller-owned); t_end[k]. */
@@ -249,8 +248,7 @@ typedef struct {
  * state buffer; on the per-face classic path its face arrays).  max_slots
  * bounds concurrent requests.  Classic 1D/2D and SharpClaw methods, with or
  * without a source term; on the per-face path (a capacity field, or 2D
- * varying-medium acoustics) the kernels run request by request and there is
- * no source term (CLAW_EINVAL). */
+ * varying-medium acoustics) the kernels run request by request. */
 claw_status claw_server_create(const claw_method* m, size_t hbm_budget_bytes, int max_slots,
                                void* stream, claw_server** out);
 /* Submit one solve: grid, initial state (host memory, the method's precision

@@ -951,6 +951,7 @@ struct claw_batch {
   int faces = 0;              // per-face classic path (capacity / media-aware transverse)
   void* work3 = nullptr;      // the members' face arrays, one allocation
   std::vector<size_t> work3_bytes;
+  Tile* d_tile0 = nullptr;    // (member 0, t) for the source steps of one member at a time
   cudaGraphExec_t gexec = nullptr;
   int gk = 0;
   int bound = 0;
@@ -983,6 +984,8 @@ void batch_free(claw_batch* b) {
   if (b->work) cudaFree(b->work);
   if (b->work3) cudaFree(b->work3);
   b->work3 = nullptr;
+  if (b->d_tile0) cudaFree(b->d_tile0);
+  b->d_tile0 = nullptr;
   if (b->d_ctl) cudaFree(b->d_ctl);
   if (b->d_mem) cudaFree(b->d_mem);
   if (b->d_tiles) cudaFree(b->d_tiles);
@@ -1009,7 +1012,8 @@ cudaError_t batch_attempt(claw_batch* b, cudaStream_t st) {
       const Member& mb = b->h_mem[k];
       const int n3[3] = {mb.nx, mb.ny, 1};
       e = launch_attempt(b->ks, b->m, b->d_mem + k, nullptr, mb.ntiles, b->consts.data(), b->bw,
-                         b->h, st, nullptr, 0, 1, n3, mb.work3, b->work3_bytes[k]);
+                         b->h, st, b->d_tile0, maxspeed_tiles(mb.nx, mb.ny), 1, n3, mb.work3,
+                         b->work3_bytes[k]);
     }
     return e;
   }
@@ -1029,8 +1033,6 @@ claw_status claw_batch_create(const claw_method* m, const claw_grid* grids, int 
   if (nd == 3) return bfail(nullptr, "batches take 1D or 2D grids");
   const int faces = m->scheme == CLAW_CLASSIC && nd <= 2 &&
                     (m->capa_index >= 0 || (nd == 2 && m->rp == CLAW_RP_ACOUSTICS_VC));
-  if (faces && m->source != CLAW_SOURCE_NONE)
-    return bfail(nullptr, "batches on the per-face path take no source term");
   for (int k = 0; k < n; ++k) {
     if (const char* why = check_grid(grids[k], *m)) return bfail(nullptr, why);
     if (grids[k].ndim != nd) return bfail(nullptr, "all members need the same ndim");
@@ -1086,6 +1088,15 @@ claw_status claw_batch_bind(claw_batch* b, void* const* q, const void* const* au
       w3 += b->work3_bytes[k];
     }
     BCK(cudaMalloc(&b->work3, w3));
+    if (b->m.source != CLAW_SOURCE_NONE) {
+      int most = 1;
+      for (int k = 0; k < n; ++k)
+        most = std::max(most, maxspeed_tiles((int)b->grids[k].n[0], (int)b->grids[k].n[1]));
+      std::vector<Tile> t0(most);
+      for (int t = 0; t < most; ++t) t0[t] = Tile{0, t};
+      BCK(cudaMalloc(&b->d_tile0, sizeof(Tile) * most));
+      BCK(cudaMemcpy(b->d_tile0, t0.data(), sizeof(Tile) * most, cudaMemcpyHostToDevice));
+    }
   }
   BCK(cudaMalloc(&b->d_ctl, sizeof(DevCtl) * n));
   BCK(cudaMalloc(&b->d_mem, sizeof(Member) * n));
@@ -1298,6 +1309,8 @@ struct claw_server {
   DevCtl* h_gather = nullptr;
   int bw = 128, h = 16;
   int faces = 0;  // per-face classic path: kernels run request by request
+  Tile* d_tile0 = nullptr;  // (member 0, t): source steps of one request at a time
+  size_t cap_tile0 = 0;
   std::string err;
 };
 
@@ -1345,8 +1358,6 @@ claw_status claw_server_create(const claw_method* m, size_t hbm_budget_bytes, in
   if (const char* why = check_method(*m, nd)) return sfail(nullptr, why);
   const int faces = m->scheme == CLAW_CLASSIC && nd <= 2 &&
                     (m->capa_index >= 0 || (nd == 2 && m->rp == CLAW_RP_ACOUSTICS_VC));
-  if (faces && m->source != CLAW_SOURCE_NONE)
-    return sfail(nullptr, "the per-face path serves no source term");
   KernelSet ks = kernels_for(m->rp, nd, m->prec);
   if (!ks.valid) return sfail(nullptr, "no kernels for this solver/dimension/precision");
   claw_server* v = new claw_server();
@@ -1474,6 +1485,23 @@ claw_status claw_server_pump(claw_server* v, int steps, int* running, int* queue
       VCK(cudaMemcpyAsync(v->d_stiles, hs.data(), sizeof(Tile) * hs.size(),
                           cudaMemcpyHostToDevice, v->st));
     v->nstiles = (int)hs.size();
+    if (v->faces && v->m.source != CLAW_SOURCE_NONE) {
+      size_t most = 1;
+      for (uint64_t t : v->running) {
+        const Req& r = v->reqs[t];
+        most = std::max<size_t>(most, (size_t)maxspeed_tiles(r.mem.nx, r.mem.ny));
+      }
+      if (most > v->cap_tile0) {
+        if (v->d_tile0) VCK(cudaFreeAsync(v->d_tile0, v->st));
+        v->cap_tile0 = std::max(most, 2 * v->cap_tile0);
+        std::vector<Tile> t0(v->cap_tile0);
+        for (size_t t = 0; t < v->cap_tile0; ++t) t0[t] = Tile{0, (int)t};
+        VCK(cudaMallocAsync(&v->d_tile0, sizeof(Tile) * v->cap_tile0, v->st));
+        VCK(cudaMemcpyAsync(v->d_tile0, t0.data(), sizeof(Tile) * v->cap_tile0,
+                            cudaMemcpyHostToDevice, v->st));
+        VCK(cudaStreamSynchronize(v->st));  // t0 is a host temporary
+      }
+    }
     if (hm.size() > v->cap_mem) {
       if (v->d_mem) VCK(cudaFreeAsync(v->d_mem, v->st));
       v->cap_mem = std::max<size_t>(hm.size(), 2 * v->cap_mem);
@@ -1520,8 +1548,9 @@ claw_status claw_server_pump(claw_server* v, int steps, int* running, int* queue
           const Req& r = v->reqs[v->running[k]];
           const int n3[3] = {r.mem.nx, r.mem.ny, 1};
           VCK(launch_attempt(v->ks, v->m, v->d_mem + k, nullptr, r.mem.ntiles,
-                             v->consts.data(), v->bw, v->h, v->st, nullptr, 0, 1, n3,
-                             r.mem.work3, r.w3bytes));
+                             v->consts.data(), v->bw, v->h, v->st, v->d_tile0,
+                             maxspeed_tiles(r.mem.nx, r.mem.ny), 1, n3, r.mem.work3,
+                             r.w3bytes));
         }
       } else {
         VCK(launch_attempt(v->ks, v->m, v->d_mem, v->d_tiles, v->ntiles, v->consts.data(),
@@ -1603,6 +1632,7 @@ claw_status claw_server_destroy(claw_server* v) {
   if (v->d_mem) cudaFreeAsync(v->d_mem, v->st);
   if (v->d_tiles) cudaFreeAsync(v->d_tiles, v->st);
   if (v->d_stiles) cudaFreeAsync(v->d_stiles, v->st);
+  if (v->d_tile0) cudaFreeAsync(v->d_tile0, v->st);
   if (v->d_gather) cudaFree(v->d_gather);
   if (v->h_gather) cudaFreeHost(v->h_gather);
   if (v->st) cudaStreamSynchronize(v->st);

@@ -248,3 +248,55 @@ def test_dimensional_splitting_on_the_per_face_path(orc, case):
         qg, ig = gpu_evolve(spec, "fp64", t_end, use_graph=graph)
         assert ig["status"] == 0 and ig["steps"] == io["steps"] and ig["t"] == t_end
         assert rel_maxnorm(qg, qo) <= FP64_TOL
+
+
+def _axisym_with_capacity(nx, ny, t, split):
+    """The axisymmetric shock-bubble on a grid stretched in z (a capacity
+    field), so that the source steps run with the per-face kernels."""
+    sp = wl.shock_bubble_axisym(nx=nx, ny=ny, t_end=t, sub=2, source_split=split)
+    xi = (np.arange(nx) + 0.5) / nx
+    kap = np.broadcast_to(1.0 + 0.2 * np.cos(np.pi * xi), (ny, nx))
+    sp.update(num_aux=1, capa_index=0, aux=np.ascontiguousarray(kap[None]))
+    return sp
+
+
+@pytest.mark.parametrize("split", ["godunov", "strang"])
+def test_per_face_path_with_source_solver_batch_server(orc, split):
+    import torch
+    from paper_1111_6583_gb300 import claw
+    specs = [_axisym_with_capacity(nx, ny, t, split) for nx, ny, t in ((64, 16, 0.06),
+                                                                        (80, 20, 0.05))]
+    alone = []
+    for k, sp in enumerate(specs):
+        s = claw.Solver(sp, "fp64")
+        ia = s.evolve(sp["t_end"])
+        alone.append((s.q.double().cpu().numpy(), ia))
+        s.close()
+        if k == 0:
+            qo, io = oracle_evolve(orc, sp, sp["t_end"])
+            assert io["status"] == "ok" and io["steps"] == ia["steps"]
+            assert rel_maxnorm(alone[0][0], qo) <= FP64_TOL
+    b = claw.Batch(specs, "fp64")
+    infos = b.evolve()
+    torch.cuda.synchronize()
+    for k in range(len(specs)):
+        assert infos[k]["steps"] == alone[k][1]["steps"]
+        assert np.array_equal(alone[k][0], b.q[k].double().cpu().numpy())
+    b.close()
+    sv = claw.Server(specs[0], "fp64", budget_bytes=64 << 20, max_slots=4)
+    tickets = [sv.submit(sp) for sp in specs]
+    results = {}
+    guard = 0
+    while len(results) < len(tickets):
+        sv.pump(4)
+        for t in tickets:
+            if t not in results:
+                r = sv.poll(t)
+                if r is not None:
+                    results[t] = r
+        guard += 1
+        assert guard < 100000
+    sv.close()
+    for k, t in enumerate(tickets):
+        assert results[t]["steps"] == alone[k][1]["steps"]
+        assert np.array_equal(alone[k][0], results[t]["q"].astype(np.float64))
