@@ -281,7 +281,7 @@ static int harten_hyman(const orc_prob* P, int dir, int m, int nw, const double*
                         const double* qr, const double* W, const double* s, double* amdq,
                         double* apdq) {
   double total[MAXM];
-  double qm[MAXM];
+  double qm[MAXM] = {0};
   int last = nw - 1;
   for (int k = 0; k < m; ++k) {
     total[k] = 0.0;
@@ -997,7 +997,7 @@ int orc_classic_step(const orc_prob* P, double* q, const double* aux, double dt,
   source_before(P, q, dt);
   if (P->dim_split) {
     /* Godunov dimensional splitting: x sweeps over dt, then y sweeps over dt */
-    double c1, c2;
+    double c1 = 0.0, c2 = 0.0;
     st = classic2d(P, q, aux, dt, &c1, 1);
     if (st == ORC_OK) st = classic2d(P, q, aux, dt, &c2, 2);
     *cfl = (c1 >= c2 || isnan(c1)) ? c1 : c2;
@@ -1082,7 +1082,7 @@ static void rp3(const orc_prob* P, int d, const double* ql, const double* qr, do
     s[0] = P->params[d];
   } else {
     /* acoustics (p, u, v, w): the two waves of the normal velocity 1+d */
-    double alpha[MAXW], r[MAXW * MAXM], d_[MAXM];
+    double alpha[MAXW], r[MAXW * MAXM], d_[MAXM] = {0};
     int n = 1 + d;
     for (int k = 0; k < m; ++k) d_[k] = qr[k] - ql[k];
     acoustics_eig(P, n, -1, 0, d_, alpha, r, s);
