@@ -211,10 +211,11 @@ claw_status claw_solver_destroy(claw_solver* s);
 /* launch per step over a table of tiles (each grid keeps its own t, dt).  */
 /* ---------------------------------------------------------------------- */
 
-/* grids[n]: one per member (same ndim and method; 1D or 2D).  Row-kernel
+/* grids[n]: one per member (same ndim and method; 1D, 2D or 3D).  Row-kernel
  * methods run one fused launch per step over all members' tiles; methods on
  * the per-face classic path (a capacity field, or 2D varying-medium
- * acoustics) run its kernels member by member inside each attempt. */
+ * acoustics) and 3D grids (the face sweeps and update of Sec. 2's 3D
+ * algorithm) run their kernels member by member inside each attempt. */
 claw_status claw_batch_create(const claw_method* m, const claw_grid* grids, int n, void* stream,
                               claw_batch** out);
 /* q[k], aux[k]: device pointers of member k (caller-owned); t_end[k]. */

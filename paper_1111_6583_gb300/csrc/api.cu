@@ -1005,6 +1005,17 @@ void batch_free(claw_batch* b) {
 }
 
 cudaError_t batch_attempt(claw_batch* b, cudaStream_t st) {
+  if (b->nd == 3) {
+    // sweeps and update of one 3D member at a time, each on its own face arrays
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < b->n && e == cudaSuccess; ++k) {
+      const Member& mb = b->h_mem[k];
+      LaunchArgs a{b->d_mem + k, nullptr, mb.ntiles, b->consts.data(), 0, 0, 0, st,
+                   {mb.nx, mb.ny, mb.nz}, mb.work3, b->work3_bytes[k]};
+      e = b->ks.classic(a);
+    }
+    return e;
+  }
   if (b->faces) {
     // the per-face kernels take one member: sweeps and update member by member
     cudaError_t e = cudaSuccess;
@@ -1030,7 +1041,6 @@ claw_status claw_batch_create(const claw_method* m, const claw_grid* grids, int 
   if (!m || !grids || !out || n <= 0) return bfail(nullptr, "bad argument");
   *out = nullptr;
   const int nd = grids[0].ndim;
-  if (nd == 3) return bfail(nullptr, "batches take 1D or 2D grids");
   const int faces = m->scheme == CLAW_CLASSIC && nd <= 2 &&
                     (m->capa_index >= 0 || (nd == 2 && m->rp == CLAW_RP_ACOUSTICS_VC));
   for (int k = 0; k < n; ++k) {
@@ -1079,6 +1089,17 @@ claw_status claw_batch_bind(claw_batch* b, void* const* q, const void* const* au
     total += b->sbytes[k] * (b->nbuf - 1 + pre_buffers(b->m));
   }
   BCK(cudaMalloc(&b->work, total));
+  if (b->nd == 3) {
+    size_t w3 = 0;
+    b->work3_bytes.assign(n, 0);
+    for (int k = 0; k < n; ++k) {
+      const claw_grid& g = b->grids[k];
+      b->work3_bytes[k] = align256(classic3d_work_bytes((int)g.n[0], (int)g.n[1], (int)g.n[2],
+                                                        b->m.num_eqn, b->prec));
+      w3 += b->work3_bytes[k];
+    }
+    BCK(cudaMalloc(&b->work3, w3));
+  }
   if (b->faces) {
     size_t w3 = 0;
     b->work3_bytes.assign(n, 0);
@@ -1123,8 +1144,15 @@ claw_status claw_batch_bind(claw_batch* b, void* const* q, const void* const* au
     mb.aux = aux ? aux[k] : nullptr;
     mb.nx = (int)g.n[0];
     mb.ny = (int)g.n[1];
+    mb.nz = 1;
     mb.ctl = b->d_ctl + k;
-    if (b->faces) {
+    if (b->nd == 3) {
+      // the 3D kernels take one member; the update's blocks count the arrivals
+      mb.nz = (int)g.n[2];
+      mb.ntiles = (int)((cells_of(g) + 255) / 256);
+      mb.work3 = w3p;
+      w3p += b->work3_bytes[k];
+    } else if (b->faces) {
       // the update's blocks (256 cells each) count the arrivals
       mb.ntiles = (int)((cells_of(g) + 255) / 256);
       mb.work3 = w3p;
@@ -1133,14 +1161,14 @@ claw_status claw_batch_bind(claw_batch* b, void* const* q, const void* const* au
       mb.ntiles = tiles_of(b->m.scheme, b->nd, b->prec, mb.nx, mb.ny, b->bw, b->h);
       for (int t = 0; t < mb.ntiles; ++t) b->h_tiles.push_back(Tile{k, t});
     }
-    const int ms = maxspeed_tiles(mb.nx, mb.ny);
+    const int ms = b->nd == 3 ? 0 : maxspeed_tiles(mb.nx, mb.ny);
     for (int t = 0; t < ms; ++t) mt.push_back(Tile{k, t});
     b->h_ctl[k] = make_ctl(b->m, g, b->nbuf, 0.0, t_end[k]);
   }
   b->ntiles = (int)b->h_tiles.size();
   b->nmtiles = (int)mt.size();
   BCK(cudaMalloc(&b->d_tiles, sizeof(Tile) * std::max(b->ntiles, 1)));
-  BCK(cudaMalloc(&b->d_mtiles, sizeof(Tile) * b->nmtiles));
+  BCK(cudaMalloc(&b->d_mtiles, sizeof(Tile) * std::max(b->nmtiles, 1)));
   BCK(cudaEventRecord(b->ev_a, b->ustream));
   BCK(cudaStreamWaitEvent(b->st, b->ev_a, 0));
   BCK(cudaMemcpyAsync(b->d_ctl, b->h_ctl, sizeof(DevCtl) * n, cudaMemcpyHostToDevice, b->st));
@@ -1148,10 +1176,20 @@ claw_status claw_batch_bind(claw_batch* b, void* const* q, const void* const* au
   if (b->ntiles > 0)
     BCK(cudaMemcpyAsync(b->d_tiles, b->h_tiles.data(), sizeof(Tile) * b->ntiles,
                         cudaMemcpyHostToDevice, b->st));
-  BCK(cudaMemcpyAsync(b->d_mtiles, mt.data(), sizeof(Tile) * b->nmtiles, cudaMemcpyHostToDevice,
-                      b->st));
-  LaunchArgs a{b->d_mem, b->d_mtiles, b->nmtiles, b->consts.data(), 0, 0, 0, b->st};
-  BCK(b->ks.maxspeed(a));
+  if (b->nmtiles > 0)
+    BCK(cudaMemcpyAsync(b->d_mtiles, mt.data(), sizeof(Tile) * b->nmtiles,
+                        cudaMemcpyHostToDevice, b->st));
+  if (b->nd == 3) {
+    for (int k = 0; k < n; ++k) {
+      const claw_grid& g = b->grids[k];
+      LaunchArgs a{b->d_mem + k, nullptr, 0, b->consts.data(), 0, 0, 0, b->st,
+                   {(int)g.n[0], (int)g.n[1], (int)g.n[2]}, nullptr, 0};
+      BCK(b->ks.maxspeed(a));
+    }
+  } else {
+    LaunchArgs a{b->d_mem, b->d_mtiles, b->nmtiles, b->consts.data(), 0, 0, 0, b->st};
+    BCK(b->ks.maxspeed(a));
+  }
   BCK(launch_dt_init(b->d_ctl, n, b->st));
   BCK(cudaStreamSynchronize(b->st));
   b->bound = 1;

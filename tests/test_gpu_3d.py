@@ -57,3 +57,48 @@ def test_3d_controller_run(orc):
     qg, ig = gpu_evolve(spec, "fp64", 0.15)
     assert ig["steps"] == io["steps"] and ig["t"] == 0.15
     assert rel_maxnorm(qg, qo) <= FP64_TOL
+
+
+def _batch_specs(rp, bc):
+    specs = []
+    for k, (n3, te) in enumerate([((16, 12, 10), 0.15), ((9, 13, 11), 0.08), ((20, 8, 6), 0.2)]):
+        sp = wl.random_3d(rp, *n3, seed=wl.SEED + 31 * k, bc=bc)
+        sp["t_end"] = te
+        specs.append(sp)
+    return specs
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+@pytest.mark.parametrize("rp,bc", [("acoustics", "wall"), ("advection", "periodic")])
+def test_3d_batch_members_match_oracle(orc, rp, bc, use_graph):
+    """A batch of 3D grids of different shapes and end times: each member takes
+    the oracle's CFL steps and ends at its own t_end with the oracle's state."""
+    import torch
+    from paper_1111_6583_gb300 import claw
+    specs = _batch_specs(rp, bc)
+    b = claw.Batch(specs, "fp64")
+    infos = b.evolve(use_graph=use_graph)
+    torch.cuda.synchronize()
+    for k, sp in enumerate(specs):
+        qo, io = oracle_evolve(orc, sp, sp["t_end"])
+        assert infos[k]["steps"] == io["steps"] and infos[k]["t"] == sp["t_end"], k
+        assert rel_maxnorm(b.q[k].double().cpu().numpy(), qo) <= FP64_TOL, k
+    b.close()
+
+
+def test_3d_batch_fp32_matches_solvers():
+    """FP32 3D batch members against FP32 single-grid solvers of the same grids."""
+    import torch
+    from paper_1111_6583_gb300 import claw
+    specs = _batch_specs("acoustics", "wall")
+    b = claw.Batch(specs, "fp32")
+    infos = b.evolve()
+    torch.cuda.synchronize()
+    for k, sp in enumerate(specs):
+        s = claw.Solver(sp, "fp32")
+        ia = s.evolve(sp["t_end"])
+        assert infos[k]["steps"] == ia["steps"] and infos[k]["t"] == ia["t"], k
+        qa = s.q.double().cpu().numpy()
+        assert rel_maxnorm(b.q[k].double().cpu().numpy(), qa) <= 1e-6, k
+        s.close()
+    b.close()
