@@ -20,8 +20,8 @@ namespace claw {
 // prepares each cell once (CellPrep: the per-cell part of the Riemann solve),
 // then streams through its K + 3 interfaces with a three-interface register
 // window: solve interface j, limit interface j-1 with its neighbours, fold the
-// correction into the fluctuations and emit cell j-3.  No shared memory but
-// the control values thread 0 reads for the tile (two barriers per tile).
+// correction into the fluctuations and emit cell j-3.  No shared memory and
+// no block barrier: each warp reads its member's control values itself.
 // ---------------------------------------------------------------------------
 template <typename R, int K>
 struct VecIO;
@@ -121,35 +121,30 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? 8 : 1)
   constexpr int M = RP::M, MW = RP::MW, MA = RP::MA;
   constexpr int MAS = MA > 0 ? MA : 1;
   constexpr int T = NT * K;
+  constexpr int NW = NT / 32;  // warp units per tile
   using CP = CellPrep<RP, R>;
   using Cell = typename CP::Cell;
-  __shared__ int s_done, s_cur, s_nbuf;
-  __shared__ R s_dtdx;
+  const int lane = threadIdx.x & 31;
 
-  for (int it = blockIdx.x; it < ntiles_total; it += gridDim.x) {
-    const Tile tl = tiles ? tiles[it] : Tile{0, it};
+  // Each warp walks its own units (a quarter tile of 32 K cells at NT = 128)
+  // and reads the control values itself: no block barrier, so the warps of a
+  // block overlap one another's loads, arithmetic and stores.
+  const int nunits = ntiles_total * NW;
+  for (int u = blockIdx.x * NW + (threadIdx.x >> 5); u < nunits; u += gridDim.x * NW) {
+    const Tile tl = tiles ? tiles[u / NW] : Tile{0, u / NW};
     const Member& mb = members[tl.member];
     DevCtl* ctl = mb.ctl;
-    if (threadIdx.x == 0) {
-      s_done = ctl->done;
-      // FP32: one multiply by the stored 1/dx (an FP64 division here would
-      // hold every thread of the block at the barrier below)
-      if constexpr (sizeof(R) == 4) s_dtdx = (R)(ctl->dt * ctl->idx[0]);
-      else s_dtdx = ctl->dt / ctl->dx[0];
-      s_cur = ctl->cur;
-      s_nbuf = ctl->nbuf;
-    }
-    __syncthreads();
-    if (s_done) {
-      __syncthreads();
-      continue;
-    }
+    if (ctl->done) continue;  // uniform over the warp
+    const int cur = ctl->cur, nbuf = ctl->nbuf;
+    // FP32: one multiply by the stored 1/dx; FP64: the exact quotient
+    R dtdx;
+    if constexpr (sizeof(R) == 4) dtdx = (R)(ctl->dt * ctl->idx[0]);
+    else dtdx = ctl->dt / ctl->dx[0];
     const int nx = mb.nx;
-    const int base = tl.tile * T + threadIdx.x * K;
-    const R* __restrict__ q = (const R*)mb.q[s_cur];
-    R* __restrict__ qo = (R*)mb.q[(s_cur + 1) % s_nbuf];
+    const int base = tl.tile * T + (u % NW) * (32 * K) + lane * K;
+    const R* __restrict__ q = (const R*)mb.q[cur];
+    R* __restrict__ qo = (R*)mb.q[(cur + 1) % nbuf];
     const R* __restrict__ aux = (const R*)mb.aux;
-    const R dtdx = s_dtdx;
     R smax = R(0);
     int bad = 0;
     if (base < nx) {
@@ -301,7 +296,6 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? 8 : 1)
     }
     // per-warp atomics; the controllers run in the next launch
     fold_warp<R>(ctl, smax, bad);
-    __syncthreads();  // s_* are rewritten by the next tile
   }
 }
 
