@@ -15,13 +15,17 @@
 namespace claw {
 
 // ---------------------------------------------------------------------------
-// 1D: each thread owns K consecutive cells.  It loads them (16-byte vector
-// loads when the fields are aligned) plus two ghost/halo cells on each side,
-// prepares each cell once (CellPrep: the per-cell part of the Riemann solve),
-// then streams through its K + 3 interfaces with a three-interface register
-// window: solve interface j, limit interface j-1 with its neighbours, fold the
-// correction into the fluctuations and emit cell j-3.  No shared memory and
-// no block barrier: each warp reads its member's control values itself.
+// 1D: each lane owns K consecutive cells, loaded with 16-byte vector loads
+// when the fields are aligned (ghost cells by index remap).  It prepares its
+// cells once (CellPrep: the per-cell part of the Riemann solve) and solves the
+// K interfaces on their left, the first one with the prepared cell of the
+// lane below (a warp shuffle).  Limiting interface k needs the waves of
+// interfaces k-1 and k+1, and the update of the last cell needs the
+// fluctuation and correction of interface K: those come from the neighbour
+// lanes by shuffles too.  Lanes 0 and 31 are the warp's halo and write
+// nothing, so a warp writes 30 K cells and no cell is prepared or solved
+// twice inside it.  No shared memory and no block barrier: each warp reads
+// its member's control values itself.
 // ---------------------------------------------------------------------------
 template <typename R, int K>
 struct VecIO;
@@ -114,163 +118,171 @@ struct CellPrep<RpElasticity<R, 1>, R> {
   }
 };
 
+// limited second-order correction F (Eq. (lwflux)) of interface `c` from the
+// waves of its neighbours `l` and `r` (the upwind one per wave decides theta)
+template <class RP, typename R>
+__device__ __forceinline__ void limit1d(const MConsts<R>& C, const R (&Wl)[RP::MW][RP::M],
+                                        const R (&Wc)[RP::MW][RP::M], const R (&sc)[RP::MW],
+                                        const R (&Wr)[RP::MW][RP::M], R dtdx, R (&F)[RP::M]) {
+  constexpr int M = RP::M, MW = RP::MW;
+  if (C.order != 2) {
+#pragma unroll
+    for (int k = 0; k < M; ++k) F[k] = R(0);
+    return;
+  }
+  R dot[MW], nrm[MW];
+#pragma unroll
+  for (int p = 0; p < MW; ++p) {
+    R d = R(0), n2 = R(0);
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      const R up = sc[p] > R(0) ? Wl[p][k] : Wr[p][k];
+      d += up * Wc[p][k];
+      n2 += Wc[p][k] * Wc[p][k];
+    }
+    dot[p] = d;
+    nrm[p] = n2;
+  }
+  correction<RP, R>(C, Wc, sc, dot, nrm, dtdx, F);
+}
+
 template <class RP, typename R, int NT, int K>
 __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? 8 : 1)
     classic1d_kernel(const Member* __restrict__ members, const Tile* __restrict__ tiles,
                      int ntiles_total, const MConsts<R> C) {
   constexpr int M = RP::M, MW = RP::MW, MA = RP::MA;
   constexpr int MAS = MA > 0 ? MA : 1;
-  constexpr int T = NT * K;
-  constexpr int NW = NT / 32;  // warp units per tile
+  constexpr int NW = NT / 32;      // warp units per tile
+  constexpr int WC = 30 * K;       // cells a warp unit writes (lanes 1..30)
+  constexpr int T = NW * WC;       // cells per tile
+  constexpr unsigned FULL = 0xffffffffu;
   using CP = CellPrep<RP, R>;
   using Cell = typename CP::Cell;
+  constexpr int NCR = sizeof(Cell) / sizeof(R);
+  static_assert(NCR * sizeof(R) == sizeof(Cell), "Cell holds values of type R only");
   const int lane = threadIdx.x & 31;
 
-  // Each warp walks its own units (a quarter tile of 32 K cells at NT = 128)
-  // and reads the control values itself: no block barrier, so the warps of a
-  // block overlap one another's loads, arithmetic and stores.
+  // Each warp walks its own units and reads the control values itself: no
+  // block barrier, so the warps of a block overlap one another's loads,
+  // arithmetic and stores.
   const int nunits = ntiles_total * NW;
   for (int u = blockIdx.x * NW + (threadIdx.x >> 5); u < nunits; u += gridDim.x * NW) {
     const Tile tl = tiles ? tiles[u / NW] : Tile{0, u / NW};
     const Member& mb = members[tl.member];
     DevCtl* ctl = mb.ctl;
-    if (ctl->done) continue;  // uniform over the warp
+    const int nx = mb.nx;
+    const int ustart = tl.tile * T + (u % NW) * WC;
+    if (ctl->done || ustart >= nx) continue;  // uniform over the warp
     const int cur = ctl->cur, nbuf = ctl->nbuf;
     // FP32: one multiply by the stored 1/dx; FP64: the exact quotient
     R dtdx;
     if constexpr (sizeof(R) == 4) dtdx = (R)(ctl->dt * ctl->idx[0]);
     else dtdx = ctl->dt / ctl->dx[0];
-    const int nx = mb.nx;
-    const int base = tl.tile * T + (u % NW) * (32 * K) + lane * K;
     const R* __restrict__ q = (const R*)mb.q[cur];
     R* __restrict__ qo = (R*)mb.q[(cur + 1) % nbuf];
     const R* __restrict__ aux = (const R*)mb.aux;
+
+    // lane l holds cells g0 .. g0+K-1; lanes 0 and 31 are the unit's halo
+    const int g0 = ustart + (lane - 1) * K;
+    const bool inside = g0 >= 0 && g0 + K <= nx;
+    const bool rows16 = ((size_t)nx * sizeof(R)) % 16 == 0;  // every field 16-B aligned
+    const bool q_ok = ((((size_t)q) | ((size_t)qo)) & 15) == 0 && (M == 1 || rows16);
+    const bool a_ok = MA == 0 || ((((size_t)aux) & 15) == 0 && (MA == 1 || rows16));
+    const bool vec = inside && q_ok && a_ok;
+    R qa[K][M];
+    R aa[K][MAS];
+    if (vec) {
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+        R v[K];
+        VecIO<R, K>::load(q + (size_t)k * nx + g0, v);
+#pragma unroll
+        for (int c = 0; c < K; ++c) qa[c][k] = v[c];
+      }
+#pragma unroll
+      for (int k = 0; k < MA; ++k) {
+        R v[K];
+        VecIO<R, K>::load(aux + (size_t)k * nx + g0, v);
+#pragma unroll
+        for (int c = 0; c < K; ++c) aa[c][k] = v[c];
+      }
+    } else {
+      // ghost cells by remap; cells beyond the two-cell ghost layer are
+      // clamped into it (only halo lanes hold them and nothing reads them)
+#pragma unroll
+      for (int c = 0; c < K; ++c) {
+        const int gi = max(-2, min(g0 + c, nx + 1));
+        load_cell<M, R>(C, q, nx, 1, gi, 0, RP::WALL_X, -1, qa[c]);
+        if (MA > 0) load_aux<MA, R>(C, aux, nx, 1, gi, 0, aa[c]);
+      }
+    }
+
+    // each cell prepared once; interface k lies between cells k-1 and k
+    // (global index g0+k), its left cell from the lane below
+    Cell pc[K];
+#pragma unroll
+    for (int c = 0; c < K; ++c) CP::prep(C, qa[c], aa[c], pc[c]);
+    Cell left;
+    {
+      const R* a = reinterpret_cast<const R*>(&pc[K - 1]);
+      R* b = reinterpret_cast<R*>(&left);
+#pragma unroll
+      for (int i = 0; i < NCR; ++i) b[i] = __shfl_up_sync(FULL, a[i], 1);
+    }
+    R W[K][MW][M], s[K][MW], am[K][M], ap[K][M];
+    CP::solve(C, left, pc[0], W[0], s[0], am[0], ap[0]);
+#pragma unroll
+    for (int k = 1; k < K; ++k) CP::solve(C, pc[k - 1], pc[k], W[k], s[k], am[k], ap[k]);
+
+    // max speed over the unit's interfaces ustart .. ustart+WC (and <= nx)
     R smax = R(0);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int gi = g0 + k;
+      if (gi >= ustart && gi <= ustart + WC && gi <= nx) {
+#pragma unroll
+        for (int p = 0; p < MW; ++p) smax = nanmax(smax, (R)fabs(s[k][p]));
+      }
+    }
+
+    // waves of interface -1 (lane below) and K (lane above)
+    R Wm[MW][M], Wp[MW][M], sp[MW], amK[M];
+#pragma unroll
+    for (int p = 0; p < MW; ++p) {
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+        Wm[p][k] = __shfl_up_sync(FULL, W[K - 1][p][k], 1);
+        Wp[p][k] = __shfl_down_sync(FULL, W[0][p][k], 1);
+      }
+      sp[p] = __shfl_down_sync(FULL, s[0][p], 1);
+    }
+#pragma unroll
+    for (int k = 0; k < M; ++k) amK[k] = __shfl_down_sync(FULL, am[0][k], 1);
+
+    // limit interfaces 0..K-1 (F of interface K comes from the lane above)
+    // and update each cell once both of its interfaces are limited:
+    // Q_c - dt/dx [(A+dQ - F)_{c-1/2} + (A-dQ + F)_{c+1/2}]
+    R qout[K][M], Fl[M], FK[M];
+    limit1d<RP, R>(C, Wm, W[0], s[0], K > 1 ? W[1] : Wp, dtdx, Fl);
+#pragma unroll
+    for (int k = 0; k < M; ++k) FK[k] = __shfl_down_sync(FULL, Fl[k], 1);
+#pragma unroll
+    for (int c = 1; c < K; ++c) {
+      R Fr[M];
+      limit1d<RP, R>(C, W[c - 1], W[c], s[c], c + 1 < K ? W[c + 1] : Wp, dtdx, Fr);
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+        qout[c - 1][k] = qa[c - 1][k] - dtdx * ((ap[c - 1][k] - Fl[k]) + (am[c][k] + Fr[k]));
+        Fl[k] = Fr[k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < M; ++k)
+      qout[K - 1][k] = qa[K - 1][k] - dtdx * ((ap[K - 1][k] - Fl[k]) + (amK[k] + FK[k]));
+
     int bad = 0;
-    if (base < nx) {
-      // raw cells base-2 .. base+K+1 ; qa[c] is cell base-2+c
-      R qa[K + 4][M];
-      R aa[K + 4][MAS];
-      const bool full = base + K <= nx;
-      const bool rows16 = ((size_t)nx * sizeof(R)) % 16 == 0;  // every field 16-B aligned
-      const bool q_ok = ((((size_t)q) | ((size_t)qo)) & 15) == 0 && (M == 1 || rows16);
-      const bool a_ok = MA == 0 || ((((size_t)aux) & 15) == 0 && (MA == 1 || rows16));
-      const bool vec = full && q_ok && a_ok;
-      if (vec) {
-#pragma unroll
-        for (int k = 0; k < M; ++k) {
-          R v[K];
-          VecIO<R, K>::load(q + (size_t)k * nx + base, v);
-#pragma unroll
-          for (int c = 0; c < K; ++c) qa[c + 2][k] = v[c];
-        }
-        if (MA > 0) {
-#pragma unroll
-          for (int k = 0; k < MA; ++k) {
-            R v[K];
-            VecIO<R, K>::load(aux + (size_t)k * nx + base, v);
-#pragma unroll
-            for (int c = 0; c < K; ++c) aa[c + 2][k] = v[c];
-          }
-        }
-      } else {
-#pragma unroll
-        for (int c = 0; c < K; ++c) {
-          load_cell<M, R>(C, q, nx, 1, min(base + c, nx + 1), 0, RP::WALL_X, -1, qa[c + 2]);
-          if (MA > 0) load_aux<MA, R>(C, aux, nx, 1, min(base + c, nx + 1), 0, aa[c + 2]);
-        }
-      }
-      if (base >= 2 && base + K + 2 <= nx) {
-        // halo cells inside the grid: plain loads
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          const int c = h < 2 ? h : K + h;  // local slots 0,1 and K+2,K+3
-          const size_t gi = (size_t)(base - 2 + c);
-#pragma unroll
-          for (int k = 0; k < M; ++k) qa[c][k] = __ldg(q + (size_t)k * nx + gi);
-#pragma unroll
-          for (int k = 0; k < MA; ++k) aa[c][k] = __ldg(aux + (size_t)k * nx + gi);
-        }
-      } else {
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          const int c = h < 2 ? h : K + h;
-          const int gi = min(base - 2 + c, nx + 1);
-          load_cell<M, R>(C, q, nx, 1, gi, 0, RP::WALL_X, -1, qa[c]);
-          if (MA > 0) load_aux<MA, R>(C, aux, nx, 1, gi, 0, aa[c]);
-        }
-      }
-      // streaming window over interfaces jj = 0..K+2 (interface jj lies between
-      // qa[jj] and qa[jj+1], global index base-1+jj)
-      R W0[MW][M], W1[MW][M], W2[MW][M];  // interfaces jj-2, jj-1, jj
-      R s1[MW], s2[MW];
-      R am1[M], ap1[M], am2[M], ap2[M];
-      R Ap_prev[M];  // A^+ dQ - F of the interface left of the next cell
-      R qout[K][M];
-      Cell cl, cr;
-      CP::prep(C, qa[0], aa[0], cl);
-#pragma unroll
-      for (int jj = 0; jj < K + 3; ++jj) {
-        if (jj >= 1) {
-#pragma unroll
-          for (int p = 0; p < MW; ++p) {
-            s1[p] = s2[p];
-#pragma unroll
-            for (int k = 0; k < M; ++k) {
-              W0[p][k] = W1[p][k];
-              W1[p][k] = W2[p][k];
-            }
-          }
-#pragma unroll
-          for (int k = 0; k < M; ++k) {
-            am1[k] = am2[k];
-            ap1[k] = ap2[k];
-          }
-        }
-        CP::prep(C, qa[jj + 1], aa[jj + 1], cr);
-        CP::solve(C, cl, cr, W2, s2, am2, ap2);
-        cl = cr;
-        {
-          const int gj = base - 1 + jj;
-          if (jj >= 1 && jj <= K + 1 && gj <= nx) {
-#pragma unroll
-            for (int p = 0; p < MW; ++p) smax = nanmax(smax, (R)fabs(s2[p]));
-          }
-        }
-        if (jj >= 2) {
-          // limit interface jj-1 with neighbours jj-2 and jj
-          R F[M];
-          if (C.order == 2) {
-            R dot[MW], nrm[MW];
-#pragma unroll
-            for (int p = 0; p < MW; ++p) {
-              R d = R(0), n2 = R(0);
-#pragma unroll
-              for (int k = 0; k < M; ++k) {
-                const R up = s1[p] > R(0) ? W0[p][k] : W2[p][k];
-                d += up * W1[p][k];
-                n2 += W1[p][k] * W1[p][k];
-              }
-              dot[p] = d;
-              nrm[p] = n2;
-            }
-            correction<RP, R>(C, W1, s1, dot, nrm, dtdx, F);
-          } else {
-#pragma unroll
-            for (int k = 0; k < M; ++k) F[k] = R(0);
-          }
-          // cell jj-3 (local) lies between interfaces jj-2 and jj-1
-          if (jj >= 3) {
-#pragma unroll
-            for (int k = 0; k < M; ++k)
-              qout[jj - 3][k] = qa[jj - 1][k] - dtdx * (Ap_prev[k] + (am1[k] + F[k]));
-          }
-#pragma unroll
-          for (int k = 0; k < M; ++k) Ap_prev[k] = ap1[k] - F[k];
-        }
-      }
-      // store cells base .. base+K-1
-      if (vec) {
+    if (lane >= 1 && lane <= 30) {
+      if (vec && g0 + K <= ustart + WC) {
 #pragma unroll
         for (int k = 0; k < M; ++k) {
           R v[K];
@@ -279,16 +291,16 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? 8 : 1)
             v[c] = qout[c][k];
             bad |= !isfinite(v[c]);
           }
-          VecIO<R, K>::store(qo + (size_t)k * nx + base, v);
+          VecIO<R, K>::store(qo + (size_t)k * nx + g0, v);
         }
       } else {
 #pragma unroll
         for (int c = 0; c < K; ++c) {
-          if (base + c < nx) {
+          if (g0 + c < nx) {
 #pragma unroll
             for (int k = 0; k < M; ++k) {
               bad |= !isfinite(qout[c][k]);
-              qo[(size_t)k * nx + base + c] = qout[c][k];
+              qo[(size_t)k * nx + g0 + c] = qout[c][k];
             }
           }
         }

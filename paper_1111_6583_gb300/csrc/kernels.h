@@ -52,7 +52,8 @@ struct KernelSet {
 // tile geometry shared by the host (tile tables) and the kernels
 constexpr int kClassic1dThreads = 128;
 constexpr int classic1d_K(int) { return 4; }  // cells per thread (FP64 and FP32)
-constexpr int classic1d_T(int prec) { return kClassic1dThreads * classic1d_K(prec); }
+// a warp writes the cells of its lanes 1..30 (lanes 0 and 31 hold its halo)
+constexpr int classic1d_T(int prec) { return kClassic1dThreads / 32 * 30 * classic1d_K(prec); }
 inline int classic1d_tiles(int nx, int prec) {
   return (nx + classic1d_T(prec) - 1) / classic1d_T(prec);
 }
