@@ -27,6 +27,12 @@ namespace claw {
 // twice inside it.  No shared memory and no block barrier: each warp reads
 // its member's control values itself.
 // ---------------------------------------------------------------------------
+// cache hint: fetch the 128-byte line holding p into L1 (no register
+// result; p must lie inside an allocation)
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 template <typename R, int K>
 struct VecIO;
 template <>
@@ -146,7 +152,7 @@ __device__ __forceinline__ void limit1d(const MConsts<R>& C, const R (&Wl)[RP::M
   correction<RP, R>(C, Wc, sc, dot, nrm, dtdx, F);
 }
 
-template <class RP, typename R, int NT, int K>
+template <class RP, typename R, int NT, int K, int SPW>
 __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? 8 : 1)
     classic1d_kernel(const Member* __restrict__ members, const Tile* __restrict__ tiles,
                      int ntiles_total, const MConsts<R> C) {
@@ -162,17 +168,25 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? 8 : 1)
   static_assert(NCR * sizeof(R) == sizeof(Cell), "Cell holds values of type R only");
   const int lane = threadIdx.x & 31;
 
-  // Each warp walks its own units and reads the control values itself: no
-  // block barrier, so the warps of a block overlap one another's loads,
-  // arithmetic and stores.
-  const int nunits = ntiles_total * NW;
-  for (int u = blockIdx.x * NW + (threadIdx.x >> 5); u < nunits; u += gridDim.x * NW) {
-    const Tile tl = tiles ? tiles[u / NW] : Tile{0, u / NW};
+  // A warp takes a work item: SPW consecutive units of one tile (SPW = NW,
+  // or 1 when the tiles are too few to give every resident warp an item).  It
+  // reads the member and control values once per item, asks L1 for each next
+  // unit's cells while it works on the current one, and folds its speeds into
+  // the control block once per item.  No block barrier: the warps of a block
+  // overlap one another's loads, arithmetic and stores.
+  constexpr int spw = SPW;
+  static_assert(NW % SPW == 0, "an item is a whole number of a tile's units");
+  constexpr int ipt = NW / spw;  // items per tile
+  const int nitems = ntiles_total * ipt;
+  for (int it = blockIdx.x * NW + (threadIdx.x >> 5); it < nitems; it += gridDim.x * NW) {
+    const Tile tl = tiles ? tiles[it / ipt] : Tile{0, it / ipt};
     const Member& mb = members[tl.member];
     DevCtl* ctl = mb.ctl;
+    if (ctl->done) continue;  // uniform over the warp
     const int nx = mb.nx;
-    const int ustart = tl.tile * T + (u % NW) * WC;
-    if (ctl->done || ustart >= nx) continue;  // uniform over the warp
+    const int sub0 = (it % ipt) * spw;
+    const int t0 = tl.tile * T;
+    if (t0 + sub0 * WC >= nx) continue;
     const int cur = ctl->cur, nbuf = ctl->nbuf;
     // FP32: one multiply by the stored 1/dx; FP64: the exact quotient
     R dtdx;
@@ -181,131 +195,145 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? 8 : 1)
     const R* __restrict__ q = (const R*)mb.q[cur];
     R* __restrict__ qo = (R*)mb.q[(cur + 1) % nbuf];
     const R* __restrict__ aux = (const R*)mb.aux;
-
-    // lane l holds cells g0 .. g0+K-1; lanes 0 and 31 are the unit's halo
-    const int g0 = ustart + (lane - 1) * K;
-    const bool inside = g0 >= 0 && g0 + K <= nx;
     const bool rows16 = ((size_t)nx * sizeof(R)) % 16 == 0;  // every field 16-B aligned
     const bool q_ok = ((((size_t)q) | ((size_t)qo)) & 15) == 0 && (M == 1 || rows16);
     const bool a_ok = MA == 0 || ((((size_t)aux) & 15) == 0 && (MA == 1 || rows16));
-    const bool vec = inside && q_ok && a_ok;
-    R qa[K][M];
-    R aa[K][MAS];
-    if (vec) {
-#pragma unroll
-      for (int k = 0; k < M; ++k) {
-        R v[K];
-        VecIO<R, K>::load(q + (size_t)k * nx + g0, v);
-#pragma unroll
-        for (int c = 0; c < K; ++c) qa[c][k] = v[c];
-      }
-#pragma unroll
-      for (int k = 0; k < MA; ++k) {
-        R v[K];
-        VecIO<R, K>::load(aux + (size_t)k * nx + g0, v);
-#pragma unroll
-        for (int c = 0; c < K; ++c) aa[c][k] = v[c];
-      }
-    } else {
-      // ghost cells by remap; cells beyond the two-cell ghost layer are
-      // clamped into it (only halo lanes hold them and nothing reads them)
-#pragma unroll
-      for (int c = 0; c < K; ++c) {
-        const int gi = max(-2, min(g0 + c, nx + 1));
-        load_cell<M, R>(C, q, nx, 1, gi, 0, RP::WALL_X, -1, qa[c]);
-        if (MA > 0) load_aux<MA, R>(C, aux, nx, 1, gi, 0, aa[c]);
-      }
-    }
-
-    // each cell prepared once; interface k lies between cells k-1 and k
-    // (global index g0+k), its left cell from the lane below
-    Cell pc[K];
-#pragma unroll
-    for (int c = 0; c < K; ++c) CP::prep(C, qa[c], aa[c], pc[c]);
-    Cell left;
-    {
-      const R* a = reinterpret_cast<const R*>(&pc[K - 1]);
-      R* b = reinterpret_cast<R*>(&left);
-#pragma unroll
-      for (int i = 0; i < NCR; ++i) b[i] = __shfl_up_sync(FULL, a[i], 1);
-    }
-    R W[K][MW][M], s[K][MW], am[K][M], ap[K][M];
-    CP::solve(C, left, pc[0], W[0], s[0], am[0], ap[0]);
-#pragma unroll
-    for (int k = 1; k < K; ++k) CP::solve(C, pc[k - 1], pc[k], W[k], s[k], am[k], ap[k]);
-
-    // max speed over the unit's interfaces ustart .. ustart+WC (and <= nx)
     R smax = R(0);
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const int gi = g0 + k;
-      if (gi >= ustart && gi <= ustart + WC && gi <= nx) {
-#pragma unroll
-        for (int p = 0; p < MW; ++p) smax = nanmax(smax, (R)fabs(s[k][p]));
-      }
-    }
-
-    // waves of interface -1 (lane below) and K (lane above)
-    R Wm[MW][M], Wp[MW][M], sp[MW], amK[M];
-#pragma unroll
-    for (int p = 0; p < MW; ++p) {
-#pragma unroll
-      for (int k = 0; k < M; ++k) {
-        Wm[p][k] = __shfl_up_sync(FULL, W[K - 1][p][k], 1);
-        Wp[p][k] = __shfl_down_sync(FULL, W[0][p][k], 1);
-      }
-      sp[p] = __shfl_down_sync(FULL, s[0][p], 1);
-    }
-#pragma unroll
-    for (int k = 0; k < M; ++k) amK[k] = __shfl_down_sync(FULL, am[0][k], 1);
-
-    // limit interfaces 0..K-1 (F of interface K comes from the lane above)
-    // and update each cell once both of its interfaces are limited:
-    // Q_c - dt/dx [(A+dQ - F)_{c-1/2} + (A-dQ + F)_{c+1/2}]
-    R qout[K][M], Fl[M], FK[M];
-    limit1d<RP, R>(C, Wm, W[0], s[0], K > 1 ? W[1] : Wp, dtdx, Fl);
-#pragma unroll
-    for (int k = 0; k < M; ++k) FK[k] = __shfl_down_sync(FULL, Fl[k], 1);
-#pragma unroll
-    for (int c = 1; c < K; ++c) {
-      R Fr[M];
-      limit1d<RP, R>(C, W[c - 1], W[c], s[c], c + 1 < K ? W[c + 1] : Wp, dtdx, Fr);
-#pragma unroll
-      for (int k = 0; k < M; ++k) {
-        qout[c - 1][k] = qa[c - 1][k] - dtdx * ((ap[c - 1][k] - Fl[k]) + (am[c][k] + Fr[k]));
-        Fl[k] = Fr[k];
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < M; ++k)
-      qout[K - 1][k] = qa[K - 1][k] - dtdx * ((ap[K - 1][k] - Fl[k]) + (amK[k] + FK[k]));
-
     int bad = 0;
-    if (lane >= 1 && lane <= 30) {
-      if (vec && g0 + K <= ustart + WC) {
+    for (int sub = sub0; sub < sub0 + spw; ++sub) {
+      const int ustart = t0 + sub * WC;
+      if (ustart >= nx) break;  // uniform over the warp
+
+      // lane l holds cells g0 .. g0+K-1; lanes 0 and 31 are the unit's halo
+      const int g0 = ustart + (lane - 1) * K;
+      if (sub + 1 < sub0 + spw) {
+        // L1 prefetch of this lane's cells of the next unit
+        const int gn = g0 + WC;
+        if (gn >= 0 && gn < nx) {
+#pragma unroll
+          for (int f = 0; f < M + MA; ++f)
+            prefetch_l1(f < M ? (const void*)(q + (size_t)f * nx + gn)
+                              : (const void*)(aux + (size_t)(f - M) * nx + gn));
+        }
+      }
+      const bool inside = g0 >= 0 && g0 + K <= nx;
+      const bool vec = inside && q_ok && a_ok;
+      R qa[K][M];
+      R aa[K][MAS];
+      if (vec) {
 #pragma unroll
         for (int k = 0; k < M; ++k) {
           R v[K];
+          VecIO<R, K>::load(q + (size_t)k * nx + g0, v);
 #pragma unroll
-          for (int c = 0; c < K; ++c) {
-            v[c] = qout[c][k];
-            bad |= !isfinite(v[c]);
-          }
-          VecIO<R, K>::store(qo + (size_t)k * nx + g0, v);
+          for (int c = 0; c < K; ++c) qa[c][k] = v[c];
+        }
+#pragma unroll
+        for (int k = 0; k < MA; ++k) {
+          R v[K];
+          VecIO<R, K>::load(aux + (size_t)k * nx + g0, v);
+#pragma unroll
+          for (int c = 0; c < K; ++c) aa[c][k] = v[c];
         }
       } else {
+        // ghost cells by remap; cells beyond the two-cell ghost layer are
+        // clamped into it (only halo lanes hold them and nothing reads them)
 #pragma unroll
         for (int c = 0; c < K; ++c) {
-          if (g0 + c < nx) {
+          const int gi = max(-2, min(g0 + c, nx + 1));
+          load_cell<M, R>(C, q, nx, 1, gi, 0, RP::WALL_X, -1, qa[c]);
+          if (MA > 0) load_aux<MA, R>(C, aux, nx, 1, gi, 0, aa[c]);
+        }
+      }
+
+      // each cell prepared once; interface k lies between cells k-1 and k
+      // (global index g0+k), its left cell from the lane below
+      Cell pc[K];
 #pragma unroll
-            for (int k = 0; k < M; ++k) {
-              bad |= !isfinite(qout[c][k]);
-              qo[(size_t)k * nx + g0 + c] = qout[c][k];
+      for (int c = 0; c < K; ++c) CP::prep(C, qa[c], aa[c], pc[c]);
+      Cell left;
+      {
+        const R* a = reinterpret_cast<const R*>(&pc[K - 1]);
+        R* b = reinterpret_cast<R*>(&left);
+#pragma unroll
+        for (int i = 0; i < NCR; ++i) b[i] = __shfl_up_sync(FULL, a[i], 1);
+      }
+      R W[K][MW][M], s[K][MW], am[K][M], ap[K][M];
+      CP::solve(C, left, pc[0], W[0], s[0], am[0], ap[0]);
+#pragma unroll
+      for (int k = 1; k < K; ++k) CP::solve(C, pc[k - 1], pc[k], W[k], s[k], am[k], ap[k]);
+
+      // max speed over the unit's interfaces ustart .. ustart+WC (and <= nx)
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int gi = g0 + k;
+        if (gi >= ustart && gi <= ustart + WC && gi <= nx) {
+#pragma unroll
+          for (int p = 0; p < MW; ++p) smax = nanmax(smax, (R)fabs(s[k][p]));
+        }
+      }
+
+      // waves of interface -1 (lane below) and K (lane above)
+      R Wm[MW][M], Wp[MW][M], sp[MW], amK[M];
+#pragma unroll
+      for (int p = 0; p < MW; ++p) {
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+          Wm[p][k] = __shfl_up_sync(FULL, W[K - 1][p][k], 1);
+          Wp[p][k] = __shfl_down_sync(FULL, W[0][p][k], 1);
+        }
+        sp[p] = __shfl_down_sync(FULL, s[0][p], 1);
+      }
+#pragma unroll
+      for (int k = 0; k < M; ++k) amK[k] = __shfl_down_sync(FULL, am[0][k], 1);
+
+      // limit interfaces 0..K-1 (F of interface K comes from the lane above)
+      // and update each cell once both of its interfaces are limited:
+      // Q_c - dt/dx [(A+dQ - F)_{c-1/2} + (A-dQ + F)_{c+1/2}]
+      R qout[K][M], Fl[M], FK[M];
+      limit1d<RP, R>(C, Wm, W[0], s[0], K > 1 ? W[1] : Wp, dtdx, Fl);
+#pragma unroll
+      for (int k = 0; k < M; ++k) FK[k] = __shfl_down_sync(FULL, Fl[k], 1);
+#pragma unroll
+      for (int c = 1; c < K; ++c) {
+        R Fr[M];
+        limit1d<RP, R>(C, W[c - 1], W[c], s[c], c + 1 < K ? W[c + 1] : Wp, dtdx, Fr);
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+          qout[c - 1][k] = qa[c - 1][k] - dtdx * ((ap[c - 1][k] - Fl[k]) + (am[c][k] + Fr[k]));
+          Fl[k] = Fr[k];
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < M; ++k)
+        qout[K - 1][k] = qa[K - 1][k] - dtdx * ((ap[K - 1][k] - Fl[k]) + (amK[k] + FK[k]));
+
+      if (lane >= 1 && lane <= 30) {
+        if (vec && g0 + K <= ustart + WC) {
+#pragma unroll
+          for (int k = 0; k < M; ++k) {
+            R v[K];
+#pragma unroll
+            for (int c = 0; c < K; ++c) {
+              v[c] = qout[c][k];
+              bad |= !isfinite(v[c]);
+            }
+            VecIO<R, K>::store(qo + (size_t)k * nx + g0, v);
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < K; ++c) {
+            if (g0 + c < nx) {
+#pragma unroll
+              for (int k = 0; k < M; ++k) {
+                bad |= !isfinite(qout[c][k]);
+                qo[(size_t)k * nx + g0 + c] = qout[c][k];
+              }
             }
           }
         }
       }
-    }
+    }  // units of the item
     // per-warp atomics; the controllers run in the next launch
     fold_warp<R>(ctl, smax, bad);
   }

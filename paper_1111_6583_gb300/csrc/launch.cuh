@@ -215,8 +215,17 @@ struct Launchers {
       return cudaErrorNotSupported;
     } else if constexpr (ND == 1) {
       constexpr int K = sizeof(R) == 8 ? classic1d_K(0) : classic1d_K(1);
-      constexpr auto kern = classic1d_kernel<RP, R, kClassic1dThreads, K>;
-      kern<<<persistent_grid<kern>(kClassic1dThreads, a.ntiles_total), kClassic1dThreads, 0,
+      // a warp takes a whole tile when the tiles fill every resident warp
+      // (blocks x NW), else a single unit
+      constexpr int NW = kClassic1dThreads / 32;
+      constexpr auto kt = classic1d_kernel<RP, R, kClassic1dThreads, K, NW>;
+      constexpr auto ku = classic1d_kernel<RP, R, kClassic1dThreads, K, 1>;
+      const long long cap = (long long)persistent_grid<kt>(kClassic1dThreads, 1 << 30) * NW;
+      if (a.ntiles_total >= cap)
+        kt<<<persistent_grid<kt>(kClassic1dThreads, (a.ntiles_total + NW - 1) / NW),
+             kClassic1dThreads, 0, a.stream>>>(a.members, a.tiles, a.ntiles_total, C);
+      else
+        ku<<<persistent_grid<ku>(kClassic1dThreads, a.ntiles_total), kClassic1dThreads, 0,
              a.stream>>>(a.members, a.tiles, a.ntiles_total, C);
       const cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
