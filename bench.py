@@ -321,13 +321,16 @@ def bench_elasticity(members, steps, fp64_sample):
     return out
 
 
-def bench_serving(nreq, prec, rate=200.0, budget=120 << 30):
+def bench_serving(nreq, prec, rate=200.0, budget=120 << 30, policy="srw", min_cells=1 << 23):
     """Poisson stream of 2D shallow-water solves through the continuous-
-    batching server; latency = completion - arrival (server clock)."""
+    batching server; latency = completion - arrival (server clock).  policy:
+    the server's schedule ('srw': shortest remaining work first, min_cells
+    cells per attempt; 'all': every running request in every attempt)."""
     from paper_1111_6583_gb300 import claw
     from paper_1111_6583_gb300 import workloads as wl
     stream_reqs = wl.serving_stream(nreq, rate)
     sv = claw.Server(wl.sw_humps_2d(64, [], 1.0), prec, budget_bytes=budget, max_slots=512)
+    sv.schedule(policy, min_cells)
     specs = [wl.sw_humps_2d(r["n"], r["humps"], r["t_end"]) for r in stream_reqs]
     t0 = claw.clock()
     pending = {}
@@ -342,19 +345,19 @@ def bench_serving(nreq, prec, rate=200.0, budget=120 << 30):
             nxt += 1
         if pending:
             sv.pump(8)
-            for tk in list(pending):
+            for tk in sv.take_done():
                 r = sv.poll(tk, want_state=False)
-                if r is not None:
-                    i = pending.pop(tk)
-                    lat.append(r["t_done"] - (t0 + stream_reqs[i]["arrival"]))
-                    n = specs[i]["n"][0]
-                    cell_updates += n * n * r["steps"]
+                i = pending.pop(tk)
+                lat.append(r["t_done"] - (t0 + stream_reqs[i]["arrival"]))
+                n = specs[i]["n"][0]
+                cell_updates += n * n * r["steps"]
         elif nxt < nreq:
             time.sleep(max(0.0, min(0.002, stream_reqs[nxt]["arrival"] - now)))
     wall = claw.clock() - t0
     sv.close()
     lat = np.array(lat)
-    return {"requests": nreq, "rate_per_s": rate, "prec": prec,
+    return {"requests": nreq, "rate_per_s": rate, "prec": prec, "schedule": policy,
+            "min_cells": min_cells if policy == "srw" else None,
             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
             "throughput_cell_updates_per_s": cell_updates / wall, "wall_s": wall}
 
@@ -722,6 +725,8 @@ def main():
             line["batched_elasticity"] = {"error": repr(ex)}
         try:
             line["serving"] = bench_serving(args.serve_requests, "fp32")
+            line["serving_every_request_per_attempt"] = bench_serving(
+                args.serve_requests, "fp32", policy="all")
         except Exception as ex:
             line["serving"] = {"error": repr(ex)}
         line["cpu_baseline"] = cpu_baseline_sw2d(args.n)

@@ -137,6 +137,8 @@ typedef struct {
 typedef struct claw_solver claw_solver;
 typedef struct claw_batch claw_batch;
 typedef struct claw_server claw_server;
+/* server schedules (claw_server_schedule) */
+enum { CLAW_SCHED_ALL = 0, CLAW_SCHED_SRW = 1 };
 
 /* Fill *m with the defaults for a Riemann solver in ndim dimensions:
  * classic, MC limiter, order 2, transverse 2, FP64, CFL 0.9/1.0, walls...
@@ -257,10 +259,23 @@ claw_status claw_server_create(const claw_method* m, size_t hbm_budget_bytes, in
  * CLAW_EBUDGET when the request alone exceeds the budget. */
 claw_status claw_server_submit(claw_server* sv, const claw_grid* g, const void* q0_host,
                                const void* aux_host, double t_end, uint64_t* ticket);
-/* Drive the server: admit queued requests that fit, run one fused step for
- * all running requests, retire finished ones.  Returns the number of
- * running requests in *running. */
+/* Drive the server: admit queued requests that fit (first come, first
+ * served), take `steps` fused step attempts over the requests the schedule
+ * picks (below), retire finished ones.  Returns the number of running and
+ * queued requests in *running and *queued (either may be NULL). */
 claw_status claw_server_pump(claw_server* sv, int steps, int* running, int* queued);
+/* Which running requests a pump steps.  CLAW_SCHED_ALL: every running request
+ * in every attempt.  CLAW_SCHED_SRW (the default, min_cells = 2^23): shortest
+ * remaining work first -- requests not yet stepped, then any left out of 16
+ * pumps in a row, then the rest by estimated remaining cell updates (cells x
+ * (t_end - t) / dt from the last pump), until the picked requests hold
+ * min_cells cells.  The schedule changes only when a request advances, never
+ * its arithmetic: each result is the same under either policy. */
+claw_status claw_server_schedule(claw_server* sv, int policy, int64_t min_cells);
+/* Tickets of the requests that finished since the last call, oldest first,
+ * at most cap of them (the rest stay for the next call); *n = how many were
+ * written.  A client polls these instead of every ticket it holds. */
+claw_status claw_server_take_done(claw_server* sv, uint64_t* tickets, int cap, int* n);
 /* Poll a ticket; when done, copies the final state to q_host_out (may be
  * NULL) and releases it.  CLAW_EBUSY while queued or running. */
 claw_status claw_server_poll(claw_server* sv, uint64_t ticket, void* q_host_out,

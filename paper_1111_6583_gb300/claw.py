@@ -26,6 +26,7 @@ RP = {"advection": 0, "acoustics": 1, "sw_roe": 2, "euler_roe": 3, "euler_hlle":
       "elasticity_fwave": 5, "euler_tracer": 6, "acoustics_vc": 7}
 SOURCE = {"none": 0, "axisymmetric": 1}
 SOURCE_SPLIT = {"godunov": 1, "strang": 2}
+SCHED = {"all": 0, "srw": 1}
 LIM = {"none": 0, "minmod": 1, "superbee": 2, "vanleer": 3, "mc": 4}
 BC = {"periodic": 0, "wall": 1, "extrap": 2, "inflow": 3}
 TIME_INTEGRATOR = {"ssp_rk3": 0, "ssp104": 1}
@@ -107,6 +108,9 @@ _SIGS = {
                                           _P(ctypes.c_uint64)]),
     "claw_server_pump": (ctypes.c_int, [_VP, ctypes.c_int, _P(ctypes.c_int), _P(ctypes.c_int)]),
     "claw_server_poll": (ctypes.c_int, [_VP, ctypes.c_uint64, _VP, _P(claw_req_info)]),
+    "claw_server_schedule": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int64]),
+    "claw_server_take_done": (ctypes.c_int, [_VP, _P(ctypes.c_uint64), ctypes.c_int,
+                                             _P(ctypes.c_int)]),
     "claw_server_destroy": (ctypes.c_int, [_VP]),
     "claw_sharp_step_noalloc": (ctypes.c_int, [_P(claw_method), _P(claw_grid), _VP, _VP, _VP,
                                                ctypes.c_double, _VP, _P(ctypes.c_double)]),
@@ -401,6 +405,18 @@ class Server:
         _check(st, self.h)
         self.shapes[t.value] = q0.shape
         return t.value
+
+    def schedule(self, policy="srw", min_cells=1 << 23):
+        """'all': every running request steps in every attempt; 'srw':
+        shortest remaining work first, min_cells cells per attempt."""
+        _check(load().claw_server_schedule(self.h, SCHED[policy], int(min_cells)), self.h)
+
+    def take_done(self, cap=1024):
+        """Tickets finished since the last call (oldest first)."""
+        buf = (ctypes.c_uint64 * cap)()
+        n = ctypes.c_int()
+        _check(load().claw_server_take_done(self.h, buf, int(cap), ctypes.byref(n)), self.h)
+        return [int(buf[i]) for i in range(n.value)]
 
     def pump(self, steps=8):
         r, qd = ctypes.c_int(), ctypes.c_int()

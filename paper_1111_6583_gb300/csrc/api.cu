@@ -1322,6 +1322,8 @@ struct Req {
   size_t dbytes = 0;
   size_t w3bytes = 0;  // per-face path: the request's face arrays
   Member mem{};
+  double rem = -1.0;   // estimated cell updates left (< 0: not stepped yet)
+  int idle = 0;        // pumps in a row this request was left out of
 };
 }  // namespace
 
@@ -1345,10 +1347,19 @@ struct claw_server {
   bool dirty = true;
   DevCtl* d_gather = nullptr;
   DevCtl* h_gather = nullptr;
-  int bw = 128, h = 16;
+  // 2D classic tile for every request: the shape the autotuner picks for a
+  // 1024 x 1024 FP32 grid, and the fastest of those tried on a mixed stream
+  int bw = 64, h = 21;
   int faces = 0;  // per-face classic path: kernels run request by request
   Tile* d_tile0 = nullptr;  // (member 0, t): source steps of one request at a time
   size_t cap_tile0 = 0;
+  // scheduling: the requests the step tables cover (d_smem, d_tiles, d_stiles)
+  int sched = CLAW_SCHED_SRW;
+  long long sched_cells = 1LL << 23;
+  std::vector<uint64_t> sel;
+  Member* d_smem = nullptr;
+  size_t cap_smem = 0;
+  std::deque<uint64_t> completed;  // finished, not yet handed out by take_done
   std::string err;
 };
 
@@ -1502,27 +1513,18 @@ claw_status claw_server_pump(claw_server* v, int steps, int* running, int* queue
     v->queue.pop_front();
     v->dirty = true;
   }
-  // 2. rebuild the member and tile tables when the running set changed
+  // 2. rebuild the member table of the running requests when the set changed
   if (v->dirty) {
     std::vector<Member> hm;
-    std::vector<Tile> ht, mt, hs;
-    for (size_t i = 0; i < v->running.size(); ++i) {
-      const Req& r = v->reqs[v->running[i]];
-      hm.push_back(r.mem);
-      if (!v->faces)
-        for (int t = 0; t < r.mem.ntiles; ++t) ht.push_back(Tile{(int)i, t});
-      if (v->m.source != CLAW_SOURCE_NONE)
-        for (int t = 0; t < maxspeed_tiles(r.mem.nx, r.mem.ny); ++t) hs.push_back(Tile{(int)i, t});
+    for (uint64_t t : v->running) hm.push_back(v->reqs[t].mem);
+    if (hm.size() > v->cap_mem) {
+      if (v->d_mem) VCK(cudaFreeAsync(v->d_mem, v->st));
+      v->cap_mem = std::max<size_t>(hm.size(), 2 * v->cap_mem);
+      VCK(cudaMallocAsync(&v->d_mem, sizeof(Member) * v->cap_mem, v->st));
     }
-    if (hs.size() > v->cap_stiles) {
-      if (v->d_stiles) VCK(cudaFreeAsync(v->d_stiles, v->st));
-      v->cap_stiles = std::max<size_t>(hs.size(), 2 * v->cap_stiles);
-      VCK(cudaMallocAsync(&v->d_stiles, sizeof(Tile) * v->cap_stiles, v->st));
-    }
-    if (!hs.empty())
-      VCK(cudaMemcpyAsync(v->d_stiles, hs.data(), sizeof(Tile) * hs.size(),
-                          cudaMemcpyHostToDevice, v->st));
-    v->nstiles = (int)hs.size();
+    if (!hm.empty())
+      VCK(cudaMemcpyAsync(v->d_mem, hm.data(), sizeof(Member) * hm.size(), cudaMemcpyHostToDevice,
+                          v->st));
     if (v->faces && v->m.source != CLAW_SOURCE_NONE) {
       size_t most = 1;
       for (uint64_t t : v->running) {
@@ -1540,24 +1542,6 @@ claw_status claw_server_pump(claw_server* v, int steps, int* running, int* queue
         VCK(cudaStreamSynchronize(v->st));  // t0 is a host temporary
       }
     }
-    if (hm.size() > v->cap_mem) {
-      if (v->d_mem) VCK(cudaFreeAsync(v->d_mem, v->st));
-      v->cap_mem = std::max<size_t>(hm.size(), 2 * v->cap_mem);
-      VCK(cudaMallocAsync(&v->d_mem, sizeof(Member) * v->cap_mem, v->st));
-    }
-    if (ht.size() > v->cap_tiles) {
-      if (v->d_tiles) VCK(cudaFreeAsync(v->d_tiles, v->st));
-      v->cap_tiles = std::max<size_t>(ht.size(), 2 * v->cap_tiles);
-      VCK(cudaMallocAsync(&v->d_tiles, sizeof(Tile) * v->cap_tiles, v->st));
-    }
-    if (!hm.empty()) {
-      VCK(cudaMemcpyAsync(v->d_mem, hm.data(), sizeof(Member) * hm.size(), cudaMemcpyHostToDevice,
-                          v->st));
-      if (!ht.empty())
-        VCK(cudaMemcpyAsync(v->d_tiles, ht.data(), sizeof(Tile) * ht.size(),
-                            cudaMemcpyHostToDevice, v->st));
-    }
-    v->ntiles = (int)ht.size();
     // first dt for the newly admitted requests
     if (!admitted.empty()) {
       std::vector<Tile> ms;
@@ -1577,28 +1561,100 @@ claw_status claw_server_pump(claw_server* v, int steps, int* running, int* queue
     }
     v->dirty = false;
   }
-  // 3. fused step attempts over every running request
+  // 3. choose the requests to step (every running one, or the least
+  // remaining work first until sched_cells cells are covered), rebuild the
+  // step tables when the choice changed, and run the fused step attempts
   if (!v->running.empty()) {
+    std::vector<uint64_t> sel;
+    if (v->sched == CLAW_SCHED_ALL) {
+      sel = v->running;
+    } else {
+      // not yet stepped first, then requests left out of kStarve pumps, then
+      // by remaining work; ties by ticket (arrival order)
+      constexpr int kStarve = 16;
+      std::vector<uint64_t> order = v->running;
+      auto key = [&](uint64_t t) {
+        const Req& r = v->reqs[t];
+        const int cls = r.rem < 0 ? 0 : (r.idle >= kStarve ? 1 : 2);
+        return std::make_tuple(cls, cls == 2 ? r.rem : 0.0, t);
+      };
+      std::sort(order.begin(), order.end(),
+                [&](uint64_t a, uint64_t b) { return key(a) < key(b); });
+      long long cells = 0;
+      for (uint64_t t : order) {
+        const Req& r = v->reqs[t];
+        if (cells >= v->sched_cells && r.rem >= 0 && r.idle < kStarve) continue;
+        sel.push_back(t);
+        cells += (long long)cells_of(r.g);
+      }
+      // keep the member order of the running list (tile tables stay stable)
+      std::vector<uint64_t> ordered;
+      for (uint64_t t : v->running)
+        if (std::find(sel.begin(), sel.end(), t) != sel.end()) ordered.push_back(t);
+      sel.swap(ordered);
+    }
+    if (sel != v->sel) {
+      std::vector<Member> hm;
+      std::vector<Tile> ht, hs;
+      for (size_t i = 0; i < sel.size(); ++i) {
+        const Req& r = v->reqs[sel[i]];
+        hm.push_back(r.mem);
+        if (!v->faces)
+          for (int t = 0; t < r.mem.ntiles; ++t) ht.push_back(Tile{(int)i, t});
+        if (v->m.source != CLAW_SOURCE_NONE)
+          for (int t = 0; t < maxspeed_tiles(r.mem.nx, r.mem.ny); ++t) hs.push_back(Tile{(int)i, t});
+      }
+      if (hm.size() > v->cap_smem) {
+        if (v->d_smem) VCK(cudaFreeAsync(v->d_smem, v->st));
+        v->cap_smem = std::max<size_t>(hm.size(), 2 * v->cap_smem);
+        VCK(cudaMallocAsync(&v->d_smem, sizeof(Member) * v->cap_smem, v->st));
+      }
+      VCK(cudaMemcpyAsync(v->d_smem, hm.data(), sizeof(Member) * hm.size(),
+                          cudaMemcpyHostToDevice, v->st));
+      if (ht.size() > v->cap_tiles) {
+        if (v->d_tiles) VCK(cudaFreeAsync(v->d_tiles, v->st));
+        v->cap_tiles = std::max<size_t>(ht.size(), 2 * v->cap_tiles);
+        VCK(cudaMallocAsync(&v->d_tiles, sizeof(Tile) * v->cap_tiles, v->st));
+      }
+      if (!ht.empty())
+        VCK(cudaMemcpyAsync(v->d_tiles, ht.data(), sizeof(Tile) * ht.size(),
+                            cudaMemcpyHostToDevice, v->st));
+      v->ntiles = (int)ht.size();
+      if (hs.size() > v->cap_stiles) {
+        if (v->d_stiles) VCK(cudaFreeAsync(v->d_stiles, v->st));
+        v->cap_stiles = std::max<size_t>(hs.size(), 2 * v->cap_stiles);
+        VCK(cudaMallocAsync(&v->d_stiles, sizeof(Tile) * v->cap_stiles, v->st));
+      }
+      if (!hs.empty())
+        VCK(cudaMemcpyAsync(v->d_stiles, hs.data(), sizeof(Tile) * hs.size(),
+                            cudaMemcpyHostToDevice, v->st));
+      v->nstiles = (int)hs.size();
+      v->sel = sel;
+    }
     for (int i = 0; i < steps; ++i) {
       if (v->faces) {
         // the per-face kernels take one member: request by request
-        for (size_t k = 0; k < v->running.size(); ++k) {
-          const Req& r = v->reqs[v->running[k]];
+        for (size_t k = 0; k < sel.size(); ++k) {
+          const Req& r = v->reqs[sel[k]];
           const int n3[3] = {r.mem.nx, r.mem.ny, 1};
-          VCK(launch_attempt(v->ks, v->m, v->d_mem + k, nullptr, r.mem.ntiles,
+          VCK(launch_attempt(v->ks, v->m, v->d_smem + k, nullptr, r.mem.ntiles,
                              v->consts.data(), v->bw, v->h, v->st, v->d_tile0,
                              maxspeed_tiles(r.mem.nx, r.mem.ny), 1, n3, r.mem.work3,
                              r.w3bytes));
         }
       } else {
-        VCK(launch_attempt(v->ks, v->m, v->d_mem, v->d_tiles, v->ntiles, v->consts.data(),
-                           v->bw, v->h, v->st, v->d_stiles, v->nstiles,
-                           (int)v->running.size()));
+        VCK(launch_attempt(v->ks, v->m, v->d_smem, v->d_tiles, v->ntiles, v->consts.data(),
+                           v->bw, v->h, v->st, v->d_stiles, v->nstiles, (int)sel.size()));
       }
     }
-    // 4. retire finished requests
+    // 4. retire finished requests; remaining-work estimates for the rest
     const int nr = (int)v->running.size();
-    std::vector<char> fin(nr, 0);
+    std::vector<char> fin(nr, 0), stepped(nr, 0);
+    for (int i = 0, j = 0; i < nr && j < (int)sel.size(); ++i)
+      if (v->running[i] == sel[j]) {
+        stepped[i] = 1;
+        ++j;
+      }
     for (int base = 0; base < nr; base += v->max_slots) {
       const int cnt = std::min(v->max_slots, nr - base);
       VCK(launch_gather_ctl(v->d_mem + base, cnt, v->d_gather, v->st));
@@ -1610,6 +1666,9 @@ claw_status claw_server_pump(claw_server* v, int steps, int* running, int* queue
         const DevCtl& c = v->h_gather[i];
         r.steps = c.steps;
         r.t_reached = c.t;
+        const double cells = (double)cells_of(r.g);
+        r.rem = (c.dt > 0.0 && c.t < r.t_end) ? cells * std::ceil((r.t_end - c.t) / c.dt) : cells;
+        r.idle = stepped[base + i] ? 0 : r.idle + 1;
         if (c.done) {
           const size_t sb = state_bytes_of(v->m, r.g);
           r.result.resize(sb);
@@ -1618,6 +1677,7 @@ claw_status claw_server_pump(claw_server* v, int steps, int* running, int* queue
           r.status = c.status;
           r.t_done = now_s();
           fin[base + i] = 1;
+          v->completed.push_back(r.ticket);
         }
       }
     }
@@ -1662,6 +1722,26 @@ claw_status claw_server_poll(claw_server* v, uint64_t ticket, void* q_host_out,
   return st;
 }
 
+claw_status claw_server_take_done(claw_server* v, uint64_t* tickets, int cap, int* n) {
+  if (!v || !n || cap < 0 || (cap > 0 && !tickets)) return sfail(v, "bad argument");
+  int k = 0;
+  while (k < cap && !v->completed.empty()) {
+    tickets[k++] = v->completed.front();
+    v->completed.pop_front();
+  }
+  *n = k;
+  return CLAW_OK;
+}
+
+claw_status claw_server_schedule(claw_server* v, int policy, int64_t min_cells) {
+  if (!v) return sfail(nullptr, "null server");
+  if (policy != CLAW_SCHED_ALL && policy != CLAW_SCHED_SRW) return sfail(v, "unknown policy");
+  if (policy == CLAW_SCHED_SRW && min_cells < 1) return sfail(v, "min_cells must be positive");
+  v->sched = policy;
+  if (policy == CLAW_SCHED_SRW) v->sched_cells = min_cells;
+  return CLAW_OK;
+}
+
 claw_status claw_server_destroy(claw_server* v) {
   if (!v) return CLAW_OK;
   if (v->st) cudaStreamSynchronize(v->st);
@@ -1671,6 +1751,7 @@ claw_status claw_server_destroy(claw_server* v) {
   if (v->d_tiles) cudaFreeAsync(v->d_tiles, v->st);
   if (v->d_stiles) cudaFreeAsync(v->d_stiles, v->st);
   if (v->d_tile0) cudaFreeAsync(v->d_tile0, v->st);
+  if (v->d_smem) cudaFreeAsync(v->d_smem, v->st);
   if (v->d_gather) cudaFree(v->d_gather);
   if (v->h_gather) cudaFreeHost(v->h_gather);
   if (v->st) cudaStreamSynchronize(v->st);

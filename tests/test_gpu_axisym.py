@@ -124,7 +124,8 @@ def test_axisymmetric_batch_equals_alone(orc):
 
 @pytest.mark.parametrize("split", ["godunov", "strang"])
 @pytest.mark.parametrize("budget_kb", [512 << 10, 300])
-def test_server_with_source_equals_alone(orc, split, budget_kb):
+@pytest.mark.parametrize("sched", [("all", 0), ("srw", 1500)])
+def test_server_with_source_equals_alone(orc, split, budget_kb, sched):
     """Axisymmetric shock-bubble requests of different sizes and final times
     through the continuous-batching server (a 300 KB budget admits about one
     at a time; Strang requests carry their half-step buffer) give the same
@@ -133,6 +134,7 @@ def test_server_with_source_equals_alone(orc, split, budget_kb):
     specs = [wl.shock_bubble_axisym(nx=nx, ny=ny, t_end=t, sub=2, source_split=split)
              for nx, ny, t in ((64, 16, 0.06), (96, 24, 0.05), (80, 20, 0.07))]
     sv = claw.Server(specs[0], "fp64", budget_bytes=budget_kb << 10, max_slots=4)
+    sv.schedule(*sched)
     tickets = [sv.submit(sp) for sp in specs]
     results = {}
     guard = 0

@@ -55,10 +55,13 @@ def test_batch_equals_alone(orc, prec, use_graph):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("budget_mb", [4096, 3])
-def test_server_equals_alone(orc, prec, budget_mb):
+@pytest.mark.parametrize("sched", [("all", 0), ("srw", 1 << 22), ("srw", 2500)])
+def test_server_equals_alone(orc, prec, budget_mb, sched):
     """Requests of different sizes and final times through the continuous-
-    batching server (a 3 MB budget admits one or two at a time) give the
-    same states as solving each alone."""
+    batching server (a 3 MB budget admits one or two at a time; every running
+    request stepped per attempt, or the least remaining work first with a
+    cell threshold that picks one or two of them) give the same states as
+    solving each alone."""
     import torch
     from paper_1111_6583_gb300 import claw
     reqs = [(48, [(0.5, 0.1, 0.4, 0.5)], 0.3), (96, [(0.3, 0.2, 0.6, 0.6)], 0.5),
@@ -66,6 +69,7 @@ def test_server_equals_alone(orc, prec, budget_mb):
             (120, [(0.4, 0.15, 0.5, 0.5)], 0.4)]
     specs = [wl.sw_humps_2d(n, humps, t) for n, humps, t in reqs]
     sv = claw.Server(specs[0], prec, budget_bytes=budget_mb << 20, max_slots=8)
+    sv.schedule(*sched)
     tickets = [sv.submit(sp) for sp in specs]
     results = {}
     guard = 0
@@ -162,3 +166,69 @@ def test_step_host_rejected_attempt():
     assert a.info()["steps"] == 1
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("policy", ["all", "srw"])
+def test_server_schedule_order(policy):
+    """A small grid with a long final time (more steps, less work) beside a
+    larger grid with a short one: stepping every request per attempt finishes
+    the larger (fewer steps) first; the shortest-remaining-work schedule, with
+    a threshold the small grid meets alone, finishes the small one first.
+    Both end at their t_end either way."""
+    from paper_1111_6583_gb300 import claw
+    big = wl.sw_humps_2d(96, [(0.2, 0.1, 0.5, 0.5)], 0.3)
+    small = wl.sw_humps_2d(32, [(0.2, 0.1, 0.5, 0.5)], 1.5)
+    sv = claw.Server(big, "fp32", budget_bytes=1 << 30, max_slots=4)
+    sv.schedule(policy, 32 * 32)
+    tb, ts = sv.submit(big), sv.submit(small)
+    done = {}
+    guard = 0
+    while len(done) < 2:
+        sv.pump(2)
+        for t in (tb, ts):
+            if t not in done:
+                r = sv.poll(t, want_state=False)
+                if r is not None:
+                    done[t] = (r, len(done))
+        guard += 1
+        assert guard < 100000
+    sv.close()
+    first = ts if policy == "srw" else tb
+    assert done[first][1] == 0
+    assert done[ts][0]["status"] == "ok" and done[tb][0]["status"] == "ok"
+    assert done[tb][0]["t"] == 0.3 and done[ts][0]["t"] == 1.5
+    assert done[ts][0]["steps"] > done[tb][0]["steps"]
+
+
+def test_server_schedule_rejects_bad_arguments():
+    from paper_1111_6583_gb300 import claw
+    sv = claw.Server(wl.sw_humps_2d(32, [], 0.1), "fp32", budget_bytes=1 << 26, max_slots=2)
+    with pytest.raises(RuntimeError):
+        sv.schedule("srw", 0)
+    lib = claw.load()
+    assert lib.claw_server_schedule(sv.h, 7, 1) != 0
+    sv.close()
+
+
+def test_server_take_done_lists_each_finished_request_once():
+    from paper_1111_6583_gb300 import claw
+    specs = [wl.sw_humps_2d(n, [(0.3, 0.1, 0.5, 0.5)], t) for n, t in ((32, 0.1), (48, 0.2),
+                                                                     (40, 0.05))]
+    sv = claw.Server(specs[0], "fp32", budget_bytes=1 << 28, max_slots=4)
+    tickets = [sv.submit(sp) for sp in specs]
+    seen = []
+    guard = 0
+    while len(seen) < len(tickets):
+        sv.pump(4)
+        got = sv.take_done(cap=1)  # at most one per call; the rest wait
+        while got:
+            seen += got
+            got = sv.take_done(cap=1)
+        guard += 1
+        assert guard < 100000
+    assert sorted(seen) == sorted(tickets) and len(set(seen)) == len(seen)
+    assert sv.take_done() == []
+    for t, sp in zip(tickets, specs):
+        r = sv.poll(t, want_state=False)
+        assert r["status"] == "ok" and r["t"] == sp["t_end"]
+    sv.close()

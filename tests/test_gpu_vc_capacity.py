@@ -191,13 +191,15 @@ def test_conserved_totals_weight_the_capacity(ndim, scheme):
     s.close()
 
 
-def test_server_on_the_per_face_path(orc):
+@pytest.mark.parametrize("sched", [("all", 0), ("srw", 2000)])
+def test_server_on_the_per_face_path(orc, sched):
     """Varying-medium, capacity requests through the continuous-batching
     server (a budget that admits one or two at a time): the same bits as
     solving each alone."""
     from paper_1111_6583_gb300 import claw
     specs = [wl.acoustics_vc_2d(n=n, t_end=t) for n, t in ((48, 0.2), (64, 0.15), (40, 0.25))]
     sv = claw.Server(specs[0], "fp64", budget_bytes=3 << 20, max_slots=4)
+    sv.schedule(*sched)
     tickets = [sv.submit(sp) for sp in specs]
     results = {}
     guard = 0
