@@ -123,9 +123,9 @@ const char* check_method(const claw_method& m, int nd) {
   if (m.lim < 0 || m.lim > 4) return "unknown limiter";
   if (m.scheme == CLAW_CLASSIC && m.order != 1 && m.order != 2) return "order must be 1 or 2";
   if (m.transverse < 0 || m.transverse > 2) return "transverse must be 0, 1 or 2";
-  if (m.scheme == CLAW_SHARPCLAW && m.weno_order != 5 && m.weno_order != 7 &&
-      m.weno_order != 9)
-    return "weno_order must be 5, 7 or 9";
+  if (m.scheme == CLAW_SHARPCLAW &&
+      (m.weno_order < 5 || m.weno_order > 13 || m.weno_order % 2 == 0))
+    return "weno_order must be odd, 5 to 13";
   if (m.scheme == CLAW_SHARPCLAW && m.time_integrator != CLAW_SSP_RK3 &&
       m.time_integrator != CLAW_SSP104)
     return "unknown time integrator";

@@ -200,6 +200,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? 8 : 1)
     const bool a_ok = MA == 0 || ((((size_t)aux) & 15) == 0 && (MA == 1 || rows16));
     R smax = R(0);
     int bad = 0;
+    float nf = 0.f;  // FP32: sum of result * 0
     for (int sub = sub0; sub < sub0 + spw; ++sub) {
       const int ustart = t0 + sub * WC;
       if (ustart >= nx) break;  // uniform over the warp
@@ -263,11 +264,12 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? 8 : 1)
 #pragma unroll
       for (int k = 1; k < K; ++k) CP::solve(C, pc[k - 1], pc[k], W[k], s[k], am[k], ap[k]);
 
-      // max speed over the unit's interfaces ustart .. ustart+WC (and <= nx)
+      // max speed over the unit's interfaces ustart .. ustart+WC that are
+      // <= nx: lanes 1..30 their K, lane 31 its first, lane 0 none
+      const int nsp = min(lane == 0 ? 0 : (lane == 31 ? 1 : K), nx + 1 - g0);
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        const int gi = g0 + k;
-        if (gi >= ustart && gi <= ustart + WC && gi <= nx) {
+        if (k < nsp) {
 #pragma unroll
           for (int p = 0; p < MW; ++p) smax = nanmax(smax, (R)fabs(s[k][p]));
         }
@@ -308,6 +310,9 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? 8 : 1)
       for (int k = 0; k < M; ++k)
         qout[K - 1][k] = qa[K - 1][k] - dtdx * ((ap[K - 1][k] - Fl[k]) + (amK[k] + FK[k]));
 
+      // non-finite results: FP32 folds them into one sum of v * 0 (NaN for
+      // a NaN or an infinity, else 0) tested once per item; FP64 tests each
+      // value on its bit pattern (the FP64 pipe is the scarce unit)
       if (lane >= 1 && lane <= 30) {
         if (vec && g0 + K <= ustart + WC) {
 #pragma unroll
@@ -316,7 +321,8 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? 8 : 1)
 #pragma unroll
             for (int c = 0; c < K; ++c) {
               v[c] = qout[c][k];
-              bad |= !isfinite(v[c]);
+              if constexpr (sizeof(R) == 4) nf = fmaf(v[c], 0.f, nf);
+              else bad |= !isfinite(v[c]);
             }
             VecIO<R, K>::store(qo + (size_t)k * nx + g0, v);
           }
@@ -326,7 +332,8 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? 8 : 1)
             if (g0 + c < nx) {
 #pragma unroll
               for (int k = 0; k < M; ++k) {
-                bad |= !isfinite(qout[c][k]);
+                if constexpr (sizeof(R) == 4) nf = fmaf(qout[c][k], 0.f, nf);
+                else bad |= !isfinite(qout[c][k]);
                 qo[(size_t)k * nx + g0 + c] = qout[c][k];
               }
             }
@@ -334,6 +341,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? 8 : 1)
         }
       }
     }  // units of the item
+    if constexpr (sizeof(R) == 4) bad |= !isfinite(nf);
     // per-warp atomics; the controllers run in the next launch
     fold_warp<R>(ctl, smax, bad);
   }

@@ -24,7 +24,7 @@ Run: python gen_weno.py  (rewrites weno_hi.cuh beside this file).
 import os
 from fractions import Fraction as Fr
 
-ORDERS_R = (4, 5)  # WENO7, WENO9
+ORDERS_R = (4, 5, 6, 7)  # WENO7 .. WENO13
 
 
 # --- polynomials as coefficient lists (lowest degree first) ---------------

@@ -263,6 +263,8 @@ struct Launchers {
         case 3: sharp_launch<3>(a, C, op); break;
         case 4: sharp_launch<4>(a, C, op); break;
         case 5: sharp_launch<5>(a, C, op); break;
+        case 6: sharp_launch<6>(a, C, op); break;
+        case 7: sharp_launch<7>(a, C, op); break;
         default: return cudaErrorInvalidValue;
       }
     }

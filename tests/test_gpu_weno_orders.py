@@ -1,9 +1,9 @@
-"""GPU parity of SharpClaw with seventh- and ninth-order WENO (Sec. 3.1 and
-the PyWENO subsection) against the oracle, whose coefficients come from an
+"""GPU parity of SharpClaw with WENO of orders 7 to 13 (Sec. 3.1 and the
+PyWENO subsection) against the oracle, whose coefficients come from an
 independent exact derivation: every Riemann solver in 1D, the 2D systems,
 component- and characteristic-wise, boundary conditions that reach the
-wider ghost layer, FP32, and the shock-bubble with WENO7 + SSP(10,4)
-through the controller.
+wider ghost layers (4 to 7 cells), FP32, and the shock-bubble with WENO7 +
+SSP(10,4) through the controller.
 """
 import numpy as np
 import pytest
@@ -16,6 +16,7 @@ pytestmark = pytest.mark.gpu
 
 RPS_1D = ["advection", "acoustics", "sw_roe", "euler_roe", "euler_hlle", "elasticity_fwave"]
 RPS_2D = ["advection", "acoustics", "sw_roe", "euler_roe", "euler_hlle"]
+ORDERS = [7, 9, 11, 13]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -27,7 +28,7 @@ def _built():
     __graft_entry__.build()
 
 
-@pytest.mark.parametrize("order", [7, 9])
+@pytest.mark.parametrize("order", ORDERS)
 @pytest.mark.parametrize("rp", RPS_1D)
 @pytest.mark.parametrize("char", [0, 1])
 def test_weno_order_1d_fp64(orc, order, rp, char):
@@ -41,7 +42,7 @@ def test_weno_order_1d_fp64(orc, order, rp, char):
     assert np.allclose(cg, co, rtol=1e-13, atol=0)
 
 
-@pytest.mark.parametrize("order", [7, 9])
+@pytest.mark.parametrize("order", ORDERS)
 @pytest.mark.parametrize("rp", RPS_2D)
 def test_weno_order_2d_fp64(orc, order, rp):
     spec = wl.random_smooth_2d(rp, 70, 37, scheme="sharpclaw", char_decomp=1, weno_order=order)
@@ -51,10 +52,10 @@ def test_weno_order_2d_fp64(orc, order, rp):
     assert rel_maxnorm(qg, qo) <= FP64_TOL
 
 
-@pytest.mark.parametrize("order", [7, 9])
+@pytest.mark.parametrize("order", ORDERS)
 @pytest.mark.parametrize("bc", ["wall", "extrap"])
 def test_weno_order_boundaries(orc, order, bc):
-    """Ghost layers of width 4 and 5 filled by wall and extrapolation rules."""
+    """Ghost layers of width 4 to 7 filled by wall and extrapolation rules."""
     s1 = wl.random_1d("euler_roe", 64, bc=(bc, bc), scheme="sharpclaw", char_decomp=1,
                       weno_order=order)
     qo, _ = oracle_fixed_steps(orc, s1, 0.1 / 64, 3)
@@ -67,7 +68,7 @@ def test_weno_order_boundaries(orc, order, bc):
     assert rel_maxnorm(qg, qo) <= FP64_TOL
 
 
-@pytest.mark.parametrize("order", [7, 9])
+@pytest.mark.parametrize("order", ORDERS)
 def test_weno_order_2d_fp32(orc, order):
     spec = wl.random_smooth_2d("euler_roe", 70, 37, scheme="sharpclaw", char_decomp=1,
                                weno_order=order)
