@@ -149,11 +149,82 @@ __device__ __forceinline__ void add_fc_own(R* __restrict__ work, const Faces3& L
   for (int c = 0; c < M; ++c) base[c] += v[c];
 }
 
+// transverse and double-transverse propagation of the fluctuation av that
+// enters cell c0 across its faces in direction D (Sec. 2, LeVeque 1997):
+// split in each transverse direction e into the four transverse faces of c0
+// (summed here, one update per face) and, split again in the third direction
+// g, into the g-faces of the cells c0 +- e.  The splits are linear in av, so
+// the two fluctuations entering a cell from its two D-faces are propagated
+// as one sum.
+template <class RP, typename R, int D>
+__device__ __forceinline__ void propagate3(const MConsts<R>& C, R* __restrict__ work,
+                                           const Faces3& L, int nx, int ny, int nz,
+                                           const int (&c0)[3], const R (&av)[RP::M], R dtdn,
+                                           const R (&k3)[3]) {
+  constexpr int M = RP::M;
+  constexpr int E1 = (D + 1) % 3, E2 = (D + 2) % 3;
+  R lo1[M], hi1[M], lo2[M], hi2[M];
+#pragma unroll
+  for (int c = 0; c < M; ++c) lo1[c] = hi1[c] = lo2[c] = hi2[c] = R(0);
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    // transverse direction e and third direction g
+    R em[M], ep[M];
+    if (t == 0) Trans3<RP, R, E1>::split(C, av, em, ep);
+    else Trans3<RP, R, E2>::split(C, av, em, ep);
+    const int e = t == 0 ? E1 : E2;
+    const int g = t == 0 ? E2 : E1;
+    R(&elo)[M] = t == 0 ? lo1 : lo2;
+    R(&ehi)[M] = t == 0 ? hi1 : hi2;
+    R(&glo)[M] = t == 0 ? lo2 : lo1;
+    R(&ghi)[M] = t == 0 ? hi2 : hi1;
+    const R h = R(-0.5) * dtdn;
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+      ehi[c] += h * ep[c];
+      elo[c] += h * em[c];
+    }
+    const R dte = k3[e];
+#pragma unroll
+    for (int sg = 0; sg < 2; ++sg) {
+      const R(&bv)[M] = sg == 0 ? ep : em;
+      const R k6 = (sg == 0 ? R(1) : R(-1)) * dtdn * dte * (R(1) / R(6));
+      R gm[M], gp[M];
+      if (t == 0) Trans3<RP, R, E2>::split(C, bv, gm, gp);
+      else Trans3<RP, R, E1>::split(C, bv, gm, gp);
+#pragma unroll
+      for (int c = 0; c < M; ++c) {
+        ghi[c] += k6 * gp[c];
+        glo[c] += k6 * gm[c];
+      }
+      // the g-faces of the cell the piece moved on to, c0 +- e
+      int c2[3] = {c0[0], c0[1], c0[2]};
+      c2[e] += sg == 0 ? 1 : -1;
+      int fu2[3] = {c2[0], c2[1], c2[2]};
+      fu2[g] = c2[g] + 1;
+      add_fc<M, R>(work, L, g, nx, ny, nz, fu2, -k6, gp);
+      add_fc<M, R>(work, L, g, nx, ny, nz, c2, -k6, gm);
+    }
+  }
+  int u1[3] = {c0[0], c0[1], c0[2]};
+  u1[E1] = c0[E1] + 1;
+  int u2[3] = {c0[0], c0[1], c0[2]};
+  u2[E2] = c0[E2] + 1;
+  add_fc<M, R>(work, L, E1, nx, ny, nz, u1, R(1), hi1);
+  add_fc<M, R>(work, L, E1, nx, ny, nz, c0, R(1), lo1);
+  add_fc<M, R>(work, L, E2, nx, ny, nz, u2, R(1), hi2);
+  add_fc<M, R>(work, L, E2, nx, ny, nz, c0, R(1), lo2);
+}
+
+// faces along D one sweep thread walks
+constexpr int kSweep3dFaces = 8;
+
 template <class RP, typename R, int D>
 __global__ void __launch_bounds__(256)
     classic3d_sweep(const Member* __restrict__ members, const MConsts<R> C) {
   constexpr int M = RP::M, MW = RP::MW;
   constexpr int E1 = (D + 1) % 3, E2 = (D + 2) % 3;
+  constexpr int T = kSweep3dFaces;
   const Member& mb = members[0];
   DevCtl* ctl = mb.ctl;
   __shared__ int s_done, s_cur;
@@ -168,153 +239,139 @@ __global__ void __launch_bounds__(256)
   const int nx = mb.nx, ny = mb.ny, nz = mb.nz;
   const int n3[3] = {nx, ny, nz};
   const int nd = n3[D], ne1 = n3[E1], ne2 = n3[E2];
-  // faces i = 0..nd in D, lines a = -1..ne1, b = -1..ne2
-  const long long total = (long long)(nd + 1) * (ne1 + 2) * (ne2 + 2);
+  const int nseg = (nd + 1 + T - 1) / T;
+  // segments of T faces along D (faces 0..nd), lines a = -1..ne1, b = -1..ne2
+  const long long total = (long long)nseg * (ne1 + 2) * (ne2 + 2);
   const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   R smax = R(0);
   if (id < total) {
-    // x varies fastest across threads in every sweep (coalesced loads and
-    // face-array updates); coordinates along D run 0..nd, across it -1..n
+    // x varies fastest across threads (in the x sweep: the segment index)
     int ext[3], v[3];
-    ext[D] = nd + 1;
+    ext[D] = nseg;
     ext[E1] = ne1 + 2;
     ext[E2] = ne2 + 2;
     const long long q01 = (long long)ext[0] * ext[1];
     v[0] = (int)(id % ext[0]);
     v[1] = (int)((id / ext[0]) % ext[1]);
     v[2] = (int)(id / q01);
-    const int i = v[D], a = v[E1] - 1, b = v[E2] - 1;
+    const int i0 = v[D] * T, i1 = min(i0 + T, nd + 1);
+    const int a = v[E1] - 1, b = v[E2] - 1;
     const R* __restrict__ q = (const R*)mb.q[s_cur];
     R* __restrict__ work = (R*)mb.work3;
     Faces3 L;
     faces3_layout(nx, ny, nz, M, L);
     const R dtdn = s_k[D];
-    // cells i-2 .. i+1 along D on line (a, b)
-    R cell[4][M];
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
+    const R k3[3] = {s_k[0], s_k[1], s_k[2]};
+    const bool interior_line = a >= 0 && a < ne1 && b >= 0 && b < ne2;
+    auto load = [&](int i, R (&out)[M]) {
       int c3[3];
-      c3[D] = i - 2 + t;
+      c3[D] = i;
       c3[E1] = a;
       c3[E2] = b;
-      load_cell3<M, R>(C, q, nx, ny, nz, c3[0], c3[1], c3[2], RP::WALL_X, 2, 3, cell[t]);
-    }
-    // faces i-1, i, i+1 (solves of cell pairs (t, t+1))
-    R W[3][MW][M], s[3][MW], am[M], ap[M];
+      load_cell3<M, R>(C, q, nx, ny, nz, c3[0], c3[1], c3[2], RP::WALL_X, 2, 3, out);
+    };
+    // window: waves of faces i-1 (Wl), i (Wc) and i+1 (Wr); face i lies
+    // between cells i-1 and i
+    R Wl[MW][M], Wc[MW][M], Wr[MW][M], sl[MW], sc[MW], sr[MW];
+    R amc[M], apc[M], amr[M], apr[M];
+    R cl[M], cr[M];
     {
       R x[RP::NCTX], amt[M], apt[M];
-      RP::template solve<D>(C, cell[0], cell[1], nullptr, nullptr, W[0], s[0], amt, apt, x);
-      RP::template solve<D>(C, cell[1], cell[2], nullptr, nullptr, W[1], s[1], am, ap, x);
-      RP::template solve<D>(C, cell[2], cell[3], nullptr, nullptr, W[2], s[2], amt, apt, x);
+      load(i0 - 2, cl);
+      load(i0 - 1, cr);
+      RP::template solve<D>(C, cl, cr, nullptr, nullptr, Wl, sl, amt, apt, x);
+      load(i0, cl);
+      RP::template solve<D>(C, cr, cl, nullptr, nullptr, Wc, sc, amc, apc, x);
     }
-    // (cell[2] is cell i, cell[1] is cell i-1: face i solved into W[1])
-    const bool interior_line = a >= 0 && a < ne1 && b >= 0 && b < ne2;
-    if (interior_line) {
+    // cl holds cell i0 here
+    R P[M];  // A+dQ - F of the face left of the current cell (enters it)
+    int c0[3];
+    c0[E1] = a;
+    c0[E2] = b;
+    for (int i = i0; i < i1; ++i) {
+      {
+        R x[RP::NCTX];
+        load(i + 1, cr);
+        RP::template solve<D>(C, cl, cr, nullptr, nullptr, Wr, sr, amr, apr, x);
 #pragma unroll
-      for (int p = 0; p < MW; ++p) smax = nanmax(smax, (R)fabs(s[1][p]));
-    }
-    R F[M];
-    if (C.order == 2) {
-      R dot[MW], nrm[MW];
-#pragma unroll
-      for (int p = 0; p < MW; ++p) {
-        R d_ = R(0), n2 = R(0);
-#pragma unroll
-        for (int c = 0; c < M; ++c) {
-          const R up = s[1][p] > R(0) ? W[0][p][c] : W[2][p][c];
-          d_ += up * W[1][p][c];
-          n2 += W[1][p][c] * W[1][p][c];
-        }
-        dot[p] = d_;
-        nrm[p] = n2;
+        for (int c = 0; c < M; ++c) cl[c] = cr[c];
       }
-      correction<RP, R, D>(C, W[1], s[1], dot, nrm, dtdn, F);
-    } else {
+      if (interior_line) {
 #pragma unroll
-      for (int c = 0; c < M; ++c) F[c] = R(0);
-    }
-    int f[3];
-    f[D] = i;
-    f[E1] = a;
-    f[E2] = b;
-    if (interior_line) {
-      const size_t fi = face_index<R>(D, nx, ny, f);
-#pragma unroll
-      for (int c = 0; c < M; ++c) {
-        work[L.off_am[D] + fi * M + c] = am[c];
-        work[L.off_ap[D] + fi * M + c] = ap[c];
+        for (int p = 0; p < MW; ++p) smax = nanmax(smax, (R)fabs(sc[p]));
       }
-      // within this sweep only this thread touches the D-face's correction
-      add_fc_own<M, R>(work, L, D, nx, ny, nz, f, F);
-    }
-    if (C.transverse) {
-      R apq[M], amq[M];
+      R F[M];
+      if (C.order == 2) {
+        R dot[MW], nrm[MW];
 #pragma unroll
-      for (int c = 0; c < M; ++c) {
-        apq[c] = ap[c] - (C.transverse == 2 ? F[c] : R(0));
-        amq[c] = am[c] + (C.transverse == 2 ? F[c] : R(0));
-      }
-#pragma unroll
-      for (int side = 0; side < 2; ++side) {
-        const R(&av)[M] = side == 0 ? apq : amq;
-        int c0[3];
-        c0[D] = side == 0 ? i : i - 1;
-        c0[E1] = a;
-        c0[E2] = b;
-        // the four transverse faces of c0 (lower / upper in E1 and E2) take
-        // two pieces each: summed here, one update per face
-        R lo1[M], hi1[M], lo2[M], hi2[M];
-#pragma unroll
-        for (int c = 0; c < M; ++c) lo1[c] = hi1[c] = lo2[c] = hi2[c] = R(0);
-#pragma unroll
-        for (int t = 0; t < 2; ++t) {
-          // transverse direction e and third direction g
-          R em[M], ep[M];
-          if (t == 0) Trans3<RP, R, E1>::split(C, av, em, ep);
-          else Trans3<RP, R, E2>::split(C, av, em, ep);
-          const int e = t == 0 ? E1 : E2;
-          const int g = t == 0 ? E2 : E1;
-          R(&elo)[M] = t == 0 ? lo1 : lo2;
-          R(&ehi)[M] = t == 0 ? hi1 : hi2;
-          R(&glo)[M] = t == 0 ? lo2 : lo1;
-          R(&ghi)[M] = t == 0 ? hi2 : hi1;
-          const R h = R(-0.5) * dtdn;
+        for (int p = 0; p < MW; ++p) {
+          R d_ = R(0), n2 = R(0);
 #pragma unroll
           for (int c = 0; c < M; ++c) {
-            ehi[c] += h * ep[c];
-            elo[c] += h * em[c];
+            const R up = sc[p] > R(0) ? Wl[p][c] : Wr[p][c];
+            d_ += up * Wc[p][c];
+            n2 += Wc[p][c] * Wc[p][c];
           }
-          const R dte = s_k[e];
-#pragma unroll
-          for (int sg = 0; sg < 2; ++sg) {
-            const R(&bv)[M] = sg == 0 ? ep : em;
-            const R k6 = (sg == 0 ? R(1) : R(-1)) * dtdn * dte * (R(1) / R(6));
-            R gm[M], gp[M];
-            if (t == 0) Trans3<RP, R, E2>::split(C, bv, gm, gp);
-            else Trans3<RP, R, E1>::split(C, bv, gm, gp);
-#pragma unroll
-            for (int c = 0; c < M; ++c) {
-              ghi[c] += k6 * gp[c];
-              glo[c] += k6 * gm[c];
-            }
-            // the g-faces of the cell the piece moved on to, c0 +- e
-            int c2[3] = {c0[0], c0[1], c0[2]};
-            c2[e] += sg == 0 ? 1 : -1;
-            int fu2[3] = {c2[0], c2[1], c2[2]};
-            fu2[g] = c2[g] + 1;
-            add_fc<M, R>(work, L, g, nx, ny, nz, fu2, -k6, gp);
-            add_fc<M, R>(work, L, g, nx, ny, nz, c2, -k6, gm);
-          }
+          dot[p] = d_;
+          nrm[p] = n2;
         }
-        int u1[3] = {c0[0], c0[1], c0[2]};
-        u1[E1] = c0[E1] + 1;
-        int u2[3] = {c0[0], c0[1], c0[2]};
-        u2[E2] = c0[E2] + 1;
-        add_fc<M, R>(work, L, E1, nx, ny, nz, u1, R(1), hi1);
-        add_fc<M, R>(work, L, E1, nx, ny, nz, c0, R(1), lo1);
-        add_fc<M, R>(work, L, E2, nx, ny, nz, u2, R(1), hi2);
-        add_fc<M, R>(work, L, E2, nx, ny, nz, c0, R(1), lo2);
+        correction<RP, R, D>(C, Wc, sc, dot, nrm, dtdn, F);
+      } else {
+#pragma unroll
+        for (int c = 0; c < M; ++c) F[c] = R(0);
       }
+      if (interior_line) {
+        int f[3];
+        f[D] = i;
+        f[E1] = a;
+        f[E2] = b;
+        const size_t fi = face_index<R>(D, nx, ny, f);
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+          work[L.off_am[D] + fi * M + c] = amc[c];
+          work[L.off_ap[D] + fi * M + c] = apc[c];
+        }
+        // within this sweep only this thread touches the D-face's correction
+        add_fc_own<M, R>(work, L, D, nx, ny, nz, f, F);
+      }
+      if (C.transverse) {
+        // cell i-1 takes A-dQ + F of face i, plus (inside the segment) the
+        // A+dQ - F of face i-1 carried in P
+        const R tf = C.transverse == 2 ? R(1) : R(0);
+        R av[M];
+#pragma unroll
+        for (int c = 0; c < M; ++c) av[c] = amc[c] + tf * F[c];
+        if (i > i0) {
+#pragma unroll
+          for (int c = 0; c < M; ++c) av[c] = P[c] + av[c];
+        }
+        c0[D] = i - 1;
+        propagate3<RP, R, D>(C, work, L, nx, ny, nz, c0, av, dtdn, k3);
+#pragma unroll
+        for (int c = 0; c < M; ++c) P[c] = apc[c] - tf * F[c];
+      }
+      // slide the window
+#pragma unroll
+      for (int p = 0; p < MW; ++p) {
+        sl[p] = sc[p];
+        sc[p] = sr[p];
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+          Wl[p][c] = Wc[p][c];
+          Wc[p][c] = Wr[p][c];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < M; ++c) {
+        amc[c] = amr[c];
+        apc[c] = apr[c];
+      }
+    }
+    if (C.transverse) {
+      // the last face's A+dQ - F enters cell i1-1 (its other face belongs to
+      // the next segment)
+      c0[D] = i1 - 1;
+      propagate3<RP, R, D>(C, work, L, nx, ny, nz, c0, P, dtdn, k3);
     }
   }
   R sx = D == 0 ? smax : R(0), sy = D == 1 ? smax : R(0), sz = D == 2 ? smax : R(0);

@@ -202,8 +202,11 @@ struct Launchers {
       const long long nx = a.n3[0], ny = a.n3[1], nz = a.n3[2];
       cudaError_t e = cudaMemsetAsync(a.work3, 0, a.work3_bytes, a.stream);
       if (e != cudaSuccess) return e;
-      const long long f0 = (nx + 1) * (ny + 2) * (nz + 2), f1 = (ny + 1) * (nz + 2) * (nx + 2),
-                      f2 = (nz + 1) * (nx + 2) * (ny + 2);
+      // one thread per kSweep3dFaces faces along the sweep, on every line
+      constexpr long long T = kSweep3dFaces;
+      const long long f0 = (nx + T) / T * (ny + 2) * (nz + 2),
+                      f1 = (ny + T) / T * (nz + 2) * (nx + 2),
+                      f2 = (nz + T) / T * (nx + 2) * (ny + 2);
       classic3d_sweep<RP, R, 0><<<(unsigned)((f0 + 255) / 256), 256, 0, a.stream>>>(a.members, C);
       classic3d_sweep<RP, R, 1><<<(unsigned)((f1 + 255) / 256), 256, 0, a.stream>>>(a.members, C);
       classic3d_sweep<RP, R, 2><<<(unsigned)((f2 + 255) / 256), 256, 0, a.stream>>>(a.members, C);
