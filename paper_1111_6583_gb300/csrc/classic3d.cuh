@@ -217,7 +217,7 @@ __device__ __forceinline__ void propagate3(const MConsts<R>& C, R* __restrict__ 
 }
 
 // faces along D one sweep thread walks
-constexpr int kSweep3dFaces = 8;
+constexpr int kSweep3dFaces = 16;
 
 template <class RP, typename R, int D>
 __global__ void __launch_bounds__(256)
