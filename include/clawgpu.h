@@ -254,6 +254,12 @@ typedef struct {
  * varying-medium acoustics) the kernels run request by request. */
 claw_status claw_server_create(const claw_method* m, size_t hbm_budget_bytes, int max_slots,
                                void* stream, claw_server** out);
+/* The same for grids of ndim dimensions (1, 2 or 3; claw_server_create takes
+ * 2 when num_eqn is the 2D system's field count, else 1).  3D requests run
+ * the classic face sweeps and update request by request (Sec. 2's 3D
+ * algorithm with transverse and double-transverse terms). */
+claw_status claw_server_create_nd(const claw_method* m, int ndim, size_t hbm_budget_bytes,
+                                  int max_slots, void* stream, claw_server** out);
 /* Submit one solve: grid, initial state (host memory, the method's precision
  * and layout), aux (host, may be NULL), t_end.  Returns a ticket.  Fails with
  * CLAW_EBUDGET when the request alone exceeds the budget. */

@@ -108,6 +108,8 @@ _SIGS = {
                                           _P(ctypes.c_uint64)]),
     "claw_server_pump": (ctypes.c_int, [_VP, ctypes.c_int, _P(ctypes.c_int), _P(ctypes.c_int)]),
     "claw_server_poll": (ctypes.c_int, [_VP, ctypes.c_uint64, _VP, _P(claw_req_info)]),
+    "claw_server_create_nd": (ctypes.c_int, [_P(claw_method), ctypes.c_int, ctypes.c_size_t,
+                                             ctypes.c_int, _VP, _P(_VP)]),
     "claw_server_schedule": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int64]),
     "claw_server_take_done": (ctypes.c_int, [_VP, _P(ctypes.c_uint64), ctypes.c_int,
                                              _P(ctypes.c_int)]),
@@ -387,9 +389,9 @@ class Server:
         self.np_dtype = np.float32 if prec in ("fp32", FP32) else np.float64
         self.stream = stream if stream is not None else current_stream_handle()
         h = ctypes.c_void_p()
-        _check(load().claw_server_create(ctypes.byref(self.method), int(budget_bytes),
-                                         int(max_slots), ctypes.c_void_p(self.stream),
-                                         ctypes.byref(h)))
+        _check(load().claw_server_create_nd(ctypes.byref(self.method), int(spec["ndim"]),
+                                            int(budget_bytes), int(max_slots),
+                                            ctypes.c_void_p(self.stream), ctypes.byref(h)))
         self.h = h
         self.shapes = {}
 

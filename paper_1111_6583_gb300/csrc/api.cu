@@ -1383,6 +1383,9 @@ claw_status sfail(claw_server* v, const char* what, cudaError_t e = cudaSuccess)
   } while (0)
 
 size_t req_faces_bytes(const claw_server* v, const claw_grid& g) {
+  if (v->nd == 3)
+    return align256(classic3d_work_bytes((int)g.n[0], (int)g.n[1], (int)g.n[2], v->m.num_eqn,
+                                         v->prec));
   return v->faces ? align256(faces_work_bytes(v->nd, (int)g.n[0], (int)g.n[1], v->m.num_eqn,
                                               v->prec))
                   : 0;
@@ -1399,11 +1402,11 @@ extern "C" {
 
 double claw_clock(void) { return now_s(); }
 
-claw_status claw_server_create(const claw_method* m, size_t hbm_budget_bytes, int max_slots,
-                               void* stream, claw_server** out) {
-  if (!m || !out || max_slots <= 0) return sfail(nullptr, "bad argument");
+claw_status claw_server_create_nd(const claw_method* m, int ndim, size_t hbm_budget_bytes,
+                                  int max_slots, void* stream, claw_server** out) {
+  if (!m || !out || max_slots <= 0 || ndim < 1 || ndim > 3) return sfail(nullptr, "bad argument");
   *out = nullptr;
-  const int nd = (m->num_eqn == num_eqn(m->rp, 2)) ? 2 : 1;
+  const int nd = ndim;
   if (const char* why = check_method(*m, nd)) return sfail(nullptr, why);
   const int faces = m->scheme == CLAW_CLASSIC && nd <= 2 &&
                     (m->capa_index >= 0 || (nd == 2 && m->rp == CLAW_RP_ACOUSTICS_VC));
@@ -1440,6 +1443,14 @@ claw_status claw_server_create(const claw_method* m, size_t hbm_budget_bytes, in
   }
   *out = v;
   return CLAW_OK;
+}
+
+claw_status claw_server_create(const claw_method* m, size_t hbm_budget_bytes, int max_slots,
+                               void* stream, claw_server** out) {
+  if (!m) return sfail(nullptr, "bad argument");
+  // the dimension from the number of fields: 2D when it matches the 2D system
+  const int nd = (m->num_eqn == num_eqn(m->rp, 2)) ? 2 : 1;
+  return claw_server_create_nd(m, nd, hbm_budget_bytes, max_slots, stream, out);
 }
 
 claw_status claw_server_submit(claw_server* v, const claw_grid* g, const void* q0_host,
@@ -1493,7 +1504,8 @@ claw_status claw_server_pump(claw_server* v, int steps, int* running, int* queue
     p += align256(sizeof(DevCtl));
     r.mem.nx = (int)r.g.n[0];
     r.mem.ny = (int)r.g.n[1];
-    if (v->faces) {
+    r.mem.nz = v->nd == 3 ? (int)r.g.n[2] : 1;
+    if (v->faces || v->nd == 3) {
       // face arrays; the update's blocks (256 cells each) count the arrivals
       r.w3bytes = req_faces_bytes(v, r.g);
       r.mem.work3 = p;
@@ -1543,7 +1555,16 @@ claw_status claw_server_pump(claw_server* v, int steps, int* running, int* queue
       }
     }
     // first dt for the newly admitted requests
-    if (!admitted.empty()) {
+    if (!admitted.empty() && v->nd == 3) {
+      for (size_t i = 0; i < v->running.size(); ++i) {
+        const Req& r = v->reqs[v->running[i]];
+        if (std::find(admitted.begin(), admitted.end(), r.ticket) == admitted.end()) continue;
+        LaunchArgs a{v->d_mem + i, nullptr, 0, v->consts.data(), 0, 0, 0, v->st,
+                     {r.mem.nx, r.mem.ny, r.mem.nz}, nullptr, 0};
+        VCK(v->ks.maxspeed(a));
+      }
+      for (uint64_t t : admitted) VCK(launch_dt_init(v->reqs[t].mem.ctl, 1, v->st));
+    } else if (!admitted.empty()) {
       std::vector<Tile> ms;
       for (size_t i = 0; i < v->running.size(); ++i) {
         const Req& r = v->reqs[v->running[i]];
@@ -1599,7 +1620,7 @@ claw_status claw_server_pump(claw_server* v, int steps, int* running, int* queue
       for (size_t i = 0; i < sel.size(); ++i) {
         const Req& r = v->reqs[sel[i]];
         hm.push_back(r.mem);
-        if (!v->faces)
+        if (!v->faces && v->nd != 3)
           for (int t = 0; t < r.mem.ntiles; ++t) ht.push_back(Tile{(int)i, t});
         if (v->m.source != CLAW_SOURCE_NONE)
           for (int t = 0; t < maxspeed_tiles(r.mem.nx, r.mem.ny); ++t) hs.push_back(Tile{(int)i, t});
@@ -1632,7 +1653,15 @@ claw_status claw_server_pump(claw_server* v, int steps, int* running, int* queue
       v->sel = sel;
     }
     for (int i = 0; i < steps; ++i) {
-      if (v->faces) {
+      if (v->nd == 3) {
+        // the 3D sweeps take one member: request by request
+        for (size_t k = 0; k < sel.size(); ++k) {
+          const Req& r = v->reqs[sel[k]];
+          LaunchArgs a{v->d_smem + k, nullptr, r.mem.ntiles, v->consts.data(), 0, 0, 0, v->st,
+                       {r.mem.nx, r.mem.ny, r.mem.nz}, r.mem.work3, r.w3bytes};
+          VCK(v->ks.classic(a));
+        }
+      } else if (v->faces) {
         // the per-face kernels take one member: request by request
         for (size_t k = 0; k < sel.size(); ++k) {
           const Req& r = v->reqs[sel[k]];

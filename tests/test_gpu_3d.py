@@ -102,3 +102,58 @@ def test_3d_batch_fp32_matches_solvers():
         assert rel_maxnorm(b.q[k].double().cpu().numpy(), qa) <= 1e-6, k
         s.close()
     b.close()
+
+
+@pytest.mark.parametrize("sched", [("all", 0), ("srw", 1500)])
+def test_3d_server_matches_solver_and_oracle(orc, sched):
+    """3D requests of different shapes and end times through the continuous-
+    batching server (a budget that admits one or two at a time): each takes
+    the single-grid solver's CFL steps and ends at its state (the face sweeps
+    sum by atomics, so to rounding), and the FP64 oracle's."""
+    from paper_1111_6583_gb300 import claw
+    specs = _batch_specs("acoustics", "wall")
+    sv = claw.Server(specs[0], "fp64", budget_bytes=1 << 20, max_slots=4)
+    sv.schedule(*sched)
+    tickets = [sv.submit(sp) for sp in specs]
+    done = {}
+    guard = 0
+    while len(done) < len(tickets):
+        sv.pump(3)
+        for t in sv.take_done():
+            done[t] = sv.poll(t)
+        guard += 1
+        assert guard < 100000
+    sv.close()
+    for t, sp in zip(tickets, specs):
+        r = done[t]
+        assert r["status"] == "ok" and r["t"] == sp["t_end"]
+        s = claw.Solver(sp, "fp64")
+        ia = s.evolve(sp["t_end"])
+        qa = s.q.double().cpu().numpy()
+        s.close()
+        assert ia["steps"] == r["steps"]
+        assert rel_maxnorm(r["q"], qa) <= 1e-13
+        qo, io = oracle_evolve(orc, sp, sp["t_end"])
+        assert io["steps"] == r["steps"] and rel_maxnorm(r["q"], qo) <= FP64_TOL
+
+
+def test_1d_advection_server_takes_its_dimension_from_the_grid():
+    """A one-field method is ambiguous between dimensions; the server made
+    from a 1D spec serves 1D grids and refuses others."""
+    from paper_1111_6583_gb300 import claw
+    sp = wl.random_1d("advection", 200)
+    sp["t_end"] = 0.1
+    sv = claw.Server(sp, "fp64", budget_bytes=1 << 24, max_slots=2)
+    t = sv.submit(sp)
+    with pytest.raises(RuntimeError):
+        sv.submit(wl.random_3d("advection", 8, 8, 8))
+    while not sv.take_done():
+        sv.pump(4)
+    r = sv.poll(t)
+    sv.close()
+    s = claw.Solver(sp, "fp64")
+    ia = s.evolve(0.1)
+    qa = s.q.double().cpu().numpy()
+    s.close()
+    assert r["status"] == "ok" and r["steps"] == ia["steps"]
+    assert np.array_equal(qa, r["q"].astype(np.float64))
