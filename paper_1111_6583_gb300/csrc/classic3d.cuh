@@ -3,9 +3,10 @@
 // for scalar advection and linear acoustics.
 //
 // One attempt = a zero fill of the per-face arrays, three face sweeps (one per
-// direction; a thread per face, its limiter neighbours solved again in the
-// thread) that accumulate fluctuations and correction fluxes on the faces of
-// interior cells, and an update kernel whose last block runs the controller.
+// direction; a thread walks a segment of faces along the direction with a
+// sliding window of waves) that accumulate fluctuations and correction fluxes
+// on the faces of interior cells, and an update kernel whose last block runs
+// the controller.
 // Transverse pieces: a fluctuation a that enters cell c across a d-face adds
 // -dt/(2 dx_d) E^+-a to the e-faces of c; the part E^+-a has moved on into
 // cell c +- e, so its third-direction split F^+-E^+-a moves 1/6 (dt/dx_d)
