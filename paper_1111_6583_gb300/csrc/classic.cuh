@@ -46,6 +46,16 @@ struct VecIO<float, 4> {
   }
 };
 template <>
+struct VecIO<double, 2> {
+  __device__ static __forceinline__ void load(const double* p, double (&v)[2]) {
+    const double2 a = __ldg((const double2*)p);
+    v[0] = a.x; v[1] = a.y;
+  }
+  __device__ static __forceinline__ void store(double* p, const double (&v)[2]) {
+    ((double2*)p)[0] = make_double2(v[0], v[1]);
+  }
+};
+template <>
 struct VecIO<double, 4> {
   __device__ static __forceinline__ void load(const double* p, double (&v)[4]) {
     const double2 a = __ldg((const double2*)p), b = __ldg((const double2*)p + 1);

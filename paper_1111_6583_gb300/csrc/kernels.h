@@ -51,7 +51,9 @@ struct KernelSet {
 
 // tile geometry shared by the host (tile tables) and the kernels
 constexpr int kClassic1dThreads = 128;
-constexpr int classic1d_K(int) { return 4; }  // cells per thread (FP64 and FP32)
+// cells per lane: FP32 4 (16-byte loads; the fastest batched form), FP64 2
+// (twice the warps for the small single grids the FP64 form runs)
+constexpr int classic1d_K(int prec) { return prec == 0 ? 2 : 4; }
 // a warp writes the cells of its lanes 1..30 (lanes 0 and 31 hold its halo)
 constexpr int classic1d_T(int prec) { return kClassic1dThreads / 32 * 30 * classic1d_K(prec); }
 inline int classic1d_tiles(int nx, int prec) {

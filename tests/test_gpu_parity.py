@@ -1,7 +1,7 @@
 """GPU parity: the CUDA kernels (through the C ABI) against the CPU oracle on
 the same seeded inputs, element by element.
 
-Sizes span several tiles with ragged tails (1D tiles of 512 cells; 2D
+Sizes span several tiles with ragged tails (1D tiles of 240 cells in FP64 and 480 in FP32; 2D
 strips of 60/124 columns and row segments of 8..128 rows; SharpClaw tiles of
 16x8 and 128 cells).  FP64 tolerance: max-norm relative 1e-12; FP32: 1e-5
 relative on smooth data, L1 1e-4 where the data have jumps.
