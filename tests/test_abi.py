@@ -112,3 +112,28 @@ def test_method_init_and_validation_without_gpu(lib_path):
                                   ctypes.byref(h)) == claw.CLAW_EINVAL
     assert b"source_split" in lib.claw_last_error(None)
     assert lib.claw_version().startswith(b"clawgpu")
+
+
+def test_server_entry_points_validate_without_gpu(lib_path):
+    """The server's argument checks return before any CUDA call: the
+    dimension of claw_server_create_nd, a method the dimension cannot take,
+    and null handles for the schedule and completion calls."""
+    from paper_1111_6583_gb300 import claw
+    lib = claw.load()
+    m = claw.claw_method()
+    h = ctypes.c_void_p()
+    lib.claw_method_init(ctypes.byref(m), claw.RP["acoustics"], 3)
+    for nd in (0, 4):
+        assert lib.claw_server_create_nd(ctypes.byref(m), nd, 1 << 20, 4, None,
+                                         ctypes.byref(h)) == claw.CLAW_EINVAL
+    assert lib.claw_server_create_nd(ctypes.byref(m), 3, 1 << 20, 0, None,
+                                     ctypes.byref(h)) == claw.CLAW_EINVAL
+    # SharpClaw has no 3D form
+    m.scheme = claw.SHARPCLAW
+    assert lib.claw_server_create_nd(ctypes.byref(m), 3, 1 << 20, 4, None,
+                                     ctypes.byref(h)) == claw.CLAW_EINVAL
+    assert b"3D" in lib.claw_last_error(None)
+    assert lib.claw_server_schedule(None, claw.SCHED["srw"], 1) == claw.CLAW_EINVAL
+    n = ctypes.c_int()
+    buf = (ctypes.c_uint64 * 4)()
+    assert lib.claw_server_take_done(None, buf, 4, ctypes.byref(n)) == claw.CLAW_EINVAL
