@@ -122,15 +122,20 @@ def test_smoothness_indicator_on_polynomial_data(r):
         assert abs(vk @ Bk @ vk) <= 1e-14 * (np.abs(vk) @ np.abs(Bk) @ np.abs(vk))
 
 
-@pytest.mark.parametrize("r", [3, 4, 5])
+@pytest.mark.parametrize("r", range(3, 10))
 def test_design_order_on_smooth_data(r):
     """Order 2r-1 with the optimal weights; at least 2r-2 with the Jiang-Shu
-    weights (epsilon 1e-6) at a point where f' != 0, on these grids."""
+    weights (epsilon 1e-6) at a point where f' != 0, on these grids.  From
+    order 11 on, the grids stay coarse (8 and 16 cells across the unit) so
+    that the errors (down to 1e-13) stay above FP64 round-off; there the
+    observed order still approaches 2r-1 from below (10.8, 12.7, 14.7, 16.6),
+    hence the wider margin."""
     F = lambda x: -np.cos(2 * np.pi * x) / (2 * np.pi) + np.exp(x)
     f = lambda x: np.sin(2 * np.pi * x) + np.exp(x)
     x0 = 0.3
-    Ns = (20, 40, 80) if r == 3 else (10, 20, 40)
-    for eps, need in ((1e30, 2 * r - 1 - 0.1), (1e-6, 2 * r - 2 - 0.5)):
+    Ns = (20, 40, 80) if r == 3 else ((10, 20, 40) if r <= 5 else (8, 16))
+    margin = 0.1 if r <= 5 else 0.5
+    for eps, need in ((1e30, 2 * r - 1 - margin), (1e-6, 2 * r - 2 - 0.5)):
         errs = []
         for N in Ns:
             h = 1.0 / N
@@ -140,14 +145,14 @@ def test_design_order_on_smooth_data(r):
         assert math.log2(errs[-2] / errs[-1]) >= need, (eps, errs)
 
 
-@pytest.mark.parametrize("order", [7, 9])
+@pytest.mark.parametrize("order", [7, 9, 11, 13])
 def test_sharpclaw_operator_order_on_advection(orc, order):
     """Semi-discrete operator of linear advection (u = 1, periodic) on the
     averages of a smooth function: L(Q)_i against the exact
     -(f(x_{i+1/2}) - f(x_{i-1/2}))/dx converges at the WENO order (optimal
     weights, so the design order shows on coarse grids)."""
     errs = []
-    Ns = (16, 32) if order == 9 else (32, 64)
+    Ns = {7: (32, 64), 9: (16, 32), 11: (24, 48), 13: (24, 48)}[order]
     for N in Ns:
         spec = wl.random_1d("advection", N, jump=False, scheme="sharpclaw", char_decomp=0,
                             weno_order=order, weno_eps=1e30, params=[1.0])
@@ -162,7 +167,7 @@ def test_sharpclaw_operator_order_on_advection(orc, order):
     assert math.log2(errs[0] / errs[1]) >= order - 0.3, errs
 
 
-@pytest.mark.parametrize("order", [5, 7, 9])
+@pytest.mark.parametrize("order", [5, 7, 9, 11, 13, 15, 17])
 def test_sharpclaw_high_order_conserves_and_is_scalar_invariant(orc, order):
     """Periodic 2D Euler: sum of L over the grid vanishes (telescoping
     fluctuations); scalar advection: characteristic- and component-wise
