@@ -566,7 +566,8 @@ def profile_case(case, tile=None):
     acou2d -- 1024^2 constant-medium acoustics FP64, tile 128 x 32, 3 steps;
     psystem -- 1024^2 p-system checkerboard FP64, one SSP(10,4) step (10 stages);
     weno7 -- 1024x512 shock-bubble FP64, WENO7 + SSP(10,4), one step;
-    acou3d -- 256^3 constant-medium acoustics FP64, 3 steps."""
+    acou3d -- 256^3 constant-medium acoustics FP64, 3 steps (acou3d128: 128^3,
+    small enough for a multi-pass capture)."""
     import torch
     from paper_1111_6583_gb300 import claw
     from paper_1111_6583_gb300 import workloads as wl
@@ -603,8 +604,8 @@ def profile_case(case, tile=None):
         s = claw.Solver(sp, "fp64")
         s.set_t_end(0.2)
         s.advance(1)
-    elif case == "acou3d":
-        sp = wl.acoustics_3d(n=256)
+    elif case in ("acou3d", "acou3d128"):
+        sp = wl.acoustics_3d(n=256 if case == "acou3d" else 128)
         s = claw.Solver(sp, "fp64")
         s.set_t_end(sp["t_end"])
         s.advance(3)
@@ -643,7 +644,7 @@ def main():
                     help="BW,H: fixed 2D tile shape for --case sw2d1024 and --record-traffic")
     ap.add_argument("--case", default=None,
                     help="run one short launch sequence for a profiler (sw2d64, sw2d32, sw2d1024, "
-                         "elast, sharp, axisym, vc, acou2d, psystem, weno7, acou3d)")
+                         "elast, sharp, axisym, vc, acou2d, psystem, weno7, acou3d, acou3d128)")
     args = ap.parse_args()
     if args.record_traffic:
         if not args.tile:
