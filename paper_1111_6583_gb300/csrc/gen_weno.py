@@ -163,8 +163,8 @@ def emit(r):
     return "\n".join(out)
 
 
-def main():
-    here = os.path.dirname(os.path.abspath(__file__))
+def render():
+    """the text of weno_hi.cuh"""
     parts = ["// weno_hi.cuh -- generated by gen_weno.py from exact rational derivations;",
              "// do not edit.  Higher-order WENO reconstructions (Sec. 3.1, PyWENO",
              "// subsection) used by the SharpClaw stage kernel.",
@@ -173,8 +173,13 @@ def main():
         parts.append(emit(r))
         parts.append("")
     parts.append("}  // namespace claw")
+    return "\n".join(parts) + "\n"
+
+
+def main():
+    here = os.path.dirname(os.path.abspath(__file__))
     with open(os.path.join(here, "weno_hi.cuh"), "w") as f:
-        f.write("\n".join(parts) + "\n")
+        f.write(render())
 
 
 if __name__ == "__main__":
