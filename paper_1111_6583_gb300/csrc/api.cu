@@ -14,6 +14,7 @@
 #include <deque>
 #include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "claw_common.cuh"
@@ -1593,26 +1594,26 @@ claw_status claw_server_pump(claw_server* v, int steps, int* running, int* queue
       // not yet stepped first, then requests left out of kStarve pumps, then
       // by remaining work; ties by ticket (arrival order)
       constexpr int kStarve = 16;
-      std::vector<uint64_t> order = v->running;
-      auto key = [&](uint64_t t) {
+      const int nr = (int)v->running.size();
+      std::vector<std::tuple<int, double, uint64_t, int>> order(nr);
+      for (int i = 0; i < nr; ++i) {
+        const uint64_t t = v->running[i];
         const Req& r = v->reqs[t];
         const int cls = r.rem < 0 ? 0 : (r.idle >= kStarve ? 1 : 2);
-        return std::make_tuple(cls, cls == 2 ? r.rem : 0.0, t);
-      };
-      std::sort(order.begin(), order.end(),
-                [&](uint64_t a, uint64_t b) { return key(a) < key(b); });
+        order[i] = std::make_tuple(cls, cls == 2 ? r.rem : 0.0, t, i);
+      }
+      std::sort(order.begin(), order.end());
+      std::vector<int> picked;
       long long cells = 0;
-      for (uint64_t t : order) {
-        const Req& r = v->reqs[t];
-        if (cells >= v->sched_cells && r.rem >= 0 && r.idle < kStarve) continue;
-        sel.push_back(t);
+      for (const auto& o : order) {
+        const Req& r = v->reqs[std::get<2>(o)];
+        if (cells >= v->sched_cells && std::get<0>(o) == 2) continue;
+        picked.push_back(std::get<3>(o));
         cells += (long long)cells_of(r.g);
       }
       // keep the member order of the running list (tile tables stay stable)
-      std::vector<uint64_t> ordered;
-      for (uint64_t t : v->running)
-        if (std::find(sel.begin(), sel.end(), t) != sel.end()) ordered.push_back(t);
-      sel.swap(ordered);
+      std::sort(picked.begin(), picked.end());
+      for (int i : picked) sel.push_back(v->running[i]);
     }
     if (sel != v->sel) {
       std::vector<Member> hm;
