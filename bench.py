@@ -392,7 +392,7 @@ def bench_shockbubble(prec, steps, warmup, nx=2048, ny=1024, weno_order=5,
 
 
 def bench_axisym(prec, steps, warmup, nx=1280, ny=320, dim_split=0, source_split="godunov"):
-    """The axisymmetric shock-bubble of Sec. 6.2 at the paper's 1280 x 320:
+    """The axisymmetric shock-bubble of Sec. 7.2 at the paper's 1280 x 320:
     Euler + tracer, classic unsplit with full transverse corrections (or
     dimensionally split), geometric source by Godunov (or Strang) splitting;
     one step = the step kernel (two when split) + the source kernel (two for
@@ -475,7 +475,7 @@ def bench_acoustics_table1(prec, steps, warmup, nd, n):
 
 
 def bench_psystem(prec, steps, warmup, periods=32, cells_per_period=64):
-    """2D p-system in the checkerboard medium (Sec. 6.3), SharpClaw WENO5
+    """2D p-system in the checkerboard medium (Sec. 7.3), SharpClaw WENO5
     component-wise + SSP(10,4): one step = ten fused stage launches."""
     import torch
     from paper_1111_6583_gb300 import claw

@@ -4,15 +4,17 @@
  * Alghamdi, Quezada de Luna, Parsani, Knepley, Emmett: "PyClaw: Accessible,
  * Extensible, Scalable Tools for Wave Propagation Problems").
  *
- * The library advances  kappa q_t + div f(q, x) = s(q, x)  (Sec. 3,
- * Eq. (conslaw); kappa = 1, s = 0 here) on uniform Cartesian grids with
+ * The library advances  kappa q_t + div f(q, x) = s(q, x)  (Sec. 2,
+ * Eq. (conslaw); kappa = 1 unless a capacity field is named by capa_index,
+ * s = 0 unless claw_method.source names a source term) on uniform Cartesian
+ * grids with
  *   - Clawpack-classic: Godunov update in fluctuation form (Eq. (fluxdiff))
  *     plus limited second-order corrections (Eq. (lwflux)) and, in 2D,
- *     transverse corrections (Sec. 3.1, "transverse Riemann solver");
+ *     transverse corrections (Sec. 2.1, "transverse Riemann solver");
  *   - SharpClaw: WENO5 reconstruction of interface values, fluctuations from
- *     interface and in-cell Riemann problems, SSP-RK3 in time (Sec. 3 method
- *     of lines, Sec. 3.1);
- * each step ending with the CFL check and choice of the next step (Sec. 5).
+ *     interface and in-cell Riemann problems, SSP-RK3 in time (Sec. 2 method
+ *     of lines, Sec. 2.1);
+ * each step ending with the CFL check and choice of the next step (Sec. 4).
  *
  * Conventions
  *   - Every call returns claw_status (0 = CLAW_OK).  No call throws.
@@ -22,7 +24,7 @@
  *     claw_bind_state and frees them at destroy.
  *   - State layout: field-major, interior cells only, x fastest:
  *       q[m][nz][ny][nx] (3D), q[m][ny][nx] (2D), q[m][nx] (1D) -- PyClaw's
- *       field-major q[m, i, j] (Sec. 4.2).  3D adds double-transverse terms.
+ *       field-major q[m, i, j] (Sec. 3.2).  3D adds double-transverse terms.
  *     aux has the same layout with num_aux fields.
  *   - CLAW_FP64: q/aux are double.  CLAW_FP32: q/aux are float and the
  *     Riemann/limiter/WENO arithmetic is float; time, dt, the CFL number and
@@ -60,10 +62,10 @@ enum { CLAW_CLASSIC = 0, CLAW_SHARPCLAW = 1 };
 enum { CLAW_RP_ADVECTION = 0, CLAW_RP_ACOUSTICS = 1, CLAW_RP_SW_ROE = 2,
        CLAW_RP_EULER_ROE = 3, CLAW_RP_EULER_HLLE = 4, CLAW_RP_ELASTICITY_FWAVE = 5,
        CLAW_RP_EULER_TRACER = 6, CLAW_RP_ACOUSTICS_VC = 7 };
-/* Source terms (Eq. (conslaw) right-hand side) by fractional steps (Sec. 3;
- * Sec. 6.1 uses Strang's splitting): CLAW_SOURCE_AXISYMMETRIC is the
+/* Source terms (Eq. (conslaw) right-hand side) by fractional steps (Sec. 2;
+ * Sec. 7.1 uses Strang's splitting): CLAW_SOURCE_AXISYMMETRIC is the
  * geometric source of the Euler equations in cylindrical symmetry about
- * y = 0 (Sec. 6.2: (z, r) = (x, y); -(1/r)(rho v, rho u v, rho v^2,
+ * y = 0 (Sec. 7.2: (z, r) = (x, y); -(1/r)(rho v, rho u v, rho v^2,
  * (E + p) v), tracer none), integrated over each fractional step by a
  * two-stage second-order Runge-Kutta method.  CLAW_SPLIT_GODUNOV: the source
  * over dt after every accepted step; CLAW_SPLIT_STRANG: over dt/2 before the
@@ -74,13 +76,13 @@ enum { CLAW_SPLIT_GODUNOV = 1, CLAW_SPLIT_STRANG = 2 };
 enum { CLAW_LIM_NONE = 0, CLAW_LIM_MINMOD = 1, CLAW_LIM_SUPERBEE = 2, CLAW_LIM_VANLEER = 3,
        CLAW_LIM_MC = 4 };
 enum { CLAW_BC_PERIODIC = 0, CLAW_BC_WALL = 1, CLAW_BC_EXTRAP = 2, CLAW_BC_INFLOW = 3 };
-/* SharpClaw time integrators (Sec. 3.1): Shu-Osher three-stage SSP-RK3, and
+/* SharpClaw time integrators (Sec. 2.1): Shu-Osher three-stage SSP-RK3, and
  * Ketcheson's ten-stage fourth-order SSP(10,4) in its two-register low-storage
  * form (SSP coefficient 6, so the CFL limit is about six times that of one
  * forward-Euler stage spread over ten stages). */
 enum { CLAW_SSP_RK3 = 0, CLAW_SSP104 = 1 };
 
-/* Domain (Sec. 4.2: tensor product of equispaced 1D grids).  n[d] cells on
+/* Domain (Sec. 3.2: tensor product of equispaced 1D grids).  n[d] cells on
  * [lower[d], upper[d]]; entries beyond ndim are ignored. */
 typedef struct {
   int ndim;            /* 1, 2 or 3 (3D: classic scheme, advection and acoustics) */
@@ -88,7 +90,7 @@ typedef struct {
   double lower[3], upper[3];
 } claw_grid;
 
-/* Solver description (Sec. 4.2 Solver; Listing 1 and the SharpClaw listing). */
+/* Solver description (Sec. 3.2 Solver; Listing 1 and the SharpClaw listing). */
 typedef struct {
   int scheme;          /* CLAW_CLASSIC | CLAW_SHARPCLAW                          */
   int rp;              /* CLAW_RP_* Riemann solver                               */
@@ -96,7 +98,7 @@ typedef struct {
   int prec;            /* CLAW_FP64 | CLAW_FP32                                   */
   int order;           /* classic: 1 Godunov, 2 with limited corrections          */
   int transverse;      /* classic 2D: 0 none, 1 fluctuations, 2 with corrections  */
-  int weno_order;      /* SharpClaw: 5 (default), 7, 9, 11 or 13 (Sec. 3.1, PyWENO orders) */
+  int weno_order;      /* SharpClaw: 5 (default), 7, 9, 11 or 13 (Sec. 3.3, PyWENO orders) */
   int char_decomp;     /* SharpClaw: 0 component-wise, 1 characteristic-wise      */
   int entropy_fix;     /* Harten-Hyman fix in the Roe solvers (SW, Euler)         */
   int max_retries;     /* rejected attempts allowed per step                      */
@@ -153,7 +155,7 @@ claw_status claw_solver_create(const claw_method* m, const claw_grid* g, void* s
                                claw_solver** out);
 
 /* Bind the caller's device state q_dev (and aux_dev, NULL if num_aux == 0) at
- * time t0; allocates the work buffers and computes the first dt (Sec. 5).
+ * time t0; allocates the work buffers and computes the first dt (Sec. 4).
  * Data are read from q_dev on the stream; the caller must not write q_dev
  * while the handle runs.  Rebinding replaces the previous state. */
 claw_status claw_bind_state(claw_solver* s, void* q_dev, const void* aux_dev, double t0);
@@ -178,7 +180,7 @@ claw_status claw_solver_tune(claw_solver* s, int mode, int* bw, int* h);
 claw_status claw_advance(claw_solver* s, int n);
 claw_status claw_set_t_end(claw_solver* s, double t_end, int64_t max_steps);
 
-/* Advance to t_end (final step clipped to land on it, Sec. 5) or max_steps
+/* Advance to t_end (final step clipped to land on it, Sec. 4) or max_steps
  * accepted steps (<= 0: no limit).  use_graph != 0 replays a captured CUDA
  * graph of attempts.  The result is in q_dev on return. */
 claw_status claw_evolve_to_time(claw_solver* s, double t_end, int64_t max_steps, int use_graph,

@@ -153,7 +153,7 @@ static int euler_eig(const orc_prob* P, int a, int b, double un, double ut, doub
   return nw;
 }
 
-/* Euler with a passive tracer phi (phi_t + u . grad phi = 0, Sec. 6.2): the
+/* Euler with a passive tracer phi (phi_t + u . grad phi = 0, Sec. 7.2): the
  * Euler waves with a zero tracer component, and a tracer wave (jump of phi
  * alone) moving with the normal velocity, placed before the u + c wave so
  * that the first and last waves stay the acoustic ones. */
@@ -393,7 +393,7 @@ void orc_riemann(const orc_prob* P, int dir, const double* ql, const double* qr,
       break;
     }
     case ORC_RP_ELASTICITY_FWAVE: {
-      /* p-system (Sec. 6.3): sigma(eps) = exp(K eps) - 1, normal velocity
+      /* p-system (Sec. 7.3): sigma(eps) = exp(K eps) - 1, normal velocity
        * u_n = m_n / rho, normal flux (-u_n, -sigma) in the (eps, m_n)
        * components; the tangential momentum has no normal flux (2D) */
       int n = comp_n(P, dir), t = comp_t(P, dir);
@@ -576,7 +576,7 @@ static void correction_flux(const orc_prob* P, int m, int nw, const double* Wl,
 }
 
 /* ------------------------------------------------------------------------ */
-/* ghost cells (Sec. 5: periodic, reflecting, outflow, inflow)               */
+/* ghost cells (Sec. 4: periodic, reflecting, outflow, inflow)               */
 /* ------------------------------------------------------------------------ */
 
 static int wall_comp(const orc_prob* P, int dir) {
@@ -937,8 +937,8 @@ static int classic2d(const orc_prob* P, double* q, const double* aux, double dt,
 static int classic3d(const orc_prob* P, double* q, double dt, double* cfl);
 
 /* ------------------------------------------------------------------------ */
-/* source terms by fractional steps (Sec. 3, Eq. (conslaw) right-hand side;  */
-/* Sec. 6.2 axisymmetric Euler)                                              */
+/* source terms by fractional steps (Sec. 2, Eq. (conslaw) right-hand side;  */
+/* Sec. 7.2 axisymmetric Euler)                                              */
 /* ------------------------------------------------------------------------ */
 
 /* axisymmetric geometric source of the Euler equations in (z, r) = (x, y):
@@ -990,7 +990,7 @@ static void source_after(const orc_prob* P, double* q, double dt) {
 
 int orc_classic_step(const orc_prob* P, double* q, const double* aux, double dt, double* cfl) {
   if (P->ndim == 1) return classic1d(P, q, aux, dt, cfl);
-  /* the 2D p-system is solved with SharpClaw only (normal solves, Sec. 6.3) */
+  /* the 2D p-system is solved with SharpClaw only (normal solves, Sec. 7.3) */
   if (P->ndim == 2 && P->rp == ORC_RP_ELASTICITY_FWAVE) return ORC_EINVAL;
   if (P->ndim == 3) return classic3d(P, q, dt, cfl);
   int st;
@@ -1536,7 +1536,7 @@ int orc_sharp_step(const orc_prob* P, double* q, const double* aux, double dt, d
 }
 
 /* ------------------------------------------------------------------------ */
-/* CFL control (Sec. 5: check the Courant number, choose the next step)      */
+/* CFL control (Sec. 4: check the Courant number, choose the next step)      */
 /* ------------------------------------------------------------------------ */
 
 static void max_speeds3(const orc_prob* P, const double* q, double* smax) {

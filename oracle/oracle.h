@@ -6,14 +6,14 @@
  * call this code: only the tests, the smoke check and the benchmark's CPU
  * baseline leg use it.  It shares no header, helper, table or constant with the
  * CUDA library; the two sides are written independently from the paper
- * (Sec. 3: Eq. (conslaw), Eq. (fluxdiff), Eq. (lwflux); Sec. 3.1) and from the
+ * (Sec. 2: Eq. (conslaw), Eq. (fluxdiff), Eq. (lwflux); Sec. 2.1) and from the
  * published methods the paper cites (LeVeque 1997 wave propagation; LeVeque's
  * FVM book for limiters, Roe/transverse solvers and the Harten-Hyman entropy
  * fix; Ketcheson-Parsani-LeVeque for SharpClaw; Jiang-Shu WENO5; Shu-Osher
  * SSP-RK3; Einfeldt HLLE; Bale-LeVeque-Mitran-Rossmanith f-waves).
  *
  * Layout: q is field-major, interior cells only: q[m][nz][ny][nx] (x fastest),
- * matching PyClaw's q[m,i,j] field-major arrays (Sec. 4.2).  1D uses ny = 1.
+ * matching PyClaw's q[m,i,j] field-major arrays (Sec. 3.2).  1D uses ny = 1.
  */
 #ifndef CLAW_ORACLE_H
 #define CLAW_ORACLE_H
@@ -63,12 +63,12 @@ typedef struct {
    * weno_b[(k*r+a)*r+b] smoothness quadratic forms */
   double weno_c[81], weno_d[9], weno_b[729];
   int source;           /* 0 none; 1 axisymmetric Euler geometric source about y = 0
-                           (r = y; Sec. 6.2), by fractional steps (source_split) */
+                           (r = y; Sec. 7.2), by fractional steps (source_split) */
   int dim_split;        /* classic 2D: 0 unsplit; 1 dimensional splitting (x sweeps,
                            then y sweeps, Godunov) */
   double lower[2];      /* lower corner of the grid (cell centres for the source) */
   int capa_index;       /* aux field holding the capacity kappa (Eq. (conslaw)); -1 none */
-  int source_split;     /* fractional steps for the source (Sec. 3; Sec. 6.1 uses Strang):
+  int source_split;     /* fractional steps for the source (Sec. 2; Sec. 7.1 uses Strang):
                            1 Godunov, S(dt) after the step; 2 Strang, S(dt/2) before
                            and after it */
 } orc_prob;

@@ -1,5 +1,5 @@
 """WENO coefficients of odd order 2r-1 from their definitions, in exact
-rational arithmetic (Sec. 3.1, subsection on PyWENO: reconstruction
+rational arithmetic (Sec. 3.3 (PyWENO): reconstruction
 coefficients, optimal linear weights and smoothness coefficients computed
 symbolically for any order).
 

@@ -306,6 +306,15 @@ double now_s() {
 
 void claw::set_last_error(const char* msg) { g_err = msg; }
 
+// the same validation, constants and kernel sets for the library's other
+// translation units (the allocation-free step)
+const char* claw::validate_method(const claw_method& m, int nd) { return check_method(m, nd); }
+const char* claw::validate_grid(const claw_grid& g, const claw_method& m) {
+  return check_grid(g, m);
+}
+std::vector<unsigned char> claw::method_consts(const claw_method& m) { return make_consts(m); }
+claw::KernelSet claw::kernels_of(int rp, int nd, int prec) { return kernels_for(rp, nd, prec); }
+
 // ===========================================================================
 // single-grid solver
 // ===========================================================================
@@ -548,7 +557,7 @@ claw_status claw_method_init(claw_method* m, int rp, int ndim) {
     g_err = "unknown Riemann solver for this dimension";
     return CLAW_EINVAL;
   }
-  // the 2D p-system has normal solves only (Sec. 6.3 uses SharpClaw)
+  // the 2D p-system has normal solves only (Sec. 7.3 uses SharpClaw)
   m->scheme = (rp == CLAW_RP_ELASTICITY_FWAVE && ndim == 2) ? CLAW_SHARPCLAW : CLAW_CLASSIC;
   m->rp = rp;
   m->lim = CLAW_LIM_MC;

@@ -3,9 +3,9 @@
 // One launch = one attempt of one step for every member of a tile table:
 // ghost-cell remap in the loads, Riemann solve at every interface, wave
 // limiting, second-order corrections (Eq. (lwflux)), transverse corrections in
-// 2D (Sec. 3.1; LeVeque 1997), conservative update (Eq. (fluxdiff)) and the
+// 2D (Sec. 2.1; LeVeque 1997), conservative update (Eq. (fluxdiff)) and the
 // maximum wave speed.  In 2D the last block of a member to finish runs the
-// CFL controller (Sec. 5); in 1D each warp folds its speed into the control
+// CFL controller (Sec. 4); in 1D each warp folds its speed into the control
 // block by atomics and a controller launch follows the step kernel.
 #pragma once
 

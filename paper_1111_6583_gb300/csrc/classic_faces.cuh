@@ -1,5 +1,5 @@
-// classic_faces.cuh -- the classic step (Sec. 3, Eq. (fluxdiff), Eq. (lwflux);
-// Sec. 3.1 transverse propagation) on a per-face decomposition, for the cases
+// classic_faces.cuh -- the classic step (Sec. 2, Eq. (fluxdiff), Eq. (lwflux);
+// Sec. 2.1 transverse propagation) on a per-face decomposition, for the cases
 // the row-walk kernels do not cover: a capacity function kappa (Eq. (conslaw),
 // capacity-form differencing) in 1D or 2D, and 2D solvers whose transverse
 // split needs the media of the neighbouring cells.

@@ -1,9 +1,9 @@
 // claw_common.cuh -- device-side types shared by the kernels of libclawgpu.
 //
 // Control block, member (grid) descriptors, method constants, ghost-cell index
-// remapping (Sec. 5: periodic, reflecting, outflow, inflow ghost cells done
+// remapping (Sec. 4: periodic, reflecting, outflow, inflow ghost cells done
 // inside the tile loads, with no separate halo pass), block reductions and the
-// on-device CFL controller (Sec. 5: check the Courant number, choose the next
+// on-device CFL controller (Sec. 4: check the Courant number, choose the next
 // step).
 #pragma once
 

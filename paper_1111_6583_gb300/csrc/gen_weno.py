@@ -1,5 +1,5 @@
 """Generate weno_hi.cuh: device WENO reconstructions of odd order 2r-1 > 5
-(Sec. 3.1 and the PyWENO subsection: reconstruction coefficients, optimal
+(Sec. 3.3: reconstruction coefficients, optimal
 weights and smoothness coefficients derived symbolically for any order, then
 emitted as straight-line kernels).
 
@@ -166,7 +166,7 @@ def emit(r):
 def render():
     """the text of weno_hi.cuh"""
     parts = ["// weno_hi.cuh -- generated by gen_weno.py from exact rational derivations;",
-             "// do not edit.  Higher-order WENO reconstructions (Sec. 3.1, PyWENO",
+             "// do not edit.  Higher-order WENO reconstructions (Sec. 3.3, PyWENO",
              "// subsection) used by the SharpClaw stage kernel.",
              "#pragma once", "", '#include "riemann.cuh"', "", "namespace claw {", ""]
     for r in ORDERS_R:

@@ -6,6 +6,10 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
+#include "clawgpu.h"
+
 namespace claw {
 
 struct Member;
@@ -124,5 +128,12 @@ constexpr int kTotalsThreads = 256;
 
 // record the message that claw_last_error returns (api.cu)
 void set_last_error(const char* msg);
+
+// argument checks of the handle API (nullptr when valid, else the reason),
+// the method constants MConsts<R> as bytes, and a solver's kernel set (api.cu)
+const char* validate_method(const claw_method& m, int nd);
+const char* validate_grid(const claw_grid& g, const claw_method& m);
+std::vector<unsigned char> method_consts(const claw_method& m);
+KernelSet kernels_of(int rp, int nd, int prec);
 
 }  // namespace claw

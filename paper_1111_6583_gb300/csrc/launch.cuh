@@ -1,5 +1,5 @@
 // launch.cuh -- launchers of the fused kernels for one Riemann solver, and the
-// first-order wave-speed kernel used to choose the first dt (Sec. 5).
+// first-order wave-speed kernel used to choose the first dt (Sec. 4).
 #pragma once
 
 #include "classic.cuh"
@@ -96,7 +96,7 @@ inline int persistent_grid(int threads, int ntiles) {
   return ntiles < 1 ? 1 : (ntiles < cap ? ntiles : cap);
 }
 
-// Axisymmetric Euler geometric source (Sec. 6.2) by fractional steps: with
+// Axisymmetric Euler geometric source (Sec. 7.2) by fractional steps: with
 // r = y (cell centre) and v the radial velocity,
 // psi(q) = -(1/r) (rho v, rho u v, rho v^2, (E + p) v, 0 for a tracer), over a
 // time h by the two-stage Runge-Kutta method q1 = q + h psi(q),

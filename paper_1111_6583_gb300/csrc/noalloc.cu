@@ -56,48 +56,6 @@ cudaError_t scratch_address(void** out) {
   return cudaSuccess;
 }
 
-KernelSet noalloc_kernels(int rp, int nd, int prec) {
-  switch (rp) {
-    case CLAW_RP_ADVECTION: return claw_kernels_advection(nd, prec);
-    case CLAW_RP_ACOUSTICS: return claw_kernels_acoustics(nd, prec);
-    case CLAW_RP_SW_ROE: return claw_kernels_sw(nd, prec);
-    case CLAW_RP_EULER_ROE: return claw_kernels_euler_roe(nd, prec);
-    case CLAW_RP_EULER_HLLE: return claw_kernels_euler_hlle(nd, prec);
-    case CLAW_RP_ELASTICITY_FWAVE: return claw_kernels_elasticity(nd, prec);
-  }
-  return KernelSet{};
-}
-
-template <typename R>
-void noalloc_consts(const claw_method& m, MConsts<R>& C) {
-  std::memset(&C, 0, sizeof(C));
-  for (int k = 0; k < 8; ++k) {
-    C.p[k] = (R)m.params[k];
-    C.inflow[k] = (R)m.inflow[k];
-  }
-  if (m.rp == CLAW_RP_ACOUSTICS) {
-    const double c = std::sqrt(m.params[1] / m.params[0]);
-    const double Z = m.params[0] * c;
-    C.aco_c = (R)c;
-    C.aco_Z = (R)Z;
-    C.aco_h = (R)(1.0 / (2.0 * Z));
-  }
-  C.g = (R)m.params[0];
-  C.gamma = (R)m.params[0];
-  C.gm1 = (R)(m.params[0] - 1.0);
-  C.weno_eps = (R)m.weno_eps;
-  C.capa = -1;  // no capacity field on this path
-  C.lim = m.lim;
-  C.order = m.order;
-  C.transverse = m.transverse;
-  C.entropy_fix = m.entropy_fix;
-  C.char_decomp = m.char_decomp;
-  for (int d = 0; d < 2; ++d) {
-    C.bc_lo[d] = m.bc_lower[d];
-    C.bc_hi[d] = m.bc_upper[d];
-  }
-}
-
 size_t al256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // errors are reported through claw_last_error
@@ -116,22 +74,30 @@ claw_status claw_sharp_step_noalloc(const claw_method* m, const claw_grid* g, co
                                     void* q_out, const void* aux, double dt, void* stream,
                                     double* cfl) {
   if (!m || !g || !q_in || !q_out) return nfail("null argument");
+  // the checks of the handle API first (grid extents up to INT_MAX / 2,
+  // num_eqn and num_aux against the solver, limiter, precision, boundaries...)
+  if (const char* why = validate_grid(*g, *m)) return nfail(why);
+  if (const char* why = validate_method(*m, g->ndim)) return nfail(why);
+  // then what this step does not take
   if (m->scheme != CLAW_SHARPCLAW) return nfail("claw_sharp_step_noalloc needs scheme SharpClaw");
   if (g->ndim != 1 && g->ndim != 2) return nfail("ndim must be 1 or 2");
-  const int nx = (int)g->n[0], ny = g->ndim == 2 ? (int)g->n[1] : 1;
-  if (g->n[0] < 4 || (g->ndim == 2 && g->n[1] < 4)) return nfail("each direction needs >= 4 cells");
   if (m->weno_order != 5) return nfail("the allocation-free step takes WENO5 only");
-  if (m->capa_index != -1 || m->source != 0)
+  if (m->time_integrator != CLAW_SSP_RK3)
+    return nfail("the allocation-free step takes the SSP-RK3 integrator only");
+  if (m->capa_index != -1 || m->source != CLAW_SOURCE_NONE)
     return nfail("the allocation-free step takes no capacity or source term");
   if (!(dt > 0)) return nfail("dt must be positive");
-  if (m->num_aux > 0 && !aux) return nfail("this solver needs aux fields");
-  if (m->char_decomp && m->rp == CLAW_RP_ELASTICITY_FWAVE)
-    return nfail("no characteristic projection for the f-wave elasticity solver");
-  KernelSet ks = noalloc_kernels(m->rp, g->ndim, m->prec);
-  if (!ks.valid || ks.M != m->num_eqn) return nfail("unsupported solver/dimension/precision");
-  for (int d = 0; d < g->ndim; ++d)
-    if ((m->bc_lower[d] == CLAW_BC_PERIODIC) != (m->bc_upper[d] == CLAW_BC_PERIODIC))
-      return nfail("periodic boundaries must be paired");
+  KernelSet ks = kernels_of(m->rp, g->ndim, m->prec);
+  if (!ks.valid || ks.M != m->num_eqn || !ks.sharp)
+    return nfail("unsupported solver/dimension/precision");
+  if (m->num_aux != ks.MA) return nfail("num_aux does not match the Riemann solver");
+  if (ks.MA > 0 && !aux) return nfail("this solver needs aux fields");
+  if (q_in == q_out) return nfail("q_in and q_out must be different buffers");
+  const int nx = (int)g->n[0], ny = g->ndim == 2 ? (int)g->n[1] : 1;
+  // cell count first, so the byte count below cannot wrap
+  if ((size_t)nx * (size_t)ny > kNoallocScratchBytes)
+    return nfail("grid too large for the no-allocation step: more cells than the " +
+                 std::to_string(kNoallocScratchBytes) + "-byte scratch array holds");
 
   // scratch layout: [stage 1 state][stage 2 state][control block][2 descriptors]
   const size_t es = m->prec == CLAW_FP64 ? 8 : 4;
@@ -192,9 +158,13 @@ claw_status claw_sharp_step_noalloc(const claw_method* m, const claw_grid* g, co
       cudaSuccess)
     return nfail("descriptor upload", e);
 
+  // method constants on the host stack: the kernels take them by value
   alignas(16) unsigned char consts[sizeof(MConsts<double>)];
-  if (m->prec == CLAW_FP64) noalloc_consts<double>(*m, *(MConsts<double>*)consts);
-  else noalloc_consts<float>(*m, *(MConsts<float>*)consts);
+  {
+    const std::vector<unsigned char> v = method_consts(*m);
+    if (v.size() > sizeof(consts)) return nfail("method constants do not fit");
+    std::memcpy(consts, v.data(), v.size());
+  }
   for (int s = 0; s < 3; ++s) {
     LaunchArgs a{s < 2 ? mem : mem_last, nullptr, ntiles, consts, 0, 0, s, st};
     if ((e = ks.sharp(a)) != cudaSuccess) return nfail("stage launch", e);

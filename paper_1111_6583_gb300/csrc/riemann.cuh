@@ -4,10 +4,10 @@
 // Each solver is a policy struct templated on the working precision R and the
 // dimension ND, with compile-time direction DIR (0 = x, 1 = y):
 //   solve<DIR>(C, ql, qr, al, ar, W, s, am, ap, ctx)   normal solve: waves W^p,
-//       speeds s^p, fluctuations A^-dQ, A^+dQ (Sec. 3, fluctuation form) and a
+//       speeds s^p, fluctuations A^-dQ, A^+dQ (Sec. 2, fluctuation form) and a
 //       linearisation ctx kept for the transverse solve;
 //   trans<DIR>(C, ctx, a, bm, bp)   split a normal fluctuation a into the
-//       down-/up-going transverse fluctuations B^-a, B^+a (Sec. 3.1);
+//       down-/up-going transverse fluctuations B^-a, B^+a (Sec. 2.1);
 //   to_char / from_char   characteristic projection for SharpClaw.
 // Formulas: LeVeque, Finite Volume Methods for Hyperbolic Problems (acoustics,
 // shallow-water and Euler Roe solvers, Harten-Hyman entropy fix, transverse
@@ -805,9 +805,9 @@ struct RpEulerHLLE : EulerBase<R, ND> {
 
 // ---------------------------------------------------------------------------
 // nonlinear elasticity / p-system (eps, rho u) with f-waves, aux (rho, K),
-// sigma(eps) = exp(K eps) - 1 (Sec. 6.3 constitutive law, shifted to sigma(0)=0)
+// sigma(eps) = exp(K eps) - 1 (Sec. 7.3 constitutive law, shifted to sigma(0)=0)
 // ---------------------------------------------------------------------------
-// Nonlinear elasticity / p-system with f-waves (Sec. 6.3; Bale-LeVeque-
+// Nonlinear elasticity / p-system with f-waves (Sec. 7.3; Bale-LeVeque-
 // Mitran-Rossmanith f-wave splitting): q = (eps, m_x[, m_y]), aux (rho, K) per
 // cell, sigma = exp(K eps) - 1, normal flux (-m_n/rho, -sigma) in the
 // (eps, m_n) components and none in the tangential momentum.  Each side uses
@@ -1011,7 +1011,7 @@ struct trans_aux_rp<RP, decltype((void)RP::TRANS_AUX, void())> {
 };
 
 // ---------------------------------------------------------------------------
-// Euler with a passive tracer phi (phi_t + u . grad phi = 0; Sec. 6.2): the
+// Euler with a passive tracer phi (phi_t + u . grad phi = 0; Sec. 7.2): the
 // Euler Roe solver on the first ND + 2 components and a tracer wave (the jump
 // of phi alone) moving with the normal Roe velocity, placed before the u + c
 // wave.  The tracer equation is not in conservation form, so SharpClaw's

@@ -1,5 +1,5 @@
-// sharpclaw.cuh -- fused SharpClaw stage kernel (Sec. 3 method of lines;
-// Sec. 3.1: WENO reconstruction, normal Riemann problems only in multi-D).
+// sharpclaw.cuh -- fused SharpClaw stage kernel (Sec. 2 method of lines;
+// Sec. 2.1: WENO reconstruction, normal Riemann problems only in multi-D).
 //
 // One launch = one Runge-Kutta stage for every member of a tile table.  A
 // block stages a TX x TY tile of Q^(k) plus an RW-cell halo (ghost remap in

@@ -110,7 +110,7 @@ def sw_dambreak_2d(n=1024, t_end=1.5, transverse=2, lim="mc"):
 
 
 # --------------------------------------------------------------------------
-# 2D Euler shock-bubble (Sec. 6.2, planar form)
+# 2D Euler shock-bubble (Sec. 7.2, planar form)
 # --------------------------------------------------------------------------
 def post_shock_state(mach=2.0, gamma=1.4, rho1=1.0, p1=1.0):
     """Rankine-Hugoniot state behind a shock of the given Mach number moving
@@ -172,7 +172,7 @@ def post_shock_state_from_pressure(p2, gamma=1.4, rho1=1.0, p1=1.0):
 
 def shock_bubble_axisym(nx=1280, ny=320, t_end=0.6, scheme="classic", gamma=1.4, sub=16,
                         dim_split=0, cfl=(0.8, 1.0), source_split="godunov"):
-    """The shock-bubble interaction of Sec. 6.2 in its axisymmetric form:
+    """The shock-bubble interaction of Sec. 7.2 in its axisymmetric form:
     (z, r) = (x, y) on [0, 2] x [0, 0.5], Euler with a passive tracer and the
     geometric source -(1/r)(rho v, rho u v, rho v^2, (E + p) v) by Godunov
     (or Strang) splitting.  Ahead of the shock rho = p = 1 at rest; a sphere of rho = 0.1
@@ -233,7 +233,7 @@ def euler_quadrants_2d(n=100, t_end=0.3, gamma=1.4):
 
 
 # --------------------------------------------------------------------------
-# 1D nonlinear elasticity in a layered medium (Sec. 6.3, 1D analogue)
+# 1D nonlinear elasticity in a layered medium (Sec. 7.3, 1D analogue)
 # --------------------------------------------------------------------------
 def layered_medium(x, width=0.5):
     """(rho, K) = (1, 1) on even layers [2k w, (2k+1) w), (4, 4) on odd ones."""
@@ -273,7 +273,7 @@ def elasticity_ensemble(members=4096, seed=SEED, lo_exp=12, hi_exp=16, t_end=50.
 # serving stream: 2D shallow-water humps
 # --------------------------------------------------------------------------
 def checkerboard_medium(x, y, k_hi=5.0, rho_hi=5.0):
-    """(rho, K) of the checkerboard crystal of Sec. 6.3: (1, 1) where
+    """(rho, K) of the checkerboard crystal of Sec. 7.3: (1, 1) where
     (x - floor(x) - 1/2)(y - floor(y) - 1/2) < 0, (rho_hi, k_hi) where > 0
     (lengths in material periods)."""
     s = (x - np.floor(x) - 0.5) * (y - np.floor(y) - 0.5)
@@ -283,7 +283,7 @@ def checkerboard_medium(x, y, k_hi=5.0, rho_hi=5.0):
 
 def psystem_checkerboard_2d(periods=32, cells_per_period=64, amp=5.0, var=5.0, t_end=20.0,
                             weno_order=5, integrator="ssp104", cfl=(1.0, 1.2)):
-    """2D p-system in the checkerboard medium (Sec. 6.3) at reduced size:
+    """2D p-system in the checkerboard medium (Sec. 7.3) at reduced size:
     the positive quadrant [0, periods]^2, walls at x = 0 and y = 0 (the
     problem's mirror symmetry), zero-order extrapolation at the far sides,
     Gaussian stress pulse sigma_0 = amp exp(-(x^2 + y^2) / (2 var)) at the

@@ -1,6 +1,6 @@
 """Checks against the cited fixtures under tests/golden/: values the paper
-prints (the shock-bubble post-shock state of Sec. 6.2, the checkerboard rule
-of Sec. 6.3) and Toro's tabulated star state of Sod's problem, which pins the
+prints (the shock-bubble post-shock state of Sec. 7.2, the checkerboard rule
+of Sec. 7.3) and Toro's tabulated star state of Sod's problem, which pins the
 exact Riemann solver that the oracle's Sod convergence pins compare with.
 """
 import os

@@ -1,4 +1,4 @@
-"""GPU parity of the axisymmetric shock-bubble pieces (Sec. 6.2) against the
+"""GPU parity of the axisymmetric shock-bubble pieces (Sec. 7.2) against the
 oracle: the Euler Roe solver with a passive tracer (classic and SharpClaw),
 dimensionally split classic steps, and the geometric source applied after
 accepted steps only (Godunov splitting), alone and in batches.

@@ -1,4 +1,4 @@
-"""GPU parity of the 2D p-system in a checkerboard medium (Sec. 6.3: f-wave
+"""GPU parity of the 2D p-system in a checkerboard medium (Sec. 7.3: f-wave
 normal solves with per-cell (rho, K), SharpClaw WENO) against the oracle.
 """
 import numpy as np

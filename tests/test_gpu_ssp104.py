@@ -1,5 +1,5 @@
 """GPU parity of SharpClaw with the ten-stage fourth-order SSP(10,4) time
-integrator (Sec. 3.1; Ketcheson 2008, low-storage form) against the oracle:
+integrator (Sec. 2.1; Ketcheson 2008, low-storage form) against the oracle:
 fixed steps in 1D and 2D, the CFL controller at Courant numbers above one
 (the method's SSP coefficient is 6), and batched members equal to solves
 alone.

@@ -1,4 +1,4 @@
-"""GPU parity of SharpClaw with WENO of orders 7 to 13 (Sec. 3.1 and the
+"""GPU parity of SharpClaw with WENO of orders 7 to 13 (Sec. 2.1 and the
 PyWENO subsection) against the oracle, whose coefficients come from an
 independent exact derivation: every Riemann solver in 1D, the 2D systems,
 component- and characteristic-wise, boundary conditions that reach the

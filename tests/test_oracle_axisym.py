@@ -1,5 +1,5 @@
 """Pins for the oracle's pieces of the axisymmetric shock-bubble setup
-(Sec. 6.2): the Euler Roe solver with a passive tracer, the geometric source
+(Sec. 7.2): the Euler Roe solver with a passive tracer, the geometric source
 by Godunov splitting, and dimensionally split classic steps.
 
 Pinned against closed forms and reductions that do not use the oracle's own

@@ -1,4 +1,4 @@
-"""Pins for the oracle's 2D p-system (Sec. 6.3: strain and momenta in a
+"""Pins for the oracle's 2D p-system (Sec. 7.3: strain and momenta in a
 spatially varying medium, f-wave normal solves, SharpClaw WENO).
 
 Pinned against facts that do not come from the oracle's own formulas: the

@@ -1,5 +1,5 @@
-"""Pins for the source term by Strang splitting (Sec. 3 operator splitting;
-Sec. 6.1 uses Strang's method): half a source step, the hyperbolic step,
+"""Pins for the source term by Strang splitting (Sec. 2 operator splitting;
+Sec. 7.1 uses Strang's method): half a source step, the hyperbolic step,
 half a source step.
 
 Pinned by orders of accuracy, consistency and controller behaviour, not by

@@ -1,4 +1,4 @@
-"""Pins for the oracle's WENO reconstructions of odd order 2r-1 (Sec. 3.1 and
+"""Pins for the oracle's WENO reconstructions of odd order 2r-1 (Sec. 2.1 and
 the PyWENO subsection: reconstruction coefficients, optimal weights and
 smoothness coefficients of any order) and for SharpClaw with WENO7/WENO9.
 

@@ -1,7 +1,7 @@
 """The generator of the GPU's WENO 7..13 reconstructions (csrc/gen_weno.py)
 against the oracle's independent derivation (oracle/weno_coeffs.py), exactly
 in rational arithmetic: candidate coefficients, optimal weights and
-smoothness forms (Sec. 3.1, PyWENO subsection), and the emitted sum-of-squares
+smoothness forms (Sec. 3.3, PyWENO), and the emitted sum-of-squares
 form of each smoothness indicator.  No GPU needed."""
 import importlib.util
 import os
