@@ -4,8 +4,8 @@ SharpClaw (PyClaw, Ketcheson et al.).
 TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
 benchmark's CPU-baseline leg may import this package.  It shares no code with
 the CUDA library: the C source ``oracle.c`` is an independent restatement of
-the method (Sec. 3, Eq. (fluxdiff) and Eq. (lwflux); Sec. 3.1 on transverse
-solvers and SharpClaw; Sec. 5 on ghost cells and the CFL check).
+the method (Sec. 2, Eq. (fluxdiff) and Eq. (lwflux); Sec. 2.1 on transverse
+solvers and SharpClaw; Sec. 4 on ghost cells and the CFL check).
 
 Every function here marshals numpy arrays into the C oracle; no arithmetic of
 the method is done in Python.
@@ -16,6 +16,7 @@ the paper prints no worked example, so no pin uses a printed value.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -91,38 +92,66 @@ def _load():
     global _lib
     if _lib is None:
         build()
-        lib = ctypes.CDLL(_SO)
-        P = ctypes.POINTER(_Prob)
-        lib.orc_num_eqn.restype = ctypes.c_int
-        lib.orc_num_waves.restype = ctypes.c_int
-        lib.orc_riemann.argtypes = [P, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
-        lib.orc_transverse.argtypes = [P, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
-        lib.orc_phi.restype = ctypes.c_double
-        lib.orc_phi.argtypes = [ctypes.c_int, ctypes.c_double]
-        lib.orc_weno5.restype = ctypes.c_double
-        lib.orc_weno5.argtypes = [_dp, ctypes.c_double]
-        lib.orc_weno_r.restype = ctypes.c_double
-        lib.orc_weno_r.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp, ctypes.c_double]
-        lib.orc_char_matrices.argtypes = [P, ctypes.c_int, _dp, _dp, _dp, _dp]
-        lib.orc_fill_ghost.argtypes = [P, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
-        lib.orc_classic_step.argtypes = [P, _dp, _dp, ctypes.c_double, _dp]
-        lib.orc_sharp_L.argtypes = [P, _dp, _dp, _dp, _dp]
-        lib.orc_sharp_step.argtypes = [P, _dp, _dp, ctypes.c_double, _dp]
-        lib.orc_ssp_rk3_linear.restype = ctypes.c_double
-        lib.orc_ssp_rk3_linear.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
-        lib.orc_ssp104_linear.restype = ctypes.c_double
-        lib.orc_ssp104_linear.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
-        lib.orc_max_speeds.argtypes = [P, _dp, _dp, _dp]
-        lib.orc_transverse_vc.restype = None
-        lib.orc_transverse_vc.argtypes = [P, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
-        lib.orc_source_step.restype = None
-        lib.orc_source_step.argtypes = [P, _dp, ctypes.c_double]
-        lib.orc_evolve.argtypes = [P, _dp, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
-                                   ctypes.POINTER(_RunInfo)]
-        lib.orc_totals.argtypes = [P, _dp, _dp]
-        lib.orc_threads.restype = ctypes.c_int
-        _lib = lib
+        _lib = _bind(ctypes.CDLL(_SO))
     return _lib
+
+
+def build_variant(source_text: str, path: str) -> str:
+    """Compile a modified copy of oracle.c into the shared library ``path``
+    (same flags as build()).  Tests use it to plant a mistake in the oracle
+    and check that the pins catch it; the oracle itself is never changed."""
+    src = path + ".c"
+    with open(src, "w") as f:
+        f.write(source_text)
+    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC",
+                    "-shared", "-std=c11", "-I" + _HERE, src, "-o", path, "-lm"], check=True)
+    return path
+
+
+@contextlib.contextmanager
+def variant(path: str):
+    """Run the functions of this module on the library ``path`` (a variant from
+    build_variant) inside the with-block."""
+    global _lib
+    saved = _load()
+    _lib = _bind(ctypes.CDLL(path))
+    try:
+        yield
+    finally:
+        _lib = saved
+
+
+def _bind(lib):
+    P = ctypes.POINTER(_Prob)
+    lib.orc_num_eqn.restype = ctypes.c_int
+    lib.orc_num_waves.restype = ctypes.c_int
+    lib.orc_riemann.argtypes = [P, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+    lib.orc_transverse.argtypes = [P, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+    lib.orc_phi.restype = ctypes.c_double
+    lib.orc_phi.argtypes = [ctypes.c_int, ctypes.c_double]
+    lib.orc_weno5.restype = ctypes.c_double
+    lib.orc_weno5.argtypes = [_dp, ctypes.c_double]
+    lib.orc_weno_r.restype = ctypes.c_double
+    lib.orc_weno_r.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp, ctypes.c_double]
+    lib.orc_char_matrices.argtypes = [P, ctypes.c_int, _dp, _dp, _dp, _dp]
+    lib.orc_fill_ghost.argtypes = [P, _dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp]
+    lib.orc_classic_step.argtypes = [P, _dp, _dp, ctypes.c_double, _dp]
+    lib.orc_sharp_L.argtypes = [P, _dp, _dp, _dp, _dp]
+    lib.orc_sharp_step.argtypes = [P, _dp, _dp, ctypes.c_double, _dp]
+    lib.orc_ssp_rk3_linear.restype = ctypes.c_double
+    lib.orc_ssp_rk3_linear.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
+    lib.orc_ssp104_linear.restype = ctypes.c_double
+    lib.orc_ssp104_linear.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
+    lib.orc_max_speeds.argtypes = [P, _dp, _dp, _dp]
+    lib.orc_transverse_vc.restype = None
+    lib.orc_transverse_vc.argtypes = [P, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp]
+    lib.orc_source_step.restype = None
+    lib.orc_source_step.argtypes = [P, _dp, ctypes.c_double]
+    lib.orc_evolve.argtypes = [P, _dp, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                               ctypes.POINTER(_RunInfo)]
+    lib.orc_totals.argtypes = [P, _dp, _dp]
+    lib.orc_threads.restype = ctypes.c_int
+    return lib
 
 
 def _ptr(a):

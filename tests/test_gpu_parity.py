@@ -277,3 +277,70 @@ def test_checkpoint_restore_bitwise():
     assert np.array_equal(b.q.cpu().numpy(), qa)
     a.close()
     b.close()
+
+
+# --------------------------------------------------------------------------
+# transonic rarefactions: the entropy fix acts at the sonic point
+# --------------------------------------------------------------------------
+def _sonic_sod_spec(n, order):
+    """Toro's sonic-rarefaction Sod variant (x0 = 0.3, t = 0.2)."""
+    g = 1.4
+    x = (np.arange(n) + 0.5) / n
+    left = x < 0.3
+    rho = np.where(left, 1.0, 0.125)
+    u = np.where(left, 0.75, 0.0)
+    p = np.where(left, 1.0, 0.1)
+    spec = wl._base(1, [n], [0.0], [1.0], "euler_roe", params=[g], order=order,
+                    bc_lower=["extrap"], bc_upper=["extrap"])
+    spec.update(q0=np.ascontiguousarray(np.stack([rho, rho * u, p / (g - 1) + 0.5 * rho * u * u])),
+                aux=None)
+    return spec
+
+
+def _dambreak10_spec(n, order, ndim=1, axis=0):
+    """Dam break h = 10 | 1 (transonic rarefaction) on [-5, 5]; in 2D the data
+    vary along `axis` only, with walls across it and periodic along the other."""
+    if ndim == 1:
+        x = -5.0 + (np.arange(n) + 0.5) * 10.0 / n
+        spec = wl._base(1, [n], [-5.0], [5.0], "sw_roe", params=[1.0], order=order,
+                        bc_lower=["extrap"], bc_upper=["extrap"])
+        spec.update(q0=np.ascontiguousarray(np.stack([np.where(x < 0, 10.0, 1.0), np.zeros(n)])),
+                    aux=None)
+        return spec
+    m = 19
+    shape = (m, n) if axis == 0 else (n, m)  # (ny, nx)
+    nn = [n, m] if axis == 0 else [m, n]
+    lo = [-5.0, 0.0] if axis == 0 else [0.0, -5.0]
+    hi = [5.0, 1.0] if axis == 0 else [1.0, 5.0]
+    bcl = ["extrap", "periodic"] if axis == 0 else ["periodic", "extrap"]
+    x = -5.0 + (np.arange(n) + 0.5) * 10.0 / n
+    h1 = np.where(x < 0, 10.0, 1.0)
+    h = np.broadcast_to(h1[None, :] if axis == 0 else h1[:, None], shape)
+    spec = wl._base(2, nn, lo, hi, "sw_roe", params=[1.0], order=order, bc_lower=bcl,
+                    bc_upper=list(bcl))
+    spec.update(q0=np.ascontiguousarray(np.stack([h, np.zeros(shape), np.zeros(shape)])), aux=None)
+    return spec
+
+
+@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("case", ["sonic_sod", "dambreak10"])
+def test_entropy_fix_transonic_full_run(orc, case, order):
+    """Controller runs to t_end on data whose rarefaction crosses the sonic
+    point, so the Harten-Hyman split acts in every step."""
+    spec = _sonic_sod_spec(437, order) if case == "sonic_sod" else _dambreak10_spec(437, order)
+    t_end = 0.2 if case == "sonic_sod" else 0.5
+    qo, io = oracle_evolve(orc, spec, t_end)
+    qg, ig = gpu_evolve(spec, "fp64", t_end)
+    assert ig["steps"] == io["steps"] and ig["t"] == t_end
+    assert rel_maxnorm(qg, qo) <= FP64_TOL
+    q32, _ = gpu_evolve(spec, "fp32", t_end)
+    assert rel_l1(q32, qo) <= FP32_SHOCK_L1_TOL
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_entropy_fix_transonic_2d_both_directions(orc, axis):
+    spec = _dambreak10_spec(211, 2, ndim=2, axis=axis)
+    qo, io = oracle_evolve(orc, spec, 0.5)
+    qg, ig = gpu_evolve(spec, "fp64", 0.5)
+    assert ig["steps"] == io["steps"] and ig["t"] == 0.5
+    assert rel_maxnorm(qg, qo) <= FP64_TOL
