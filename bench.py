@@ -33,19 +33,23 @@ METRIC = "cell-updates/s & % HBM peak, FP64 plain vs FP32 batched; p50/p99 solve
 UNIT = "cell-updates/s"
 L2_FLUSH_BYTES = 512 << 20
 
-# Algorithmic work per cell update of the headline kernel (2D SW classic,
-# Roe + HH fix, MC, transverse 2).  FLOPs: the FP64 add/sub/mul/div/sqrt
-# operations the method's formulas take per cell (two normal solves, two
-# limited corrections, four transverse splits, the update) -- 853 counted on
-# an instrumented build of the CPU oracle, less the 80 its transverse solves
-# spend recomputing the interface Roe averages; min/max/abs/compare not
-# counted.  Bytes: one read and one write of the three conserved fields.
-SW2D_FLOPS_PER_CELL = 773.0
+# Algorithmic work per cell update, counted on the oracle's own arithmetic by
+# oracle/flop_count.cpp (FP add/sub/mul/div/sqrt/exp; min, max, abs and
+# compares not counted; a CPU test pins these constants to its output):
+# - headline 2D SW classic (Roe + HH, MC, transverse 2): the oracle's step on
+#   smooth data with every wave non-zero (904.95 per cell at 1024^2) less the
+#   four Roe averages (20 each) its transverse solver re-derives per cell,
+#   which the kernel takes from the normal solve;
+# - SharpClaw 2D Euler, WENO5 characteristic-wise: one L(Q) evaluation per
+#   stage (three per SSP-RK3 step);
+# - 1D elasticity f-wave classic step.
+# Bytes: one read and one write of the conserved fields (plus aux reads).
+SW2D_FLOPS_PER_CELL = 825.0
+EULER2D_WENO5_FLOPS_PER_CELL_STAGE = 3032.4
+ELAST1D_FLOPS_PER_CELL = 96.0
 SW2D_BYTES_PER_CELL = {"fp64": 48.0, "fp32": 24.0}
 ELAST1D_BYTES_PER_CELL = {"fp64": 48.0, "fp32": 24.0}  # q read+write, aux read
-# FP64 ALU peak derived from unit counts and clocks: 152 SMs x 2.07 GHz x
-# 4 FP64 FLOP/clk/SM (two FP64 FMA lanes per SM) = 1.259 TFLOP/s.
-FP64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12
+ACOU1D_BYTES_PER_CELL = {"fp64": 32.0, "fp32": 16.0}   # q read+write
 
 
 TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "traffic_classic2d_sw_fp64_1024.json")
@@ -95,10 +99,10 @@ def record_traffic(csv_path, tile):
     t = "%d,%d" % tuple(tile)
     rec = {"kernel": "classic2d_kernel<RpSW<double,2>>", "workload": "dam break 1024x1024 FP64",
            "tile": list(tile), "dram_bytes_per_launch": b, "sources_sha256": kernel_sha(),
-           "command": "python bench.py --case sw2d1024 --tile %s > gpurun_out/plain.log 2>&1 && "
+           "command": "python bench.py --case sw2d1024 --tile %s > plain.log 2>&1 && "
                       "ncu --metrics gpu__time_duration.sum,dram__bytes_read.sum,"
                       "dram__bytes_write.sum --clock-control none -k regex:classic2d --csv "
-                      "--log-file gpurun_out/traffic_sw2d.csv python bench.py --case sw2d1024 "
+                      "--log-file traffic_sw2d.csv python bench.py --case sw2d1024 "
                       "--tile %s" % (t, t)}
     json.dump(rec, open(TRAFFIC_RECORD, "w"), indent=1)
     print(json.dumps(rec))
@@ -222,6 +226,8 @@ def timed_steps(solver, stream, steps, flush):
 
 
 def bench_sw2d(prec, steps, warmup, n=1024):
+    """Timed step attempts of the dam break; also returns how many of them the
+    controller accepted (the headline counts accepted steps only)."""
     import torch
     from paper_1111_6583_gb300 import claw
     from paper_1111_6583_gb300 import workloads as wl
@@ -234,8 +240,10 @@ def bench_sw2d(prec, steps, warmup, n=1024):
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
         s.advance(warmup)
     stream.synchronize()
+    before = s.info()["steps"]
     ms = timed_steps(s, stream, steps, flush)
     info = s.info()
+    info["accepted_in_timed"] = info["steps"] - before
     s.close()
     return spec, ms, info, (bw, h)
 
@@ -498,6 +506,256 @@ def bench_psystem(prec, steps, warmup, periods=32, cells_per_period=64):
                                                    prec.upper())}
 
 
+def _sig(x, d=4):
+    """x rounded to d significant digits (None and non-numbers pass through)."""
+    if isinstance(x, bool) or not isinstance(x, (int, float)) or x == 0 or x != x:
+        return x
+    import math
+    return round(x, d - 1 - int(math.floor(math.log10(abs(x)))))
+
+
+def _compact(o):
+    if isinstance(o, dict):
+        return {k: _compact(v) for k, v in o.items()}
+    if isinstance(o, (list, tuple)):
+        return [_compact(v) for v in o]
+    return _sig(o)
+
+
+def bench_acoustics_1d(prec="fp64", n=2000, t_end=2.0):
+    """The 1D acoustics pulse (2000 cells, periodic, MC, CFL 0.9) run to t = 2
+    with the controller from replayed CUDA graphs of step attempts: time per
+    accepted step and steps per second (the state is 32 KB: latency-bound)."""
+    import torch
+    from paper_1111_6583_gb300 import claw
+    from paper_1111_6583_gb300 import workloads as wl
+    spec = wl.acoustics_1d(n=n, t_end=t_end)
+    out = {}
+    for rep in range(2):  # the first run builds and uploads the graphs
+        s = claw.Solver(spec, prec)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        info = s.evolve(t_end, use_graph=True)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        s.close()
+        out = {"steps": info["steps"], "t": info["t"], "us_per_step": ms * 1e3 / info["steps"],
+               "steps_per_s": info["steps"] / (ms * 1e-3),
+               "value": n * info["steps"] / (ms * 1e-3), "unit": UNIT}
+    return out
+
+
+def bench_acoustics_1d_hbm(prec, steps, warmup, log2n=26):
+    """Roofline form of the 1D acoustics step: 2^26 cells (same physics, the
+    pulse on a longer periodic line), one fused step kernel + controller per
+    step; algorithmic bytes = one read and one write of the two fields."""
+    import torch
+    from paper_1111_6583_gb300 import claw
+    from paper_1111_6583_gb300 import workloads as wl
+    n = 1 << log2n
+    spec = wl.acoustics_1d(n=n, t_end=1e9)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = claw.Solver(spec, prec, stream=stream.cuda_stream)
+        s.set_t_end(1e9)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        s.advance(warmup)
+    stream.synchronize()
+    ms = timed_steps(s, stream, steps, flush)
+    s.close()
+    avg = sum(ms) / len(ms)
+    gbs = ACOU1D_BYTES_PER_CELL[prec] * n / (avg * 1e-3) / 1e9
+    return {"cells": n, "ms_per_step": avg, "value": n / (avg * 1e-3), "unit": UNIT,
+            "hbm_gbs": gbs}
+
+
+def err_vs_oracle(q, ref):
+    """max-norm relative (per field, maximised) and L1 relative errors of q
+    against the FP64 oracle's result ref."""
+    q = np.asarray(q, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    big = np.abs(ref).max()
+    mx = 0.0
+    for k in range(ref.shape[0]):
+        den = np.abs(ref[k]).max()
+        den = big if den < 1e-12 * big else den
+        mx = max(mx, float(np.abs(q[k] - ref[k]).max() / den))
+    return {"max_rel": mx, "l1_rel": float(np.abs(q - ref).sum() / np.abs(ref).sum())}
+
+
+def errors_vs_oracle():
+    """Outside every timed region: the FP32 (and FP64) GPU results of the
+    workloads at the oracle's sizes, run to their final times, against the
+    FP64 oracle: dam break 256^2 to t = 1.5, shock-bubble 256 x 128 to t =
+    0.2, sampled ensemble members to t = 50 (batched FP32 launch), and one
+    served FP32 request."""
+    import torch
+    import oracle
+    from paper_1111_6583_gb300 import claw
+    from paper_1111_6583_gb300 import workloads as wl
+    oracle.build()
+    out = {}
+
+    def gpu_run(spec, prec, t_end):
+        s = claw.Solver(spec, prec)
+        info = s.evolve(t_end)
+        torch.cuda.synchronize()
+        q = s.q.double().cpu().numpy()
+        s.close()
+        return q, info
+
+    for name, spec, t_end in (("dambreak_256", wl.sw_dambreak_2d(n=256), 1.5),
+                              ("shock_bubble_256x128", wl.shock_bubble_2d(nx=256, ny=128), 0.2)):
+        qo, io = oracle.evolve(oracle.make_problem(spec), spec["q0"], spec.get("aux"),
+                               t_end=t_end)
+        row = {"t": t_end, "oracle_steps": io["steps"]}
+        for prec in ("fp64", "fp32"):
+            q, info = gpu_run(spec, prec, t_end)
+            row[prec] = err_vs_oracle(q, qo)
+            row[prec]["steps"] = info["steps"]
+        out[name] = row
+    # ensemble members: three of the smaller grids (spread over 2^12..2^14)
+    ens = wl.elasticity_ensemble(4096)
+    small = sorted((e["n"], k) for k, e in enumerate(ens) if e["n"] <= (1 << 14))
+    pick = [small[0][1], small[len(small) // 2][1], small[-1][1]]
+    specs = [wl.elasticity_member(ens[k]["n"], ens[k]["amp"], ens[k]["width"], t_end=50.0)
+             for k in pick]
+    b = claw.Batch(specs, "fp32")
+    binfo = b.evolve()
+    qs = [t.double().cpu().numpy() for t in b.sync()]
+    b.close()
+    rows = []
+    for k, sp, q, bi in zip(pick, specs, qs, binfo):
+        qo, io = oracle.evolve(oracle.make_problem(sp), sp["q0"], sp["aux"], t_end=50.0)
+        e = err_vs_oracle(q, qo)
+        e.update(member=k, cells=sp["n"][0], steps=bi["steps"], oracle_steps=io["steps"])
+        rows.append(e)
+    out["ensemble_members_t50"] = rows
+    # one served FP32 request against the oracle: the smallest of the first 20
+    # of the benchmark's stream
+    req = min(wl.serving_stream(400, 200.0)[:20], key=lambda r: r["n"])
+    sp = wl.sw_humps_2d(req["n"], req["humps"], req["t_end"])
+    sv = claw.Server(sp, "fp32", budget_bytes=1 << 30, max_slots=4)
+    tk = sv.submit(sp)
+    res = None
+    while res is None:
+        sv.pump(64)
+        res = sv.poll(tk)
+    sv.close()
+    qo, io = oracle.evolve(oracle.make_problem(sp), sp["q0"], None, t_end=req["t_end"])
+    e = err_vs_oracle(res["q"], qo)
+    e.update(cells=req["n"] ** 2, t=req["t_end"], steps=res["steps"], oracle_steps=io["steps"])
+    out["served_request"] = e
+    return out
+
+
+def cpu_single_thread(budget_s=3.0):
+    """The oracle on one host thread at its parity sizes (run in a child
+    process with OMP_NUM_THREADS=1): cell-updates/s per workload."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-single",
+                        str(budget_s)], capture_output=True, text=True, env=env, timeout=600)
+    if r.returncode != 0:
+        return {"error": r.stderr[-300:]}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def _cpu_single_child(budget_s):
+    import oracle
+    from paper_1111_6583_gb300 import workloads as wl
+    oracle.build()
+    out = {"threads": oracle.threads()}
+
+    def rate(spec, cells):
+        # the first dt from the controller, then steps of that size
+        P = oracle.make_problem(spec)
+        q, info = oracle.evolve(P, spec["q0"], spec.get("aux"), t0=0.0, t_end=1e9, max_steps=1)
+        dt = info["dt_next"]
+        steps = 0
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < budget_s:
+            q, _ = oracle.step(P, q, spec.get("aux"), dt)
+            steps += 1
+        return cells * steps / (time.perf_counter() - t0)
+
+    out["acoustics_1d_2000"] = rate(wl.acoustics_1d(2000), 2000)
+    out["dambreak_256"] = rate(wl.sw_dambreak_2d(n=256), 256 * 256)
+    out["shock_bubble_256x128"] = rate(wl.shock_bubble_2d(nx=256, ny=128), 256 * 128)
+    # a 64-member subset of the ensemble, two steps per member per round
+    ens = wl.elasticity_ensemble(64)
+    members = []
+    for e in ens:
+        sp = wl.elasticity_member(e["n"], e["amp"], e["width"])
+        P = oracle.make_problem(sp)
+        q, info = oracle.evolve(P, sp["q0"], sp["aux"], t0=0.0, t_end=1e9, max_steps=1)
+        members.append((P, q, sp["aux"], info["dt_next"], e["n"]))
+    tot, el = 0, 0.0
+    while el < budget_s:
+        for P, q, aux, dt, n in members:
+            t0 = time.perf_counter()
+            oracle.step(P, q, aux, dt)
+            el += time.perf_counter() - t0
+            tot += n
+    out["ensemble_64_members"] = tot / el
+    out["serving_64sq"] = rate(wl.sw_humps_2d(64, [(0.5, 0.5, 0.5, 0.1)], 1.0), 64 * 64)
+    print(json.dumps(out))
+
+
+def summary(line):
+    """Short digest of the line's results (the last key, so that a record that
+    keeps only the end of the output still has it)."""
+    g = lambda *ks: _dig(line, ks)
+    s = {
+        "headline_fp64_1024": {"ms": g("ms_per_step"), "cu_s": g("value"),
+                               "alu_frac": g("roofline", "frac"),
+                               "peak_fp64_tf": g("roofline", "peak")},
+        "peaks_measured": g("peaks"),
+        "dambreak_fp32_1024": {"ms": g("fp32", "ms_per_step"), "cu_s": g("fp32", "value"),
+                               "alu_frac": g("fp32", "alu_frac")},
+        "dambreak_4096": {p: {"ms": g("dambreak_4096", p, "ms_per_step"),
+                              "hbm_frac": g("dambreak_4096", p, "hbm_frac"),
+                              "alu_frac": g("dambreak_4096", p, "alu_frac")}
+                          for p in ("fp64", "fp32")},
+        "acoustics_1d_2000": {"us_step": g("acoustics_1d", "us_per_step"),
+                              "steps_s": g("acoustics_1d", "steps_per_s")},
+        "acoustics_1d_2p26": {p: {"ms": g("acoustics_1d_2p26", p, "ms_per_step"),
+                                  "hbm_frac": g("acoustics_1d_2p26", p, "hbm_frac")}
+                              for p in ("fp64", "fp32")},
+        "shock_bubble_2048x1024": {p: {"ms": g("shock_bubble", p, "ms_per_step"),
+                                       "alu_frac": g("shock_bubble", p, "alu_frac")}
+                                   for p in ("fp64", "fp32")},
+        "ensemble_4096": {"fp32_ms": g("batched_elasticity", "fp32_ms_per_step"),
+                          "fp32_hbm_frac": g("batched_elasticity", "fp32_hbm_frac"),
+                          "fp32_cu_s": g("batched_elasticity", "fp32_batched"),
+                          "fp64_1at_cu_s": g("batched_elasticity", "fp64_one_at_a_time")},
+        "serving": {p: {k: g(key, k) for k in ("p50_s", "p99_s",
+                                                "throughput_cell_updates_per_s", "requests")}
+                    for p, key in (("fp32", "serving"), ("fp64", "serving_fp64"))},
+        "fp32_err_vs_oracle": {
+            "dambreak_256_t1.5": g("errors_vs_oracle", "dambreak_256", "fp32", "l1_rel"),
+            "shock_bubble_256x128_t0.2": g("errors_vs_oracle", "shock_bubble_256x128", "fp32",
+                                           "l1_rel"),
+            "ensemble_t50_max": max([r.get("l1_rel", 0) for r in
+                                     g("errors_vs_oracle", "ensemble_members_t50") or []] or
+                                    [None], key=lambda v: -1 if v is None else v),
+            "served": g("errors_vs_oracle", "served_request", "l1_rel")},
+        "fp64_err_vs_oracle_max": {
+            "dambreak_256": g("errors_vs_oracle", "dambreak_256", "fp64", "max_rel"),
+            "shock_bubble": g("errors_vs_oracle", "shock_bubble_256x128", "fp64", "max_rel")},
+    }
+    return _compact(s)
+
+
+def _dig(d, ks):
+    for k in ks:
+        if not isinstance(d, dict) or k not in d:
+            return None
+        d = d[k]
+    return d
+
+
 def cpu_baseline_sw2d(n=1024, budget_s=12.0):
     """The oracle as it stands on the host cores: steps of the headline
     workload until about budget_s of CPU time."""
@@ -637,6 +895,7 @@ def main():
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-requests-fp64", type=int, default=60)
     ap.add_argument("--members", type=int, default=4096)
     ap.add_argument("--record-traffic", default=None,
                     help="write the headline kernel's traffic record from an ncu csv")
@@ -645,7 +904,11 @@ def main():
     ap.add_argument("--case", default=None,
                     help="run one short launch sequence for a profiler (sw2d64, sw2d32, sw2d1024, "
                          "elast, sharp, axisym, vc, acou2d, psystem, weno7, acou3d, acou3d128)")
+    ap.add_argument("--cpu-single", type=float, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.cpu_single is not None:
+        _cpu_single_child(args.cpu_single)
+        return
     if args.record_traffic:
         if not args.tile:
             raise SystemExit("--record-traffic needs the --tile the capture ran")
@@ -664,9 +927,13 @@ def main():
     import torch
     import __graft_entry__
     __graft_entry__.build()
+    from paper_1111_6583_gb300 import claw
     rank, world, local = dist_setup(args.gpus)
     torch.cuda.set_device(local)
     hbm, hbm_kind = peaks()
+    # measured ALU denominators (FMA probes, before the timed region)
+    fp64_tf = claw.fma_peak("fp64")
+    fp32_tf = claw.fma_peak("fp32")
 
     barrier(world)
     torch.cuda.synchronize()
@@ -676,10 +943,11 @@ def main():
     barrier(world)
     total_ms = max_over_ranks(sum(ms), world)
     cells = args.n * args.n
-    value = replica_value(cells * args.steps, total_ms, world)
+    accepted = info["accepted_in_timed"]
+    value = replica_value(cells * accepted, total_ms, world)
     avg_ms = sum(ms) / len(ms)
-    flops = SW2D_FLOPS_PER_CELL * cells
-    achieved_tf = flops / (avg_ms * 1e-3) / 1e12
+    achieved_tf = SW2D_FLOPS_PER_CELL * cells / (avg_ms * 1e-3) / 1e12
+    hbm_gbs = SW2D_BYTES_PER_CELL["fp64"] * cells / (avg_ms * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -688,54 +956,98 @@ def main():
                                "transverse 2, FP64" % (args.n, args.n),
                    "global_batch": world, "seq_len": 0, "parallelism": "replicas",
                    "tile": {"bw": shape[0], "h": shape[1]},
-                   "l2": "flushed between timed steps (512 MB write, untimed)"},
+                   "l2": "flushed between timed steps (512 MB write, untimed)",
+                   "accepted_steps": accepted},
         "gpu_launches": args.steps,
-        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
+        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": fp64_tf,
+                     "unit": "TFLOP/s", "frac": achieved_tf / fp64_tf,
                      "traffic": recorded_traffic(shape),
-                     "peak_kind": "derived FP64 (152 SM x 2.07 GHz x 4 FLOP/clk)",
-                     "hbm_gbs": SW2D_BYTES_PER_CELL["fp64"] * cells / (avg_ms * 1e-3) / 1e9,
-                     "hbm_frac": SW2D_BYTES_PER_CELL["fp64"] * cells / (avg_ms * 1e-3) / 1e9 / hbm,
+                     "peak_kind": "measured in this run: FP64 FMA probe (claw_fma_peak), burst",
+                     "flops_per_cell": SW2D_FLOPS_PER_CELL,
+                     "hbm_gbs": hbm_gbs, "hbm_frac": hbm_gbs / hbm, "hbm_peak": hbm,
                      "hbm_peak_kind": hbm_kind},
+        "peaks": {"fp64_fma_tflops": fp64_tf, "fp32_fma_tflops": fp32_tf, "hbm_gbs": hbm,
+                  "hbm_kind": hbm_kind},
         "clocks": clk.summary(),
     }
     if rank == 0 and not args.no_extras:
+        ex = {}
         spec32, ms32, info32, shape32 = bench_sw2d("fp32", args.steps, args.warmup, args.n)
         avg32 = sum(ms32) / len(ms32)
         gbs32 = SW2D_BYTES_PER_CELL["fp32"] * cells / (avg32 * 1e-3) / 1e9
-        line["fp32"] = {"value": cells * len(ms32) / (sum(ms32) * 1e-3), "unit": UNIT,
-                        "ms_per_step": avg32, "hbm_gbs": gbs32, "hbm_frac": gbs32 / hbm,
-                        "tile": {"bw": shape32[0], "h": shape32[1]}}
+        ex["fp32"] = {"value": cells * info32["accepted_in_timed"] / (sum(ms32) * 1e-3),
+                      "unit": UNIT, "ms_per_step": avg32, "hbm_gbs": gbs32,
+                      "hbm_frac": gbs32 / hbm,
+                      "alu_frac": SW2D_FLOPS_PER_CELL * cells / (avg32 * 1e-3) / 1e12 / fp32_tf,
+                      "tile": list(shape32)}
         line["e2e"] = e2e_sw2d("fp64", max(5, args.steps // 4), 3, args.n)
-        line["shock_bubble"] = {p: bench_shockbubble(p, 5, 3) for p in ("fp64", "fp32")}
-        line["shock_bubble"]["fp64_weno7_ssp104"] = bench_shockbubble("fp64", 3, 3, weno_order=7,
-                                                                      integrator="ssp104")
-        line["psystem_checkerboard"] = {p: bench_psystem(p, 3, 3) for p in ("fp64", "fp32")}
-        line["axisym_shock_bubble"] = {p: bench_axisym(p, 20, 3) for p in ("fp64", "fp32")}
-        line["axisym_shock_bubble"]["fp64_split"] = bench_axisym("fp64", 20, 3, dim_split=1)
-        line["axisym_shock_bubble"]["fp64_strang"] = bench_axisym("fp64", 20, 3,
-                                                                  source_split="strang")
-        line["acoustics_table1"] = {
-            "2d_" + p: bench_acoustics_table1(p, 20, 3, 2, 1024) for p in ("fp64", "fp32")}
-        line["acoustics_table1"].update({
-            "3d_" + p: bench_acoustics_table1(p, 5, 3, 3, 256) for p in ("fp64", "fp32")})
-        line["acoustics_vc_capacity"] = {p: bench_acoustics_vc(p, 10, 3) for p in ("fp64", "fp32")}
+        big = {}
+        for p in ("fp64", "fp32"):
+            _, msb, ib, shb = bench_sw2d(p, 10, 3, 4096)
+            ab = sum(msb) / len(msb)
+            gb = SW2D_BYTES_PER_CELL[p] * 4096 * 4096 / (ab * 1e-3) / 1e9
+            big[p] = {"ms_per_step": ab, "value": 4096 * 4096 / (ab * 1e-3), "hbm_gbs": gb,
+                      "hbm_frac": gb / hbm, "tile": list(shb),
+                      "alu_frac": SW2D_FLOPS_PER_CELL * 4096 * 4096 / (ab * 1e-3) / 1e12
+                      / (fp64_tf if p == "fp64" else fp32_tf)}
+        ex["dambreak_4096"] = big
+        ex["acoustics_1d"] = bench_acoustics_1d("fp64")
+        a26 = {}
+        for p in ("fp64", "fp32"):
+            r = bench_acoustics_1d_hbm(p, 10, 3)
+            r["hbm_frac"] = r["hbm_gbs"] / hbm
+            a26[p] = r
+        ex["acoustics_1d_2p26"] = a26
+        sb = {p: bench_shockbubble(p, 5, 3) for p in ("fp64", "fp32")}
+        for p in ("fp64", "fp32"):
+            fl = 3 * EULER2D_WENO5_FLOPS_PER_CELL_STAGE * 2048 * 1024
+            sb[p]["alu_frac"] = fl / (sb[p]["ms_per_step"] * 1e-3) / 1e12 / (
+                fp64_tf if p == "fp64" else fp32_tf)
+        sb["fp64_weno7_ssp104"] = bench_shockbubble("fp64", 3, 3, weno_order=7,
+                                                    integrator="ssp104")
+        ex["shock_bubble"] = sb
+        ex["psystem_checkerboard"] = {p: bench_psystem(p, 3, 3) for p in ("fp64", "fp32")}
+        ax = {p: bench_axisym(p, 20, 3) for p in ("fp64", "fp32")}
+        ax["fp64_split"] = bench_axisym("fp64", 20, 3, dim_split=1)
+        ax["fp64_strang"] = bench_axisym("fp64", 20, 3, source_split="strang")
+        ex["axisym_shock_bubble"] = ax
+        at = {"2d_" + p: bench_acoustics_table1(p, 20, 3, 2, 1024) for p in ("fp64", "fp32")}
+        at.update({"3d_" + p: bench_acoustics_table1(p, 5, 3, 3, 256) for p in ("fp64", "fp32")})
+        ex["acoustics_table1"] = at
+        ex["acoustics_vc_capacity"] = {p: bench_acoustics_vc(p, 10, 3) for p in ("fp64", "fp32")}
         try:
-            line["batched_elasticity"] = bench_elasticity(args.members, 100, 16)
-        except Exception as ex:  # reported, not hidden
-            line["batched_elasticity"] = {"error": repr(ex)}
+            be = bench_elasticity(args.members, 100, 16)
+            gbe = ELAST1D_BYTES_PER_CELL["fp32"] * be["cells"] / (be["fp32_ms_per_step"] * 1e-3)
+            be["fp32_hbm_gbs"] = gbe / 1e9
+            be["fp32_hbm_frac"] = gbe / 1e9 / hbm
+            be["fp32_alu_frac"] = (ELAST1D_FLOPS_PER_CELL * be["cells"] /
+                                   (be["fp32_ms_per_step"] * 1e-3) / 1e12 / fp32_tf)
+            ex["batched_elasticity"] = be
+        except Exception as e:  # reported, not hidden
+            ex["batched_elasticity"] = {"error": repr(e)}
         try:
-            line["serving"] = bench_serving(args.serve_requests, "fp32")
-            line["serving_every_request_per_attempt"] = bench_serving(
+            ex["serving"] = bench_serving(args.serve_requests, "fp32")
+            ex["serving_every_request_per_attempt"] = bench_serving(
                 args.serve_requests, "fp32", policy="all")
-        except Exception as ex:
-            line["serving"] = {"error": repr(ex)}
+            ex["serving_fp64"] = bench_serving(args.serve_requests_fp64, "fp64")
+            ex["serving_fp64"]["note"] = ("FP64 plain form on the first %d requests of the same "
+                                          "stream (its queue grows without bound on the whole "
+                                          "stream)" % args.serve_requests_fp64)
+        except Exception as e:
+            ex["serving"] = {"error": repr(e)}
+        try:
+            ex["errors_vs_oracle"] = errors_vs_oracle()
+        except Exception as e:
+            ex["errors_vs_oracle"] = {"error": repr(e)}
+        line.update(_compact(ex))
         line["cpu_baseline"] = cpu_baseline_sw2d(args.n)
+        line["cpu_single_thread"] = _compact(cpu_single_thread())
+        line["summary"] = summary(line)
     elif rank == 0:
         line["e2e"] = e2e_sw2d("fp64", max(5, args.steps // 4), 3, args.n)
         line["cpu_baseline"] = cpu_baseline_sw2d(args.n, budget_s=5.0)
     if rank == 0:
-        print(json.dumps(line))
+        print(json.dumps(line, separators=(",", ":")))
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

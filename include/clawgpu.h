@@ -314,6 +314,18 @@ claw_status claw_sharp_step_noalloc(const claw_method* m, const claw_grid* g, co
                                     void* q_out, const void* aux, double dt, void* stream,
                                     double* cfl);
 
+/* ---------------------------------------------------------------------- */
+/* Diagnostics                                                              */
+/* ---------------------------------------------------------------------- */
+
+/* Measured FMA throughput of the current device in TFLOP/s (one FMA = 2
+ * FLOPs), for the ALU roofline of the FP64-bound kernels: a probe kernel with
+ * eight independent FMA chains per thread, as many blocks as fit at once on
+ * every SM, the best of five timed launches on stream (cudaStream_t, may be
+ * NULL; synchronised).  prec: CLAW_FP64 or CLAW_FP32.  Takes about 10-100 ms.
+ * Not part of the paper's method. */
+claw_status claw_fma_peak(int prec, void* stream, double* tflops);
+
 /* Seconds on the server's clock (monotonic). */
 double claw_clock(void);
 

@@ -116,6 +116,7 @@ _SIGS = {
     "claw_server_destroy": (ctypes.c_int, [_VP]),
     "claw_sharp_step_noalloc": (ctypes.c_int, [_P(claw_method), _P(claw_grid), _VP, _VP, _VP,
                                                ctypes.c_double, _VP, _P(ctypes.c_double)]),
+    "claw_fma_peak": (ctypes.c_int, [ctypes.c_int, _VP, _P(ctypes.c_double)]),
     "claw_clock": (ctypes.c_double, []),
     "claw_last_error": (ctypes.c_char_p, [_VP]),
     "claw_version": (ctypes.c_char_p, []),
@@ -454,3 +455,13 @@ class Server:
 
 def clock():
     return load().claw_clock()
+
+
+def fma_peak(prec="fp64", stream=None):
+    """Measured FMA throughput of the current device in TFLOP/s (claw_fma_peak)."""
+    out = ctypes.c_double(0.0)
+    st = load().claw_fma_peak(FP64 if prec == "fp64" else FP32, stream,
+                              ctypes.byref(out))
+    if st != CLAW_OK:
+        raise RuntimeError(load().claw_last_error(None).decode())
+    return out.value

@@ -150,8 +150,9 @@ def test_noalloc_rejects_grid_beyond_scratch():
     m = claw.method_from_spec(spec, "fp64")
     g = claw.grid_from_spec(spec)
     x = torch.zeros(16, dtype=torch.float64, device="cuda")
+    y = torch.zeros(16, dtype=torch.float64, device="cuda")
     st = lib.claw_sharp_step_noalloc(ctypes.byref(m), ctypes.byref(g),
-                                     ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                     ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
                                      None, 1e-3, None, None)
     assert st == claw.CLAW_EINVAL
     assert b"too large" in lib.claw_last_error(None)
