@@ -171,7 +171,8 @@ claw_status claw_step(claw_solver* s, double dt, claw_step_info* info);
 /* Tile shape of the 2D classic kernel: mode 0 runs the autotuner (times the
  * candidate shapes on the bound state without changing it) and returns the
  * choice in *bw, *h; mode 1 sets *bw (64 or 128 threads = strip width + 4)
- * and *h (rows per block).  Other schemes/dimensions ignore the shape. */
+ * and *h (rows per block).  Every shape gives the same result bit for bit.
+ * Other schemes/dimensions ignore the shape. */
 claw_status claw_solver_tune(claw_solver* s, int mode, int* bw, int* h);
 
 /* Enqueue n controller step attempts on the stream without synchronising

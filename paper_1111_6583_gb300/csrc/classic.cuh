@@ -136,12 +136,13 @@ struct CellPrep<RpElasticity<R, 1>, R> {
 
 // limited second-order correction F (Eq. (lwflux)) of interface `c` from the
 // waves of its neighbours `l` and `r` (the upwind one per wave decides theta)
-template <class RP, typename R>
-__device__ __forceinline__ void limit1d(const MConsts<R>& C, const R (&Wl)[RP::MW][RP::M],
+template <class RP, typename R, int LIMC = -1>
+__device__ __forceinline__ void limit1d(const MConsts<R>& C, int order,
+                                        const R (&Wl)[RP::MW][RP::M],
                                         const R (&Wc)[RP::MW][RP::M], const R (&sc)[RP::MW],
                                         const R (&Wr)[RP::MW][RP::M], R dtdx, R (&F)[RP::M]) {
   constexpr int M = RP::M, MW = RP::MW;
-  if (C.order != 2) {
+  if (order != 2) {
 #pragma unroll
     for (int k = 0; k < M; ++k) F[k] = R(0);
     return;
@@ -159,14 +160,18 @@ __device__ __forceinline__ void limit1d(const MConsts<R>& C, const R (&Wl)[RP::M
     dot[p] = d;
     nrm[p] = n2;
   }
-  correction<RP, R>(C, Wc, sc, dot, nrm, dtdx, F);
+  correction<RP, R, 0, LIMC>(C, Wc, sc, dot, nrm, dtdx, F);
 }
 
-template <class RP, typename R, int NT, int K, int SPW>
+// FAST: the MC limiter and second order fixed at compile time (the launcher
+// takes it for FP32 methods with those settings)
+template <class RP, typename R, int NT, int K, int SPW, bool FAST = false>
 __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? 8 : 1)
     classic1d_kernel(const Member* __restrict__ members, const Tile* __restrict__ tiles,
                      int ntiles_total, const MConsts<R> C) {
   constexpr int M = RP::M, MW = RP::MW, MA = RP::MA;
+  constexpr int LIMC = FAST ? CLAW_LIM_MC : -1;
+  const int order = FAST ? 2 : C.order;
   constexpr int MAS = MA > 0 ? MA : 1;
   constexpr int NW = NT / 32;      // warp units per tile
   constexpr int WC = 30 * K;       // cells a warp unit writes (lanes 1..30)
@@ -303,13 +308,13 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? 8 : 1)
       // and update each cell once both of its interfaces are limited:
       // Q_c - dt/dx [(A+dQ - F)_{c-1/2} + (A-dQ + F)_{c+1/2}]
       R qout[K][M], Fl[M], FK[M];
-      limit1d<RP, R>(C, Wm, W[0], s[0], K > 1 ? W[1] : Wp, dtdx, Fl);
+      limit1d<RP, R, LIMC>(C, order, Wm, W[0], s[0], K > 1 ? W[1] : Wp, dtdx, Fl);
 #pragma unroll
       for (int k = 0; k < M; ++k) FK[k] = __shfl_down_sync(FULL, Fl[k], 1);
 #pragma unroll
       for (int c = 1; c < K; ++c) {
         R Fr[M];
-        limit1d<RP, R>(C, W[c - 1], W[c], s[c], c + 1 < K ? W[c + 1] : Wp, dtdx, Fr);
+        limit1d<RP, R, LIMC>(C, order, W[c - 1], W[c], s[c], c + 1 < K ? W[c + 1] : Wp, dtdx, Fr);
 #pragma unroll
         for (int k = 0; k < M; ++k) {
           qout[c - 1][k] = qa[c - 1][k] - dtdx * ((ap[c - 1][k] - Fl[k]) + (am[c][k] + Fr[k]));
@@ -385,11 +390,16 @@ __device__ __forceinline__ void solve_cells(const MConsts<R>& C, const R (&ql)[R
 // sweep: 0 the unsplit step (Q^n in slot 0 -> slot 1, runs the controller);
 // dimensional splitting (Godunov) as two launches: 1 the x sweeps (slot 0 ->
 // slot 1), 2 the y sweeps (slot 1 -> slot 2, runs the controller).
-template <class RP, typename R, int BW>
+// FAST: the MC limiter, second order and transverse mode 2 fixed at compile
+// time (the launcher takes it for FP32 methods with those settings)
+template <class RP, typename R, int BW, bool FAST = false>
 __global__ void __launch_bounds__(BW)
     classic2d_kernel(const Member* __restrict__ members, const Tile* __restrict__ tiles,
                      int ntiles_total, const MConsts<R> C, int H, int sweep) {
   constexpr int M = RP::M, MW = RP::MW, NC = RP::NCTX;
+  constexpr int LIMC = FAST ? CLAW_LIM_MC : -1;
+  const int order = FAST ? 2 : C.order;
+  const int transverse = FAST ? 2 : C.transverse;
   constexpr int NP = RP::NPC > 0 ? RP::NPC : 1;
   using NZX = typename RP::template NZ<0>;
   using NZY = typename RP::template NZ<1>;
@@ -451,6 +461,7 @@ __global__ void __launch_bounds__(BW)
     const R dtdx = s_k[0], dtdy = s_k[1], kxy = s_k[2];
     const size_t plane = (size_t)nx * ny;
 
+    const ColMap cm = col_map(C, cload, nx);  // the thread's column, remapped once
     R qm2[M], qm1[M], qc[M];
     R pm1[NP], pcc[NP];
 #pragma unroll
@@ -484,7 +495,7 @@ __global__ void __launch_bounds__(BW)
         qm1[k] = qc[k];
       }
       if (live) {
-        load_cell<M, R>(C, q, nx, ny, cload, Rw, RP::WALL_X, RP::WALL_Y, qc);
+        load_cell_col<M, R>(C, q, nx, ny, cm, Rw, RP::WALL_X, RP::WALL_Y, qc);
 #pragma unroll
         for (int k = 0; k < M; ++k) qs[k][l] = qc[k];
         if constexpr (RP::NPC > 0) {
@@ -551,7 +562,7 @@ __global__ void __launch_bounds__(BW)
       // (4) x-limiting, corrections, transverse propagation
       if (xrow && xlim) {
         R F[M];
-        if (C.order == 2) {
+        if (order == 2) {
           R dot[MW], nrm[MW];
 #pragma unroll
           for (int p = 0; p < MW; ++p) {
@@ -566,7 +577,7 @@ __global__ void __launch_bounds__(BW)
             dot[p] = b;
             nrm[p] = a;
           }
-          correction<RP, R, 0>(C, xW, xs, dot, nrm, dtdx, F);
+          correction<RP, R, 0, LIMC>(C, xW, xs, dot, nrm, dtdx, F);
         } else {
 #pragma unroll
           for (int k = 0; k < M; ++k) F[k] = R(0);
@@ -584,12 +595,12 @@ __global__ void __launch_bounds__(BW)
 #pragma unroll
           for (int p = 0; p < MW; ++p) smx = max_nonneg(smx, (R)fabs(xs[p]));
         }
-        if (C.transverse) {
+        if (transverse) {
           R tp[M], tm[M], bmp[M], bpp[M], bmm[M], bpm[M];
 #pragma unroll
           for (int k = 0; k < M; ++k) {
-            tp[k] = C.transverse == 2 ? ap_[k] : xap[k];
-            tm[k] = C.transverse == 2 ? am_[k] : xam[k];
+            tp[k] = transverse == 2 ? ap_[k] : xap[k];
+            tm[k] = transverse == 2 ? am_[k] : xam[k];
           }
           RP::template trans<0>(C, xx, tp, bmp, bpp);
           RP::template trans<0>(C, xx, tm, bmm, bpm);
@@ -613,11 +624,11 @@ __global__ void __launch_bounds__(BW)
       // (5) y-limiting of interface Rw-1, corrections, transverse propagation
       if (live && doy && ylim && Rw - 1 >= r0 && Rw - 1 <= rend + 1) {
         R G[M];
-        if (C.order == 2) {
+        if (order == 2) {
           R dot[MW];
 #pragma unroll
           for (int p = 0; p < MW; ++p) dot[p] = gt0(ys[p]) ? ydot[p] : ndot[p];
-          correction<RP, R, 1>(C, yW, ys, dot, ynrm, dtdy, G);
+          correction<RP, R, 1, LIMC>(C, yW, ys, dot, ynrm, dtdy, G);
         } else {
 #pragma unroll
           for (int k = 0; k < M; ++k) G[k] = R(0);
@@ -630,12 +641,12 @@ __global__ void __launch_bounds__(BW)
           acc1[k] -= dtdy * bp_[k];
           acc0[k] -= dtdy * bm_[k];
         }
-        if (C.transverse) {
+        if (transverse) {
           R tp[M], tm[M], amp[M], app[M], amm[M], apm[M];
 #pragma unroll
           for (int k = 0; k < M; ++k) {
-            tp[k] = C.transverse == 2 ? bp_[k] : yap[k];
-            tm[k] = C.transverse == 2 ? bm_[k] : yam[k];
+            tp[k] = transverse == 2 ? bp_[k] : yap[k];
+            tm[k] = transverse == 2 ? bm_[k] : yam[k];
           }
           RP::template trans<1>(C, yx, tp, amp, app);
           RP::template trans<1>(C, yx, tm, amm, apm);
@@ -754,3 +765,4 @@ __global__ void __launch_bounds__(BW)
 }
 
 }  // namespace claw
+

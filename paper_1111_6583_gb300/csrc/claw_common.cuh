@@ -156,6 +156,46 @@ __device__ __forceinline__ void load_cell(const MConsts<R>& C, const R* __restri
     if (fy && k == wall_y) out[k] = -out[k];
 }
 
+// The column part of load_cell's remap, for a thread that keeps its column
+// while it walks down rows (computed once per tile).
+struct ColMap {
+  int cc, fx, ix;
+};
+template <typename R>
+__device__ __forceinline__ ColMap col_map(const MConsts<R>& C, int c, int nx) {
+  ColMap m;
+  m.cc = bc_map(c, nx, C.bc_lo[0], C.bc_hi[0], m.fx, m.ix);
+  return m;
+}
+// load_cell with the column remap given: the same values
+template <int M, typename R>
+__device__ __forceinline__ void load_cell_col(const MConsts<R>& C, const R* __restrict__ q, int nx,
+                                              int ny, const ColMap& cm, int r, int wall_x,
+                                              int wall_y, R (&out)[M]) {
+  int fy, iy;
+  const int rr = bc_map(r, ny, C.bc_lo[1], C.bc_hi[1], fy, iy);
+  if (iy) {
+#pragma unroll
+    for (int k = 0; k < M; ++k) out[k] = C.inflow[k];
+    return;
+  }
+  if (cm.ix) {
+#pragma unroll
+    for (int k = 0; k < M; ++k) out[k] = C.inflow[k];
+  } else {
+    const size_t plane = (size_t)nx * ny;
+    const size_t off = (size_t)rr * nx + cm.cc;
+#pragma unroll
+    for (int k = 0; k < M; ++k) out[k] = __ldg(q + k * plane + off);
+#pragma unroll
+    for (int k = 0; k < M; ++k)
+      if (cm.fx && k == wall_x) out[k] = -out[k];
+  }
+#pragma unroll
+  for (int k = 0; k < M; ++k)
+    if (fy && k == wall_y) out[k] = -out[k];
+}
+
 // aux fields: same index map, no sign flips, inflow treated as extrapolation
 template <int MA, typename R>
 __device__ __forceinline__ void load_aux(const MConsts<R>& C, const R* __restrict__ a, int nx,

@@ -217,12 +217,26 @@ struct Launchers {
       (void)C;
       return cudaErrorNotSupported;
     } else if constexpr (ND == 1) {
+      if (sizeof(R) == 4 && C.lim == CLAW_LIM_MC && C.order == 2)
+        return classic1d<true>(a, C);
+      return classic1d<false>(a, C);
+    } else {
+      if (sizeof(R) == 4 && C.lim == CLAW_LIM_MC && C.order == 2 && C.transverse == 2)
+        return classic2d<true>(a, C);
+      return classic2d<false>(a, C);
+    }
+    return cudaGetLastError();
+  }
+  // FAST (FP32 only): the common settings fixed at compile time
+  template <bool FAST>
+  static cudaError_t classic1d(const LaunchArgs& a, const MConsts<R>& C) {
+    if constexpr (ND == 1 && (!FAST || sizeof(R) == 4)) {
       constexpr int K = sizeof(R) == 8 ? classic1d_K(0) : classic1d_K(1);
       // a warp takes a whole tile when the tiles fill every resident warp
       // (blocks x NW), else a single unit
       constexpr int NW = kClassic1dThreads / 32;
-      constexpr auto kt = classic1d_kernel<RP, R, kClassic1dThreads, K, NW>;
-      constexpr auto ku = classic1d_kernel<RP, R, kClassic1dThreads, K, 1>;
+      constexpr auto kt = classic1d_kernel<RP, R, kClassic1dThreads, K, NW, FAST>;
+      constexpr auto ku = classic1d_kernel<RP, R, kClassic1dThreads, K, 1, FAST>;
       const long long cap = (long long)persistent_grid<kt>(kClassic1dThreads, 1 << 30) * NW;
       if (a.ntiles_total >= cap)
         kt<<<persistent_grid<kt>(kClassic1dThreads, (a.ntiles_total + NW - 1) / NW),
@@ -234,18 +248,30 @@ struct Launchers {
       if (e != cudaSuccess) return e;
       return launch_controllers(a.members, a.nmembers > 0 ? a.nmembers : 1, a.stream);
     } else {
+      (void)a;
+      (void)C;
+      return cudaErrorNotSupported;
+    }
+  }
+  template <bool FAST>
+  static cudaError_t classic2d(const LaunchArgs& a, const MConsts<R>& C) {
+    if constexpr (ND == 2 && RP::MA == 0 && (!FAST || sizeof(R) == 4)) {
       if constexpr (classic2d_fits<RP, R>(128)) {
         if (a.bw == 128) {
-          classic2d_kernel<RP, R, 128><<<launch_grid(a.ntiles_total), 128, 0, a.stream>>>(
+          classic2d_kernel<RP, R, 128, FAST><<<launch_grid(a.ntiles_total), 128, 0, a.stream>>>(
               a.members, a.tiles, a.ntiles_total, C, a.h, a.sweep);
           return cudaGetLastError();
         }
       }
       if (a.bw != 64) return cudaErrorInvalidValue;
-      classic2d_kernel<RP, R, 64><<<launch_grid(a.ntiles_total), 64, 0, a.stream>>>(
+      classic2d_kernel<RP, R, 64, FAST><<<launch_grid(a.ntiles_total), 64, 0, a.stream>>>(
           a.members, a.tiles, a.ntiles_total, C, a.h, a.sweep);
+      return cudaGetLastError();
+    } else {
+      (void)a;
+      (void)C;
+      return cudaErrorNotSupported;
     }
-    return cudaGetLastError();
   }
   static cudaError_t sharp(const LaunchArgs& a) {
     const MConsts<R>& C = *(const MConsts<R>*)a.consts;

@@ -41,7 +41,11 @@ template <>
 struct FM<float> {
   __device__ static __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
   __device__ static __forceinline__ float rcp(float a) { return __fdividef(1.f, a); }
-  __device__ static __forceinline__ float sqrt(float a) { return a > 0.f ? a * rsqrtf(a) : sqrtf(a); }
+  // a rsqrt(a) for a > 0; sqrt(+-0) = +-0 and NaN below zero by selects (no branch)
+  __device__ static __forceinline__ float sqrt(float a) {
+    const float y = a * rsqrtf(a);
+    return a > 0.f ? y : (a == 0.f ? a : __int_as_float(0x7fffffff));
+  }
   __device__ static __forceinline__ float rsqrt(float a) { return rsqrtf(a); }
   __device__ static __forceinline__ float exp(float a) { return __expf(a); }
 };
@@ -60,6 +64,10 @@ template <typename R>
 __device__ __forceinline__ bool lt0(R x) {
   return fbits(x) < 0 && (fbits(x) << 1) != 0;
 }
+// FP32: one float compare each (the FP32 pipes are not scarce); a NaN is
+// neither positive nor negative here
+__device__ __forceinline__ bool gt0(float x) { return x > 0.f; }
+__device__ __forceinline__ bool lt0(float x) { return x < 0.f; }
 // larger of two non-negative values (or NaNs with clear sign bit, which win:
 // their bit patterns lie above +inf)
 template <typename R>
@@ -88,8 +96,9 @@ __device__ __forceinline__ void split_waves(const R (&W)[MW][M], const R (&s)[MW
     am[k] = R(0);
     ap[k] = R(0);
   }
-  if (lt0(s[0]) && gt0(s[MW - 1])) {
-    // first family left-going, last right-going (every subsonic state)
+  if (sizeof(R) == 8 && lt0(s[0]) && gt0(s[MW - 1])) {
+    // first family left-going, last right-going (every subsonic state; FP64
+    // skips the products with zero, FP32 takes the select form below)
 #pragma unroll
     for (int k = 0; k < M; ++k) {
       if (NZ::f(0, k)) am[k] = s[0] * W[0][k];
@@ -1179,6 +1188,11 @@ __device__ __forceinline__ R limiter_mc(R th) {
   const auto b = fbits(th);
   return b < fbits(R(1) / R(3)) ? two_th : (b <= fbits(R(3)) ? mid : R(2));
 }
+// FP32: max(0, min((1+th)/2, 2, 2 th)) by min/max (no branch)
+template <>
+__device__ __forceinline__ float limiter_mc<float>(float th) {
+  return fmaxf(0.f, fminf(fminf(0.5f * (1.f + th), 2.f), 2.f * th));
+}
 // the same as one fused multiply-add, a th + b with (a, b) chosen by the
 // branch: (2, 0), (1/2, 1/2) or (0, 2); the middle branch rounds once
 template <typename R>
@@ -1198,17 +1212,42 @@ __device__ __forceinline__ R limiter_mc_fma(R th) {
 // product of the norms is a normal number, the reciprocals come from one
 // division (1/n_p = prod_{q != p} n_q / prod_q n_q).  DIR selects the
 // solver's structural zeros.
-template <class RP, typename R, int DIR = 0>
+// LIMC >= 0 fixes the limiter at compile time (else C.lim).  FP32 takes
+// every wave's ratio by selects, without branches.
+template <class RP, typename R, int DIR = 0, int LIMC = -1>
 __device__ __forceinline__ void correction(const MConsts<R>& C, const R (&W)[RP::MW][RP::M],
                                            const R (&s)[RP::MW], const R (&dot_up)[RP::MW],
                                            const R (&nrm)[RP::MW], R dtdn, R (&F)[RP::M]) {
   using NZ = typename RP::template NZ<DIR>;
   constexpr int MW = RP::MW;
+  const int lim = LIMC >= 0 ? LIMC : C.lim;
 #pragma unroll
   for (int k = 0; k < RP::M; ++k) F[k] = R(0);
+  if constexpr (sizeof(R) == 4) {
+    const R hd = R(0.5) * dtdn;
+#pragma unroll
+    for (int p = 0; p < MW; ++p) {
+      const R th = FM<R>::div(dot_up[p], nrm[p]);
+      R phi = lim == CLAW_LIM_MC ? limiter_mc<R>(th) : limiter<R>(lim, th);
+      phi = lim == CLAW_LIM_NONE ? R(1) : phi;
+      phi = nrm[p] == R(0) ? R(0) : phi;  // a zero wave gets no correction
+      const R a = fabsf(s[p]);
+      R cf;
+      if (MW >= 3 && !RP::FWAVE) {
+        cf = (R(0.5) - hd * a) * a * phi;
+      } else {
+        const R sg = RP::FWAVE ? (s[p] > R(0) ? R(1) : (s[p] < R(0) ? R(-1) : R(0))) : a;
+        cf = R(0.5) * sg * (R(1) - dtdn * a) * phi;
+      }
+#pragma unroll
+      for (int k = 0; k < RP::M; ++k)
+        if (NZ::f(p, k)) F[k] += cf * W[p][k];
+    }
+    return;
+  }
   R inv[MW];
   bool batched = false;
-  if (MW >= 3 && C.lim != CLAW_LIM_NONE) {
+  if (MW >= 3 && lim != CLAW_LIM_NONE) {
     // every partial product must be a normal number: a subnormal one (a tiny
     // wave next to large ones) would lose precision in the reciprocals
     R pre[MW];
@@ -1237,14 +1276,14 @@ __device__ __forceinline__ void correction(const MConsts<R>& C, const R (&W)[RP:
   for (int p = 0; p < MW; ++p) {
     R phi;
     if (fbits(nrm[p]) == 0) phi = R(0);
-    else if (C.lim == CLAW_LIM_NONE) phi = R(1);
+    else if (lim == CLAW_LIM_NONE) phi = R(1);
     else {
       const R th = batched ? dot_up[p] * inv[p] : FM<R>::div(dot_up[p], nrm[p]);
       // systems of three or more waves take the fused forms (one rounding
       // less per wave; the long linear runs of two-wave systems keep the
       // oracle's order)
-      phi = C.lim == CLAW_LIM_MC ? (MW >= 3 ? limiter_mc_fma<R>(th) : limiter_mc<R>(th))
-                                 : limiter<R>(C.lim, th);
+      phi = lim == CLAW_LIM_MC ? (MW >= 3 ? limiter_mc_fma<R>(th) : limiter_mc<R>(th))
+                               : limiter<R>(lim, th);
     }
     const R a = fabs(s[p]);
     R cf;

@@ -96,10 +96,13 @@ def test_classic2d_fixed_dt_fp64(orc, rp, order, transverse):
         assert info["cfl"] == pytest.approx(co[-1], rel=1e-13)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("rp,nx,ny", [("sw_roe", 131, 70), ("euler_roe", 250, 61),
-                                       ("sw_roe", 372, 33)])
-def test_classic2d_tile_shapes_bitwise(rp, nx, ny):
-    """Every tile shape gives the same bits: narrow last strips whose upper
+                                       ("sw_roe", 372, 33), ("acoustics", 113, 57),
+                                       ("advection", 85, 40)])
+def test_classic2d_tile_shapes_bitwise(rp, nx, ny, prec):
+    """Every tile shape gives the same bits, in both precisions (strips of 60
+    and 124 columns): narrow last strips whose upper
     warps sit idle (131 and 250 columns), a last strip exactly full (372 =
     3 x 124), chunk heights that do not divide the rows (29, 13, 7), one
     chunk for all rows, and the autotuned shape."""
@@ -108,7 +111,7 @@ def test_classic2d_tile_shapes_bitwise(rp, nx, ny):
     dt = 0.25 / nx
     out = []
     for tune in ((128, 32), (128, 29), (64, 13), (128, 7), (64, 128), None):
-        s = claw.Solver(spec, "fp64")
+        s = claw.Solver(spec, prec)
         if tune is None:
             s.tune()
         else:
