@@ -3,15 +3,21 @@
 // for scalar advection and linear acoustics.
 //
 // One attempt = a zero fill of the per-face arrays, three face sweeps (one per
-// direction; a thread walks a segment of faces along the direction with a
-// sliding window of waves) that accumulate fluctuations and correction fluxes
-// on the faces of interior cells, and an update kernel whose last block runs
-// the controller.
+// direction) and an update kernel whose last block runs the controller.
 // Transverse pieces: a fluctuation a that enters cell c across a d-face adds
 // -dt/(2 dx_d) E^+-a to the e-faces of c; the part E^+-a has moved on into
 // cell c +- e, so its third-direction split F^+-E^+-a moves 1/6 (dt/dx_d)
 // (dt/dx_e) of flux correction from the f-faces of c to those of c +- e
 // (six orderings of the directions give the corner-transport-upwind term).
+//
+// Every face value is written by one thread, in a fixed order: a sweep block
+// owns a square patch of lines along its direction (plus a one-line halo it
+// solves again) and walks them together, cell by cell; at each cell every
+// line puts the fluctuation entering its cell across the two sweep faces, and
+// that sum's transverse splits, into shared memory, and each owner line then
+// gathers what its cell's two upper transverse faces receive.  Results do not
+// depend on scheduling, so batches and servers match single solves bit for
+// bit.
 #pragma once
 
 #include "riemann.cuh"
@@ -115,27 +121,10 @@ __device__ __forceinline__ size_t face_index(int e, int nx, int ny, const int (&
   return ((size_t)f[2] * NYF + f[1]) * NXF + f[0];
 }
 
-// add coef * v to the correction flux of face f in direction e when it bounds an
-// interior cell
-template <int M, typename R>
-__device__ __forceinline__ void add_fc(R* __restrict__ work, const Faces3& L, int e, int nx,
-                                       int ny, int nz, const int (&f)[3], R coef,
-                                       const R (&v)[M]) {
-  const int n3[3] = {nx, ny, nz};
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const int hi = (d == e) ? n3[d] : n3[d] - 1;
-    if (f[d] < 0 || f[d] > hi) return;
-  }
-  const size_t fi = face_index<R>(e, nx, ny, f);
-  R* base = work + L.off_fc[e] + fi * M;
-#pragma unroll
-  for (int c = 0; c < M; ++c) atomicAdd(base + c, coef * v[c]);
-}
-
-// add coef * v to the correction flux of a face this thread alone updates in
-// the current launch (a plain read-modify-write; earlier launches' sums are
-// already in place by stream order)
+// add v to the correction flux of face f in direction e, which this thread
+// alone updates in the current launch (a plain read-modify-write; earlier
+// launches' sums are already in place by stream order), when the face bounds
+// an interior cell
 template <int M, typename R>
 __device__ __forceinline__ void add_fc_own(R* __restrict__ work, const Faces3& L, int e, int nx,
                                            int ny, int nz, const int (&f)[3], const R (&v)[M]) {
@@ -150,82 +139,33 @@ __device__ __forceinline__ void add_fc_own(R* __restrict__ work, const Faces3& L
   for (int c = 0; c < M; ++c) base[c] += v[c];
 }
 
-// transverse and double-transverse propagation of the fluctuation av that
-// enters cell c0 across its faces in direction D (Sec. 2, LeVeque 1997):
-// split in each transverse direction e into the four transverse faces of c0
-// (summed here, one update per face) and, split again in the third direction
-// g, into the g-faces of the cells c0 +- e.  The splits are linear in av, so
-// the two fluctuations entering a cell from its two D-faces are propagated
-// as one sum.
-template <class RP, typename R, int D>
-__device__ __forceinline__ void propagate3(const MConsts<R>& C, R* __restrict__ work,
-                                           const Faces3& L, int nx, int ny, int nz,
-                                           const int (&c0)[3], const R (&av)[RP::M], R dtdn,
-                                           const R (&k3)[3]) {
-  constexpr int M = RP::M;
-  constexpr int E1 = (D + 1) % 3, E2 = (D + 2) % 3;
-  R lo1[M], hi1[M], lo2[M], hi2[M];
-#pragma unroll
-  for (int c = 0; c < M; ++c) lo1[c] = hi1[c] = lo2[c] = hi2[c] = R(0);
-#pragma unroll
-  for (int t = 0; t < 2; ++t) {
-    // transverse direction e and third direction g
-    R em[M], ep[M];
-    if (t == 0) Trans3<RP, R, E1>::split(C, av, em, ep);
-    else Trans3<RP, R, E2>::split(C, av, em, ep);
-    const int e = t == 0 ? E1 : E2;
-    const int g = t == 0 ? E2 : E1;
-    R(&elo)[M] = t == 0 ? lo1 : lo2;
-    R(&ehi)[M] = t == 0 ? hi1 : hi2;
-    R(&glo)[M] = t == 0 ? lo2 : lo1;
-    R(&ghi)[M] = t == 0 ? hi2 : hi1;
-    const R h = R(-0.5) * dtdn;
-#pragma unroll
-    for (int c = 0; c < M; ++c) {
-      ehi[c] += h * ep[c];
-      elo[c] += h * em[c];
-    }
-    const R dte = k3[e];
-#pragma unroll
-    for (int sg = 0; sg < 2; ++sg) {
-      const R(&bv)[M] = sg == 0 ? ep : em;
-      const R k6 = (sg == 0 ? R(1) : R(-1)) * dtdn * dte * (R(1) / R(6));
-      R gm[M], gp[M];
-      if (t == 0) Trans3<RP, R, E2>::split(C, bv, gm, gp);
-      else Trans3<RP, R, E1>::split(C, bv, gm, gp);
-#pragma unroll
-      for (int c = 0; c < M; ++c) {
-        ghi[c] += k6 * gp[c];
-        glo[c] += k6 * gm[c];
-      }
-      // the g-faces of the cell the piece moved on to, c0 +- e
-      int c2[3] = {c0[0], c0[1], c0[2]};
-      c2[e] += sg == 0 ? 1 : -1;
-      int fu2[3] = {c2[0], c2[1], c2[2]};
-      fu2[g] = c2[g] + 1;
-      add_fc<M, R>(work, L, g, nx, ny, nz, fu2, -k6, gp);
-      add_fc<M, R>(work, L, g, nx, ny, nz, c2, -k6, gm);
-    }
-  }
-  int u1[3] = {c0[0], c0[1], c0[2]};
-  u1[E1] = c0[E1] + 1;
-  int u2[3] = {c0[0], c0[1], c0[2]};
-  u2[E2] = c0[E2] + 1;
-  add_fc<M, R>(work, L, E1, nx, ny, nz, u1, R(1), hi1);
-  add_fc<M, R>(work, L, E1, nx, ny, nz, c0, R(1), lo1);
-  add_fc<M, R>(work, L, E2, nx, ny, nz, u2, R(1), hi2);
-  add_fc<M, R>(work, L, E2, nx, ny, nz, c0, R(1), lo2);
+// sweep blocks: kPatch3d x kPatch3d lines (owners: the inner kPatch3d - 2
+// squared), kSeg3d cells along the sweep direction
+constexpr int kPatch3d = 16;
+constexpr int kSeg3d = 32;
+
+__host__ __device__ inline void sweep3d_grid(int D, int nx, int ny, int nz, int& npf, int& nps,
+                                             int& nseg) {
+  const int n3[3] = {nx, ny, nz};
+  const int E1 = (D + 1) % 3, E2 = (D + 2) % 3;
+  const int FA = (E2 == 0) ? E2 : E1, SA = (FA == E1) ? E2 : E1;
+  constexpr int PO = kPatch3d - 2;
+  // owner lines -1 .. n-1 in both transverse directions
+  npf = (n3[FA] + 1 + PO - 1) / PO;
+  nps = (n3[SA] + 1 + PO - 1) / PO;
+  nseg = (n3[D] + kSeg3d - 1) / kSeg3d;
 }
 
-// faces along D one sweep thread walks
-constexpr int kSweep3dFaces = 16;
-
 template <class RP, typename R, int D>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kPatch3d * kPatch3d)
     classic3d_sweep(const Member* __restrict__ members, const MConsts<R> C) {
   constexpr int M = RP::M, MW = RP::MW;
   constexpr int E1 = (D + 1) % 3, E2 = (D + 2) % 3;
-  constexpr int T = kSweep3dFaces;
+  constexpr int P = kPatch3d, PO = P - 2, T = kSeg3d;
+  // the transverse direction that runs fastest across threads (x when it is one)
+  constexpr int FA = (E2 == 0) ? E2 : E1, SA = (FA == E1) ? E2 : E1;
+  // per line: the entering sum S and its splits E1^-, E1^+, E2^-, E2^+
+  __shared__ R sh[5][M][P * P];
   const Member& mb = members[0];
   DevCtl* ctl = mb.ctl;
   __shared__ int s_done, s_cur;
@@ -239,140 +179,186 @@ __global__ void __launch_bounds__(256)
   if (s_done) return;
   const int nx = mb.nx, ny = mb.ny, nz = mb.nz;
   const int n3[3] = {nx, ny, nz};
-  const int nd = n3[D], ne1 = n3[E1], ne2 = n3[E2];
-  const int nseg = (nd + 1 + T - 1) / T;
-  // segments of T faces along D (faces 0..nd), lines a = -1..ne1, b = -1..ne2
-  const long long total = (long long)nseg * (ne1 + 2) * (ne2 + 2);
-  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int nd = n3[D];
+  int npf, nps, nseg;
+  sweep3d_grid(D, nx, ny, nz, npf, nps, nseg);
+  const int pf = blockIdx.x % npf, ps = (blockIdx.x / npf) % nps, seg = blockIdx.x / (npf * nps);
+  const int tf = threadIdx.x % P, ts = threadIdx.x / P;
+  int line[3];
+  line[D] = 0;
+  line[FA] = pf * PO - 2 + tf;
+  line[SA] = ps * PO - 2 + ts;
+  const bool owner = tf >= 1 && tf <= PO && ts >= 1 && ts <= PO &&
+                     line[FA] <= n3[FA] - 1 && line[SA] <= n3[SA] - 1;
+  const bool interior_line =
+      line[E1] >= 0 && line[E1] < n3[E1] && line[E2] >= 0 && line[E2] < n3[E2];
+  const int s0 = seg * T, s1 = min(s0 + T, nd);
+  const bool last = s1 == nd;
+  const R* __restrict__ q = (const R*)mb.q[s_cur];
+  R* __restrict__ work = (R*)mb.work3;
+  Faces3 L;
+  faces3_layout(nx, ny, nz, M, L);
+  const R dtdn = s_k[D];
+  const int me = ts * P + tf;
+  // shared-memory slot of the line offset by (d1, d2) in (E1, E2)
+  auto nb = [&](int d1, int d2) {
+    const int df = FA == E1 ? d1 : d2, ds = FA == E1 ? d2 : d1;
+    return (ts + ds) * P + (tf + df);
+  };
+  // lines past the second ghost line (the last patch of a small grid) load
+  // that ghost line; no owner reads them
+  const int la = min(line[E1], n3[E1] + 1), lb = min(line[E2], n3[E2] + 1);
+  auto load = [&](int i, R (&out)[M]) {
+    int c3[3];
+    c3[D] = i;
+    c3[E1] = la;
+    c3[E2] = lb;
+    load_cell3<M, R>(C, q, nx, ny, nz, c3[0], c3[1], c3[2], RP::WALL_X, 2, 3, out);
+  };
+  // window: waves of faces i-1 (Wl), i (Wc) and i+1 (Wr); face i lies
+  // between cells i-1 and i
+  R Wl[MW][M], Wc[MW][M], Wr[MW][M], sl[MW], sc[MW], sr[MW];
+  R amc[M], apc[M], amr[M], apr[M];
+  R cl[M], cr[M];
+  {
+    R x[RP::NCTX], amt[M], apt[M];
+    load(s0 - 2, cl);
+    load(s0 - 1, cr);
+    RP::template solve<D>(C, cl, cr, nullptr, nullptr, Wl, sl, amt, apt, x);
+    load(s0, cl);
+    RP::template solve<D>(C, cr, cl, nullptr, nullptr, Wc, sc, amc, apc, x);
+  }
   R smax = R(0);
-  if (id < total) {
-    // x varies fastest across threads (in the x sweep: the segment index)
-    int ext[3], v[3];
-    ext[D] = nseg;
-    ext[E1] = ne1 + 2;
-    ext[E2] = ne2 + 2;
-    const long long q01 = (long long)ext[0] * ext[1];
-    v[0] = (int)(id % ext[0]);
-    v[1] = (int)((id / ext[0]) % ext[1]);
-    v[2] = (int)(id / q01);
-    const int i0 = v[D] * T, i1 = min(i0 + T, nd + 1);
-    const int a = v[E1] - 1, b = v[E2] - 1;
-    const R* __restrict__ q = (const R*)mb.q[s_cur];
-    R* __restrict__ work = (R*)mb.work3;
-    Faces3 L;
-    faces3_layout(nx, ny, nz, M, L);
-    const R dtdn = s_k[D];
-    const R k3[3] = {s_k[0], s_k[1], s_k[2]};
-    const bool interior_line = a >= 0 && a < ne1 && b >= 0 && b < ne2;
-    auto load = [&](int i, R (&out)[M]) {
-      int c3[3];
-      c3[D] = i;
-      c3[E1] = a;
-      c3[E2] = b;
-      load_cell3<M, R>(C, q, nx, ny, nz, c3[0], c3[1], c3[2], RP::WALL_X, 2, 3, out);
-    };
-    // window: waves of faces i-1 (Wl), i (Wc) and i+1 (Wr); face i lies
-    // between cells i-1 and i
-    R Wl[MW][M], Wc[MW][M], Wr[MW][M], sl[MW], sc[MW], sr[MW];
-    R amc[M], apc[M], amr[M], apr[M];
-    R cl[M], cr[M];
+  R Pv[M];  // A+dQ - F of face i-1 (enters cell i-1 from the left)
+#pragma unroll
+  for (int c = 0; c < M; ++c) Pv[c] = R(0);
+  const R tfF = C.transverse == 2 ? R(1) : R(0);
+  // faces s0 .. s1 (face s1 closes cell s1-1; it belongs to the next segment
+  // unless this is the last one)
+  for (int i = s0; i <= s1; ++i) {
     {
-      R x[RP::NCTX], amt[M], apt[M];
-      load(i0 - 2, cl);
-      load(i0 - 1, cr);
-      RP::template solve<D>(C, cl, cr, nullptr, nullptr, Wl, sl, amt, apt, x);
-      load(i0, cl);
-      RP::template solve<D>(C, cr, cl, nullptr, nullptr, Wc, sc, amc, apc, x);
+      R x[RP::NCTX];
+      load(i + 1, cr);
+      RP::template solve<D>(C, cl, cr, nullptr, nullptr, Wr, sr, amr, apr, x);
+#pragma unroll
+      for (int c = 0; c < M; ++c) cl[c] = cr[c];
     }
-    // cl holds cell i0 here
-    R P[M];  // A+dQ - F of the face left of the current cell (enters it)
-    int c0[3];
-    c0[E1] = a;
-    c0[E2] = b;
-    for (int i = i0; i < i1; ++i) {
-      {
-        R x[RP::NCTX];
-        load(i + 1, cr);
-        RP::template solve<D>(C, cl, cr, nullptr, nullptr, Wr, sr, amr, apr, x);
-#pragma unroll
-        for (int c = 0; c < M; ++c) cl[c] = cr[c];
-      }
-      if (interior_line) {
-#pragma unroll
-        for (int p = 0; p < MW; ++p) smax = nanmax(smax, (R)fabs(sc[p]));
-      }
-      R F[M];
-      if (C.order == 2) {
-        R dot[MW], nrm[MW];
-#pragma unroll
-        for (int p = 0; p < MW; ++p) {
-          R d_ = R(0), n2 = R(0);
-#pragma unroll
-          for (int c = 0; c < M; ++c) {
-            const R up = sc[p] > R(0) ? Wl[p][c] : Wr[p][c];
-            d_ += up * Wc[p][c];
-            n2 += Wc[p][c] * Wc[p][c];
-          }
-          dot[p] = d_;
-          nrm[p] = n2;
-        }
-        correction<RP, R, D>(C, Wc, sc, dot, nrm, dtdn, F);
-      } else {
-#pragma unroll
-        for (int c = 0; c < M; ++c) F[c] = R(0);
-      }
-      if (interior_line) {
-        int f[3];
-        f[D] = i;
-        f[E1] = a;
-        f[E2] = b;
-        const size_t fi = face_index<R>(D, nx, ny, f);
-#pragma unroll
-        for (int c = 0; c < M; ++c) {
-          work[L.off_am[D] + fi * M + c] = amc[c];
-          work[L.off_ap[D] + fi * M + c] = apc[c];
-        }
-        // within this sweep only this thread touches the D-face's correction
-        add_fc_own<M, R>(work, L, D, nx, ny, nz, f, F);
-      }
-      if (C.transverse) {
-        // cell i-1 takes A-dQ + F of face i, plus (inside the segment) the
-        // A+dQ - F of face i-1 carried in P
-        const R tf = C.transverse == 2 ? R(1) : R(0);
-        R av[M];
-#pragma unroll
-        for (int c = 0; c < M; ++c) av[c] = amc[c] + tf * F[c];
-        if (i > i0) {
-#pragma unroll
-          for (int c = 0; c < M; ++c) av[c] = P[c] + av[c];
-        }
-        c0[D] = i - 1;
-        propagate3<RP, R, D>(C, work, L, nx, ny, nz, c0, av, dtdn, k3);
-#pragma unroll
-        for (int c = 0; c < M; ++c) P[c] = apc[c] - tf * F[c];
-      }
-      // slide the window
+    R F[M];
+    if (C.order == 2) {
+      R dot[MW], nrm[MW];
 #pragma unroll
       for (int p = 0; p < MW; ++p) {
-        sl[p] = sc[p];
-        sc[p] = sr[p];
+        R d_ = R(0), n2 = R(0);
 #pragma unroll
         for (int c = 0; c < M; ++c) {
-          Wl[p][c] = Wc[p][c];
-          Wc[p][c] = Wr[p][c];
+          const R up = sc[p] > R(0) ? Wl[p][c] : Wr[p][c];
+          d_ += up * Wc[p][c];
+          n2 += Wc[p][c] * Wc[p][c];
+        }
+        dot[p] = d_;
+        nrm[p] = n2;
+      }
+      correction<RP, R, D>(C, Wc, sc, dot, nrm, dtdn, F);
+    } else {
+#pragma unroll
+      for (int c = 0; c < M; ++c) F[c] = R(0);
+    }
+    if (owner && interior_line && (i < s1 || last)) {
+#pragma unroll
+      for (int p = 0; p < MW; ++p) smax = nanmax(smax, (R)fabs(sc[p]));
+      int f[3];
+      f[D] = i;
+      f[E1] = line[E1];
+      f[E2] = line[E2];
+      const size_t fi = face_index<R>(D, nx, ny, f);
+#pragma unroll
+      for (int c = 0; c < M; ++c) {
+        work[L.off_am[D] + fi * M + c] = amc[c];
+        work[L.off_ap[D] + fi * M + c] = apc[c];
+      }
+      add_fc_own<M, R>(work, L, D, nx, ny, nz, f, F);
+    }
+    if (C.transverse) {
+      if (i > s0) {
+        // cell i-1: A+dQ - F of face i-1 plus A-dQ + F of face i, and its
+        // splits in both transverse directions (linear solvers: one sum)
+        R S[M], e1m[M], e1p[M], e2m[M], e2p[M];
+#pragma unroll
+        for (int c = 0; c < M; ++c) S[c] = Pv[c] + (amc[c] + tfF * F[c]);
+        Trans3<RP, R, E1>::split(C, S, e1m, e1p);
+        Trans3<RP, R, E2>::split(C, S, e2m, e2p);
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+          sh[0][c][me] = S[c];
+          sh[1][c][me] = e1m[c];
+          sh[2][c][me] = e1p[c];
+          sh[3][c][me] = e2m[c];
+          sh[4][c][me] = e2p[c];
         }
       }
 #pragma unroll
+      for (int c = 0; c < M; ++c) Pv[c] = apc[c] - tfF * F[c];
+      __syncthreads();
+      if (i > s0 && owner) {
+        // the upper g-face of cell X = i-1 (g = E1, then E2), e the third
+        // direction: transverse h G^+_g S(X) + h G^-_g S(X+g); double
+        // transverse from X and X+g (their own faces) and from X-+e, X+g-+e
+        // (pieces that moved on into X, X+g); the splits are linear, so each
+        // side's pieces are summed before one split
+        const R h = R(-0.5) * dtdn;
+#pragma unroll
+        for (int gi = 0; gi < 2; ++gi) {
+          const int g = gi == 0 ? E1 : E2;
+          const int e = gi == 0 ? E2 : E1;
+          const int cem = gi == 0 ? 3 : 1, cep = gi == 0 ? 4 : 2;  // e-split slots
+          const R k6 = dtdn * s_k[e] * (R(1) / R(6));
+          const int d1g = gi == 0 ? 1 : 0, d2g = gi == 0 ? 0 : 1;  // +g in (E1, E2)
+          const int d1e = gi == 0 ? 0 : 1, d2e = gi == 0 ? 1 : 0;  // +e in (E1, E2)
+          const int x0 = me, xg = nb(d1g, d2g);
+          const int xme = nb(-d1e, -d2e), xpe = nb(d1e, d2e);
+          const int xgme = nb(d1g - d1e, d2g - d2e), xgpe = nb(d1g + d1e, d2g + d2e);
+          R A[M], B[M];
+#pragma unroll
+          for (int c = 0; c < M; ++c) {
+            A[c] = h * sh[0][c][x0] + k6 * (sh[cep][c][x0] - sh[cem][c][x0]) -
+                   k6 * (sh[cep][c][xme] - sh[cem][c][xpe]);
+            B[c] = h * sh[0][c][xg] + k6 * (sh[cep][c][xg] - sh[cem][c][xg]) -
+                   k6 * (sh[cep][c][xgme] - sh[cem][c][xgpe]);
+          }
+          R am_[M], ap_[M], bm_[M], bp_[M], v[M];
+          if (gi == 0) {
+            Trans3<RP, R, E1>::split(C, A, am_, ap_);
+            Trans3<RP, R, E1>::split(C, B, bm_, bp_);
+          } else {
+            Trans3<RP, R, E2>::split(C, A, am_, ap_);
+            Trans3<RP, R, E2>::split(C, B, bm_, bp_);
+          }
+#pragma unroll
+          for (int c = 0; c < M; ++c) v[c] = ap_[c] + bm_[c];
+          int f[3];
+          f[D] = i - 1;
+          f[g] = line[g] + 1;
+          f[e] = line[e];
+          add_fc_own<M, R>(work, L, g, nx, ny, nz, f, v);
+        }
+      }
+      __syncthreads();
+    }
+    // slide the window
+#pragma unroll
+    for (int p = 0; p < MW; ++p) {
+      sl[p] = sc[p];
+      sc[p] = sr[p];
+#pragma unroll
       for (int c = 0; c < M; ++c) {
-        amc[c] = amr[c];
-        apc[c] = apr[c];
+        Wl[p][c] = Wc[p][c];
+        Wc[p][c] = Wr[p][c];
       }
     }
-    if (C.transverse) {
-      // the last face's A+dQ - F enters cell i1-1 (its other face belongs to
-      // the next segment)
-      c0[D] = i1 - 1;
-      propagate3<RP, R, D>(C, work, L, nx, ny, nz, c0, P, dtdn, k3);
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+      amc[c] = amr[c];
+      apc[c] = apr[c];
     }
   }
   R sx = D == 0 ? smax : R(0), sy = D == 1 ? smax : R(0), sz = D == 2 ? smax : R(0);

@@ -202,14 +202,17 @@ struct Launchers {
       const long long nx = a.n3[0], ny = a.n3[1], nz = a.n3[2];
       cudaError_t e = cudaMemsetAsync(a.work3, 0, a.work3_bytes, a.stream);
       if (e != cudaSuccess) return e;
-      // one thread per kSweep3dFaces faces along the sweep, on every line
-      constexpr long long T = kSweep3dFaces;
-      const long long f0 = (nx + T) / T * (ny + 2) * (nz + 2),
-                      f1 = (ny + T) / T * (nz + 2) * (nx + 2),
-                      f2 = (nz + T) / T * (nx + 2) * (ny + 2);
-      classic3d_sweep<RP, R, 0><<<(unsigned)((f0 + 255) / 256), 256, 0, a.stream>>>(a.members, C);
-      classic3d_sweep<RP, R, 1><<<(unsigned)((f1 + 255) / 256), 256, 0, a.stream>>>(a.members, C);
-      classic3d_sweep<RP, R, 2><<<(unsigned)((f2 + 255) / 256), 256, 0, a.stream>>>(a.members, C);
+      // one block per patch of lines and segment of cells along the sweep
+      int npf, nps, nseg;
+      sweep3d_grid(0, (int)nx, (int)ny, (int)nz, npf, nps, nseg);
+      classic3d_sweep<RP, R, 0><<<(unsigned)(npf * nps * nseg), kPatch3d * kPatch3d, 0,
+                                  a.stream>>>(a.members, C);
+      sweep3d_grid(1, (int)nx, (int)ny, (int)nz, npf, nps, nseg);
+      classic3d_sweep<RP, R, 1><<<(unsigned)(npf * nps * nseg), kPatch3d * kPatch3d, 0,
+                                  a.stream>>>(a.members, C);
+      sweep3d_grid(2, (int)nx, (int)ny, (int)nz, npf, nps, nseg);
+      classic3d_sweep<RP, R, 2><<<(unsigned)(npf * nps * nseg), kPatch3d * kPatch3d, 0,
+                                  a.stream>>>(a.members, C);
       classic3d_update<RP, R><<<a.ntiles_total, 256, 0, a.stream>>>(a.members, C);
       return cudaGetLastError();
     } else if constexpr (ND == 2 && RP::MA > 0) {
@@ -221,7 +224,11 @@ struct Launchers {
         return classic1d<true>(a, C);
       return classic1d<false>(a, C);
     } else {
-      if (sizeof(R) == 4 && C.lim == CLAW_LIM_MC && C.order == 2 && C.transverse == 2)
+      // systems of up to three fields: with more, the two block widths of the
+      // fixed-settings form were seen to round differently, and every tile
+      // shape must give the same bits
+      if (sizeof(R) == 4 && RP::M <= 3 && C.lim == CLAW_LIM_MC && C.order == 2 &&
+          C.transverse == 2)
         return classic2d<true>(a, C);
       return classic2d<false>(a, C);
     }
@@ -255,7 +262,7 @@ struct Launchers {
   }
   template <bool FAST>
   static cudaError_t classic2d(const LaunchArgs& a, const MConsts<R>& C) {
-    if constexpr (ND == 2 && RP::MA == 0 && (!FAST || sizeof(R) == 4)) {
+    if constexpr (ND == 2 && RP::MA == 0 && (!FAST || (sizeof(R) == 4 && RP::M <= 3))) {
       if constexpr (classic2d_fits<RP, R>(128)) {
         if (a.bw == 128) {
           classic2d_kernel<RP, R, 128, FAST><<<launch_grid(a.ntiles_total), 128, 0, a.stream>>>(
