@@ -125,8 +125,8 @@ const char* check_method(const claw_method& m, int nd) {
   if (m.scheme == CLAW_CLASSIC && m.order != 1 && m.order != 2) return "order must be 1 or 2";
   if (m.transverse < 0 || m.transverse > 2) return "transverse must be 0, 1 or 2";
   if (m.scheme == CLAW_SHARPCLAW &&
-      (m.weno_order < 5 || m.weno_order > 13 || m.weno_order % 2 == 0))
-    return "weno_order must be odd, 5 to 13";
+      (m.weno_order < 5 || m.weno_order > 17 || m.weno_order % 2 == 0))
+    return "weno_order must be odd, 5 to 17";
   if (m.scheme == CLAW_SHARPCLAW && m.time_integrator != CLAW_SSP_RK3 &&
       m.time_integrator != CLAW_SSP104)
     return "unknown time integrator";
@@ -176,9 +176,10 @@ const char* check_grid(const claw_grid& g, const claw_method& m) {
   return nullptr;
 }
 
-int tiles_of(int scheme, int nd, int prec, int nx, int ny, int bw, int h) {
+// ma: the solver's aux fields (the 1D classic tile depends on them)
+int tiles_of(int scheme, int nd, int prec, int ma, int nx, int ny, int bw, int h) {
   if (scheme == CLAW_CLASSIC)
-    return nd == 1 ? classic1d_tiles(nx, prec) : classic2d_tiles(nx, ny, bw, h);
+    return nd == 1 ? classic1d_tiles(nx, prec, ma) : classic2d_tiles(nx, ny, bw, h);
   return nd == 1 ? sharp_tiles(nx, 1, kSharpTX1, 1) : sharp_tiles(nx, ny, kSharpTX2, kSharpTY2);
 }
 
@@ -628,9 +629,10 @@ claw_status claw_solver_create(const claw_method* m, const claw_grid* g, void* s
                  ? 1
                  : 0;
   if (s->faces) s->tuned = 1;  // no tile shapes to choose
-  s->ntiles = (s->nd == 3 || s->faces) ? (int)((cells_of(s->g) + 255) / 256)
-                         : tiles_of(m->scheme, s->nd, s->prec, (int)s->g.n[0], (int)s->g.n[1],
-                                    s->bw, s->h);
+  s->ntiles = (s->nd == 3 || s->faces)
+                  ? (int)((cells_of(s->g) + 255) / 256)
+                  : tiles_of(m->scheme, s->nd, s->prec, s->ks.MA, (int)s->g.n[0],
+                             (int)s->g.n[1], s->bw, s->h);
   *out = s;
   return CLAW_OK;
 }
@@ -700,8 +702,8 @@ claw_status claw_solver_tune(claw_solver* s, int mode, int* bw, int* h) {
     s->bw = *bw;
     s->h = *h;
     if (s->nd != 3 && !s->faces)
-      s->ntiles = tiles_of(s->m.scheme, s->nd, s->prec, (int)s->g.n[0], (int)s->g.n[1], s->bw,
-                           s->h);
+      s->ntiles = tiles_of(s->m.scheme, s->nd, s->prec, s->ks.MA, (int)s->g.n[0],
+                           (int)s->g.n[1], s->bw, s->h);
     s->tuned = 1;
     drop_graph(s);
     SCK(enter(s));
@@ -1168,7 +1170,7 @@ claw_status claw_batch_bind(claw_batch* b, void* const* q, const void* const* au
       mb.work3 = w3p;
       w3p += b->work3_bytes[k];
     } else {
-      mb.ntiles = tiles_of(b->m.scheme, b->nd, b->prec, mb.nx, mb.ny, b->bw, b->h);
+      mb.ntiles = tiles_of(b->m.scheme, b->nd, b->prec, b->ks.MA, mb.nx, mb.ny, b->bw, b->h);
       for (int t = 0; t < mb.ntiles; ++t) b->h_tiles.push_back(Tile{k, t});
     }
     const int ms = b->nd == 3 ? 0 : maxspeed_tiles(mb.nx, mb.ny);
@@ -1521,7 +1523,8 @@ claw_status claw_server_pump(claw_server* v, int steps, int* running, int* queue
       r.mem.work3 = p;
       r.mem.ntiles = (int)((cells_of(r.g) + 255) / 256);
     } else {
-      r.mem.ntiles = tiles_of(v->m.scheme, v->nd, v->prec, r.mem.nx, r.mem.ny, v->bw, v->h);
+      r.mem.ntiles =
+          tiles_of(v->m.scheme, v->nd, v->prec, v->ks.MA, r.mem.nx, r.mem.ny, v->bw, v->h);
     }
     DevCtl c = make_ctl(v->m, r.g, v->nbuf, 0.0, r.t_end);
     VCK(cudaMemcpyAsync(r.mem.q[0], r.q0.data(), r.q0.size(), cudaMemcpyHostToDevice, v->st));

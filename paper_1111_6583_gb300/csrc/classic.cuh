@@ -46,6 +46,18 @@ struct VecIO<float, 4> {
   }
 };
 template <>
+struct VecIO<float, 8> {
+  __device__ static __forceinline__ void load(const float* p, float (&v)[8]) {
+    const float4 a = __ldg((const float4*)p), b = __ldg((const float4*)p + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  }
+  __device__ static __forceinline__ void store(float* p, const float (&v)[8]) {
+    ((float4*)p)[0] = make_float4(v[0], v[1], v[2], v[3]);
+    ((float4*)p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+  }
+};
+template <>
 struct VecIO<double, 2> {
   __device__ static __forceinline__ void load(const double* p, double (&v)[2]) {
     const double2 a = __ldg((const double2*)p);
@@ -106,11 +118,22 @@ struct CellPrep<RpElasticity<R, 1>, R> {
   };
   __device__ static __forceinline__ void prep(const MConsts<R>&, const R (&q)[2],
                                               const R (&a)[2], Cell& c) {
-    const R ir = FM<R>::rcp(a[0]);
     c.e = FM<R>::exp(a[1] * q[0]);
-    c.u = q[1] * ir;
-    c.c = FM<R>::sqrt(a[1] * c.e * ir);
-    c.Z = a[0] * c.c;
+    if constexpr (sizeof(R) == 4) {
+      // one reciprocal square root r = 1/sqrt(K e rho) gives them all:
+      // c = K e r, Z = rho c = K e rho r, 1/rho = c r
+      const R t = a[1] * c.e;
+      const R u = t * a[0];
+      const R r = FM<R>::rsqrt(u);
+      c.c = t * r;
+      c.Z = u * r;
+      c.u = q[1] * (c.c * r);
+    } else {
+      const R ir = FM<R>::rcp(a[0]);
+      c.u = q[1] * ir;
+      c.c = FM<R>::sqrt(a[1] * c.e * ir);
+      c.Z = a[0] * c.c;
+    }
   }
   // the f-wave solve of RpElasticity on prepared cells
   __device__ static __forceinline__ void solve(const MConsts<R>&, const Cell& l, const Cell& r,
@@ -166,7 +189,7 @@ __device__ __forceinline__ void limit1d(const MConsts<R>& C, int order,
 // FAST: the MC limiter and second order fixed at compile time (the launcher
 // takes it for FP32 methods with those settings)
 template <class RP, typename R, int NT, int K, int SPW, bool FAST = false>
-__global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? 8 : 1)
+__global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? (K >= 8 ? 4 : 8) : 1)
     classic1d_kernel(const Member* __restrict__ members, const Tile* __restrict__ tiles,
                      int ntiles_total, const MConsts<R> C) {
   constexpr int M = RP::M, MW = RP::MW, MA = RP::MA;

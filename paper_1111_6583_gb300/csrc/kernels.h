@@ -55,13 +55,17 @@ struct KernelSet {
 
 // tile geometry shared by the host (tile tables) and the kernels
 constexpr int kClassic1dThreads = 128;
-// cells per lane: FP32 4 (16-byte loads; the fastest batched form), FP64 2
-// (twice the warps for the small single grids the FP64 form runs)
-constexpr int classic1d_K(int prec) { return prec == 0 ? 2 : 4; }
+// cells per lane: FP64 2 (more warps for the small single grids the FP64
+// form runs); FP32 8 for solvers without aux fields (two 16-byte loads per
+// field: 2^26-cell acoustics 0.42 -> 0.28 ms) and 4 for solvers that read
+// aux fields (the elasticity ensemble is faster with 4: 0.59 vs 0.76 ms)
+constexpr int classic1d_K(int prec, int ma) { return prec == 0 ? 2 : (ma == 0 ? 8 : 4); }
 // a warp writes the cells of its lanes 1..30 (lanes 0 and 31 hold its halo)
-constexpr int classic1d_T(int prec) { return kClassic1dThreads / 32 * 30 * classic1d_K(prec); }
-inline int classic1d_tiles(int nx, int prec) {
-  return (nx + classic1d_T(prec) - 1) / classic1d_T(prec);
+constexpr int classic1d_T(int prec, int ma) {
+  return kClassic1dThreads / 32 * 30 * classic1d_K(prec, ma);
+}
+inline int classic1d_tiles(int nx, int prec, int ma) {
+  return (nx + classic1d_T(prec, ma) - 1) / classic1d_T(prec, ma);
 }
 constexpr int kSharpTX2 = 16, kSharpTY2 = 8;  // 2D SharpClaw tile
 constexpr int kSharpTX1 = 128;                // 1D SharpClaw tile
