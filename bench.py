@@ -825,7 +825,7 @@ def profile_case(case, tile=None):
     psystem -- 1024^2 p-system checkerboard FP64, one SSP(10,4) step (10 stages);
     weno7 -- 1024x512 shock-bubble FP64, WENO7 + SSP(10,4), one step;
     acou3d -- 256^3 constant-medium acoustics FP64, 3 steps (acou3d128: 128^3,
-    small enough for a multi-pass capture)."""
+    small enough for a multi-pass capture; acou3d_f32, acou3d128_f32: FP32)."""
     import torch
     from paper_1111_6583_gb300 import claw
     from paper_1111_6583_gb300 import workloads as wl
@@ -862,9 +862,9 @@ def profile_case(case, tile=None):
         s = claw.Solver(sp, "fp64")
         s.set_t_end(0.2)
         s.advance(1)
-    elif case in ("acou3d", "acou3d128"):
-        sp = wl.acoustics_3d(n=256 if case == "acou3d" else 128)
-        s = claw.Solver(sp, "fp64")
+    elif case in ("acou3d", "acou3d128", "acou3d_f32", "acou3d128_f32"):
+        sp = wl.acoustics_3d(n=128 if "128" in case else 256)
+        s = claw.Solver(sp, "fp32" if case.endswith("f32") else "fp64")
         s.set_t_end(sp["t_end"])
         s.advance(3)
     elif case == "vc":
@@ -903,7 +903,8 @@ def main():
                     help="BW,H: fixed 2D tile shape for --case sw2d1024 and --record-traffic")
     ap.add_argument("--case", default=None,
                     help="run one short launch sequence for a profiler (sw2d64, sw2d32, sw2d1024, "
-                         "elast, sharp, axisym, vc, acou2d, psystem, weno7, acou3d, acou3d128)")
+                         "elast, sharp, axisym, vc, acou2d, psystem, weno7, acou3d, acou3d128, "
+                         "acou3d_f32, acou3d128_f32)")
     ap.add_argument("--cpu-single", type=float, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.cpu_single is not None:

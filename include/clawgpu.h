@@ -98,7 +98,7 @@ typedef struct {
   int prec;            /* CLAW_FP64 | CLAW_FP32                                   */
   int order;           /* classic: 1 Godunov, 2 with limited corrections          */
   int transverse;      /* classic 2D: 0 none, 1 fluctuations, 2 with corrections  */
-  int weno_order;      /* SharpClaw: 5 (default), 7, 9, 11 or 13 (Sec. 3.3, PyWENO orders) */
+  int weno_order;      /* SharpClaw: 5 (default), 7, 9, ..., 17 (Sec. 3.3, PyWENO orders) */
   int char_decomp;     /* SharpClaw: 0 component-wise, 1 characteristic-wise      */
   int entropy_fix;     /* Harten-Hyman fix in the Roe solvers (SW, Euler)         */
   int max_retries;     /* rejected attempts allowed per step                      */

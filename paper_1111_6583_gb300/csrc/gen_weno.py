@@ -17,14 +17,22 @@ candidate stencil k = v[k..k+r-1].
     that vanishes on constants; on the differences v[k+j] - v[k] (j >= 1) it
     is positive definite and is emitted as sum_i D_i y_i^2 with y = L^T dv
     (exact LDL^T), which keeps the rounding of beta small where the data
-    are nearly constant.
+    are nearly constant.  Orders 15 and 17 (r = 8, 9), whose forms carry
+    coefficients in the thousands, are emitted instead as tables in constant
+    memory and one out-of-line function per precision that follows the plain
+    definitions step by step -- q_k = sum_j c_kj v_{k+j}, beta_k = sum_a sum_b
+    B_ab dv_a dv_b, alpha_k = d_k / (eps + beta_k)^2, sum_k alpha_k q_k /
+    sum alpha -- each product, sum and quotient rounded once in that order
+    (no contraction): the values the definitions give, at the cost of speed
+    these rarely used orders can bear.
 
 Run: python gen_weno.py  (rewrites weno_hi.cuh beside this file).
 """
 import os
 from fractions import Fraction as Fr
 
-ORDERS_R = (4, 5, 6, 7)  # WENO7 .. WENO13
+ORDERS_R = (4, 5, 6, 7, 8, 9)  # WENO7 .. WENO17
+FULL_FORM_R = 8  # from this r on, the full quadratic form (see above)
 
 
 # --- polynomials as coefficient lists (lowest degree first) ---------------
@@ -120,7 +128,57 @@ def lit(x):
     return "R(%s)" % repr(float(x))
 
 
+def emit_tables(r):
+    """orders from FULL_FORM_R on: coefficient tables and the stepwise form"""
+    c, d, B = derive(r)
+    n = 2 * r - 1
+    o = 2 * r - 1
+    out = []
+    out.append("// WENO%d coefficients: candidates c[k][j], optimal weights d[k], smoothness" % o)
+    out.append("// forms B[k][a-1][b-1] on the differences v[k+a] - v[k] (a, b >= 1)")
+    out.append("static __constant__ double kWeno%dC[%d][%d] = {" % (o, r, r))
+    for k in range(r):
+        out.append("    {%s}," % ", ".join(repr(float(x)) for x in c[k]))
+    out.append("};")
+    out.append("static __constant__ double kWeno%dD[%d] = {%s};"
+               % (o, r, ", ".join(repr(float(x)) for x in d)))
+    out.append("static __constant__ double kWeno%dB[%d][%d][%d] = {" % (o, r, r - 1, r - 1))
+    for k in range(r):
+        rows = ["{%s}" % ", ".join(repr(float(B[k][a][b])) for b in range(1, r))
+                for a in range(1, r)]
+        out.append("    {%s}," % ", ".join(rows))
+    out.append("};")
+    out.append("// WENO%d: left-biased value at the right edge of the centre cell of" % o)
+    out.append("// v[0..%d], stepwise from the definitions (see gen_weno.py)." % (n - 1))
+    out.append("template <typename R>")
+    out.append("__device__ __noinline__ R weno%d(const R (&v)[%d], R eps) {" % (o, n))
+    out.append("  R qk[%d], al[%d];" % (r, r))
+    out.append("  R sum = R(0);")
+    out.append("#pragma unroll 1")
+    out.append("  for (int k = 0; k < %d; ++k) {" % r)
+    out.append("    R q = R(0), beta = R(0);")
+    out.append("    for (int j = 0; j < %d; ++j) q = add_rn(q, mul_rn((R)kWeno%dC[k][j], v[k + j]));"
+               % (r, o))
+    out.append("    for (int a = 1; a < %d; ++a)" % r)
+    out.append("      for (int b = 1; b < %d; ++b)" % r)
+    out.append("        beta = add_rn(beta, mul_rn(mul_rn((R)kWeno%dB[k][a - 1][b - 1], "
+               "v[k + a] - v[k]), v[k + b] - v[k]));" % o)
+    out.append("    qk[k] = q;")
+    out.append("    const R e = add_rn(eps, beta);")
+    out.append("    al[k] = (R)kWeno%dD[k] / mul_rn(e, e);" % o)
+    out.append("    sum = add_rn(sum, al[k]);")
+    out.append("  }")
+    out.append("  R out = R(0);")
+    out.append("#pragma unroll 1")
+    out.append("  for (int k = 0; k < %d; ++k) out = add_rn(out, mul_rn(al[k] / sum, qk[k]));" % r)
+    out.append("  return out;")
+    out.append("}")
+    return "\n".join(out)
+
+
 def emit(r):
+    if r >= FULL_FORM_R:
+        return emit_tables(r)
     c, d, B = derive(r)
     n = 2 * r - 1
     out = []
@@ -132,9 +190,9 @@ def emit(r):
         terms = " + ".join("%s * v[%d]" % (lit(c[k][j]), k + j) for j in range(r))
         out.append("  const R q%d = %s;" % (k, terms))
     for k in range(r):
-        L, D = ldl_on_differences(B[k])
         for j in range(1, r):
             out.append("  const R d%d_%d = v[%d] - v[%d];" % (k, j, k + j, k))
+        L, D = ldl_on_differences(B[k])
         ys = []
         for i in range(r - 1):
             terms = " + ".join("%s * d%d_%d" % (lit(L[j][i]), k, j + 1) for j in range(i, r - 1)
@@ -168,7 +226,13 @@ def render():
     parts = ["// weno_hi.cuh -- generated by gen_weno.py from exact rational derivations;",
              "// do not edit.  Higher-order WENO reconstructions (Sec. 3.3, PyWENO",
              "// subsection) used by the SharpClaw stage kernel.",
-             "#pragma once", "", '#include "riemann.cuh"', "", "namespace claw {", ""]
+             "#pragma once", "", '#include "riemann.cuh"', "", "namespace claw {", "",
+             "// a product and a sum rounded once each (never fused)",
+             "__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }",
+             "__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }",
+             "__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }",
+             "__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }",
+             ""]
     for r in ORDERS_R:
         parts.append(emit(r))
         parts.append("")

@@ -238,7 +238,7 @@ struct Launchers {
   template <bool FAST>
   static cudaError_t classic1d(const LaunchArgs& a, const MConsts<R>& C) {
     if constexpr (ND == 1 && (!FAST || sizeof(R) == 4)) {
-      constexpr int K = sizeof(R) == 8 ? classic1d_K(0) : classic1d_K(1);
+      constexpr int K = classic1d_K(sizeof(R) == 8 ? 0 : 1, RP::MA);
       // a warp takes a whole tile when the tiles fill every resident warp
       // (blocks x NW), else a single unit
       constexpr int NW = kClassic1dThreads / 32;
@@ -301,6 +301,8 @@ struct Launchers {
         case 5: sharp_launch<5>(a, C, op); break;
         case 6: sharp_launch<6>(a, C, op); break;
         case 7: sharp_launch<7>(a, C, op); break;
+        case 8: sharp_launch<8>(a, C, op); break;
+        case 9: sharp_launch<9>(a, C, op); break;
         default: return cudaErrorInvalidValue;
       }
     }

@@ -85,7 +85,7 @@ __device__ __forceinline__ void div_many(const R (&n)[N], const R (&d)[N], R (&q
   for (int i = 0; i < N; ++i) q[i] = FM<R>::div(n[i], d[i]);
 }
 
-// WENO of order 2 RW - 1 (7 .. 13; WENO5 takes weno5_pair): left-biased value at the right edge of cell
+// WENO of order 2 RW - 1 (7 .. 17; WENO5 takes weno5_pair): left-biased value at the right edge of cell
 // v[o + RW - 1] from v[o .. o + 2 RW - 2] (REV: the mirrored stencil, value at
 // the left edge of cell v[o + RW], read from v[o + 2 RW - 1] downwards).
 template <int RW, bool REV, typename R, int NV>
@@ -97,7 +97,9 @@ __device__ __forceinline__ R weno_edge(const R (&w)[NV], R eps) {
   if constexpr (RW == 4) return weno7<R>(v, eps);
   else if constexpr (RW == 5) return weno9<R>(v, eps);
   else if constexpr (RW == 6) return weno11<R>(v, eps);
-  else return weno13<R>(v, eps);
+  else if constexpr (RW == 7) return weno13<R>(v, eps);
+  else if constexpr (RW == 8) return weno15<R>(v, eps);
+  else return weno17<R>(v, eps);
 }
 
 template <class RP, typename R, int ND, int TX, int TY, int RW>

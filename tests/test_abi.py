@@ -81,12 +81,12 @@ def test_method_init_and_validation_without_gpu(lib_path):
     g.ndim = 1
     assert lib.claw_solver_create(ctypes.byref(m), ctypes.byref(g), None,
                                   ctypes.byref(h)) == claw.CLAW_EINVAL
-    # SharpClaw options: odd WENO orders 5..13, the two SSP integrators, and
+    # SharpClaw options: odd WENO orders 5..17, the two SSP integrators, and
     # a grid at least as wide as the WENO ghost layer
     lib.claw_method_init(ctypes.byref(m), claw.RP["euler_roe"], 1)
     m.scheme = claw.SHARPCLAW
     g.n[0] = 64
-    for bad in (15, 6, 3):
+    for bad in (19, 6, 3):
         m.weno_order = bad
         assert lib.claw_solver_create(ctypes.byref(m), ctypes.byref(g), None,
                                       ctypes.byref(h)) == claw.CLAW_EINVAL

@@ -1,9 +1,10 @@
-"""GPU parity of SharpClaw with WENO of orders 7 to 13 (Sec. 2.1 and the
+"""GPU parity of SharpClaw with WENO of orders 7 to 17 (Sec. 2.1 and the
 PyWENO subsection) against the oracle, whose coefficients come from an
 independent exact derivation: every Riemann solver in 1D, the 2D systems,
 component- and characteristic-wise, boundary conditions that reach the
-wider ghost layers (4 to 7 cells), FP32, and the shock-bubble with WENO7 +
-SSP(10,4) through the controller.
+wider ghost layers (4 to 9 cells), FP32, and the shock-bubble with WENO7 +
+SSP(10,4) through the controller.  Orders 15 and 17 take the smoothness
+indicators' full quadratic forms in the definitions' order on both sides.
 """
 import numpy as np
 import pytest
@@ -16,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 RPS_1D = ["advection", "acoustics", "sw_roe", "euler_roe", "euler_hlle", "elasticity_fwave"]
 RPS_2D = ["advection", "acoustics", "sw_roe", "euler_roe", "euler_hlle"]
-ORDERS = [7, 9, 11, 13]
+ORDERS = [7, 9, 11, 13, 15, 17]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -55,7 +56,7 @@ def test_weno_order_2d_fp64(orc, order, rp):
 @pytest.mark.parametrize("order", ORDERS)
 @pytest.mark.parametrize("bc", ["wall", "extrap"])
 def test_weno_order_boundaries(orc, order, bc):
-    """Ghost layers of width 4 to 7 filled by wall and extrapolation rules."""
+    """Ghost layers of width 4 to 9 filled by wall and extrapolation rules."""
     s1 = wl.random_1d("euler_roe", 64, bc=(bc, bc), scheme="sharpclaw", char_decomp=1,
                       weno_order=order)
     qo, _ = oracle_fixed_steps(orc, s1, 0.1 / 64, 3)

@@ -1,8 +1,9 @@
-"""The generator of the GPU's WENO 7..13 reconstructions (csrc/gen_weno.py)
+"""The generator of the GPU's WENO 7..17 reconstructions (csrc/gen_weno.py)
 against the oracle's independent derivation (oracle/weno_coeffs.py), exactly
 in rational arithmetic: candidate coefficients, optimal weights and
-smoothness forms (Sec. 3.3, PyWENO), and the emitted sum-of-squares
-form of each smoothness indicator.  No GPU needed."""
+smoothness forms (Sec. 3.3, PyWENO), the emitted sum-of-squares form of each
+smoothness indicator (orders 7..13), and the full form's coefficients as
+emitted (orders 15, 17).  No GPU needed."""
 import importlib.util
 import os
 from fractions import Fraction
@@ -47,6 +48,26 @@ def test_emitted_sum_of_squares_is_the_smoothness_form(gen, r):
         # constants: rows and columns of B_k sum to zero
         for a in range(r):
             assert sum(Bk[a]) == 0
+
+
+@pytest.mark.parametrize("r", [8, 9])
+def test_emitted_tables_are_the_coefficients(gen, r):
+    """Orders 15 and 17: the emitted tables hold, entry by entry, the doubles
+    nearest the exact candidate coefficients, optimal weights and smoothness
+    forms (on the differences, a, b >= 1)."""
+    import re
+    c, d, B = gen.derive(r)
+    text = gen.emit(r)
+    o = 2 * r - 1
+
+    def table(name):
+        body = text.split("kWeno%d%s" % (o, name))[1].split(";")[0]
+        return [float(x) for x in re.findall(r"-?\d[\d.e+-]*", body.split("=")[1])]
+
+    assert table("C") == [float(x) for row in c for x in row]
+    assert table("D") == [float(x) for x in d]
+    assert table("B") == [float(B[k][a][b]) for k in range(r) for a in range(1, r)
+                          for b in range(1, r)]
 
 
 def test_generated_header_is_current(gen):
