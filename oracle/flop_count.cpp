@@ -69,6 +69,11 @@ inline CD exp(CD a) { ++n_tr; return CD(std::exp(a.v)); }
 inline CD log(CD a) { ++n_tr; return CD(std::log(a.v)); }
 inline CD log1p(CD a) { ++n_tr; return CD(std::log1p(a.v)); }
 inline CD pow(CD a, CD b) { ++n_tr; return CD(std::pow(a.v, b.v)); }
+inline CD fma(CD a, CD b, CD c) {
+  ++n_mul;
+  ++n_add;
+  return CD(std::fma(a.v, b.v, c.v));
+}
 inline CD fabs(CD a) { return CD(std::fabs(a.v)); }
 inline CD fmin(CD a, CD b) { return CD(std::fmin(a.v, b.v)); }
 inline CD fmax(CD a, CD b) { return CD(std::fmax(a.v, b.v)); }

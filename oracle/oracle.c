@@ -1293,15 +1293,49 @@ double orc_weno5(const double* v, double eps) {
  * v_k^T B[k] v_k over the stencil's r cells.  beta measures derivatives only,
  * so it is unchanged when a constant is subtracted from the data; the form is
  * evaluated on v - v[k] to keep its rounding relative to the variation. */
+/* Error-free transformations: a + b = s + e exactly (Knuth's TwoSum) and
+ * a b = p + e exactly (by one fused multiply-add). */
+static void two_sum(double a, double b, double* s, double* e) {
+  *s = a + b;
+  const double z = *s - a;
+  *e = (a - (*s - z)) + (b - z);
+}
+static void two_prod(double a, double b, double* p, double* e) {
+  *p = a * b;
+  *e = fma(a, b, -*p);
+}
+
+/* The smoothness indicator beta = sum_a sum_b B_ab dv_a dv_b on the
+ * differences dv_j = v_j - v_0 (Sec. 3.3: the form of sum_l int (p^(l))^2).
+ * Its terms grow with the order (coefficients in the thousands at orders 15
+ * and 17) while beta itself stays of the size of dv^2, so a plain running sum
+ * would carry rounding errors far above beta's own; the products and the sum
+ * are therefore evaluated by error-free transformations with compensation
+ * (Ogita, Rump and Oishi, "Accurate sum and dot product", 2005), which
+ * returns the form's value to about one rounding. */
+static double smoothness_form(int r, const double* Bk, const double* v) {
+  double hi = 0.0, lo = 0.0;
+  for (int a = 0; a < r; ++a) {
+    const double da = v[a] - v[0];
+    for (int b = 0; b < r; ++b) {
+      const double db = v[b] - v[0];
+      double x, xe, y, ye, se;
+      two_prod(Bk[a * r + b], da, &x, &xe);  /* B da = x + xe */
+      two_prod(x, db, &y, &ye);              /* x db = y + ye */
+      two_sum(hi, y, &hi, &se);
+      lo += se + ye + xe * db;
+    }
+  }
+  return hi + lo;
+}
+
 double orc_weno_r(int r, const double* c, const double* d, const double* B, const double* v,
                   double eps) {
   double qk[9], alpha[9], sum = 0.0;
   for (int k = 0; k < r; ++k) {
-    double q = 0.0, beta = 0.0;
+    double q = 0.0;
     for (int j = 0; j < r; ++j) q += c[k * r + j] * v[k + j];
-    for (int a = 0; a < r; ++a)
-      for (int b = 0; b < r; ++b)
-        beta += B[(k * r + a) * r + b] * (v[k + a] - v[k]) * (v[k + b] - v[k]);
+    const double beta = smoothness_form(r, B + k * r * r, v + k);
     qk[k] = q;
     alpha[k] = d[k] / ((eps + beta) * (eps + beta));
     sum += alpha[k];

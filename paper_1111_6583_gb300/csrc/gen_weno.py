@@ -17,14 +17,17 @@ candidate stencil k = v[k..k+r-1].
     that vanishes on constants; on the differences v[k+j] - v[k] (j >= 1) it
     is positive definite and is emitted as sum_i D_i y_i^2 with y = L^T dv
     (exact LDL^T), which keeps the rounding of beta small where the data
-    are nearly constant.  Orders 15 and 17 (r = 8, 9), whose forms carry
-    coefficients in the thousands, are emitted instead as tables in constant
-    memory and one out-of-line function per precision that follows the plain
-    definitions step by step -- q_k = sum_j c_kj v_{k+j}, beta_k = sum_a sum_b
-    B_ab dv_a dv_b, alpha_k = d_k / (eps + beta_k)^2, sum_k alpha_k q_k /
-    sum alpha -- each product, sum and quotient rounded once in that order
-    (no contraction): the values the definitions give, at the cost of speed
-    these rarely used orders can bear.
+    are nearly constant.  Orders 15 and 17 (r = 8, 9) have form coefficients
+    in the thousands: there both the form's rounded coefficients and a plain
+    sum of its terms carry errors far above beta, so these orders are
+    emitted as tables in constant memory (the doubles nearest c, d and B)
+    and one out-of-line function per precision that follows the definitions
+    step by step -- q_k = sum_j c_kj v_{k+j}; beta_k = sum_a sum_b B_ab dv_a
+    dv_b by error-free products and a compensated sum (Ogita, Rump and Oishi,
+    "Accurate sum and dot product"); alpha_k = d_k / (eps + beta_k)^2; sum_k
+    alpha_k q_k / sum alpha -- each operation rounded once, in that order:
+    the value of the definition on those doubles to about one rounding, at a
+    cost these rarely used orders can bear.
 
 Run: python gen_weno.py  (rewrites weno_hi.cuh beside this file).
 """
@@ -156,13 +159,26 @@ def emit_tables(r):
     out.append("  R sum = R(0);")
     out.append("#pragma unroll 1")
     out.append("  for (int k = 0; k < %d; ++k) {" % r)
-    out.append("    R q = R(0), beta = R(0);")
+    out.append("    R q = R(0), beta;")
     out.append("    for (int j = 0; j < %d; ++j) q = add_rn(q, mul_rn((R)kWeno%dC[k][j], v[k + j]));"
                % (r, o))
-    out.append("    for (int a = 1; a < %d; ++a)" % r)
-    out.append("      for (int b = 1; b < %d; ++b)" % r)
-    out.append("        beta = add_rn(beta, mul_rn(mul_rn((R)kWeno%dB[k][a - 1][b - 1], "
-               "v[k + a] - v[k]), v[k + b] - v[k]));" % o)
+    out.append("    // beta: error-free products and a compensated sum (the zero terms of")
+    out.append("    // dv_0 = 0 are left out: they change neither part)")
+    out.append("    R hi = R(0), lo = R(0);")
+    out.append("    for (int a = 1; a < %d; ++a) {" % r)
+    out.append("      const R da = v[k + a] - v[k];")
+    out.append("      for (int b = 1; b < %d; ++b) {" % r)
+    out.append("        const R db = v[k + b] - v[k];")
+    out.append("        const R bab = (R)kWeno%dB[k][a - 1][b - 1];" % o)
+    out.append("        const R x = mul_rn(bab, da), xe = fma_rn(bab, da, -x);")
+    out.append("        const R y = mul_rn(x, db), ye = fma_rn(x, db, -y);")
+    out.append("        const R s = add_rn(hi, y), z = sub_rn(s, hi);")
+    out.append("        const R se = add_rn(sub_rn(hi, sub_rn(s, z)), sub_rn(y, z));")
+    out.append("        hi = s;")
+    out.append("        lo = add_rn(lo, add_rn(add_rn(se, ye), mul_rn(xe, db)));")
+    out.append("      }")
+    out.append("    }")
+    out.append("    beta = add_rn(hi, lo);")
     out.append("    qk[k] = q;")
     out.append("    const R e = add_rn(eps, beta);")
     out.append("    al[k] = (R)kWeno%dD[k] / mul_rn(e, e);" % o)
@@ -227,11 +243,19 @@ def render():
              "// do not edit.  Higher-order WENO reconstructions (Sec. 3.3, PyWENO",
              "// subsection) used by the SharpClaw stage kernel.",
              "#pragma once", "", '#include "riemann.cuh"', "", "namespace claw {", "",
-             "// a product and a sum rounded once each (never fused)",
+             "// operations rounded once each (never fused or reordered)",
              "__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }",
              "__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }",
              "__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }",
              "__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }",
+             "__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }",
+             "__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }",
+             "__device__ __forceinline__ double fma_rn(double a, double b, double c) {",
+             "  return __fma_rn(a, b, c);",
+             "}",
+             "__device__ __forceinline__ float fma_rn(float a, float b, float c) {",
+             "  return __fmaf_rn(a, b, c);",
+             "}",
              ""]
     for r in ORDERS_R:
         parts.append(emit(r))

@@ -204,3 +204,71 @@ def test_sharpclaw_weno7_resolves_a_discontinuity_without_overshoot(orc):
     assert info["status"] == "ok" and info["t"] == 1.0
     assert abs(q.sum() - q0.sum()) <= 1e-12 * q0.sum()
     assert q.max() <= 1.05 and q.min() >= -0.05
+
+
+def _edge_exact(r, v, eps):
+    """The WENO edge value of the definitions in exact rational arithmetic, on
+    the doubles nearest the exact coefficients (the tables the oracle reads)
+    and the double inputs v."""
+    c, d, B = weno_coefficients(r)
+    V = [Fraction(x) for x in v]
+    e = Fraction(eps)
+    num, den = Fraction(0), Fraction(0)
+    for k in range(r):
+        q = sum(Fraction(float(c[k][j])) * V[k + j] for j in range(r))
+        beta = sum(Fraction(float(B[k][a][b])) * (V[k + a] - V[k]) * (V[k + b] - V[k])
+                   for a in range(r) for b in range(r))
+        alpha = Fraction(float(d[k])) / ((e + beta) * (e + beta))
+        num += alpha * q
+        den += alpha
+    return float(num / den)
+
+
+def _edge_plain(r, v, eps):
+    """The same definitions summed plainly in double precision."""
+    c, d, B = weno_coefficients(r)
+    al, qs = [], []
+    for k in range(r):
+        q = 0.0
+        for j in range(r):
+            q += float(c[k][j]) * v[k + j]
+        beta = 0.0
+        for a in range(r):
+            for b in range(r):
+                beta += float(B[k][a][b]) * (v[k + a] - v[k]) * (v[k + b] - v[k])
+        qs.append(q)
+        al.append(float(d[k]) / ((eps + beta) * (eps + beta)))
+    s = sum(al)
+    return sum((a / s) * q for a, q in zip(al, qs))
+
+
+@pytest.mark.parametrize("r", [4, 5, 6, 7, 8, 9])
+def test_edge_value_is_the_definitions_accurately(r):
+    """On smooth data, smooth data with a small jump (intermediate weights), a
+    kink and noise, the oracle's edge value equals the exact rational
+    evaluation of the definitions on the same doubles to 1e-12 relative (what
+    remains is the candidate sums' rounding, a few ulps of sum |c_kj v_j|).
+    Plain double sums of the smoothness forms -- terms of size |B| dv^2
+    against beta of size dv^2 -- miss by 1e-10 and more at order 17 on the
+    same data, which is why the oracle evaluates the forms by error-free
+    transformations."""
+    rng = np.random.Generator(np.random.PCG64(6583 + r))
+    n = 2 * r - 1
+    i = np.arange(n)
+    families = [
+        lambda: np.sin(rng.uniform(0, 6) + i * rng.uniform(0.002, 0.1)) * rng.uniform(0.5, 3.0),
+        lambda: (np.sin(rng.uniform(0, 6) + i * rng.uniform(0.01, 0.1)) +
+                 np.where(i >= rng.integers(1, n), rng.uniform(1e-4, 1e-2), 0.0)),
+        lambda: np.abs(i - rng.uniform(3, n - 3)) * rng.uniform(0.01, 0.1),
+        lambda: rng.normal(size=n),
+    ]
+    worst, worst_plain = 0.0, 0.0
+    for t in range(80):
+        v = [float(y) for y in families[t % len(families)]()]
+        ex = _edge_exact(r, v, 1e-6)
+        got = oracle.weno_r(r, np.array(v))
+        worst = max(worst, abs(got - ex) / abs(ex))
+        worst_plain = max(worst_plain, abs(_edge_plain(r, v, 1e-6) - ex) / abs(ex))
+    assert worst <= 1e-12, worst
+    if r == 9:
+        assert worst_plain > 1e-10, worst_plain
