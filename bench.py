@@ -291,6 +291,7 @@ def bench_elasticity(members, steps, fp64_sample):
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         b = claw.Batch(specs, "fp32", stream=stream.cuda_stream)
+        shape = b.tune()  # how warps take work, timed on the bound members
         b.advance(3)
     stream.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -301,7 +302,8 @@ def bench_elasticity(members, steps, fp64_sample):
     stream.synchronize()
     ms = e0.elapsed_time(e1)
     out = {"members": members, "cells": cells, "steps": steps,
-           "fp32_batched": cells * steps / (ms * 1e-3), "fp32_ms_per_step": ms / steps}
+           "fp32_batched": cells * steps / (ms * 1e-3), "fp32_ms_per_step": ms / steps,
+           "work_mode": {1: "whole tiles", 2: "single units"}.get(shape[1], "automatic")}
     b.close()
     # FP64, one grid at a time (each member its own solver and launches)
     sample = specs[:fp64_sample]
@@ -329,11 +331,14 @@ def bench_elasticity(members, steps, fp64_sample):
     return out
 
 
-def bench_serving(nreq, prec, rate=200.0, budget=120 << 30, policy="srw", min_cells=1 << 23):
+def bench_serving(nreq, prec, rate=200.0, budget=120 << 30, policy="srw", min_cells=1 << 23,
+                  tune_at=32):
     """Poisson stream of 2D shallow-water solves through the continuous-
     batching server; latency = completion - arrival (server clock).  policy:
     the server's schedule ('srw': shortest remaining work first, min_cells
-    cells per attempt; 'all': every running request in every attempt)."""
+    cells per attempt; 'all': every running request in every attempt).  The
+    server tunes its tile shape once, on the live mix, when tune_at requests
+    are running (0: never)."""
     from paper_1111_6583_gb300 import claw
     from paper_1111_6583_gb300 import workloads as wl
     stream_reqs = wl.serving_stream(nreq, rate)
@@ -345,6 +350,7 @@ def bench_serving(nreq, prec, rate=200.0, budget=120 << 30, policy="srw", min_ce
     nxt = 0
     lat = []
     cell_updates = 0
+    tile = None
     while nxt < nreq or pending:
         now = claw.clock() - t0
         while nxt < nreq and stream_reqs[nxt]["arrival"] <= now:
@@ -352,7 +358,9 @@ def bench_serving(nreq, prec, rate=200.0, budget=120 << 30, policy="srw", min_ce
             pending[tk] = nxt
             nxt += 1
         if pending:
-            sv.pump(8)
+            running, _ = sv.pump(8)
+            if tile is None and tune_at and running >= tune_at:
+                tile = sv.tune()
             for tk in sv.take_done():
                 r = sv.poll(tk, want_state=False)
                 i = pending.pop(tk)
@@ -366,6 +374,7 @@ def bench_serving(nreq, prec, rate=200.0, budget=120 << 30, policy="srw", min_ce
     lat = np.array(lat)
     return {"requests": nreq, "rate_per_s": rate, "prec": prec, "schedule": policy,
             "min_cells": min_cells if policy == "srw" else None,
+            "tile": list(tile) if tile else "fixed 64 x 21 (not tuned)",
             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
             "throughput_cell_updates_per_s": cell_updates / wall, "wall_s": wall}
 

@@ -117,6 +117,8 @@ _SIGS = {
     "claw_sharp_step_noalloc": (ctypes.c_int, [_P(claw_method), _P(claw_grid), _VP, _VP, _VP,
                                                ctypes.c_double, _VP, _P(ctypes.c_double)]),
     "claw_fma_peak": (ctypes.c_int, [ctypes.c_int, _VP, _P(ctypes.c_double)]),
+    "claw_batch_tune": (ctypes.c_int, [_VP, ctypes.c_int, _P(ctypes.c_int), _P(ctypes.c_int)]),
+    "claw_server_tune": (ctypes.c_int, [_VP, ctypes.c_int, _P(ctypes.c_int), _P(ctypes.c_int)]),
     "claw_clock": (ctypes.c_double, []),
     "claw_last_error": (ctypes.c_char_p, [_VP]),
     "claw_version": (ctypes.c_char_p, []),
@@ -360,6 +362,13 @@ class Batch:
     def advance(self, n=1):
         _check(load().claw_batch_advance(self.h, int(n)), self.h)
 
+    def tune(self, bw=None, h=None):
+        """Autotune the fused launch (no arguments) or set it; returns (bw, h)."""
+        b, hh = ctypes.c_int(bw or 0), ctypes.c_int(h or 0)
+        _check(load().claw_batch_tune(self.h, 0 if h is None else 1, ctypes.byref(b),
+                                      ctypes.byref(hh)), self.h)
+        return b.value, hh.value
+
     def info(self):
         infos = (claw_step_info * self.n)()
         _check(load().claw_batch_info(self.h, infos), self.h)
@@ -413,6 +422,14 @@ class Server:
         """'all': every running request steps in every attempt; 'srw':
         shortest remaining work first, min_cells cells per attempt."""
         _check(load().claw_server_schedule(self.h, SCHED[policy], int(min_cells)), self.h)
+
+    def tune(self, bw=None, h=None):
+        """Autotune the fused launch on the running requests (no arguments) or
+        set it; returns (bw, h)."""
+        b, hh = ctypes.c_int(bw or 0), ctypes.c_int(h or 0)
+        _check(load().claw_server_tune(self.h, 0 if h is None else 1, ctypes.byref(b),
+                                       ctypes.byref(hh)), self.h)
+        return b.value, hh.value
 
     def take_done(self, cap=1024):
         """Tickets finished since the last call (oldest first)."""

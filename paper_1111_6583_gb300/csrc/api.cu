@@ -183,6 +183,101 @@ int tiles_of(int scheme, int nd, int prec, int ma, int nx, int ny, int bw, int h
   return nd == 1 ? sharp_tiles(nx, 1, kSharpTX1, 1) : sharp_tiles(nx, ny, kSharpTX2, kSharpTY2);
 }
 
+// Candidate launch shapes of the fused classic step: 2D tile shapes (bw, h)
+// for strips of 60 and 124 columns and a range of chunk heights; 1D work
+// modes (h = kWork1dTiles / kWork1dUnits).  Every candidate gives the same
+// bits; they differ only in speed.
+std::vector<std::pair<int, int>> tile_candidates(int nd, int max_bw) {
+  std::vector<std::pair<int, int>> c;
+  if (nd == 1) {
+    c.push_back({0, kWork1dTiles});
+    c.push_back({0, kWork1dUnits});
+    return c;
+  }
+  for (int bw : {64, 128}) {
+    if (bw > max_bw) continue;
+    for (int h : {8, 12, 16, 21, 24, 32, 41, 48, 64, 96, 128}) c.push_back({bw, h});
+  }
+  return c;
+}
+
+// Time the candidate shapes on a table of members (hm: host copies whose
+// control blocks are the real ones) and return the fastest in bw, h.  The trial attempts run on dry copies of the control
+// blocks, so every t, dt and buffer rotation stays as it was (a trial writes
+// only each member's next work buffer, which the next real attempt
+// rewrites); only the classic step runs, no source step.
+cudaError_t tune_members(const KernelSet& ks, int nd, const claw_method& m,
+                         const std::vector<Member>& hm, const void* consts, cudaStream_t st,
+                         int& bw, int& h) {
+  const int n = (int)hm.size();
+  if (n == 0) return cudaSuccess;
+  DevCtl* dctl = nullptr;
+  Member* dmem = nullptr;
+  Tile* dtiles = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc(&dctl, sizeof(DevCtl) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&dmem, sizeof(Member) * n);
+  // copies of the real control blocks (gathered through the real table)
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dmem, hm.data(), sizeof(Member) * n, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = launch_gather_ctl(dmem, n, dctl, st);
+  if (e == cudaSuccess) e = launch_set_dry_n(dctl, n, 1, st);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  std::vector<Member> tm(hm);
+  for (int k = 0; k < n; ++k) {
+    tm[k].ctl = dctl + k;
+    tm[k].qpre = nullptr;  // trial attempts read Q^n itself
+  }
+  size_t cap = 0;
+  float best = 1e30f;
+  int bb = bw, bh = h;
+  for (const auto& pr : tile_candidates(nd, ks.max_bw)) {
+    if (e != cudaSuccess) break;
+    std::vector<Tile> tt;
+    for (int k = 0; k < n; ++k) {
+      tm[k].ntiles = tiles_of(m.scheme, nd, m.prec, ks.MA, tm[k].nx, tm[k].ny, pr.first,
+                              pr.second);
+      for (int t = 0; t < tm[k].ntiles; ++t) tt.push_back(Tile{k, t});
+    }
+    if (tt.size() > cap) {
+      if (dtiles) cudaFree(dtiles);
+      cap = tt.size();
+      if ((e = cudaMalloc(&dtiles, sizeof(Tile) * cap)) != cudaSuccess) break;
+    }
+    if ((e = cudaMemcpyAsync(dmem, tm.data(), sizeof(Member) * n, cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
+      break;
+    if ((e = cudaMemcpyAsync(dtiles, tt.data(), sizeof(Tile) * tt.size(), cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess)
+      break;
+    LaunchArgs a{dmem, dtiles, (int)tt.size(), consts, pr.first, pr.second, 0, st};
+    a.nmembers = n;
+    if ((e = ks.classic(a)) != cudaSuccess) break;  // warm-up
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 3; ++r) ks.classic(a);
+    cudaEventRecord(e1, st);
+    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;  // tt, tm stay alive till here
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      bb = pr.first;
+      bh = pr.second;
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (dtiles) cudaFree(dtiles);
+  if (dmem) cudaFree(dmem);
+  if (dctl) cudaFree(dctl);
+  if (e != cudaSuccess) return e;
+  if (nd == 2) bw = bb;
+  h = bh;
+  return cudaSuccess;
+}
+
 int maxspeed_tiles(int nx, int ny) {
   const long long n = (long long)nx * ny;
   return (int)((n + kMaxspeedCells - 1) / kMaxspeedCells);
@@ -434,6 +529,16 @@ cudaError_t build_graph(claw_solver* s, int k) {
 // with a dry control block (attempts leave t, dt and the state untouched) and
 // keep the fastest.
 cudaError_t autotune(claw_solver* s) {
+  if (s->m.scheme == CLAW_CLASSIC && s->nd == 1 && !s->faces) {
+    // 1D: how warps take work (whole tiles or single units)
+    int bw = s->bw, h = s->h;
+    cudaError_t e = tune_members(s->ks, 1, s->m, {s->h_mem}, s->consts.data(), s->st, bw, h);
+    if (e != cudaSuccess) return e;
+    s->h = h;
+    s->tuned = 1;
+    drop_graph(s);
+    return cudaSuccess;
+  }
   if (s->m.scheme != CLAW_CLASSIC || s->nd != 2 || s->faces) {
     s->tuned = 1;
     return cudaSuccess;
@@ -697,6 +802,14 @@ claw_status claw_solver_tune(claw_solver* s, int mode, int* bw, int* h) {
     SCK(autotune(s));
     SCK(leave(s));
   } else {
+    if (s->nd == 1 && h && (*h == kWork1dTiles || *h == kWork1dUnits)) {
+      s->h = *h;
+      s->tuned = 1;
+      drop_graph(s);
+      if (bw) *bw = s->bw;
+      SCK(cudaStreamSynchronize(s->st));
+      return CLAW_OK;
+    }
     if (!bw || !h || (*bw != 64 && *bw != 128) || *h < 1 || *bw > s->ks.max_bw)
       return fail(s, "bad tile shape");
     s->bw = *bw;
@@ -1305,6 +1418,54 @@ claw_status claw_batch_evolve(claw_batch* b, int use_graph, int64_t max_steps,
   return worst;
 }
 
+claw_status claw_batch_tune(claw_batch* b, int mode, int* bw, int* h) {
+  if (!b || !b->bound) return bfail(b, "batch not bound");
+  const bool tunable = b->m.scheme == CLAW_CLASSIC && !b->faces && b->nd <= 2;
+  if (tunable) {
+    int nbw = b->bw, nh = b->h;
+    if (mode == 0) {
+      BCK(cudaEventRecord(b->ev_a, b->ustream));
+      BCK(cudaStreamWaitEvent(b->st, b->ev_a, 0));
+      BCK(tune_members(b->ks, b->nd, b->m, b->h_mem, b->consts.data(), b->st, nbw, nh));
+    } else {
+      if (!bw || !h) return bfail(b, "bad tile shape");
+      if (b->nd == 2 && ((*bw != 64 && *bw != 128) || *bw > b->ks.max_bw || *h < 1))
+        return bfail(b, "bad tile shape");
+      if (b->nd == 1 && *h != kWork1dTiles && *h != kWork1dUnits)
+        return bfail(b, "bad 1D work mode (1 whole tiles, 2 single units)");
+      if (b->nd == 2) nbw = *bw;
+      nh = *h;
+    }
+    b->bw = nbw;
+    b->h = nh;
+    // the tile table and the members' tile counts for the new shape
+    b->h_tiles.clear();
+    for (int k = 0; k < b->n; ++k) {
+      Member& mb = b->h_mem[k];
+      mb.ntiles = tiles_of(b->m.scheme, b->nd, b->prec, b->ks.MA, mb.nx, mb.ny, b->bw, b->h);
+      for (int t = 0; t < mb.ntiles; ++t) b->h_tiles.push_back(Tile{k, t});
+    }
+    if ((int)b->h_tiles.size() > b->ntiles) {
+      BCK(cudaStreamSynchronize(b->st));
+      BCK(cudaFree(b->d_tiles));
+      b->d_tiles = nullptr;
+      BCK(cudaMalloc(&b->d_tiles, sizeof(Tile) * b->h_tiles.size()));
+    }
+    b->ntiles = (int)b->h_tiles.size();
+    BCK(cudaMemcpyAsync(b->d_mem, b->h_mem.data(), sizeof(Member) * b->n,
+                        cudaMemcpyHostToDevice, b->st));
+    BCK(cudaMemcpyAsync(b->d_tiles, b->h_tiles.data(), sizeof(Tile) * b->ntiles,
+                        cudaMemcpyHostToDevice, b->st));
+    BCK(cudaStreamSynchronize(b->st));
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+    b->gk = 0;
+  }
+  if (bw) *bw = b->bw;
+  if (h) *h = b->h;
+  return CLAW_OK;
+}
+
 claw_status claw_batch_destroy(claw_batch* b) {
   if (!b) return CLAW_OK;
   if (b->st) cudaStreamSynchronize(b->st);
@@ -1781,6 +1942,42 @@ claw_status claw_server_schedule(claw_server* v, int policy, int64_t min_cells) 
   if (policy == CLAW_SCHED_SRW && min_cells < 1) return sfail(v, "min_cells must be positive");
   v->sched = policy;
   if (policy == CLAW_SCHED_SRW) v->sched_cells = min_cells;
+  return CLAW_OK;
+}
+
+claw_status claw_server_tune(claw_server* v, int mode, int* bw, int* h) {
+  if (!v) return sfail(nullptr, "null server");
+  const bool tunable = v->m.scheme == CLAW_CLASSIC && !v->faces && v->nd <= 2;
+  if (tunable) {
+    int nbw = v->bw, nh = v->h;
+    if (mode == 0) {
+      if (v->running.empty()) return sfail(v, "no running requests to tune on");
+      std::vector<Member> hm;
+      for (uint64_t t : v->running) hm.push_back(v->reqs[t].mem);
+      VCK(cudaStreamSynchronize(v->st));
+      VCK(tune_members(v->ks, v->nd, v->m, hm, v->consts.data(), v->st, nbw, nh));
+    } else {
+      if (!bw || !h) return sfail(v, "bad tile shape");
+      if (v->nd == 2 && ((*bw != 64 && *bw != 128) || *bw > v->ks.max_bw || *h < 1))
+        return sfail(v, "bad tile shape");
+      if (v->nd == 1 && *h != kWork1dTiles && *h != kWork1dUnits)
+        return sfail(v, "bad 1D work mode (1 whole tiles, 2 single units)");
+      if (v->nd == 2) nbw = *bw;
+      nh = *h;
+    }
+    v->bw = nbw;
+    v->h = nh;
+    // running requests take the new shape from their next attempt on
+    for (uint64_t t : v->running) {
+      Req& r = v->reqs[t];
+      r.mem.ntiles = tiles_of(v->m.scheme, v->nd, v->prec, v->ks.MA, r.mem.nx, r.mem.ny, v->bw,
+                              v->h);
+    }
+    v->sel.clear();
+    v->dirty = true;
+  }
+  if (bw) *bw = v->bw;
+  if (h) *h = v->h;
   return CLAW_OK;
 }
 

@@ -126,6 +126,16 @@ cudaError_t launch_set_dry(DevCtl* ctl, int dry, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+__global__ void set_dry_n_kernel(DevCtl* c, int n, int dry) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) c[k].dry = dry;
+}
+cudaError_t launch_set_dry_n(DevCtl* ctls, int n, int dry, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  set_dry_n_kernel<<<(n + 127) / 128, 128, 0, st>>>(ctls, n, dry);
+  return cudaGetLastError();
+}
+
 // Shu-Osher SSP-RK3: Q1 = Q + dt L(Q); Q2 = 3/4 Q + 1/4 (Q1 + dt L(Q1));
 // Q3 = 1/3 Q + 2/3 (Q2 + dt L(Q2)).  Slots: Q^n 0, Q1 1, Q2 2, Q3 1.
 static const StageOp kRK3[3] = {

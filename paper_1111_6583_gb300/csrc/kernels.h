@@ -23,7 +23,8 @@ struct LaunchArgs {
   int ntiles_total;        // work items of this launch
   const void* consts;      // host pointer to MConsts<R>
   int bw;                  // 2D classic: threads per block (strip width + 4)
-  int h;                   // 2D classic: rows per block
+  int h;                   // 2D classic: rows per block; 1D classic: how warps take
+                           // work (kWork1dTiles, kWork1dUnits, else automatic)
   int stage;               // SharpClaw SSP-RK3 stage 0..2 (used when stage_op is null)
   cudaStream_t stream;
   int n3[3];               // 3D: cells per direction
@@ -67,6 +68,9 @@ constexpr int classic1d_T(int prec, int ma) {
 inline int classic1d_tiles(int nx, int prec, int ma) {
   return (nx + classic1d_T(prec, ma) - 1) / classic1d_T(prec, ma);
 }
+// 1D classic work modes (LaunchArgs::h): a warp takes a whole tile, or one
+// unit of it; any other value: whole tiles when they fill every resident warp
+constexpr int kWork1dTiles = 1, kWork1dUnits = 2;
 constexpr int kSharpTX2 = 16, kSharpTY2 = 8;  // 2D SharpClaw tile
 constexpr int kSharpTX1 = 128;                // 1D SharpClaw tile
 constexpr int kMaxspeedCells = 256;           // cells per max-speed block
@@ -128,6 +132,7 @@ cudaError_t launch_totals(const void* q, const void* kappa, int prec, long long 
 cudaError_t launch_reset_cur(DevCtl* ctl, cudaStream_t st);
 cudaError_t launch_gather_ctl(const Member* members, int n, DevCtl* out, cudaStream_t st);
 cudaError_t launch_set_dry(DevCtl* ctl, int dry, cudaStream_t st);
+cudaError_t launch_set_dry_n(DevCtl* ctls, int n, int dry, cudaStream_t st);
 constexpr int kTotalsThreads = 256;
 
 // record the message that claw_last_error returns (api.cu)

@@ -245,7 +245,9 @@ struct Launchers {
       constexpr auto kt = classic1d_kernel<RP, R, kClassic1dThreads, K, NW, FAST>;
       constexpr auto ku = classic1d_kernel<RP, R, kClassic1dThreads, K, 1, FAST>;
       const long long cap = (long long)persistent_grid<kt>(kClassic1dThreads, 1 << 30) * NW;
-      if (a.ntiles_total >= cap)
+      const bool whole =
+          a.h == kWork1dTiles || (a.h != kWork1dUnits && a.ntiles_total >= cap);
+      if (whole)
         kt<<<persistent_grid<kt>(kClassic1dThreads, (a.ntiles_total + NW - 1) / NW),
              kClassic1dThreads, 0, a.stream>>>(a.members, a.tiles, a.ntiles_total, C);
       else
