@@ -176,7 +176,9 @@ __device__ __forceinline__ void limit1d(const MConsts<R>& C, int order,
     R d = R(0), n2 = R(0);
 #pragma unroll
     for (int k = 0; k < M; ++k) {
-      const R up = sc[p] > R(0) ? Wl[p][k] : Wr[p][k];
+      // upwind neighbour: left for a right-going wave
+      const bool right = signed_waves<RP>::value ? p != 0 : sc[p] > R(0);
+      const R up = right ? Wl[p][k] : Wr[p][k];
       d += up * Wc[p][k];
       n2 += Wc[p][k] * Wc[p][k];
     }
@@ -309,7 +311,12 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? (K >= 8 ?
       for (int k = 0; k < K; ++k) {
         if (k < nsp) {
 #pragma unroll
-          for (int p = 0; p < MW; ++p) smax = nanmax(smax, (R)fabs(s[k][p]));
+          for (int p = 0; p < MW; ++p) {
+            // FP32: a non-finite speed makes the results non-finite too, and
+            // the finiteness sum below reports those, so a plain max will do
+            if constexpr (sizeof(R) == 4) smax = fmaxf(smax, fabsf(s[k][p]));
+            else smax = nanmax(smax, (R)fabs(s[k][p]));
+          }
         }
       }
 

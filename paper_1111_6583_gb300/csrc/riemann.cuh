@@ -831,6 +831,8 @@ struct RpElasticity {
     __device__ static constexpr bool f(int, int k) { return k == 0 || k == (ND == 1 ? 1 : 1 + DIR); }
   };
   static constexpr bool FWAVE = true;
+  // s^1 = -c_l < 0 < c_r = s^2 for every state (c = sqrt(K e^(K eps) / rho) > 0)
+  static constexpr bool SIGNED_WAVES = true;
   static constexpr int WALL_X = 1, WALL_Y = (ND == 2) ? 2 : -1;
   template <int DIR>
   __device__ static __forceinline__ void solve(const MConsts<R>&, const R (&ql)[M],
@@ -1162,6 +1164,24 @@ struct incell_solve<RP, decltype((void)RP::INCELL_SOLVE, void())> {
   static constexpr bool value = RP::INCELL_SOLVE;
 };
 
+// solvers of two waves whose first always moves left and second right
+// (RP::SIGNED_WAVES): the upwind side and the sign of each wave are known
+// without looking at the speeds
+template <class RP, class = void>
+struct signed_waves {
+  static constexpr bool value = false;
+};
+template <class RP>
+struct signed_waves<RP, decltype((void)RP::SIGNED_WAVES, void())> {
+  static constexpr bool value = RP::SIGNED_WAVES && RP::MW == 2;
+};
+// sign of wave p's speed: -1, 0 or 1
+template <class RP, typename R>
+__device__ __forceinline__ R wave_sign(int p, R s) {
+  if constexpr (signed_waves<RP>::value) return p == 0 ? R(-1) : R(1);
+  else return s > R(0) ? R(1) : (s < R(0) ? R(-1) : R(0));
+}
+
 // ---------------------------------------------------------------------------
 // wave limiters (LeVeque FVM book, high-resolution methods)
 // ---------------------------------------------------------------------------
@@ -1236,7 +1256,7 @@ __device__ __forceinline__ void correction(const MConsts<R>& C, const R (&W)[RP:
       if (MW >= 3 && !RP::FWAVE) {
         cf = (R(0.5) - hd * a) * a * phi;
       } else {
-        const R sg = RP::FWAVE ? (s[p] > R(0) ? R(1) : (s[p] < R(0) ? R(-1) : R(0))) : a;
+        const R sg = RP::FWAVE ? wave_sign<RP, R>(p, s[p]) : a;
         cf = R(0.5) * sg * (R(1) - dtdn * a) * phi;
       }
 #pragma unroll
@@ -1290,7 +1310,9 @@ __device__ __forceinline__ void correction(const MConsts<R>& C, const R (&W)[RP:
     if (MW >= 3 && !RP::FWAVE) {
       cf = (R(0.5) - hd * a) * a * phi;  // 1/2 |s| (1 - dt/dx |s|) phi
     } else {
-      const R sg = RP::FWAVE ? (gt0(s[p]) ? R(1) : (lt0(s[p]) ? R(-1) : R(0))) : a;
+      const R sg = RP::FWAVE ? (signed_waves<RP>::value ? (p == 0 ? R(-1) : R(1))
+                                                       : (gt0(s[p]) ? R(1) : (lt0(s[p]) ? R(-1) : R(0))))
+                             : a;
       cf = R(0.5) * sg * (R(1) - dtdn * a) * phi;
     }
 #pragma unroll
