@@ -50,6 +50,11 @@ ELAST1D_FLOPS_PER_CELL = 96.0
 SW2D_BYTES_PER_CELL = {"fp64": 48.0, "fp32": 24.0}
 ELAST1D_BYTES_PER_CELL = {"fp64": 48.0, "fp32": 24.0}  # q read+write, aux read
 ACOU1D_BYTES_PER_CELL = {"fp64": 32.0, "fp32": 16.0}   # q read+write
+# ALU peaks from unit counts and clocks (for comparison with the measured FMA
+# rate the roofline uses): 152 SMs x 2.07 GHz x 2 FLOP per FMA x FMA lanes per
+# SM per clock (FP64: 2; FP32: 128)
+FP64_PEAK_DERIVED_TFLOPS = 152 * 2.07e9 * 2 * 2 / 1e12
+FP32_PEAK_DERIVED_TFLOPS = 152 * 2.07e9 * 2 * 128 / 1e12
 
 
 TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "traffic_classic2d_sw_fp64_1024.json")
@@ -973,11 +978,13 @@ def main():
                      "unit": "TFLOP/s", "frac": achieved_tf / fp64_tf,
                      "traffic": recorded_traffic(shape),
                      "peak_kind": "measured in this run: FP64 FMA probe (claw_fma_peak), burst",
+                     "peak_derived": FP64_PEAK_DERIVED_TFLOPS,
                      "flops_per_cell": SW2D_FLOPS_PER_CELL,
                      "hbm_gbs": hbm_gbs, "hbm_frac": hbm_gbs / hbm, "hbm_peak": hbm,
                      "hbm_peak_kind": hbm_kind},
         "peaks": {"fp64_fma_tflops": fp64_tf, "fp32_fma_tflops": fp32_tf, "hbm_gbs": hbm,
-                  "hbm_kind": hbm_kind},
+                  "hbm_kind": hbm_kind, "fp64_derived_tflops": FP64_PEAK_DERIVED_TFLOPS,
+                  "fp32_derived_tflops": FP32_PEAK_DERIVED_TFLOPS},
         "clocks": clk.summary(),
     }
     if rank == 0 and not args.no_extras:
