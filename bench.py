@@ -946,9 +946,14 @@ def main():
     rank, world, local = dist_setup(args.gpus)
     torch.cuda.set_device(local)
     hbm, hbm_kind = peaks()
-    # measured ALU denominators (FMA probes, before the timed region)
+    # measured ALU denominators (FMA probes, before the timed region) and the
+    # device's SM count and L2 size
     fp64_tf = claw.fma_peak("fp64")
     fp32_tf = claw.fma_peak("fp32")
+    props = torch.cuda.get_device_properties(local)
+    device = {"name": props.name, "sms": props.multi_processor_count,
+              "l2_bytes": getattr(props, "L2_cache_size", None),
+              "hbm_bytes": props.total_memory}
 
     barrier(world)
     torch.cuda.synchronize()
@@ -985,6 +990,7 @@ def main():
         "peaks": {"fp64_fma_tflops": fp64_tf, "fp32_fma_tflops": fp32_tf, "hbm_gbs": hbm,
                   "hbm_kind": hbm_kind, "fp64_derived_tflops": FP64_PEAK_DERIVED_TFLOPS,
                   "fp32_derived_tflops": FP32_PEAK_DERIVED_TFLOPS},
+        "device": device,
         "clocks": clk.summary(),
     }
     if rank == 0 and not args.no_extras:

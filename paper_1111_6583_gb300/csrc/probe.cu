@@ -15,11 +15,14 @@ constexpr int kThreads = 256;
 
 // Each thread runs kChains independent chains a <- a * b + c for `iters`
 // rounds: 2 kChains iters FLOPs per thread.  With b = 1 - 2^-20 and a small c
-// the values stay bounded; the sum is stored only if it equals a value it
-// cannot take, which keeps every chain live without a store per thread.
+// the values stay positive and bounded; the sum is stored (to a device
+// variable of this file) only if it equals a value it cannot take, which
+// keeps every chain live without a store per thread.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) fma_probe_kernel(T* __restrict__ sink, int iters,
-                                                             T b, T c) {
+__device__ T g_probe_sink;
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) fma_probe_kernel(int iters, T b, T c) {
   T a[kChains];
 #pragma unroll
   for (int k = 0; k < kChains; ++k) a[k] = T(threadIdx.x) * T(1e-3) + T(k);
@@ -30,7 +33,7 @@ __global__ void __launch_bounds__(kThreads) fma_probe_kernel(T* __restrict__ sin
   T s = T(0);
 #pragma unroll
   for (int k = 0; k < kChains; ++k) s += a[k];
-  if (s == T(-1234.5)) sink[blockIdx.x] = s;
+  if (s == T(-1234.5)) g_probe_sink<T> = s;
 }
 
 template <typename T>
@@ -42,7 +45,6 @@ cudaError_t run_probe(cudaStream_t st, int iters, double* tflops) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fma_probe_kernel<T>, kThreads, 0);
   if (e != cudaSuccess) return e;
   const int blocks = sms * (per_sm > 0 ? per_sm : 1);
-  T* sink = nullptr;  // never written (see the kernel)
   cudaEvent_t a, b;
   if ((e = cudaEventCreate(&a)) != cudaSuccess) return e;
   if ((e = cudaEventCreate(&b)) != cudaSuccess) {
@@ -53,7 +55,7 @@ cudaError_t run_probe(cudaStream_t st, int iters, double* tflops) {
   float best = 0.f;
   for (int rep = 0; rep < 6 && e == cudaSuccess; ++rep) {  // the first run warms up
     cudaEventRecord(a, st);
-    fma_probe_kernel<T><<<blocks, kThreads, 0, st>>>(sink, iters, mul, add);
+    fma_probe_kernel<T><<<blocks, kThreads, 0, st>>>(iters, mul, add);
     cudaEventRecord(b, st);
     e = cudaEventSynchronize(b);
     if (e == cudaSuccess) e = cudaGetLastError();
