@@ -42,11 +42,16 @@ L2_FLUSH_BYTES = 512 << 20
 #   which the kernel takes from the normal solve;
 # - SharpClaw 2D Euler, WENO5 characteristic-wise: one L(Q) evaluation per
 #   stage (three per SSP-RK3 step);
-# - 1D elasticity f-wave classic step.
+# - 1D elasticity f-wave classic step;
+# - 1D acoustics classic step (MC): the oracle's step (95 per cell) less the
+#   medium constants it re-derives at every interface (c = sqrt(K/rho): one
+#   division and one square root; Z = rho c and 2 Z twice: three products),
+#   which the kernel takes as constants.
 # Bytes: one read and one write of the conserved fields (plus aux reads).
 SW2D_FLOPS_PER_CELL = 825.0
 EULER2D_WENO5_FLOPS_PER_CELL_STAGE = 3032.4
 ELAST1D_FLOPS_PER_CELL = 96.0
+ACOU1D_FLOPS_PER_CELL = 90.0
 SW2D_BYTES_PER_CELL = {"fp64": 48.0, "fp32": 24.0}
 ELAST1D_BYTES_PER_CELL = {"fp64": 48.0, "fp32": 24.0}  # q read+write, aux read
 ACOU1D_BYTES_PER_CELL = {"fp64": 32.0, "fp32": 16.0}   # q read+write
@@ -735,7 +740,8 @@ def summary(line):
         "acoustics_1d_2000": {"us_step": g("acoustics_1d", "us_per_step"),
                               "steps_s": g("acoustics_1d", "steps_per_s")},
         "acoustics_1d_2p26": {p: {"ms": g("acoustics_1d_2p26", p, "ms_per_step"),
-                                  "hbm_frac": g("acoustics_1d_2p26", p, "hbm_frac")}
+                                  "hbm_frac": g("acoustics_1d_2p26", p, "hbm_frac"),
+                                  "alu_frac": g("acoustics_1d_2p26", p, "alu_frac")}
                               for p in ("fp64", "fp32")},
         "shock_bubble_2048x1024": {p: {"ms": g("shock_bubble", p, "ms_per_step"),
                                        "alu_frac": g("shock_bubble", p, "alu_frac")}
@@ -839,7 +845,8 @@ def profile_case(case, tile=None):
     psystem -- 1024^2 p-system checkerboard FP64, one SSP(10,4) step (10 stages);
     weno7 -- 1024x512 shock-bubble FP64, WENO7 + SSP(10,4), one step;
     acou3d -- 256^3 constant-medium acoustics FP64, 3 steps (acou3d128: 128^3,
-    small enough for a multi-pass capture; acou3d_f32, acou3d128_f32: FP32)."""
+    small enough for a multi-pass capture; acou3d_f32, acou3d128_f32: FP32);
+    acou1d, acou1d_f32 -- 2^25-cell 1D acoustics, 3 steps (FP64, FP32)."""
     import torch
     from paper_1111_6583_gb300 import claw
     from paper_1111_6583_gb300 import workloads as wl
@@ -880,6 +887,11 @@ def profile_case(case, tile=None):
         sp = wl.acoustics_3d(n=128 if "128" in case else 256)
         s = claw.Solver(sp, "fp32" if case.endswith("f32") else "fp64")
         s.set_t_end(sp["t_end"])
+        s.advance(3)
+    elif case in ("acou1d", "acou1d_f32"):
+        s = claw.Solver(wl.acoustics_1d(n=1 << 25, t_end=1e9),
+                        "fp32" if case.endswith("f32") else "fp64")
+        s.set_t_end(1e9)
         s.advance(3)
     elif case == "vc":
         sp = wl.acoustics_vc_2d(n=1024)
@@ -1019,6 +1031,8 @@ def main():
         for p in ("fp64", "fp32"):
             r = bench_acoustics_1d_hbm(p, 10, 3)
             r["hbm_frac"] = r["hbm_gbs"] / hbm
+            r["alu_frac"] = (ACOU1D_FLOPS_PER_CELL * r["cells"] / (r["ms_per_step"] * 1e-3)
+                             / 1e12 / (fp64_tf if p == "fp64" else fp32_tf))
             a26[p] = r
         ex["acoustics_1d_2p26"] = a26
         sb = {p: bench_shockbubble(p, 5, 3) for p in ("fp64", "fp32")}

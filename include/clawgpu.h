@@ -341,6 +341,18 @@ claw_status claw_sharp_step_noalloc(const claw_method* m, const claw_grid* g, co
  * Not part of the paper's method. */
 claw_status claw_fma_peak(int prec, void* stream, double* tflops);
 
+/* Self-test of the bounded wait on the shared-memory barriers that complete
+ * the bulk asynchronous copies of the staged 1D kernels.  One thread waits
+ * limit_us microseconds (1 .. 1e6) on a barrier that nothing arrives at and
+ * must give up (*gave_up = 1, *waited_us = the time it waited); it then
+ * copies 256 bytes from global to shared memory in bulk, waits for that copy
+ * and compares it word by word (*copied = 1 when it completed and matched).
+ * Runs on stream (cudaStream_t, may be NULL; synchronised).  The kernels
+ * report such a timeout as CLAW_ETIMEOUT on the grid's status.  Not part of
+ * the paper's method. */
+claw_status claw_async_wait_probe(int limit_us, void* stream, int* gave_up, int* copied,
+                                  double* waited_us);
+
 /* Seconds on the server's clock (monotonic). */
 double claw_clock(void);
 

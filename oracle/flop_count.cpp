@@ -16,6 +16,8 @@
 //              of L(Q) (one SSP stage) on an n x n grid of smooth data
 //   elast1d    classic 1D nonlinear elasticity, f-waves, MC: one step on n
 //              cells of a layered medium
+//   acou1d     classic 1D linear acoustics (rho = 1, K = 4), MC: one step on
+//              n periodic cells of smooth data
 // prints one JSON object: operations per cell by kind, the total, and the
 // operations of one Roe-average evaluation (sw2d, euler2d).
 #include <math.h>
@@ -128,7 +130,7 @@ void report(const char* w, long long cells, long long roe) {
 
 int main(int argc, char** argv) {
   if (argc < 3) {
-    fprintf(stderr, "usage: flop_count sw2d|euler2d|elast1d n\n");
+    fprintf(stderr, "usage: flop_count sw2d|euler2d|elast1d|acou1d n\n");
     return 2;
   }
   const char* w = argv[1];
@@ -208,6 +210,21 @@ int main(int argc, char** argv) {
     report(w, n, 0);
     free(q);
     free(aux);
+  } else if (!strcmp(w, "acou1d")) {
+    base(P, 1, n, 1, ORC_RP_ACOUSTICS, 2, 2);
+    P.params[0] = 1.0;
+    P.params[1] = 4.0;
+    CD* q = (CD*)malloc(sizeof(CD) * 2 * n);
+    for (int i = 0; i < n; ++i) {
+      const double x = (i + 0.5) / n;
+      q[i] = 1.0 + 0.5 * std::sin(2 * M_PI * x);
+      q[n + i] = 0.25 * std::cos(2 * M_PI * x);
+    }
+    CD cfl;
+    reset();
+    orc_classic_step(&P, q, nullptr, CD(0.2 / n), &cfl);
+    report(w, n, 0);
+    free(q);
   } else {
     fprintf(stderr, "unknown workload %s\n", w);
     return 2;

@@ -117,6 +117,8 @@ _SIGS = {
     "claw_sharp_step_noalloc": (ctypes.c_int, [_P(claw_method), _P(claw_grid), _VP, _VP, _VP,
                                                ctypes.c_double, _VP, _P(ctypes.c_double)]),
     "claw_fma_peak": (ctypes.c_int, [ctypes.c_int, _VP, _P(ctypes.c_double)]),
+    "claw_async_wait_probe": (ctypes.c_int, [ctypes.c_int, _VP, _P(ctypes.c_int),
+                                             _P(ctypes.c_int), _P(ctypes.c_double)]),
     "claw_batch_tune": (ctypes.c_int, [_VP, ctypes.c_int, _P(ctypes.c_int), _P(ctypes.c_int)]),
     "claw_server_tune": (ctypes.c_int, [_VP, ctypes.c_int, _P(ctypes.c_int), _P(ctypes.c_int)]),
     "claw_clock": (ctypes.c_double, []),
@@ -472,6 +474,17 @@ class Server:
 
 def clock():
     return load().claw_clock()
+
+
+def async_wait_probe(limit_us=20000, stream=None):
+    """Self-test of the bounded barrier wait (claw_async_wait_probe): returns
+    (gave_up, copied, waited_us)."""
+    g, c, w = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
+    st = load().claw_async_wait_probe(int(limit_us), stream, ctypes.byref(g), ctypes.byref(c),
+                                      ctypes.byref(w))
+    if st != CLAW_OK:
+        raise RuntimeError(load().claw_last_error(None).decode())
+    return bool(g.value), bool(c.value), w.value
 
 
 def fma_peak(prec="fp64", stream=None):

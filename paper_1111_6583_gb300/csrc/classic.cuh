@@ -9,6 +9,7 @@
 // block by atomics and a controller launch follows the step kernel.
 #pragma once
 
+#include "async_copy.cuh"
 #include "kernels.h"
 #include "riemann.cuh"
 
@@ -37,6 +38,11 @@ template <typename R, int K>
 struct VecIO;
 template <>
 struct VecIO<float, 4> {
+  // from a 16-byte aligned shared-memory slot
+  __device__ static __forceinline__ void load_shared(const float* p, float (&v)[4]) {
+    const float4 a = *(const float4*)p;
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  }
   __device__ static __forceinline__ void load(const float* p, float (&v)[4]) {
     const float4 a = __ldg((const float4*)p);
     v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
@@ -47,6 +53,12 @@ struct VecIO<float, 4> {
 };
 template <>
 struct VecIO<float, 8> {
+  // from a 16-byte aligned shared-memory slot
+  __device__ static __forceinline__ void load_shared(const float* p, float (&v)[8]) {
+    const float4 a = ((const float4*)p)[0], b = ((const float4*)p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  }
   __device__ static __forceinline__ void load(const float* p, float (&v)[8]) {
     const float4 a = __ldg((const float4*)p), b = __ldg((const float4*)p + 1);
     v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
@@ -59,6 +71,11 @@ struct VecIO<float, 8> {
 };
 template <>
 struct VecIO<double, 2> {
+  // from a 16-byte aligned shared-memory slot
+  __device__ static __forceinline__ void load_shared(const double* p, double (&v)[2]) {
+    const double2 a = *(const double2*)p;
+    v[0] = a.x; v[1] = a.y;
+  }
   __device__ static __forceinline__ void load(const double* p, double (&v)[2]) {
     const double2 a = __ldg((const double2*)p);
     v[0] = a.x; v[1] = a.y;
@@ -69,6 +86,11 @@ struct VecIO<double, 2> {
 };
 template <>
 struct VecIO<double, 4> {
+  // from a 16-byte aligned shared-memory slot
+  __device__ static __forceinline__ void load_shared(const double* p, double (&v)[4]) {
+    const double2 a = ((const double2*)p)[0], b = ((const double2*)p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  }
   __device__ static __forceinline__ void load(const double* p, double (&v)[4]) {
     const double2 a = __ldg((const double2*)p), b = __ldg((const double2*)p + 1);
     v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
@@ -188,9 +210,26 @@ __device__ __forceinline__ void limit1d(const MConsts<R>& C, int order,
   correction<RP, R, 0, LIMC>(C, Wc, sc, dot, nrm, dtdx, F);
 }
 
+// Shared-memory ring of the staged form: per warp S slots, each holding the
+// 32 K cells of every field (and aux field) that one warp unit reads, and one
+// barrier per slot.
+template <typename R, int NW, int S, int NF, int FOOT>
+struct Ring1d {
+  alignas(128) R cell[NW][S][NF][FOOT];
+  alignas(8) unsigned long long bar[NW][S];
+};
+template <typename R, int NW, int NF, int FOOT>
+struct Ring1d<R, NW, 0, NF, FOOT> {};
+
 // FAST: the MC limiter and second order fixed at compile time (the launcher
-// takes it for FP32 methods with those settings)
-template <class RP, typename R, int NT, int K, int SPW, bool FAST = false>
+// takes it for FP32 methods with those settings).
+// S > 0 (staged form): a unit whose 32 K cells lie inside the grid, with
+// 16-byte aligned fields, arrives in shared memory by bulk asynchronous
+// copies (one per field) that the warp's lane 0 issues up to S units ahead,
+// into a ring of S slots; the lanes read their cells from the slot.  Edge
+// units and unaligned fields take the direct loads.  The arithmetic is the
+// same either way, so both forms give the same bits.
+template <class RP, typename R, int NT, int K, int SPW, bool FAST = false, int S = 0>
 __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? (K >= 8 ? 4 : 8) : 1)
     classic1d_kernel(const Member* __restrict__ members, const Tile* __restrict__ tiles,
                      int ntiles_total, const MConsts<R> C) {
@@ -207,6 +246,91 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? (K >= 8 ?
   constexpr int NCR = sizeof(Cell) / sizeof(R);
   static_assert(NCR * sizeof(R) == sizeof(Cell), "Cell holds values of type R only");
   const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;  // warp in block
+
+  // staged form: the ring, and the warp's producer cursor (the consumer's
+  // sequence of units, walked up to S units ahead)
+  constexpr int NF = M + MA;    // fields a unit reads
+  constexpr int FOOT = 32 * K;  // cells of a unit's footprint (lanes 0..31)
+  static_assert(S == 0 || (FOOT * sizeof(R)) % 16 == 0, "bulk copies move multiples of 16 B");
+  __shared__ Ring1d<R, NW, S, NF, FOOT> ring;
+  [[maybe_unused]] unsigned phase = 0u;  // expected parity per slot
+  [[maybe_unused]] unsigned pend = 0u;   // slots with a copy in flight
+  [[maybe_unused]] int j = 0, pj = 0;    // units consumed; units the producer passed
+  // producer cursor: item p_it; its unit starting at cell p_us (valid while
+  // p_us < p_uend, the end of the item's units in the grid); p_q, p_a the
+  // item's input fields, p_q null when they cannot be copied in bulk
+  [[maybe_unused]] int p_it = 0, p_us = 0, p_uend = 0, p_nx = 0;
+  [[maybe_unused]] const R* p_q = nullptr;
+  [[maybe_unused]] const R* p_a = nullptr;
+  // fields that bulk copies may read: 16-byte aligned bases and rows
+  auto stage_ok = [&](const R* qq, const R* aa, int n) {
+    const bool rows16 = ((size_t)n * sizeof(R)) % 16 == 0;
+    return ((size_t)qq & 15) == 0 && (M == 1 || rows16) &&
+           (MA == 0 || (((size_t)aa & 15) == 0 && (MA == 1 || rows16)));
+  };
+  // a unit whose whole footprint [ustart - K, ustart + 31 K) lies in the grid
+  auto stage_unit = [&](int ustart, int n) { return ustart >= K && ustart + 31 * K <= n; };
+  // move the producer cursor to the next item with a unit in the grid
+  auto p_next_item = [&]() {
+    for (;;) {
+      p_it += gridDim.x * NW;
+      if (p_it >= ntiles_total * (NW / SPW)) {
+        p_us = p_uend = 0;
+        return;
+      }
+      const Tile tl = tiles ? tiles[p_it / (NW / SPW)] : Tile{0, p_it / (NW / SPW)};
+      const Member& mb = members[tl.member];
+      const DevCtl* pc = mb.ctl;
+      if (pc->done) continue;
+      p_nx = mb.nx;
+      p_us = tl.tile * T + (p_it % (NW / SPW)) * SPW * WC;
+      p_uend = min(p_nx, p_us + SPW * WC);
+      if (p_us >= p_uend) continue;
+      p_q = (const R*)mb.q[pc->cur];
+      p_a = (const R*)mb.aux;
+      if (!stage_ok(p_q, p_a, p_nx)) p_q = nullptr;
+      return;
+    }
+  };
+  // the producer's unit into slot pj % S (lane 0 issues), then the next one.
+  // The slot was last read at the start of unit pj - S, whose cell values
+  // every lane has since used in arithmetic and passed through full-warp
+  // shuffles, so those reads are complete before lane 0 refills the slot.
+  auto p_issue = [&]() {
+    if constexpr (S > 0) {
+      const int slot = pj % S;
+      if (p_q && stage_unit(p_us, p_nx)) {
+        if (lane == 0) {
+          const unsigned bar = smem_u32(&ring.bar[wib][slot]);
+          constexpr unsigned fb = FOOT * sizeof(R);
+          mbar_arrive_expect_tx(bar, NF * fb);
+#pragma unroll
+          for (int f = 0; f < M; ++f)
+            bulk_g2s(smem_u32(&ring.cell[wib][slot][f][0]), p_q + (size_t)f * p_nx + p_us - K,
+                     fb, bar);
+#pragma unroll
+          for (int f = 0; f < MA; ++f)
+            bulk_g2s(smem_u32(&ring.cell[wib][slot][M + f][0]),
+                     p_a + (size_t)f * p_nx + p_us - K, fb, bar);
+        }
+        pend |= 1u << slot;
+      }
+      ++pj;
+      p_us += WC;
+      if (p_us >= p_uend) p_next_item();
+    }
+  };
+  if constexpr (S > 0) {
+    if (lane == 0) {
+#pragma unroll
+      for (int sl = 0; sl < S; ++sl) mbar_init(smem_u32(&ring.bar[wib][sl]), 1u);
+      fence_mbar_init();
+    }
+    __syncwarp();
+    p_it = blockIdx.x * NW + wib - gridDim.x * NW;
+    p_next_item();
+  }
 
   // A warp takes a work item: SPW consecutive units of one tile (SPW = NW,
   // or 1 when the tiles are too few to give every resident warp an item).  It
@@ -238,6 +362,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? (K >= 8 ?
     const bool rows16 = ((size_t)nx * sizeof(R)) % 16 == 0;  // every field 16-B aligned
     const bool q_ok = ((((size_t)q) | ((size_t)qo)) & 15) == 0 && (M == 1 || rows16);
     const bool a_ok = MA == 0 || ((((size_t)aux) & 15) == 0 && (MA == 1 || rows16));
+    [[maybe_unused]] const bool s_ok = S > 0 && stage_ok(q, aux, nx);  // as p_q != null
     R smax = R(0);
     int bad = 0;
     float nf = 0.f;  // FP32: sum of result * 0
@@ -247,7 +372,11 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? (K >= 8 ?
 
       // lane l holds cells g0 .. g0+K-1; lanes 0 and 31 are the unit's halo
       const int g0 = ustart + (lane - 1) * K;
-      if (sub + 1 < sub0 + spw) {
+      if constexpr (S > 0) {
+        // keep the producer S units ahead (the slot it refills was read by
+        // the previous unit)
+        while (p_us < p_uend && pj < j + S) p_issue();
+      } else if (sub + 1 < sub0 + spw) {
         // L1 prefetch of this lane's cells of the next unit
         const int gn = g0 + WC;
         if (gn >= 0 && gn < nx) {
@@ -261,7 +390,42 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? (K >= 8 ?
       const bool vec = inside && q_ok && a_ok;
       R qa[K][M];
       R aa[K][MAS];
-      if (vec) {
+      bool staged = false;
+      if constexpr (S > 0) staged = s_ok && stage_unit(ustart, nx);
+      if (staged) {
+        if constexpr (S > 0) {
+          const int slot = j % S;
+          const unsigned bit = 1u << slot;
+          bool got = mbar_wait_bounded(smem_u32(&ring.bar[wib][slot]), (phase & bit) ? 1u : 0u);
+          got = __all_sync(FULL, got);
+          if (!got) {
+            // a copy that did not complete in time: report it, wait (bounded)
+            // for the copies still in flight, and leave
+            if (lane == 0) atomicOr(&ctl->bad, 2u);
+#pragma unroll
+            for (int sl = 0; sl < S; ++sl)
+              if ((pend >> sl) & 1u)
+                mbar_wait_bounded(smem_u32(&ring.bar[wib][sl]), (phase >> sl) & 1u);
+            return;
+          }
+          phase ^= bit;
+          pend &= ~bit;
+#pragma unroll
+          for (int k = 0; k < M; ++k) {
+            R v[K];
+            VecIO<R, K>::load_shared(&ring.cell[wib][slot][k][lane * K], v);
+#pragma unroll
+            for (int c = 0; c < K; ++c) qa[c][k] = v[c];
+          }
+#pragma unroll
+          for (int k = 0; k < MA; ++k) {
+            R v[K];
+            VecIO<R, K>::load_shared(&ring.cell[wib][slot][M + k][lane * K], v);
+#pragma unroll
+            for (int c = 0; c < K; ++c) aa[c][k] = v[c];
+          }
+        }
+      } else if (vec) {
 #pragma unroll
         for (int k = 0; k < M; ++k) {
           R v[K];
@@ -385,6 +549,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? (K >= 8 ?
           }
         }
       }
+      if constexpr (S > 0) ++j;
     }  // units of the item
     if constexpr (sizeof(R) == 4) bad |= !isfinite(nf);
     // per-warp atomics; the controllers run in the next launch

@@ -43,7 +43,8 @@ struct DevCtl {
   int ndim;
   int dry;          // timing runs: attempts leave t, dt and cur unchanged
   unsigned int arrive;  // blocks finished in the current attempt
-  unsigned int bad;     // non-finite value seen in the current attempt
+  unsigned int bad;     // bit 1: non-finite value seen in the current attempt;
+                        // bit 2: a bounded wait on an asynchronous copy gave up
 };
 
 // One grid of a launch.  Single solves use a table of one member.
@@ -259,7 +260,8 @@ static __device__ __noinline__ void run_controller(DevCtl* c) {
   }
   c->accepted = 0;
   if (bad || isnan(nu)) {
-    c->status = CLAW_ENONPHYSICAL;
+    // bit 1: a non-finite value; bit 2: a bounded wait gave up
+    c->status = (bad & 2u) ? CLAW_ETIMEOUT : CLAW_ENONPHYSICAL;
     c->done = 1;
   } else if (!c->forced && nu > c->cfl_max) {
     c->rejects += 1;

@@ -61,6 +61,14 @@ constexpr int kClassic1dThreads = 128;
 // field: 2^26-cell acoustics 0.42 -> 0.28 ms) and 4 for solvers that read
 // aux fields (the elasticity ensemble is faster with 4: 0.59 vs 0.76 ms)
 constexpr int classic1d_K(int prec, int ma) { return prec == 0 ? 2 : (ma == 0 ? 8 : 4); }
+// staged form: slots of the shared-memory ring per warp through which bulk
+// asynchronous copies deliver the units (0: direct loads).  FP32 solvers of
+// one or two fields without aux fields (the streaming-bound ones); FP64,
+// bound by the FP64 pipe, and the heavier solvers, bound by instruction
+// issue, keep the direct loads.
+constexpr int classic1d_S(int prec, int m, int ma) {
+  return prec == 1 && ma == 0 && m <= 2 ? 3 : 0;
+}
 // a warp writes the cells of its lanes 1..30 (lanes 0 and 31 hold its halo)
 constexpr int classic1d_T(int prec, int ma) {
   return kClassic1dThreads / 32 * 30 * classic1d_K(prec, ma);

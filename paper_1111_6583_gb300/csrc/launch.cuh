@@ -242,8 +242,9 @@ struct Launchers {
       // a warp takes a whole tile when the tiles fill every resident warp
       // (blocks x NW), else a single unit
       constexpr int NW = kClassic1dThreads / 32;
-      constexpr auto kt = classic1d_kernel<RP, R, kClassic1dThreads, K, NW, FAST>;
-      constexpr auto ku = classic1d_kernel<RP, R, kClassic1dThreads, K, 1, FAST>;
+      constexpr int S = classic1d_S(sizeof(R) == 8 ? 0 : 1, RP::M, RP::MA);
+      constexpr auto kt = classic1d_kernel<RP, R, kClassic1dThreads, K, NW, FAST, S>;
+      constexpr auto ku = classic1d_kernel<RP, R, kClassic1dThreads, K, 1, FAST, S>;
       const long long cap = (long long)persistent_grid<kt>(kClassic1dThreads, 1 << 30) * NW;
       const bool whole =
           a.h == kWork1dTiles || (a.h != kWork1dUnits && a.ntiles_total >= cap);

@@ -1,10 +1,13 @@
 // probe.cu -- FMA throughput probe: the measured denominator of the ALU
 // rooflines that the benchmark reports for the FP64-bound kernels (and the
-// FP32 forms).  Not part of the method.
+// FP32 forms); and a self-test of the bulk-copy barrier wait that the staged
+// 1D kernels use (a copy that completes, a wait that must give up).  Not part
+// of the method.
 #include <cuda_runtime.h>
 
 #include <string>
 
+#include "async_copy.cuh"
 #include "clawgpu.h"
 #include "kernels.h"
 
@@ -71,7 +74,71 @@ cudaError_t run_probe(cudaStream_t st, int iters, double* tflops) {
   return cudaSuccess;
 }
 
+// --- bounded barrier waits ------------------------------------------------
+constexpr int kProbeWords = 64;  // 256 bytes
+__device__ __align__(16) unsigned g_copy_src[kProbeWords];
+__device__ unsigned g_copy_dst[kProbeWords];
+__device__ unsigned long long g_wait_out[3];  // gave up, copied, ns waited
+
+__device__ __forceinline__ unsigned probe_word(int i) { return 2654435761u * (unsigned)(i + 1); }
+
+__global__ void copy_src_fill_kernel() {
+  if (threadIdx.x < kProbeWords) g_copy_src[threadIdx.x] = probe_word(threadIdx.x);
+}
+
+// one thread: (1) a barrier that nothing arrives at, waited on for limit_ns:
+// the wait must give up; (2) a 256-byte bulk copy into shared memory that
+// completes on a second barrier, compared word by word
+__global__ void wait_probe_kernel(unsigned long long limit_ns) {
+  __shared__ __align__(16) unsigned buf[kProbeWords];
+  __shared__ __align__(8) unsigned long long bars[2];
+  const unsigned b0 = claw::smem_u32(&bars[0]), b1 = claw::smem_u32(&bars[1]);
+  claw::mbar_init(b0, 1u);
+  claw::mbar_init(b1, 1u);
+  claw::fence_mbar_init();
+  const unsigned long long t0 = claw::global_ns();
+  const bool got0 = claw::mbar_wait_bounded(b0, 0u, limit_ns);
+  const unsigned long long waited = claw::global_ns() - t0;
+  claw::fence_proxy_async_smem();
+  claw::mbar_arrive_expect_tx(b1, sizeof(buf));
+  claw::bulk_g2s(claw::smem_u32(buf), g_copy_src, sizeof(buf), b1);
+  bool same = claw::mbar_wait_bounded(b1, 0u);
+  if (same) {
+    for (int i = 0; i < kProbeWords; ++i) {
+      g_copy_dst[i] = buf[i];
+      same = same && buf[i] == probe_word(i);
+    }
+  }
+  g_wait_out[0] = got0 ? 0ull : 1ull;
+  g_wait_out[1] = same ? 1ull : 0ull;
+  g_wait_out[2] = waited;
+}
+
 }  // namespace
+
+extern "C" claw_status claw_async_wait_probe(int limit_us, void* stream, int* gave_up,
+                                             int* copied, double* waited_us) {
+  if (!gave_up || !copied || !waited_us || limit_us < 1 || limit_us > 1000000) {
+    claw::set_last_error("claw_async_wait_probe: limit_us in 1..1e6 and non-null outputs");
+    return CLAW_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned long long out[3] = {0ull, 0ull, 0ull};
+  copy_src_fill_kernel<<<1, kProbeWords, 0, st>>>();
+  wait_probe_kernel<<<1, 1, 0, st>>>((unsigned long long)limit_us * 1000ull);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyFromSymbolAsync(out, g_wait_out, sizeof(out), 0,
+                                                      cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    claw::set_last_error((std::string("claw_async_wait_probe: ") + cudaGetErrorString(e)).c_str());
+    return CLAW_ECUDA;
+  }
+  *gave_up = (int)out[0];
+  *copied = (int)out[1];
+  *waited_us = (double)out[2] * 1e-3;
+  return CLAW_OK;
+}
 
 extern "C" claw_status claw_fma_peak(int prec, void* stream, double* tflops) {
   if (!tflops || (prec != CLAW_FP64 && prec != CLAW_FP32)) {

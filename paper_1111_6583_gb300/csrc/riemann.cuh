@@ -194,6 +194,8 @@ struct RpAcoustics {
     __device__ static constexpr bool f(int, int k) { return k == 0 || k == 1 + DIR; }
   };
   static constexpr bool FWAVE = false;
+  // speeds -c < 0 < c (rho, K > 0 are checked on the host)
+  static constexpr bool SIGNED_WAVES = true;
   static constexpr int WALL_X = 1, WALL_Y = (ND == 2) ? 2 : -1;
   template <int DIR>
   __device__ static __forceinline__ void solve(const MConsts<R>& C, const R (&ql)[M],

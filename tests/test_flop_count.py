@@ -9,6 +9,9 @@ counting number type), so the ALU roofline numerators are reproducible.
 * SharpClaw 2D Euler, WENO5 characteristic-wise: one L(Q) evaluation (one SSP
   stage), the in-cell Riemann problems included.
 * Classic 1D elasticity (f-waves): one step.
+* Classic 1D acoustics: one step, less the medium constants the oracle
+  re-derives at every interface (c = sqrt(K/rho): a division and a square
+  root; Z = rho c and 2 Z, twice: three products).
 """
 import json
 import os
@@ -51,6 +54,12 @@ def test_elasticity1d_flops_per_cell(counter):
     r = counter("elast1d", 1000000)
     assert abs(r["total"] - bench.ELAST1D_FLOPS_PER_CELL) < 0.01, r
     assert abs(r["transcendental"] - 2.0) < 1e-3  # one exp per cell side prepared twice
+
+
+def test_acoustics1d_flops_per_cell(counter):
+    r = counter("acou1d", 1000000)
+    assert abs(r["sqrt"] - 1.0) < 1e-4 and abs(r["div"] - 7.0) < 1e-4, r
+    assert abs(r["total"] - 5.0 - bench.ACOU1D_FLOPS_PER_CELL) < 0.01, r
 
 
 def test_counting_type_counts_what_it_should(counter):
