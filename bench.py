@@ -390,9 +390,10 @@ def bench_serving(nreq, prec, rate=200.0, budget=120 << 30, policy="srw", min_ce
 
 
 def bench_shockbubble(prec, steps, warmup, nx=2048, ny=1024, weno_order=5,
-                      integrator="ssp_rk3"):
+                      integrator="ssp_rk3", tile=None):
     """2D Euler shock-bubble, SharpClaw WENO-char: one step = three fused
-    stage launches (SSP-RK3, CFL 0.8) or ten (SSP(10,4), CFL 2.0)."""
+    stage launches (SSP-RK3, CFL 0.8) or ten (SSP(10,4), CFL 2.0).  The
+    stage tile is the autotuner's pick (WENO5), or `tile` when given."""
     import torch
     from paper_1111_6583_gb300 import claw
     from paper_1111_6583_gb300 import workloads as wl
@@ -404,6 +405,7 @@ def bench_shockbubble(prec, steps, warmup, nx=2048, ny=1024, weno_order=5,
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         s = claw.Solver(spec, prec, stream=stream.cuda_stream)
+        shape = s.tune(*tile) if tile else s.tune()
         s.set_t_end(0.2)
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
         s.advance(warmup)
@@ -412,6 +414,7 @@ def bench_shockbubble(prec, steps, warmup, nx=2048, ny=1024, weno_order=5,
     s.close()
     avg = sum(ms) / len(ms)
     return {"value": nx * ny * len(ms) / (sum(ms) * 1e-3), "unit": UNIT, "ms_per_step": avg,
+            "tile": list(shape),
             "workload": "2D Euler shock-bubble %dx%d, SharpClaw WENO%d-char + %s, %s"
                         % (nx, ny, weno_order,
                            "SSP-RK3" if integrator == "ssp_rk3" else "SSP(10,4)",

@@ -168,13 +168,16 @@ claw_status claw_bind_state(claw_solver* s, void* q_dev, const void* aux_dev, do
  * claw_sync_state to have it in q_dev. */
 claw_status claw_step(claw_solver* s, double dt, claw_step_info* info);
 
-/* Launch shape of the classic step: mode 0 runs the autotuner (times the
- * candidate shapes on the bound state without changing it) and returns the
- * choice in *bw, *h; mode 1 sets them.  2D: *bw (64 or 128 threads = strip
- * width + 4) and *h (rows per block).  1D: *h is how warps take work
- * (1: a whole tile of 4 warp units, 2: one unit; *bw is ignored).  Every
- * shape gives the same result bit for bit.  Other schemes/dimensions ignore
- * the shape. */
+/* Launch shape of the step: mode 0 runs the autotuner (times the candidate
+ * shapes on the bound state without changing it) and returns the choice in
+ * *bw, *h; mode 1 sets them (CLAW_EINVAL for a shape the method does not
+ * have).  Classic 2D: *bw (64 or 128 threads = strip width + 4) and *h (rows
+ * per block).  Classic 1D: *h is how warps take work (1: a whole tile of 4
+ * warp units, 2: one unit; *bw is ignored).  SharpClaw 2D: the tile of cells
+ * a block reconstructs, *bw x *h = 16 x 8, 32 x 4, 32 x 8 or 16 x 16 with
+ * fifth-order WENO (timed on the first stage), 16 x 8 with the higher
+ * orders; SharpClaw 1D: 128 x 1.  Every shape gives the same result bit for
+ * bit.  3D grids and the per-face classic path ignore the shape. */
 claw_status claw_solver_tune(claw_solver* s, int mode, int* bw, int* h);
 
 /* Enqueue n controller step attempts on the stream without synchronising
@@ -235,11 +238,11 @@ claw_status claw_batch_evolve(claw_batch* b, int use_graph, int64_t max_steps,
 /* Enqueue n fused step attempts for all unfinished members (no sync). */
 claw_status claw_batch_advance(claw_batch* b, int n);
 claw_status claw_batch_info(claw_batch* b, claw_step_info* info);
-/* Launch shape of the batch's fused classic step, as claw_solver_tune: mode 0
- * times the candidates on all bound members at once (dry attempts: no
- * member's state, t or dt changes) and keeps the fastest; mode 1 sets *bw,
- * *h.  Results do not depend on the shape.  Call after claw_batch_bind;
- * SharpClaw, per-face and 3D batches keep their fixed launches. */
+/* Launch shape of the batch's fused step (classic or SharpClaw), as
+ * claw_solver_tune: mode 0 times the candidates on all bound members at once
+ * (dry attempts: no member's state, t or dt changes) and keeps the fastest;
+ * mode 1 sets *bw, *h.  Results do not depend on the shape.  Call after
+ * claw_batch_bind; per-face and 3D batches keep their fixed launches. */
 claw_status claw_batch_tune(claw_batch* b, int mode, int* bw, int* h);
 claw_status claw_batch_sync_state(claw_batch* b);
 claw_status claw_batch_destroy(claw_batch* b);
@@ -289,7 +292,7 @@ claw_status claw_server_pump(claw_server* sv, int steps, int* running, int* queu
  * min_cells cells.  The schedule changes only when a request advances, never
  * its arithmetic: each result is the same under either policy. */
 claw_status claw_server_schedule(claw_server* sv, int policy, int64_t min_cells);
-/* Launch shape of the server's fused classic step, as claw_batch_tune: mode 0
+/* Launch shape of the server's fused step, as claw_batch_tune: mode 0
  * times the candidates on the requests running now (the live mix; dry
  * attempts change none of them; CLAW_EINVAL when none is running), mode 1
  * sets *bw, *h.  Running requests take the shape from their next attempt;

@@ -180,15 +180,38 @@ const char* check_grid(const claw_grid& g, const claw_method& m) {
 int tiles_of(int scheme, int nd, int prec, int ma, int nx, int ny, int bw, int h) {
   if (scheme == CLAW_CLASSIC)
     return nd == 1 ? classic1d_tiles(nx, prec, ma) : classic2d_tiles(nx, ny, bw, h);
-  return nd == 1 ? sharp_tiles(nx, 1, kSharpTX1, 1) : sharp_tiles(nx, ny, kSharpTX2, kSharpTY2);
+  if (nd == 1) return sharp_tiles(nx, 1, kSharpTX1, 1);
+  int tx, ty;
+  sharp2d_shape(bw, h, tx, ty);
+  return sharp_tiles(nx, ny, tx, ty);
 }
 
-// Candidate launch shapes of the fused classic step: 2D tile shapes (bw, h)
-// for strips of 60 and 124 columns and a range of chunk heights; 1D work
-// modes (h = kWork1dTiles / kWork1dUnits).  Every candidate gives the same
+// The launch shape a scheme starts with: the 2D SharpClaw default tile, or
+// the classic defaults (bw, h) the caller holds.
+void default_shape(const claw_method& m, int nd, int& bw, int& h) {
+  if (m.scheme != CLAW_SHARPCLAW) return;
+  bw = nd == 1 ? kSharpTX1 : kSharpTX2;
+  h = nd == 1 ? 1 : kSharpTY2;
+}
+
+// Candidate launch shapes of the fused step: classic 2D tile shapes (bw, h)
+// for strips of 60 and 124 columns and a range of chunk heights; classic 1D
+// work modes (h = kWork1dTiles / kWork1dUnits); the 2D SharpClaw tiles of
+// the fifth-order stage (kSharpShapes2).  Every candidate gives the same
 // bits; they differ only in speed.
-std::vector<std::pair<int, int>> tile_candidates(int nd, int max_bw) {
+std::vector<std::pair<int, int>> tile_candidates(const KernelSet& ks, const claw_method& m,
+                                                 int nd) {
   std::vector<std::pair<int, int>> c;
+  const int max_bw = ks.max_bw;
+  if (m.scheme == CLAW_SHARPCLAW) {
+    if (nd == 2 && m.weno_order == 5) {
+      for (int i = 0; i < 4; ++i)
+        if (i == 0 || ((ks.sharp_shapes >> i) & 1))
+          c.push_back({kSharpShapes2[i][0], kSharpShapes2[i][1]});
+    } else
+      c.push_back(nd == 1 ? std::make_pair(kSharpTX1, 1) : std::make_pair(kSharpTX2, kSharpTY2));
+    return c;
+  }
   if (nd == 1) {
     c.push_back({0, kWork1dTiles});
     c.push_back({0, kWork1dUnits});
@@ -199,6 +222,34 @@ std::vector<std::pair<int, int>> tile_candidates(int nd, int max_bw) {
     for (int h : {8, 12, 16, 21, 24, 32, 41, 48, 64, 96, 128}) c.push_back({bw, h});
   }
   return c;
+}
+
+// Why a launch shape set by hand cannot be taken (null when it can).
+const char* bad_shape(const KernelSet& ks, const claw_method& m, int nd, int bw, int h) {
+  const int max_bw = ks.max_bw;
+  if (m.scheme == CLAW_SHARPCLAW) {
+    for (const auto& pr : tile_candidates(ks, m, nd))
+      if (pr.first == bw && pr.second == h) return nullptr;
+    return nd == 2 ? "bad SharpClaw tile (WENO5: 16x8, 32x4, 32x8, 16x16; higher orders: 16x8)"
+                   : "the 1D SharpClaw tile is 128 x 1";
+  }
+  if (nd == 1)
+    return h == kWork1dTiles || h == kWork1dUnits
+               ? nullptr
+               : "bad 1D work mode (1 whole tiles, 2 single units)";
+  if ((bw != 64 && bw != 128) || bw > max_bw || h < 1) return "bad tile shape";
+  return nullptr;
+}
+
+// One trial attempt of a tuning candidate: the classic step, or the first
+// stage of the SharpClaw integrator (it writes only a work buffer)
+cudaError_t trial_launch(const KernelSet& ks, const claw_method& m, LaunchArgs a) {
+  if (m.scheme == CLAW_CLASSIC) return ks.classic(a);
+  const StageOp* ops;
+  stage_table(m.time_integrator, &ops);
+  a.stage = 0;
+  a.stage_op = ops;
+  return ks.sharp(a);
 }
 
 // Time the candidate shapes on a table of members (hm: host copies whose
@@ -232,7 +283,7 @@ cudaError_t tune_members(const KernelSet& ks, int nd, const claw_method& m,
   size_t cap = 0;
   float best = 1e30f;
   int bb = bw, bh = h;
-  for (const auto& pr : tile_candidates(nd, ks.max_bw)) {
+  for (const auto& pr : tile_candidates(ks, m, nd)) {
     if (e != cudaSuccess) break;
     std::vector<Tile> tt;
     for (int k = 0; k < n; ++k) {
@@ -253,9 +304,17 @@ cudaError_t tune_members(const KernelSet& ks, int nd, const claw_method& m,
       break;
     LaunchArgs a{dmem, dtiles, (int)tt.size(), consts, pr.first, pr.second, 0, st};
     a.nmembers = n;
-    if ((e = ks.classic(a)) != cudaSuccess) break;  // warm-up
+    if ((e = trial_launch(ks, m, a)) != cudaSuccess) {  // warm-up
+      // a shape this solver does not have, or that the device cannot launch
+      // (configuration errors leave the context usable): skip it
+      if (e != cudaErrorNotSupported && e != cudaErrorInvalidValue &&
+          e != cudaErrorLaunchOutOfResources && e != cudaErrorInvalidConfiguration)
+        break;
+      e = cudaSuccess;
+      continue;
+    }
     cudaEventRecord(e0, st);
-    for (int r = 0; r < 3; ++r) ks.classic(a);
+    for (int r = 0; r < 3; ++r) trial_launch(ks, m, a);
     cudaEventRecord(e1, st);
     if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;  // tt, tm stay alive till here
     float ms = 0.f;
@@ -539,6 +598,19 @@ cudaError_t autotune(claw_solver* s) {
     drop_graph(s);
     return cudaSuccess;
   }
+  if (s->m.scheme == CLAW_SHARPCLAW && s->nd == 2 && s->m.weno_order == 5) {
+    // the SharpClaw tile, timed on the first stage with a dry control block
+    int bw = s->bw, h = s->h;
+    cudaError_t e = tune_members(s->ks, 2, s->m, {s->h_mem}, s->consts.data(), s->st, bw, h);
+    if (e != cudaSuccess) return e;
+    s->bw = bw;
+    s->h = h;
+    s->ntiles = tiles_of(s->m.scheme, 2, s->prec, s->ks.MA, (int)s->g.n[0], (int)s->g.n[1],
+                         bw, h);
+    s->tuned = 1;
+    drop_graph(s);
+    return upload_member(s);
+  }
   if (s->m.scheme != CLAW_CLASSIC || s->nd != 2 || s->faces) {
     s->tuned = 1;
     return cudaSuccess;
@@ -713,6 +785,7 @@ claw_status claw_solver_create(const claw_method* m, const claw_grid* g, void* s
   s->nbuf = nbuf_of(*m);
   s->ks = ks;
   s->bw = std::min(s->bw, ks.max_bw);
+  default_shape(*m, s->nd, s->bw, s->h);
   s->consts = make_consts(*m);
   s->ustream = (cudaStream_t)stream;
   s->sbytes = state_bytes_of(*m, s->g);
@@ -802,7 +875,8 @@ claw_status claw_solver_tune(claw_solver* s, int mode, int* bw, int* h) {
     SCK(autotune(s));
     SCK(leave(s));
   } else {
-    if (s->nd == 1 && h && (*h == kWork1dTiles || *h == kWork1dUnits)) {
+    if (s->m.scheme == CLAW_CLASSIC && s->nd == 1 && h &&
+        (*h == kWork1dTiles || *h == kWork1dUnits)) {
       s->h = *h;
       s->tuned = 1;
       drop_graph(s);
@@ -810,8 +884,8 @@ claw_status claw_solver_tune(claw_solver* s, int mode, int* bw, int* h) {
       SCK(cudaStreamSynchronize(s->st));
       return CLAW_OK;
     }
-    if (!bw || !h || (*bw != 64 && *bw != 128) || *h < 1 || *bw > s->ks.max_bw)
-      return fail(s, "bad tile shape");
+    if (!bw || !h) return fail(s, "bad tile shape");
+    if (const char* why = bad_shape(s->ks, s->m, s->nd, *bw, *h)) return fail(s, why);
     s->bw = *bw;
     s->h = *h;
     if (s->nd != 3 && !s->faces)
@@ -1184,6 +1258,7 @@ claw_status claw_batch_create(const claw_method* m, const claw_grid* grids, int 
   b->ks = ks;
   b->faces = faces;
   b->bw = std::min(b->bw, ks.max_bw);
+  default_shape(*m, nd, b->bw, b->h);
   b->consts = make_consts(*m);
   b->grids.assign(grids, grids + n);
   for (auto& g : b->grids)
@@ -1420,7 +1495,7 @@ claw_status claw_batch_evolve(claw_batch* b, int use_graph, int64_t max_steps,
 
 claw_status claw_batch_tune(claw_batch* b, int mode, int* bw, int* h) {
   if (!b || !b->bound) return bfail(b, "batch not bound");
-  const bool tunable = b->m.scheme == CLAW_CLASSIC && !b->faces && b->nd <= 2;
+  const bool tunable = !b->faces && b->nd <= 2;
   if (tunable) {
     int nbw = b->bw, nh = b->h;
     if (mode == 0) {
@@ -1429,11 +1504,10 @@ claw_status claw_batch_tune(claw_batch* b, int mode, int* bw, int* h) {
       BCK(tune_members(b->ks, b->nd, b->m, b->h_mem, b->consts.data(), b->st, nbw, nh));
     } else {
       if (!bw || !h) return bfail(b, "bad tile shape");
-      if (b->nd == 2 && ((*bw != 64 && *bw != 128) || *bw > b->ks.max_bw || *h < 1))
-        return bfail(b, "bad tile shape");
-      if (b->nd == 1 && *h != kWork1dTiles && *h != kWork1dUnits)
-        return bfail(b, "bad 1D work mode (1 whole tiles, 2 single units)");
-      if (b->nd == 2) nbw = *bw;
+      const int want_bw = (b->m.scheme == CLAW_CLASSIC && b->nd == 1) ? b->bw : *bw;
+      if (const char* why = bad_shape(b->ks, b->m, b->nd, want_bw, *h))
+        return bfail(b, why);
+      nbw = want_bw;
       nh = *h;
     }
     b->bw = nbw;
@@ -1593,6 +1667,7 @@ claw_status claw_server_create_nd(const claw_method* m, int ndim, size_t hbm_bud
   v->ks = ks;
   v->faces = faces;
   v->bw = std::min(v->bw, ks.max_bw);
+  default_shape(*m, nd, v->bw, v->h);
   v->consts = make_consts(*m);
   v->budget = hbm_budget_bytes;
   v->max_slots = max_slots;
@@ -1947,7 +2022,7 @@ claw_status claw_server_schedule(claw_server* v, int policy, int64_t min_cells) 
 
 claw_status claw_server_tune(claw_server* v, int mode, int* bw, int* h) {
   if (!v) return sfail(nullptr, "null server");
-  const bool tunable = v->m.scheme == CLAW_CLASSIC && !v->faces && v->nd <= 2;
+  const bool tunable = !v->faces && v->nd <= 2;
   if (tunable) {
     int nbw = v->bw, nh = v->h;
     if (mode == 0) {
@@ -1958,11 +2033,10 @@ claw_status claw_server_tune(claw_server* v, int mode, int* bw, int* h) {
       VCK(tune_members(v->ks, v->nd, v->m, hm, v->consts.data(), v->st, nbw, nh));
     } else {
       if (!bw || !h) return sfail(v, "bad tile shape");
-      if (v->nd == 2 && ((*bw != 64 && *bw != 128) || *bw > v->ks.max_bw || *h < 1))
-        return sfail(v, "bad tile shape");
-      if (v->nd == 1 && *h != kWork1dTiles && *h != kWork1dUnits)
-        return sfail(v, "bad 1D work mode (1 whole tiles, 2 single units)");
-      if (v->nd == 2) nbw = *bw;
+      const int want_bw = (v->m.scheme == CLAW_CLASSIC && v->nd == 1) ? v->bw : *bw;
+      if (const char* why = bad_shape(v->ks, v->m, v->nd, want_bw, *h))
+        return sfail(v, why);
+      nbw = want_bw;
       nh = *h;
     }
     v->bw = nbw;

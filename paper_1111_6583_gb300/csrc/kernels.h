@@ -52,6 +52,8 @@ struct KernelSet {
   launch_fn maxspeed;      // first-order interface speeds into ctl->smax
   launch_fn source;        // axisymmetric Euler source step (2D Euler systems)
   int max_bw;              // 2D classic: widest block whose static shared memory fits
+  int sharp_shapes;        // 2D SharpClaw WENO5: bit i set when tile kSharpShapes2[i]
+                           // fits in a block's shared memory
 };
 
 // tile geometry shared by the host (tile tables) and the kernels
@@ -79,8 +81,24 @@ inline int classic1d_tiles(int nx, int prec, int ma) {
 // 1D classic work modes (LaunchArgs::h): a warp takes a whole tile, or one
 // unit of it; any other value: whole tiles when they fill every resident warp
 constexpr int kWork1dTiles = 1, kWork1dUnits = 2;
-constexpr int kSharpTX2 = 16, kSharpTY2 = 8;  // 2D SharpClaw tile
+constexpr int kSharpTX2 = 16, kSharpTY2 = 8;  // 2D SharpClaw tile (default)
 constexpr int kSharpTX1 = 128;                // 1D SharpClaw tile
+// shared memory one block may hold on the device (227 KB)
+constexpr size_t kSmemPerBlock = 227 * 1024;
+// 2D SharpClaw tiles (TX, TY) of the fifth-order WENO stage that the
+// autotuner tries; the higher orders keep the default
+constexpr int kSharpShapes2[4][2] = {{16, 8}, {32, 4}, {32, 8}, {16, 16}};
+// the 2D SharpClaw tile that a launch shape (bw, h) names: one of
+// kSharpShapes2, any other pair the default
+inline void sharp2d_shape(int bw, int h, int& tx, int& ty) {
+  tx = kSharpTX2;
+  ty = kSharpTY2;
+  for (const auto& sh : kSharpShapes2)
+    if (sh[0] == bw && sh[1] == h) {
+      tx = bw;
+      ty = h;
+    }
+}
 constexpr int kMaxspeedCells = 256;           // cells per max-speed block
 
 // Tiles of the 2D classic kernel.  A block of BW threads owns a strip of

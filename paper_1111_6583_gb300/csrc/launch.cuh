@@ -297,30 +297,62 @@ struct Launchers {
         stage_table(0, &rk3);
         op = rk3[a.stage];
       }
+      cudaError_t e = cudaErrorInvalidValue;
       switch (C.weno_r) {
         case 0:
-        case 3: sharp_launch<3>(a, C, op); break;
-        case 4: sharp_launch<4>(a, C, op); break;
-        case 5: sharp_launch<5>(a, C, op); break;
-        case 6: sharp_launch<6>(a, C, op); break;
-        case 7: sharp_launch<7>(a, C, op); break;
-        case 8: sharp_launch<8>(a, C, op); break;
-        case 9: sharp_launch<9>(a, C, op); break;
-        default: return cudaErrorInvalidValue;
+        case 3: e = sharp_launch<3>(a, C, op); break;
+        case 4: e = sharp_launch<4>(a, C, op); break;
+        case 5: e = sharp_launch<5>(a, C, op); break;
+        case 6: e = sharp_launch<6>(a, C, op); break;
+        case 7: e = sharp_launch<7>(a, C, op); break;
+        case 8: e = sharp_launch<8>(a, C, op); break;
+        case 9: e = sharp_launch<9>(a, C, op); break;
+        default: break;
       }
+      if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
   }
+  // 2D: the tile that (a.bw, a.h) names (sharp2d_shape); the fifth-order
+  // stage has every shape of kSharpShapes2 whose static shared memory fits a
+  // block, the higher orders the default only (cudaErrorNotSupported
+  // otherwise)
   template <int RW>
-  static void sharp_launch(const LaunchArgs& a, const MConsts<R>& C, const StageOp& op) {
+  static cudaError_t sharp_launch(const LaunchArgs& a, const MConsts<R>& C, const StageOp& op) {
     if constexpr (ND == 1) {
       sharp_stage_kernel<RP, R, 1, kSharpTX1, 1, RW>
           <<<launch_grid(a.ntiles_total), kSharpTX1, 0, a.stream>>>(a.members, a.tiles,
                                                                  a.ntiles_total, C, op);
+      return cudaSuccess;
     } else if constexpr (ND == 2) {
-      sharp_stage_kernel<RP, R, 2, kSharpTX2, kSharpTY2, RW>
-          <<<launch_grid(a.ntiles_total), kSharpTX2 * kSharpTY2, 0, a.stream>>>(
-              a.members, a.tiles, a.ntiles_total, C, op);
+      int tx, ty;
+      sharp2d_shape(a.bw, a.h, tx, ty);
+      if (tx == kSharpTX2 && ty == kSharpTY2) return sharp2d<kSharpTX2, kSharpTY2, RW>(a, C, op);
+      if constexpr (RW == 3) {
+        if (tx == 32 && ty == 4) return sharp2d<32, 4, RW>(a, C, op);
+        if (tx == 32 && ty == 8) return sharp2d<32, 8, RW>(a, C, op);
+        if (tx == 16 && ty == 16) return sharp2d<16, 16, RW>(a, C, op);
+      }
+      return cudaErrorNotSupported;
+    } else {
+      (void)a;
+      (void)C;
+      (void)op;
+      return cudaErrorNotSupported;
+    }
+  }
+  template <int TX, int TY, int RW>
+  static cudaError_t sharp2d(const LaunchArgs& a, const MConsts<R>& C, const StageOp& op) {
+    if constexpr (sharp_smem_bytes<RP, R, 2, TX, TY, RW>() <= kSmemPerBlock) {
+      sharp_stage_kernel<RP, R, 2, TX, TY, RW>
+          <<<launch_grid(a.ntiles_total), TX * TY, 0, a.stream>>>(a.members, a.tiles,
+                                                                 a.ntiles_total, C, op);
+      return cudaSuccess;
+    } else {
+      (void)a;
+      (void)C;
+      (void)op;
+      return cudaErrorNotSupported;
     }
   }
   static cudaError_t source(const LaunchArgs& a) {
@@ -361,6 +393,11 @@ KernelSet make_set(bool has_char) {
   k.maxspeed = &Launchers<RP, R, ND>::maxspeed;
   k.source = &Launchers<RP, R, ND>::source;
   k.max_bw = classic2d_fits<RP, R>(128) ? 128 : 64;
+  constexpr size_t lim = kSmemPerBlock;
+  k.sharp_shapes = (sharp_smem_bytes<RP, R, 2, 16, 8, 3>() <= lim ? 1 : 0) |
+                   (sharp_smem_bytes<RP, R, 2, 32, 4, 3>() <= lim ? 2 : 0) |
+                   (sharp_smem_bytes<RP, R, 2, 32, 8, 3>() <= lim ? 4 : 0) |
+                   (sharp_smem_bytes<RP, R, 2, 16, 16, 3>() <= lim ? 8 : 0);
   return k;
 }
 

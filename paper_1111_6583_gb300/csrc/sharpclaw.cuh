@@ -102,6 +102,19 @@ __device__ __forceinline__ R weno_edge(const R (&w)[NV], R eps) {
   else return weno17<R>(v, eps);
 }
 
+// static shared memory of sharp_stage_kernel (the arrays declared in it)
+template <class RP, typename R, int ND, int TX, int TY, int RW>
+constexpr size_t sharp_smem_bytes() {
+  constexpr int M = RP::M, MA = RP::MA, G = RW;
+  constexpr int MAS = MA > 0 ? MA : 1;
+  constexpr int HX = TX + 2 * G, HY = (ND == 2) ? TY + 2 * G : 1;
+  constexpr int NE = (ND == 2) ? ((TX + 1) * TY > TX * (TY + 1) ? (TX + 1) * TY : TX * (TY + 1))
+                               : TX + 1;
+  return sizeof(R) * ((size_t)M * HY * HX + (size_t)MAS * (MA > 0 ? HY * HX : 1) +
+                      (size_t)HY * HX + 4 * (size_t)M * NE + 3) +
+         3 * sizeof(int);
+}
+
 template <class RP, typename R, int ND, int TX, int TY, int RW>
 __global__ void __launch_bounds__(TX * TY)
     sharp_stage_kernel(const Member* __restrict__ members, const Tile* __restrict__ tiles,

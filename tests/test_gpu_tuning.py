@@ -109,3 +109,71 @@ def test_server_tuned_on_live_mix_bitwise():
         torch.cuda.synchronize()
         assert np.array_equal(s.q.cpu().numpy(), a["q"])
         s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_sharpclaw_2d_tiles_bitwise(prec):
+    """Every SharpClaw 2D tile (WENO5, characteristic-wise Euler) gives the
+    default tile's bits; the autotuner's pick is one of them; shapes the
+    method does not have are refused."""
+    import torch
+    from paper_1111_6583_gb300 import claw
+    spec = wl.shock_bubble_2d(nx=100, ny=52)  # ragged in both directions
+    out, chosen = {}, None
+    for shape in (None, "auto", (32, 4), (32, 8), (16, 16)):
+        s = claw.Solver(spec, prec)
+        if shape == "auto":
+            chosen = s.tune()
+        elif shape:
+            assert tuple(s.tune(*shape)) == shape
+        info = s.evolve(0.02, max_steps=6)
+        torch.cuda.synchronize()
+        out[shape] = (info["steps"], s.q.double().cpu().numpy())
+        s.close()
+    ref = out[None]
+    for shape, (st, q) in out.items():
+        assert st == ref[0], shape
+        assert np.array_equal(q, ref[1]), (shape, chosen)
+    assert tuple(chosen) in ((16, 8), (32, 4), (32, 8), (16, 16))
+    s = claw.Solver(spec, prec)
+    for bad in ((64, 21), (8, 16)):
+        with pytest.raises(RuntimeError):
+            s.tune(*bad)
+    s.close()
+    sp7 = dict(spec, weno_order=7)
+    s = claw.Solver(sp7, prec)
+    with pytest.raises(RuntimeError):
+        s.tune(32, 4)  # higher orders keep the default tile
+    assert tuple(s.tune()) == (16, 8)
+    s.close()
+
+
+def test_sharpclaw_batch_and_server_tiles_bitwise():
+    """A SharpClaw batch and a SharpClaw server tuned (auto and by hand) give
+    their untuned bits."""
+    import torch
+    from paper_1111_6583_gb300 import claw
+    specs = [wl.shock_bubble_2d(nx=nx, ny=ny) for nx, ny in ((64, 32), (100, 52), (48, 40))]
+    for sp in specs:
+        sp["t_end"] = 0.01
+    ref, steps, _ = _batch_run(specs, "fp32", None)
+    for shape in ("auto", (32, 4), (16, 16)):
+        q, st, chosen = _batch_run(specs, "fp32", shape)
+        assert st == steps, shape
+        for a, b in zip(q, ref):
+            assert np.array_equal(a, b), (shape, chosen)
+    sv = claw.Server(specs[0], "fp32", budget_bytes=1 << 30, max_slots=8)
+    tickets = [sv.submit(sp) for sp in specs]
+    sv.pump(1)
+    assert tuple(sv.tune()) in ((16, 8), (32, 4), (32, 8), (16, 16))
+    done, pumps = {}, 0
+    while len(done) < len(tickets):
+        sv.pump(2)
+        pumps += 1
+        for t in sv.take_done():
+            done[t] = sv.poll(t)
+        assert pumps < 100000
+    sv.close()
+    for t, b in zip(tickets, ref):
+        assert np.array_equal(done[t]["q"], b)
+    torch.cuda.synchronize()
