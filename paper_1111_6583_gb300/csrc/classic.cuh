@@ -440,6 +440,16 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? (K >= 8 ?
 #pragma unroll
           for (int c = 0; c < K; ++c) aa[c][k] = v[c];
         }
+      } else if (inside) {
+        // interior cells of fields that are not 16-byte aligned (rows whose
+        // length is not a multiple of the vector): plain loads, no remap
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+#pragma unroll
+          for (int k = 0; k < M; ++k) qa[c][k] = __ldg(q + (size_t)k * nx + g0 + c);
+#pragma unroll
+          for (int k = 0; k < MA; ++k) aa[c][k] = __ldg(aux + (size_t)k * nx + g0 + c);
+        }
       } else {
         // ghost cells by remap; cells beyond the two-cell ghost layer are
         // clamped into it (only halo lanes hold them and nothing reads them)
