@@ -545,6 +545,17 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? (K >= 8 ?
             }
             VecIO<R, K>::store(qo + (size_t)k * nx + g0, v);
           }
+        } else if (inside) {
+          // unaligned rows: plain stores of the lane's interior cells
+#pragma unroll
+          for (int k = 0; k < M; ++k) {
+#pragma unroll
+            for (int c = 0; c < K; ++c) {
+              if constexpr (sizeof(R) == 4) nf = fmaf(qout[c][k], 0.f, nf);
+              else bad |= !isfinite(qout[c][k]);
+              qo[(size_t)k * nx + g0 + c] = qout[c][k];
+            }
+          }
         } else {
 #pragma unroll
           for (int c = 0; c < K; ++c) {
