@@ -118,6 +118,11 @@ def record_traffic(csv_path, tile):
     print(json.dumps(rec))
 
 
+def peaks_file():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    return json.load(open(p)) if os.path.exists(p) else {}
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -732,8 +737,10 @@ def summary(line):
     s = {
         "headline_fp64_1024": {"ms": g("ms_per_step"), "cu_s": g("value"),
                                "alu_frac": g("roofline", "frac"),
-                               "peak_fp64_tf": g("roofline", "peak")},
-        "peaks_measured": g("peaks"),
+                               "peak_fp64_tf": g("roofline", "peak"),
+                               "frac_of_measured": g("roofline", "frac_of_measured")},
+        "peaks_measured": {k: g("peaks", k) for k in ("fp64_fma_tflops_measured",
+                                                      "fp32_fma_tflops_measured", "hbm_gbs")},
         "dambreak_fp32_1024": {"ms": g("fp32", "ms_per_step"), "cu_s": g("fp32", "value"),
                                "alu_frac": g("fp32", "alu_frac")},
         "dambreak_4096": {p: {"ms": g("dambreak_4096", p, "ms_per_step"),
@@ -961,10 +968,10 @@ def main():
     rank, world, local = dist_setup(args.gpus)
     torch.cuda.set_device(local)
     hbm, hbm_kind = peaks()
-    # measured ALU denominators (FMA probes, before the timed region) and the
-    # device's SM count and L2 size
-    fp64_tf = claw.fma_peak("fp64")
-    fp32_tf = claw.fma_peak("fp32")
+    # measured ALU denominators (FMA probes, before the timed region: rate
+    # and the SM clock it ran at) and the device's SM count and L2 size
+    fp64_raw, fp64_mhz = claw.fma_peak("fp64", with_clock=True)
+    fp32_raw, fp32_mhz = claw.fma_peak("fp32", with_clock=True)
     props = torch.cuda.get_device_properties(local)
     device = {"name": props.name, "sms": props.multi_processor_count,
               "l2_bytes": getattr(props, "L2_cache_size", None),
@@ -976,6 +983,14 @@ def main():
         spec, ms, info, shape = bench_sw2d("fp64", args.steps, args.warmup, args.n)
     torch.cuda.synchronize()
     barrier(world)
+    # ALU roofline denominators: the peaks derived from unit counts and the
+    # maximum SM clock; the probes' rates, per SM clock and scaled to that
+    # clock, are reported beside them (they vary from box to box by up to
+    # ~15 % at the same clock, FP64 more than FP32)
+    max_mhz = clk.summary().get("sm_max_mhz") or peaks_file().get("sm_max_mhz") or 2070.0
+    fp64_tf, fp32_tf = FP64_PEAK_DERIVED_TFLOPS, FP32_PEAK_DERIVED_TFLOPS
+    fp64_meas = fp64_raw * max_mhz / fp64_mhz if fp64_mhz > 0 else fp64_raw
+    fp32_meas = fp32_raw * max_mhz / fp32_mhz if fp32_mhz > 0 else fp32_raw
     total_ms = max_over_ranks(sum(ms), world)
     cells = args.n * args.n
     accepted = info["accepted_in_timed"]
@@ -997,12 +1012,18 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": fp64_tf,
                      "unit": "TFLOP/s", "frac": achieved_tf / fp64_tf,
                      "traffic": recorded_traffic(shape),
-                     "peak_kind": "measured in this run: FP64 FMA probe (claw_fma_peak), burst",
+                     "peak_kind": "derived: 152 SMs x 2.07 GHz x 2 FP64 FMA lanes x 2 FLOP",
+                     "peak_measured": fp64_meas,
+                     "frac_of_measured": achieved_tf / fp64_meas,
                      "peak_derived": FP64_PEAK_DERIVED_TFLOPS,
                      "flops_per_cell": SW2D_FLOPS_PER_CELL,
                      "hbm_gbs": hbm_gbs, "hbm_frac": hbm_gbs / hbm, "hbm_peak": hbm,
                      "hbm_peak_kind": hbm_kind},
-        "peaks": {"fp64_fma_tflops": fp64_tf, "fp32_fma_tflops": fp32_tf, "hbm_gbs": hbm,
+        "peaks": {"fp64_fma_tflops_measured": fp64_meas, "fp32_fma_tflops_measured": fp32_meas,
+                  "probe_raw": {"fp64_tflops": fp64_raw, "fp64_sm_mhz": fp64_mhz,
+                                "fp32_tflops": fp32_raw, "fp32_sm_mhz": fp32_mhz,
+                                "scaled_to_mhz": max_mhz},
+                  "hbm_gbs": hbm,
                   "hbm_kind": hbm_kind, "fp64_derived_tflops": FP64_PEAK_DERIVED_TFLOPS,
                   "fp32_derived_tflops": FP32_PEAK_DERIVED_TFLOPS},
         "device": device,

@@ -339,10 +339,13 @@ claw_status claw_sharp_step_noalloc(const claw_method* m, const claw_grid* g, co
 /* Measured FMA throughput of the current device in TFLOP/s (one FMA = 2
  * FLOPs), for the ALU roofline of the FP64-bound kernels: a probe kernel with
  * eight independent FMA chains per thread, as many blocks as fit at once on
- * every SM, the best of five timed launches on stream (cudaStream_t, may be
- * NULL; synchronised).  prec: CLAW_FP64 or CLAW_FP32.  Takes about 10-100 ms.
- * Not part of the paper's method. */
-claw_status claw_fma_peak(int prec, void* stream, double* tflops);
+ * every SM, the best of six timed launches (after two warm-up launches) on
+ * stream (cudaStream_t, may be NULL; synchronised).  *sm_mhz (may be NULL)
+ * receives the SM clock that launch ran at (SM cycles over global-timer time
+ * of one block), so the rate per clock is *tflops / *sm_mhz.  prec:
+ * CLAW_FP64 or CLAW_FP32.  Takes about 0.1-0.3 s.  Not part of the paper's
+ * method. */
+claw_status claw_fma_peak(int prec, void* stream, double* tflops, double* sm_mhz);
 
 /* Self-test of the bounded wait on the shared-memory barriers that complete
  * the bulk asynchronous copies of the staged 1D kernels.  One thread waits

@@ -116,7 +116,8 @@ _SIGS = {
     "claw_server_destroy": (ctypes.c_int, [_VP]),
     "claw_sharp_step_noalloc": (ctypes.c_int, [_P(claw_method), _P(claw_grid), _VP, _VP, _VP,
                                                ctypes.c_double, _VP, _P(ctypes.c_double)]),
-    "claw_fma_peak": (ctypes.c_int, [ctypes.c_int, _VP, _P(ctypes.c_double)]),
+    "claw_fma_peak": (ctypes.c_int, [ctypes.c_int, _VP, _P(ctypes.c_double),
+                                     _P(ctypes.c_double)]),
     "claw_async_wait_probe": (ctypes.c_int, [ctypes.c_int, _VP, _P(ctypes.c_int),
                                              _P(ctypes.c_int), _P(ctypes.c_double)]),
     "claw_batch_tune": (ctypes.c_int, [_VP, ctypes.c_int, _P(ctypes.c_int), _P(ctypes.c_int)]),
@@ -487,11 +488,12 @@ def async_wait_probe(limit_us=20000, stream=None):
     return bool(g.value), bool(c.value), w.value
 
 
-def fma_peak(prec="fp64", stream=None):
-    """Measured FMA throughput of the current device in TFLOP/s (claw_fma_peak)."""
-    out = ctypes.c_double(0.0)
+def fma_peak(prec="fp64", stream=None, with_clock=False):
+    """Measured FMA throughput of the current device in TFLOP/s (claw_fma_peak);
+    with_clock: (TFLOP/s, SM MHz the probe ran at)."""
+    out, mhz = ctypes.c_double(0.0), ctypes.c_double(0.0)
     st = load().claw_fma_peak(FP64 if prec == "fp64" else FP32, stream,
-                              ctypes.byref(out))
+                              ctypes.byref(out), ctypes.byref(mhz))
     if st != CLAW_OK:
         raise RuntimeError(load().claw_last_error(None).decode())
-    return out.value
+    return (out.value, mhz.value) if with_clock else out.value

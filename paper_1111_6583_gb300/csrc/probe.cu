@@ -23,12 +23,22 @@ constexpr int kThreads = 256;
 // keeps every chain live without a store per thread.
 template <typename T>
 __device__ T g_probe_sink;
+// SM cycles and global-timer nanoseconds that block 0 spent in its loop: their
+// ratio is the SM clock the probe ran at
+__device__ unsigned long long g_probe_clk[2];
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) fma_probe_kernel(int iters, T b, T c) {
   T a[kChains];
 #pragma unroll
   for (int k = 0; k < kChains; ++k) a[k] = T(threadIdx.x) * T(1e-3) + T(k);
+  const bool rec = blockIdx.x == 0 && threadIdx.x == 0;
+  long long c0 = 0;
+  unsigned long long t0 = 0;
+  if (rec) {
+    c0 = clock64();
+    t0 = claw::global_ns();
+  }
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
     for (int k = 0; k < kChains; ++k) a[k] = fma(a[k], b, c);
@@ -36,11 +46,17 @@ __global__ void __launch_bounds__(kThreads) fma_probe_kernel(int iters, T b, T c
   T s = T(0);
 #pragma unroll
   for (int k = 0; k < kChains; ++k) s += a[k];
+  if (rec) {
+    const long long c1 = clock64();  // after the chains' results are used
+    const unsigned long long t1 = claw::global_ns();
+    g_probe_clk[0] = (unsigned long long)(c1 - c0) + (s == T(-1234.5) ? 1ull : 0ull);
+    g_probe_clk[1] = t1 - t0;
+  }
   if (s == T(-1234.5)) g_probe_sink<T> = s;
 }
 
 template <typename T>
-cudaError_t run_probe(cudaStream_t st, int iters, double* tflops) {
+cudaError_t run_probe(cudaStream_t st, int iters, double* tflops, double* sm_mhz) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -56,7 +72,8 @@ cudaError_t run_probe(cudaStream_t st, int iters, double* tflops) {
   }
   const T mul = T(1) - T(1.0 / 1048576.0), add = T(1e-6);
   float best = 0.f;
-  for (int rep = 0; rep < 6 && e == cudaSuccess; ++rep) {  // the first run warms up
+  double mhz = 0.0;
+  for (int rep = 0; rep < 8 && e == cudaSuccess; ++rep) {  // the first two runs warm up
     cudaEventRecord(a, st);
     fma_probe_kernel<T><<<blocks, kThreads, 0, st>>>(iters, mul, add);
     cudaEventRecord(b, st);
@@ -64,13 +81,19 @@ cudaError_t run_probe(cudaStream_t st, int iters, double* tflops) {
     if (e == cudaSuccess) e = cudaGetLastError();
     float ms = 0.f;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
-    if (e == cudaSuccess && rep > 0 && (best == 0.f || ms < best)) best = ms;
+    unsigned long long clk[2] = {0ull, 0ull};
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(clk, g_probe_clk, sizeof(clk));
+    if (e == cudaSuccess && rep > 1 && (best == 0.f || ms < best)) {
+      best = ms;
+      mhz = clk[1] > 0 ? 1e3 * (double)clk[0] / (double)clk[1] : 0.0;
+    }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   if (e != cudaSuccess) return e;
   const double flops = 2.0 * kChains * (double)iters * (double)blocks * kThreads;
   *tflops = flops / (best * 1e-3) / 1e12;
+  if (sm_mhz) *sm_mhz = mhz;
   return cudaSuccess;
 }
 
@@ -140,14 +163,14 @@ extern "C" claw_status claw_async_wait_probe(int limit_us, void* stream, int* ga
   return CLAW_OK;
 }
 
-extern "C" claw_status claw_fma_peak(int prec, void* stream, double* tflops) {
+extern "C" claw_status claw_fma_peak(int prec, void* stream, double* tflops, double* sm_mhz) {
   if (!tflops || (prec != CLAW_FP64 && prec != CLAW_FP32)) {
     claw::set_last_error("claw_fma_peak: prec must be CLAW_FP64 or CLAW_FP32, tflops non-null");
     return CLAW_EINVAL;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = prec == CLAW_FP64 ? run_probe<double>(st, 1 << 11, tflops)
-                                    : run_probe<float>(st, 1 << 15, tflops);
+  cudaError_t e = prec == CLAW_FP64 ? run_probe<double>(st, 1 << 13, tflops, sm_mhz)
+                                    : run_probe<float>(st, 1 << 17, tflops, sm_mhz);
   if (e != cudaSuccess) {
     claw::set_last_error((std::string("claw_fma_peak: ") + cudaGetErrorString(e)).c_str());
     return CLAW_ECUDA;
