@@ -847,7 +847,8 @@ def profile_case(case, tile=None):
     """A short fixed launch sequence of one kernel for ncu captures (untimed):
     sw2d64/sw2d32 -- 2048^2 dam break, autotune (40 launches) then 3 steps;
     elast -- 1024-member FP32 elasticity batch, 5 fused steps;
-    sharp -- 1024x512 shock-bubble FP64, 2 SharpClaw steps (6 stage launches);
+    sharp, sharp_f32 -- 1024x512 shock-bubble FP64 / FP32, 2 SharpClaw steps (6
+    stage launches, default tile);
     sw2d1024 -- the headline 1024^2 FP64 dam break, autotune (or --tile) then 4 steps;
     axisym -- 1280x320 axisymmetric shock-bubble FP64, tune then 3 steps;
     vc -- 1024^2 varying-medium acoustics with capacity FP64, 3 steps;
@@ -912,8 +913,9 @@ def profile_case(case, tile=None):
         ens = wl.elasticity_ensemble(1024)
         b = claw.Batch([wl.elasticity_member(e["n"], e["amp"], e["width"]) for e in ens], "fp32")
         b.advance(5)
-    elif case == "sharp":
-        s = claw.Solver(wl.shock_bubble_2d(nx=1024, ny=512), "fp64")
+    elif case in ("sharp", "sharp_f32"):
+        s = claw.Solver(wl.shock_bubble_2d(nx=1024, ny=512),
+                        "fp32" if case.endswith("f32") else "fp64")
         s.set_t_end(0.2)
         s.advance(2)
     else:
