@@ -13,6 +13,8 @@
 // last block runs the CFL controller.
 #pragma once
 
+#include <type_traits>
+
 #include "kernels.h"
 #include "riemann.cuh"
 #include "weno_hi.cuh"
@@ -108,8 +110,7 @@ constexpr size_t sharp_smem_bytes() {
   constexpr int M = RP::M, MA = RP::MA, G = RW;
   constexpr int MAS = MA > 0 ? MA : 1;
   constexpr int HX = TX + 2 * G, HY = (ND == 2) ? TY + 2 * G : 1;
-  constexpr int NE = (ND == 2) ? ((TX + 1) * TY > TX * (TY + 1) ? (TX + 1) * TY : TX * (TY + 1))
-                               : TX + 1;
+  constexpr int NE = (ND == 2) ? (TX + 1) * TY + TX * (TY + 1) : TX + 1;
   return sizeof(R) * ((size_t)M * HY * HX + (size_t)MAS * (MA > 0 ? HY * HX : 1) +
                       (size_t)HY * HX + 4 * (size_t)M * NE + 3) +
          3 * sizeof(int);
@@ -125,8 +126,11 @@ __global__ void __launch_bounds__(TX * TY)
   constexpr int G = RW;        // ghost / halo width
   constexpr int NS = 2 * RW;   // cells around an interface
   constexpr int HX = TX + 2 * G, HY = (ND == 2) ? TY + 2 * G : 1;
-  constexpr int NE = (ND == 2) ? ((TX + 1) * TY > TX * (TY + 1) ? (TX + 1) * TY : TX * (TY + 1))
-                               : TX + 1;
+  // interface slots: the x-interfaces (TX + 1 per row) first, then the
+  // y-interfaces (TY + 1 per column)
+  constexpr int NEX = (ND == 2) ? (TX + 1) * TY : TX + 1;
+  constexpr int NEY = (ND == 2) ? TX * (TY + 1) : 0;
+  constexpr int NE = NEX + NEY;
   __shared__ R Qt[M][HY][HX];
   __shared__ R At[MAS][MA > 0 ? HY : 1][MA > 0 ? HX : 1];
   __shared__ R Kt[HY][HX];  // capacity kappa (when the method has one)
@@ -202,195 +206,182 @@ __global__ void __launch_bounds__(TX * TY)
     for (int k = 0; k < M; ++k) L[k] = R(0);
     R smx = R(0), smy = R(0);
 
-#pragma unroll
-    for (int dir = 0; dir < ND; ++dir) {
-      // interfaces of this direction: along-line index a (0..n), line index b
+    // (a, b) every interface of both directions, each by one thread:
+    // reconstruction of its two edge values, then its Riemann problem
+    // (q^R_{a-1}, q^L_a) from the same thread's edge values
+    auto interface = [&](auto dirc, int le, int e) {
+      constexpr int dir = decltype(dirc)::value;
       const int na = (dir == 0) ? TX + 1 : TY + 1;
-      const int nl = (dir == 0) ? TY : TX;
-      const R idn = s_idn[dir];
-      // (a) reconstruction at every interface
-      for (int e = tid; e < na * nl; e += NT) {
-        const int a = e % na, b = e / na;
-        R cell[NS][M];
+      const int a = le % na, b = le / na;
+      R cell[NS][M];
 #pragma unroll
-        for (int k6 = 0; k6 < NS; ++k6) {
-          // cells a-RW .. a+RW-1 along the line
-          const int hi = (dir == 0) ? a + k6 : G + b;
-          const int hj = (dir == 0) ? ((ND == 2) ? G + b : 0) : a + k6;
+      for (int k6 = 0; k6 < NS; ++k6) {
+        // cells a-RW .. a+RW-1 along the line
+        const int hi = (dir == 0) ? a + k6 : G + b;
+        const int hj = (dir == 0) ? ((ND == 2) ? G + b : 0) : a + k6;
 #pragma unroll
-          for (int k = 0; k < M; ++k) cell[k6][k] = Qt[k][hj][hi];
-        }
-        R wm[M], wp[M];
-        if (C.char_decomp) {
-          R x[NC];
-          R w[NS][M];
-          if (dir == 0) {
-            RP::template char_ctx<0>(C, cell[RW - 1], cell[RW], x);
+        for (int k = 0; k < M; ++k) cell[k6][k] = Qt[k][hj][hi];
+      }
+      R wm[M], wp[M];
+      if (C.char_decomp) {
+        R x[NC];
+        R w[NS][M];
+        RP::template char_ctx<dir>(C, cell[RW - 1], cell[RW], x);
 #pragma unroll
-            for (int k6 = 0; k6 < NS; ++k6) RP::template to_char<0>(C, x, cell[k6], w[k6]);
-          } else {
-            RP::template char_ctx<1>(C, cell[RW - 1], cell[RW], x);
-#pragma unroll
-            for (int k6 = 0; k6 < NS; ++k6) RP::template to_char<1>(C, x, cell[k6], w[k6]);
-          }
-          R um[M], up[M];
-          if constexpr (RW == 3) {
-            R nn[2 * M], dd[2 * M], vv[2 * M];
-#pragma unroll
-            for (int k = 0; k < M; ++k)
-              weno5_pair<R>(w[0][k], w[1][k], w[2][k], w[3][k], w[4][k], w[5][k], C.weno_eps,
-                            nn[k], dd[k], nn[M + k], dd[M + k]);
-            div_many<R, 2 * M>(nn, dd, vv);
-#pragma unroll
-            for (int k = 0; k < M; ++k) {
-              um[k] = vv[k];
-              up[k] = vv[M + k];
-            }
-          } else {
-#pragma unroll
-            for (int k = 0; k < M; ++k) {
-              R line[NS];
-#pragma unroll
-              for (int k6 = 0; k6 < NS; ++k6) line[k6] = w[k6][k];
-              um[k] = weno_edge<RW, false>(line, C.weno_eps);
-              up[k] = weno_edge<RW, true>(line, C.weno_eps);
-            }
-          }
-          if (dir == 0) {
-            RP::template from_char<0>(C, x, um, wm);
-            RP::template from_char<0>(C, x, up, wp);
-          } else {
-            RP::template from_char<1>(C, x, um, wm);
-            RP::template from_char<1>(C, x, up, wp);
-          }
-        } else if constexpr (RW == 3) {
+        for (int k6 = 0; k6 < NS; ++k6) RP::template to_char<dir>(C, x, cell[k6], w[k6]);
+        R um[M], up[M];
+        if constexpr (RW == 3) {
           R nn[2 * M], dd[2 * M], vv[2 * M];
 #pragma unroll
           for (int k = 0; k < M; ++k)
-            weno5_pair<R>(cell[0][k], cell[1][k], cell[2][k], cell[3][k], cell[4][k], cell[5][k],
-                          C.weno_eps, nn[k], dd[k], nn[M + k], dd[M + k]);
+            weno5_pair<R>(w[0][k], w[1][k], w[2][k], w[3][k], w[4][k], w[5][k], C.weno_eps,
+                          nn[k], dd[k], nn[M + k], dd[M + k]);
           div_many<R, 2 * M>(nn, dd, vv);
 #pragma unroll
           for (int k = 0; k < M; ++k) {
-            wm[k] = vv[k];
-            wp[k] = vv[M + k];
+            um[k] = vv[k];
+            up[k] = vv[M + k];
           }
         } else {
 #pragma unroll
           for (int k = 0; k < M; ++k) {
             R line[NS];
 #pragma unroll
-            for (int k6 = 0; k6 < NS; ++k6) line[k6] = cell[k6][k];
-            wm[k] = weno_edge<RW, false>(line, C.weno_eps);
-            wp[k] = weno_edge<RW, true>(line, C.weno_eps);
+            for (int k6 = 0; k6 < NS; ++k6) line[k6] = w[k6][k];
+            um[k] = weno_edge<RW, false>(line, C.weno_eps);
+            up[k] = weno_edge<RW, true>(line, C.weno_eps);
           }
         }
+        RP::template from_char<dir>(C, x, um, wm);
+        RP::template from_char<dir>(C, x, up, wp);
+      } else if constexpr (RW == 3) {
+        R nn[2 * M], dd[2 * M], vv[2 * M];
+#pragma unroll
+        for (int k = 0; k < M; ++k)
+          weno5_pair<R>(cell[0][k], cell[1][k], cell[2][k], cell[3][k], cell[4][k], cell[5][k],
+                        C.weno_eps, nn[k], dd[k], nn[M + k], dd[M + k]);
+        div_many<R, 2 * M>(nn, dd, vv);
 #pragma unroll
         for (int k = 0; k < M; ++k) {
-          ER[k][e] = wm[k];
-          EL[k][e] = wp[k];
+          wm[k] = vv[k];
+          wp[k] = vv[M + k];
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+          R line[NS];
+#pragma unroll
+          for (int k6 = 0; k6 < NS; ++k6) line[k6] = cell[k6][k];
+          wm[k] = weno_edge<RW, false>(line, C.weno_eps);
+          wp[k] = weno_edge<RW, true>(line, C.weno_eps);
         }
       }
-      __syncthreads();
-      // (b) interface Riemann problems (q^R_{a-1}, q^L_a)
-      for (int e = tid; e < na * nl; e += NT) {
-        const int a = e % na, b = e / na;
-        R ql[M], qr[M], al[MAS], ar[MAS];
 #pragma unroll
-        for (int k = 0; k < M; ++k) {
-          ql[k] = ER[k][e];
-          qr[k] = EL[k][e];
+      for (int k = 0; k < M; ++k) {
+        ER[k][e] = wm[k];
+        EL[k][e] = wp[k];
+      }
+      R al[MAS], ar[MAS];
+      if (MA > 0) {
+        const int hil = (dir == 0) ? G + a - 1 : G + b, hir = (dir == 0) ? G + a : G + b;
+        const int hjl = (dir == 0) ? ((ND == 2) ? G + b : 0) : G + a - 1;
+        const int hjr = (dir == 0) ? ((ND == 2) ? G + b : 0) : G + a;
+#pragma unroll
+        for (int k = 0; k < MA; ++k) {
+          al[k] = At[k][MA > 0 ? hjl : 0][MA > 0 ? hil : 0];
+          ar[k] = At[k][MA > 0 ? hjr : 0][MA > 0 ? hir : 0];
         }
-        if (MA > 0) {
+      }
+      R W[MW][M], s[MW], am[M], ap[M], x[NC];
+      RP::template solve<dir>(C, wm, wp, al, ar, W, s, am, ap, x);
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+        FM[k][e] = am[k];
+        FP[k][e] = ap[k];
+      }
+      // interfaces 0..n of interior lines count for the Courant number
+      const int ga = ((dir == 0) ? c0 : r0) + a, gb = ((dir == 0) ? r0 : c0) + b;
+      const int nA = (dir == 0) ? nx : ny, nB = (dir == 0) ? ny : nx;
+      if (ga <= nA && gb < nB) {
+        R m_ = R(0);
+        if (C.capa < 0) {
+#pragma unroll
+          for (int p = 0; p < MW; ++p) m_ = nanmax(m_, (R)fabs(s[p]));
+        } else {
+          // a wave's Courant number uses the capacity of the cell it enters
           const int hil = (dir == 0) ? G + a - 1 : G + b, hir = (dir == 0) ? G + a : G + b;
           const int hjl = (dir == 0) ? ((ND == 2) ? G + b : 0) : G + a - 1;
           const int hjr = (dir == 0) ? ((ND == 2) ? G + b : 0) : G + a;
+          const R kl = Kt[hjl][hil], kr = Kt[hjr][hir];
 #pragma unroll
-          for (int k = 0; k < MA; ++k) {
-            al[k] = At[k][MA > 0 ? hjl : 0][MA > 0 ? hil : 0];
-            ar[k] = At[k][MA > 0 ? hjr : 0][MA > 0 ? hir : 0];
-          }
+          for (int p = 0; p < MW; ++p)
+            m_ = nanmax(m_, gt0(s[p]) ? ::claw::FM<R>::div(s[p], kr)
+                                      : (lt0(s[p]) ? ::claw::FM<R>::div(-s[p], kl) : R(0)));
         }
-        R W[MW][M], s[MW], am[M], ap[M], x[NC];
-        if (dir == 0) RP::template solve<0>(C, ql, qr, al, ar, W, s, am, ap, x);
-        else RP::template solve<1>(C, ql, qr, al, ar, W, s, am, ap, x);
-#pragma unroll
-        for (int k = 0; k < M; ++k) {
-          FM[k][e] = am[k];
-          FP[k][e] = ap[k];
-        }
-        // interfaces 0..n of interior lines count for the Courant number
-        const int ga = ((dir == 0) ? c0 : r0) + a, gb = ((dir == 0) ? r0 : c0) + b;
-        const int nA = (dir == 0) ? nx : ny, nB = (dir == 0) ? ny : nx;
-        if (ga <= nA && gb < nB) {
-          R m_ = R(0);
-          if (C.capa < 0) {
-#pragma unroll
-            for (int p = 0; p < MW; ++p) m_ = nanmax(m_, (R)fabs(s[p]));
-          } else {
-            // a wave's Courant number uses the capacity of the cell it enters
-            const int hil = (dir == 0) ? G + a - 1 : G + b, hir = (dir == 0) ? G + a : G + b;
-            const int hjl = (dir == 0) ? ((ND == 2) ? G + b : 0) : G + a - 1;
-            const int hjr = (dir == 0) ? ((ND == 2) ? G + b : 0) : G + a;
-            const R kl = Kt[hjl][hil], kr = Kt[hjr][hir];
-#pragma unroll
-            for (int p = 0; p < MW; ++p)
-              m_ = nanmax(m_, gt0(s[p]) ? ::claw::FM<R>::div(s[p], kr)
-                                        : (lt0(s[p]) ? ::claw::FM<R>::div(-s[p], kl) : R(0)));
-          }
-          if (dir == 0) smx = nanmax(smx, m_);
-          else smy = nanmax(smy, m_);
-        }
+        if (dir == 0) smx = nanmax(smx, m_);
+        else smy = nanmax(smy, m_);
       }
-      __syncthreads();
-      // (c) in-cell Riemann problem (q^L_i, q^R_i) and the cell's L
-      for (int cidx = tid; cidx < TX * TY; cidx += NT) {
-        const int ci = cidx % TX, cj = cidx / TX;
-        const int a = (dir == 0) ? ci : cj, b = (dir == 0) ? cj : ci;
-        const int e0 = b * na + a, e1 = e0 + 1;
-        R ql[M], qr[M], al[MAS];
-#pragma unroll
-        for (int k = 0; k < M; ++k) {
-          ql[k] = EL[k][e0];
-          qr[k] = ER[k][e1];
-        }
-        if (MA > 0) {
-#pragma unroll
-          for (int k = 0; k < MA; ++k)
-            al[k] = At[k][MA > 0 ? ((ND == 2) ? G + cj : 0) : 0][MA > 0 ? G + ci : 0];
-        }
-        // total fluctuation A dQ_i = A^- + A^+ of the solve (q^L_i, q^R_i), which
-        // for every conservative solver here equals the flux jump
-        // f(q^R_i) - f(q^L_i); systems with a non-conservative component
-        // (the advected tracer) take the solve itself
-        R adq[M];
-        if constexpr (incell_solve<RP>::value) {
-          R W[MW][M], s_[MW], am[M], ap[M], x[NC];
-          if (dir == 0) RP::template solve<0>(C, ql, qr, al, al, W, s_, am, ap, x);
-          else RP::template solve<1>(C, ql, qr, al, al, W, s_, am, ap, x);
-#pragma unroll
-          for (int k = 0; k < M; ++k) adq[k] = am[k] + ap[k];
-        } else {
-          R fl[M], fr[M];
-          if (dir == 0) {
-            RP::template flux<0>(C, ql, al, fl);
-            RP::template flux<0>(C, qr, al, fr);
-          } else {
-            RP::template flux<1>(C, ql, al, fl);
-            RP::template flux<1>(C, qr, al, fr);
-          }
-#pragma unroll
-          for (int k = 0; k < M; ++k) adq[k] = fr[k] - fl[k];
-        }
-        // thread cidx == tid owns cell (ci, cj) (NT == TX*TY); with a capacity
-        // the cell's L is -(1/(kappa_i dx)) (...)
-        const R idk = C.capa < 0 ? idn
-                                 : ::claw::FM<R>::div(idn, Kt[(ND == 2) ? G + cj : 0][G + ci]);
-#pragma unroll
-        for (int k = 0; k < M; ++k) L[k] -= (FP[k][e0] + FM[k][e1] + adq[k]) * idk;
+    };
+    // the y-interfaces start on a warp boundary of the loop so that no warp
+    // runs both directions' code (slots NEX .. NEXP-1 stay idle)
+    constexpr int NEXP = (ND == 2) ? (NEX + 31) / 32 * 32 : NEX;
+    for (int t = tid; t < NEXP + NEY; t += NT) {
+      if (t < NEX) interface(std::integral_constant<int, 0>{}, t, t);
+      else if constexpr (ND == 2) {
+        if (t >= NEXP) interface(std::integral_constant<int, 1>{}, t - NEXP, NEX + t - NEXP);
       }
-      __syncthreads();
     }
+    __syncthreads();
+
+    // (c) the in-cell Riemann problems (q^L_i, q^R_i) and the cell's L, x then y
+    auto incell = [&](auto dirc, int ci, int cj) {
+      constexpr int dir = decltype(dirc)::value;
+      const int na = (dir == 0) ? TX + 1 : TY + 1;
+      const int a = (dir == 0) ? ci : cj, b = (dir == 0) ? cj : ci;
+      const int e0 = (dir == 0 ? 0 : NEX) + b * na + a, e1 = e0 + 1;
+      R ql[M], qr[M], al[MAS];
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+        ql[k] = EL[k][e0];
+        qr[k] = ER[k][e1];
+      }
+      if (MA > 0) {
+#pragma unroll
+        for (int k = 0; k < MA; ++k)
+          al[k] = At[k][MA > 0 ? ((ND == 2) ? G + cj : 0) : 0][MA > 0 ? G + ci : 0];
+      }
+      // total fluctuation A dQ_i = A^- + A^+ of the solve (q^L_i, q^R_i), which
+      // for every conservative solver here equals the flux jump
+      // f(q^R_i) - f(q^L_i); systems with a non-conservative component
+      // (the advected tracer) take the solve itself
+      R adq[M];
+      if constexpr (incell_solve<RP>::value) {
+        R W[MW][M], s_[MW], am[M], ap[M], x[NC];
+        RP::template solve<dir>(C, ql, qr, al, al, W, s_, am, ap, x);
+#pragma unroll
+        for (int k = 0; k < M; ++k) adq[k] = am[k] + ap[k];
+      } else {
+        R fl[M], fr[M];
+        RP::template flux<dir>(C, ql, al, fl);
+        RP::template flux<dir>(C, qr, al, fr);
+#pragma unroll
+        for (int k = 0; k < M; ++k) adq[k] = fr[k] - fl[k];
+      }
+      // with a capacity the cell's L is -(1/(kappa_i dx)) (...)
+      const R idn = s_idn[dir];
+      const R idk = C.capa < 0 ? idn
+                               : ::claw::FM<R>::div(idn, Kt[(ND == 2) ? G + cj : 0][G + ci]);
+#pragma unroll
+      for (int k = 0; k < M; ++k) L[k] -= (FP[k][e0] + FM[k][e1] + adq[k]) * idk;
+    };
+    // thread cidx == tid owns cell (ci, cj) (NT == TX*TY)
+    for (int cidx = tid; cidx < TX * TY; cidx += NT) {
+      const int ci = cidx % TX, cj = cidx / TX;
+      incell(std::integral_constant<int, 0>{}, ci, cj);
+      if constexpr (ND == 2) incell(std::integral_constant<int, 1>{}, ci, cj);
+    }
+    // (no barrier: the combination below reads only this thread's L and the
+    // staged Q^(k); the barriers of finish_attempt precede the next tile)
 
     // (d) Runge-Kutta stage combination: v = Q^(k) + g dt L, then up to two
     // linear combinations with earlier states
