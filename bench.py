@@ -118,6 +118,44 @@ def record_traffic(csv_path, tile):
     print(json.dumps(rec))
 
 
+def copy_rate_gbs(nbytes=1 << 30, reps=5):
+    """A device-to-device copy of nbytes (read + write bytes over the best of
+    `reps` CUDA-event timings): the copy rate of this run, beside the
+    measured one in MEASURED_PEAKS.json."""
+    import torch
+    a = torch.empty(nbytes // 4, dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = None
+    for _ in range(reps + 1):
+        e0.record()
+        b.copy_(a)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None or ms < best else best
+    del a, b
+    return 2.0 * nbytes / (best * 1e-3) / 1e9
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
 def peaks_file():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     return json.load(open(p)) if os.path.exists(p) else {}
@@ -240,9 +278,10 @@ def timed_steps(solver, stream, steps, flush):
     return [a.elapsed_time(b) for a, b in evs]
 
 
-def bench_sw2d(prec, steps, warmup, n=1024):
+def bench_sw2d(prec, steps, warmup, n=1024, tile=None):
     """Timed step attempts of the dam break; also returns how many of them the
-    controller accepted (the headline counts accepted steps only)."""
+    controller accepted (the headline counts accepted steps only).  The tile
+    is the autotuner's pick, or `tile` (bw, h) when given."""
     import torch
     from paper_1111_6583_gb300 import claw
     from paper_1111_6583_gb300 import workloads as wl
@@ -250,7 +289,7 @@ def bench_sw2d(prec, steps, warmup, n=1024):
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         s = claw.Solver(spec, prec, stream=stream.cuda_stream)
-        bw, h = s.tune()
+        bw, h = s.tune(*tile) if tile else s.tune()
         s.set_t_end(1.5)
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
         s.advance(warmup)
@@ -743,6 +782,9 @@ def summary(line):
                                                       "fp32_fma_tflops_measured", "hbm_gbs")},
         "dambreak_fp32_1024": {"ms": g("fp32", "ms_per_step"), "cu_s": g("fp32", "value"),
                                "alu_frac": g("fp32", "alu_frac")},
+        "dambreak_8192": {p: {"ms": g("dambreak_8192", p, "ms_per_step"),
+                              "alu_frac": g("dambreak_8192", p, "alu_frac")}
+                          for p in ("fp64", "fp32")},
         "dambreak_4096": {p: {"ms": g("dambreak_4096", p, "ms_per_step"),
                               "hbm_frac": g("dambreak_4096", p, "hbm_frac"),
                               "alu_frac": g("dambreak_4096", p, "alu_frac")}
@@ -805,7 +847,7 @@ def cpu_baseline_sw2d(n=1024, budget_s=12.0):
             break
     el = time.perf_counter() - t0
     return {"value": n * n * steps / el, "unit": UNIT, "cores": oracle.threads(),
-            "kind": "oracle",
+            "cpu_model": cpu_model(), "kind": "oracle",
             "sample": "%d steps of the %dx%d FP64 dam break (dt = 0.9 dx / 2)" % (steps, n, n)}
 
 
@@ -835,7 +877,8 @@ def reference_arm(args):
             "config": {"workload": "2D shallow-water dam break 1024x1024, classic Roe+HH, MC, "
                                    "transverse 2, FP64", "global_batch": 1, "seq_len": 0,
                        "parallelism": "replicas"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cb["cores"],
+                             "cpu_model": cb.get("cpu_model"), "kind": "oracle",
                              "sample": "%d timed oracle steps of the 1024x1024 workload"
                                        % args.steps},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -978,6 +1021,7 @@ def main():
     device = {"name": props.name, "sms": props.multi_processor_count,
               "l2_bytes": getattr(props, "L2_cache_size", None),
               "hbm_bytes": props.total_memory}
+    copy_gbs = copy_rate_gbs()
 
     barrier(world)
     torch.cuda.synchronize()
@@ -1025,7 +1069,8 @@ def main():
                   "probe_raw": {"fp64_tflops": fp64_raw, "fp64_sm_mhz": fp64_mhz,
                                 "fp32_tflops": fp32_raw, "fp32_sm_mhz": fp32_mhz,
                                 "scaled_to_mhz": max_mhz},
-                  "hbm_gbs": hbm,
+                  "hbm_gbs": hbm, "hbm_copy_gbs_this_run": copy_gbs,
+                  "hbm_nominal_gbs": 7900.0,
                   "hbm_kind": hbm_kind, "fp64_derived_tflops": FP64_PEAK_DERIVED_TFLOPS,
                   "fp32_derived_tflops": FP32_PEAK_DERIVED_TFLOPS},
         "device": device,
@@ -1052,6 +1097,18 @@ def main():
                       "alu_frac": SW2D_FLOPS_PER_CELL * 4096 * 4096 / (ab * 1e-3) / 1e12
                       / (fp64_tf if p == "fp64" else fp32_tf)}
         ex["dambreak_4096"] = big
+        # 8192^2 (1.6 GB per FP64 state copy), on the 4096^2 tile (no tuning
+        # trials at this size)
+        huge = {}
+        for p in ("fp64", "fp32"):
+            _, msh, _, shh = bench_sw2d(p, 3, 2, 8192, tile=big[p]["tile"])
+            ah = sum(msh) / len(msh)
+            gh = SW2D_BYTES_PER_CELL[p] * 8192 * 8192 / (ah * 1e-3) / 1e9
+            huge[p] = {"ms_per_step": ah, "value": 8192 * 8192 / (ah * 1e-3), "hbm_gbs": gh,
+                       "hbm_frac": gh / hbm, "tile": list(shh),
+                       "alu_frac": SW2D_FLOPS_PER_CELL * 8192 * 8192 / (ah * 1e-3) / 1e12
+                       / (fp64_tf if p == "fp64" else fp32_tf)}
+        ex["dambreak_8192"] = huge
         ex["acoustics_1d"] = bench_acoustics_1d("fp64")
         a26 = {}
         for p in ("fp64", "fp32"):
