@@ -8,7 +8,8 @@ oracle finishes a few steps of these sizes in seconds).
 - axisymmetric shock-bubble, 1280 x 320, classic + source, FP64;
 - the 4096-member FP32 elasticity ensemble (90.7 M cells, one batch), sampled
   members compared with the oracle run of that member alone;
-- the Table 1 acoustics system: 2D at 1024^2, 3D at 64^3.
+- the Table 1 acoustics system: 2D at 1024^2, 3D at 64^3;
+- the 2^26-cell 1D acoustics line of the roofline variant, FP64 and FP32.
 FP32 runs are compared with the FP64 oracle (L1 where the data have jumps).
 """
 import numpy as np
@@ -117,3 +118,18 @@ def _gpu_steps_untuned(spec, prec, t_end, steps):
     q = s.q.double().cpu().numpy()
     s.close()
     return q, info
+
+
+def test_acoustics_1d_2p26(orc):
+    """The 2^26-cell 1D acoustics line the bench times (FP32 staged through
+    the shared-memory ring, FP64 direct), two controller steps each, every
+    cell against the oracle."""
+    spec = wl.acoustics_1d(n=1 << 26, t_end=1e9)
+    qo, io = oracle_evolve(orc, spec, 1e9, max_steps=2)
+    qg, ig = _gpu_steps_untuned(spec, "fp64", 1e9, 2)
+    assert ig["status"] == 0 and ig["steps"] == io["steps"] == 2
+    assert rel_maxnorm(qg, qo) <= FP64_TOL
+    del qg
+    q32, i32 = _gpu_steps_untuned(spec, "fp32", 1e9, 2)
+    assert i32["status"] == 0 and i32["steps"] == 2
+    assert rel_l1(q32, qo) <= FP32_SHOCK_L1_TOL
