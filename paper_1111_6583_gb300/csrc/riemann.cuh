@@ -37,10 +37,20 @@ struct FM<double> {
   __device__ static __forceinline__ double rsqrt(double a) { return ::rsqrt(a); }
   __device__ static __forceinline__ double exp(double a) { return ::exp(a); }
 };
+// FP32 reciprocal: the hardware approximation (PTX rcp.approx.ftz.f32,
+// relative error about 2^-23; subnormal inputs and results flush to zero)
+__device__ __forceinline__ float rcp_approx(float a) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
+}
 template <>
 struct FM<float> {
-  __device__ static __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
-  __device__ static __forceinline__ float rcp(float a) { return __fdividef(1.f, a); }
+  // a * (1/b) from the approximate reciprocal: two roundings, no range
+  // handling (a zero b gives an infinity, as a zero wave norm does in the
+  // limiter, where the zero-wave test decides)
+  __device__ static __forceinline__ float div(float a, float b) { return a * rcp_approx(b); }
+  __device__ static __forceinline__ float rcp(float a) { return rcp_approx(a); }
   // a rsqrt(a) for a > 0; sqrt(+-0) = +-0 and NaN below zero by selects (no branch)
   __device__ static __forceinline__ float sqrt(float a) {
     const float y = a * rsqrtf(a);
