@@ -318,7 +318,7 @@ static __device__ __forceinline__ void finish_attempt(DevCtl* ctl, T sx, T sy, i
     sz = nanmax(sz, __shfl_xor_sync(0xffffffffu, sz, o));
   }
   __syncthreads();
-  if (bad) atomicOr(&red_bad, 1);
+  if (bad) atomicOr(&red_bad, bad);  // bit 1 non-finite, bit 2 a wait gave up
   if (lane == 0) {
     red_x[warp] = sx;
     red_y[warp] = sy;
@@ -341,7 +341,7 @@ static __device__ __forceinline__ void finish_attempt(DevCtl* ctl, T sx, T sy, i
       if (ad != 0.0) atomicMax(&ctl->smax[0], (unsigned long long)__double_as_longlong(ad));
       if (bd != 0.0) atomicMax(&ctl->smax[1], (unsigned long long)__double_as_longlong(bd));
       if (zd != 0.0) atomicMax(&ctl->smax[2], (unsigned long long)__double_as_longlong(zd));
-      if (red_bad) atomicOr(&ctl->bad, 1u);
+      if (red_bad) atomicOr(&ctl->bad, (unsigned)red_bad);
       if (run_ctl) {
         __threadfence();
         const unsigned prev = atomicAdd(&ctl->arrive, 1u);

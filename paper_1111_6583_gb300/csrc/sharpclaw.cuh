@@ -15,6 +15,7 @@
 
 #include <type_traits>
 
+#include "async_copy.cuh"
 #include "kernels.h"
 #include "riemann.cuh"
 #include "weno_hi.cuh"
@@ -110,10 +111,14 @@ constexpr size_t sharp_smem_bytes() {
   constexpr int M = RP::M, MA = RP::MA, G = RW;
   constexpr int MAS = MA > 0 ? MA : 1;
   constexpr int HX = TX + 2 * G, HY = (ND == 2) ? TY + 2 * G : 1;
+  constexpr bool kStageRows = TX * TY <= 128;
+  constexpr int A = 16 / (int)sizeof(R), OX = kStageRows ? (A - G % A) % A : 0;
+  constexpr int HXP0 = (OX + HX + A - 1) / A * A;
+  constexpr int HXP = !kStageRows ? HX : ((HXP0 / A) % 2 == 1 ? HXP0 : HXP0 + A);
   constexpr int NE = (ND == 2) ? (TX + 1) * TY + TX * (TY + 1) : TX + 1;
-  return sizeof(R) * ((size_t)M * HY * HX + (size_t)MAS * (MA > 0 ? HY * HX : 1) +
+  return sizeof(R) * ((size_t)M * HY * HXP + (size_t)MAS * (MA > 0 ? HY * HXP : 1) +
                       (size_t)HY * HX + 4 * (size_t)M * NE + 3) +
-         3 * sizeof(int);
+         3 * sizeof(int) + 8;
 }
 
 template <class RP, typename R, int ND, int TX, int TY, int RW>
@@ -131,8 +136,23 @@ __global__ void __launch_bounds__(TX * TY)
   constexpr int NEX = (ND == 2) ? (TX + 1) * TY : TX + 1;
   constexpr int NEY = (ND == 2) ? TX * (TY + 1) : 0;
   constexpr int NE = NEX + NEY;
-  __shared__ R Qt[M][HY][HX];
-  __shared__ R At[MAS][MA > 0 ? HY : 1][MA > 0 ? HX : 1];
+  // staged rows: a tile row of a field is HXP values from the 16-byte
+  // boundary at or below the halo's first cell; cell hi of the halo sits at
+  // column OX + hi (tiles start at multiples of TX, a multiple of A)
+  // Staged rows, for tiles of 128 threads or fewer (with 256-thread tiles
+  // the staging state spilled and the copies measured slower than the
+  // cell-by-cell loads in FP32: 0.64-0.71 against 0.61 ms per shock-bubble
+  // step); rows padded to an odd number of 16-byte units, so that a column
+  // of cells spreads over the shared-memory banks (the y-interface phase
+  // reads down columns).  Without staging the rows are HX values, OX = 0.
+  constexpr bool kStageRows = NT <= 128;
+  constexpr int A = 16 / (int)sizeof(R), OX = kStageRows ? (A - G % A) % A : 0;
+  constexpr int HXP0 = (OX + HX + A - 1) / A * A;
+  constexpr int HXP = !kStageRows ? HX : ((HXP0 / A) % 2 == 1 ? HXP0 : HXP0 + A);
+  static_assert(!kStageRows || TX % A == 0, "tile columns start on 16-byte boundaries");
+  __shared__ __align__(16) R Qt[M][HY][HXP];
+  __shared__ __align__(16) R At[MAS][MA > 0 ? HY : 1][MA > 0 ? HXP : 1];
+  __shared__ __align__(8) unsigned long long s_bar;  // completes the staging copies
   __shared__ R Kt[HY][HX];  // capacity kappa (when the method has one)
   __shared__ R EL[M][NE];  // left edge value of the cell right of an interface
   __shared__ R ER[M][NE];  // right edge value of the cell left of an interface
@@ -143,6 +163,13 @@ __global__ void __launch_bounds__(TX * TY)
 
   const int tid = threadIdx.x;
   const int ti = tid % TX, tj = tid / TX;
+  [[maybe_unused]] unsigned phase = 0u;  // parity of the staging barrier's phase
+  if constexpr (kStageRows) {
+    if (tid == 0) {
+      mbar_init(smem_u32(&s_bar), 1u);
+      fence_mbar_init();
+    }
+  }
 
   for (int it = blockIdx.x; it < ntiles_total; it += gridDim.x) {
     const Tile tl = tiles ? tiles[it] : Tile{0, it};
@@ -175,31 +202,71 @@ __global__ void __launch_bounds__(TX * TY)
     const R* __restrict__ aux = (const R*)mb.aux;
     const size_t plane = (size_t)nx * ny;
 
-    // stage Q^(k) (and aux) with a G-cell halo, corners skipped in 2D
-    for (int idx = tid; idx < HX * HY; idx += NT) {
-      const int hi = idx % HX, hj = idx / HX;
-      if (ND == 2) {
-        const bool xin = hi >= G && hi < G + TX, yin = hj >= G && hj < G + TY;
-        if (!xin && !yin) continue;
+    // stage Q^(k) (and aux) with a G-cell halo.  A tile whose halo rows lie
+    // inside the grid, with 16-byte aligned fields and rows, arrives by
+    // bulk asynchronous copies, one per row and field (HXP values each, the
+    // corners and the padding included), completing on the block's
+    // barrier; the others (and methods with a capacity field) are loaded
+    // cell by cell with the ghost-cell remap, corners skipped in 2D.
+    int bad = 0;
+    const int xa = c0 - G - OX;  // first staged column
+    bool staged = false;
+    if constexpr (kStageRows)
+      staged = C.capa < 0 && xa >= 0 && xa + HXP <= nx &&
+               (ND == 1 || (r0 - G >= 0 && r0 + TY + G <= ny)) &&
+               ((size_t)nx * sizeof(R)) % 16 == 0 && ((size_t)qk & 15) == 0 &&
+               (MA == 0 || ((size_t)aux & 15) == 0);
+    if (staged) {
+      const unsigned bar = smem_u32(&s_bar);
+      constexpr int NCP = (M + MA) * HY;
+      constexpr unsigned RB = HXP * sizeof(R);
+      if (tid == 0) mbar_arrive_expect_tx(bar, NCP * RB);
+      // a block's later tile refills rows that its previous tile read
+      // (those reads precede the barriers of finish_attempt)
+      if (it != (int)blockIdx.x && tid < NCP) fence_proxy_async_smem();
+      for (int cp = tid; cp < NCP; cp += NT) {
+        const int f = cp / HY, hj = cp % HY;
+        const int r = (ND == 2) ? r0 - G + hj : 0;
+        const R* src = f < M ? qk + (size_t)f * plane + (size_t)r * nx + xa
+                             : aux + (size_t)(f - M) * plane + (size_t)r * nx + xa;
+        R* dst = f < M ? &Qt[f][hj][0] : &At[MA > 0 ? f - M : 0][MA > 0 ? hj : 0][0];
+        bulk_g2s(smem_u32(dst), src, RB, bar);
       }
-      const int c = c0 - G + hi, r = (ND == 2) ? r0 - G + hj : 0;
-      R v[M];
-      load_cell<M, R>(C, qk, nx, ny, min(c, nx + G - 1), (ND == 2) ? min(r, ny + G - 1) : 0,
-                      RP::WALL_X, RP::WALL_Y, v);
-#pragma unroll
-      for (int k = 0; k < M; ++k) Qt[k][hj][hi] = v[k];
-      if (MA > 0) {
-        R a[MAS];
-        load_aux<MA, R>(C, aux, nx, ny, min(c, nx + G - 1),
-                        (ND == 2) ? min(r, ny + G - 1) : 0, a);
-#pragma unroll
-        for (int k = 0; k < MA; ++k) At[k][MA > 0 ? hj : 0][MA > 0 ? hi : 0] = a[k];
+      const bool got = mbar_wait_bounded(bar, phase);
+      if (__syncthreads_or(!got)) {
+        // a copy did not complete in time: wait (bounded) for the rest,
+        // report CLAW_ETIMEOUT through the control block, compute nothing
+        mbar_wait_bounded(bar, phase);
+        bad = 2;
       }
-      if (C.capa >= 0)
-        Kt[hj][hi] = load_aux_field<R>(C, aux, nx, ny, min(c, nx + G - 1),
-                                       (ND == 2) ? min(r, ny + G - 1) : 0, C.capa);
+      phase ^= 1u;
+    } else {
+      for (int idx = tid; idx < HX * HY; idx += NT) {
+        const int hi = idx % HX, hj = idx / HX;
+        if (ND == 2) {
+          const bool xin = hi >= G && hi < G + TX, yin = hj >= G && hj < G + TY;
+          if (!xin && !yin) continue;
+        }
+        const int c = c0 - G + hi, r = (ND == 2) ? r0 - G + hj : 0;
+        R v[M];
+        load_cell<M, R>(C, qk, nx, ny, min(c, nx + G - 1), (ND == 2) ? min(r, ny + G - 1) : 0,
+                        RP::WALL_X, RP::WALL_Y, v);
+#pragma unroll
+        for (int k = 0; k < M; ++k) Qt[k][hj][OX + hi] = v[k];
+        if (MA > 0) {
+          R a[MAS];
+          load_aux<MA, R>(C, aux, nx, ny, min(c, nx + G - 1),
+                          (ND == 2) ? min(r, ny + G - 1) : 0, a);
+#pragma unroll
+          for (int k = 0; k < MA; ++k) At[k][MA > 0 ? hj : 0][MA > 0 ? OX + hi : 0] = a[k];
+        }
+        if (C.capa >= 0)
+          Kt[hj][hi] = load_aux_field<R>(C, aux, nx, ny, min(c, nx + G - 1),
+                                         (ND == 2) ? min(r, ny + G - 1) : 0, C.capa);
+      }
+      __syncthreads();
     }
-    __syncthreads();
+    const bool skip = bad != 0;
 
     R L[M];
 #pragma unroll
@@ -220,7 +287,7 @@ __global__ void __launch_bounds__(TX * TY)
         const int hi = (dir == 0) ? a + k6 : G + b;
         const int hj = (dir == 0) ? ((ND == 2) ? G + b : 0) : a + k6;
 #pragma unroll
-        for (int k = 0; k < M; ++k) cell[k6][k] = Qt[k][hj][hi];
+        for (int k = 0; k < M; ++k) cell[k6][k] = Qt[k][hj][OX + hi];
       }
       R wm[M], wp[M];
       if (C.char_decomp) {
@@ -288,8 +355,8 @@ __global__ void __launch_bounds__(TX * TY)
         const int hjr = (dir == 0) ? ((ND == 2) ? G + b : 0) : G + a;
 #pragma unroll
         for (int k = 0; k < MA; ++k) {
-          al[k] = At[k][MA > 0 ? hjl : 0][MA > 0 ? hil : 0];
-          ar[k] = At[k][MA > 0 ? hjr : 0][MA > 0 ? hir : 0];
+          al[k] = At[k][MA > 0 ? hjl : 0][MA > 0 ? OX + hil : 0];
+          ar[k] = At[k][MA > 0 ? hjr : 0][MA > 0 ? OX + hir : 0];
         }
       }
       R W[MW][M], s[MW], am[M], ap[M], x[NC];
@@ -325,7 +392,7 @@ __global__ void __launch_bounds__(TX * TY)
     // the y-interfaces start on a warp boundary of the loop so that no warp
     // runs both directions' code (slots NEX .. NEXP-1 stay idle)
     constexpr int NEXP = (ND == 2) ? (NEX + 31) / 32 * 32 : NEX;
-    for (int t = tid; t < NEXP + NEY; t += NT) {
+    for (int t = skip ? NEXP + NEY : tid; t < NEXP + NEY; t += NT) {
       if (t < NEX) interface(std::integral_constant<int, 0>{}, t, t);
       else if constexpr (ND == 2) {
         if (t >= NEXP) interface(std::integral_constant<int, 1>{}, t - NEXP, NEX + t - NEXP);
@@ -348,7 +415,7 @@ __global__ void __launch_bounds__(TX * TY)
       if (MA > 0) {
 #pragma unroll
         for (int k = 0; k < MA; ++k)
-          al[k] = At[k][MA > 0 ? ((ND == 2) ? G + cj : 0) : 0][MA > 0 ? G + ci : 0];
+          al[k] = At[k][MA > 0 ? ((ND == 2) ? G + cj : 0) : 0][MA > 0 ? OX + G + ci : 0];
       }
       // total fluctuation A dQ_i = A^- + A^+ of the solve (q^L_i, q^R_i), which
       // for every conservative solver here equals the flux jump
@@ -375,7 +442,7 @@ __global__ void __launch_bounds__(TX * TY)
       for (int k = 0; k < M; ++k) L[k] -= (FP[k][e0] + FM[k][e1] + adq[k]) * idk;
     };
     // thread cidx == tid owns cell (ci, cj) (NT == TX*TY)
-    for (int cidx = tid; cidx < TX * TY; cidx += NT) {
+    for (int cidx = skip ? TX * TY : tid; cidx < TX * TY; cidx += NT) {
       const int ci = cidx % TX, cj = cidx / TX;
       incell(std::integral_constant<int, 0>{}, ci, cj);
       if constexpr (ND == 2) incell(std::integral_constant<int, 1>{}, ci, cj);
@@ -385,8 +452,7 @@ __global__ void __launch_bounds__(TX * TY)
 
     // (d) Runge-Kutta stage combination: v = Q^(k) + g dt L, then up to two
     // linear combinations with earlier states
-    int bad = 0;
-    {
+    if (!skip) {
       const int c = c0 + ti, r = r0 + tj;
       if (c < nx && r < ny) {
         const size_t off = (size_t)r * nx + c;
@@ -394,7 +460,7 @@ __global__ void __launch_bounds__(TX * TY)
         const R a0 = (R)op.a0, a1 = (R)op.a1, b0 = (R)op.b0, b1 = (R)op.b1;
 #pragma unroll
         for (int k = 0; k < M; ++k) {
-          const R qkv = Qt[k][(ND == 2) ? G + tj : 0][G + ti];
+          const R qkv = Qt[k][(ND == 2) ? G + tj : 0][OX + G + ti];
           const R v = qkv + gdt * L[k];
           const R o = (op.a0 != 0.0) ? a0 * qa[k * plane + off] + a1 * v : a1 * v;
           bad |= !isfinite(o);

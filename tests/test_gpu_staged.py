@@ -90,3 +90,45 @@ def test_bounded_wait_self_test():
     gave_up, copied, waited = claw.async_wait_probe(20000)
     assert gave_up and copied
     assert 20000.0 <= waited < 2e6
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_sharpclaw_staged_rows_equal_loaded_cells(prec):
+    """SharpClaw stages the halo rows of interior tiles by bulk copies when
+    the state is 16-byte aligned, and loads cell by cell otherwise: a state
+    that starts 4 (FP32) or 8 (FP64) bytes off the boundary gives the same
+    bits (2D Euler, WENO5-char; 2D p-system with aux fields)."""
+    import torch
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    for spec, t_end in ((wl.shock_bubble_2d(nx=128, ny=64), 0.02),
+                        (wl.psystem_checkerboard_2d(periods=2, cells_per_period=32), 0.05)):
+        ref, st = _run_prec(spec, prec, t_end)
+        got, st2 = _run_prec(spec, prec, t_end, q=_offset_copy_dt(spec["q0"], dt))
+        assert st == st2 and st > 2
+        assert np.array_equal(ref, got)
+
+
+def _offset_copy_dt(a, dtype):
+    """a as a contiguous CUDA tensor of `dtype` starting one element past a
+    16-byte boundary."""
+    import torch
+    a = np.asarray(a)
+    es = torch.empty(0, dtype=dtype).element_size()
+    flat = torch.empty(a.size + 16, dtype=dtype, device="cuda")
+    base = flat.data_ptr()
+    off = ((16 - base % 16) % 16) // es + 1
+    v = flat[off:off + a.size].view(a.shape)
+    assert v.data_ptr() % 16 != 0
+    v.copy_(torch.as_tensor(a, dtype=dtype))
+    return v
+
+
+def _run_prec(spec, prec, t_end, q=None):
+    import torch
+    from paper_1111_6583_gb300 import claw
+    s = claw.Solver(spec, prec, q=q)
+    info = s.evolve(t_end)
+    torch.cuda.synchronize()
+    out = s.sync().double().cpu().numpy().copy()
+    s.close()
+    return out, info["steps"]
