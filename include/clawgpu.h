@@ -279,10 +279,15 @@ claw_status claw_server_create_nd(const claw_method* m, int ndim, size_t hbm_bud
  * CLAW_EBUDGET when the request alone exceeds the budget. */
 claw_status claw_server_submit(claw_server* sv, const claw_grid* g, const void* q0_host,
                                const void* aux_host, double t_end, uint64_t* ticket);
-/* Drive the server: admit queued requests that fit (first come, first
- * served), take `steps` fused step attempts over the requests the schedule
- * picks (below), retire finished ones.  Returns the number of running and
- * queued requests in *running and *queued (either may be NULL). */
+/* Drive the server: take `steps` fused step attempts over the requests the
+ * schedule picks (below), retire the requests found finished, admit queued
+ * requests that fit (first come, first served).  The pump is pipelined: it
+ * enqueues its attempts first and does the bookkeeping of the previous
+ * pump's attempts (statuses gathered on the device) while the GPU runs them,
+ * so a request is stepped from the pump after the one that admitted it and
+ * retired by the pump after the one whose attempts finished it; the
+ * arithmetic of every request is unchanged.  Returns the number of running
+ * and queued requests in *running and *queued (either may be NULL). */
 claw_status claw_server_pump(claw_server* sv, int steps, int* running, int* queued);
 /* Which running requests a pump steps.  CLAW_SCHED_ALL: every running request
  * in every attempt.  CLAW_SCHED_SRW (the default, min_cells = 2^23): shortest

@@ -1593,7 +1593,21 @@ struct claw_server {
   int ntiles = 0, nstiles = 0;
   bool dirty = true;
   DevCtl* d_gather = nullptr;
-  DevCtl* h_gather = nullptr;
+  DevCtl* h_gather = nullptr;  // pinned, two halves of max_slots (one per pump parity)
+  // pipelined pumps: the statuses gathered after the last pump's attempts
+  cudaStream_t cst = nullptr;  // result copies of finished requests
+  cudaEvent_t ev_gather[2] = {nullptr, nullptr}, ev_copy = nullptr;
+  bool gather_pending = false;
+  int gpar = 0;                          // parity of the next gather
+  std::vector<uint64_t> gathered;        // the requests of the pending gather
+  std::vector<char> gathered_stepped;    // ... and whether that pump stepped them
+  // pinned staging of a pump's uploads (copies from pageable memory would
+  // wait for the stream's queued attempts); reused by the next pump after
+  // ev_stage
+  unsigned char* stage = nullptr;
+  size_t stage_cap = 0, stage_off = 0;
+  cudaEvent_t ev_stage = nullptr;
+  bool stage_used = false;
   // 2D classic tile for every request: the shape the autotuner picks for a
   // 1024 x 1024 FP32 grid, and the fastest of those tried on a mixed stream
   int bw = 64, h = 21;
@@ -1673,8 +1687,13 @@ claw_status claw_server_create_nd(const claw_method* m, int ndim, size_t hbm_bud
   v->max_slots = max_slots;
   v->ustream = (cudaStream_t)stream;
   cudaError_t e = cudaStreamCreateWithFlags(&v->st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&v->cst, cudaStreamNonBlocking);
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+    e = cudaEventCreateWithFlags(&v->ev_gather[k], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&v->ev_copy, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&v->ev_stage, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMalloc(&v->d_gather, sizeof(DevCtl) * max_slots);
-  if (e == cudaSuccess) e = cudaMallocHost(&v->h_gather, sizeof(DevCtl) * max_slots);
+  if (e == cudaSuccess) e = cudaMallocHost(&v->h_gather, 2 * sizeof(DevCtl) * max_slots);
   if (e == cudaSuccess) {
     cudaMemPool_t pool;
     int dev = 0;
@@ -1727,9 +1746,128 @@ claw_status claw_server_submit(claw_server* v, const claw_grid* g, const void* q
   return CLAW_OK;
 }
 
+namespace {
+// Upload n bytes from host memory to dst on the server's stream through the
+// pinned staging buffer (the host copy is immediate; the transfer runs in
+// stream order).  Growing the buffer waits for the stream (the transfers
+// already queued from the old one) first.
+cudaError_t stage_upload(claw_server* v, void* dst, const void* src, size_t n) {
+  if (n == 0) return cudaSuccess;
+  size_t off = (v->stage_off + 255) & ~(size_t)255;
+  if (off + n > v->stage_cap) {
+    cudaError_t e = cudaStreamSynchronize(v->st);
+    if (e != cudaSuccess) return e;
+    if (v->stage) cudaFreeHost(v->stage);
+    v->stage = nullptr;
+    v->stage_cap = std::max<size_t>({2 * v->stage_cap, n + 256, (size_t)16 << 20});
+    if ((e = cudaMallocHost(&v->stage, v->stage_cap)) != cudaSuccess) {
+      v->stage_cap = 0;
+      return e;
+    }
+    off = 0;
+  }
+  std::memcpy(v->stage + off, src, n);
+  v->stage_off = off + n;
+  return cudaMemcpyAsync(dst, v->stage + off, n, cudaMemcpyHostToDevice, v->st);
+}
+}  // namespace
+
 claw_status claw_server_pump(claw_server* v, int steps, int* running, int* queued) {
   if (!v) return sfail(nullptr, "null server");
-  // 1. admission: first-come first-served while the budget and slots allow
+  // The pump is pipelined: its attempts are enqueued first, then the host
+  // reads the statuses the previous pump gathered, retires, admits and
+  // chooses the next pump's requests while the GPU runs them.  A request is
+  // therefore stepped from the pump after the one that admitted it, and
+  // handed out by the pump after the one whose attempts finished it.
+  // 1. this pump's attempts, over the step tables chosen at the end of the
+  // previous pump (requests that finished since are skipped by the kernels,
+  // their control blocks say done): the GPU runs them while the host does
+  // the bookkeeping below
+  std::vector<uint64_t> launched = v->sel;
+  if (!v->sel.empty()) {
+    for (int i = 0; i < steps; ++i) {
+      if (v->nd == 3) {
+        // the 3D sweeps take one member: request by request
+        for (size_t k = 0; k < v->sel.size(); ++k) {
+          const Req& r = v->reqs[v->sel[k]];
+          LaunchArgs a{v->d_smem + k, nullptr, r.mem.ntiles, v->consts.data(), 0, 0, 0, v->st,
+                       {r.mem.nx, r.mem.ny, r.mem.nz}, r.mem.work3, r.w3bytes};
+          VCK(v->ks.classic(a));
+        }
+      } else if (v->faces) {
+        // the per-face kernels take one member: request by request
+        for (size_t k = 0; k < v->sel.size(); ++k) {
+          const Req& r = v->reqs[v->sel[k]];
+          const int n3[3] = {r.mem.nx, r.mem.ny, 1};
+          VCK(launch_attempt(v->ks, v->m, v->d_smem + k, nullptr, r.mem.ntiles,
+                             v->consts.data(), v->bw, v->h, v->st, v->d_tile0,
+                             maxspeed_tiles(r.mem.nx, r.mem.ny), 1, n3, r.mem.work3,
+                             r.w3bytes));
+        }
+      } else {
+        VCK(launch_attempt(v->ks, v->m, v->d_smem, v->d_tiles, v->ntiles, v->consts.data(),
+                           v->bw, v->h, v->st, v->d_stiles, v->nstiles, (int)v->sel.size()));
+      }
+    }
+  }
+  // 2. the previous pump's statuses, gathered after its attempts: retire
+  // finished requests (their results copied on the copy stream once those
+  // attempts are done, their memory freed after the copies), update the
+  // remaining-work estimates
+  if (v->gather_pending) {
+    const int g = v->gpar ^ 1;  // parity of the pending gather
+    VCK(cudaEventSynchronize(v->ev_gather[g]));
+    v->gather_pending = false;
+    const std::vector<uint64_t>& gt = v->gathered;
+    std::vector<char> fin(gt.size(), 0);
+    bool any_fin = false;
+    for (size_t i = 0; i < gt.size(); ++i) {
+      Req& r = v->reqs[gt[i]];
+      const DevCtl& c = v->h_gather[g * v->max_slots + i];
+      r.steps = c.steps;
+      r.t_reached = c.t;
+      const double cells = (double)cells_of(r.g);
+      r.rem = (c.dt > 0.0 && c.t < r.t_end) ? cells * std::ceil((r.t_end - c.t) / c.dt) : cells;
+      r.idle = v->gathered_stepped[i] ? 0 : r.idle + 1;
+      if (c.done) {
+        if (!any_fin) VCK(cudaStreamWaitEvent(v->cst, v->ev_gather[g], 0));
+        any_fin = true;
+        const size_t sb = state_bytes_of(v->m, r.g);
+        r.result.resize(sb);
+        VCK(cudaMemcpyAsync(r.result.data(), r.mem.q[c.cur], sb, cudaMemcpyDeviceToHost, v->cst));
+        r.status = c.status;
+        fin[i] = 1;
+      }
+    }
+    if (any_fin) {
+      VCK(cudaStreamSynchronize(v->cst));
+      VCK(cudaEventRecord(v->ev_copy, v->cst));
+      VCK(cudaStreamWaitEvent(v->st, v->ev_copy, 0));
+      const double now = now_s();
+      std::vector<uint64_t> keep;
+      for (uint64_t t : v->running) {
+        const auto it = std::find(gt.begin(), gt.end(), t);
+        if (it != gt.end() && fin[it - gt.begin()]) {
+          Req& r = v->reqs[t];
+          r.t_done = now;
+          v->completed.push_back(r.ticket);
+          VCK(cudaFreeAsync(r.dblock, v->st));
+          r.dblock = nullptr;
+          v->used -= r.dbytes;
+          v->dirty = true;
+        } else {
+          keep.push_back(t);
+        }
+      }
+      v->running.swap(keep);
+    }
+  }
+  // 3. admission: first-come first-served while the budget and slots allow
+  if (v->stage_used) {  // the last pump's uploads are done before their staging is reused
+    VCK(cudaEventSynchronize(v->ev_stage));
+    v->stage_used = false;
+  }
+  v->stage_off = 0;
   std::vector<uint64_t> admitted;
   while (!v->queue.empty() && (int)v->running.size() < v->max_slots) {
     Req& r = v->reqs[v->queue.front()];
@@ -1763,18 +1901,16 @@ claw_status claw_server_pump(claw_server* v, int steps, int* running, int* queue
           tiles_of(v->m.scheme, v->nd, v->prec, v->ks.MA, r.mem.nx, r.mem.ny, v->bw, v->h);
     }
     DevCtl c = make_ctl(v->m, r.g, v->nbuf, 0.0, r.t_end);
-    VCK(cudaMemcpyAsync(r.mem.q[0], r.q0.data(), r.q0.size(), cudaMemcpyHostToDevice, v->st));
-    if (!r.aux0.empty())
-      VCK(cudaMemcpyAsync((void*)r.mem.aux, r.aux0.data(), r.aux0.size(), cudaMemcpyHostToDevice,
-                          v->st));
-    VCK(cudaMemcpyAsync(r.mem.ctl, &c, sizeof(DevCtl), cudaMemcpyHostToDevice, v->st));
+    VCK(stage_upload(v, r.mem.q[0], r.q0.data(), r.q0.size()));
+    if (!r.aux0.empty()) VCK(stage_upload(v, (void*)r.mem.aux, r.aux0.data(), r.aux0.size()));
+    VCK(stage_upload(v, r.mem.ctl, &c, sizeof(DevCtl)));
     r.t_admit = now_s();
     admitted.push_back(r.ticket);
     v->running.push_back(r.ticket);
     v->queue.pop_front();
     v->dirty = true;
   }
-  // 2. rebuild the member table of the running requests when the set changed
+  // 4. rebuild the member table of the running requests when the set changed
   if (v->dirty) {
     std::vector<Member> hm;
     for (uint64_t t : v->running) hm.push_back(v->reqs[t].mem);
@@ -1784,8 +1920,7 @@ claw_status claw_server_pump(claw_server* v, int steps, int* running, int* queue
       VCK(cudaMallocAsync(&v->d_mem, sizeof(Member) * v->cap_mem, v->st));
     }
     if (!hm.empty())
-      VCK(cudaMemcpyAsync(v->d_mem, hm.data(), sizeof(Member) * hm.size(), cudaMemcpyHostToDevice,
-                          v->st));
+      VCK(stage_upload(v, v->d_mem, hm.data(), sizeof(Member) * hm.size()));
     if (v->faces && v->m.source != CLAW_SOURCE_NONE) {
       size_t most = 1;
       for (uint64_t t : v->running) {
@@ -1823,7 +1958,7 @@ claw_status claw_server_pump(claw_server* v, int steps, int* running, int* queue
       }
       Tile* d_ms = nullptr;
       VCK(cudaMallocAsync(&d_ms, sizeof(Tile) * ms.size(), v->st));
-      VCK(cudaMemcpyAsync(d_ms, ms.data(), sizeof(Tile) * ms.size(), cudaMemcpyHostToDevice, v->st));
+      VCK(stage_upload(v, d_ms, ms.data(), sizeof(Tile) * ms.size()));
       LaunchArgs a{v->d_mem, d_ms, (int)ms.size(), v->consts.data(), 0, 0, 0, v->st};
       VCK(v->ks.maxspeed(a));
       for (uint64_t t : admitted) VCK(launch_dt_init(v->reqs[t].mem.ctl, 1, v->st));
@@ -1831,10 +1966,13 @@ claw_status claw_server_pump(claw_server* v, int steps, int* running, int* queue
     }
     v->dirty = false;
   }
-  // 3. choose the requests to step (every running one, or the least
-  // remaining work first until sched_cells cells are covered), rebuild the
-  // step tables when the choice changed, and run the fused step attempts
-  if (!v->running.empty()) {
+  // 5. choose the requests the next pump steps (every running one, or the
+  // least remaining work first until sched_cells cells are covered) and
+  // rebuild the step tables when the choice changed (stream-ordered after
+  // this pump's attempts, which read the old ones)
+  if (v->running.empty()) {
+    v->sel.clear();
+  } else {
     std::vector<uint64_t> sel;
     if (v->sched == CLAW_SCHED_ALL) {
       sel = v->running;
@@ -1879,16 +2017,14 @@ claw_status claw_server_pump(claw_server* v, int steps, int* running, int* queue
         v->cap_smem = std::max<size_t>(hm.size(), 2 * v->cap_smem);
         VCK(cudaMallocAsync(&v->d_smem, sizeof(Member) * v->cap_smem, v->st));
       }
-      VCK(cudaMemcpyAsync(v->d_smem, hm.data(), sizeof(Member) * hm.size(),
-                          cudaMemcpyHostToDevice, v->st));
+      VCK(stage_upload(v, v->d_smem, hm.data(), sizeof(Member) * hm.size()));
       if (ht.size() > v->cap_tiles) {
         if (v->d_tiles) VCK(cudaFreeAsync(v->d_tiles, v->st));
         v->cap_tiles = std::max<size_t>(ht.size(), 2 * v->cap_tiles);
         VCK(cudaMallocAsync(&v->d_tiles, sizeof(Tile) * v->cap_tiles, v->st));
       }
       if (!ht.empty())
-        VCK(cudaMemcpyAsync(v->d_tiles, ht.data(), sizeof(Tile) * ht.size(),
-                            cudaMemcpyHostToDevice, v->st));
+        VCK(stage_upload(v, v->d_tiles, ht.data(), sizeof(Tile) * ht.size()));
       v->ntiles = (int)ht.size();
       if (hs.size() > v->cap_stiles) {
         if (v->d_stiles) VCK(cudaFreeAsync(v->d_stiles, v->st));
@@ -1896,83 +2032,30 @@ claw_status claw_server_pump(claw_server* v, int steps, int* running, int* queue
         VCK(cudaMallocAsync(&v->d_stiles, sizeof(Tile) * v->cap_stiles, v->st));
       }
       if (!hs.empty())
-        VCK(cudaMemcpyAsync(v->d_stiles, hs.data(), sizeof(Tile) * hs.size(),
-                            cudaMemcpyHostToDevice, v->st));
+        VCK(stage_upload(v, v->d_stiles, hs.data(), sizeof(Tile) * hs.size()));
       v->nstiles = (int)hs.size();
       v->sel = sel;
     }
-    for (int i = 0; i < steps; ++i) {
-      if (v->nd == 3) {
-        // the 3D sweeps take one member: request by request
-        for (size_t k = 0; k < sel.size(); ++k) {
-          const Req& r = v->reqs[sel[k]];
-          LaunchArgs a{v->d_smem + k, nullptr, r.mem.ntiles, v->consts.data(), 0, 0, 0, v->st,
-                       {r.mem.nx, r.mem.ny, r.mem.nz}, r.mem.work3, r.w3bytes};
-          VCK(v->ks.classic(a));
-        }
-      } else if (v->faces) {
-        // the per-face kernels take one member: request by request
-        for (size_t k = 0; k < sel.size(); ++k) {
-          const Req& r = v->reqs[sel[k]];
-          const int n3[3] = {r.mem.nx, r.mem.ny, 1};
-          VCK(launch_attempt(v->ks, v->m, v->d_smem + k, nullptr, r.mem.ntiles,
-                             v->consts.data(), v->bw, v->h, v->st, v->d_tile0,
-                             maxspeed_tiles(r.mem.nx, r.mem.ny), 1, n3, r.mem.work3,
-                             r.w3bytes));
-        }
-      } else {
-        VCK(launch_attempt(v->ks, v->m, v->d_smem, v->d_tiles, v->ntiles, v->consts.data(),
-                           v->bw, v->h, v->st, v->d_stiles, v->nstiles, (int)sel.size()));
-      }
-    }
-    // 4. retire finished requests; remaining-work estimates for the rest
-    const int nr = (int)v->running.size();
-    std::vector<char> fin(nr, 0), stepped(nr, 0);
-    for (int i = 0, j = 0; i < nr && j < (int)sel.size(); ++i)
-      if (v->running[i] == sel[j]) {
-        stepped[i] = 1;
-        ++j;
-      }
-    for (int base = 0; base < nr; base += v->max_slots) {
-      const int cnt = std::min(v->max_slots, nr - base);
-      VCK(launch_gather_ctl(v->d_mem + base, cnt, v->d_gather, v->st));
-      VCK(cudaMemcpyAsync(v->h_gather + 0, v->d_gather, sizeof(DevCtl) * cnt,
-                          cudaMemcpyDeviceToHost, v->st));
-      VCK(cudaStreamSynchronize(v->st));
-      for (int i = 0; i < cnt; ++i) {
-        Req& r = v->reqs[v->running[base + i]];
-        const DevCtl& c = v->h_gather[i];
-        r.steps = c.steps;
-        r.t_reached = c.t;
-        const double cells = (double)cells_of(r.g);
-        r.rem = (c.dt > 0.0 && c.t < r.t_end) ? cells * std::ceil((r.t_end - c.t) / c.dt) : cells;
-        r.idle = stepped[base + i] ? 0 : r.idle + 1;
-        if (c.done) {
-          const size_t sb = state_bytes_of(v->m, r.g);
-          r.result.resize(sb);
-          VCK(cudaMemcpyAsync(r.result.data(), r.mem.q[c.cur], sb, cudaMemcpyDeviceToHost, v->st));
-          VCK(cudaStreamSynchronize(v->st));
-          r.status = c.status;
-          r.t_done = now_s();
-          fin[base + i] = 1;
-          v->completed.push_back(r.ticket);
-        }
-      }
-    }
-    std::vector<uint64_t> keep;
-    for (int i = 0; i < nr; ++i) {
-      const uint64_t t = v->running[i];
-      Req& r = v->reqs[t];
-      if (fin[i]) {
-        VCK(cudaFreeAsync(r.dblock, v->st));
-        r.dblock = nullptr;
-        v->used -= r.dbytes;
-        v->dirty = true;
-      } else {
-        keep.push_back(t);
-      }
-    }
-    v->running.swap(keep);
+  }
+  if (v->stage_off > 0) {
+    VCK(cudaEventRecord(v->ev_stage, v->st));
+    v->stage_used = true;
+  }
+  // 6. gather the statuses of the running requests after this pump's
+  // attempts (read by the next pump)
+  if (!v->running.empty()) {
+    const int cnt = (int)v->running.size();
+    VCK(launch_gather_ctl(v->d_mem, cnt, v->d_gather, v->st));
+    VCK(cudaMemcpyAsync(v->h_gather + v->gpar * v->max_slots, v->d_gather, sizeof(DevCtl) * cnt,
+                        cudaMemcpyDeviceToHost, v->st));
+    VCK(cudaEventRecord(v->ev_gather[v->gpar], v->st));
+    v->gathered = v->running;
+    v->gathered_stepped.assign(cnt, 0);
+    for (int i = 0; i < cnt; ++i)
+      v->gathered_stepped[i] = std::find(launched.begin(), launched.end(), v->running[i]) !=
+                               launched.end();
+    v->gather_pending = true;
+    v->gpar ^= 1;
   }
   if (running) *running = (int)v->running.size();
   if (queued) *queued = (int)v->queue.size();
@@ -2068,6 +2151,13 @@ claw_status claw_server_destroy(claw_server* v) {
   if (v->d_gather) cudaFree(v->d_gather);
   if (v->h_gather) cudaFreeHost(v->h_gather);
   if (v->st) cudaStreamSynchronize(v->st);
+  if (v->cst) cudaStreamSynchronize(v->cst);
+  for (int k = 0; k < 2; ++k)
+    if (v->ev_gather[k]) cudaEventDestroy(v->ev_gather[k]);
+  if (v->ev_copy) cudaEventDestroy(v->ev_copy);
+  if (v->ev_stage) cudaEventDestroy(v->ev_stage);
+  if (v->stage) cudaFreeHost(v->stage);
+  if (v->cst) cudaStreamDestroy(v->cst);
   if (v->st) cudaStreamDestroy(v->st);
   delete v;
   return CLAW_OK;
