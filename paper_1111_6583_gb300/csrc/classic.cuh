@@ -6,7 +6,9 @@
 // 2D (Sec. 2.1; LeVeque 1997), conservative update (Eq. (fluxdiff)) and the
 // maximum wave speed.  In 2D the last block of a member to finish runs the
 // CFL controller (Sec. 4); in 1D each warp folds its speed into the control
-// block by atomics and a controller launch follows the step kernel.
+// block by atomics and either the warp whose item completes the member's
+// attempt (single-unit items) or a controller launch after the kernel (whole
+// tiles) runs the controller.
 #pragma once
 
 #include "async_copy.cuh"
@@ -25,8 +27,10 @@ namespace claw {
 // fluctuation and correction of interface K: those come from the neighbour
 // lanes by shuffles too.  Lanes 0 and 31 are the warp's halo and write
 // nothing, so a warp writes 30 K cells and no cell is prepared or solved
-// twice inside it.  No shared memory and no block barrier: each warp reads
-// its member's control values itself.
+// twice inside it.  No block barrier: each warp reads its member's control
+// values itself.  With single-unit work items the warp whose item completes a
+// member's attempt (an arrival count per member) runs that member's
+// controller; with whole tiles a controller launch follows the kernel.
 // ---------------------------------------------------------------------------
 // cache hint: fetch the 128-byte line holding p into L1 (no register
 // result; p must lie inside an allocation)
@@ -254,6 +258,7 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? (K >= 8 ?
   constexpr int FOOT = 32 * K;  // cells of a unit's footprint (lanes 0..31)
   static_assert(S == 0 || (FOOT * sizeof(R)) % 16 == 0, "bulk copies move multiples of 16 B");
   __shared__ Ring1d<R, NW, S, NF, FOOT> ring;
+  bool failed = false;                   // a bounded wait of this warp gave up
   [[maybe_unused]] unsigned phase = 0u;  // expected parity per slot
   [[maybe_unused]] unsigned pend = 0u;   // slots with a copy in flight
   [[maybe_unused]] int j = 0, pj = 0;    // units consumed; units the producer passed
@@ -368,14 +373,14 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? (K >= 8 ?
     float nf = 0.f;  // FP32: sum of result * 0
     for (int sub = sub0; sub < sub0 + spw; ++sub) {
       const int ustart = t0 + sub * WC;
-      if (ustart >= nx) break;  // uniform over the warp
+      if (ustart >= nx || failed) break;  // uniform over the warp
 
       // lane l holds cells g0 .. g0+K-1; lanes 0 and 31 are the unit's halo
       const int g0 = ustart + (lane - 1) * K;
       if constexpr (S > 0) {
         // keep the producer S units ahead (the slot it refills was read by
         // the previous unit)
-        while (p_us < p_uend && pj < j + S) p_issue();
+        while (!failed && p_us < p_uend && pj < j + S) p_issue();
       } else if (sub + 1 < sub0 + spw) {
         // L1 prefetch of this lane's cells of the next unit
         const int gn = g0 + WC;
@@ -399,14 +404,16 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? (K >= 8 ?
           bool got = mbar_wait_bounded(smem_u32(&ring.bar[wib][slot]), (phase & bit) ? 1u : 0u);
           got = __all_sync(FULL, got);
           if (!got) {
-            // a copy that did not complete in time: report it, wait (bounded)
-            // for the copies still in flight, and leave
-            if (lane == 0) atomicOr(&ctl->bad, 2u);
+            // a copy that did not complete in time: wait (bounded) for the
+            // copies still in flight, report it, and compute nothing more
+            // (the warp still arrives for its items, so the controller runs)
 #pragma unroll
             for (int sl = 0; sl < S; ++sl)
               if ((pend >> sl) & 1u)
                 mbar_wait_bounded(smem_u32(&ring.bar[wib][sl]), (phase >> sl) & 1u);
-            return;
+            failed = true;
+            bad |= 2;
+            break;
           }
           phase ^= bit;
           pend &= ~bit;
@@ -573,8 +580,23 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? (K >= 8 ?
       if constexpr (S > 0) ++j;
     }  // units of the item
     if constexpr (sizeof(R) == 4) bad |= !isfinite(nf);
-    // per-warp atomics; the controllers run in the next launch
+    // per-warp atomics; with single-unit items (the small grids, where a
+    // launch more per attempt is felt) the warp that completes the member's
+    // attempt runs its controller, with whole tiles (the large grids and
+    // batches, where a fence per item would stall the warps) a controller
+    // launch follows
     fold_warp<R>(ctl, smax, bad);
+    if constexpr (SPW == 1) {
+      if (lane == 0) {
+        __threadfence();
+        const unsigned items = (unsigned)((nx + WC - 1) / WC);
+        if (atomicAdd(&ctl->arrive, 1u) == items - 1u) {
+          __threadfence();
+          run_controller(ctl);
+        }
+      }
+      __syncwarp();
+    }
   }
 }
 

@@ -16,9 +16,10 @@ namespace claw {
 
 // ---------------------------------------------------------------------------
 // Per-grid controller state, resident in device memory.  Kernels read dt/cur
-// at their start; the last block of an attempt (or, for the 1D row kernel, a
-// controller launch after it) runs the controller, which writes the next
-// dt/cur.  Stream order makes the update visible to the next launch.
+// at their start; the last block of an attempt (for the 1D row kernel, the
+// last warp item, or a controller launch after it) runs the controller, which
+// writes the next dt/cur.  Stream order makes the update visible to the next
+// launch.
 // ---------------------------------------------------------------------------
 struct DevCtl {
   double t, dt, t_end, dt_max;
@@ -354,10 +355,10 @@ static __device__ __forceinline__ void finish_attempt(DevCtl* ctl, T sx, T sy, i
   }
 }
 
-// Fold a per-thread maximum speed (direction 0) and bad flag into the control
-// block with one atomic per warp: no block barrier and no arrival count.  The
-// controller then runs in a separate launch (launch_controllers) once the
-// attempt's kernel has finished.  Called by every thread of a full warp.
+// Fold a per-thread maximum speed (direction 0) and bad flags into the
+// control block with one atomic per warp, no block barrier (the caller
+// counts the warp's arrival for the controller, or a controller launch
+// follows).  Called by every thread of a full warp.
 template <typename T>
 static __device__ __forceinline__ void fold_warp(DevCtl* ctl, T sx, int bad) {
 #pragma unroll
@@ -368,7 +369,7 @@ static __device__ __forceinline__ void fold_warp(DevCtl* ctl, T sx, int bad) {
   if ((threadIdx.x & 31) == 0) {
     const double d = (double)sx;
     if (d != 0.0) atomicMax(&ctl->smax[0], (unsigned long long)__double_as_longlong(d));
-    if (bad) atomicOr(&ctl->bad, 1u);
+    if (bad) atomicOr(&ctl->bad, (unsigned)bad);  // bit 1 non-finite, bit 2 a wait gave up
   }
 }
 

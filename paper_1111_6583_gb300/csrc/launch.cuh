@@ -255,7 +255,7 @@ struct Launchers {
         ku<<<persistent_grid<ku>(kClassic1dThreads, a.ntiles_total), kClassic1dThreads, 0,
              a.stream>>>(a.members, a.tiles, a.ntiles_total, C);
       const cudaError_t e = cudaGetLastError();
-      if (e != cudaSuccess) return e;
+      if (e != cudaSuccess || !whole) return e;  // single units run their controllers
       return launch_controllers(a.members, a.nmembers > 0 ? a.nmembers : 1, a.stream);
     } else {
       (void)a;
