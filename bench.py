@@ -900,7 +900,9 @@ def profile_case(case, tile=None):
     weno7 -- 1024x512 shock-bubble FP64, WENO7 + SSP(10,4), one step;
     acou3d -- 256^3 constant-medium acoustics FP64, 3 steps (acou3d128: 128^3,
     small enough for a multi-pass capture; acou3d_f32, acou3d128_f32: FP32);
-    acou1d, acou1d_f32 -- 2^25-cell 1D acoustics, 3 steps (FP64, FP32)."""
+    acou1d, acou1d_f32 -- 2^25-cell 1D acoustics, 3 steps (FP64, FP32);
+    acou2000 -- the 2000-cell 1D acoustics of the latency workload, FP64, 20
+    step attempts."""
     import torch
     from paper_1111_6583_gb300 import claw
     from paper_1111_6583_gb300 import workloads as wl
@@ -942,6 +944,10 @@ def profile_case(case, tile=None):
         s = claw.Solver(sp, "fp32" if case.endswith("f32") else "fp64")
         s.set_t_end(sp["t_end"])
         s.advance(3)
+    elif case == "acou2000":
+        s = claw.Solver(wl.acoustics_1d(n=2000), "fp64")
+        s.set_t_end(2.0)
+        s.advance(20)
     elif case in ("acou1d", "acou1d_f32"):
         s = claw.Solver(wl.acoustics_1d(n=1 << 25, t_end=1e9),
                         "fp32" if case.endswith("f32") else "fp64")
