@@ -243,6 +243,9 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? (K >= 8 ?
   constexpr int MAS = MA > 0 ? MA : 1;
   constexpr int NW = NT / 32;      // warp units per tile
   constexpr int WC = 30 * K;       // cells a warp unit writes (lanes 1..30)
+  // the halo lane 0 solves interfaces between its own cells only: with K >= 2
+  // its last one is the valid left neighbour that lane 1's limiter needs
+  static_assert(K >= 2, "two or more cells per lane");
   constexpr int T = NW * WC;       // cells per tile
   constexpr unsigned FULL = 0xffffffffu;
   using CP = CellPrep<RP, R>;
