@@ -232,3 +232,36 @@ def test_server_take_done_lists_each_finished_request_once():
         r = sv.poll(t, want_state=False)
         assert r["status"] == "ok" and r["t"] == sp["t_end"]
     sv.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_server_1d_requests_match_single_solves(orc, prec):
+    """1D requests (elasticity in the layered medium, uneven sizes, a budget
+    that admits a few at a time) through the pipelined server: each result
+    equals its single solve bit for bit, and the FP64 ones the oracle."""
+    from paper_1111_6583_gb300 import claw
+    specs = [wl.elasticity_member(n, a, w, t_end=t)
+             for n, a, w, t in ((300, 0.3, 2.0, 3.0), (1000, 0.2, 3.0, 2.0),
+                                (4099, 0.4, 1.5, 1.0), (777, 0.25, 2.5, 4.0))]
+    sv = claw.Server(specs[0], prec, budget_bytes=1 << 20, max_slots=8)
+    tickets = [sv.submit(sp) for sp in specs]
+    results, guard = {}, 0
+    while len(results) < len(tickets):
+        sv.pump(3)
+        for t in sv.take_done():
+            results[t] = sv.poll(t)
+        guard += 1
+        assert guard < 100000
+    sv.close()
+    for t, sp in zip(tickets, specs):
+        r = results[t]
+        assert r["status"] == "ok" and r["t"] == sp["t_end"]
+        s = claw.Solver(sp, prec)
+        ia = s.evolve(sp["t_end"])
+        qa = s.q.double().cpu().numpy()
+        s.close()
+        assert ia["steps"] == r["steps"]
+        assert np.array_equal(qa, r["q"].astype(np.float64))
+        if prec == "fp64":
+            qo, io = oracle_evolve(orc, sp, sp["t_end"])
+            assert rel_maxnorm(r["q"], qo) <= FP64_TOL
