@@ -20,6 +20,12 @@
 #include "claw_common.cuh"
 #include "kernels.h"
 
+namespace claw {
+// k_common.cu: copy the state of slot ctl->cur into slot dst on the device
+cudaError_t launch_select_copy(const Member* mem, const DevCtl* ctl, int dst, size_t bytes,
+                               cudaStream_t st);
+}  // namespace claw
+
 using namespace claw;
 
 namespace {
@@ -1101,9 +1107,14 @@ claw_status claw_step_host(claw_solver* s, const void* q_host_in, void* q_host_o
   SCK(cudaMemcpyAsync(s->q_user, q_host_in, s->sbytes, cudaMemcpyHostToDevice, s->st));
   SCK(launch_reset_cur(s->d_ctl, s->st));
   for (int i = 0; i < n; ++i) SCK(solver_attempt(s, s->st));
-  SCK(read_ctl(s));
-  SCK(cudaMemcpyAsync(q_host_out, s->h_mem.q[s->h_ctl->cur], s->sbytes, cudaMemcpyDeviceToHost,
-                      s->st));
+  // the slot that holds the result when every attempt is accepted; a device
+  // copy moves the result there otherwise, so both reads queue behind the
+  // attempts with one synchronisation at the end
+  const int shift = make_ctl(s->m, s->g, s->nbuf, 0.0, 0.0).accept_shift;
+  const int dst = (int)(((long long)(n > 0 ? n : 0) * shift) % s->nbuf);
+  SCK(launch_select_copy(s->d_mem, s->d_ctl, dst, s->sbytes, s->st));
+  SCK(cudaMemcpyAsync(q_host_out, s->h_mem.q[dst], s->sbytes, cudaMemcpyDeviceToHost, s->st));
+  SCK(cudaMemcpyAsync(s->h_ctl, s->d_ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, s->st));
   SCK(cudaStreamSynchronize(s->st));
   SCK(leave(s));
   return s->h_ctl->status;

@@ -218,6 +218,35 @@ cudaError_t launch_reset_cur(DevCtl* ctl, cudaStream_t st) {
   reset_cur_kernel<<<1, 1, 0, st>>>(ctl);
   return cudaGetLastError();
 }
+
+// Copy the state in buffer slot ctl->cur into slot dst (nothing when they are
+// the same slot), so that the host can queue its read of slot dst without
+// first reading the control block.
+__global__ void select_copy_kernel(const Member* __restrict__ mem, const DevCtl* __restrict__ ctl,
+                                   int dst, size_t bytes) {
+  const int cur = ctl->cur;
+  if (cur == dst) return;
+  const unsigned char* src = (const unsigned char*)mem->q[cur];
+  unsigned char* out = (unsigned char*)mem->q[dst];
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  if (((((size_t)src) | ((size_t)out) | bytes) & 15) == 0) {
+    const uint4* s4 = (const uint4*)src;
+    uint4* o4 = (uint4*)out;
+    for (size_t i = t; i < bytes / 16; i += stride) o4[i] = s4[i];
+  } else {
+    for (size_t i = t; i < bytes; i += stride) out[i] = src[i];
+  }
+}
+
+cudaError_t launch_select_copy(const Member* mem, const DevCtl* ctl, int dst, size_t bytes,
+                               cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  select_copy_kernel<<<(sms > 0 ? sms : 1) * 4, 256, 0, st>>>(mem, ctl, dst, bytes);
+  return cudaGetLastError();
+}
 cudaError_t launch_count_active(const DevCtl* ctls, int n, int* out, cudaStream_t st) {
   count_active_kernel<<<1, 256, 0, st>>>(ctls, n, out);
   return cudaGetLastError();
