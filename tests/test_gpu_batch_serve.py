@@ -265,3 +265,20 @@ def test_server_1d_requests_match_single_solves(orc, prec):
         if prec == "fp64":
             qo, io = oracle_evolve(orc, sp, sp["t_end"])
             assert rel_maxnorm(r["q"], qo) <= FP64_TOL
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_step_host_rejected_attempt_returns_qn(prec):
+    """claw_step_host whose only attempt is rejected (a first dt far above the
+    stable one, no retries): CLAW_ECFL, and the state copied back is Q^n
+    (the device moves it into the slot the host reads)."""
+    import torch
+    from paper_1111_6583_gb300 import claw
+    spec = wl.random_smooth_2d("sw_roe", 96, 64, dt_initial=0.5, max_retries=0)
+    s = claw.Solver(spec, prec)
+    hin, hout = _host_pair(spec, prec)
+    st = s.step_host(hin, hout, 1)
+    torch.cuda.synchronize()
+    s.close()
+    assert st == claw.CLAW_ECFL
+    assert torch.equal(hout, hin)
