@@ -23,7 +23,9 @@ namespace claw {
 
 constexpr int kFacesThreads = 256;
 
-// records per face: amdq, apdq, F, B^-a+, B^+a+, B^-a-, B^+a- (M values each)
+// records per face: amdq, apdq, F, B^-a+, B^+a+, B^-a-, B^+a- (M values each);
+// x-face (a, row r) at (r + 1) (nx + 1) + a, y-face (row b, column c) at
+// b (nx + 2) + c + 1 (rows r and columns c from -1, the ghost lines)
 __host__ __device__ inline size_t faces_count(int nd, int nx, int ny, int dir) {
   if (nd == 1) return dir == 0 ? (size_t)nx + 1 : 0;
   return dir == 0 ? (size_t)(nx + 1) * (ny + 2) : (size_t)(ny + 1) * (nx + 2);
@@ -57,8 +59,11 @@ __global__ void __launch_bounds__(kFacesThreads)
   const R* __restrict__ aux = (const R*)mb.aux;
   R smax = R(0);
   if (id < nf) {
-    const int f = (int)(id % (n + 1));
-    const int l = (nd == 2) ? (int)(id / (n + 1)) - 1 : 0;
+    // x-faces line by line (row r: faces 0..nx), y-faces row of faces by row
+    // of faces (face row b: columns -1..nx), so that consecutive threads read
+    // neighbouring cells and write neighbouring records in both sweeps
+    const int f = (D == 0) ? (int)(id % (n + 1)) : (int)(id / lines);
+    const int l = (nd == 2) ? ((D == 0) ? (int)(id / (n + 1)) : (int)(id % lines)) - 1 : 0;
     const R dtdn = s_dtdn;
     R cell[4][M], au[4][MAS];
 #pragma unroll
@@ -212,7 +217,7 @@ __global__ void __launch_bounds__(kFacesThreads)
     auto xf = [&](int a, int r) -> size_t {
       return nd == 2 ? (size_t)(r + 1) * (nx + 1) + a : (size_t)a;
     };
-    auto yf = [&](int c, int b) -> size_t { return (size_t)(c + 1) * (ny + 1) + b; };
+    auto yf = [&](int c, int b) -> size_t { return (size_t)b * (nx + 2) + (c + 1); };
     const size_t plane = (size_t)nx * ny;
 #pragma unroll
     for (int k = 0; k < M; ++k) {
