@@ -2,22 +2,25 @@
 // solves, limited corrections, transverse and double-transverse propagation,
 // for scalar advection and linear acoustics.
 //
-// One attempt = a zero fill of the per-face arrays, three face sweeps (one per
-// direction) and an update kernel whose last block runs the controller.
+// One attempt = three face sweeps (one per direction; a zero fill of the
+// per-face arrays before them only without transverse terms) and an update
+// kernel whose last block runs the controller.
 // Transverse pieces: a fluctuation a that enters cell c across a d-face adds
 // -dt/(2 dx_d) E^+-a to the e-faces of c; the part E^+-a has moved on into
 // cell c +- e, so its third-direction split F^+-E^+-a moves 1/6 (dt/dx_d)
 // (dt/dx_e) of flux correction from the f-faces of c to those of c +- e
 // (six orderings of the directions give the corner-transport-upwind term).
 //
-// Every face value is written by one thread, in a fixed order: a sweep block
-// owns a square patch of lines along its direction (plus a one-line halo it
-// solves again) and walks them together, cell by cell; at each cell every
-// line puts the fluctuation entering its cell across the two sweep faces, and
-// that sum's transverse splits, into shared memory, and each owner line then
-// gathers what its cell's two upper transverse faces receive.  Results do not
-// depend on scheduling, so batches and servers match single solves bit for
-// bit.
+// Every face value is written by one thread, in a fixed order.  y and z
+// sweeps: a block owns a square patch of lines along its direction (plus a
+// one-line halo it solves again) and walks them together, cell by cell; at
+// each cell every line puts the fluctuation entering its cell across the two
+// sweep faces, and that sum's transverse splits, into shared memory, and each
+// owner line then gathers what its cell's two upper transverse faces receive.
+// x sweep: lanes along x, a block of y lines walking z planes
+// (classic3d_xsweep below), so that a warp's accesses stay contiguous.
+// Results do not depend on scheduling, so batches and servers match single
+// solves bit for bit.
 #pragma once
 
 #include "riemann.cuh"
@@ -115,6 +118,38 @@ __host__ __device__ inline void faces3_layout(int nx, int ny, int nz, int M, Fac
   }
 }
 
+// the M values of one face record (M consecutive elements of a record whose
+// offset is a multiple of M; the face arrays start on 256-byte boundaries):
+// one 16-byte access per 16 bytes when M = 4, so a thread's record moves in
+// one (FP32) or two (FP64) accesses instead of four
+template <int M, typename R>
+__device__ __forceinline__ void ld_rec(const R* p, R (&v)[M]) {
+  if constexpr (M == 4 && sizeof(R) == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  } else if constexpr (M == 4 && sizeof(R) == 8) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0];
+    const double2 b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  } else {
+#pragma unroll
+    for (int c = 0; c < M; ++c) v[c] = p[c];
+  }
+}
+
+template <int M, typename R>
+__device__ __forceinline__ void st_rec(R* p, const R (&v)[M]) {
+  if constexpr (M == 4 && sizeof(R) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else if constexpr (M == 4 && sizeof(R) == 8) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < M; ++c) p[c] = v[c];
+  }
+}
+
 template <typename R>
 __device__ __forceinline__ size_t face_index(int e, int nx, int ny, const int (&f)[3]) {
   const int NXF = nx + (e == 0), NYF = ny + (e == 1);
@@ -122,9 +157,11 @@ __device__ __forceinline__ size_t face_index(int e, int nx, int ny, const int (&
 }
 
 // add v to the correction flux of face f in direction e, which this thread
-// alone updates in the current launch (a plain read-modify-write; earlier
-// launches' sums are already in place by stream order), when the face bounds
-// an interior cell
+// alone updates in the current launch (earlier launches' sums are already in
+// place by stream order), when the face bounds an interior cell.  The adds
+// are reductions done in the L2: with one writer per value and launch the sum
+// is the one a read-modify-write gives (FP32 reductions flush a subnormal
+// result to zero), and no load sits on the thread's path to the next cell.
 template <int M, typename R>
 __device__ __forceinline__ void add_fc_own(R* __restrict__ work, const Faces3& L, int e, int nx,
                                            int ny, int nz, const int (&f)[3], const R (&v)[M]) {
@@ -135,8 +172,15 @@ __device__ __forceinline__ void add_fc_own(R* __restrict__ work, const Faces3& L
     if (f[d] < 0 || f[d] > hi) return;
   }
   R* base = work + L.off_fc[e] + face_index<R>(e, nx, ny, f) * M;
+  if constexpr (M == 4 && sizeof(R) == 4) {
+    // one 16-byte vector reduction for the record (16-byte aligned)
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(base), "f"(v[0]),
+                 "f"(v[1]), "f"(v[2]), "f"(v[3])
+                 : "memory");
+  } else {
 #pragma unroll
-  for (int c = 0; c < M; ++c) base[c] += v[c];
+    for (int c = 0; c < M; ++c) atomicAdd(base + c, v[c]);
+  }
 }
 
 // sweep blocks: kPatch3d x kPatch3d lines (owners: the inner kPatch3d - 2
@@ -271,11 +315,8 @@ __global__ void __launch_bounds__(kPatch3d * kPatch3d)
       f[E1] = line[E1];
       f[E2] = line[E2];
       const size_t fi = face_index<R>(D, nx, ny, f);
-#pragma unroll
-      for (int c = 0; c < M; ++c) {
-        work[L.off_am[D] + fi * M + c] = amc[c];
-        work[L.off_ap[D] + fi * M + c] = apc[c];
-      }
+      st_rec<M, R>(work + L.off_am[D] + fi * M, amc);
+      st_rec<M, R>(work + L.off_ap[D] + fi * M, apc);
       add_fc_own<M, R>(work, L, D, nx, ny, nz, f, F);
     }
     if (C.transverse) {
@@ -365,6 +406,210 @@ __global__ void __launch_bounds__(kPatch3d * kPatch3d)
   finish_attempt<R>(ctl, sx, sy, 0, 0, false, sz);
 }
 
+// The x sweep with lanes along x.  In the walking sweep above, x is the
+// sweep direction and the 32 threads of a warp sit on 32 different (y, z)
+// lines, so every load and face store of a warp touches 32 separate sectors.
+// Here a warp holds 32 consecutive cells of one x line (28 owned cells, two
+// halo cells below and two above), the block's NW warps hold NW consecutive
+// y lines (the first and last are halo lines), and the block walks the z
+// planes of a segment.  Neighbour waves along x come by warp shuffles; what
+// crosses lines goes through shared memory once per plane; every global
+// access of a warp is one contiguous run along x.
+//
+// The transverse terms of the walking sweep regroup by line.  For a cell X
+// of plane k with entering sum S and its splits (e1 = y, e2 = z):
+//   A_y(X) = h S(X) + k6z (e2p(X) - e2m(X)) - k6z (e2p(X - z) - e2m(X + z))
+//   A_z(X) = h S(X) + k6y (e1p(X) - e1m(X)) - k6y (e1p(X - y) - e1m(X + y))
+// (h = -dt/(2 dx), k6e = (dt/dx)(dt/dx_e)/6).  The upper y-face of X gets
+// G_y^+ A_y(X) + G_y^- A_y(X + y) and the upper z-face
+// G_z^+ A_z(X) + G_z^- A_z(X + z).  A_y needs only the cell's own line (three
+// planes, kept in registers) and A_z the neighbouring lines of the same plane
+// (shared memory); A_y of the line above goes through shared memory too and
+// A_z of the plane above is the next step's value on the same line.
+//
+// With transverse terms on, this sweep is the first writer of every record
+// of the step: each x-face record, and the correction flux of each y- and
+// z-face, gets exactly one owner, which stores it (no zero fill, no
+// read-modify-write).  Without transverse terms the y- and z-face fluxes
+// stay as the zero fill left them.
+constexpr int kXOwn3d = 28;  // owned cells per warp (lanes 2 .. 29)
+constexpr int kXSweepLines = 8;  // y lines per block (owners: the inner six)
+constexpr int kZSeg3d = 32;  // owned planes per block
+
+__host__ __device__ inline void xsweep3d_grid(int NW, int nx, int ny, int nz, int& nxc, int& nyb,
+                                              int& nzs) {
+  nxc = (nx + kXOwn3d - 1) / kXOwn3d;
+  nyb = (ny + 1 + (NW - 2) - 1) / (NW - 2);  // owner lines -1 .. ny-1
+  nzs = (nz + 1 + kZSeg3d - 1) / kZSeg3d;    // owner planes -1 .. nz-1
+}
+
+// NB = 2: the shared exchange is double-buffered by plane parity (one
+// barrier per plane); NB = 1: one buffer, a second barrier before it is
+// rewritten
+template <class RP, typename R, int NW, int NB>
+__global__ void __launch_bounds__(32 * NW)
+    classic3d_xsweep(const Member* __restrict__ members, const MConsts<R> C) {
+  constexpr int M = RP::M, MW = RP::MW;
+  static_assert(NW >= 3 && (NB == 1 || NB == 2), "three or more lines, one or two buffers");
+  // per buffer: e1m and e1p of plane p, A_y of plane p - 1, per line and lane
+  __shared__ R sh[NB][3][M][NW][32];
+  const Member& mb = members[0];
+  DevCtl* ctl = mb.ctl;
+  __shared__ int s_done, s_cur;
+  __shared__ R s_k[3];
+  if (threadIdx.x == 0) {
+    s_done = ctl->done;
+    s_cur = ctl->cur;
+    for (int d = 0; d < 3; ++d) s_k[d] = (R)(ctl->dt / ctl->dx[d]);
+  }
+  __syncthreads();
+  if (s_done) return;
+  const int nx = mb.nx, ny = mb.ny, nz = mb.nz;
+  int nxc, nyb, nzs;
+  xsweep3d_grid(NW, nx, ny, nz, nxc, nyb, nzs);
+  const int bx = blockIdx.x % nxc, by = (blockIdx.x / nxc) % nyb, bz = blockIdx.x / (nxc * nyb);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int x0 = bx * kXOwn3d;
+  const int j = by * (NW - 2) - 2 + w;  // this warp's line; owners are warps 1 .. NW-2
+  const int z0 = bz * kZSeg3d - 1, z1 = min(z0 + kZSeg3d, nz);  // owner planes [z0, z1)
+  // lane l holds cell x0 - 2 + l and the face below it; lines and cells past
+  // the second ghost layer load that layer (no owner reads them)
+  const int f = x0 - 2 + lane;
+  const int xc = min(f, nx + 1), jl = min(j, ny + 1);
+  const bool owner_line = w >= 1 && w <= NW - 2 && j <= ny - 1;
+  const bool interior_line = j >= 0;  // j <= ny - 1 for owners
+  const bool own_cell = lane >= 2 && lane <= 29 && f <= nx - 1;
+  const bool own_face = (lane >= 2 && lane <= 29 && f <= nx) || (lane == 30 && f == nx);
+  const R* __restrict__ q = (const R*)mb.q[s_cur];
+  R* __restrict__ work = (R*)mb.work3;
+  Faces3 L;
+  faces3_layout(nx, ny, nz, M, L);
+  const R dtdn = s_k[0];
+  const R tfF = C.transverse == 2 ? R(1) : R(0);
+  const R h = R(-0.5) * dtdn;
+  const R k6y = dtdn * s_k[1] * (R(1) / R(6)), k6z = dtdn * s_k[2] * (R(1) / R(6));
+  const bool trans = C.transverse != 0;
+  // the line's values of earlier planes: S, e2p, e2m of plane p-1, e2p of
+  // plane p-2, A_z of plane p-1
+  R S1[M], e2p1[M], e2m1[M], e2p2[M], Az1[M];
+#pragma unroll
+  for (int c = 0; c < M; ++c) S1[c] = e2p1[c] = e2m1[c] = e2p2[c] = Az1[c] = R(0);
+  R smax = R(0);
+  for (int pz = z0 - 1; pz <= z1; ++pz) {
+    const int b = NB == 2 ? (pz & 1) : 0;
+    R qc[M], ql[M];
+    load_cell3<M, R>(C, q, nx, ny, nz, xc, jl, pz, RP::WALL_X, 2, 3, qc);
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+      ql[c] = __shfl_up_sync(0xffffffffu, qc[c], 1);
+      if (lane == 0) ql[c] = qc[c];
+    }
+    R W[MW][M], s[MW], am[M], ap[M], F[M];
+    {
+      R x[RP::NCTX];
+      RP::template solve<0>(C, ql, qc, nullptr, nullptr, W, s, am, ap, x);
+    }
+    if (C.order == 2) {
+      R dot[MW], nrm[MW];
+#pragma unroll
+      for (int p = 0; p < MW; ++p) {
+        const bool left = s[p] > R(0);
+        R d_ = R(0), n2 = R(0);
+#pragma unroll
+        for (int c = 0; c < M; ++c) {
+          const R wl = __shfl_up_sync(0xffffffffu, W[p][c], 1);
+          const R wr = __shfl_down_sync(0xffffffffu, W[p][c], 1);
+          const R up = left ? wl : wr;
+          d_ += up * W[p][c];
+          n2 += W[p][c] * W[p][c];
+        }
+        dot[p] = d_;
+        nrm[p] = n2;
+      }
+      correction<RP, R, 0>(C, W, s, dot, nrm, dtdn, F);
+    } else {
+#pragma unroll
+      for (int c = 0; c < M; ++c) F[c] = R(0);
+    }
+    if (owner_line && interior_line && own_face && pz >= 0 && pz >= z0 && pz < z1) {
+#pragma unroll
+      for (int p = 0; p < MW; ++p) smax = nanmax(smax, (R)fabs(s[p]));
+      const int fx[3] = {f, j, pz};
+      const size_t fi = face_index<R>(0, nx, ny, fx);
+      st_rec<M, R>(work + L.off_am[0] + fi * M, am);
+      st_rec<M, R>(work + L.off_ap[0] + fi * M, ap);
+      if (trans) {
+        st_rec<M, R>(work + L.off_fc[0] + fi * M, F);
+      } else {
+        add_fc_own<M, R>(work, L, 0, nx, ny, nz, fx, F);
+      }
+    }
+    if (!trans) continue;
+    // cell f: A+dQ - F of face f plus A-dQ + F of face f + 1
+    R S[M], e1m[M], e1p[M], e2m[M], e2p[M], Ay[M];
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+      const R amn = __shfl_down_sync(0xffffffffu, am[c], 1);
+      const R Fn = __shfl_down_sync(0xffffffffu, F[c], 1);
+      S[c] = (ap[c] - tfF * F[c]) + (amn + tfF * Fn);
+    }
+    Trans3<RP, R, 1>::split(C, S, e1m, e1p);
+    Trans3<RP, R, 2>::split(C, S, e2m, e2p);
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+      Ay[c] = h * S1[c] + k6z * (e2p1[c] - e2m1[c]) - k6z * (e2p2[c] - e2m[c]);  // plane pz-1
+      sh[b][0][c][w][lane] = e1m[c];
+      sh[b][1][c][w][lane] = e1p[c];
+      sh[b][2][c][w][lane] = Ay[c];
+    }
+    __syncthreads();
+    R Az[M];
+    if (w >= 1 && w <= NW - 2) {
+#pragma unroll
+      for (int c = 0; c < M; ++c)
+        Az[c] = h * S[c] + k6y * (e1p[c] - e1m[c]) -
+                k6y * (sh[b][1][c][w - 1][lane] - sh[b][0][c][w + 1][lane]);
+    } else {
+#pragma unroll
+      for (int c = 0; c < M; ++c) Az[c] = R(0);
+    }
+    const int k = pz - 1;
+    if (owner_line && own_cell && k >= z0) {
+      R Ayu[M], apA[M], amA[M], apB[M], amB[M], v[M];
+#pragma unroll
+      for (int c = 0; c < M; ++c) Ayu[c] = sh[b][2][c][w + 1][lane];
+      // upper y-face of cell (f, j, k)
+      Trans3<RP, R, 1>::split(C, Ay, amA, apA);
+      Trans3<RP, R, 1>::split(C, Ayu, amB, apB);
+#pragma unroll
+      for (int c = 0; c < M; ++c) v[c] = apA[c] + amB[c];
+      if (k >= 0) {
+        const int fy[3] = {f, j + 1, k};
+        st_rec<M, R>(work + L.off_fc[1] + face_index<R>(1, nx, ny, fy) * M, v);
+      }
+      // upper z-face of cell (f, j, k)
+      Trans3<RP, R, 2>::split(C, Az1, amA, apA);
+      Trans3<RP, R, 2>::split(C, Az, amB, apB);
+#pragma unroll
+      for (int c = 0; c < M; ++c) v[c] = apA[c] + amB[c];
+      if (j >= 0) {
+        const int fz[3] = {f, j, k + 1};
+        st_rec<M, R>(work + L.off_fc[2] + face_index<R>(2, nx, ny, fz) * M, v);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < M; ++c) {
+      e2p2[c] = e2p1[c];
+      e2p1[c] = e2p[c];
+      e2m1[c] = e2m[c];
+      S1[c] = S[c];
+      Az1[c] = Az[c];
+    }
+    if (NB == 1) __syncthreads();
+  }
+  finish_attempt<R>(ctl, smax, R(0), 0, 0, false, R(0));
+}
+
 template <class RP, typename R>
 __global__ void __launch_bounds__(256)
     classic3d_update(const Member* __restrict__ members, const MConsts<R> C) {
@@ -401,11 +646,13 @@ __global__ void __launch_bounds__(256)
       hi[d] += 1;
       const size_t fl = face_index<R>(d, nx, ny, lo), fh = face_index<R>(d, nx, ny, hi);
       const R dtdn = s_k[d];
+      R apl[M], amh[M], fch[M], fcl[M];
+      ld_rec<M, R>(work + L.off_ap[d] + fl * M, apl);
+      ld_rec<M, R>(work + L.off_am[d] + fh * M, amh);
+      ld_rec<M, R>(work + L.off_fc[d] + fh * M, fch);
+      ld_rec<M, R>(work + L.off_fc[d] + fl * M, fcl);
 #pragma unroll
-      for (int c = 0; c < M; ++c) {
-        v[c] = v[c] - dtdn * (work[L.off_ap[d] + fl * M + c] + work[L.off_am[d] + fh * M + c]) -
-               dtdn * (work[L.off_fc[d] + fh * M + c] - work[L.off_fc[d] + fl * M + c]);
-      }
+      for (int c = 0; c < M; ++c) v[c] = v[c] - dtdn * (apl[c] + amh[c]) - dtdn * (fch[c] - fcl[c]);
     }
 #pragma unroll
     for (int c = 0; c < M; ++c) {

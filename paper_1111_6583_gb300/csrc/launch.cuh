@@ -200,13 +200,20 @@ struct Launchers {
     }
     if constexpr (ND == 3) {
       const long long nx = a.n3[0], ny = a.n3[1], nz = a.n3[2];
-      cudaError_t e = cudaMemsetAsync(a.work3, 0, a.work3_bytes, a.stream);
-      if (e != cudaSuccess) return e;
-      // one block per patch of lines and segment of cells along the sweep
+      // with transverse terms the x sweep writes every record first (no fill)
+      if (!C.transverse) {
+        cudaError_t e = cudaMemsetAsync(a.work3, 0, a.work3_bytes, a.stream);
+        if (e != cudaSuccess) return e;
+      }
+      // x: lanes along x, a block of kXSweepLines y lines walks a segment of
+      // z planes; y, z: one block per patch of lines and segment of cells
+      // along the sweep
+      constexpr int NW = kXSweepLines, NB = sizeof(R) == 4 ? 2 : 1;
+      int nxc, nyb, nzs;
+      xsweep3d_grid(NW, (int)nx, (int)ny, (int)nz, nxc, nyb, nzs);
+      classic3d_xsweep<RP, R, NW, NB><<<(unsigned)(nxc * nyb * nzs), 32 * NW, 0, a.stream>>>(
+          a.members, C);
       int npf, nps, nseg;
-      sweep3d_grid(0, (int)nx, (int)ny, (int)nz, npf, nps, nseg);
-      classic3d_sweep<RP, R, 0><<<(unsigned)(npf * nps * nseg), kPatch3d * kPatch3d, 0,
-                                  a.stream>>>(a.members, C);
       sweep3d_grid(1, (int)nx, (int)ny, (int)nz, npf, nps, nseg);
       classic3d_sweep<RP, R, 1><<<(unsigned)(npf * nps * nseg), kPatch3d * kPatch3d, 0,
                                   a.stream>>>(a.members, C);

@@ -60,6 +60,26 @@ def test_3d_several_patches_and_segments(orc, rp):
     assert rel_maxnorm(q32, qo) <= FP32_SMOOTH_TOL
 
 
+@pytest.mark.parametrize("n3", [(56, 5, 31), (29, 6, 33), (5, 4, 4)])
+def test_3d_x_sweep_chunks(orc, n3):
+    """The x sweep's decomposition: 28 owned cells per warp (nx = 56 puts the
+    last face in the halo lane of the second chunk), six owner lines per
+    block (ny + 1 = 6: one block exactly; ny = 6: a second block with one
+    line), 32 owner planes per segment (nz + 1 = 32 exactly; nz = 33: a
+    second segment), and a grid smaller than one chunk (four cells, the
+    smallest a direction may have)."""
+    spec = wl.random_3d("acoustics", *n3, bc="wall")
+    spec["bc_lower"] = ["wall", "extrap", "periodic"]
+    spec["bc_upper"] = ["extrap", "wall", "periodic"]
+    dt = 0.2 / max(n3)
+    qo, co = oracle_fixed_steps(orc, spec, dt, 3)
+    qg, cg = gpu_fixed_steps(spec, "fp64", dt, 3)
+    assert rel_maxnorm(qg, qo) <= FP64_TOL
+    assert np.allclose(cg, co, rtol=1e-13, atol=0)
+    q32, _ = gpu_fixed_steps(spec, "fp32", dt, 3)
+    assert rel_maxnorm(q32, qo) <= FP32_SMOOTH_TOL
+
+
 def test_3d_diagonal_shift():
     n = 16
     spec = wl.random_3d("advection", n, n, n, params=[1.0, 1.0, 1.0], order=2, transverse=2)
