@@ -433,7 +433,7 @@ __global__ void __launch_bounds__(kPatch3d * kPatch3d)
 // read-modify-write).  Without transverse terms the y- and z-face fluxes
 // stay as the zero fill left them.
 constexpr int kXOwn3d = 28;  // owned cells per warp (lanes 2 .. 29)
-constexpr int kXSweepLines = 8;  // y lines per block (owners: the inner six)
+constexpr int kXSweepLines = 12;  // y lines per block (owners: the inner ten)
 constexpr int kZSeg3d = 32;  // owned planes per block
 
 __host__ __device__ inline void xsweep3d_grid(int NW, int nx, int ny, int nz, int& nxc, int& nyb,

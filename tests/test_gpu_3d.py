@@ -60,14 +60,14 @@ def test_3d_several_patches_and_segments(orc, rp):
     assert rel_maxnorm(q32, qo) <= FP32_SMOOTH_TOL
 
 
-@pytest.mark.parametrize("n3", [(56, 5, 31), (29, 6, 33), (5, 4, 4)])
+@pytest.mark.parametrize("n3", [(56, 9, 31), (29, 10, 33), (5, 4, 4)])
 def test_3d_x_sweep_chunks(orc, n3):
     """The x sweep's decomposition: 28 owned cells per warp (nx = 56 puts the
-    last face in the halo lane of the second chunk), six owner lines per
-    block (ny + 1 = 6: one block exactly; ny = 6: a second block with one
-    line), 32 owner planes per segment (nz + 1 = 32 exactly; nz = 33: a
-    second segment), and a grid smaller than one chunk (four cells, the
-    smallest a direction may have)."""
+    last face in the halo lane of the second chunk), ten owner lines per
+    block (lines -1 .. ny-1: ny = 9 fills one block exactly, ny = 10 leaves
+    one line for a second block), 32 owner planes per segment (nz + 1 = 32
+    exactly; nz = 33: a second segment), and a grid smaller than one chunk
+    (four cells, the smallest a direction may have)."""
     spec = wl.random_3d("acoustics", *n3, bc="wall")
     spec["bc_lower"] = ["wall", "extrap", "periodic"]
     spec["bc_upper"] = ["extrap", "wall", "periodic"]
