@@ -197,19 +197,25 @@ __device__ __forceinline__ void limit1d(const MConsts<R>& C, int order,
     return;
   }
   R dot[MW], nrm[MW];
+  constexpr int KS = strength_k<RP, 0>();
 #pragma unroll
   for (int p = 0; p < MW; ++p) {
-    R d = R(0), n2 = R(0);
+    // upwind neighbour: left for a right-going wave
+    const bool right = signed_waves<RP>::value ? p != 0 : sc[p] > R(0);
+    if constexpr (KS >= 0) {
+      dot[p] = right ? Wl[p][KS] : Wr[p][KS];
+      nrm[p] = Wc[p][KS];
+    } else {
+      R d = R(0), n2 = R(0);
 #pragma unroll
-    for (int k = 0; k < M; ++k) {
-      // upwind neighbour: left for a right-going wave
-      const bool right = signed_waves<RP>::value ? p != 0 : sc[p] > R(0);
-      const R up = right ? Wl[p][k] : Wr[p][k];
-      d += up * Wc[p][k];
-      n2 += Wc[p][k] * Wc[p][k];
+      for (int k = 0; k < M; ++k) {
+        const R up = right ? Wl[p][k] : Wr[p][k];
+        d += up * Wc[p][k];
+        n2 += Wc[p][k] * Wc[p][k];
+      }
+      dot[p] = d;
+      nrm[p] = n2;
     }
-    dot[p] = d;
-    nrm[p] = n2;
   }
   correction<RP, R, 0, LIMC>(C, Wc, sc, dot, nrm, dtdx, F);
 }

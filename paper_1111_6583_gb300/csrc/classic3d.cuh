@@ -290,17 +290,23 @@ __global__ void __launch_bounds__(kPatch3d * kPatch3d)
     R F[M];
     if (C.order == 2) {
       R dot[MW], nrm[MW];
+      constexpr int KS = strength_k<RP, D>();
 #pragma unroll
       for (int p = 0; p < MW; ++p) {
-        R d_ = R(0), n2 = R(0);
+        if constexpr (KS >= 0) {
+          dot[p] = sc[p] > R(0) ? Wl[p][KS] : Wr[p][KS];
+          nrm[p] = Wc[p][KS];
+        } else {
+          R d_ = R(0), n2 = R(0);
 #pragma unroll
-        for (int c = 0; c < M; ++c) {
-          const R up = sc[p] > R(0) ? Wl[p][c] : Wr[p][c];
-          d_ += up * Wc[p][c];
-          n2 += Wc[p][c] * Wc[p][c];
+          for (int c = 0; c < M; ++c) {
+            const R up = sc[p] > R(0) ? Wl[p][c] : Wr[p][c];
+            d_ += up * Wc[p][c];
+            n2 += Wc[p][c] * Wc[p][c];
+          }
+          dot[p] = d_;
+          nrm[p] = n2;
         }
-        dot[p] = d_;
-        nrm[p] = n2;
       }
       correction<RP, R, D>(C, Wc, sc, dot, nrm, dtdn, F);
     } else {
@@ -511,20 +517,28 @@ __global__ void __launch_bounds__(32 * NW)
     }
     if (C.order == 2) {
       R dot[MW], nrm[MW];
+      constexpr int KS = strength_k<RP, 0>();
 #pragma unroll
       for (int p = 0; p < MW; ++p) {
         const bool left = s[p] > R(0);
-        R d_ = R(0), n2 = R(0);
+        if constexpr (KS >= 0) {
+          const R wl = __shfl_up_sync(0xffffffffu, W[p][KS], 1);
+          const R wr = __shfl_down_sync(0xffffffffu, W[p][KS], 1);
+          dot[p] = left ? wl : wr;
+          nrm[p] = W[p][KS];
+        } else {
+          R d_ = R(0), n2 = R(0);
 #pragma unroll
-        for (int c = 0; c < M; ++c) {
-          const R wl = __shfl_up_sync(0xffffffffu, W[p][c], 1);
-          const R wr = __shfl_down_sync(0xffffffffu, W[p][c], 1);
-          const R up = left ? wl : wr;
-          d_ += up * W[p][c];
-          n2 += W[p][c] * W[p][c];
+          for (int c = 0; c < M; ++c) {
+            const R wl = __shfl_up_sync(0xffffffffu, W[p][c], 1);
+            const R wr = __shfl_down_sync(0xffffffffu, W[p][c], 1);
+            const R up = left ? wl : wr;
+            d_ += up * W[p][c];
+            n2 += W[p][c] * W[p][c];
+          }
+          dot[p] = d_;
+          nrm[p] = n2;
         }
-        dot[p] = d_;
-        nrm[p] = n2;
       }
       correction<RP, R, 0>(C, W, s, dot, nrm, dtdn, F);
     } else {

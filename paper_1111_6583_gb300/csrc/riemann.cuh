@@ -78,6 +78,11 @@ __device__ __forceinline__ bool lt0(R x) {
 // neither positive nor negative here
 __device__ __forceinline__ bool gt0(float x) { return x > 0.f; }
 __device__ __forceinline__ bool lt0(float x) { return x < 0.f; }
+// x is +0 or -0
+__device__ __forceinline__ bool zero_mag(double x) {
+  return (fbits(x) & 0x7fffffffffffffffLL) == 0;
+}
+__device__ __forceinline__ bool zero_mag(float x) { return x == 0.f; }
 // larger of two non-negative values (or NaNs with clear sign bit, which win:
 // their bit patterns lie above +inf)
 template <typename R>
@@ -149,6 +154,9 @@ struct RpAdvection {
   struct NZ : AllNZ {};
   static constexpr bool FWAVE = false;
   static constexpr int WALL_X = -1, WALL_Y = -1;
+  // the wave is the jump itself: its one component is its strength
+  template <int DIR>
+  __host__ __device__ static constexpr int strength() { return 0; }
   template <int DIR>
   __device__ static __forceinline__ void solve(const MConsts<R>& C, const R (&ql)[M],
                                                const R (&qr)[M], const R*, const R*,
@@ -207,6 +215,10 @@ struct RpAcoustics {
   // speeds -c < 0 < c (rho, K > 0 are checked on the host)
   static constexpr bool SIGNED_WAVES = true;
   static constexpr int WALL_X = 1, WALL_Y = (ND == 2) ? 2 : -1;
+  // W^1 = a1 (-Z, 1), W^2 = a2 (Z, 1) in (p, u_n): the normal velocity
+  // component of each wave is its strength
+  template <int DIR>
+  __host__ __device__ static constexpr int strength() { return Dirs<ND, DIR>::n; }
   template <int DIR>
   __device__ static __forceinline__ void solve(const MConsts<R>& C, const R (&ql)[M],
                                                const R (&qr)[M], const R*, const R*,
@@ -1187,6 +1199,28 @@ template <class RP>
 struct signed_waves<RP, decltype((void)RP::SIGNED_WAVES, void())> {
   static constexpr bool value = RP::SIGNED_WAVES && RP::MW == 2;
 };
+// Systems whose waves of each family are multiples of one fixed vector
+// (constant-coefficient advection and acoustics): W^p = alpha_p r^p, so the
+// limiter's ratio (W^p_up . W^p) / (W^p . W^p) is alpha_p,up / alpha_p, the
+// ratio of any one component that r^p does not zero.  RP::strength<DIR>()
+// names such a component; the kernels then hand `correction` that component
+// of the upwind wave and of the wave itself in place of the dot product and
+// the norm (a signed value, zero exactly when the wave is).  Other solvers
+// give -1.
+template <class RP, class = void>
+struct has_strength {
+  static constexpr bool value = false;
+};
+template <class RP>
+struct has_strength<RP, decltype((void)RP::template strength<0>(), void())> {
+  static constexpr bool value = true;
+};
+template <class RP, int DIR>
+__host__ __device__ constexpr int strength_k() {
+  if constexpr (has_strength<RP>::value) return RP::template strength<DIR>();
+  else return -1;
+}
+
 // sign of wave p's speed: -1, 0 or 1
 template <class RP, typename R>
 __device__ __forceinline__ R wave_sign(int p, R s) {
@@ -1239,7 +1273,9 @@ __device__ __forceinline__ R limiter_mc_fma(R th) {
 // Second-order correction at one interface (Eq. (lwflux) with limited waves):
 //   F = 1/2 sum_p c_p phi(theta_p) W^p,  c_p = |s|(1 - dt/dx |s|)   (waves)
 //                                          = sgn(s)(1 - dt/dx |s|) (f-waves)
-// dot_up[p] = W^p_upwind . W^p, nrm[p] = W^p . W^p (zero wave -> no correction).
+// dot_up[p] = W^p_upwind . W^p, nrm[p] = W^p . W^p (zero wave -> no correction);
+// for the solvers with wave strengths (strength_k >= 0) the strength
+// component of W^p_upwind and of W^p (same ratio, nrm[p] signed).
 // theta_p = dot_up[p] / nrm[p]; with three or more waves, when every partial
 // product of the norms is a normal number, the reciprocals come from one
 // division (1/n_p = prod_{q != p} n_q / prod_q n_q).  DIR selects the
@@ -1252,6 +1288,7 @@ __device__ __forceinline__ void correction(const MConsts<R>& C, const R (&W)[RP:
                                            const R (&nrm)[RP::MW], R dtdn, R (&F)[RP::M]) {
   using NZ = typename RP::template NZ<DIR>;
   constexpr int MW = RP::MW;
+  static_assert(strength_k<RP, DIR>() < 0 || MW <= 2, "signed strengths: no batched reciprocal");
   const int lim = LIMC >= 0 ? LIMC : C.lim;
 #pragma unroll
   for (int k = 0; k < RP::M; ++k) F[k] = R(0);
@@ -1307,7 +1344,7 @@ __device__ __forceinline__ void correction(const MConsts<R>& C, const R (&W)[RP:
 #pragma unroll
   for (int p = 0; p < MW; ++p) {
     R phi;
-    if (fbits(nrm[p]) == 0) phi = R(0);
+    if (zero_mag(nrm[p])) phi = R(0);
     else if (lim == CLAW_LIM_NONE) phi = R(1);
     else {
       const R th = batched ? dot_up[p] * inv[p] : FM<R>::div(dot_up[p], nrm[p]);
