@@ -1344,7 +1344,8 @@ __device__ __forceinline__ void correction(const MConsts<R>& C, const R (&W)[RP:
 #pragma unroll
   for (int p = 0; p < MW; ++p) {
     R phi;
-    if (zero_mag(nrm[p])) phi = R(0);
+    // a norm is never -0; a signed strength may be
+    if (strength_k<RP, DIR>() >= 0 ? zero_mag(nrm[p]) : fbits(nrm[p]) == 0) phi = R(0);
     else if (lim == CLAW_LIM_NONE) phi = R(1);
     else {
       const R th = batched ? dot_up[p] * inv[p] : FM<R>::div(dot_up[p], nrm[p]);
