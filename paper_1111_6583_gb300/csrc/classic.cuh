@@ -650,6 +650,8 @@ __global__ void __launch_bounds__(BW)
   constexpr int NP = RP::NPC > 0 ? RP::NPC : 1;
   using NZX = typename RP::template NZ<0>;
   using NZY = typename RP::template NZ<1>;
+  // limiter ratios from wave strengths where the solver has them
+  constexpr int KSX = strength_k<RP, 0>(), KSY = strength_k<RP, 1>();
   constexpr int TX = BW - 4;
   // neighbour contributions: systems of up to three fields publish the raw
   // vectors (the receiver multiplies and adds them, saving the sender's pass
@@ -761,15 +763,21 @@ __global__ void __launch_bounds__(BW)
         solve_cells<RP, 1, R, NP>(C, qm1, qc, pm1, pcc, nW, ns, nam, nap, nx_);
 #pragma unroll
         for (int p = 0; p < MW; ++p) {
-          R a = R(0), b = R(0);
+          if constexpr (KSY >= 0) {
+            // wave strengths: the new interface's strength serves as its
+            // "norm" and as the upper neighbour's term of interface Rw-1
+            nnrm[p] = ndot[p] = nW[p][KSY];
+          } else {
+            R a = R(0), b = R(0);
 #pragma unroll
-          for (int k = 0; k < M; ++k) {
-            if (!NZY::f(p, k)) continue;
-            a += nW[p][k] * nW[p][k];
-            b += nW[p][k] * yW[p][k];
+            for (int k = 0; k < M; ++k) {
+              if (!NZY::f(p, k)) continue;
+              a += nW[p][k] * nW[p][k];
+              b += nW[p][k] * yW[p][k];
+            }
+            nnrm[p] = a;
+            ndot[p] = b;
           }
-          nnrm[p] = a;
-          ndot[p] = b;
         }
         if (col_in && Rw >= r0 && Rw <= rend + 1) {
 #pragma unroll
@@ -814,15 +822,20 @@ __global__ void __launch_bounds__(BW)
 #pragma unroll
           for (int p = 0; p < MW; ++p) {
             const int lu = gt0(xs[p]) ? l - 1 : l + 1;
-            R a = R(0), b = R(0);
+            if constexpr (KSX >= 0) {
+              dot[p] = xws[p][KSX][lu];
+              nrm[p] = xW[p][KSX];
+            } else {
+              R a = R(0), b = R(0);
 #pragma unroll
-            for (int k = 0; k < M; ++k) {
-              if (!NZX::f(p, k)) continue;
-              b += xws[p][k][lu] * xW[p][k];
-              a += xW[p][k] * xW[p][k];
+              for (int k = 0; k < M; ++k) {
+                if (!NZX::f(p, k)) continue;
+                b += xws[p][k][lu] * xW[p][k];
+                a += xW[p][k] * xW[p][k];
+              }
+              dot[p] = b;
+              nrm[p] = a;
             }
-            dot[p] = b;
-            nrm[p] = a;
           }
           correction<RP, R, 0, LIMC>(C, xW, xs, dot, nrm, dtdx, F);
         } else {
@@ -993,8 +1006,14 @@ __global__ void __launch_bounds__(BW)
 #pragma unroll
         for (int p = 0; p < MW; ++p) {
           ys[p] = ns[p];
-          ynrm[p] = nnrm[p];
-          ydot[p] = ndot[p];
+          if constexpr (KSY >= 0) {
+            // the lower neighbour's strength of the next interface to limit
+            ydot[p] = ynrm[p];
+            ynrm[p] = nnrm[p];
+          } else {
+            ynrm[p] = nnrm[p];
+            ydot[p] = ndot[p];
+          }
 #pragma unroll
           for (int k = 0; k < M; ++k) yW[p][k] = nW[p][k];
         }
