@@ -158,6 +158,10 @@ struct RpAdvection {
   template <int DIR>
   __host__ __device__ static constexpr int strength() { return 0; }
   template <int DIR>
+  __device__ static __forceinline__ void wave_of(const MConsts<R>&, int, R al, R (&w)[M]) {
+    w[0] = al;
+  }
+  template <int DIR>
   __device__ static __forceinline__ void solve(const MConsts<R>& C, const R (&ql)[M],
                                                const R (&qr)[M], const R*, const R*,
                                                R (&W)[MW][M], R (&s)[MW], R (&am)[M],
@@ -219,6 +223,15 @@ struct RpAcoustics {
   // component of each wave is its strength
   template <int DIR>
   __host__ __device__ static constexpr int strength() { return Dirs<ND, DIR>::n; }
+  // the wave of family p with strength al (normal velocity al)
+  template <int DIR>
+  __device__ static __forceinline__ void wave_of(const MConsts<R>& C, int p, R al, R (&w)[M]) {
+    constexpr int n = Dirs<ND, DIR>::n;
+#pragma unroll
+    for (int k = 0; k < M; ++k) w[k] = R(0);
+    w[0] = (p == 0 ? -C.aco_Z : C.aco_Z) * al;
+    w[n] = al;
+  }
   template <int DIR>
   __device__ static __forceinline__ void solve(const MConsts<R>& C, const R (&ql)[M],
                                                const R (&qr)[M], const R*, const R*,
@@ -1270,6 +1283,31 @@ __device__ __forceinline__ R limiter_mc_fma(R th) {
   return a * th + c;
 }
 
+// phi(theta) a for theta = u / a without the division: phi vanishes for
+// theta <= 0, and for same-signed u and a each limiter's phi(u/a) a is
+// sgn(a) g(|u|, |a|) (identities of the limiter functions; the rounding
+// differs from forming theta first):
+//   minmod   min(|u|, |a|)
+//   superbee max(min(2|u|, |a|), min(|u|, 2|a|))
+//   MC       min(|a + u| / 2, 2|a|, 2|u|)
+//   van Leer 2 |u| |a| / (|u| + |a|)
+//   none     a
+template <typename R>
+__device__ __forceinline__ R limited_strength(int lim, R u, R a) {
+  if (lim == CLAW_LIM_NONE) return a;
+  const bool same = (gt0(u) && gt0(a)) || (lt0(u) && lt0(a));
+  const R au = fabs(u), aa = fabs(a);
+  R g;
+  switch (lim) {
+    case CLAW_LIM_MINMOD: g = fmin(au, aa); break;
+    case CLAW_LIM_SUPERBEE: g = fmax(fmin(R(2) * au, aa), fmin(au, R(2) * aa)); break;
+    case CLAW_LIM_VANLEER: g = FM<R>::div(R(2) * au * aa, au + aa); break;
+    default: g = fmin(R(0.5) * fabs(a + u), fmin(R(2) * aa, R(2) * au)); break;  // MC
+  }
+  g = same ? g : R(0);
+  return lt0(a) ? -g : g;
+}
+
 // Second-order correction at one interface (Eq. (lwflux) with limited waves):
 //   F = 1/2 sum_p c_p phi(theta_p) W^p,  c_p = |s|(1 - dt/dx |s|)   (waves)
 //                                          = sgn(s)(1 - dt/dx |s|) (f-waves)
@@ -1292,6 +1330,24 @@ __device__ __forceinline__ void correction(const MConsts<R>& C, const R (&W)[RP:
   const int lim = LIMC >= 0 ? LIMC : C.lim;
 #pragma unroll
   for (int k = 0; k < RP::M; ++k) F[k] = R(0);
+  if constexpr (strength_k<RP, DIR>() >= 0 && !RP::FWAVE && sizeof(R) == 8) {
+    // FP64 wave strengths: the limited strength phi_p a_p by the
+    // division-free forms (no IEEE division on the FP64 pipe), then its wave
+    // phi_p W^p from the solver's eigenvector.  FP32 keeps theta = u / a:
+    // its division is one approximate reciprocal, cheaper than the selects.
+#pragma unroll
+    for (int p = 0; p < MW; ++p) {
+      const R al = limited_strength<R>(lim, dot_up[p], nrm[p]);
+      const R a = fabs(s[p]);
+      const R cf = R(0.5) * a * (R(1) - dtdn * a);
+      R w[RP::M];
+      RP::template wave_of<DIR>(C, p, al, w);
+#pragma unroll
+      for (int k = 0; k < RP::M; ++k)
+        if (NZ::f(p, k)) F[k] += cf * w[k];
+    }
+    return;
+  }
   if constexpr (sizeof(R) == 4) {
     const R hd = R(0.5) * dtdn;
 #pragma unroll
