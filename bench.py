@@ -55,6 +55,12 @@ ACOU1D_FLOPS_PER_CELL = 90.0
 SW2D_BYTES_PER_CELL = {"fp64": 48.0, "fp32": 24.0}
 ELAST1D_BYTES_PER_CELL = {"fp64": 48.0, "fp32": 24.0}  # q read+write, aux read
 ACOU1D_BYTES_PER_CELL = {"fp64": 32.0, "fp32": 16.0}   # q read+write
+# 3D acoustics (4 fields, w bytes per value), per cell and step: the x sweep
+# reads the state and stores five face records (6 m w); the y and z sweeps
+# read the state, store two records and reduce into three, a read and a write
+# each at the DRAM (9 m w each); the update reads the state and nine records
+# and writes the state (11 m w): 35 m w in all
+ACOU3D_BYTES_PER_CELL = {"fp32": 35 * 4 * 4, "fp64": 35 * 4 * 8}
 # ALU peaks from unit counts and clocks (for comparison with the measured FMA
 # rate the roofline uses): 152 SMs x 2.07 GHz x 2 FLOP per FMA x FMA lanes per
 # SM per clock (FP64: 2; FP32: 128)
@@ -795,6 +801,9 @@ def summary(line):
                                   "hbm_frac": g("acoustics_1d_2p26", p, "hbm_frac"),
                                   "alu_frac": g("acoustics_1d_2p26", p, "alu_frac")}
                               for p in ("fp64", "fp32")},
+        "acoustics_3d_256": {"fp64_ms": g("acoustics_table1", "3d_fp64", "ms_per_step"),
+                             "fp32_ms": g("acoustics_table1", "3d_fp32", "ms_per_step"),
+                             "fp32_hbm_frac": g("acoustics_table1", "3d_fp32", "hbm_frac")},
         "shock_bubble_2048x1024": {p: {"ms": g("shock_bubble", p, "ms_per_step"),
                                        "alu_frac": g("shock_bubble", p, "alu_frac")}
                                    for p in ("fp64", "fp32")},
@@ -1139,6 +1148,10 @@ def main():
         ex["axisym_shock_bubble"] = ax
         at = {"2d_" + p: bench_acoustics_table1(p, 20, 3, 2, 1024) for p in ("fp64", "fp32")}
         at.update({"3d_" + p: bench_acoustics_table1(p, 5, 3, 3, 256) for p in ("fp64", "fp32")})
+        # 3D: algorithmic bytes per cell and step over the four launches
+        g3 = ACOU3D_BYTES_PER_CELL["fp32"] * 256 ** 3 / (at["3d_fp32"]["ms_per_step"] * 1e-3)
+        at["3d_fp32"]["hbm_gbs"] = g3 / 1e9
+        at["3d_fp32"]["hbm_frac"] = g3 / 1e9 / hbm
         ex["acoustics_table1"] = at
         ex["acoustics_vc_capacity"] = {p: bench_acoustics_vc(p, 10, 3) for p in ("fp64", "fp32")}
         try:
