@@ -813,9 +813,9 @@ claw_status claw_solver_create(const claw_method* m, const claw_grid* g, void* s
                  ? 1
                  : 0;
   if (s->faces) s->tuned = 1;  // no tile shapes to choose
-  s->ntiles = (s->nd == 3 || s->faces)
-                  ? (int)((cells_of(s->g) + 255) / 256)
-                  : tiles_of(m->scheme, s->nd, s->prec, s->ks.MA, (int)s->g.n[0],
+  s->ntiles = s->nd == 3 ? classic3d_update_blocks(cells_of(s->g))
+             : s->faces    ? (int)((cells_of(s->g) + 255) / 256)
+                           : tiles_of(m->scheme, s->nd, s->prec, s->ks.MA, (int)s->g.n[0],
                              (int)s->g.n[1], s->bw, s->h);
   *out = s;
   return CLAW_OK;
@@ -1360,7 +1360,7 @@ claw_status claw_batch_bind(claw_batch* b, void* const* q, const void* const* au
     if (b->nd == 3) {
       // the 3D kernels take one member; the update's blocks count the arrivals
       mb.nz = (int)g.n[2];
-      mb.ntiles = (int)((cells_of(g) + 255) / 256);
+      mb.ntiles = classic3d_update_blocks(cells_of(g));
       mb.work3 = w3p;
       w3p += b->work3_bytes[k];
     } else if (b->faces) {
@@ -1906,7 +1906,8 @@ claw_status claw_server_pump(claw_server* v, int steps, int* running, int* queue
       // face arrays; the update's blocks (256 cells each) count the arrivals
       r.w3bytes = req_faces_bytes(v, r.g);
       r.mem.work3 = p;
-      r.mem.ntiles = (int)((cells_of(r.g) + 255) / 256);
+      r.mem.ntiles = v->nd == 3 ? classic3d_update_blocks(cells_of(r.g))
+                                : (int)((cells_of(r.g) + 255) / 256);
     } else {
       r.mem.ntiles =
           tiles_of(v->m.scheme, v->nd, v->prec, v->ks.MA, r.mem.nx, r.mem.ny, v->bw, v->h);

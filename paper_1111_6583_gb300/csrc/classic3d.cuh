@@ -23,6 +23,7 @@
 // solves bit for bit.
 #pragma once
 
+#include "kernels.h"
 #include "riemann.cuh"
 
 namespace claw {
@@ -642,15 +643,18 @@ __global__ void __launch_bounds__(256)
   if (s_done) return;
   const int nx = mb.nx, ny = mb.ny, nz = mb.nz;
   const long long ncell = (long long)nx * ny * nz;
-  const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   int bad = 0;
-  if (id < ncell) {
+  const R* __restrict__ q = (const R*)mb.q[s_cur];
+  R* __restrict__ qo = (R*)mb.q[(s_cur + 1) % s_nbuf];
+  const R* __restrict__ work = (const R*)mb.work3;
+  Faces3 L;
+  faces3_layout(nx, ny, nz, M, L);
+  // kUpdateCells3d cells per block, consecutive threads on consecutive cells
+#pragma unroll
+  for (int u = 0; u < kUpdateCells3d / 256; ++u) {
+    const long long id = (long long)blockIdx.x * kUpdateCells3d + u * 256 + threadIdx.x;
+    if (id >= ncell) break;
     const int i = (int)(id % nx), j = (int)((id / nx) % ny), k = (int)(id / ((long long)nx * ny));
-    const R* __restrict__ q = (const R*)mb.q[s_cur];
-    R* __restrict__ qo = (R*)mb.q[(s_cur + 1) % s_nbuf];
-    const R* __restrict__ work = (const R*)mb.work3;
-    Faces3 L;
-    faces3_layout(nx, ny, nz, M, L);
     R v[M];
 #pragma unroll
     for (int c = 0; c < M; ++c) v[c] = q[(size_t)c * ncell + id];

@@ -126,6 +126,13 @@ __host__ __device__ inline int sharp_tiles(int nx, int ny, int TX, int TY) {
   return ((nx + TX - 1) / TX) * ((ny + TY - 1) / TY);
 }
 
+// 3D update: cells per block (256 threads, four cells each); the update's
+// blocks count the arrivals for the controller
+constexpr int kUpdateCells3d = 1024;
+inline int classic3d_update_blocks(long long cells) {
+  return (int)((cells + kUpdateCells3d - 1) / kUpdateCells3d);
+}
+
 inline size_t classic3d_work_bytes(int nx, int ny, int nz, int M, int prec) {
   size_t faces = (size_t)(nx + 1) * ny * nz + (size_t)nx * (ny + 1) * nz + (size_t)nx * ny * (nz + 1);
   return faces * 3 * M * (prec == 0 ? 8 : 4);
