@@ -96,6 +96,27 @@ def test_classic2d_fixed_dt_fp64(orc, rp, order, transverse):
         assert info["cfl"] == pytest.approx(co[-1], rel=1e-13)
 
 
+@pytest.mark.parametrize("rp", ["acoustics", "advection"])
+@pytest.mark.parametrize("lim", ["minmod", "superbee", "vanleer", "none"])
+def test_classic2d_wave_strength_limiters(orc, rp, lim):
+    """The constant-coefficient solvers limit by wave strengths (FP64: the
+    division-free forms of phi(u/a) a); every limiter in 2D and in 3D, FP64
+    against the oracle's dot-product form, FP32 against it too."""
+    spec = _spec2d(rp, 131, 70, lim=lim)
+    dt = 0.25 / 131
+    qo, co = oracle_fixed_steps(orc, spec, dt, 4)
+    qg, cg = gpu_fixed_steps(spec, "fp64", dt, 4)
+    assert rel_maxnorm(qg, qo) <= FP64_TOL
+    assert np.allclose(cg, co, rtol=1e-13, atol=0)
+    q32, _ = gpu_fixed_steps(spec, "fp32", dt, 4)
+    assert rel_maxnorm(q32, qo) <= FP32_SMOOTH_TOL
+    spec = wl.random_3d(rp, 30, 17, 13, bc="wall", lim=lim)
+    dt = 0.2 / 30
+    qo, _ = oracle_fixed_steps(orc, spec, dt, 3)
+    qg, _ = gpu_fixed_steps(spec, "fp64", dt, 3)
+    assert rel_maxnorm(qg, qo) <= FP64_TOL
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("rp,nx,ny", [("sw_roe", 131, 70), ("euler_roe", 250, 61),
                                        ("sw_roe", 372, 33), ("acoustics", 113, 57),
