@@ -260,6 +260,13 @@ __global__ void __launch_bounds__(NT, (sizeof(R) == 4 && RP::M <= 2) ? (K >= 8 ?
   static_assert(NCR * sizeof(R) == sizeof(Cell), "Cell holds values of type R only");
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;  // warp in block
+  // Launched as a programmatic dependent of the previous attempt (single-unit
+  // launches of small grids): wait until that launch has completed and its
+  // memory is visible, then let the next attempt's launch begin (its blocks
+  // wait here in turn), so that launch latency overlaps this attempt.  For a
+  // launch without the attribute both return at once.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
   // staged form: the ring, and the warp's producer cursor (the consumer's
   // sequence of units, walked up to S units ahead)

@@ -258,9 +258,22 @@ struct Launchers {
       if (whole)
         kt<<<persistent_grid<kt>(kClassic1dThreads, (a.ntiles_total + NW - 1) / NW),
              kClassic1dThreads, 0, a.stream>>>(a.members, a.tiles, a.ntiles_total, C);
-      else
-        ku<<<persistent_grid<ku>(kClassic1dThreads, a.ntiles_total), kClassic1dThreads, 0,
-             a.stream>>>(a.members, a.tiles, a.ntiles_total, C);
+      else {
+        // single units (small grids, where launch latency is the step's
+        // cost): a programmatic dependent launch on the previous attempt
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)persistent_grid<ku>(kClassic1dThreads, a.ntiles_total));
+        cfg.blockDim = dim3(kClassic1dThreads);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = a.stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        const cudaError_t el = cudaLaunchKernelEx(&cfg, ku, a.members, a.tiles, a.ntiles_total, C);
+        if (el != cudaSuccess) return el;
+      }
       const cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess || !whole) return e;  // single units run their controllers
       return launch_controllers(a.members, a.nmembers > 0 ? a.nmembers : 1, a.stream);
