@@ -4,10 +4,12 @@
 // capacity-form differencing) in 1D or 2D, and 2D solvers whose transverse
 // split needs the media of the neighbouring cells.
 //
-// One attempt = a sweep per direction (a thread per face; it loads the four
-// cells of the face's limiter stencil, solves the three faces, limits and
-// corrects the middle one, and splits its two fluctuations transversely) that
-// writes a record per face, then an update kernel (a thread per cell) that
+// One attempt = a sweep per direction that writes a record per face (y
+// faces: a thread per face loads the four cells of the face's limiter
+// stencil and solves the three faces; x faces: a warp takes 30 consecutive
+// faces of a line, solves each once and passes the neighbours' waves by
+// shuffles; then each face is limited and corrected and its two fluctuations
+// split transversely), then an update kernel (a thread per cell) that
 // gathers the records of the cell's faces and of the faces whose transverse
 // pieces reach it, and whose last block runs the controller.
 //
@@ -29,6 +31,19 @@ constexpr int kFacesThreads = 256;
 __host__ __device__ inline size_t faces_count(int nd, int nx, int ny, int dir) {
   if (nd == 1) return dir == 0 ? (size_t)nx + 1 : 0;
   return dir == 0 ? (size_t)(nx + 1) * (ny + 2) : (size_t)(ny + 1) * (nx + 2);
+}
+
+// x sweep: a warp takes a chunk of 30 consecutive faces of one line (lanes
+// 1..30) and solves each of them once, plus the face below the chunk (lane 0)
+// and the one above it (lane 31) for the limiter; chunks per line
+constexpr int kFacesChunk = 30;
+__host__ __device__ inline int faces_x_chunks(int nx) {
+  return (nx + 1 + kFacesChunk - 1) / kFacesChunk;
+}
+// threads of a sweep launch
+__host__ __device__ inline size_t faces_sweep_threads(int nd, int nx, int ny, int dir) {
+  if (dir == 1) return faces_count(nd, nx, ny, 1);
+  return (size_t)32 * faces_x_chunks(nx) * (nd == 2 ? ny + 2 : 1);
 }
 
 template <class RP, typename R, int D>
@@ -58,16 +73,29 @@ __global__ void __launch_bounds__(kFacesThreads)
   const R* __restrict__ q = (const R*)step_input(mb, s_cur, s_nbuf, in_rel);
   const R* __restrict__ aux = (const R*)mb.aux;
   R smax = R(0);
-  if (id < nf) {
+  // x sweep: warp chunks (the face of lane t is 30 k - 1 + t on its line; a
+  // chunk's halo lanes may stand past the grid's last ghost face, where they
+  // load the last ghost cells and own nothing); y sweep: a thread per face
+  const int lane = threadIdx.x & 31;
+  const int cpl = faces_x_chunks(nx);
+  const long long gw = id >> 5;
+  const bool live = (D == 0) ? gw < (long long)cpl * lines : id < nf;  // warp-uniform for x
+  if (live) {
     // x-faces line by line (row r: faces 0..nx), y-faces row of faces by row
     // of faces (face row b: columns -1..nx), so that consecutive threads read
     // neighbouring cells and write neighbouring records in both sweeps
-    const int f = (D == 0) ? (int)(id % (n + 1)) : (int)(id / lines);
-    const int l = (nd == 2) ? ((D == 0) ? (int)(id / (n + 1)) : (int)(id % lines)) - 1 : 0;
+    const int fraw = (D == 0) ? (int)(gw % cpl) * kFacesChunk - 1 + lane : (int)(id / lines);
+    const int l = (nd == 2) ? ((D == 0) ? (int)(gw / cpl) : (int)(id % lines)) - 1 : 0;
+    const bool own = (D == 0) ? (lane >= 1 && lane <= kFacesChunk && fraw <= n) : true;
+    // every load below stays within the ghost layer (f <= n + 1)
+    const int f = (D == 0) ? min(fraw, n + 1) : fraw;
     const R dtdn = s_dtdn;
     R cell[4][M], au[4][MAS];
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
+      // x sweep: only the face's own two cells (its neighbours' waves come
+      // from the lanes beside it)
+      if (D == 0 && (t == 0 || t == 3)) continue;
       const int a = f - 2 + t;
       const int i = (D == 0) ? a : l, j = (D == 0) ? l : a;
       load_cell<M, R>(C, q, nx, ny, i, j, RP::WALL_X, RP::WALL_Y, cell[t]);
@@ -82,11 +110,22 @@ __global__ void __launch_bounds__(kFacesThreads)
       ikr = FM<R>::rcp(load_aux_field<R>(C, aux, nx, ny, D == 0 ? f : l, D == 0 ? l : f, C.capa));
     }
     R W[3][MW][M], s[3][MW], am[M], ap[M], x[NC], amx[M], apx[M], xx[NC];
-    RP::template solve<D>(C, cell[0], cell[1], au[0], au[1], W[0], s[0], amx, apx, xx);
     RP::template solve<D>(C, cell[1], cell[2], au[1], au[2], W[1], s[1], am, ap, x);
-    RP::template solve<D>(C, cell[2], cell[3], au[2], au[3], W[2], s[2], amx, apx, xx);
+    if constexpr (D == 0) {
+#pragma unroll
+      for (int p = 0; p < MW; ++p) {
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+          W[0][p][k] = __shfl_up_sync(0xffffffffu, W[1][p][k], 1);
+          W[2][p][k] = __shfl_down_sync(0xffffffffu, W[1][p][k], 1);
+        }
+      }
+    } else {
+      RP::template solve<D>(C, cell[0], cell[1], au[0], au[1], W[0], s[0], amx, apx, xx);
+      RP::template solve<D>(C, cell[2], cell[3], au[2], au[3], W[2], s[2], amx, apx, xx);
+    }
     // Courant number of the interior faces of interior lines
-    if (l >= 0 && l < ((nd == 2) ? nl : 1)) {
+    if (own && l >= 0 && l < ((nd == 2) ? nl : 1)) {
 #pragma unroll
       for (int p = 0; p < MW; ++p) {
         const R sp = s[1][p];
@@ -120,7 +159,7 @@ __global__ void __launch_bounds__(kFacesThreads)
     // the face's record
     const size_t NF = (size_t)nf;
     R* rec = (R*)mb.work3 + (D == 0 ? 0 : 7 * (size_t)M * faces_count(nd, nx, ny, 0));
-    const size_t fi = (size_t)id;
+    const size_t fi = (D == 0) ? (size_t)(l + (nd == 2 ? 1 : 0)) * (n + 1) + fraw : (size_t)id;
     R bma[M], bpa[M], bmb[M], bpb[M];
 #pragma unroll
     for (int k = 0; k < M; ++k) bma[k] = bpa[k] = bmb[k] = bpb[k] = R(0);
@@ -162,7 +201,7 @@ __global__ void __launch_bounds__(kFacesThreads)
       }
     }
 #pragma unroll
-    for (int k = 0; k < M; ++k) {
+    for (int k = 0; k < M && own; ++k) {
       rec[(0 * M + k) * NF + fi] = am[k];
       rec[(1 * M + k) * NF + fi] = ap[k];
       rec[(2 * M + k) * NF + fi] = F[k];

@@ -183,7 +183,7 @@ struct Launchers {
     if constexpr (ND <= 2) {
       if (uses_faces<RP, ND>(C.capa)) {
         const int nx = a.n3[0], ny = ND == 2 ? a.n3[1] : 1;
-        const size_t fx = faces_count(ND, nx, ny, 0), fy = faces_count(ND, nx, ny, 1);
+        const size_t fx = faces_sweep_threads(ND, nx, ny, 0), fy = faces_sweep_threads(ND, nx, ny, 1);
         // a.sweep: 0 unsplit; 1 / 2 the x / y sweep of a dimensionally split step
         if (a.sweep != 2)
           faces_sweep<RP, R, 0><<<(unsigned)((fx + kFacesThreads - 1) / kFacesThreads),
