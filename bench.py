@@ -1066,9 +1066,11 @@ def main():
         "config": {"workload": "2D shallow-water dam break %dx%d, classic Roe+HH, MC, "
                                "transverse 2, FP64" % (args.n, args.n),
                    "global_batch": world, "seq_len": 0, "parallelism": "replicas",
-                   "tile": {"bw": shape[0], "h": shape[1]},
-                   "l2": "flushed between timed steps (512 MB write, untimed)",
-                   "accepted_steps": accepted},
+                   "l2": "flushed between timed steps (512 MB write, untimed)"},
+        # launch shape and accepted steps beside the workload (the workload
+        # keys are the ones both arms share)
+        "tile": {"bw": shape[0], "h": shape[1]},
+        "accepted_steps": accepted,
         "gpu_launches": args.steps,
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": fp64_tf,
                      "unit": "TFLOP/s", "frac": achieved_tf / fp64_tf,
