@@ -80,6 +80,24 @@ def test_3d_x_sweep_chunks(orc, n3):
     assert rel_maxnorm(q32, qo) <= FP32_SMOOTH_TOL
 
 
+@pytest.mark.parametrize("rp", ["acoustics", "advection"])
+def test_3d_inflow_boundaries(orc, rp):
+    """Inflow faces in each direction (the ghost cells take a given state)
+    beside walls and extrapolation, over several x chunks, y blocks and z
+    segments; FP64 and FP32 against the oracle."""
+    spec = wl.random_3d(rp, 61, 12, 35, bc="extrap")
+    spec["bc_lower"] = ["inflow", "inflow", "extrap"]
+    spec["bc_upper"] = ["extrap", "wall" if rp == "acoustics" else "extrap", "inflow"]
+    spec["inflow"] = list(np.asarray(spec["q0"])[:, 0, 0, 0] * 1.05)
+    dt = 0.2 / 61
+    qo, co = oracle_fixed_steps(orc, spec, dt, 3)
+    qg, cg = gpu_fixed_steps(spec, "fp64", dt, 3)
+    assert rel_maxnorm(qg, qo) <= FP64_TOL
+    assert np.allclose(cg, co, rtol=1e-13, atol=0)
+    q32, _ = gpu_fixed_steps(spec, "fp32", dt, 3)
+    assert rel_maxnorm(q32, qo) <= FP32_SMOOTH_TOL
+
+
 def test_3d_diagonal_shift():
     n = 16
     spec = wl.random_3d("advection", n, n, n, params=[1.0, 1.0, 1.0], order=2, transverse=2)
